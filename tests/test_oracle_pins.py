@@ -1,0 +1,398 @@
+"""Pins for the CPU oracle: each check compares the oracle with something other than itself
+(the paper's worked example, its identities, closed forms, invariants, brute force).
+
+CPU only (no GPU marker)."""
+import math
+
+import numpy as np
+import pytest
+
+import tt_oracle as O
+from conftest import read_golden
+from paper_2309_08093_gb300 import synth
+
+
+def _rng(seed):
+    return np.random.default_rng(seed)
+
+
+def _rand_tables(rng, dims, J):
+    hs = [rng.integers(0, J, size=n) for n in dims]
+    vs = [rng.choice([-1.0, 1.0], size=n) for n in dims]
+    return hs, vs
+
+
+# ---------------------------------------------------------------------------------------------
+# Sec. 2.2 worked example
+
+def test_worked_example_tensorsketch_matrix():
+    g = read_golden("tensorsketch_worked_example.txt")
+    m = int(g["m"][0][0])
+    h1 = np.array([int(x) - 1 for x in g["h1"][0]])
+    h2 = np.array([int(x) - 1 for x in g["h2"][0]])
+    v1 = np.array([float(x) for x in g["v1"][0]])
+    v2 = np.array([float(x) for x in g["v2"][0]])
+    S_printed = np.array([[float(x) for x in row] for row in g["S"]])
+    Omega_printed = np.array([[float(x) for x in row] for row in g["Omega"]])
+    v_printed = np.array([float(x) for x in g["v"][0]])
+    h_printed = np.array([int(x) - 1 for x in g["h"][0]])
+    S = O.tensorsketch_matrix([h1, h2], [v1, v2], m)
+    assert np.array_equal(S, S_printed)
+    assert np.array_equal(np.abs(S), Omega_printed)
+    assert np.array_equal(S.sum(axis=0), v_printed)
+    assert np.array_equal(np.argmax(np.abs(S), axis=0), h_printed)
+
+
+def test_worked_example_through_data_sketch():
+    """A 2 x 2 x 1 tensor sketched along its last (singleton) mode: Y = S vec(A)."""
+    g = read_golden("tensorsketch_worked_example.txt")
+    S_printed = np.array([[float(x) for x in row] for row in g["S"]])
+    hs = [np.array([0, 1]), np.array([0, 1]), np.array([0])]
+    vs = [np.array([1.0, -1.0]), np.array([-1.0, 1.0]), np.array([1.0])]
+    A = np.asfortranarray(np.arange(1.0, 5.0).reshape(2, 2, 1, order="F"))
+    Y = O.sketch_unfolding(A, hs, vs, 2, 2)
+    assert np.array_equal(Y[:, 0], S_printed @ A.ravel(order="F"))
+
+
+# ---------------------------------------------------------------------------------------------
+# hash / sign draws
+
+def test_splitmix64_published_vector():
+    g = read_golden("splitmix64_vectors.txt")
+    seed = int(g["seed"][0][0])
+    expect = [int(x) for x in g["out"][0]]
+    assert O.splitmix64_sequence(seed, 3) == expect
+
+
+def test_hash_words_match_python_integers():
+    """numpy uint64 wrapping arithmetic vs exact Python integers mod 2^64."""
+    M = (1 << 64) - 1
+
+    def mix(z):
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M
+        return z ^ (z >> 31)
+
+    def word(seed, sweep, mode, stream, i):
+        z = seed
+        for f in (sweep, mode, stream, i):
+            z = mix((z + (f + 1) * 0x9E3779B97F4A7C15) & M)
+        return z
+
+    idx = np.arange(50)
+    got = O.hash_words(987654321123, 7, 3, 1, idx)
+    assert [int(x) for x in got] == [word(987654321123, 7, 3, 1, int(i)) for i in idx]
+
+
+def test_hash_tables_distribution():
+    """h_k uniform on [0, J) and v_k balanced (chi-square / binomial bounds)."""
+    J, n = 64, 64 * 400
+    hs, vs = O.draw_sketch(12345, 0, [n], J)
+    counts = np.bincount(hs[0], minlength=J)
+    chi2 = ((counts - n / J) ** 2 / (n / J)).sum()
+    assert chi2 < J + 6 * math.sqrt(2 * J)  # ~6 sigma above the mean of chi2(J-1)
+    assert abs(vs[0].sum()) < 6 * math.sqrt(n)
+    # pairwise: h(i) and h(i+1) independent -> joint counts on a 8x8 grid close to uniform
+    a, b = hs[0][:-1] % 8, hs[0][1:] % 8
+    joint = np.bincount(a * 8 + b, minlength=64)
+    e = (n - 1) / 64
+    assert ((joint - e) ** 2 / e).sum() < 64 + 6 * math.sqrt(128)
+
+
+def test_hash_tables_change_with_sweep_and_mode():
+    h_a, v_a = O.draw_sketch(5, 0, [100, 100], 4096)
+    h_b, v_b = O.draw_sketch(5, 1, [100, 100], 4096)
+    assert not np.array_equal(h_a[0], h_b[0])
+    assert not np.array_equal(h_a[0], h_a[1])
+    assert np.all((h_a[0] >= 0) & (h_a[0] < 4096))
+    assert set(np.unique(v_a[0])) <= {-1.0, 1.0}
+
+
+# ---------------------------------------------------------------------------------------------
+# unfoldings and the TT format
+
+def test_unfold_matches_index_formula():
+    A = synth.random_tensor((3, 4, 2, 5), 1)
+    for k in range(4):
+        Ak = O.unfold(A, k)
+        others = [s for s in range(4) if s != k]
+        for idx in np.ndindex(A.shape):
+            j, stride = 0, 1
+            for s in others:
+                j += idx[s] * stride
+                stride *= A.shape[s]
+            assert Ak[idx[k], j] == A[idx]
+
+
+def test_tt_full_elementwise_products():
+    cores = synth.random_tt((3, 2, 4, 2), (1, 2, 3, 2, 1), 2)
+    T = O.tt_full(cores)
+    for idx in np.ndindex(T.shape):
+        p = np.ones((1, 1))
+        for k, i in enumerate(idx):
+            p = p @ cores[k][:, i, :]
+        assert abs(T[idx] - p[0, 0]) < 1e-12
+
+
+def test_interface_reproduces_unfolding():
+    """(G_{>k}^T kron G_{<k}) G_{k(2)}^T = A_(k)^T for A = [[G]] (Eq. (lrtt_sub) at zero residual)."""
+    cores = synth.random_tt((3, 4, 2, 3), (1, 2, 3, 2, 1), 3)
+    A = O.tt_full(cores)
+    for k in range(4):
+        H = O.interface_matrix(cores, k)
+        assert np.allclose(H @ O.mode2_unfold(cores[k]).T, O.unfold(A, k).T, atol=1e-12)
+        r0, n, r1 = cores[k].shape
+        assert np.array_equal(O.mode2_fold(O.mode2_unfold(cores[k]), r0, r1), cores[k])
+
+
+def test_left_right_unfold_index_formula():
+    G = synth.random_tensor((2, 3, 4), 4)
+    L, R = O.left_unfold(G), O.right_unfold(G)
+    for a, i, b in np.ndindex(G.shape):
+        assert L[a + 2 * i, b] == G[a, i, b]
+        assert R[a, i + 3 * b] == G[a, i, b]
+
+
+# ---------------------------------------------------------------------------------------------
+# part (a): Y_k = S A_(k)^T
+
+@pytest.mark.parametrize("dims,J", [((3, 4, 5), 8), ((2, 3, 2, 4), 16), ((5, 2), 4), ((4, 3, 2, 2, 3), 32)])
+def test_data_sketch_definition_vs_dense(dims, J):
+    rng = _rng(sum(dims) + J)
+    A = synth.random_tensor(dims, J)
+    hs, vs = _rand_tables(rng, dims, J)
+    for k in range(len(dims)):
+        Y = O.sketch_unfolding(A, hs, vs, J, k)
+        assert Y.shape == (J, dims[k])
+        assert np.allclose(Y, O.sketch_unfolding_dense(A, hs, vs, J, k), atol=1e-13)
+
+
+def test_data_sketch_injective_hash_is_a_transpose():
+    """With J = n_2, h_2 a permutation and v = +1, S is a permutation and Y_1 = P A^T."""
+    A = synth.random_tensor((6, 7), 11)
+    perm = np.random.default_rng(3).permutation(7)
+    Y = O.sketch_unfolding(A, [np.zeros(6, int), perm], [np.ones(6), np.ones(7)], 7, 0)
+    expect = np.zeros((7, 6))
+    expect[perm, :] = A.T
+    assert np.array_equal(Y, expect)
+
+
+# ---------------------------------------------------------------------------------------------
+# part (b): Lemma 1, Cor. 1, Cor. 2, Thm 1/2
+
+def test_lemma1_and_corollaries():
+    rng = _rng(7)
+    J = 8
+    F = O.dft_matrix(J)
+    Finv = np.linalg.inv(F)
+    dims = (3, 5, 4)
+    hs, vs = _rand_tables(rng, dims, J)
+    S1 = O.countsketch_matrix(hs[0], vs[0], J)
+    S2 = O.countsketch_matrix(hs[1], vs[1], J)
+    S3 = O.countsketch_matrix(hs[2], vs[2], J)
+    # Lemma 1
+    S12 = O.tensorsketch_matrix(hs[:2], vs[:2], J)
+    assert np.allclose(S12, Finv @ O.face_split(F @ S2, F @ S1), atol=1e-12)
+    # Corollary 1 (three factors)
+    S123 = O.tensorsketch_matrix(hs, vs, J)
+    assert np.allclose(S123, Finv @ O.face_split(O.face_split(F @ S3, F @ S2), F @ S1), atol=1e-12)
+    # Corollary 2: S (B kron A) = F^{-1}[(F S2 B) [] (F S1 A)]
+    A = rng.standard_normal((3, 2))
+    B = rng.standard_normal((5, 3))
+    assert np.allclose(S12 @ np.kron(B, A), Finv @ O.face_split(F @ S2 @ B, F @ S1 @ A), atol=1e-12)
+
+
+def test_mixed_product_rule():
+    rng = _rng(8)
+    A, B = rng.standard_normal((3, 2)), rng.standard_normal((4, 5))
+    C, D = rng.standard_normal((6, 3)), rng.standard_normal((6, 4))
+    assert np.allclose(O.face_split(D, C) @ np.kron(B, A), O.face_split(D @ B, C @ A), atol=1e-12)
+
+
+@pytest.mark.parametrize("dims,ranks,J", [((3, 4, 2), (1, 2, 3, 1), 8), ((2, 3, 4, 3), (1, 2, 2, 3, 1), 16),
+                                          ((4, 2, 3, 2, 3), (1, 3, 2, 2, 2, 1), 16), ((5, 4), (1, 3, 1), 4)])
+def test_interface_sketch_three_routes(dims, ranks, J):
+    rng = _rng(len(dims) * 31 + J)
+    cores = synth.random_tt(dims, ranks, J)
+    hs, vs = _rand_tables(rng, dims, J)
+    for k in range(len(dims)):
+        dense = O.sketch_interface_dense(cores, hs, vs, J, k)
+        conv = O.sketch_interface_conv(cores, hs, vs, J, k)
+        fft = O.sketch_interface_fft(cores, hs, vs, J, k)
+        assert dense.shape == (J, ranks[k] * ranks[k + 1])
+        assert np.allclose(conv, dense, atol=1e-12)
+        assert np.allclose(fft, dense, atol=1e-12)
+
+
+def test_interface_sketch_conv_vs_fft_medium():
+    dims, ranks, J = (20, 30, 25, 10), (1, 4, 5, 3, 1), 256
+    cores = synth.random_tt(dims, ranks, 9)
+    hs, vs = O.draw_sketch(99, 0, dims, J)
+    for k in range(4):
+        a = O.sketch_interface_conv(cores, hs, vs, J, k)
+        b = O.sketch_interface_fft(cores, hs, vs, J, k)
+        assert np.linalg.norm(a - b) <= 1e-12 * np.linalg.norm(a)
+
+
+def test_data_sketch_of_tt_tensor_equals_interface_sketch():
+    """For A = [[G]]: S A_(k)^T = (S H_k) G_{k(2)}^T, linking parts (a) and (b)."""
+    dims, ranks, J = (6, 5, 7, 4), (1, 3, 2, 3, 1), 32
+    cores = synth.random_tt(dims, ranks, 12)
+    A = O.tt_full(cores)
+    hs, vs = O.draw_sketch(4, 2, dims, J)
+    for k in range(4):
+        Y = O.sketch_unfolding(A, hs, vs, J, k)
+        SH = O.sketch_interface_fft(cores, hs, vs, J, k)
+        assert np.allclose(Y, SH @ O.mode2_unfold(cores[k]).T, atol=1e-10)
+
+
+# ---------------------------------------------------------------------------------------------
+# part (c): Eq. (ite)
+
+def test_prox_update_vs_augmented_least_squares():
+    rng = _rng(21)
+    J, n, r0, r1 = 40, 7, 3, 4
+    Y = rng.standard_normal((J, n))
+    SH = rng.standard_normal((J, r0 * r1))
+    G = rng.standard_normal((r0, n, r1))
+    for sigma in (1e-3, 0.5, 3.0):
+        a = O.prox_update(Y, SH, G, sigma)
+        b = O.prox_update_augmented(Y, SH, G, sigma)
+        assert np.allclose(a, b, atol=1e-10)
+
+
+def test_prox_update_sigma_zero_is_least_squares():
+    rng = _rng(22)
+    Y, SH = rng.standard_normal((30, 5)), rng.standard_normal((30, 6))
+    G = rng.standard_normal((2, 5, 3))
+    X, *_ = np.linalg.lstsq(SH, Y, rcond=None)
+    assert np.allclose(O.mode2_unfold(O.prox_update(Y, SH, G, 0.0)), X.T, atol=1e-10)
+
+
+def test_prox_update_sigma_zero_singular_raises():
+    Y = np.ones((4, 2))
+    SH = np.zeros((4, 3))
+    with pytest.raises(O.NotSPD):
+        O.prox_update(Y, SH, np.zeros((1, 2, 3)), 0.0)
+
+
+def test_identity_sketch_reduces_to_exact_prox_als():
+    """m = prod_{i!=k} n_i, injective hash, v = +1: S is a permutation, so (ite) equals the exact
+    proximal update of Eq. (lrtt_sub_prox)."""
+    dims, ranks = (3, 4, 2), (1, 2, 2, 1)
+    cores = synth.random_tt(dims, ranks, 5)
+    A = synth.random_tensor(dims, 6)
+    k, sigma = 1, 0.3
+    J = dims[0] * dims[2]
+    hs = [np.arange(3), np.zeros(4, int), np.arange(2) * 3]  # h_0(i)+h_2(j) = i + 3 j: a bijection
+    vs = [np.ones(3), np.ones(4), np.ones(2)]
+    Y = O.sketch_unfolding(A, hs, vs, J, k)
+    SH = O.sketch_interface_dense(cores, hs, vs, J, k)
+    got = O.prox_update(Y, SH, cores[k], sigma)
+    H = O.interface_matrix(cores, k)
+    X = np.linalg.solve(H.T @ H + sigma * np.eye(4), (O.unfold(A, k) @ H + sigma * O.mode2_unfold(cores[k])).T)
+    assert np.allclose(O.mode2_unfold(got), X.T, atol=1e-12)
+
+
+# ---------------------------------------------------------------------------------------------
+# orthogonalisation
+
+@pytest.mark.parametrize("shape", [(12, 4), (5, 5), (3, 7)])
+def test_qr_nonneg(shape):
+    M = _rng(sum(shape)).standard_normal(shape)
+    Q, R = O.qr_nonneg(M)
+    assert np.allclose(Q @ R, M, atol=1e-12)
+    assert np.allclose(np.triu(R), R)
+    assert np.all(np.diag(R) >= 0)
+    m, n = shape
+    q = min(m, n)
+    assert np.allclose(Q[:, :q].T @ Q[:, :q], np.eye(q), atol=1e-12)
+    assert Q.shape == (m, n) and R.shape == (n, n)
+
+
+def test_orthogonalization_invariants():
+    cores = synth.random_tt((4, 5, 3, 6), (1, 3, 4, 3, 1), 13)
+    T = O.tt_full(cores)
+    oc = O.orthogonalize_right_to_left(cores)
+    assert np.allclose(O.tt_full(oc), T, atol=1e-10 * np.abs(T).max())
+    for k in range(1, 4):
+        R = O.right_unfold(oc[k])
+        assert np.allclose(R @ R.T, np.eye(R.shape[0]), atol=1e-12)
+    # ||[[G]]|| lives in the first core after right-to-left orthogonalisation
+    assert abs(np.linalg.norm(oc[0].ravel()) - np.linalg.norm(T.ravel())) < 1e-10 * np.linalg.norm(T.ravel())
+    oc2 = list(oc)
+    O.left_orthogonalize_step(oc2, 0)
+    L = O.left_unfold(oc2[0])
+    assert np.allclose(L.T @ L, np.eye(L.shape[1]), atol=1e-12)
+    assert np.allclose(O.tt_full(oc2), T, atol=1e-10 * np.abs(T).max())
+
+
+# ---------------------------------------------------------------------------------------------
+# whole method
+
+def test_exact_tt_is_a_fixed_point():
+    """If A = [[G*]] then G* is a fixed point of Eq. (ite) for any sigma (Y = S H G*^T)."""
+    dims, ranks = (6, 7, 5, 6), (1, 3, 3, 2, 1)
+    cores = synth.random_tt(dims, ranks, 14)
+    A = O.tt_full(cores)
+    for sigma in (0.0, 0.5):
+        new, rc = O.tt_ts_sweep(A, cores, 77, 0, 64, sigma)
+        assert O.rel_error(A, new) < 1e-11
+        assert rc < 1e-10
+
+
+def test_exact_recovery_from_random_init():
+    dims, ranks = (8, 9, 7, 8), (1, 3, 3, 3, 1)
+    A = O.tt_full(synth.random_tt(dims, ranks, 15))
+    init = synth.random_tt(dims, ranks, 16)
+    cores, ch = O.tt_ts(A, init, 31, 128, 1e-3, 30)
+    assert O.rel_error(A, cores) < 1e-8
+
+
+def test_unsketched_prox_als_monotone_and_vs_ttsvd():
+    dims, ranks = (6, 7, 6, 5), (1, 3, 4, 3, 1)
+    rng = np.random.default_rng(17)
+    A = synth.add_noise(O.tt_full(synth.random_tt(dims, ranks, 17)), 0.05, rng)
+    svd_cores = O.tt_svd(A, ranks)
+    e_svd = O.rel_error(A, svd_cores)
+    cores = svd_cores
+    errs = [e_svd]
+    for _ in range(6):
+        cores = O.prox_als_sweep(A, cores, 0.1)
+        errs.append(O.rel_error(A, cores))
+    assert all(errs[i + 1] <= errs[i] + 1e-12 for i in range(len(errs) - 1))
+    # TT-SVD quasi-optimality: e_svd <= sqrt(d-1) * e_best <= sqrt(d-1) * e_als
+    assert e_svd <= math.sqrt(len(dims) - 1) * errs[-1] + 1e-12
+
+
+def test_ttsvd_exact_on_tt_tensor():
+    dims, ranks = (5, 6, 4, 3), (1, 2, 3, 2, 1)
+    A = O.tt_full(synth.random_tt(dims, ranks, 18))
+    assert O.rel_error(A, O.tt_svd(A, ranks)) < 1e-12
+
+
+def test_sketched_gram_unbiased():
+    """E_S[(S H)^T (S H)] = H^T H (TensorSketch preserves inner products in expectation)."""
+    dims, ranks, J = (4, 5, 3), (1, 2, 2, 1), 16
+    cores = synth.random_tt(dims, ranks, 19)
+    k = 1
+    H = O.interface_matrix(cores, k)
+    acc = np.zeros((4, 4))
+    acc2 = np.zeros((4, 4))
+    T = 600
+    for t in range(T):
+        hs, vs = O.draw_sketch(1000 + t, 0, dims, J)
+        SH = O.sketch_interface_fft(cores, hs, vs, J, k)
+        G = SH.T @ SH
+        acc += G
+        acc2 += G * G
+    mean = acc / T
+    sd = np.sqrt(np.maximum(acc2 / T - mean ** 2, 0) / T)
+    assert np.all(np.abs(mean - H.T @ H) <= 5 * sd + 1e-9)
+
+
+def test_rel_error_closed_forms():
+    cores = synth.random_tt((3, 4, 5), (1, 2, 2, 1), 20)
+    T = O.tt_full(cores)
+    assert O.rel_error(T, cores) < 1e-14
+    assert abs(O.rel_error(2 * T, cores) - 0.5) < 1e-14
