@@ -1,0 +1,172 @@
+/*
+ * tt_sketch.h -- C ABI of the GB300 (sm_103a) TensorSketch proximal TT-ALS library.
+ *
+ * The library computes the hot path of Algorithm 1 (TT-TS) of Chen, Jiang, Yu, Qi,
+ * "Low-rank Tensor Train Decomposition Using TensorSketch" (arXiv 2309.08093):
+ *   (a) the TensorSketch of the data unfolding, Y_k = S A_(k)^T           (Alg. 1, Sec. 3)
+ *   (b) the FFT TensorSketch of the TT interface matrix, S H_k            (Theorems 1 and 2)
+ *   (c) the proximal normal-equation update of core k                     (Eq. (ite), Sec. 3)
+ * plus the orthogonalisation steps of Algorithm 1 and the relative error of Sec. 5.
+ *
+ * Conventions (0-based; the paper is 1-based):
+ *   - tensor A has d modes of sizes n[0..d-1] and is stored densely with mode 0 fastest
+ *     (linear index i = sum_s i_s prod_{t<s} n_t, the bijection of Sec. 2.2);
+ *   - TT core k has shape r[k] x n[k] x r[k+1] and is stored FP32 with r[k] fastest
+ *     (element (a, i, b) at a + r[k]*(i + n[k]*b)); r[0] = r[d] = 1 (Sec. 2.1);
+ *   - Y_k (sketch of the mode-k unfolding) is FP32, J x n[k], row-major: Y_k[b*n[k] + i];
+ *   - S H_k is FP32, J x s_k with s_k = r[k]*r[k+1], column-major: SH[b + J*c] with column
+ *     c = a + r[k]*b' (a indexes r[k], b' indexes r[k+1]; matches G_{k(2)}, Sec. 3).
+ *   - The sketch size m of the paper is J; J must be a power of two, 2 <= J <= 16384.
+ *
+ * Hash/sign draws (Sec. 2.2, Eqs. (eqn_h), (eqn_v)): per sweep t and mode k the library draws
+ *   h_k(i) = word(seed, t, k, 0, i) mod J,  v_k(i) = 1 - 2 * (word(seed, t, k, 1, i) >> 63),
+ * where word() chains SplitMix64 output steps:  step(z, f) = mix64(z + (f+1) * 0x9E3779B97F4A7C15),
+ * word(seed, t, k, s, i) = step(step(step(step(seed, t), k), s), i), and mix64 is the SplitMix64
+ * finaliser (Steele, Lea, Flood 2014). With TT_FLAG_FIXED_SKETCH every sweep uses t = 0.
+ *
+ * Ownership: every pointer named *_dev is device memory owned by the caller; the library never
+ * frees it. Arrays of pointers (float* const* ...) are HOST arrays of d device pointers. The
+ * context owns its hash tables, plans and workspaces (allocated in tt_sketch_init).
+ *
+ * Streams: all work is enqueued on the stream given to tt_sketch_init. Calls that return host
+ * scalars (tt_prox_als_sweep with rel_change_out, tt_rel_error, tt_sketch_tables) synchronise
+ * that stream; the others are asynchronous.
+ *
+ * Errors: every int-returning call returns TT_OK (0) or a negative TT_E* code; the message of
+ * the last failure is available from tt_last_error(ctx). On error no output is guaranteed.
+ * Invalid arguments are rejected on the host before anything is launched.
+ */
+#ifndef TT_SKETCH_H
+#define TT_SKETCH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tt_ctx tt_ctx; /* opaque, library-owned */
+
+/* storage type of the data tensor A */
+enum { TT_F64 = 0, TT_F32 = 1, TT_BF16 = 2, TT_FP8E4M3 = 3 };
+
+/* status codes */
+enum {
+  TT_OK = 0,
+  TT_EINVAL = -1,      /* bad shape, rank, J, k, dtype or null pointer */
+  TT_ENOMEM = -2,      /* device or host allocation failed */
+  TT_ECUDA = -3,       /* a CUDA runtime call or kernel launch failed */
+  TT_ENOTSPD = -4,     /* the Gram matrix of Eq. (ite) is not positive definite (sigma = 0) */
+  TT_ETIMEOUT = -5,    /* a bounded device-side wait gave up */
+  TT_ENONFINITE = -6   /* a NaN or Inf reached a solve */
+};
+
+/* flags */
+#define TT_FLAG_FIXED_SKETCH 1u /* draw h_k, v_k once (t = 0) instead of once per sweep */
+
+typedef struct {
+  int d;              /* order of the tensor, 2 <= d <= 8 */
+  const int64_t* n;   /* host array of d mode sizes, each >= 1 */
+  const int* r;       /* host array of d+1 TT ranks, r[0] = r[d] = 1, each >= 1;
+                         r[k]*r[k+1] <= 256 */
+  int J;              /* sketch size m (power of two, 2..16384) */
+  double lambda;      /* proximal weight sigma >= 0 of Eq. (lrtt_sub_prox) */
+  uint64_t seed;      /* seed of the hash/sign draws */
+  int dtype;          /* TT_F64, TT_F32, TT_BF16 or TT_FP8E4M3: storage type of A */
+  unsigned flags;     /* TT_FLAG_* */
+} tt_params;
+
+/*
+ * Create a context for tensors of the given shape (Alg. 1 inputs: A's shape, TT ranks,
+ * sketch size m, sigma). `cuda_stream` is a cudaStream_t (NULL = legacy default stream).
+ * Allocates all device workspaces. Returns TT_EINVAL for inconsistent parameters.
+ */
+int tt_sketch_init(tt_ctx** out, const tt_params* p, void* cuda_stream);
+
+/* Release the context and its device memory (never the caller's buffers). NULL is a no-op. */
+void tt_sketch_destroy(tt_ctx* ctx);
+
+/* Message of the last failure on this context ("" if none). Valid until the next call. */
+const char* tt_last_error(const tt_ctx* ctx);
+
+/*
+ * Copy the hash and sign tables of sweep `sweep` (Sec. 2.2; drawn on the device) to host
+ * arrays of sum_k n[k] entries, mode 0 first: h_host[off_k + i] = h_k(i) in [0, J),
+ * v_host[off_k + i] = v_k(i) in {+1, -1}. Synchronises the stream.
+ */
+int tt_sketch_tables(tt_ctx* ctx, uint64_t sweep, int32_t* h_host, int8_t* v_host);
+
+/*
+ * Replace the drawn tables by caller-given ones (host arrays laid out as in tt_sketch_tables;
+ * h values must lie in [0, J), v values in {+1, -1}). From then on every sweep uses them, as
+ * with TT_FLAG_FIXED_SKETCH. Used to reproduce the worked example of Sec. 2.2.
+ */
+int tt_sketch_set_tables(tt_ctx* ctx, const int32_t* h_host, const int8_t* v_host);
+
+/*
+ * Part (a): Y_k = S A_(k)^T (Alg. 1, "compute S A_(k)^T"; S is the TensorSketch built from
+ * the CountSketches of all modes s != k, Eqs. (eqn_h), (eqn_v)). Every entry of A is read.
+ *   A_dev       : the dense tensor in the storage type of the context;
+ *   scales_dev  : for TT_FP8E4M3, n[0] FP32 scales (A(i) = scale[i_0] * fp8(i)); else NULL;
+ *   k           : mode in [0, d), or -1 for all modes;
+ *   sweep       : sweep index t selecting the hash draw;
+ *   Y_dev       : host array of d device pointers; Y_dev[k] (J x n[k], row-major) is written
+ *                 for each requested mode (other entries may be NULL).
+ */
+int tt_sketch_unfold(tt_ctx* ctx, const void* A_dev, const float* scales_dev, int k,
+                     uint64_t sweep, float* const* Y_dev);
+
+/*
+ * Part (b): S H_k with H_k = G_{>k}^T kron G_{<k}, computed as
+ * F^{-1}[(F S_{>k} G_{>k}^T) face-split (F S_{<k} G_{<k})] (Theorem 1) with the two factors
+ * formed by slice-wise products of the FFT-sketched cores (Theorem 2).
+ *   cores_dev : host array of d device pointers to the FP32 cores (read only);
+ *   SH_dev    : J x s_k FP32 column-major output.
+ */
+int tt_sketch_interface(tt_ctx* ctx, float* const* cores_dev, int k, uint64_t sweep,
+                        float* SH_dev);
+
+/*
+ * Part (c): the proximal update of core k by Eq. (ite) (read with S^T S):
+ *   G_{k(2)} <- (Y_k^T SH_k + sigma G_{k(2)}) (SH_k^T SH_k + sigma I)^{-1},
+ * solved through a Cholesky factorisation. Y_dev: J x n[k] row-major; SH_dev: J x s_k
+ * column-major; core_dev is read (proximal centre) and overwritten with the update.
+ * Returns TT_ENOTSPD if the Gram matrix is not positive definite (then core_dev is unchanged).
+ * Synchronises the stream (the status is read back).
+ */
+int tt_prox_update(tt_ctx* ctx, const float* Y_dev, const float* SH_dev, float* core_dev, int k);
+
+/*
+ * Orthogonalisation steps of Algorithm 1, in place on the FP32 cores (host array of device
+ * pointers). direction = -1: the right-to-left orthogonalisation of all cores (each G_k^R,
+ * k = d-1..1, gets orthonormal rows and the triangular factor moves into core k-1).
+ * direction = +1 with 0 <= k < d-1: [Q, R] = qr(G_k^L), G_k <- Q, G_{k+1} <- R G_{k+1}^R.
+ * Triangular factors have a non-negative diagonal; a wide unfolding (rows < columns) gets
+ * zero-padded factors so the ranks keep their sizes.
+ */
+int tt_orthogonalize(tt_ctx* ctx, float* const* cores_dev, int direction, int k);
+
+/*
+ * `nsweeps` outer iterations of Algorithm 1 starting at sweep index `first_sweep`: right-to-left
+ * orthogonalisation, a fresh sketch, then for k = 0..d-1 parts (b), (a), (c) and (k < d-1) the QR
+ * step. Cores are updated in place. If rel_change_out is not NULL it receives, per sweep,
+ * max_k ||G_k^(t+1) - G_k^(t)||_F / ||G_k^(t+1)||_F (Sec. 5), where G_k^(t) is core k right
+ * before its update; the call then synchronises. Returns TT_ENOTSPD if a Gram matrix is not
+ * positive definite (cores are then left as they were after the last successful update).
+ */
+int tt_prox_als_sweep(tt_ctx* ctx, const void* A_dev, const float* scales_dev,
+                      float* const* cores_dev, int nsweeps, uint64_t first_sweep,
+                      double* rel_change_out);
+
+/*
+ * Relative error ||A - [[G_1, ..., G_d]]||_F / ||A||_F (Sec. 5) with FP64 accumulation.
+ * Reads every entry of A once; synchronises and writes *out on the host.
+ */
+int tt_rel_error(tt_ctx* ctx, const void* A_dev, const float* scales_dev,
+                 float* const* cores_dev, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TT_SKETCH_H */

@@ -1,0 +1,179 @@
+// Public entry points of tt_sketch.h and the sweep driver of Algorithm 1.
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "tt_internal.cuh"
+
+static int check_data(tt_ctx* c, const void* A, const float* scales) {
+  if (!A) return tt_fail(c, TT_EINVAL, "null tensor pointer");
+  if (c->dtype == TT_FP8E4M3 && !scales) return tt_fail(c, TT_EINVAL, "FP8 storage needs n[0] slice scales");
+  if (c->dtype != TT_FP8E4M3 && scales) return tt_fail(c, TT_EINVAL, "slice scales are only used with FP8 storage");
+  return TT_OK;
+}
+
+static int check_cores(tt_ctx* c, float* const* cores) {
+  if (!cores) return tt_fail(c, TT_EINVAL, "null core array");
+  for (int k = 0; k < c->d; ++k)
+    if (!cores[k]) return tt_fail(c, TT_EINVAL, "null core pointer %d", k);
+  return TT_OK;
+}
+
+int tt_read_status(tt_ctx* c) {
+  int st = 0;
+  TT_CUDA(c, cudaMemcpyAsync(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  TT_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (st == TT_ENOTSPD) return tt_fail(c, TT_ENOTSPD, "Gram matrix of the proximal update is not positive definite");
+  if (st == TT_ENONFINITE) return tt_fail(c, TT_ENONFINITE, "non-finite value reached the proximal solve");
+  if (st != 0) return tt_fail(c, st, "device status %d", st);
+  return TT_OK;
+}
+
+static int reset_status(tt_ctx* c) {
+  TT_CUDA(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
+  return TT_OK;
+}
+
+#define TT_TRY(x)            \
+  do {                       \
+    int _rc = (x);           \
+    if (_rc) return _rc;     \
+  } while (0)
+
+extern "C" int tt_sketch_unfold(tt_ctx* c, const void* A, const float* scales, int k, uint64_t sweep,
+                                float* const* Y) {
+  if (!c) return TT_EINVAL;
+  TT_TRY(check_data(c, A, scales));
+  if (!Y) return tt_fail(c, TT_EINVAL, "null output array");
+  if (k < -1 || k >= c->d) return tt_fail(c, TT_EINVAL, "mode %d outside [-1, %d)", k, c->d);
+  for (int kk = 0; kk < c->d; ++kk)
+    if ((k == -1 || k == kk) && !Y[kk]) return tt_fail(c, TT_EINVAL, "null output for mode %d", kk);
+  c->err.clear();
+  TT_TRY(tt_ensure_tables(c, sweep));
+  for (int kk = 0; kk < c->d; ++kk)
+    if (k == -1 || k == kk) TT_TRY(tt_launch_unfold(c, A, scales, kk, Y[kk]));
+  return TT_OK;
+}
+
+static int build_all_ghat(tt_ctx* c, float* const* cores) {
+  for (int j = 0; j < c->d; ++j) TT_TRY(tt_launch_core_fft(c, cores[j], j));
+  return TT_OK;
+}
+
+extern "C" int tt_sketch_interface(tt_ctx* c, float* const* cores, int k, uint64_t sweep, float* SH) {
+  if (!c) return TT_EINVAL;
+  TT_TRY(check_cores(c, cores));
+  if (!SH) return tt_fail(c, TT_EINVAL, "null output");
+  if (k < 0 || k >= c->d) return tt_fail(c, TT_EINVAL, "mode %d outside [0, %d)", k, c->d);
+  c->err.clear();
+  TT_TRY(tt_ensure_tables(c, sweep));
+  TT_TRY(build_all_ghat(c, cores));
+  TT_TRY(tt_launch_suffixes(c));
+  TT_TRY(tt_launch_prefix_reset(c));
+  for (int j = 0; j < k; ++j) TT_TRY(tt_launch_prefix_step(c, j));
+  TT_TRY(tt_launch_interface_from_chain(c, k, SH));
+  return TT_OK;
+}
+
+extern "C" int tt_prox_update(tt_ctx* c, const float* Y, const float* SH, float* core, int k) {
+  if (!c) return TT_EINVAL;
+  if (!Y || !SH || !core) return tt_fail(c, TT_EINVAL, "null pointer");
+  if (k < 0 || k >= c->d) return tt_fail(c, TT_EINVAL, "mode %d outside [0, %d)", k, c->d);
+  c->err.clear();
+  TT_TRY(reset_status(c));
+  TT_TRY(tt_launch_prox_update(c, Y, SH, core, k, nullptr));
+  return tt_read_status(c);
+}
+
+extern "C" int tt_orthogonalize(tt_ctx* c, float* const* cores, int direction, int k) {
+  if (!c) return TT_EINVAL;
+  TT_TRY(check_cores(c, cores));
+  c->err.clear();
+  TT_TRY(reset_status(c));
+  if (direction == -1) {
+    for (int kk = c->d - 1; kk >= 1; --kk) TT_TRY(tt_launch_lq_right(c, cores[kk - 1], cores[kk], kk));
+  } else if (direction == 1) {
+    if (k < 0 || k >= c->d - 1) return tt_fail(c, TT_EINVAL, "QR step needs 0 <= k < d-1 (k=%d)", k);
+    TT_TRY(tt_launch_qr_left(c, cores[k], cores[k + 1], k));
+  } else {
+    return tt_fail(c, TT_EINVAL, "direction must be -1 or +1");
+  }
+  return tt_read_status(c);
+}
+
+// One outer iteration of Algorithm 1; change slots receive ||dG_k||^2, ||G_k||^2 per core.
+static int one_sweep(tt_ctx* c, const void* A, const float* scales, float* const* cores, uint64_t sweep,
+                     double* change_slots) {
+  const int d = c->d;
+  for (int kk = d - 1; kk >= 1; --kk) TT_TRY(tt_launch_lq_right(c, cores[kk - 1], cores[kk], kk));
+  TT_TRY(tt_ensure_tables(c, sweep));
+  TT_TRY(build_all_ghat(c, cores));
+  TT_TRY(tt_launch_suffixes(c));
+  TT_TRY(tt_launch_prefix_reset(c));
+  for (int k = 0; k < d; ++k) {
+    TT_TRY(tt_launch_interface_from_chain(c, k, c->d_SH));
+    TT_TRY(tt_launch_unfold(c, A, scales, k, c->d_Y));
+    TT_TRY(tt_launch_prox_update(c, c->d_Y, c->d_SH, cores[k], k, change_slots ? change_slots + 2 * k : nullptr));
+    if (k < d - 1) {
+      TT_TRY(tt_launch_qr_left(c, cores[k], cores[k + 1], k));
+      TT_TRY(tt_launch_core_fft(c, cores[k], k));
+      TT_TRY(tt_launch_prefix_step(c, k));
+    }
+  }
+  return TT_OK;
+}
+
+extern "C" int tt_prox_als_sweep(tt_ctx* c, const void* A, const float* scales, float* const* cores,
+                                 int nsweeps, uint64_t first_sweep, double* rel_change_out) {
+  if (!c) return TT_EINVAL;
+  TT_TRY(check_data(c, A, scales));
+  TT_TRY(check_cores(c, cores));
+  if (nsweeps < 0) return tt_fail(c, TT_EINVAL, "nsweeps < 0");
+  c->err.clear();
+  TT_TRY(reset_status(c));
+  const int per_block = c->changes_cap / c->d;
+  std::vector<double> host;
+  for (int t0 = 0; t0 < nsweeps; t0 += per_block) {
+    const int nt = std::min(per_block, nsweeps - t0);
+    for (int t = 0; t < nt; ++t) {
+      double* slots = rel_change_out ? c->d_changes + (size_t)2 * c->d * t : nullptr;
+      TT_TRY(one_sweep(c, A, scales, cores, first_sweep + t0 + t, slots));
+    }
+    if (rel_change_out) {
+      host.resize((size_t)2 * c->d * nt);
+      TT_CUDA(c, cudaMemcpyAsync(host.data(), c->d_changes, sizeof(double) * host.size(), cudaMemcpyDeviceToHost, c->stream));
+      TT_TRY(tt_read_status(c));
+      for (int t = 0; t < nt; ++t) {
+        double mx = 0.0;
+        for (int k = 0; k < c->d; ++k) {
+          double dd = host[(size_t)2 * (c->d * t + k)], nn = host[(size_t)2 * (c->d * t + k) + 1];
+          if (nn > 0) mx = std::max(mx, sqrt(dd / nn));
+        }
+        rel_change_out[t0 + t] = mx;
+      }
+    }
+  }
+  if (!rel_change_out) {
+    // surface a failed solve without forcing a synchronisation on the success path
+    int st = 0;
+    TT_CUDA(c, cudaMemcpyAsync(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    TT_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (st != 0) return tt_read_status(c);
+  }
+  return TT_OK;
+}
+
+extern "C" int tt_rel_error(tt_ctx* c, const void* A, const float* scales, float* const* cores, double* out) {
+  if (!c) return TT_EINVAL;
+  TT_TRY(check_data(c, A, scales));
+  TT_TRY(check_cores(c, cores));
+  if (!out) return tt_fail(c, TT_EINVAL, "null output");
+  c->err.clear();
+  TT_TRY(tt_launch_rel_error(c, A, scales, cores));
+  double h[2];
+  TT_CUDA(c, cudaMemcpyAsync(h, c->d_err_acc, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  TT_CUDA(c, cudaStreamSynchronize(c->stream));
+  *out = (h[1] > 0) ? sqrt(h[0] / h[1]) : 0.0;
+  return TT_OK;
+}

@@ -1,0 +1,217 @@
+// Part (b): S H_k = F^{-1}[(F S_{>k} G_{>k}^T) face-split (F S_{<k} G_{<k})]   (Theorem 1)
+// with F S_{<k} G_{<k} and F S_{>k} G_{>k}^T formed by slice-wise products of the
+// FFT-sketched cores G_j x_2 (F S_j)                                            (Theorem 2).
+//
+// Every core is real, so each DFT is Hermitian and only the J/2+1 frequencies 0..J/2 are kept.
+//   k_core_fft     : CountSketch of one (a, b) fibre of core j into J buckets + radix-2 FFT
+//   k_suffix_chain : R_{>k}(w) = Ghat_{k+1}(w) ... Ghat_{d-1}(w) for all k   (one thread per w)
+//   k_prefix_step  : L_{<j+1}(w) = L_{<j}(w) Ghat_j(w)
+//   k_face_ifft    : column c = a + r_k b of S H_k: inverse FFT of L_{<k}(w)[a] R_{>k}(w)[b]
+#include "tt_internal.cuh"
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 c) {  // a*b + c
+  return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, c.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, c.y)));
+}
+
+// In-place radix-2 decimation-in-time FFT of length J = 2^logJ held in shared memory, input in
+// natural order (bit-reversal done here). Forward transform uses w = exp(-2 pi i / J) (Sec. 3).
+__device__ void block_fft(float2* buf, const float2* __restrict__ tw, int J, int logJ) {
+  for (int t = threadIdx.x; t < J; t += blockDim.x) {
+    int r = (int)(__brev((unsigned)t) >> (32 - logJ));
+    if (r > t) {
+      float2 x = buf[t];
+      buf[t] = buf[r];
+      buf[r] = x;
+    }
+  }
+  __syncthreads();
+  for (int len = 2, lg = 1; len <= J; len <<= 1, ++lg) {
+    int half = len >> 1;
+    int step = J >> lg;  // twiddle stride
+    for (int t = threadIdx.x; t < J / 2; t += blockDim.x) {
+      int grp = t / half, pos = t - grp * half;
+      int i = grp * len + pos, j = i + half;
+      float2 w = __ldg(tw + pos * step);
+      float2 u = buf[i], v = cmul(buf[j], w);
+      buf[i] = make_float2(u.x + v.x, u.y + v.y);
+      buf[j] = make_float2(u.x - v.x, u.y - v.y);
+    }
+    __syncthreads();
+  }
+}
+
+struct CoreFftArgs {
+  const float* core;  // r0 x n x r1, r0 fastest
+  const int32_t* h;   // h_j, n entries
+  const int8_t* v;
+  const float2* tw;
+  float2* out;        // (J/2+1) x (r0 r1), frequency-major
+  int r0, r1, n, J, logJ;
+};
+
+__global__ void k_core_fft(CoreFftArgs a) {
+  extern __shared__ float2 buf[];
+  const int fib = blockIdx.x;  // a + r0 * b
+  const int al = fib % a.r0, be = fib / a.r0;
+  for (int t = threadIdx.x; t < a.J; t += blockDim.x) buf[t] = make_float2(0.f, 0.f);
+  __syncthreads();
+  for (int i = threadIdx.x; i < a.n; i += blockDim.x) {
+    float g = a.core[al + (int64_t)a.r0 * (i + (int64_t)a.n * be)];
+    float s = a.v[i] < 0 ? -g : g;
+    atomicAdd(&buf[a.h[i]].x, s);
+  }
+  __syncthreads();
+  block_fft(buf, a.tw, a.J, a.logJ);
+  const int S = a.r0 * a.r1;
+  for (int w = threadIdx.x; w <= a.J / 2; w += blockDim.x) a.out[(int64_t)w * S + fib] = buf[w];
+}
+
+int tt_launch_core_fft(tt_ctx* c, const float* core, int j) {
+  CoreFftArgs a;
+  a.core = core;
+  a.h = c->d_h + c->noff[j];
+  a.v = c->d_v + c->noff[j];
+  a.tw = c->d_twiddle;
+  a.out = c->d_ghat + c->ghat_off[j];
+  a.r0 = c->r[j];
+  a.r1 = c->r[j + 1];
+  a.n = (int)c->n[j];
+  a.J = c->J;
+  a.logJ = c->logJ;
+  size_t smem = sizeof(float2) * c->J;
+  if (smem > 48 * 1024) TT_CUDA(c, cudaFuncSetAttribute(k_core_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_core_fft<<<a.r0 * a.r1, 512, smem, c->stream>>>(a);
+  TT_LAUNCH(c, "k_core_fft");
+  return TT_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// chain products (slice-wise products of Theorem 2), one thread per frequency
+
+struct ChainArgs {
+  const float2* ghat;
+  int64_t ghat_off[TT_MAX_D + 1];
+  float2* suffix;
+  int64_t suffix_off[TT_MAX_D + 1];
+  int r[TT_MAX_D + 1];
+  int d, H;
+};
+
+__global__ void k_suffix_chain(ChainArgs a) {
+  int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= a.H) return;
+  // R_{>d-1} = [1]
+  a.suffix[a.suffix_off[a.d - 1] + w] = make_float2(1.f, 0.f);
+  for (int k = a.d - 2; k >= 0; --k) {
+    const int ra = a.r[k + 1], rb = a.r[k + 2];
+    const float2* G = a.ghat + a.ghat_off[k + 1] + (int64_t)w * ra * rb;  // Ghat_{k+1}(w), (a + ra b)
+    const float2* Rn = a.suffix + a.suffix_off[k + 1] + (int64_t)w * rb;
+    float2* R = a.suffix + a.suffix_off[k] + (int64_t)w * ra;
+    for (int al = 0; al < ra; ++al) {
+      float2 acc = make_float2(0.f, 0.f);
+      for (int be = 0; be < rb; ++be) acc = cfma(G[al + ra * be], Rn[be], acc);
+      R[al] = acc;
+    }
+  }
+}
+
+int tt_launch_suffixes(tt_ctx* c) {
+  ChainArgs a;
+  a.ghat = c->d_ghat;
+  for (int k = 0; k <= c->d; ++k) {
+    a.ghat_off[k] = c->ghat_off[k];
+    a.suffix_off[k] = c->suffix_off[k];
+    a.r[k] = c->r[k];
+  }
+  a.suffix = c->d_suffix;
+  a.d = c->d;
+  a.H = c->J / 2 + 1;
+  k_suffix_chain<<<(a.H + 127) / 128, 128, 0, c->stream>>>(a);
+  TT_LAUNCH(c, "k_suffix_chain");
+  return TT_OK;
+}
+
+__global__ void k_prefix_reset(float2* L, int H) {
+  int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w < H) L[w] = make_float2(1.f, 0.f);
+}
+
+int tt_launch_prefix_reset(tt_ctx* c) {
+  int H = c->J / 2 + 1;
+  k_prefix_reset<<<(H + 127) / 128, 128, 0, c->stream>>>(c->d_prefix, H);
+  TT_LAUNCH(c, "k_prefix_reset");
+  return TT_OK;
+}
+
+// L_new(w)[b] = sum_a L(w)[a] Ghat_j(w)[a + ra b]; L has ra = r[j] entries per frequency
+__global__ void k_prefix_step(const float2* __restrict__ L, const float2* __restrict__ G, float2* Ln,
+                              int ra, int rb, int H) {
+  int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= H) return;
+  const float2* Lw = L + (int64_t)w * ra;
+  const float2* Gw = G + (int64_t)w * ra * rb;
+  for (int be = 0; be < rb; ++be) {
+    float2 acc = make_float2(0.f, 0.f);
+    for (int al = 0; al < ra; ++al) acc = cfma(Lw[al], Gw[al + ra * be], acc);
+    Ln[(int64_t)w * rb + be] = acc;
+  }
+}
+
+int tt_launch_prefix_step(tt_ctx* c, int j) {
+  int H = c->J / 2 + 1;
+  k_prefix_step<<<(H + 127) / 128, 128, 0, c->stream>>>(c->d_prefix, c->d_ghat + c->ghat_off[j],
+                                                        c->d_prefix_tmp, c->r[j], c->r[j + 1], H);
+  TT_LAUNCH(c, "k_prefix_step");
+  std::swap(c->d_prefix, c->d_prefix_tmp);
+  return TT_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// face-split + inverse FFT: one CTA per column c = a + r_k b of S H_k
+
+struct FaceArgs {
+  const float2* L;  // H x ra (prefix L_{<k})
+  const float2* R;  // H x rb (suffix R_{>k})
+  const float2* tw;
+  float* SH;        // J x (ra rb), column-major
+  int ra, rb, J, logJ;
+};
+
+__global__ void k_face_ifft(FaceArgs a) {
+  extern __shared__ float2 buf[];
+  const int col = blockIdx.x;
+  const int al = col % a.ra, be = col / a.ra;
+  const int H = a.J / 2 + 1;
+  // conj of the full Hermitian spectrum: X[w] = L[w][a] R[w][b] for w <= J/2,
+  // X[w] = conj(X[J - w]) above; forward FFT of conj(X) then real part / J = inverse DFT.
+  for (int w = threadIdx.x; w < a.J; w += blockDim.x) {
+    int ws = (w < H) ? w : a.J - w;
+    float2 x = cmul(a.L[(int64_t)ws * a.ra + al], a.R[(int64_t)ws * a.rb + be]);
+    if (w >= H) x.y = -x.y;
+    buf[w] = make_float2(x.x, -x.y);
+  }
+  __syncthreads();
+  block_fft(buf, a.tw, a.J, a.logJ);
+  const float inv = 1.f / (float)a.J;
+  for (int t = threadIdx.x; t < a.J; t += blockDim.x) a.SH[(int64_t)col * a.J + t] = buf[t].x * inv;
+}
+
+int tt_launch_interface_from_chain(tt_ctx* c, int k, float* SH) {
+  FaceArgs a;
+  a.L = c->d_prefix;
+  a.R = c->d_suffix + c->suffix_off[k];
+  a.tw = c->d_twiddle;
+  a.SH = SH;
+  a.ra = c->r[k];
+  a.rb = c->r[k + 1];
+  a.J = c->J;
+  a.logJ = c->logJ;
+  size_t smem = sizeof(float2) * c->J;
+  if (smem > 48 * 1024) TT_CUDA(c, cudaFuncSetAttribute(k_face_ifft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_face_ifft<<<a.ra * a.rb, 512, smem, c->stream>>>(a);
+  TT_LAUNCH(c, "k_face_ifft");
+  return TT_OK;
+}

@@ -1,0 +1,123 @@
+// Internal declarations shared by the translation units of libttsketch.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/tt_sketch.h"
+
+#define TT_MAX_D 8
+#define TT_MAX_S 160      // largest r[k]*r[k+1] handled by the dense solve kernels
+#define TT_MAX_J 16384
+#define TT_MAX_N 65536    // largest single mode size
+
+struct TtPlan0;
+
+// Library-owned state of one problem shape (see tt_sketch_init).
+struct tt_ctx {
+  int d = 0;
+  int64_t n[TT_MAX_D] = {0};
+  int r[TT_MAX_D + 1] = {0};
+  int J = 0, logJ = 0;
+  double lambda = 0.0;
+  uint64_t seed = 0;
+  int dtype = TT_F32;
+  unsigned flags = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+
+  int64_t N = 0;             // number of tensor entries
+  int64_t noff[TT_MAX_D + 1];  // offsets of mode tables (prefix sums of n)
+  int64_t stride[TT_MAX_D + 1];  // stride[k] = prod_{s<k} n_s
+  int smax = 0;              // max_k r[k]*r[k+1]
+  int64_t nmax = 0;          // max_k n[k]
+
+  // hash / sign tables of the current draw (device), sum_k n_k entries each
+  int32_t* d_h = nullptr;
+  int8_t* d_v = nullptr;
+  bool tables_valid = false;   // d_h/d_v hold the draw for `tables_sweep`
+  uint64_t tables_sweep = 0;
+  bool user_tables = false;    // tables were set by tt_sketch_set_tables
+
+  // mode-0 fiber plan (fibers grouped by destination row of Y_0)
+  int64_t M0 = 0;              // number of mode-0 fibers, N / n_0
+  uint32_t* d_plan0 = nullptr; // M0 entries: fiber index | sign in bit 31 (sorted by row)
+  int64_t* d_plan0_off = nullptr;  // J + 1 row offsets into d_plan0
+  int32_t* d_plan0_cursor = nullptr;  // J scatter cursors
+  bool plan0_valid = false;
+
+  // FFT sketches of the cores: for core j, (J/2+1) x s_j complex, frequency-major
+  float2* d_ghat = nullptr;
+  int64_t ghat_off[TT_MAX_D + 1];
+  float2* d_twiddle = nullptr;   // J/2 twiddles exp(-2 pi i t / J)
+  float2* d_suffix = nullptr;    // for each k: (J/2+1) x r[k+1] complex (suffix R_{>k})
+  int64_t suffix_off[TT_MAX_D + 1];
+  float2* d_prefix = nullptr;    // (J/2+1) x rmax complex: prefix L_{<k}
+  float2* d_prefix_tmp = nullptr;
+  int rmax = 1;
+
+  // dense workspaces
+  float* d_SH = nullptr;       // J x smax (column-major)
+  float* d_Y = nullptr;        // J x nmax (row-major), used by the sweep
+  double* d_gram = nullptr;    // (smax + nmax) x smax FP64 accumulators of [SH | Y]^T SH
+  float* d_core_old = nullptr; // proximal centre copy (nmax * smax)
+  double* d_changes = nullptr; // per (sweep, k): ||dG||^2, ||G||^2
+  int* d_status = nullptr;     // device error flag (0 = ok, else TT_E* code)
+  double* d_err_acc = nullptr; // rel-error accumulators (2 doubles)
+  int changes_cap = 0;
+};
+
+// ---------------------------------------------------------------------------------------------
+// hashing (SplitMix64 chain, see tt_sketch.h)
+
+__host__ __device__ inline uint64_t tt_mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__host__ __device__ inline uint64_t tt_step(uint64_t z, uint64_t f) {
+  return tt_mix64(z + (f + 1ull) * 0x9E3779B97F4A7C15ull);
+}
+__host__ __device__ inline uint64_t tt_word(uint64_t seed, uint64_t sweep, uint64_t mode,
+                                            uint64_t stream, uint64_t i) {
+  return tt_step(tt_step(tt_step(tt_step(seed, sweep), mode), stream), i);
+}
+
+// ---------------------------------------------------------------------------------------------
+// host helpers (tt_context.cu)
+
+int tt_fail(tt_ctx* c, int code, const char* fmt, ...);
+int tt_cuda_check(tt_ctx* c, cudaError_t e, const char* what);
+#define TT_CUDA(ctx, call)                                   \
+  do {                                                       \
+    cudaError_t _e = (call);                                 \
+    if (_e != cudaSuccess) return tt_cuda_check(ctx, _e, #call); \
+  } while (0)
+#define TT_LAUNCH(ctx, what)                                          \
+  do {                                                                \
+    cudaError_t _e = cudaGetLastError();                              \
+    if (_e != cudaSuccess) return tt_cuda_check(ctx, _e, what);       \
+  } while (0)
+
+int tt_ensure_tables(tt_ctx* c, uint64_t sweep);
+int tt_ensure_plan0(tt_ctx* c);
+
+// kernels' host entry points (one translation unit each)
+int tt_launch_unfold(tt_ctx* c, const void* A, const float* scales, int k, float* Y);
+int tt_launch_core_fft(tt_ctx* c, const float* core, int j);
+int tt_launch_suffixes(tt_ctx* c);
+int tt_launch_prefix_reset(tt_ctx* c);
+int tt_launch_prefix_step(tt_ctx* c, int j);
+int tt_launch_interface_from_chain(tt_ctx* c, int k, float* SH);
+int tt_launch_prox_update(tt_ctx* c, const float* Y, const float* SH, float* core, int k,
+                          double* change_slot);
+int tt_launch_qr_left(tt_ctx* c, float* core_k, float* core_k1, int k);
+int tt_launch_lq_right(tt_ctx* c, float* core_km1, float* core_k, int k);
+int tt_launch_rel_error(tt_ctx* c, const void* A, const float* scales, float* const* cores);
+int tt_read_status(tt_ctx* c);
+
+// element loads of the data tensor in its storage type, converted to float
+template <int DT>
+struct TtElem;

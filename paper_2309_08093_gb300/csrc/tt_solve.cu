@@ -1,0 +1,531 @@
+// Part (c): the proximal update of Eq. (ite) (read with S^T S):
+//   M = (S H_k)^T (S H_k) + sigma I,  B = Y_k^T (S H_k) + sigma G_{k(2)},  G_{k(2)} <- B M^{-1},
+// plus the QR / LQ orthogonalisation steps of Algorithm 1 and the relative error of Sec. 5.
+//
+//   k_gram        : [S H_k | Y_k]^T (S H_k) with FP32 products summed in FP32 over K-chunks of
+//                   256 rows and in FP64 across chunks (split-K, FP64 atomics)
+//   k_prox_solve  : Cholesky M = L L^T and the two triangular solves, one CTA (s <= 160)
+//   k_qr_left     : Householder QR of G_k^L, G_k <- Q, G_{k+1} <- R G_{k+1}^R
+//   k_lq_right    : the same on (G_k^R)^T: G_k^R <- Q^T, G_{k-1}^L <- G_{k-1}^L R^T
+//   k_rel_error   : ||A - [[G]]||_F^2 and ||A||_F^2, one warp per mode-0 fibre
+#include <algorithm>
+
+#include "tt_internal.cuh"
+
+// ---------------------------------------------------------------------------------------------
+// Gram and right-hand side
+
+struct GramArgs {
+  const float* SH;  // J x s column-major
+  const float* Y;   // J x n row-major
+  double* C;        // (s + n) x s row-major accumulators (zeroed by the caller)
+  int J, s, n, kchunk;
+};
+
+__global__ void __launch_bounds__(256) k_gram(GramArgs a) {
+  __shared__ float X[32][33];
+  __shared__ float B[32][33];
+  const int rows = a.s + a.n;
+  const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+  const int kb = blockIdx.z * a.kchunk, ke = min(a.J, kb + a.kchunk);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // 16 x 16 threads, 2 x 2 outputs each
+  float acc[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+  for (int b0 = kb; b0 < ke; b0 += 32) {
+    for (int idx = threadIdx.x; idx < 32 * 32; idx += 256) {
+      int kk = idx & 31, cc = idx >> 5;
+      int b = b0 + kk;
+      int gr = r0 + cc, gc = c0 + cc;
+      float xv = 0.f, bv = 0.f;
+      if (b < ke) {
+        if (gr < a.s)
+          xv = a.SH[(int64_t)gr * a.J + b];
+        else if (gr < rows)
+          xv = a.Y[(int64_t)b * a.n + (gr - a.s)];
+        if (gc < a.s) bv = a.SH[(int64_t)gc * a.J + b];
+      }
+      X[kk][cc] = xv;
+      B[kk][cc] = bv;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < 32; ++kk) {
+      float x0 = X[kk][ty], x1 = X[kk][ty + 16];
+      float y0 = B[kk][tx], y1 = B[kk][tx + 16];
+      acc[0][0] = fmaf(x0, y0, acc[0][0]);
+      acc[0][1] = fmaf(x0, y1, acc[0][1]);
+      acc[1][0] = fmaf(x1, y0, acc[1][0]);
+      acc[1][1] = fmaf(x1, y1, acc[1][1]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      int gr = r0 + ty + 16 * i, gc = c0 + tx + 16 * j;
+      if (gr < rows && gc < a.s) atomicAdd(a.C + (int64_t)gr * a.s + gc, (double)acc[i][j]);
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Cholesky + triangular solves, one CTA
+
+struct SolveArgs {
+  const double* C;  // (s + n) x s: rows [0, s) = SH^T SH, rows [s, s+n) = Y^T SH
+  float* core;      // r0 x n x r1 (read: proximal centre; written: update)
+  double* change;   // [0] += ||G_new - G_old||^2, [1] += ||G_new||^2 (may be null)
+  int* status;
+  double sigma;
+  int s, n, r0, r1;
+  int chunk_rows;
+};
+
+__device__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x < 32) {
+    t = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  }
+  return t;  // valid in thread 0
+}
+
+__global__ void __launch_bounds__(1024) k_prox_solve(SolveArgs a) {
+  extern __shared__ float sm[];
+  __shared__ int bad;
+  __shared__ double red[32];
+  const int s = a.s;
+  float* L = sm;                         // s x s, row-major, lower triangle used
+  float* Z = sm + s * s;                 // chunk_rows x s, row-major
+  if (*a.status != 0) return;
+  for (int idx = threadIdx.x; idx < s * s; idx += blockDim.x) {
+    int i = idx / s, j = idx - i * s;
+    double m = a.C[idx];
+    if (i == j) m += a.sigma;
+    L[idx] = (float)m;
+  }
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  // right-looking Cholesky, lower triangle
+  for (int j = 0; j < s; ++j) {
+    if (threadIdx.x == 0) {
+      float dj = L[j * s + j];
+      if (!(dj > 0.f) || !isfinite(dj)) {
+        bad = isfinite(dj) ? TT_ENOTSPD : TT_ENONFINITE;
+      } else {
+        L[j * s + j] = sqrtf(dj);
+      }
+    }
+    __syncthreads();
+    if (bad) break;
+    const float ljj = L[j * s + j];
+    for (int i = j + 1 + threadIdx.x; i < s; i += blockDim.x) L[i * s + j] /= ljj;
+    __syncthreads();
+    const int m = s - j - 1;
+    for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+      int ii = t / m, ll = t - ii * m;
+      if (ll <= ii) {
+        int i = j + 1 + ii, l = j + 1 + ll;
+        L[i * s + l] -= L[i * s + j] * L[l * s + j];
+      }
+    }
+    __syncthreads();
+  }
+  if (bad) {
+    if (threadIdx.x == 0) atomicCAS(a.status, 0, bad);
+    return;
+  }
+  double dsum = 0.0, nsum = 0.0;
+  for (int i0 = 0; i0 < a.n; i0 += a.chunk_rows) {
+    const int nr = min(a.chunk_rows, a.n - i0);
+    // B = Y^T SH + sigma G_{k(2)}; G_{k(2)}[i, c] with c = al + r0 be
+    for (int idx = threadIdx.x; idx < nr * s; idx += blockDim.x) {
+      int i = idx / s, c = idx - i * s;
+      int al = c % a.r0, be = c / a.r0;
+      float g = a.core[al + (int64_t)a.r0 * ((i0 + i) + (int64_t)a.n * be)];
+      Z[idx] = (float)(a.C[(int64_t)(s + i0 + i) * s + c] + a.sigma * (double)g);
+    }
+    __syncthreads();
+    // forward: W L^T = B  (column j after columns < j)
+    for (int j = 0; j < s; ++j) {
+      const float ljj = L[j * s + j];
+      for (int i = threadIdx.x; i < nr; i += blockDim.x) Z[i * s + j] /= ljj;
+      __syncthreads();
+      const int m = s - j - 1;
+      for (int t = threadIdx.x; t < nr * m; t += blockDim.x) {
+        int i = t / m, l = j + 1 + (t - (t / m) * m);
+        Z[i * s + l] -= Z[i * s + j] * L[l * s + j];
+      }
+      __syncthreads();
+    }
+    // backward: X L = W  (column j after columns > j)
+    for (int j = s - 1; j >= 0; --j) {
+      const float ljj = L[j * s + j];
+      for (int i = threadIdx.x; i < nr; i += blockDim.x) Z[i * s + j] /= ljj;
+      __syncthreads();
+      for (int t = threadIdx.x; t < nr * j; t += blockDim.x) {
+        int i = t / j, l = t - (t / j) * j;
+        Z[i * s + l] -= Z[i * s + j] * L[j * s + l];
+      }
+      __syncthreads();
+    }
+    for (int idx = threadIdx.x; idx < nr * s; idx += blockDim.x) {
+      int i = idx / s, c = idx - i * s;
+      int al = c % a.r0, be = c / a.r0;
+      int64_t off = al + (int64_t)a.r0 * ((i0 + i) + (int64_t)a.n * be);
+      float old = a.core[off], nw = Z[idx];
+      dsum += (double)(nw - old) * (double)(nw - old);
+      nsum += (double)nw * (double)nw;
+      a.core[off] = nw;
+    }
+    __syncthreads();
+  }
+  double t1 = block_sum(dsum, red);
+  double t2 = block_sum(nsum, red);
+  if (threadIdx.x == 0 && a.change) {
+    a.change[0] = t1;
+    a.change[1] = t2;
+  }
+}
+
+int tt_launch_prox_update(tt_ctx* c, const float* Y, const float* SH, float* core, int k,
+                          double* change_slot) {
+  const int s = c->r[k] * c->r[k + 1];
+  const int n = (int)c->n[k];
+  TT_CUDA(c, cudaMemsetAsync(c->d_gram, 0, sizeof(double) * (s + n) * s, c->stream));
+  GramArgs g;
+  g.SH = SH;
+  g.Y = Y;
+  g.C = c->d_gram;
+  g.J = c->J;
+  g.s = s;
+  g.n = n;
+  g.kchunk = std::max(32, std::min(256, c->J));
+  dim3 grid((s + n + 31) / 32, (s + 31) / 32, (c->J + g.kchunk - 1) / g.kchunk);
+  k_gram<<<grid, 256, 0, c->stream>>>(g);
+  TT_LAUNCH(c, "k_gram");
+  SolveArgs a;
+  a.C = c->d_gram;
+  a.core = core;
+  a.change = change_slot;
+  a.status = c->d_status;
+  a.sigma = c->lambda;
+  a.s = s;
+  a.n = n;
+  a.r0 = c->r[k];
+  a.r1 = c->r[k + 1];
+  const int budget = 48 * 1024;  // floats of shared memory for L and the RHS chunk
+  a.chunk_rows = std::max(1, std::min(n, (budget - s * s) / s));
+  size_t smem = sizeof(float) * ((size_t)s * s + (size_t)a.chunk_rows * s);
+  TT_CUDA(c, cudaFuncSetAttribute(k_prox_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_prox_solve<<<1, 1024, smem, c->stream>>>(a);
+  TT_LAUNCH(c, "k_prox_solve");
+  return TT_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Householder QR of an m x q column-major matrix held in shared memory (q small).
+// On exit: A holds Q (m x p, p = min(m, q)) in its first p columns, R (p x q) in Rm (q x q,
+// row-major, rows >= p zero), with diag(R) >= 0.
+
+__device__ float warp_sum(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ void block_householder_qr(float* A, int m, int q, float* Rm, float* tau, float* colsc) {
+  const int p = min(m, q);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = 0; j < p; ++j) {
+    float* x = A + (int64_t)j * m;
+    // norm of x[j+1 : m]
+    if (warp == 0) {
+      float ss = 0.f;
+      for (int i = j + 1 + lane; i < m; i += 32) ss = fmaf(x[i], x[i], ss);
+      ss = warp_sum(ss);
+      if (lane == 0) {
+        float alpha = x[j];
+        float xn = sqrtf(ss);
+        if (xn == 0.f) {
+          tau[j] = 0.f;
+          colsc[0] = 0.f;
+        } else {
+          float beta = -copysignf(hypotf(alpha, xn), alpha);
+          tau[j] = (beta - alpha) / beta;
+          colsc[0] = 1.f / (alpha - beta);
+          x[j] = beta;
+        }
+      }
+    }
+    __syncthreads();
+    const float sc = colsc[0];
+    const float tj = tau[j];
+    if (tj != 0.f)
+      for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) x[i] *= sc;
+    __syncthreads();
+    if (tj != 0.f) {
+      // apply H_j = I - tau v v^T (v_j = 1) to columns j+1..q-1, one warp per column
+      for (int cc = j + 1 + warp; cc < q; cc += nw) {
+        float* y = A + (int64_t)cc * m;
+        float w = 0.f;
+        for (int i = j + 1 + lane; i < m; i += 32) w = fmaf(x[i], y[i], w);
+        w = warp_sum(w) + y[j];
+        w *= tj;
+        if (lane == 0) y[j] -= w;
+        for (int i = j + 1 + lane; i < m; i += 32) y[i] = fmaf(-w, x[i], y[i]);
+      }
+    }
+    __syncthreads();
+  }
+  // R (upper trapezoid) out, zero below
+  for (int idx = threadIdx.x; idx < q * q; idx += blockDim.x) {
+    int i = idx / q, jj = idx - i * q;
+    Rm[idx] = (i < p && jj >= i) ? A[(int64_t)jj * m + i] : 0.f;
+  }
+  __syncthreads();
+  // form Q in place (backward accumulation of the reflectors), columns 0..p-1
+  for (int j = p - 1; j >= 0; --j) {
+    float* x = A + (int64_t)j * m;
+    const float tj = tau[j];
+    for (int cc = j + 1 + warp; cc < p; cc += nw) {
+      float* y = A + (int64_t)cc * m;
+      float w = 0.f;
+      for (int i = j + 1 + lane; i < m; i += 32) w = fmaf(x[i], y[i], w);
+      w = (warp_sum(w) + y[j]) * tj;
+      if (lane == 0) y[j] -= w;
+      for (int i = j + 1 + lane; i < m; i += 32) y[i] = fmaf(-w, x[i], y[i]);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      if (i < j)
+        x[i] = 0.f;
+      else if (i == j)
+        x[i] = 1.f - tj;
+      else
+        x[i] = -tj * x[i];
+    }
+    __syncthreads();
+  }
+  // non-negative diagonal of R
+  for (int j = 0; j < p; ++j) {
+    if (Rm[j * q + j] < 0.f) {
+      for (int t = threadIdx.x; t < q; t += blockDim.x) Rm[j * q + t] = -Rm[j * q + t];
+      for (int i = threadIdx.x; i < m; i += blockDim.x) A[(int64_t)j * m + i] = -A[(int64_t)j * m + i];
+    }
+    __syncthreads();
+  }
+}
+
+// G_k^L (m = r0 n rows, q = r1 cols) = Q R; G_k <- Q (zero-padded); G_{k+1} <- R G_{k+1}^R
+__global__ void __launch_bounds__(512) k_qr_left(float* core, float* next, int r0, int n, int r1,
+                                                 int ncols_next, const int* status) {
+  extern __shared__ float sm[];
+  if (*status != 0) return;
+  const int m = r0 * n, q = r1;
+  float* A = sm;
+  float* Rm = A + (int64_t)m * q;
+  float* tau = Rm + q * q;
+  float* colsc = tau + q;
+  for (int idx = threadIdx.x; idx < m * q; idx += blockDim.x) A[idx] = core[idx];
+  __syncthreads();
+  block_householder_qr(A, m, q, Rm, tau, colsc);
+  const int p = min(m, q);
+  for (int idx = threadIdx.x; idx < m * q; idx += blockDim.x) core[idx] = (idx / m < p) ? A[idx] : 0.f;
+  // next^R is r1 x ncols_next column-major: column c holds r1 contiguous entries
+  for (int cidx = threadIdx.x; cidx < ncols_next; cidx += blockDim.x) {
+    float col[TT_MAX_S];
+    float* g = next + (int64_t)cidx * r1;
+    for (int b = 0; b < r1; ++b) col[b] = g[b];
+    for (int a2 = 0; a2 < r1; ++a2) {
+      float acc = 0.f;
+      for (int b = a2; b < r1; ++b) acc = fmaf(Rm[a2 * q + b], col[b], acc);
+      g[a2] = acc;
+    }
+  }
+}
+
+// (G_k^R)^T (m = n r1 rows, q = r0 cols) = Q R; G_k^R <- Q^T; G_{k-1}^L <- G_{k-1}^L R^T
+__global__ void __launch_bounds__(512) k_lq_right(float* prev, float* core, int r0, int n, int r1,
+                                                  int nrows_prev, const int* status) {
+  extern __shared__ float sm[];
+  if (*status != 0) return;
+  const int m = n * r1, q = r0;
+  float* A = sm;
+  float* Rm = A + (int64_t)m * q;
+  float* tau = Rm + q * q;
+  float* colsc = tau + q;
+  for (int idx = threadIdx.x; idx < m * q; idx += blockDim.x) {
+    int i = idx % m, a2 = idx / m;
+    A[idx] = core[a2 + (int64_t)r0 * i];
+  }
+  __syncthreads();
+  block_householder_qr(A, m, q, Rm, tau, colsc);
+  const int p = min(m, q);
+  for (int idx = threadIdx.x; idx < m * q; idx += blockDim.x) {
+    int i = idx % m, a2 = idx / m;
+    core[a2 + (int64_t)r0 * i] = (a2 < p) ? A[idx] : 0.f;
+  }
+  // prev^L is nrows_prev x r0 column-major; row t: prev[t + nrows_prev * a]
+  for (int t = threadIdx.x; t < nrows_prev; t += blockDim.x) {
+    float row[TT_MAX_S];
+    for (int a2 = 0; a2 < r0; ++a2) row[a2] = prev[t + (int64_t)nrows_prev * a2];
+    for (int b = 0; b < r0; ++b) {
+      float acc = 0.f;
+      for (int a2 = b; a2 < r0; ++a2) acc = fmaf(row[a2], Rm[b * q + a2], acc);  // (G R^T)[t, b]
+      prev[t + (int64_t)nrows_prev * b] = acc;
+    }
+  }
+}
+
+static size_t qr_smem(int m, int q) { return sizeof(float) * ((size_t)m * q + (size_t)q * q + q + 4); }
+
+int tt_launch_qr_left(tt_ctx* c, float* core_k, float* core_k1, int k) {
+  int r0 = c->r[k], n = (int)c->n[k], r1 = c->r[k + 1];
+  size_t smem = qr_smem(r0 * n, r1);
+  TT_CUDA(c, cudaFuncSetAttribute(k_qr_left, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int ncols = (int)(c->n[k + 1] * c->r[k + 2]);
+  k_qr_left<<<1, 512, smem, c->stream>>>(core_k, core_k1, r0, n, r1, ncols, c->d_status);
+  TT_LAUNCH(c, "k_qr_left");
+  return TT_OK;
+}
+
+int tt_launch_lq_right(tt_ctx* c, float* core_km1, float* core_k, int k) {
+  int r0 = c->r[k], n = (int)c->n[k], r1 = c->r[k + 1];
+  size_t smem = qr_smem(n * r1, r0);
+  TT_CUDA(c, cudaFuncSetAttribute(k_lq_right, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int nrows = (int)(c->r[k - 1] * c->n[k - 1]);
+  k_lq_right<<<1, 512, smem, c->stream>>>(core_km1, core_k, r0, n, r1, nrows, c->d_status);
+  TT_LAUNCH(c, "k_lq_right");
+  return TT_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// relative error: one warp per mode-0 fibre f = (i_1, ..., i_{d-1})
+
+struct ErrArgs {
+  const void* A;
+  const float* scales;
+  const float* core[TT_MAX_D];
+  int64_t n[TT_MAX_D];
+  int r[TT_MAX_D + 1];
+  int d, dtype;
+  int64_t M0;
+  double* acc;  // [0] += ||A - [[G]]||^2, [1] += ||A||^2
+};
+
+template <int DT>
+__device__ float err_elem(const ErrArgs& a, int64_t idx) {
+  if constexpr (DT == TT_F64) return (float)__ldg((const double*)a.A + idx);
+  if constexpr (DT == TT_F32) return __ldg((const float*)a.A + idx);
+  if constexpr (DT == TT_BF16) return __uint_as_float(((uint32_t)__ldg((const unsigned short*)a.A + idx)) << 16);
+  if constexpr (DT == TT_FP8E4M3) {
+    uint32_t cc = __ldg((const unsigned char*)a.A + idx);
+    uint32_t sg = (cc & 0x80u) << 24, e = (cc >> 3) & 0xFu, mm = cc & 7u;
+    float mag = e ? __uint_as_float(((e + 120u) << 23) | (mm << 20)) : (float)mm * 0.001953125f;
+    return __uint_as_float(__float_as_uint(mag) | sg);
+  }
+  return 0.f;
+}
+
+template <int DT>
+__global__ void __launch_bounds__(256) k_rel_error(ErrArgs a) {
+  __shared__ float ubuf[8][2][TT_MAX_S];
+  __shared__ double red[2][8];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int n0 = (int)a.n[0], r1 = a.r[1];
+  double e2 = 0.0, a2 = 0.0;
+  for (int64_t f = warp; f < a.M0; f += nwarps) {
+    // indices of modes 1..d-1
+    int64_t idx[TT_MAX_D];
+    int64_t rem = f;
+    for (int s2 = 1; s2 < a.d; ++s2) {
+      idx[s2] = rem % a.n[s2];
+      rem /= a.n[s2];
+    }
+    // u = G_{d-1}(:, i, 0), then u <- G_s(:, i_s, :) u for s = d-2..1
+    float* u = ubuf[wib][0];
+    float* un = ubuf[wib][1];
+    {
+      const int s2 = a.d - 1, ra = a.r[s2];
+      for (int al = lane; al < ra; al += 32) u[al] = a.core[s2][al + (int64_t)ra * idx[s2]];
+    }
+    __syncwarp();
+    for (int s2 = a.d - 2; s2 >= 1; --s2) {
+      const int ra = a.r[s2], rb = a.r[s2 + 1];
+      const float* G = a.core[s2] + (int64_t)ra * idx[s2];  // G(al, i, be) at al + ra*(i + n*be)
+      const int64_t bstride = (int64_t)ra * a.n[s2];
+      for (int al = lane; al < ra; al += 32) {
+        float acc = 0.f;
+        for (int be = 0; be < rb; ++be) acc = fmaf(G[al + bstride * be], u[be], acc);
+        un[al] = acc;
+      }
+      __syncwarp();
+      float* t = u;
+      u = un;
+      un = t;
+    }
+    const int64_t base = f * n0;
+    float fe = 0.f, fa = 0.f;
+    for (int i0 = lane; i0 < n0; i0 += 32) {
+      float rec = 0.f;
+      for (int al = 0; al < r1; ++al) rec = fmaf(a.core[0][i0 + (int64_t)n0 * al], u[al], rec);
+      float x = err_elem<DT>(a, base + i0);
+      if (a.scales) x *= __ldg(a.scales + i0);
+      float dlt = x - rec;
+      fe = fmaf(dlt, dlt, fe);
+      fa = fmaf(x, x, fa);
+    }
+    e2 += fe;
+    a2 += fa;
+    __syncwarp();
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    e2 += __shfl_xor_sync(0xffffffffu, e2, o);
+    a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+  }
+  if (lane == 0) {
+    red[0][wib] = e2;
+    red[1][wib] = a2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t1 = 0.0, t2 = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      t1 += red[0][w];
+      t2 += red[1][w];
+    }
+    atomicAdd(a.acc, t1);
+    atomicAdd(a.acc + 1, t2);
+  }
+}
+
+int tt_launch_rel_error(tt_ctx* c, const void* A, const float* scales, float* const* cores) {
+  ErrArgs a;
+  a.A = A;
+  a.scales = scales;
+  for (int k = 0; k < c->d; ++k) {
+    a.core[k] = cores[k];
+    a.n[k] = c->n[k];
+  }
+  for (int k = 0; k <= c->d; ++k) a.r[k] = c->r[k];
+  a.d = c->d;
+  a.dtype = c->dtype;
+  a.M0 = c->M0;
+  a.acc = c->d_err_acc;
+  TT_CUDA(c, cudaMemsetAsync(c->d_err_acc, 0, sizeof(double) * 2, c->stream));
+  int blocks = (int)std::min<int64_t>((c->M0 + 7) / 8, 152 * 16);
+  switch (c->dtype) {
+    case TT_F64: k_rel_error<TT_F64><<<blocks, 256, 0, c->stream>>>(a); break;
+    case TT_F32: k_rel_error<TT_F32><<<blocks, 256, 0, c->stream>>>(a); break;
+    case TT_BF16: k_rel_error<TT_BF16><<<blocks, 256, 0, c->stream>>>(a); break;
+    default: k_rel_error<TT_FP8E4M3><<<blocks, 256, 0, c->stream>>>(a); break;
+  }
+  TT_LAUNCH(c, "k_rel_error");
+  return TT_OK;
+}

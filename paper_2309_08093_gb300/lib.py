@@ -1,0 +1,202 @@
+"""Thin ctypes binding to libttsketch.so (declared in include/tt_sketch.h).
+
+Function names mirror the C ABI. This module only marshals arguments (torch CUDA tensors or
+host numpy arrays to raw pointers); every step of the computation runs in the CUDA library.
+Loading fails loudly if the library has not been built: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libttsketch.so")
+
+TT_F64, TT_F32, TT_BF16, TT_FP8E4M3 = 0, 1, 2, 3
+DTYPES = {"f64": TT_F64, "f32": TT_F32, "bf16": TT_BF16, "fp8": TT_FP8E4M3}
+TT_OK, TT_EINVAL, TT_ENOMEM, TT_ECUDA, TT_ENOTSPD, TT_ETIMEOUT, TT_ENONFINITE = 0, -1, -2, -3, -4, -5, -6
+TT_FLAG_FIXED_SKETCH = 1
+
+EXPORTS = ["tt_sketch_init", "tt_sketch_destroy", "tt_last_error", "tt_sketch_tables",
+           "tt_sketch_set_tables", "tt_sketch_unfold", "tt_sketch_interface", "tt_prox_update",
+           "tt_orthogonalize", "tt_prox_als_sweep", "tt_rel_error"]
+
+
+class TtError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"tt error {code}: {msg}")
+        self.code = code
+
+
+class TtParams(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int), ("n", ctypes.POINTER(ctypes.c_int64)),
+                ("r", ctypes.POINTER(ctypes.c_int)), ("J", ctypes.c_int),
+                ("lambda_", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("dtype", ctypes.c_int), ("flags", ctypes.c_uint)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the CUDA library (raises if it is missing: build it with build.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libttsketch.so not found at {path}; run paper_2309_08093_gb300.build.build()")
+    L = ctypes.CDLL(path)
+    vp, i, u64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64
+    L.tt_sketch_init.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(TtParams), vp]
+    L.tt_sketch_destroy.argtypes = [vp]
+    L.tt_sketch_destroy.restype = None
+    L.tt_last_error.argtypes = [vp]
+    L.tt_last_error.restype = ctypes.c_char_p
+    L.tt_sketch_tables.argtypes = [vp, u64, vp, vp]
+    L.tt_sketch_set_tables.argtypes = [vp, vp, vp]
+    L.tt_sketch_unfold.argtypes = [vp, vp, vp, i, u64, ctypes.POINTER(vp)]
+    L.tt_sketch_interface.argtypes = [vp, ctypes.POINTER(vp), i, u64, vp]
+    L.tt_prox_update.argtypes = [vp, vp, vp, vp, i]
+    L.tt_orthogonalize.argtypes = [vp, ctypes.POINTER(vp), i, i]
+    L.tt_prox_als_sweep.argtypes = [vp, vp, vp, ctypes.POINTER(vp), i, u64, ctypes.POINTER(ctypes.c_double)]
+    L.tt_rel_error.argtypes = [vp, vp, vp, ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_double)]
+    for name in EXPORTS:
+        f = getattr(L, name)
+        if name not in ("tt_sketch_destroy", "tt_last_error"):
+            f.restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def _ptr_array(ts: Sequence) -> ctypes.Array:
+    arr = (ctypes.c_void_p * len(ts))()
+    for j, t in enumerate(ts):
+        arr[j] = _ptr(t)
+    return arr
+
+
+def _current_stream():
+    import torch
+
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Context:
+    """Owns one tt_ctx. Arguments are torch CUDA tensors (device buffers) unless stated."""
+
+    def __init__(self, dims: Sequence[int], ranks: Sequence[int], J: int, lam: float, seed: int,
+                 dtype: str = "f32", flags: int = 0, stream=None):
+        self.lib = load()
+        self.dims = tuple(int(x) for x in dims)
+        self.ranks = tuple(int(x) for x in ranks)
+        self.d = len(self.dims)
+        self.J = int(J)
+        self._n = (ctypes.c_int64 * self.d)(*self.dims)
+        self._r = (ctypes.c_int * (self.d + 1))(*self.ranks)
+        self.params = TtParams(self.d, self._n, self._r, self.J, float(lam), int(seed) & (2**64 - 1),
+                               DTYPES[dtype], int(flags))
+        self.ctx = ctypes.c_void_p()
+        stream = _current_stream() if stream is None else stream
+        rc = self.lib.tt_sketch_init(ctypes.byref(self.ctx), ctypes.byref(self.params), stream)
+        if rc != TT_OK:
+            raise TtError(rc, "tt_sketch_init failed (see stderr)")
+
+    def close(self):
+        if self.ctx:
+            self.lib.tt_sketch_destroy(self.ctx)
+            self.ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc: int):
+        if rc != TT_OK:
+            raise TtError(rc, self.lib.tt_last_error(self.ctx).decode())
+
+    # -- C ABI mirrors ---------------------------------------------------------------------
+    def tt_sketch_tables(self, sweep: int):
+        tot = sum(self.dims)
+        h = np.zeros(tot, dtype=np.int32)
+        v = np.zeros(tot, dtype=np.int8)
+        self._check(self.lib.tt_sketch_tables(self.ctx, int(sweep), h.ctypes.data, v.ctypes.data))
+        return h, v
+
+    def tt_sketch_set_tables(self, h: np.ndarray, v: np.ndarray):
+        h = np.ascontiguousarray(h, dtype=np.int32)
+        v = np.ascontiguousarray(v, dtype=np.int8)
+        self._check(self.lib.tt_sketch_set_tables(self.ctx, h.ctypes.data, v.ctypes.data))
+
+    def tt_sketch_unfold(self, A, k: int, sweep: int, Y: Sequence, scales=None):
+        arr = _ptr_array(Y)
+        self._check(self.lib.tt_sketch_unfold(self.ctx, _ptr(A), _ptr(scales), int(k), int(sweep), arr))
+
+    def tt_sketch_interface(self, cores: Sequence, k: int, sweep: int, SH):
+        self._check(self.lib.tt_sketch_interface(self.ctx, _ptr_array(cores), int(k), int(sweep), _ptr(SH)))
+
+    def tt_prox_update(self, Y, SH, core, k: int):
+        self._check(self.lib.tt_prox_update(self.ctx, _ptr(Y), _ptr(SH), _ptr(core), int(k)))
+
+    def tt_orthogonalize(self, cores: Sequence, direction: int, k: int = 0):
+        self._check(self.lib.tt_orthogonalize(self.ctx, _ptr_array(cores), int(direction), int(k)))
+
+    def tt_prox_als_sweep(self, A, cores: Sequence, nsweeps: int, first_sweep: int = 0, scales=None,
+                          rel_change: bool = True):
+        out = (ctypes.c_double * max(1, nsweeps))() if rel_change else None
+        self._check(self.lib.tt_prox_als_sweep(self.ctx, _ptr(A), _ptr(scales), _ptr_array(cores),
+                                               int(nsweeps), int(first_sweep), out))
+        return list(out)[:nsweeps] if rel_change else None
+
+    def tt_rel_error(self, A, cores: Sequence, scales=None) -> float:
+        out = ctypes.c_double()
+        self._check(self.lib.tt_rel_error(self.ctx, _ptr(A), _ptr(scales), _ptr_array(cores), ctypes.byref(out)))
+        return out.value
+
+
+# ---------------------------------------------------------------------------------------------
+# helpers to move synthetic inputs to the device in the ABI's layouts
+
+def device_tensor(storage: np.ndarray, dtype: str, device="cuda"):
+    """Flat storage array (memory order) -> torch CUDA tensor holding the same bytes."""
+    import torch
+
+    if dtype == "f64":
+        t = torch.from_numpy(np.ascontiguousarray(storage, dtype=np.float64))
+    elif dtype == "f32":
+        t = torch.from_numpy(np.ascontiguousarray(storage, dtype=np.float32))
+    elif dtype == "bf16":
+        t = torch.from_numpy(np.ascontiguousarray(storage, dtype=np.uint16).view(np.int16)).view(torch.bfloat16)
+    elif dtype == "fp8":
+        t = torch.from_numpy(np.ascontiguousarray(storage, dtype=np.uint8))
+    else:
+        raise ValueError(dtype)
+    return t.to(device)
+
+
+def device_cores(cores: Sequence[np.ndarray], device="cuda") -> List:
+    """FP32 device copies of TT cores in the ABI layout (r_{k-1} fastest)."""
+    import torch
+
+    return [torch.from_numpy(np.ascontiguousarray(np.asarray(g, dtype=np.float32).ravel(order="F"))).to(device)
+            for g in cores]
+
+
+def host_cores(dev_cores: Sequence, ranks: Sequence[int], dims: Sequence[int]) -> List[np.ndarray]:
+    out = []
+    for k, t in enumerate(dev_cores):
+        a = t.detach().cpu().numpy().astype(np.float64)
+        out.append(a.reshape(ranks[k], dims[k], ranks[k + 1], order="F"))
+    return out

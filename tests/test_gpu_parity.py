@@ -1,0 +1,304 @@
+"""GPU parity: the CUDA library (called through the C ABI) against the CPU FP64 oracle on the
+same seeded inputs and hash draws. Floating-point outputs are compared in relative Frobenius
+norm (sums in different orders; buckets with cancellation make element-wise relative error
+meaningless). Tolerance 1e-5 for FP32 work; integer tables bit-exact."""
+import numpy as np
+import pytest
+
+import tt_oracle as O
+from conftest import read_golden
+from paper_2309_08093_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2309_08093_gb300 import build as _build  # noqa: E402
+
+_build.build()
+from paper_2309_08093_gb300 import lib  # noqa: E402
+
+TOL = 1e-5
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    nb = np.linalg.norm(b.ravel())
+    return np.linalg.norm((a - b).ravel()) / (nb if nb > 0 else 1.0)
+
+
+def oracle_tables(ctx_dims, seed, sweep, J):
+    hs, vs = O.draw_sketch(seed, sweep, ctx_dims, J)
+    return np.concatenate(hs).astype(np.int32), np.concatenate(vs).astype(np.int8)
+
+
+def split_tables(h, v, dims):
+    hs, vs, o = [], [], 0
+    for n in dims:
+        hs.append(h[o:o + n].astype(np.int64))
+        vs.append(v[o:o + n].astype(np.float64))
+        o += n
+    return hs, vs
+
+
+# ---------------------------------------------------------------------------------------------
+# a0: hash / sign tables
+
+@pytest.mark.parametrize("dims,J,seed,sweep", [((50, 50, 50), 1024, 935972268168698347, 0),
+                                               ((100, 100, 100, 100), 4096, 7, 19),
+                                               ((3, 1, 7), 2, 2**63 + 5, 3),
+                                               ((40,) * 5, 8192, 123, 2**40 + 1),
+                                               ((256, 256, 3, 128), 16384, 0, 0)])
+def test_tables_bit_exact(dims, J, seed, sweep):
+    ranks = (1,) + (1,) * (len(dims) - 1) + (1,)
+    ctx = lib.Context(dims, ranks, J, 1e-3, seed, "f32")
+    h, v = ctx.tt_sketch_tables(sweep)
+    ho, vo = oracle_tables(dims, seed, sweep, J)
+    assert np.array_equal(h, ho)
+    assert np.array_equal(v, vo)
+    ctx.close()
+
+
+def test_fixed_sketch_flag_ignores_sweep():
+    ctx = lib.Context((5, 6, 7), (1, 2, 2, 1), 64, 1e-3, 99, "f32", flags=lib.TT_FLAG_FIXED_SKETCH)
+    h0, v0 = ctx.tt_sketch_tables(0)
+    h1, v1 = ctx.tt_sketch_tables(5)
+    assert np.array_equal(h0, h1) and np.array_equal(v0, v1)
+    ctx.close()
+
+
+# ---------------------------------------------------------------------------------------------
+# worked example of Sec. 2.2 on the GPU
+
+def test_worked_example_on_gpu():
+    g = read_golden("tensorsketch_worked_example.txt")
+    S = np.array([[float(x) for x in row] for row in g["S"]])
+    ctx = lib.Context((2, 2, 1), (1, 1, 1, 1), 2, 0.0, 0, "f32")
+    h = np.array([int(x) - 1 for x in g["h1"][0]] + [int(x) - 1 for x in g["h2"][0]] + [0], np.int32)
+    v = np.array([int(x) for x in g["v1"][0]] + [int(x) for x in g["v2"][0]] + [1], np.int8)
+    ctx.tt_sketch_set_tables(h, v)
+    A = np.arange(1.0, 5.0)
+    Ad = torch.tensor(A, dtype=torch.float32, device="cuda")
+    Y = [torch.zeros(2, 2, device="cuda"), torch.zeros(2, 2, device="cuda"), torch.zeros(2, 1, device="cuda")]
+    ctx.tt_sketch_unfold(Ad, -1, 0, Y)
+    torch.cuda.synchronize()
+    assert np.array_equal(Y[2].cpu().numpy()[:, 0], S @ A)
+    ctx.close()
+
+
+# ---------------------------------------------------------------------------------------------
+# a1: data sketch Y_k = S A_(k)^T
+
+CASES_A = [((7, 5, 9), 64, "f32"), ((3, 5, 7, 2), 16, "f32"), ((50, 50, 50), 1024, "f64"),
+           ((33, 17, 9, 5), 512, "bf16"), ((40, 12, 10, 6), 256, "fp8"), ((64, 3, 1, 20), 128, "f32"),
+           ((1, 6, 8), 32, "f32"), ((100, 30, 20), 4096, "f32"), ((130, 7, 11), 2, "f32"),
+           ((300, 4, 5), 16384, "bf16"), ((12, 10, 8, 6, 4), 8192, "bf16"), ((41, 23, 6), 256, "f32")]
+
+
+def _data(dims, storage, seed):
+    a = synth.random_tensor(dims, seed)
+    flat, scales, exact = synth.quantize(a, storage)
+    return flat, scales, exact
+
+
+@pytest.mark.parametrize("dims,J,storage", CASES_A)
+def test_unfold_sketch_parity(dims, J, storage):
+    seed = 1000 + sum(dims) + J
+    flat, scales, exact = _data(dims, storage, seed)
+    ranks = (1,) * (len(dims) + 1)
+    ctx = lib.Context(dims, ranks, J, 1e-3, seed, storage)
+    Ad = lib.device_tensor(flat, storage)
+    sd = torch.tensor(scales, device="cuda") if scales is not None else None
+    Y = [torch.zeros(J * n, device="cuda") for n in dims]
+    for sweep in (0, 3):
+        ctx.tt_sketch_unfold(Ad, -1, sweep, Y, scales=sd)
+        torch.cuda.synchronize()
+        hs, vs = O.draw_sketch(seed, sweep, dims, J)
+        for k in range(len(dims)):
+            ref = O.sketch_unfolding(exact, hs, vs, J, k)
+            got = Y[k].cpu().numpy().reshape(J, dims[k])
+            assert rel(got, ref) <= TOL, (k, rel(got, ref))
+    # single-mode call writes only that mode
+    Y1 = [None] * len(dims)
+    Y1[1] = torch.zeros(J * dims[1], device="cuda")
+    ctx.tt_sketch_unfold(Ad, 1, 0, Y1, scales=sd)
+    hs, vs = O.draw_sketch(seed, 0, dims, J)
+    assert rel(Y1[1].cpu().numpy().reshape(J, dims[1]), O.sketch_unfolding(exact, hs, vs, J, 1)) <= TOL
+    ctx.close()
+
+
+def test_unfold_sketch_rejects_bad_calls():
+    ctx = lib.Context((4, 5, 6), (1, 1, 1, 1), 16, 1e-3, 1, "f32")
+    A = torch.zeros(120, device="cuda")
+    Y = [torch.zeros(16 * n, device="cuda") for n in (4, 5, 6)]
+    with pytest.raises(lib.TtError) as e:
+        ctx.tt_sketch_unfold(A, 3, 0, Y)
+    assert e.value.code == lib.TT_EINVAL
+    with pytest.raises(lib.TtError) as e:
+        ctx.tt_sketch_unfold(A, 0, 0, Y, scales=torch.ones(4, device="cuda"))
+    assert e.value.code == lib.TT_EINVAL
+    ctx.close()
+
+
+# ---------------------------------------------------------------------------------------------
+# a2-a4: interface sketch S H_k
+
+CASES_B = [((6, 5, 7), (1, 2, 3, 1), 32), ((4, 3, 5, 6), (1, 3, 4, 2, 1), 64), ((9, 8), (1, 4, 1), 16),
+           ((20, 30, 25, 10), (1, 4, 5, 3, 1), 256), ((50, 50, 50), (1, 5, 5, 1), 1024),
+           ((10, 12, 3, 9), (1, 8, 3, 8, 1), 2048), ((7, 7, 7, 7, 7), (1, 3, 3, 3, 3, 1), 4096),
+           ((5, 6, 4), (1, 2, 2, 1), 2), ((30, 20, 10), (1, 12, 10, 1), 16384)]
+
+
+@pytest.mark.parametrize("dims,ranks,J", CASES_B)
+def test_interface_sketch_parity(dims, ranks, J):
+    seed = 77 + J
+    cores = synth.random_tt(dims, ranks, seed)
+    ctx = lib.Context(dims, ranks, J, 1e-3, seed, "f32")
+    dc = lib.device_cores(cores)
+    c32 = [np.asarray(g, np.float32).astype(np.float64) for g in cores]
+    for sweep in (0, 2):
+        hs, vs = O.draw_sketch(seed, sweep, dims, J)
+        for k in range(len(dims)):
+            s = ranks[k] * ranks[k + 1]
+            SH = torch.zeros(J * s, device="cuda")
+            ctx.tt_sketch_interface(dc, k, sweep, SH)
+            torch.cuda.synchronize()
+            got = SH.cpu().numpy().reshape(s, J).T
+            ref = O.sketch_interface_fft(c32, hs, vs, J, k)
+            assert rel(got, ref) <= TOL, (k, rel(got, ref))
+    ctx.close()
+
+
+# ---------------------------------------------------------------------------------------------
+# a5-a6: proximal update
+
+@pytest.mark.parametrize("J,n,r0,r1,sigma", [(256, 7, 3, 4, 1e-3), (4096, 100, 10, 10, 1e-3), (2048, 256, 1, 20, 0.5),
+                                             (1024, 50, 5, 5, 0.0), (8192, 40, 8, 8, 1e-3), (512, 128, 12, 12, 1e-3),
+                                             (64, 3, 1, 1, 2.0)])
+def test_prox_update_parity(J, n, r0, r1, sigma):
+    rng = np.random.default_rng(J + n)
+    s = r0 * r1
+    # well-conditioned sketched interface: orthonormal columns scaled to a near-isometry
+    SH = np.linalg.qr(rng.standard_normal((J, s)))[0] * (1.0 + 0.1 * rng.standard_normal(s))
+    Y = rng.standard_normal((J, n))
+    G = rng.standard_normal((r0, n, r1))
+    SH32, Y32, G32 = (x.astype(np.float32) for x in (SH, Y, G))
+    dims = (n, 4, 3) if r0 == 1 else (5, n, 3)
+    k = 0 if r0 == 1 else 1
+    ranks = (1, r1, 1, 1) if k == 0 else (1, r0, r1, 1)
+    ctx = lib.Context(dims, ranks, J, sigma, 5, "f32")
+    Yd = torch.from_numpy(np.ascontiguousarray(Y32)).cuda()  # J x n row-major
+    SHd = torch.from_numpy(np.ascontiguousarray(SH32.T)).cuda()  # column-major J x s
+    core = torch.from_numpy(np.ascontiguousarray(G32.ravel(order="F"))).cuda()
+    ctx.tt_prox_update(Yd, SHd, core, k)
+    got = core.cpu().numpy().astype(np.float64).reshape(r0, n, r1, order="F")
+    ref = O.prox_update(Y32.astype(np.float64), SH32.astype(np.float64), G32.astype(np.float64), sigma)
+    assert rel(got, ref) <= TOL, rel(got, ref)
+    ctx.close()
+
+
+def test_prox_update_not_spd_leaves_core():
+    ctx = lib.Context((6, 4, 3), (1, 2, 2, 1), 32, 0.0, 5, "f32")
+    Yd = torch.randn(32, 6, device="cuda")
+    SHd = torch.zeros(32 * 2, device="cuda")
+    core = torch.randn(12, device="cuda")
+    before = core.clone()
+    with pytest.raises(lib.TtError) as e:
+        ctx.tt_prox_update(Yd, SHd, core, 0)
+    assert e.value.code == lib.TT_ENOTSPD
+    assert torch.equal(core, before)
+    ctx.close()
+
+
+# ---------------------------------------------------------------------------------------------
+# a7-a8: orthogonalisation
+
+@pytest.mark.parametrize("dims,ranks", [((6, 7, 5, 4), (1, 3, 4, 2, 1)), ((256, 256, 3, 128), (1, 20, 3, 20, 1)),
+                                        ((10, 12, 3, 9), (1, 8, 3, 8, 1)), ((40, 40, 40), (1, 8, 8, 1))])
+def test_orthogonalization_parity(dims, ranks):
+    cores = synth.random_tt(dims, ranks, 31)
+    c32 = [np.asarray(g, np.float32).astype(np.float64) for g in cores]
+    ctx = lib.Context(dims, ranks, 64, 1e-3, 5, "f32")
+    dc = lib.device_cores(cores)
+    ctx.tt_orthogonalize(dc, -1)
+    got = lib.host_cores(dc, ranks, dims)
+    ref = O.orthogonalize_right_to_left(c32)
+    for k in range(len(dims)):
+        assert rel(got[k], ref[k]) <= 1e-4, (k, rel(got[k], ref[k]))
+    for k in range(len(dims) - 1):
+        ctx.tt_orthogonalize(dc, +1, k)
+        O.left_orthogonalize_step(ref, k)
+        got = lib.host_cores(dc, ranks, dims)
+        assert rel(got[k], ref[k]) <= 1e-4, (k, rel(got[k], ref[k]))
+        assert rel(got[k + 1], ref[k + 1]) <= 1e-4
+    assert rel(O.tt_full(got), O.tt_full(c32)) <= 1e-5
+    ctx.close()
+
+
+# ---------------------------------------------------------------------------------------------
+# a9: relative error
+
+@pytest.mark.parametrize("dims,ranks,storage", [((20, 18, 16), (1, 4, 5, 1), "f32"), ((9, 8, 7, 6), (1, 3, 4, 2, 1), "f64"),
+                                                ((33, 17, 9, 5), (1, 3, 3, 3, 1), "bf16"), ((40, 12, 10, 6), (1, 2, 3, 2, 1), "fp8"),
+                                                ((64, 48), (1, 7, 1), "f32")])
+def test_rel_error_parity(dims, ranks, storage):
+    true = synth.random_tt(dims, ranks, 3)
+    a = synth.add_noise(synth.contract_cores(true), 0.05, np.random.default_rng(4))
+    flat, scales, exact = synth.quantize(a, storage)
+    est = synth.random_tt(dims, ranks, 5)
+    c32 = [np.asarray(g, np.float32).astype(np.float64) for g in est]
+    ctx = lib.Context(dims, ranks, 64, 1e-3, 5, storage)
+    sd = torch.tensor(scales, device="cuda") if scales is not None else None
+    e = ctx.tt_rel_error(lib.device_tensor(flat, storage), lib.device_cores(est), scales=sd)
+    ref = O.rel_error(exact, c32)
+    assert abs(e - ref) <= 1e-5 * ref, (e, ref)
+    ctx.close()
+
+
+# ---------------------------------------------------------------------------------------------
+# whole sweeps (Algorithm 1)
+
+def _run_sweeps(w, storage, nsweeps):
+    p = synth.make_problem(w, storage=storage)
+    ctx = lib.Context(w.dims, p.ranks, w.J, w.lam, p.sketch_seed, storage)
+    A = lib.device_tensor(p.storage, storage)
+    sd = torch.tensor(p.scales, device="cuda") if p.scales is not None else None
+    dc = lib.device_cores(p.init_cores)
+    changes = ctx.tt_prox_als_sweep(A, dc, nsweeps, 0, scales=sd)
+    err = ctx.tt_rel_error(A, dc, scales=sd)
+    got = lib.host_cores(dc, p.ranks, w.dims)
+    ref, ref_changes = O.tt_ts(p.tensor, p.init_cores, p.sketch_seed, w.J, w.lam, nsweeps)
+    ctx.close()
+    return p, got, err, changes, ref, ref_changes
+
+
+def test_sweeps_order3_50_r5_parity():
+    """The order-3 50^3 workload (ranks (1,5,5,1), J=1024, lambda=1e-3, 10 sweeps)."""
+    w = synth.WORKLOADS["order3-50-r5"]
+    p, got, err, changes, ref, ref_changes = _run_sweeps(w, "f64", w.sweeps)
+    err_ref = O.rel_error(p.tensor, ref)
+    assert abs(err - err_ref) <= 1e-5 * err_ref, (err, err_ref)
+    assert rel(O.tt_full(got), O.tt_full(ref)) <= 1e-4
+    assert abs(changes[-1] - ref_changes[-1]) <= 1e-3 * max(ref_changes[-1], 1e-9) + 1e-7
+
+
+def test_sweeps_scaled_order4_parity():
+    w = synth.WORKLOADS["order4-100-r10"].scaled((24, 20, 18, 16), J=512)
+    p, got, err, changes, ref, ref_changes = _run_sweeps(w, "f32", 4)
+    err_ref = O.rel_error(p.tensor, ref)
+    assert abs(err - err_ref) <= 1e-5 * err_ref, (err, err_ref)
+
+
+def test_sweep_exact_tt_recovery_on_gpu():
+    dims, ranks = (12, 10, 11, 9), (1, 3, 3, 3, 1)
+    A = synth.contract_cores(synth.random_tt(dims, ranks, 15))
+    init = synth.random_tt(dims, ranks, 16)
+    ctx = lib.Context(dims, ranks, 256, 1e-3, 31, "f32")
+    Ad = lib.device_tensor(A.ravel(order="F"), "f32")
+    dc = lib.device_cores(init)
+    ctx.tt_prox_als_sweep(Ad, dc, 30, 0)
+    assert ctx.tt_rel_error(Ad, dc) < 1e-5
+    ctx.close()
