@@ -1,0 +1,341 @@
+#!/usr/bin/env python
+"""Benchmark of the sketched proximal TT-ALS hot path (Algorithm 1, TT-TS) on one GB300.
+
+One step = one outer iteration (sweep) of Algorithm 1 on the order-4 100^4 FP32 workload
+(TT ranks (1,10,10,10,1), 1e-2 relative noise, J = 4096, lambda = 1e-3): right-to-left
+orthogonalisation, a fresh TensorSketch draw, for every core the FFT interface sketch, the
+data sketch of the unfolding (a full read of the 400 MB tensor per core), the proximal
+Cholesky update and the QR step, then the relative error (one more read of the tensor).
+
+Prints ONE JSON line (rank 0). `--impl reference` times the CPU FP64 oracle instead.
+Under torchrun (N > 1) every rank runs an independent replica (the single-tensor path has no
+data-parallel split without a collective) and rank 0 reports the aggregate.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ALS sweeps/s + unfold-sketch HBM GB/s at equal rel. error vs plain FP32 GPU"
+UNIT = "sweeps/s"
+DEFAULT_WORKLOAD = "order4-100-r10"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--storage", default=None, help="override the workload's storage type")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-columns", type=int, default=0, help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------------------------
+# clocks during the timed region
+
+class ClockSampler:
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, gpu_id: str):
+        self.samples = []
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + ",".join(self.FIELDS), "--format=csv,noheader,nounits",
+                 "-lms", "50", "-i", gpu_id], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._reader, daemon=True)
+        self.thread.start()
+        t0 = time.time()
+        while not self.samples and time.time() - t0 < 5.0:
+            time.sleep(0.02)
+
+    def _reader(self):
+        for line in self.proc.stdout:
+            self.samples.append((time.time(), [x.strip() for x in line.split(",")]))
+
+    def stop(self):
+        if self.proc is not None:
+            time.sleep(0.12)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self, t0, t1):
+        if self.proc is None:
+            return None
+        win = [s for (t, s) in self.samples if t0 - 0.06 <= t <= t1 + 0.06] or \
+              [s for (t, s) in self.samples if t >= t0 - 0.2][:2]
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for s in win:
+            try:
+                sm.append(float(s[0]))
+                mx.append(float(s[1]))
+            except (ValueError, IndexError):
+                continue
+            for nm, val in zip(names, s[4:8]):
+                if val.strip().lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------------------
+# CPU oracle legs
+
+def _oracle_threads_env():
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[v] = "1"
+    return env
+
+
+def cpu_sample_main(args):
+    """Child process: time one oracle sweep (Algorithm 1 outer iteration) of the workload, or
+    `--cpu-columns q` columns of the oracle's data sketch per step (reference arm)."""
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    import numpy as np
+    import tt_oracle as O
+    from paper_2309_08093_gb300 import synth
+
+    w = synth.WORKLOADS[args.workload]
+    p = synth.make_problem(w, storage=args.storage)
+    if args.cpu_columns <= 0:
+        t = time.perf_counter()
+        O.tt_ts_sweep(p.tensor, p.init_cores, p.sketch_seed, 0, w.J, w.lam)
+        dt = time.perf_counter() - t
+        print(json.dumps({"sweep_s": dt}))
+        return
+    # reference arm: each step sketches q columns of Y_k by definition, cycling over modes/columns
+    hs, vs = O.draw_sketch(p.sketch_seed, 0, w.dims, w.J)
+    cols = [(k, i) for k in range(w.d) for i in range(w.dims[k])]
+    times = []
+    pos = 0
+    if args.cpu_columns < 0:  # size q so that the whole run takes about 150 s
+        t = time.perf_counter()
+        for j in range(2):
+            O.sketch_unfolding_column(p.tensor, hs, vs, w.J, cols[j][0], cols[j][1])
+        per = (time.perf_counter() - t) / 2
+        args.cpu_columns = max(1, int(150.0 / ((args.steps + args.warmup) * max(per, 1e-3))))
+    for step in range(args.warmup + args.steps):
+        t = time.perf_counter()
+        for _ in range(args.cpu_columns):
+            k, i = cols[pos % len(cols)]
+            pos += 1
+            O.sketch_unfolding_column(p.tensor, hs, vs, w.J, k, i)
+        times.append(time.perf_counter() - t)
+    timed = times[args.warmup:]
+    per_col = sum(timed) / (len(timed) * args.cpu_columns)
+    print(json.dumps({"per_column_s": per_col, "columns_per_sweep": len(cols), "steps": len(timed),
+                      "step_s": sum(timed) / len(timed), "q": args.cpu_columns}))
+
+
+def run_cpu_child(extra):
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-sample"] + extra
+    p = subprocess.run(cmd, capture_output=True, text=True, env=_oracle_threads_env(), timeout=1800)
+    if p.returncode != 0:
+        raise RuntimeError(p.stderr[-2000:])
+    return json.loads(p.stdout.strip().splitlines()[-1])
+
+
+def reference_main(args, rank, world):
+    if rank != 0:
+        return
+    from paper_2309_08093_gb300 import synth
+
+    w = synth.WORKLOADS[args.workload]
+    res = run_cpu_child(["--workload", args.workload, "--cpu-columns", "-1", "--steps", str(args.steps),
+                         "--warmup", str(args.warmup)] + (["--storage", args.storage] if args.storage else []))
+    q = res["q"]
+    sweep_s = res["per_column_s"] * res["columns_per_sweep"]
+    value = 1.0 / sweep_s
+    sample = (f"per step {q} column(s) of the data sketch Y_k = S A_(k)^T computed by the oracle's definition "
+              f"(FP64 numpy, 1 thread), cycling over all {res['columns_per_sweep']} columns of the {w.d} modes; "
+              f"sweep time = columns per sweep x mean column time (the data sketch is >95% of an oracle sweep "
+              f"on this workload)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["step_s"] * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(w, args.storage or w.storage),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(w, storage):
+    return {"workload": f"{w.name}: {'x'.join(map(str, w.dims))} {storage} tensor, TT ranks {list(w.ranks)}, "
+                        f"J={w.J}, lambda={w.lam}, noise={w.noise}",
+            "dims": list(w.dims), "ranks": list(w.ranks), "J": w.J, "lambda": w.lam, "storage": storage,
+            "step": "one sweep of Algorithm 1 (d core updates) + relative error",
+            "l2": "inputs larger than L2 (tensor %.0f MB > 129 MB)" % (w.numel * {"f64": 8, "f32": 4, "bf16": 2, "fp8": 1}[storage] / 1e6)}
+
+
+# ---------------------------------------------------------------------------------------------
+# GPU arm
+
+def main():
+    args = parse()
+    if args.cpu_sample:
+        cpu_sample_main(args)
+        return
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        reference_main(args, rank, world)
+        return
+
+    import numpy as np
+    import torch
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    from paper_2309_08093_gb300 import build, lib, synth
+
+    build.build()
+    w = synth.WORKLOADS[args.workload]
+    storage = args.storage or w.storage
+    p = synth.make_problem(w, storage=storage)
+    stream = torch.cuda.current_stream()
+    ctx = lib.Context(w.dims, p.ranks, w.J, w.lam, p.sketch_seed, storage)
+    A = lib.device_tensor(p.storage, storage, device=dev)
+    scales = torch.tensor(p.scales, device=dev) if p.scales is not None else None
+    cores = lib.device_cores(p.init_cores, device=dev)
+
+    def step(t):
+        ctx.tt_prox_als_sweep(A, cores, 1, t, scales=scales, rel_change=False)
+        return ctx.tt_rel_error(A, cores, scales=scales)
+
+    for t in range(args.warmup):
+        step(t)
+    torch.cuda.synchronize()
+
+    gpu_id = torch.cuda.get_device_properties(dev).uuid
+    gpu_id = "GPU-" + str(gpu_id) if not str(gpu_id).startswith("GPU-") else str(gpu_id)
+    clocks = ClockSampler(gpu_id)
+    ctx.tt_profile_enable(True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_wall0 = time.time()
+    e0.record(stream)
+    err = None
+    for t in range(args.steps):
+        err = step(args.warmup + t)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_wall1 = time.time()
+    if dist:
+        dist.barrier()
+    prof = ctx.tt_profile_read()
+    ctx.tt_profile_enable(False)
+    clocks.stop()
+    clk = clocks.summary(t_wall0, t_wall1)
+    ms = e0.elapsed_time(e1)
+    if dist:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    sweeps_per_s = world * args.steps / (ms / 1e3)
+
+    hbm, peak_kind = peaks()
+    unfold_avg_ms = prof["unfold_ms"] / max(1, prof["unfold_launches"])
+    bytes_per_launch = prof["unfold_bytes"] / max(1, prof["unfold_launches"])
+    achieved = bytes_per_launch / (unfold_avg_ms * 1e-3) / 1e9
+    mode_gbs = [(bytes_per_launch / (m / n * 1e-3) / 1e9) if n else None
+                for m, n in zip(prof["mode_ms"], prof["mode_launches"])]
+
+    line = None
+    if rank == 0:
+        line = {"metric": METRIC, "value": sweeps_per_s, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": storage, "data": "synthetic",
+                "config": workload_config(w, storage),
+                "rel_error_after": err,
+                "roofline": {"kernel": "unfold sketch (k_unfold_mode0 + k_unfold_col)", "bound": "hbm",
+                             "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                             "peak_kind": peak_kind, "traffic": None,
+                             "bytes_per_launch": bytes_per_launch, "avg_launch_ms": unfold_avg_ms,
+                             "per_mode_gbs": mode_gbs,
+                             "share_of_step": prof["unfold_ms"] / ms},
+                "gpu_launches": prof["kernel_launches"],
+                "clocks": clk}
+    # end-to-end through the host-buffer entry point (pinned host memory)
+    if rank == 0 and not args.no_e2e:
+        A_h = torch.from_numpy(np.ascontiguousarray(p.storage)).pin_memory().numpy() if storage != "bf16" else \
+            torch.from_numpy(np.ascontiguousarray(p.storage.view(np.int16))).pin_memory().numpy()
+        cores_h = [torch.from_numpy(np.ascontiguousarray(np.asarray(g, np.float32).ravel(order="F"))).pin_memory().numpy()
+                   for g in p.init_cores]
+        sc_h = np.ascontiguousarray(p.scales, dtype=np.float32) if p.scales is not None else None
+        ne = max(3, min(20, args.steps))
+        ctx.tt_prox_als_sweep_host(A_h, cores_h, 1, 0, scales_host=sc_h)  # warm (allocates staging)
+        t0 = time.perf_counter()
+        for t in range(ne):
+            ctx.tt_prox_als_sweep_host(A_h, cores_h, 1, t + 1, scales_host=sc_h)
+        e2e_s = (time.perf_counter() - t0) / ne
+        core_bytes = sum(int(g.size) * 4 for g in cores_h)
+        line["e2e"] = {"value": 1.0 / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(A_h.nbytes) + core_bytes
+                       + (int(sc_h.nbytes) if sc_h is not None else 0),
+                       "d2h_bytes_per_step": core_bytes + 16,
+                       "note": "tt_prox_als_sweep_host: H2D copy of the tensor and cores, one sweep, the relative "
+                               "error, D2H of the cores, rel-change and rel error; synchronised; wall clock"}
+    ctx.close()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            res = run_cpu_child(["--workload", args.workload] + (["--storage", args.storage] if args.storage else []))
+            line["cpu_baseline"] = {"value": 1.0 / res["sweep_s"], "unit": UNIT, "cores": 1, "kind": "oracle",
+                                    "sample": "one full oracle sweep (Algorithm 1 outer iteration, FP64 numpy, "
+                                              "1 thread) on the same workload, timed once"}
+        except Exception as e:  # report, do not hide
+            line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                    "sample": f"failed: {str(e)[-200:]}"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

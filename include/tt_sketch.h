@@ -68,7 +68,7 @@ typedef struct {
   int d;              /* order of the tensor, 2 <= d <= 8 */
   const int64_t* n;   /* host array of d mode sizes, each >= 1 */
   const int* r;       /* host array of d+1 TT ranks, r[0] = r[d] = 1, each >= 1;
-                         r[k]*r[k+1] <= 256 */
+                         r[k]*r[k+1] <= 160 and r[k]*n[k]*r[k+1] <= 40000 (in-CTA solves) */
   int J;              /* sketch size m (power of two, 2..16384) */
   double lambda;      /* proximal weight sigma >= 0 of Eq. (lrtt_sub_prox) */
   uint64_t seed;      /* seed of the hash/sign draws */
@@ -151,8 +151,9 @@ int tt_orthogonalize(tt_ctx* ctx, float* const* cores_dev, int direction, int k)
  * orthogonalisation, a fresh sketch, then for k = 0..d-1 parts (b), (a), (c) and (k < d-1) the QR
  * step. Cores are updated in place. If rel_change_out is not NULL it receives, per sweep,
  * max_k ||G_k^(t+1) - G_k^(t)||_F / ||G_k^(t+1)||_F (Sec. 5), where G_k^(t) is core k right
- * before its update; the call then synchronises. Returns TT_ENOTSPD if a Gram matrix is not
- * positive definite (cores are then left as they were after the last successful update).
+ * before its update. The call synchronises the stream at its end to report the status of the
+ * solves. Returns TT_ENOTSPD if a Gram matrix is not positive definite (cores are then left as
+ * they were after the last successful update).
  */
 int tt_prox_als_sweep(tt_ctx* ctx, const void* A_dev, const float* scales_dev,
                       float* const* cores_dev, int nsweeps, uint64_t first_sweep,
@@ -164,6 +165,34 @@ int tt_prox_als_sweep(tt_ctx* ctx, const void* A_dev, const float* scales_dev,
  */
 int tt_rel_error(tt_ctx* ctx, const void* A_dev, const float* scales_dev,
                  float* const* cores_dev, double* out);
+
+/*
+ * The same sweeps on HOST buffers: A_host (the dense tensor in the context's storage type,
+ * layout as above), scales_host (FP8 only, else NULL) and the d FP32 cores (host array of host
+ * pointers, updated in place). Each call copies the inputs to library-owned device buffers
+ * (allocated on first use), runs tt_prox_als_sweep, then (if rel_error_out is not NULL) the
+ * relative error of tt_rel_error, and copies the cores back; it synchronises. Host memory should
+ * be page-locked for full copy bandwidth. rel_change_out as above.
+ */
+int tt_prox_als_sweep_host(tt_ctx* ctx, const void* A_host, const float* scales_host,
+                           float* const* cores_host, int nsweeps, uint64_t first_sweep,
+                           double* rel_change_out, double* rel_error_out);
+
+/* Per-context counters for measurement (not part of the method). */
+typedef struct {
+  double unfold_ms;          /* summed device time of the unfold-sketch kernels (CUDA events) */
+  int64_t unfold_launches;   /* number of unfold-sketch kernel launches timed */
+  int64_t unfold_bytes;      /* algorithmic bytes those launches read: entries x storage size */
+  int64_t kernel_launches;   /* every kernel this library launched since the reset */
+  double mode_ms[8];         /* unfold device time per mode */
+  int64_t mode_launches[8];
+} tt_profile;
+
+/* on != 0: reset the counters and start timing unfold launches; on == 0: stop timing. */
+int tt_profile_enable(tt_ctx* ctx, int on);
+
+/* Synchronise the stream and read the counters accumulated since the last reset. */
+int tt_profile_read(tt_ctx* ctx, tt_profile* out);
 
 #ifdef __cplusplus
 }

@@ -220,7 +220,7 @@ def sketch_unfolding_column(A: np.ndarray, hs, vs, J: int, k: int, ik: int) -> n
     restricted to (sum_{s!=k} h_s(i_s)) mod J = b. S is built from the modes s != k.
     """
     d = A.ndim
-    sub = np.take(A, ik, axis=k)  # remaining modes, in order
+    sub = A[(slice(None),) * k + (ik,)]  # remaining modes, in order (a view)
     others = [s for s in range(d) if s != k]
     bucket = np.zeros(sub.shape, dtype=np.int64)
     sign = np.ones(sub.shape)

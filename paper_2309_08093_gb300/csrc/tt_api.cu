@@ -177,3 +177,101 @@ extern "C" int tt_rel_error(tt_ctx* c, const void* A, const float* scales, float
   *out = (h[1] > 0) ? sqrt(h[0] / h[1]) : 0.0;
   return TT_OK;
 }
+
+// ---------------------------------------------------------------------------------------------
+// host-buffer sweep
+
+int tt_elem_bytes(int dtype) {
+  switch (dtype) {
+    case TT_F64: return 8;
+    case TT_F32: return 4;
+    case TT_BF16: return 2;
+    default: return 1;
+  }
+}
+
+extern "C" int tt_prox_als_sweep_host(tt_ctx* c, const void* A_host, const float* scales_host,
+                                      float* const* cores_host, int nsweeps, uint64_t first_sweep,
+                                      double* rel_change_out, double* rel_error_out) {
+  if (!c) return TT_EINVAL;
+  TT_TRY(check_data(c, A_host, scales_host));
+  TT_TRY(check_cores(c, cores_host));
+  c->err.clear();
+  const size_t abytes = (size_t)c->N * tt_elem_bytes(c->dtype);
+  if (!c->d_A_stage) TT_CUDA(c, cudaMalloc(&c->d_A_stage, abytes));
+  if (scales_host && !c->d_scales_stage) TT_CUDA(c, cudaMalloc((void**)&c->d_scales_stage, sizeof(float) * c->n[0]));
+  size_t csz[TT_MAX_D];
+  for (int k = 0; k < c->d; ++k) {
+    csz[k] = sizeof(float) * (size_t)c->r[k] * c->n[k] * c->r[k + 1];
+    if (!c->d_cores_stage[k]) TT_CUDA(c, cudaMalloc((void**)&c->d_cores_stage[k], csz[k]));
+  }
+  TT_CUDA(c, cudaMemcpyAsync(c->d_A_stage, A_host, abytes, cudaMemcpyHostToDevice, c->stream));
+  if (scales_host)
+    TT_CUDA(c, cudaMemcpyAsync(c->d_scales_stage, scales_host, sizeof(float) * c->n[0], cudaMemcpyHostToDevice, c->stream));
+  for (int k = 0; k < c->d; ++k)
+    TT_CUDA(c, cudaMemcpyAsync(c->d_cores_stage[k], cores_host[k], csz[k], cudaMemcpyHostToDevice, c->stream));
+  const float* sc = scales_host ? c->d_scales_stage : nullptr;
+  int rc = tt_prox_als_sweep(c, c->d_A_stage, sc, c->d_cores_stage, nsweeps, first_sweep, rel_change_out);
+  if (rc == TT_OK && rel_error_out) rc = tt_rel_error(c, c->d_A_stage, sc, c->d_cores_stage, rel_error_out);
+  for (int k = 0; k < c->d; ++k)
+    TT_CUDA(c, cudaMemcpyAsync(cores_host[k], c->d_cores_stage[k], csz[k], cudaMemcpyDeviceToHost, c->stream));
+  TT_CUDA(c, cudaStreamSynchronize(c->stream));
+  return rc;
+}
+
+// ---------------------------------------------------------------------------------------------
+// measurement counters
+
+int tt_prof_begin(tt_ctx* c, int k) {
+  if (!c->profiling) return TT_OK;
+  while ((int)c->ev_pool.size() < c->ev_used + 2) {
+    cudaEvent_t e;
+    TT_CUDA(c, cudaEventCreate(&e));
+    c->ev_pool.push_back(e);
+  }
+  TT_CUDA(c, cudaEventRecord(c->ev_pool[c->ev_used], c->stream));
+  c->ev_mode.push_back(k);
+  c->ev_used += 1;
+  return TT_OK;
+}
+
+int tt_prof_end(tt_ctx* c) {
+  if (!c->profiling) return TT_OK;
+  TT_CUDA(c, cudaEventRecord(c->ev_pool[c->ev_used], c->stream));
+  c->ev_used += 1;
+  c->prof_bytes += (int64_t)c->N * tt_elem_bytes(c->dtype);
+  return TT_OK;
+}
+
+extern "C" int tt_profile_enable(tt_ctx* c, int on) {
+  if (!c) return TT_EINVAL;
+  if (on) {
+    TT_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->ev_used = 0;
+    c->ev_mode.clear();
+    c->prof_bytes = 0;
+    c->launches = 0;
+  }
+  c->profiling = on != 0;
+  return TT_OK;
+}
+
+extern "C" int tt_profile_read(tt_ctx* c, tt_profile* out) {
+  if (!c || !out) return TT_EINVAL;
+  TT_CUDA(c, cudaStreamSynchronize(c->stream));
+  *out = tt_profile{};
+  for (int i = 0; i + 1 < c->ev_used; i += 2) {
+    float ms = 0.f;
+    TT_CUDA(c, cudaEventElapsedTime(&ms, c->ev_pool[i], c->ev_pool[i + 1]));
+    int k = c->ev_mode[i / 2];
+    out->unfold_ms += ms;
+    out->unfold_launches += 1;
+    if (k >= 0 && k < 8) {
+      out->mode_ms[k] += ms;
+      out->mode_launches[k] += 1;
+    }
+  }
+  out->unfold_bytes = c->prof_bytes;
+  out->kernel_launches = c->launches;
+  return TT_OK;
+}

@@ -162,6 +162,11 @@ static void free_all(tt_ctx* c) {
                 c->d_gram, c->d_core_old, c->d_changes, c->d_status, c->d_err_acc};
   for (void* p : ps)
     if (p) cudaFree(p);
+  if (c->d_A_stage) cudaFree(c->d_A_stage);
+  if (c->d_scales_stage) cudaFree(c->d_scales_stage);
+  for (int k = 0; k < TT_MAX_D; ++k)
+    if (c->d_cores_stage[k]) cudaFree(c->d_cores_stage[k]);
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
 }
 
 extern "C" int tt_sketch_init(tt_ctx** out, const tt_params* p, void* stream) {

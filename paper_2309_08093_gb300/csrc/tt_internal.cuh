@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/tt_sketch.h"
 
@@ -67,6 +68,19 @@ struct tt_ctx {
   int* d_status = nullptr;     // device error flag (0 = ok, else TT_E* code)
   double* d_err_acc = nullptr; // rel-error accumulators (2 doubles)
   int changes_cap = 0;
+
+  // measurement counters (tt_profile_*)
+  int64_t launches = 0;
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<int> ev_mode;   // mode of each recorded pair (pairs at 2i, 2i+1)
+  int ev_used = 0;            // events in use
+  int64_t prof_bytes = 0;
+
+  // host-buffer entry point staging (allocated on first use)
+  void* d_A_stage = nullptr;
+  float* d_scales_stage = nullptr;
+  float* d_cores_stage[TT_MAX_D] = {nullptr};
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -99,6 +113,7 @@ int tt_cuda_check(tt_ctx* c, cudaError_t e, const char* what);
   do {                                                                \
     cudaError_t _e = cudaGetLastError();                              \
     if (_e != cudaSuccess) return tt_cuda_check(ctx, _e, what);       \
+    ++(ctx)->launches;                                                \
   } while (0)
 
 int tt_ensure_tables(tt_ctx* c, uint64_t sweep);
@@ -117,6 +132,9 @@ int tt_launch_qr_left(tt_ctx* c, float* core_k, float* core_k1, int k);
 int tt_launch_lq_right(tt_ctx* c, float* core_km1, float* core_k, int k);
 int tt_launch_rel_error(tt_ctx* c, const void* A, const float* scales, float* const* cores);
 int tt_read_status(tt_ctx* c);
+int tt_prof_begin(tt_ctx* c, int k);   // record a start event when profiling (returns TT_OK)
+int tt_prof_end(tt_ctx* c);
+int tt_elem_bytes(int dtype);
 
 // element loads of the data tensor in its storage type, converted to float
 template <int DT>

