@@ -178,6 +178,28 @@ int tt_prox_als_sweep_host(tt_ctx* ctx, const void* A_host, const float* scales_
                            float* const* cores_host, int nsweeps, uint64_t first_sweep,
                            double* rel_change_out, double* rel_error_out);
 
+/*
+ * Allocation-free proximal update. The paper has no counterpart: this is a service for callers
+ * that cannot allocate device memory -- for example an application whose memory manager has
+ * already reserved the device memory it is allowed to use, or a latency-critical loop that must
+ * not pay for cudaMalloc's implicit device-wide synchronisation. It computes exactly what
+ * tt_prox_update computes for a core of shape r0 x n x r1, without a context:
+ *   Y_dev (J x n row-major), SH_dev (J x r0*r1 column-major), core_dev (read as the proximal
+ *   centre, overwritten with the update), sigma >= 0, cuda_stream (a cudaStream_t or NULL).
+ * Limits: r0*r1 <= 160 and n <= 1024; larger sizes are rejected with TT_EINVAL (and a message
+ * on stderr) before anything is launched.
+ * Memory: it never calls cudaMalloc/cudaFree or any allocating routine. Its scratch (~1.5 MB of
+ * FP64 Gram accumulators and a status word) is a static array in the library's device image, so
+ * every GPU that loads the library holds it until the process exits. The first call on a device
+ * looks up that array's device address while the device is current; make that first call before
+ * any stream capture. All calls share the one array: each call clears what it needs, but calls
+ * that overlap on the GPU (other streams, other host threads) race and give wrong results.
+ * Synchronises `cuda_stream`; returns TT_OK, TT_ENOTSPD (core unchanged), TT_ENONFINITE,
+ * TT_EINVAL or TT_ECUDA.
+ */
+int tt_prox_update_noalloc(const float* Y_dev, const float* SH_dev, float* core_dev, int J, int n,
+                           int r0, int r1, double sigma, void* cuda_stream);
+
 /* Per-context counters for measurement (not part of the method). */
 typedef struct {
   double unfold_ms;          /* summed device time of the unfold-sketch kernels (CUDA events) */

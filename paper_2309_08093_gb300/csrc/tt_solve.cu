@@ -8,6 +8,8 @@
 //   k_qr_left     : Householder QR of G_k^L, G_k <- Q, G_{k+1} <- R G_{k+1}^R
 //   k_lq_right    : the same on (G_k^R)^T: G_k^R <- Q^T, G_{k-1}^L <- G_{k-1}^L R^T
 //   k_rel_error   : ||A - [[G]]||_F^2 and ||A||_F^2, one warp per mode-0 fibre
+#include <stdio.h>
+
 #include <algorithm>
 
 #include "tt_internal.cuh"
@@ -528,4 +530,92 @@ int tt_launch_rel_error(tt_ctx* c, const void* A, const float* scales, float* co
   }
   TT_LAUNCH(c, "k_rel_error");
   return TT_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Allocation-free variant of the proximal update (see tt_prox_update_noalloc in tt_sketch.h).
+//
+// Its only scratch -- the FP64 accumulators of [SH | Y]^T SH and the status word -- lives in the
+// file-scope array below, sized for s = r0*r1 <= 160 and n <= 1024. Every GPU that loads the
+// library holds these ~1.5 MB until the process exits. In host code `g_noalloc_scratch` only
+// names a host-side stand-in, so the device address is looked up once per device with
+// cudaGetSymbolAddress (on the first call made while that device is current).
+
+#include <mutex>
+
+#define TT_NOALLOC_MAX_S 160
+#define TT_NOALLOC_MAX_N 1024
+#define TT_NOALLOC_GRAM ((TT_NOALLOC_MAX_S + TT_NOALLOC_MAX_N) * TT_NOALLOC_MAX_S)
+#define TT_NOALLOC_MAX_DEVICES 64
+
+static __device__ __align__(256) double g_noalloc_scratch[TT_NOALLOC_GRAM + 32];
+
+static std::mutex g_noalloc_mutex;
+static void* g_noalloc_ptr[TT_NOALLOC_MAX_DEVICES];
+
+static int noalloc_scratch(void** out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= TT_NOALLOC_MAX_DEVICES) return TT_ECUDA;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return TT_ECUDA;
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return TT_OK;
+}
+
+extern "C" int tt_prox_update_noalloc(const float* Y_dev, const float* SH_dev, float* core_dev, int J, int n,
+                                      int r0, int r1, double sigma, void* cuda_stream) {
+  if (!Y_dev || !SH_dev || !core_dev) return TT_EINVAL;
+  const int s = r0 * r1;
+  if (J < 1 || n < 1 || r0 < 1 || r1 < 1 || s > TT_NOALLOC_MAX_S || n > TT_NOALLOC_MAX_N || !(sigma >= 0.0)) {
+    fprintf(stderr,
+            "tt_prox_update_noalloc: sizes outside the static scratch (need J >= 1, 1 <= n <= %d, "
+            "r0*r1 <= %d, sigma >= 0; got J=%d n=%d r0=%d r1=%d)\n",
+            TT_NOALLOC_MAX_N, TT_NOALLOC_MAX_S, J, n, r0, r1);
+    return TT_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  void* base = nullptr;
+  int rc = noalloc_scratch(&base);
+  if (rc) return rc;
+  double* gram = (double*)base;
+  int* status = (int*)(gram + TT_NOALLOC_GRAM);
+  // the array keeps the previous call's contents: clear the accumulators and the status word
+  if (cudaMemsetAsync(gram, 0, sizeof(double) * (size_t)(s + n) * s, st) != cudaSuccess) return TT_ECUDA;
+  if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return TT_ECUDA;
+  GramArgs g;
+  g.SH = SH_dev;
+  g.Y = Y_dev;
+  g.C = gram;
+  g.J = J;
+  g.s = s;
+  g.n = n;
+  g.kchunk = std::max(32, std::min(256, J));
+  dim3 grid((s + n + 31) / 32, (s + 31) / 32, (J + g.kchunk - 1) / g.kchunk);
+  k_gram<<<grid, 256, 0, st>>>(g);
+  if (cudaGetLastError() != cudaSuccess) return TT_ECUDA;
+  SolveArgs a;
+  a.C = gram;
+  a.core = core_dev;
+  a.change = nullptr;
+  a.status = status;
+  a.sigma = sigma;
+  a.s = s;
+  a.n = n;
+  a.r0 = r0;
+  a.r1 = r1;
+  const int budget = 48 * 1024;
+  a.chunk_rows = std::max(1, std::min(n, (budget - s * s) / s));
+  size_t smem = sizeof(float) * ((size_t)s * s + (size_t)a.chunk_rows * s);
+  if (cudaFuncSetAttribute(k_prox_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return TT_ECUDA;
+  k_prox_solve<<<1, 1024, smem, st>>>(a);
+  if (cudaGetLastError() != cudaSuccess) return TT_ECUDA;
+  int hst = 0;
+  if (cudaMemcpyAsync(&hst, status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return TT_ECUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return TT_ECUDA;
+  return hst;  // TT_OK, TT_ENOTSPD or TT_ENONFINITE
 }

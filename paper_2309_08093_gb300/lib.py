@@ -23,7 +23,7 @@ TT_FLAG_FIXED_SKETCH = 1
 EXPORTS = ["tt_sketch_init", "tt_sketch_destroy", "tt_last_error", "tt_sketch_tables",
            "tt_sketch_set_tables", "tt_sketch_unfold", "tt_sketch_interface", "tt_prox_update",
            "tt_orthogonalize", "tt_prox_als_sweep", "tt_rel_error", "tt_prox_als_sweep_host",
-           "tt_profile_enable", "tt_profile_read"]
+           "tt_profile_enable", "tt_profile_read", "tt_prox_update_noalloc"]
 
 
 class TtError(RuntimeError):
@@ -72,6 +72,7 @@ def load(path: str = LIB_PATH):
     L.tt_rel_error.argtypes = [vp, vp, vp, ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_double)]
     L.tt_prox_als_sweep_host.argtypes = [vp, vp, vp, ctypes.POINTER(vp), i, u64, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_double)]
+    L.tt_prox_update_noalloc.argtypes = [vp, vp, vp, i, i, i, i, ctypes.c_double, vp]
     L.tt_profile_enable.argtypes = [vp, i]
     L.tt_profile_read.argtypes = [vp, ctypes.POINTER(TtProfile)]
     for name in EXPORTS:
@@ -196,6 +197,16 @@ class Context:
         out = ctypes.c_double()
         self._check(self.lib.tt_rel_error(self.ctx, _ptr(A), _ptr(scales), _ptr_array(cores), ctypes.byref(out)))
         return out.value
+
+
+def tt_prox_update_noalloc(Y, SH, core, J: int, n: int, r0: int, r1: int, sigma: float, stream=None) -> int:
+    """Context-free proximal update that allocates no device memory (see tt_sketch.h).
+
+    For callers that cannot allocate device memory; returns the TT_* status code."""
+    L = load()
+    stream = _current_stream() if stream is None else stream
+    return L.tt_prox_update_noalloc(_ptr(Y), _ptr(SH), _ptr(core), int(J), int(n), int(r0), int(r1),
+                                    float(sigma), stream)
 
 
 # ---------------------------------------------------------------------------------------------
