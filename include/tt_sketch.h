@@ -13,7 +13,7 @@
  *     (linear index i = sum_s i_s prod_{t<s} n_t, the bijection of Sec. 2.2);
  *   - TT core k has shape r[k] x n[k] x r[k+1] and is stored FP32 with r[k] fastest
  *     (element (a, i, b) at a + r[k]*(i + n[k]*b)); r[0] = r[d] = 1 (Sec. 2.1);
- *   - Y_k (sketch of the mode-k unfolding) is FP32, J x n[k], row-major: Y_k[b*n[k] + i];
+ *   - Y_k (sketch of the mode-k unfolding) is FP32, J x n[k], column-major: Y_k[b + J*i];
  *   - S H_k is FP32, J x s_k with s_k = r[k]*r[k+1], column-major: SH[b + J*c] with column
  *     c = a + r[k]*b' (a indexes r[k], b' indexes r[k+1]; matches G_{k(2)}, Sec. 3).
  *   - The sketch size m of the paper is J; J must be a power of two, 2 <= J <= 16384.
@@ -110,7 +110,7 @@ int tt_sketch_set_tables(tt_ctx* ctx, const int32_t* h_host, const int8_t* v_hos
  *   scales_dev  : for TT_FP8E4M3, n[0] FP32 scales (A(i) = scale[i_0] * fp8(i)); else NULL;
  *   k           : mode in [0, d), or -1 for all modes;
  *   sweep       : sweep index t selecting the hash draw;
- *   Y_dev       : host array of d device pointers; Y_dev[k] (J x n[k], row-major) is written
+ *   Y_dev       : host array of d device pointers; Y_dev[k] (J x n[k], column-major) is written
  *                 for each requested mode (other entries may be NULL).
  */
 int tt_sketch_unfold(tt_ctx* ctx, const void* A_dev, const float* scales_dev, int k,
@@ -129,7 +129,7 @@ int tt_sketch_interface(tt_ctx* ctx, float* const* cores_dev, int k, uint64_t sw
 /*
  * Part (c): the proximal update of core k by Eq. (ite) (read with S^T S):
  *   G_{k(2)} <- (Y_k^T SH_k + sigma G_{k(2)}) (SH_k^T SH_k + sigma I)^{-1},
- * solved through a Cholesky factorisation. Y_dev: J x n[k] row-major; SH_dev: J x s_k
+ * solved through a Cholesky factorisation. Y_dev: J x n[k] column-major; SH_dev: J x s_k
  * column-major; core_dev is read (proximal centre) and overwritten with the update.
  * Returns TT_ENOTSPD if the Gram matrix is not positive definite (then core_dev is unchanged).
  * Synchronises the stream (the status is read back).
@@ -184,7 +184,7 @@ int tt_prox_als_sweep_host(tt_ctx* ctx, const void* A_host, const float* scales_
  * already reserved the device memory it is allowed to use, or a latency-critical loop that must
  * not pay for cudaMalloc's implicit device-wide synchronisation. It computes exactly what
  * tt_prox_update computes for a core of shape r0 x n x r1, without a context:
- *   Y_dev (J x n row-major), SH_dev (J x r0*r1 column-major), core_dev (read as the proximal
+ *   Y_dev (J x n column-major), SH_dev (J x r0*r1 column-major), core_dev (read as the proximal
  *   centre, overwritten with the update), sigma >= 0, cuda_stream (a cudaStream_t or NULL).
  * Limits: r0*r1 <= 160 and n <= 1024; larger sizes are rejected with TT_EINVAL (and a message
  * on stderr) before anything is launched.

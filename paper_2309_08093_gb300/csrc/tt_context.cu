@@ -60,98 +60,134 @@ int tt_ensure_tables(tt_ctx* c, uint64_t sweep) {
   TT_LAUNCH(c, "k_gen_tables");
   c->tables_valid = true;
   c->tables_sweep = sweep;
-  c->plan0_valid = false;
+  for (int k = 0; k < TT_MAX_D; ++k) c->rplan_valid[k] = false;
   return TT_OK;
 }
 
 // ---------------------------------------------------------------------------------------------
-// mode-0 fiber plan: fibers f = (i_1, ..., i_{d-1}) (mode 1 fastest) grouped by their row
-// b_f = (sum_{s>=1} h_s(i_s)) mod J of Y_0, with sign prod_{s>=1} v_s(i_s) in bit 31.
+// per-mode fibre plans. For mode k, the "rest" fibres r enumerate the modes s = 1..d-1, s != k
+// (mode-0 fibres of the sub-tensor A(:, .., i_k = 0, ..)), lowest mode fastest. Each gets its hash
+// c_r = (sum_s h_s(i_s)) mod J, sign prod_s v_s(i_s) and element offset sum_s i_s stride_s. The
+// plan lists the fibres grouped by c_r (counting sort) plus the distinct c values in order.
+// For k = 0 the groups are the rows of Y_0 (every mode-0 fibre lands in row c_r).
 
-struct PlanArgs {
+struct RPlanArgs {
   int64_t n[TT_MAX_D];
+  int64_t stride[TT_MAX_D];
   int64_t noff[TT_MAX_D + 1];
-  int d;
-  int J;
-  int64_t M0;
+  int d, k, J;
+  int64_t R;
 };
 
-__device__ __forceinline__ void plan_key(const PlanArgs& a, const int32_t* __restrict__ h,
-                                         const int8_t* __restrict__ v, int64_t f, int* key, int* neg) {
-  int b = 0, s = 0;
-  int64_t rem = f;
-  for (int k = 1; k < a.d; ++k) {
-    int64_t i = rem % a.n[k];
-    rem /= a.n[k];
-    b += h[a.noff[k] + i];
-    s ^= (v[a.noff[k] + i] < 0);
+__device__ __forceinline__ void rplan_entry(const RPlanArgs& a, const int32_t* __restrict__ h,
+                                            const int8_t* __restrict__ v, int64_t r, int* key, int* neg,
+                                            int64_t* off) {
+  int b = 0, sg = 0;
+  int64_t o = 0, rem = r;
+  for (int s = 1; s < a.d; ++s) {
+    if (s == a.k) continue;
+    int64_t i = rem % a.n[s];
+    rem /= a.n[s];
+    b += h[a.noff[s] + i];
+    sg ^= (v[a.noff[s] + i] < 0);
+    o += i * a.stride[s];
   }
   *key = b & (a.J - 1);
-  *neg = s;
+  *neg = sg;
+  *off = o;
 }
 
-__global__ void k_plan_count(PlanArgs a, const int32_t* h, const int8_t* v, int32_t* count) {
-  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < a.M0; f += (int64_t)gridDim.x * blockDim.x) {
+__global__ void k_rplan_count(RPlanArgs a, const int32_t* h, const int8_t* v, int32_t* count) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < a.R; r += (int64_t)gridDim.x * blockDim.x) {
     int key, neg;
-    plan_key(a, h, v, f, &key, &neg);
+    int64_t off;
+    rplan_entry(a, h, v, r, &key, &neg, &off);
     atomicAdd(&count[key], 1);
   }
 }
 
-// exclusive scan of J counts into off[0..J]; one block of 1024 threads
-__global__ void k_plan_scan(int J, const int32_t* count, int64_t* off, int32_t* cursor) {
+// exclusive scans of the counts and of the non-empty flags (one block of 1024 threads)
+__global__ void k_rplan_scan(int J, int64_t R, int32_t* count, int64_t* off, int32_t* ulist, int64_t* ustart,
+                             int32_t* ucount) {
   __shared__ int64_t part[1024];
-  int t = threadIdx.x;
-  int per = (J + 1023) / 1024;
+  __shared__ int upart[1024];
+  const int t = threadIdx.x;
+  const int per = (J + 1023) / 1024;
+  const int lo = min(J, t * per), hi = min(J, (t + 1) * per);
   int64_t s = 0;
-  for (int i = t * per; i < min(J, (t + 1) * per); ++i) s += count[i];
+  int u = 0;
+  for (int i = lo; i < hi; ++i) {
+    s += count[i];
+    u += count[i] > 0;
+  }
   part[t] = s;
+  upart[t] = u;
   __syncthreads();
   for (int o = 1; o < 1024; o <<= 1) {
     int64_t x = (t >= o) ? part[t - o] : 0;
+    int y = (t >= o) ? upart[t - o] : 0;
     __syncthreads();
     part[t] += x;
+    upart[t] += y;
     __syncthreads();
   }
   int64_t base = part[t] - s;
-  for (int i = t * per; i < min(J, (t + 1) * per); ++i) {
+  int ub = upart[t] - u;
+  for (int i = lo; i < hi; ++i) {
+    int ci = count[i];
     off[i] = base;
-    base += count[i];
-    cursor[i] = 0;
+    if (ci > 0) {
+      ulist[ub] = i;
+      ustart[ub] = base;
+      ++ub;
+    }
+    base += ci;
+    count[i] = 0;  // becomes the scatter cursor
   }
-  if (t == 1023) off[J] = part[1023];
+  if (t == 1023) {
+    off[J] = part[1023];
+    ustart[upart[1023]] = part[1023];
+    *ucount = upart[1023];
+  }
 }
 
-__global__ void k_plan_scatter(PlanArgs a, const int32_t* h, const int8_t* v, const int64_t* off,
-                               int32_t* cursor, uint32_t* plan) {
-  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < a.M0; f += (int64_t)gridDim.x * blockDim.x) {
+__global__ void k_rplan_scatter(RPlanArgs a, const int32_t* h, const int8_t* v, const int64_t* off,
+                                int32_t* cursor, uint32_t* plan) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < a.R; r += (int64_t)gridDim.x * blockDim.x) {
     int key, neg;
-    plan_key(a, h, v, f, &key, &neg);
+    int64_t o;
+    rplan_entry(a, h, v, r, &key, &neg, &o);
     int pos = atomicAdd(&cursor[key], 1);
-    plan[off[key] + pos] = (uint32_t)f | ((uint32_t)neg << 31);
+    plan[off[key] + pos] = (uint32_t)(o / a.n[0]) | ((uint32_t)neg << 31);  // fibre index | sign
   }
 }
 
-int tt_ensure_plan0(tt_ctx* c) {
-  if (c->plan0_valid) return TT_OK;
-  PlanArgs a;
-  for (int k = 0; k < c->d; ++k) a.n[k] = c->n[k];
-  for (int k = 0; k <= c->d; ++k) a.noff[k] = c->noff[k];
+int tt_ensure_rplan(tt_ctx* c, int k) {
+  if (c->rplan_valid[k]) return TT_OK;
+  RPlanArgs a;
+  for (int s = 0; s < c->d; ++s) {
+    a.n[s] = c->n[s];
+    a.stride[s] = c->stride[s];
+  }
+  for (int s = 0; s <= c->d; ++s) a.noff[s] = c->noff[s];
   a.d = c->d;
+  a.k = k;
   a.J = c->J;
-  a.M0 = c->M0;
+  a.R = c->R[k];
   int32_t* count = c->d_plan0_cursor;
   TT_CUDA(c, cudaMemsetAsync(count, 0, sizeof(int32_t) * c->J, c->stream));
-  int blocks = (int)std::min<int64_t>((c->M0 + 255) / 256, 152 * 16);
-  k_plan_count<<<blocks, 256, 0, c->stream>>>(a, c->d_h, c->d_v, count);
-  TT_LAUNCH(c, "k_plan_count");
-  k_plan_scan<<<1, 1024, 0, c->stream>>>(c->J, count, c->d_plan0_off, count);
-  TT_LAUNCH(c, "k_plan_scan");
-  k_plan_scatter<<<blocks, 256, 0, c->stream>>>(a, c->d_h, c->d_v, c->d_plan0_off, count, c->d_plan0);
-  TT_LAUNCH(c, "k_plan_scatter");
-  c->plan0_valid = true;
+  int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((a.R + 255) / 256, 152 * 16));
+  k_rplan_count<<<blocks, 256, 0, c->stream>>>(a, c->d_h, c->d_v, count);
+  TT_LAUNCH(c, "k_rplan_count");
+  k_rplan_scan<<<1, 1024, 0, c->stream>>>(c->J, a.R, count, c->d_rtmp, c->d_ulist[k], c->d_ustart[k], c->d_ucount[k]);
+  TT_LAUNCH(c, "k_rplan_scan");
+  k_rplan_scatter<<<blocks, 256, 0, c->stream>>>(a, c->d_h, c->d_v, c->d_rtmp, count, c->d_rplan[k]);
+  TT_LAUNCH(c, "k_rplan_scatter");
+  c->rplan_valid[k] = true;
   return TT_OK;
 }
+
+int tt_ensure_plan0(tt_ctx* c) { return tt_ensure_rplan(c, 0); }
 
 // ---------------------------------------------------------------------------------------------
 // lifetime
@@ -164,8 +200,14 @@ static void free_all(tt_ctx* c) {
     if (p) cudaFree(p);
   if (c->d_A_stage) cudaFree(c->d_A_stage);
   if (c->d_scales_stage) cudaFree(c->d_scales_stage);
-  for (int k = 0; k < TT_MAX_D; ++k)
+  for (int k = 0; k < TT_MAX_D; ++k) {
     if (c->d_cores_stage[k]) cudaFree(c->d_cores_stage[k]);
+    if (c->d_rplan[k]) cudaFree(c->d_rplan[k]);
+    if (c->d_ulist[k]) cudaFree(c->d_ulist[k]);
+    if (c->d_ustart[k]) cudaFree(c->d_ustart[k]);
+    if (c->d_ucount[k]) cudaFree(c->d_ucount[k]);
+  }
+  if (c->d_rtmp) cudaFree(c->d_rtmp);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
 }
 
@@ -235,9 +277,15 @@ extern "C" int tt_sketch_init(tt_ctx** out, const tt_params* p, void* stream) {
   };
   A((void**)&c->d_h, sizeof(int32_t) * c->noff[c->d]);
   A((void**)&c->d_v, sizeof(int8_t) * c->noff[c->d]);
-  A((void**)&c->d_plan0, sizeof(uint32_t) * c->M0);
-  A((void**)&c->d_plan0_off, sizeof(int64_t) * (c->J + 1));
   A((void**)&c->d_plan0_cursor, sizeof(int32_t) * c->J);
+  A((void**)&c->d_rtmp, sizeof(int64_t) * (c->J + 1));
+  for (int k = 0; k < c->d; ++k) {
+    c->R[k] = c->N / (c->n[0] * (k == 0 ? 1 : c->n[k]));
+    A((void**)&c->d_rplan[k], sizeof(uint32_t) * c->R[k]);
+    A((void**)&c->d_ulist[k], sizeof(int32_t) * c->J);
+    A((void**)&c->d_ustart[k], sizeof(int64_t) * (c->J + 1));
+    A((void**)&c->d_ucount[k], sizeof(int32_t));
+  }
   A((void**)&c->d_ghat, sizeof(float2) * c->ghat_off[c->d]);
   A((void**)&c->d_twiddle, sizeof(float2) * (c->J / 2));
   A((void**)&c->d_suffix, sizeof(float2) * c->suffix_off[c->d]);
@@ -309,6 +357,6 @@ extern "C" int tt_sketch_set_tables(tt_ctx* c, const int32_t* h_host, const int8
   TT_CUDA(c, cudaStreamSynchronize(c->stream));
   c->user_tables = true;
   c->tables_valid = true;
-  c->plan0_valid = false;
+  for (int k = 0; k < TT_MAX_D; ++k) c->rplan_valid[k] = false;
   return TT_OK;
 }

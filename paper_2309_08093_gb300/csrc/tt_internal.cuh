@@ -49,6 +49,18 @@ struct tt_ctx {
   int32_t* d_plan0_cursor = nullptr;  // J scatter cursors
   bool plan0_valid = false;
 
+  // mode-k plans: mode-0 fibres of the modes other than 0 and k ("rest" fibres r), grouped by
+  // their hash c_r = (sum_{s != 0, k} h_s(i_s)) mod J. Entry = index of the fibre at i_k = 0
+  // (element offset / n_0), sign in bit 31. Distinct c values listed in ulist / ustart.
+  int64_t R[TT_MAX_D] = {0};          // number of rest fibres of mode k
+  uint32_t* d_rplan[TT_MAX_D] = {nullptr};
+  int32_t* d_ulist[TT_MAX_D] = {nullptr};   // distinct c values (J entries max)
+  int64_t* d_ustart[TT_MAX_D] = {nullptr};  // J + 1 starts into d_rplan[k]
+  int32_t* d_ucount[TT_MAX_D] = {nullptr};  // number of distinct c values (device scalar)
+  int64_t* d_rtmp = nullptr;                 // J + 1 scratch offsets for the plan build
+  bool rplan_valid[TT_MAX_D] = {false};
+  float* d_Ypart = nullptr;                  // unused placeholder
+
   // FFT sketches of the cores: for core j, (J/2+1) x s_j complex, frequency-major
   float2* d_ghat = nullptr;
   int64_t ghat_off[TT_MAX_D + 1];
@@ -118,6 +130,7 @@ int tt_cuda_check(tt_ctx* c, cudaError_t e, const char* what);
 
 int tt_ensure_tables(tt_ctx* c, uint64_t sweep);
 int tt_ensure_plan0(tt_ctx* c);
+int tt_ensure_rplan(tt_ctx* c, int k);
 
 // kernels' host entry points (one translation unit each)
 int tt_launch_unfold(tt_ctx* c, const void* A, const float* scales, int k, float* Y);

@@ -19,7 +19,7 @@
 
 struct GramArgs {
   const float* SH;  // J x s column-major
-  const float* Y;   // J x n row-major
+  const float* Y;   // J x n column-major
   double* C;        // (s + n) x s row-major accumulators (zeroed by the caller)
   int J, s, n, kchunk;
 };
@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(256) k_gram(GramArgs a) {
         if (gr < a.s)
           xv = a.SH[(int64_t)gr * a.J + b];
         else if (gr < rows)
-          xv = a.Y[(int64_t)b * a.n + (gr - a.s)];
+          xv = a.Y[(int64_t)(gr - a.s) * a.J + b];
         if (gc < a.s) bv = a.SH[(int64_t)gc * a.J + b];
       }
       X[kk][cc] = xv;

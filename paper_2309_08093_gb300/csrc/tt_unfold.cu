@@ -3,15 +3,27 @@
 // Y_k[b, i_k] = sum over entries with that i_k of prod_{s!=k} v_s(i_s) * A(i), restricted to
 // (sum_{s!=k} h_s(i_s)) mod J = b  (Eqs. (eqn_h), (eqn_v)).
 //
-// Mode 0 (the contiguous mode): every mode-0 fiber A(:, i_1, ..., i_{d-1}) lands in ONE row
-// b_f = (sum_{s>=1} h_s(i_s)) mod J of Y_0, so Y_0[b, :] = sum_{f : b_f = b} s_f A(:, f). The
-// per-sweep plan lists fibers grouped by row; a warp owns a row, gathers its fibers with
-// 16-byte loads and sums them in registers. No atomics, one read of every entry.
+// Both kernels read A only as whole mode-0 fibres (contiguous runs of n_0 entries), gathered with
+// 16-byte loads in the order of a small per-sweep plan (tt_context.cu) and summed in registers.
 //
-// Modes k >= 1: a CTA owns column i_k of Y_k (J floats in shared memory) and streams the
-// entries with that i_k, mode-0 fibers at a time; each entry is added to its bucket
-// (h_0(i_0) + c_f) mod J with a shared-memory atomic. Column partials of CTAs that split
-// one column are combined with global atomics.
+// Mode 0: every fibre A(:, i_1, ..., i_{d-1}) lands in ONE row c = (sum_{s>=1} h_s(i_s)) mod J of
+// Y_0, so Y_0[c, :] = sum_{fibres with hash c} sign * fibre.
+//
+// Modes k >= 1: with Z_k[i_0, c] = sum over the fibres r of the modes != 0, k with hash c_r = c
+// of sign_r * A(i_0, r, i_k), the TensorSketch definition regroups to
+//     Y_k[b, i_k] = sum_{i_0} v_0(i_0) Z_k[i_0, (b - h_0(i_0)) mod J],
+// i.e. column i_k is a sum of n_0 circularly rolled rows of Z_k.
+//
+// One kernel serves both. Each CTA owns a contiguous range of (column i_k, c) groups of the plan
+// and walks it in chunks of C groups. Phase 1 builds the chunk's Z rows in shared memory: the
+// chunk's fibres are split evenly over (warp, fibre-slot) pairs, each sums its runs of equal c
+// in registers (plan words prefetched one round ahead, U fibres in flight), stores inner runs and
+// adds its first/last run (possibly shared with a neighbour) with shared-memory atomics.
+// Phase 2 (k >= 1) adds coef(i_0) * Z[c, i_0] into bucket (c + h_0(i_0)) mod J of the CTA's
+// column copy; consecutive threads take consecutive c, so the shared-memory atomics hit
+// consecutive banks. The column is flushed to global with 16-byte vector atomics when the CTA
+// moves to the next column. For mode 0, phase 2 writes the finished rows straight to Y_0.
+// Y_k is column-major (J x n_k).
 #include <algorithm>
 
 #include "tt_internal.cuh"
@@ -55,230 +67,72 @@ struct TtElem<TT_FP8E4M3> {
 // ---------------------------------------------------------------------------------------------
 // mode 0: row-owner fiber gather
 
-// Unpack a 16/8/4/2/1-byte vector of EPV elements of type DT into floats.
+// A VB-byte vector of EPV elements of type DT: loaded as raw 32-bit words (so that U loads in
+// flight cost U * VB/4 registers whatever the element type) and unpacked to floats when used.
 template <int DT, int VB>
 struct TtVec {
   static constexpr int EPV = VB / TtElem<DT>::bytes;
-  __device__ static void load(const char* p, float* out) {
+  static constexpr int W = (VB + 3) / 4;
+  struct Raw {
+    uint32_t w[W];
+  };
+  __device__ static Raw load(const char* p) {
+    Raw r;
     if constexpr (VB == 16) {
       uint4 u = __ldg(reinterpret_cast<const uint4*>(p));
-      unpack(reinterpret_cast<const uint32_t*>(&u), out);
+      r.w[0] = u.x; r.w[1] = u.y; r.w[2] = u.z; r.w[3] = u.w;
     } else if constexpr (VB == 8) {
       uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
-      unpack(reinterpret_cast<const uint32_t*>(&u), out);
+      r.w[0] = u.x; r.w[1] = u.y;
     } else if constexpr (VB == 4) {
-      uint32_t u = __ldg(reinterpret_cast<const uint32_t*>(p));
-      unpack(&u, out);
+      r.w[0] = __ldg(reinterpret_cast<const uint32_t*>(p));
     } else if constexpr (VB == 2) {
-      uint32_t u = __ldg(reinterpret_cast<const unsigned short*>(p));
-      unpack(&u, out);
+      r.w[0] = __ldg(reinterpret_cast<const unsigned short*>(p));
     } else {
-      uint32_t u = __ldg(reinterpret_cast<const unsigned char*>(p));
-      unpack(&u, out);
+      r.w[0] = __ldg(reinterpret_cast<const unsigned char*>(p));
     }
+    return r;
   }
-  __device__ static void unpack(const uint32_t* w, float* out) {
+  __device__ static Raw zero() {
+    Raw r;
+#pragma unroll
+    for (int i = 0; i < W; ++i) r.w[i] = 0u;
+    return r;
+  }
+  // acc[e] += s * element e
+  __device__ static void fma_into(const Raw& r, float s, float* acc) {
+    const uint32_t* w = r.w;
     if constexpr (DT == TT_F32) {
 #pragma unroll
-      for (int e = 0; e < EPV; ++e) out[e] = __uint_as_float(w[e]);
+      for (int e = 0; e < EPV; ++e) acc[e] = fmaf(s, __uint_as_float(w[e]), acc[e]);
     } else if constexpr (DT == TT_F64) {
 #pragma unroll
       for (int e = 0; e < EPV; ++e) {
         unsigned long long b = ((unsigned long long)w[2 * e + 1] << 32) | w[2 * e];
-        out[e] = (float)__longlong_as_double((long long)b);
+        acc[e] = fmaf(s, (float)__longlong_as_double((long long)b), acc[e]);
       }
     } else if constexpr (DT == TT_BF16) {
 #pragma unroll
-      for (int e = 0; e < EPV; ++e) out[e] = __uint_as_float(((w[e >> 1] >> (16 * (e & 1))) & 0xFFFFu) << 16);
+      for (int e = 0; e < EPV; ++e)
+        acc[e] = fmaf(s, __uint_as_float(((w[e >> 1] >> (16 * (e & 1))) & 0xFFFFu) << 16), acc[e]);
     } else {
 #pragma unroll
-      for (int e = 0; e < EPV; ++e) out[e] = tt_fp8_e4m3((w[e >> 2] >> (8 * (e & 3))) & 0xFFu);
+      for (int e = 0; e < EPV; ++e) acc[e] = fmaf(s, tt_fp8_e4m3((w[e >> 2] >> (8 * (e & 3))) & 0xFFu), acc[e]);
     }
   }
 };
 
-struct GatherArgs {
-  const char* A;
-  const float* scales;  // n0 FP8 scales or null
-  const uint32_t* plan;
-  const int64_t* off;   // J+1
-  float* Y;             // J x n0 row-major
-  int J;
-  int n0;
+// Vector geometry of a fibre: VB-byte loads, vpf vectors per fibre, lanes per fibre slot and
+// fibre slots per warp (several short fibres share one warp instruction).
+struct FibreGeom {
   int64_t fiber_bytes;
-  int vpf;              // vectors per fiber
-  int lpf;              // lanes per fiber slot (vpf if <= 32 else 32)
-  int fpi;              // fiber slots per warp (32 / lpf)
-  int nchunk;           // column chunks of 32 vectors when vpf > 32
-  int parts;            // splits of each row's fiber list (atomics when > 1)
+  int vpf, lpf, fpi, nchunk;
 };
 
-template <int DT, int VB, int U>
-__global__ void __launch_bounds__(256) k_unfold_mode0(GatherArgs g) {
-  constexpr int EPV = TtVec<DT, VB>::EPV;
-  extern __shared__ float red[];  // per warp: 32 lanes x EPV partial sums
-  const int lane = threadIdx.x & 31;
-  const int wib = threadIdx.x >> 5;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  const int slot = lane / g.lpf;
-  const int posl = lane - slot * g.lpf;
-  const bool active = slot < g.fpi;
-  const int64_t items = (int64_t)g.J * g.nchunk * g.parts;
-  float* wred = red + wib * 32 * EPV;
-  for (int64_t it = warp; it < items; it += nwarps) {
-    const int part = (int)(it % g.parts);
-    const int64_t rc = it / g.parts;
-    const int chunk = (int)(rc % g.nchunk);
-    const int row = (int)(rc / g.nchunk);
-    const int vpos = chunk * 32 + posl;  // vector index within the fiber
-    const bool lane_ok = active && vpos < g.vpf;
-    float acc[EPV];
-#pragma unroll
-    for (int e = 0; e < EPV; ++e) acc[e] = 0.f;
-    int64_t beg = g.off[row], end = g.off[row + 1];
-    int64_t len = end - beg;
-    int64_t pb = beg + len * part / g.parts, pe = beg + len * (part + 1) / g.parts;
-    for (int64_t j0 = pb; j0 < pe; j0 += (int64_t)g.fpi * U) {
-      float v[U][EPV];
-      float sg[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        int64_t j = j0 + (int64_t)u * g.fpi + slot;
-        sg[u] = 0.f;
-        if (lane_ok && j < pe) {
-          uint32_t w = __ldg(g.plan + j);
-          sg[u] = (w >> 31) ? -1.f : 1.f;
-          const char* p = g.A + (int64_t)(w & 0x7FFFFFFFu) * g.fiber_bytes + (int64_t)vpos * VB;
-          TtVec<DT, VB>::load(p, v[u]);
-        } else {
-#pragma unroll
-          for (int e = 0; e < EPV; ++e) v[u][e] = 0.f;
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u)
-#pragma unroll
-        for (int e = 0; e < EPV; ++e) acc[e] = fmaf(sg[u], v[u][e], acc[e]);
-    }
-    // combine the fiber slots (lanes with equal posl) through shared memory
-    if (g.fpi > 1) {
-#pragma unroll
-      for (int e = 0; e < EPV; ++e) wred[lane * EPV + e] = acc[e];
-      __syncwarp();
-      if (slot == 0) {
-        for (int s = 1; s < g.fpi; ++s)
-#pragma unroll
-          for (int e = 0; e < EPV; ++e) acc[e] += wred[(s * g.lpf + posl) * EPV + e];
-      }
-      __syncwarp();
-    }
-    if (slot == 0 && lane_ok) {
-      float* yrow = g.Y + (int64_t)row * g.n0;
-#pragma unroll
-      for (int e = 0; e < EPV; ++e) {
-        int i0 = vpos * EPV + e;
-        float val = acc[e];
-        if (g.scales) val *= __ldg(g.scales + i0);
-        if (g.parts > 1)
-          atomicAdd(yrow + i0, val);
-        else
-          yrow[i0] = val;
-      }
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------------------------
-// modes k >= 1: column owner with shared-memory accumulation
-
-struct ColArgs {
-  const void* A;
-  const float* scales;
-  const int32_t* h;
-  const int8_t* v;
-  float* Y;  // J x n_k row-major
-  int64_t n[TT_MAX_D];
-  int64_t noff[TT_MAX_D + 1];
-  int d, k, J;
-  int64_t P;      // prod_{s<k} n_s (contiguous block per (i_k, outer))
-  int64_t F;      // P / n_0 fibers per block
-  int64_t Q;      // prod_{s>k} n_s outer combinations
-  int nchunk;     // CTAs per column
-};
-
-template <int DT>
-__global__ void __launch_bounds__(512) k_unfold_col(ColArgs a) {
-  extern __shared__ float ycol[];
-  const int J = a.J;
-  for (int b = threadIdx.x; b < J; b += blockDim.x) ycol[b] = 0.f;
-  __syncthreads();
-  const int col = blockIdx.x / a.nchunk;
-  const int chunk = blockIdx.x % a.nchunk;
-  const int64_t pairs = a.Q * a.F;
-  const int64_t pb = pairs * chunk / a.nchunk, pe = pairs * (chunk + 1) / a.nchunk;
-  const int lane = threadIdx.x & 31;
-  const int warp = threadIdx.x >> 5;
-  const int nw = blockDim.x >> 5;
-  const int n0 = (int)a.n[0];
-  const int32_t* h0 = a.h;
-  const int8_t* v0 = a.v;
-  const int hk = a.h[a.noff[a.k] + col];
-  const int vk = a.v[a.noff[a.k] + col];
-  for (int64_t t = pb + warp; t < pe; t += nw) {
-    int64_t q = t / a.F, f = t - q * a.F;
-    // bucket offset and sign of the fiber: modes 1..k-1 from f, modes k+1..d-1 from q
-    int c = 0, neg = 0;
-    int64_t rem = f;
-    for (int s = 1; s < a.k; ++s) {
-      int64_t i = rem % a.n[s];
-      rem /= a.n[s];
-      c += a.h[a.noff[s] + i];
-      neg ^= a.v[a.noff[s] + i] < 0;
-    }
-    rem = q;
-    for (int s = a.k + 1; s < a.d; ++s) {
-      int64_t i = rem % a.n[s];
-      rem /= a.n[s];
-      c += a.h[a.noff[s] + i];
-      neg ^= a.v[a.noff[s] + i] < 0;
-    }
-    (void)hk;
-    (void)vk;
-    float sgn = neg ? -1.f : 1.f;
-    int64_t base = ((int64_t)col + a.n[a.k] * q) * a.P + f * n0;
-    for (int i0 = lane; i0 < n0; i0 += 32) {
-      float x = TtElem<DT>::get(a.A, base + i0);
-      if (a.scales) x *= __ldg(a.scales + i0);
-      int b = (__ldg(h0 + i0) + c) & (J - 1);
-      float s = (__ldg(v0 + i0) < 0) ? -sgn : sgn;
-      atomicAdd(&ycol[b], s * x);
-    }
-  }
-  __syncthreads();
-  for (int b = threadIdx.x; b < J; b += blockDim.x) {
-    float val = ycol[b];
-    if (val != 0.f) atomicAdd(a.Y + (int64_t)b * a.n[a.k] + col, val);
-  }
-}
-
-// ---------------------------------------------------------------------------------------------
-// host side
-
-template <int DT, int VB>
-static int launch_mode0_vb(tt_ctx* c, const void* A, const float* scales, float* Y) {
-  constexpr int EPV = TtVec<DT, VB>::EPV;
-  constexpr int U = (VB >= 8) ? 8 : 4;
-  GatherArgs g;
-  g.A = (const char*)A;
-  g.scales = scales;
-  g.plan = c->d_plan0;
-  g.off = c->d_plan0_off;
-  g.Y = Y;
-  g.J = c->J;
-  g.n0 = (int)c->n[0];
-  g.fiber_bytes = (int64_t)c->n[0] * TtElem<DT>::bytes;
-  g.vpf = (int)(g.fiber_bytes / VB);
+static FibreGeom fibre_geom(int64_t fiber_bytes, int VB) {
+  FibreGeom g;
+  g.fiber_bytes = fiber_bytes;
+  g.vpf = (int)(fiber_bytes / VB);
   if (g.vpf <= 32) {
     g.lpf = g.vpf;
     g.fpi = 32 / g.vpf;
@@ -288,79 +142,271 @@ static int launch_mode0_vb(tt_ctx* c, const void* A, const float* scales, float*
     g.fpi = 1;
     g.nchunk = (g.vpf + 31) / 32;
   }
-  const int threads = 256;
-  int dev_sms = 152;
-  int64_t warps_wanted = (int64_t)dev_sms * 48;
-  int64_t base_items = (int64_t)c->J * g.nchunk;
-  g.parts = (int)std::max<int64_t>(1, std::min<int64_t>(64, (warps_wanted + base_items - 1) / base_items));
-  if (g.parts > 1) TT_CUDA(c, cudaMemsetAsync(Y, 0, sizeof(float) * c->J * c->n[0], c->stream));
-  int64_t items = base_items * g.parts;
-  int blocks = (int)std::min<int64_t>((items + 7) / 8, (int64_t)dev_sms * 64);
-  size_t smem = sizeof(float) * 32 * EPV * (threads / 32);
-  k_unfold_mode0<DT, VB, U><<<blocks, threads, smem, c->stream>>>(g);
-  TT_LAUNCH(c, "k_unfold_mode0");
-  return TT_OK;
+  return g;
 }
 
-template <int DT>
-static int launch_mode0(tt_ctx* c, const void* A, const float* scales, float* Y) {
-  int64_t fb = (int64_t)c->n[0] * TtElem<DT>::bytes;
-  uintptr_t al = (uintptr_t)A;
-  if (fb % 16 == 0 && al % 16 == 0) return launch_mode0_vb<DT, 16>(c, A, scales, Y);
-  if (fb % 8 == 0 && al % 8 == 0) return launch_mode0_vb<DT, (TtElem<DT>::bytes <= 8 ? 8 : 16)>(c, A, scales, Y);
-  if constexpr (TtElem<DT>::bytes <= 4) {
-    if (fb % 4 == 0 && al % 4 == 0) return launch_mode0_vb<DT, 4>(c, A, scales, Y);
+// ---------------------------------------------------------------------------------------------
+// the gather kernel
+
+struct GArgs {
+  const char* A;
+  const float* scales;    // n0 FP8 scales or null
+  const int32_t* h0;      // h_0 (n0 entries)
+  const int8_t* v0;
+  const uint32_t* plan;   // fibre index at i_k = 0 | sign in bit 31, grouped by c
+  const int32_t* ulist;   // distinct c values
+  const int64_t* ustart;  // starts into plan (U + 1)
+  const int32_t* ucount;  // U
+  float* Y;               // J x ncol column-major (zeroed by the host when k >= 1)
+  int64_t col_fibres;     // fibre-index stride of the output column (stride_k / n0); 0 for mode 0
+  int J, n0, ncol;
+  int C;                  // c groups per chunk
+  int pitch;              // row pitch of the Z chunk (odd)
+  int elem_bytes;
+  FibreGeom fg;
+};
+
+template <int DT, int VB, int U, bool MODE0>
+__global__ void __launch_bounds__(256, 2) k_unfold_gather(GArgs a) {
+  constexpr int EPV = TtVec<DT, VB>::EPV;
+  extern __shared__ float sm[];
+  const int J = a.J;
+  float* Ys = sm;                                       // J (k >= 1 only)
+  float* Zs = Ys + (MODE0 ? 0 : J);                     // C x pitch
+  float* coef = Zs + (size_t)a.C * a.pitch;             // n0
+  int* h0s = reinterpret_cast<int*>(coef + a.n0);       // n0
+  int* cvals = h0s + a.n0;                              // C
+  int64_t* cst = reinterpret_cast<int64_t*>(sm) + ((size_t)((MODE0 ? 0 : J) + a.C * a.pitch + 2 * a.n0 + a.C + 1) / 2);
+  const int T = blockDim.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = T >> 5;
+  for (int i = threadIdx.x; i < a.n0; i += T) {
+    float cf = 1.f;
+    if (!MODE0 && __ldg(a.v0 + i) < 0) cf = -1.f;
+    if (a.scales) cf *= __ldg(a.scales + i);
+    coef[i] = cf;
+    h0s[i] = MODE0 ? 0 : __ldg(a.h0 + i);
   }
-  if constexpr (TtElem<DT>::bytes <= 2) {
-    if (fb % 2 == 0 && al % 2 == 0) return launch_mode0_vb<DT, 2>(c, A, scales, Y);
+  const int64_t U_ = *a.ucount;
+  const int64_t total = U_ * a.ncol;
+  const int64_t lo = total * blockIdx.x / gridDim.x, hi = total * (blockIdx.x + 1) / gridDim.x;
+  const int slot = lane / a.fg.lpf, posl = lane - slot * a.fg.lpf;
+  const int nslots = nw * a.fg.fpi;
+  const int gslot = warp * a.fg.fpi + slot;
+  const bool slot_ok = slot < a.fg.fpi;
+  int cur_col = -1;
+  for (int64_t p0 = lo; p0 < hi;) {
+    const int col = (int)(p0 / U_);
+    const int64_t u0 = p0 - (int64_t)col * U_;
+    const int64_t cend = min(hi, (int64_t)(col + 1) * U_);
+    const int nc = (int)((cend - p0) < (int64_t)a.C ? (cend - p0) : (int64_t)a.C);
+    if (!MODE0 && col != cur_col) {
+      if (cur_col >= 0) {  // flush the finished column
+        __syncthreads();
+        float* yc = a.Y + (int64_t)J * cur_col;
+        if ((J & 3) == 0) {
+          for (int b = threadIdx.x * 4; b < J; b += T * 4) {
+            float4 v4 = make_float4(Ys[b], Ys[b + 1], Ys[b + 2], Ys[b + 3]);
+            atomicAdd(reinterpret_cast<float4*>(yc + b), v4);
+          }
+        } else {
+          for (int b = threadIdx.x; b < J; b += T) atomicAdd(yc + b, Ys[b]);
+        }
+        __syncthreads();
+      }
+      for (int i = threadIdx.x; i < J; i += T) Ys[i] = 0.f;
+      cur_col = col;
+    }
+    for (int i = threadIdx.x; i < nc * a.pitch; i += T) Zs[i] = 0.f;
+    for (int i = threadIdx.x; i <= nc; i += T) {
+      cst[i] = __ldg(a.ustart + u0 + i);
+      if (i < nc) cvals[i] = __ldg(a.ulist + u0 + i);
+    }
+    __syncthreads();
+    // ---- phase 1: Z rows of the chunk by fibre gathers
+    {
+      const int64_t e0 = cst[0], ne = cst[nc] - e0;
+      const int64_t sb = e0 + ne * gslot / nslots, se = e0 + ne * (gslot + 1) / nslots;
+      const int64_t colf = (int64_t)col * a.col_fibres;
+      if (slot_ok && sb < se) {
+        // run containing sb: largest cu with cst[cu] <= sb
+        int lo2 = 0, hi2 = nc;  // cst[lo2] <= sb < cst[hi2]
+        while (hi2 - lo2 > 1) {
+          const int mid = (lo2 + hi2) >> 1;
+          if (cst[mid] <= sb) lo2 = mid; else hi2 = mid;
+        }
+        for (int ch = 0; ch < a.fg.nchunk; ++ch) {
+          const int vpos = ch * 32 + posl;
+          const bool lane_ok = vpos < a.fg.vpf;
+          const int64_t vbyte = (int64_t)vpos * VB;
+          int cu = lo2;
+          int64_t next_b = cst[cu + 1];
+          bool first_run = true;
+          float acc[EPV];
+#pragma unroll
+          for (int e = 0; e < EPV; ++e) acc[e] = 0.f;
+          uint32_t wn[U];
+#pragma unroll
+          for (int q = 0; q < U; ++q) wn[q] = (sb + q < se) ? __ldg(a.plan + sb + q) : 0u;
+          for (int64_t j0 = sb; j0 < se; j0 += U) {
+            typename TtVec<DT, VB>::Raw v[U];
+            uint32_t w[U];
+#pragma unroll
+            for (int q = 0; q < U; ++q) {
+              w[q] = wn[q];
+              if (lane_ok && j0 + q < se) {
+                const int64_t fib = (int64_t)(w[q] & 0x7FFFFFFFu) + colf;
+                v[q] = TtVec<DT, VB>::load(a.A + fib * a.fg.fiber_bytes + vbyte);
+              } else {
+                v[q] = TtVec<DT, VB>::zero();
+              }
+            }
+#pragma unroll
+            for (int q = 0; q < U; ++q) wn[q] = (j0 + U + q < se) ? __ldg(a.plan + j0 + U + q) : 0u;
+#pragma unroll
+            for (int q = 0; q < U; ++q) {
+              const int64_t j = j0 + q;
+              if (j < se) {
+                if (j >= next_b) {  // the run of group cu ended: write it
+                  if (lane_ok) {
+                    float* z = Zs + (size_t)cu * a.pitch + vpos * EPV;
+                    if (first_run) {
+#pragma unroll
+                      for (int e = 0; e < EPV; ++e) atomicAdd(z + e, acc[e]);
+                    } else {
+#pragma unroll
+                      for (int e = 0; e < EPV; ++e) z[e] = acc[e];
+                    }
+                  }
+#pragma unroll
+                  for (int e = 0; e < EPV; ++e) acc[e] = 0.f;
+                  first_run = false;
+                  do {
+                    ++cu;
+                    next_b = cst[cu + 1];
+                  } while (j >= next_b);
+                }
+                TtVec<DT, VB>::fma_into(v[q], (w[q] >> 31) ? -1.f : 1.f, acc);
+              }
+            }
+          }
+          if (lane_ok) {  // the slot's last run may be shared with the next slot
+            float* z = Zs + (size_t)cu * a.pitch + vpos * EPV;
+#pragma unroll
+            for (int e = 0; e < EPV; ++e) atomicAdd(z + e, acc[e]);
+          }
+        }
+      }
+    }
+    __syncthreads();
+    // ---- phase 2
+    if (MODE0) {
+      // finished rows c of Y_0: Y_0[c + J i0] = scale(i0) * Z[c, i0] (consecutive c: coalesced)
+      for (int idx = threadIdx.x; idx < nc * a.n0; idx += T) {
+        const int ul = idx % nc, i0 = idx / nc;
+        a.Y[cvals[ul] + (int64_t)J * i0] = coef[i0] * Zs[(size_t)ul * a.pitch + i0];
+      }
+    } else {
+      for (int idx = threadIdx.x; idx < nc * a.n0; idx += T) {
+        const int ul = idx % nc, i0 = idx / nc;
+        const int b = (cvals[ul] + h0s[i0]) & (J - 1);
+        atomicAdd(Ys + b, coef[i0] * Zs[(size_t)ul * a.pitch + i0]);
+      }
+    }
+    __syncthreads();
+    p0 += nc;
   }
-  if constexpr (TtElem<DT>::bytes <= 1) return launch_mode0_vb<DT, 1>(c, A, scales, Y);
-  return launch_mode0_vb<DT, TtElem<DT>::bytes>(c, A, scales, Y);
+  if (!MODE0 && cur_col >= 0) {
+    __syncthreads();
+    float* yc = a.Y + (int64_t)J * cur_col;
+    if ((J & 3) == 0) {
+      for (int b = threadIdx.x * 4; b < J; b += T * 4) {
+        float4 v4 = make_float4(Ys[b], Ys[b + 1], Ys[b + 2], Ys[b + 3]);
+        atomicAdd(reinterpret_cast<float4*>(yc + b), v4);
+      }
+    } else {
+      for (int b = threadIdx.x; b < J; b += T) atomicAdd(yc + b, Ys[b]);
+    }
+  }
 }
 
-template <int DT>
-static int launch_col(tt_ctx* c, const void* A, const float* scales, int k, float* Y) {
-  ColArgs a;
-  a.A = A;
+// ---------------------------------------------------------------------------------------------
+// host side
+
+static int pick_vb(int64_t fiber_bytes, uintptr_t base, int elem_bytes) {
+  for (int vb = 16; vb >= elem_bytes; vb >>= 1)
+    if (fiber_bytes % vb == 0 && base % vb == 0) return vb;
+  return elem_bytes;
+}
+
+static size_t gather_smem(int J, bool mode0, int C, int pitch, int n0) {
+  size_t words = (size_t)(mode0 ? 0 : J) + (size_t)C * pitch + 2 * (size_t)n0 + C + 1;
+  words = (words + 1) & ~(size_t)1;  // cst is 8-byte aligned
+  return words * 4 + sizeof(int64_t) * (C + 1);
+}
+
+template <int DT, int VB, bool MODE0>
+static int launch_gather_vb(tt_ctx* c, const void* A, const float* scales, int k, float* Y) {
+  constexpr int U = 8;
+  GArgs a;
+  a.A = (const char*)A;
   a.scales = scales;
-  a.h = c->d_h;
-  a.v = c->d_v;
+  a.h0 = c->d_h;
+  a.v0 = c->d_v;
+  a.plan = c->d_rplan[k];
+  a.ulist = c->d_ulist[k];
+  a.ustart = c->d_ustart[k];
+  a.ucount = c->d_ucount[k];
   a.Y = Y;
-  for (int s = 0; s < c->d; ++s) a.n[s] = c->n[s];
-  for (int s = 0; s <= c->d; ++s) a.noff[s] = c->noff[s];
-  a.d = c->d;
-  a.k = k;
   a.J = c->J;
-  a.P = c->stride[k];
-  a.F = a.P / c->n[0];
-  a.Q = c->N / (c->stride[k] * c->n[k]);
-  int64_t want = 152 * 4;
-  a.nchunk = (int)std::max<int64_t>(1, std::min<int64_t>((want + c->n[k] - 1) / c->n[k], a.Q * a.F));
-  TT_CUDA(c, cudaMemsetAsync(Y, 0, sizeof(float) * c->J * c->n[k], c->stream));
-  int blocks = (int)(c->n[k] * a.nchunk);
-  size_t smem = sizeof(float) * c->J;
-  if (smem > 48 * 1024) TT_CUDA(c, cudaFuncSetAttribute(k_unfold_col<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_unfold_col<DT><<<blocks, 512, smem, c->stream>>>(a);
-  TT_LAUNCH(c, "k_unfold_col");
+  a.n0 = (int)c->n[0];
+  a.ncol = MODE0 ? 1 : (int)c->n[k];
+  a.col_fibres = MODE0 ? 0 : c->stride[k] / c->n[0];
+  a.elem_bytes = TtElem<DT>::bytes;
+  a.fg = fibre_geom((int64_t)c->n[0] * TtElem<DT>::bytes, VB);
+  a.pitch = (a.n0 % 2 == 0) ? a.n0 + 1 : a.n0;
+  // chunk size: aim at two CTAs per SM (about 105 KB of shared memory each)
+  const size_t target = 105 * 1024;
+  int C = 256;
+  while (C > 32 && gather_smem(c->J, MODE0, C, a.pitch, a.n0) > target) C -= 32;
+  while (C > 1 && gather_smem(c->J, MODE0, C, a.pitch, a.n0) > 220 * 1024) C >>= 1;
+  a.C = C;
+  const size_t smem = gather_smem(c->J, MODE0, C, a.pitch, a.n0);
+  if (smem > 220 * 1024) return tt_fail(c, TT_EINVAL, "gather kernel needs %zu bytes of shared memory", smem);
+  TT_CUDA(c, cudaMemsetAsync(Y, 0, sizeof(float) * c->J * c->n[k], c->stream));  // empty groups stay 0
+  TT_CUDA(c, cudaFuncSetAttribute(k_unfold_gather<DT, VB, U, MODE0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 1;
+  TT_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_unfold_gather<DT, VB, U, MODE0>, 256, smem));
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+  const int blocks = std::max(1, sms * std::max(1, per_sm));
+  k_unfold_gather<DT, VB, U, MODE0><<<blocks, 256, smem, c->stream>>>(a);
+  TT_LAUNCH(c, "k_unfold_gather");
   return TT_OK;
+}
+
+template <int DT, bool MODE0>
+static int launch_gather(tt_ctx* c, const void* A, const float* scales, int k, float* Y) {
+  constexpr int EB = TtElem<DT>::bytes;
+  const int vb = pick_vb((int64_t)c->n[0] * EB, (uintptr_t)A, EB);
+  switch (vb) {
+    case 16: return launch_gather_vb<DT, 16, MODE0>(c, A, scales, k, Y);
+    case 8: return launch_gather_vb<DT, (EB <= 8 ? 8 : 16), MODE0>(c, A, scales, k, Y);
+    case 4: return launch_gather_vb<DT, (EB <= 4 ? 4 : EB), MODE0>(c, A, scales, k, Y);
+    case 2: return launch_gather_vb<DT, (EB <= 2 ? 2 : EB), MODE0>(c, A, scales, k, Y);
+    default: return launch_gather_vb<DT, EB, MODE0>(c, A, scales, k, Y);
+  }
 }
 
 template <int DT>
 static int unfold_dt(tt_ctx* c, const void* A, const float* scales, int k, float* Y) {
-  if (k == 0) {
-    int rc = tt_ensure_plan0(c);
-    if (rc) return rc;
-    return launch_mode0<DT>(c, A, scales, Y);
-  }
-  return launch_col<DT>(c, A, scales, k, Y);
+  if (k == 0) return launch_gather<DT, true>(c, A, scales, k, Y);
+  return launch_gather<DT, false>(c, A, scales, k, Y);
 }
 
 int tt_launch_unfold(tt_ctx* c, const void* A, const float* scales, int k, float* Y) {
-  if (k == 0) {
-    int rc = tt_ensure_plan0(c);  // plan build is not part of the timed kernel
-    if (rc) return rc;
-  }
-  int rc = tt_prof_begin(c, k);
+  int rc = tt_ensure_rplan(c, k);  // plan build is not part of the timed kernel
+  if (rc) return rc;
+  rc = tt_prof_begin(c, k);
   if (rc) return rc;
   switch (c->dtype) {
     case TT_F64: rc = unfold_dt<TT_F64>(c, A, scales, k, Y); break;

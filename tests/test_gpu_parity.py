@@ -119,14 +119,14 @@ def test_unfold_sketch_parity(dims, J, storage):
         hs, vs = O.draw_sketch(seed, sweep, dims, J)
         for k in range(len(dims)):
             ref = O.sketch_unfolding(exact, hs, vs, J, k)
-            got = Y[k].cpu().numpy().reshape(J, dims[k])
+            got = Y[k].cpu().numpy().reshape(dims[k], J).T  # column-major J x n_k
             assert rel(got, ref) <= TOL, (k, rel(got, ref))
     # single-mode call writes only that mode
     Y1 = [None] * len(dims)
     Y1[1] = torch.zeros(J * dims[1], device="cuda")
     ctx.tt_sketch_unfold(Ad, 1, 0, Y1, scales=sd)
     hs, vs = O.draw_sketch(seed, 0, dims, J)
-    assert rel(Y1[1].cpu().numpy().reshape(J, dims[1]), O.sketch_unfolding(exact, hs, vs, J, 1)) <= TOL
+    assert rel(Y1[1].cpu().numpy().reshape(dims[1], J).T, O.sketch_unfolding(exact, hs, vs, J, 1)) <= TOL
     ctx.close()
 
 
@@ -190,7 +190,7 @@ def test_prox_update_parity(J, n, r0, r1, sigma):
     k = 0 if r0 == 1 else 1
     ranks = (1, r1, 1, 1) if k == 0 else (1, r0, r1, 1)
     ctx = lib.Context(dims, ranks, J, sigma, 5, "f32")
-    Yd = torch.from_numpy(np.ascontiguousarray(Y32)).cuda()  # J x n row-major
+    Yd = torch.from_numpy(np.ascontiguousarray(Y32.T)).cuda()  # J x n column-major
     SHd = torch.from_numpy(np.ascontiguousarray(SH32.T)).cuda()  # column-major J x s
     core = torch.from_numpy(np.ascontiguousarray(G32.ravel(order="F"))).cuda()
     ctx.tt_prox_update(Yd, SHd, core, k)
