@@ -96,90 +96,157 @@ __device__ double block_sum(double v, double* sh) {
   return t;  // valid in thread 0
 }
 
+// Factorisation M = L D L^T (unit lower L, D > 0 -- the Cholesky factor is L D^{1/2}) with one
+// barrier per column: thread (ty, tx) of a 32 x 32 tiling owns the entries (i, l), i = ty mod 32,
+// l = tx mod 32, of the trailing triangle. The solve X M = B runs as three passes over blocks of
+// 32 columns: Y L^T = B (forward), V = Y D^{-1}, X L = V (backward). Within a pass each block
+// is a parallel GEMM update with the finished blocks followed by a multiplication with the
+// inverse of the block's unit-triangular diagonal part (inverted up front, one warp per block).
+#define TT_SB 32
 __global__ void __launch_bounds__(1024) k_prox_solve(SolveArgs a) {
   extern __shared__ float sm[];
   __shared__ int bad;
   __shared__ double red[32];
   const int s = a.s;
-  float* L = sm;                         // s x s, row-major, lower triangle used
-  float* Z = sm + s * s;                 // chunk_rows x s, row-major
+  const int P = s | 1;                         // odd pitch: column walks hit distinct banks
+  const int nb = (s + TT_SB - 1) / TT_SB;
+  float* M = sm;                               // s x P: L below the diagonal, D on it
+  float* Tinv = M + (size_t)s * P;             // nb blocks of 32 x 33: inverses of diagonal blocks
+  float* Z = Tinv + (size_t)nb * TT_SB * (TT_SB + 1);  // chunk_rows x P right-hand sides
+  const int t = threadIdx.x, T = blockDim.x;
+  const int lane = t & 31, warp = t >> 5;
   if (*a.status != 0) return;
-  for (int idx = threadIdx.x; idx < s * s; idx += blockDim.x) {
-    int i = idx / s, j = idx - i * s;
+  for (int idx = t; idx < s * s; idx += T) {
+    const int i = idx / s, j = idx - i * s;
     double m = a.C[idx];
     if (i == j) m += a.sigma;
-    L[idx] = (float)m;
+    M[i * P + j] = (float)m;
   }
-  if (threadIdx.x == 0) bad = 0;
+  if (t == 0) bad = 0;
   __syncthreads();
-  // right-looking Cholesky, lower triangle
+  const int ty = t >> 5, tx = t & 31;  // 32 x 32 tiling (T = 1024)
   for (int j = 0; j < s; ++j) {
-    if (threadIdx.x == 0) {
-      float dj = L[j * s + j];
-      if (!(dj > 0.f) || !isfinite(dj)) {
-        bad = isfinite(dj) ? TT_ENOTSPD : TT_ENONFINITE;
-      } else {
-        L[j * s + j] = sqrtf(dj);
-      }
+    const float p = M[j * P + j];
+    if (!(p > 0.f) || !isfinite(p)) {
+      if (t == 0) bad = isfinite(p) ? TT_ENOTSPD : TT_ENONFINITE;
+      break;
     }
-    __syncthreads();
-    if (bad) break;
-    const float ljj = L[j * s + j];
-    for (int i = j + 1 + threadIdx.x; i < s; i += blockDim.x) L[i * s + j] /= ljj;
-    __syncthreads();
-    const int m = s - j - 1;
-    for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
-      int ii = t / m, ll = t - ii * m;
-      if (ll <= ii) {
-        int i = j + 1 + ii, l = j + 1 + ll;
-        L[i * s + l] -= L[i * s + j] * L[l * s + j];
-      }
+    const float ip = 1.f / p;
+    for (int i = j + 1 + ((ty - (j + 1)) % 32 + 32) % 32; i < s; i += 32) {
+      const float mij = M[i * P + j] * ip;
+      for (int l = j + 1 + ((tx - (j + 1)) % 32 + 32) % 32; l <= i; l += 32) M[i * P + l] -= mij * M[l * P + j];
     }
     __syncthreads();
   }
+  __syncthreads();
   if (bad) {
-    if (threadIdx.x == 0) atomicCAS(a.status, 0, bad);
+    if (t == 0) atomicCAS(a.status, 0, bad);
     return;
   }
+  // L[i][j] = M[i][j] / D[j]  (i > j)
+  for (int idx = t; idx < s * s; idx += T) {
+    const int i = idx / s, j = idx - i * s;
+    if (i > j) M[i * P + j] /= M[j * P + j];
+  }
+  __syncthreads();
+  // inverses of the unit lower diagonal blocks (warp b inverts block b; lane c = column c)
+  for (int b = warp; b < nb; b += T / 32) {
+    const int c0 = b * TT_SB, w = min(TT_SB, s - c0);
+    float* Tb = Tinv + (size_t)b * TT_SB * (TT_SB + 1);
+    if (lane < w) {
+      float x[TT_SB];
+#pragma unroll
+      for (int i = 0; i < TT_SB; ++i) x[i] = 0.f;
+      for (int i = lane; i < w; ++i) {
+        float v = (i == lane) ? 1.f : 0.f;
+        for (int l = lane; l < i; ++l) v -= M[(c0 + i) * P + c0 + l] * x[l];
+        x[i] = v;
+      }
+      for (int i = 0; i < w; ++i) Tb[i * (TT_SB + 1) + lane] = x[i];  // Tb = (L_bb)^{-1}, row i col lane
+    }
+  }
+  __syncthreads();
   double dsum = 0.0, nsum = 0.0;
+  const int ZP = P;
   for (int i0 = 0; i0 < a.n; i0 += a.chunk_rows) {
     const int nr = min(a.chunk_rows, a.n - i0);
-    // B = Y^T SH + sigma G_{k(2)}; G_{k(2)}[i, c] with c = al + r0 be
-    for (int idx = threadIdx.x; idx < nr * s; idx += blockDim.x) {
-      int i = idx / s, c = idx - i * s;
-      int al = c % a.r0, be = c / a.r0;
-      float g = a.core[al + (int64_t)a.r0 * ((i0 + i) + (int64_t)a.n * be)];
-      Z[idx] = (float)(a.C[(int64_t)(s + i0 + i) * s + c] + a.sigma * (double)g);
+    for (int idx = t; idx < nr * s; idx += T) {
+      const int i = idx / s, c = idx - i * s;
+      const int al = c % a.r0, be = c / a.r0;
+      const float g = a.core[al + (int64_t)a.r0 * ((i0 + i) + (int64_t)a.n * be)];
+      Z[i * ZP + c] = (float)(a.C[(int64_t)(s + i0 + i) * s + c] + a.sigma * (double)g);
     }
     __syncthreads();
-    // forward: W L^T = B  (column j after columns < j)
-    for (int j = 0; j < s; ++j) {
-      const float ljj = L[j * s + j];
-      for (int i = threadIdx.x; i < nr; i += blockDim.x) Z[i * s + j] /= ljj;
+    // forward: Y L^T = B. Block b: Z[:, blk] -= Z[:, <c0] L[blk, <c0]^T, then Z[:, blk] <- Z[:, blk] Tb^T
+    for (int b = 0; b < nb; ++b) {
+      const int c0 = b * TT_SB, w = min(TT_SB, s - c0);
+      for (int idx = t; idx < nr * w; idx += T) {
+        const int r = idx / w, jj = idx - r * w;
+        float acc = Z[r * ZP + c0 + jj];
+        for (int l = 0; l < c0; ++l) acc -= Z[r * ZP + l] * M[(c0 + jj) * P + l];
+        Z[r * ZP + c0 + jj] = acc;
+      }
       __syncthreads();
-      const int m = s - j - 1;
-      for (int t = threadIdx.x; t < nr * m; t += blockDim.x) {
-        int i = t / m, l = j + 1 + (t - (t / m) * m);
-        Z[i * s + l] -= Z[i * s + j] * L[l * s + j];
+      const float* Tb = Tinv + (size_t)b * TT_SB * (TT_SB + 1);
+      float tmp[4];
+      int cntq = 0;
+      for (int idx = t; idx < nr * w; idx += T) {  // y_blk = z_blk (Tb)^T: y_j = sum_{l<=j} Tb[j][l] z_l
+        const int r = idx / w, jj = idx - r * w;
+        float acc = 0.f;
+        for (int l = 0; l <= jj; ++l) acc += Tb[jj * (TT_SB + 1) + l] * Z[r * ZP + c0 + l];
+        if (cntq < 4) tmp[cntq] = acc;
+        ++cntq;
+      }
+      __syncthreads();
+      cntq = 0;
+      for (int idx = t; idx < nr * w; idx += T) {
+        const int r = idx / w, jj = idx - r * w;
+        if (cntq < 4) Z[r * ZP + c0 + jj] = tmp[cntq];
+        ++cntq;
       }
       __syncthreads();
     }
-    // backward: X L = W  (column j after columns > j)
-    for (int j = s - 1; j >= 0; --j) {
-      const float ljj = L[j * s + j];
-      for (int i = threadIdx.x; i < nr; i += blockDim.x) Z[i * s + j] /= ljj;
+    // V = Y D^{-1}
+    for (int idx = t; idx < nr * s; idx += T) {
+      const int r = idx / s, c = idx - r * s;
+      Z[r * ZP + c] /= M[c * P + c];
+    }
+    __syncthreads();
+    // backward: X L = V. Block b (last first): Z[:, blk] -= Z[:, >=c1] L[>=c1, blk], then
+    // Z[:, blk] <- Z[:, blk] Tb  (x_j = sum_{i>=j} z_i Tb[i][j])
+    for (int b = nb - 1; b >= 0; --b) {
+      const int c0 = b * TT_SB, w = min(TT_SB, s - c0), c1 = c0 + w;
+      for (int idx = t; idx < nr * w; idx += T) {
+        const int r = idx / w, jj = idx - r * w;
+        float acc = Z[r * ZP + c0 + jj];
+        for (int i = c1; i < s; ++i) acc -= Z[r * ZP + i] * M[i * P + c0 + jj];
+        Z[r * ZP + c0 + jj] = acc;
+      }
       __syncthreads();
-      for (int t = threadIdx.x; t < nr * j; t += blockDim.x) {
-        int i = t / j, l = t - (t / j) * j;
-        Z[i * s + l] -= Z[i * s + j] * L[j * s + l];
+      const float* Tb = Tinv + (size_t)b * TT_SB * (TT_SB + 1);
+      float tmp[4];
+      int cntq = 0;
+      for (int idx = t; idx < nr * w; idx += T) {
+        const int r = idx / w, jj = idx - r * w;
+        float acc = 0.f;
+        for (int i = jj; i < w; ++i) acc += Z[r * ZP + c0 + i] * Tb[i * (TT_SB + 1) + jj];
+        if (cntq < 4) tmp[cntq] = acc;
+        ++cntq;
+      }
+      __syncthreads();
+      cntq = 0;
+      for (int idx = t; idx < nr * w; idx += T) {
+        const int r = idx / w, jj = idx - r * w;
+        if (cntq < 4) Z[r * ZP + c0 + jj] = tmp[cntq];
+        ++cntq;
       }
       __syncthreads();
     }
-    for (int idx = threadIdx.x; idx < nr * s; idx += blockDim.x) {
-      int i = idx / s, c = idx - i * s;
-      int al = c % a.r0, be = c / a.r0;
-      int64_t off = al + (int64_t)a.r0 * ((i0 + i) + (int64_t)a.n * be);
-      float old = a.core[off], nw = Z[idx];
+    for (int idx = t; idx < nr * s; idx += T) {
+      const int i = idx / s, c = idx - i * s;
+      const int al = c % a.r0, be = c / a.r0;
+      const int64_t off = al + (int64_t)a.r0 * ((i0 + i) + (int64_t)a.n * be);
+      const float old = a.core[off], nw = Z[i * ZP + c];
       dsum += (double)(nw - old) * (double)(nw - old);
       nsum += (double)nw * (double)nw;
       a.core[off] = nw;
@@ -188,10 +255,23 @@ __global__ void __launch_bounds__(1024) k_prox_solve(SolveArgs a) {
   }
   double t1 = block_sum(dsum, red);
   double t2 = block_sum(nsum, red);
-  if (threadIdx.x == 0 && a.change) {
+  if (t == 0 && a.change) {
     a.change[0] = t1;
     a.change[1] = t2;
   }
+}
+
+static size_t solve_smem(int s, int chunk_rows) {
+  const int P = s | 1, nb = (s + TT_SB - 1) / TT_SB;
+  return sizeof(float) * ((size_t)s * P + (size_t)nb * TT_SB * (TT_SB + 1) + (size_t)chunk_rows * P);
+}
+
+static int solve_chunk_rows(int s, int n) {
+  // rows per chunk: at most 128 (rows x 32 block columns <= 4 items per thread of 1024) and
+  // within ~200 KB of shared memory
+  int rows = std::min(n, 128);
+  while (rows > 1 && solve_smem(s, rows) > 200 * 1024) rows = (rows + 1) / 2;
+  return std::max(1, rows);
 }
 
 int tt_launch_prox_update(tt_ctx* c, const float* Y, const float* SH, float* core, int k,
@@ -220,9 +300,8 @@ int tt_launch_prox_update(tt_ctx* c, const float* Y, const float* SH, float* cor
   a.n = n;
   a.r0 = c->r[k];
   a.r1 = c->r[k + 1];
-  const int budget = 48 * 1024;  // floats of shared memory for L and the RHS chunk
-  a.chunk_rows = std::max(1, std::min(n, (budget - s * s) / s));
-  size_t smem = sizeof(float) * ((size_t)s * s + (size_t)a.chunk_rows * s);
+  a.chunk_rows = solve_chunk_rows(s, n);
+  size_t smem = solve_smem(s, a.chunk_rows);
   TT_CUDA(c, cudaFuncSetAttribute(k_prox_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k_prox_solve<<<1, 1024, smem, c->stream>>>(a);
   TT_LAUNCH(c, "k_prox_solve");
@@ -406,7 +485,11 @@ int tt_launch_lq_right(tt_ctx* c, float* core_km1, float* core_k, int k) {
 }
 
 // ---------------------------------------------------------------------------------------------
-// relative error: one warp per mode-0 fibre f = (i_1, ..., i_{d-1})
+// relative error. The tensor is walked in slabs of modes (0, 1) (contiguous n_0 x n_1 blocks):
+// for the slab's tail indices (i_2, .., i_{d-1}) one warp forms u = G_2(i_2) ... G_{d-1}(i_{d-1})
+// (r_2 entries), the CTA forms W(:, i_1) = G_1(:, i_1, :) u for the slab's i_1 range, and every
+// entry is then reconstructed as G_0(0, i_0, :) . W(:, i_1) and compared with A, reading A in
+// order. Work items are (slab, i_1-chunk) so that order-2 tensors still spread over all SMs.
 
 struct ErrArgs {
   const void* A;
@@ -414,18 +497,21 @@ struct ErrArgs {
   const float* core[TT_MAX_D];
   int64_t n[TT_MAX_D];
   int r[TT_MAX_D + 1];
-  int d, dtype;
-  int64_t M0;
-  double* acc;  // [0] += ||A - [[G]]||^2, [1] += ||A||^2
+  int d;
+  int64_t slabs;      // prod_{s>=2} n_s
+  int i1chunk;        // i_1 values per work item
+  int nchunks;        // ceil(n_1 / i1chunk)
+  int g0_in_smem;     // G_0 (n_0 x r_1) staged in shared memory
+  double* acc;        // [0] += ||A - [[G]]||^2, [1] += ||A||^2
 };
 
 template <int DT>
-__device__ float err_elem(const ErrArgs& a, int64_t idx) {
-  if constexpr (DT == TT_F64) return (float)__ldg((const double*)a.A + idx);
-  if constexpr (DT == TT_F32) return __ldg((const float*)a.A + idx);
-  if constexpr (DT == TT_BF16) return __uint_as_float(((uint32_t)__ldg((const unsigned short*)a.A + idx)) << 16);
+__device__ __forceinline__ float err_elem(const void* A, int64_t idx) {
+  if constexpr (DT == TT_F64) return (float)__ldg((const double*)A + idx);
+  if constexpr (DT == TT_F32) return __ldg((const float*)A + idx);
+  if constexpr (DT == TT_BF16) return __uint_as_float(((uint32_t)__ldg((const unsigned short*)A + idx)) << 16);
   if constexpr (DT == TT_FP8E4M3) {
-    uint32_t cc = __ldg((const unsigned char*)a.A + idx);
+    uint32_t cc = __ldg((const unsigned char*)A + idx);
     uint32_t sg = (cc & 0x80u) << 24, e = (cc >> 3) & 0xFu, mm = cc & 7u;
     float mag = e ? __uint_as_float(((e + 120u) << 23) | (mm << 20)) : (float)mm * 0.001953125f;
     return __uint_as_float(__float_as_uint(mag) | sg);
@@ -435,65 +521,94 @@ __device__ float err_elem(const ErrArgs& a, int64_t idx) {
 
 template <int DT>
 __global__ void __launch_bounds__(256) k_rel_error(ErrArgs a) {
-  __shared__ float ubuf[8][2][TT_MAX_S];
+  extern __shared__ float sm[];
+  __shared__ float ubuf[2][TT_MAX_S];
   __shared__ double red[2][8];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  const int n0 = (int)a.n[0], r1 = a.r[1];
-  double e2 = 0.0, a2 = 0.0;
-  for (int64_t f = warp; f < a.M0; f += nwarps) {
-    // indices of modes 1..d-1
-    int64_t idx[TT_MAX_D];
-    int64_t rem = f;
-    for (int s2 = 1; s2 < a.d; ++s2) {
-      idx[s2] = rem % a.n[s2];
-      rem /= a.n[s2];
-    }
-    // u = G_{d-1}(:, i, 0), then u <- G_s(:, i_s, :) u for s = d-2..1
-    float* u = ubuf[wib][0];
-    float* un = ubuf[wib][1];
-    {
-      const int s2 = a.d - 1, ra = a.r[s2];
-      for (int al = lane; al < ra; al += 32) u[al] = a.core[s2][al + (int64_t)ra * idx[s2]];
-    }
-    __syncwarp();
-    for (int s2 = a.d - 2; s2 >= 1; --s2) {
-      const int ra = a.r[s2], rb = a.r[s2 + 1];
-      const float* G = a.core[s2] + (int64_t)ra * idx[s2];  // G(al, i, be) at al + ra*(i + n*be)
-      const int64_t bstride = (int64_t)ra * a.n[s2];
-      for (int al = lane; al < ra; al += 32) {
-        float acc = 0.f;
-        for (int be = 0; be < rb; ++be) acc = fmaf(G[al + bstride * be], u[be], acc);
-        un[al] = acc;
+  const int n0 = (int)a.n[0], n1 = (int)a.n[1], r1 = a.r[1], r2 = a.r[2];
+  float* W = sm;                                   // r1 x i1chunk
+  float* G0 = sm + (size_t)r1 * a.i1chunk;         // n0 x r1 (optional)
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const float* g0 = a.core[0];
+  if (a.g0_in_smem) {
+    for (int i = threadIdx.x; i < n0 * r1; i += blockDim.x) G0[i] = g0[i];
+    g0 = G0;
+  }
+  double e2 = 0.0, x2 = 0.0;
+  const int64_t items = a.slabs * a.nchunks;
+  for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+    const int64_t t = it / a.nchunks;
+    const int ch = (int)(it - t * a.nchunks);
+    const int j0 = ch * a.i1chunk, j1 = min(n1, j0 + a.i1chunk);
+    // u = G_2(i_2) ... G_{d-1}(i_{d-1}) (r_2 entries); u = [1] when d == 2
+    if (warp == 0) {
+      int64_t idx[TT_MAX_D];
+      int64_t rem = t;
+      for (int s2 = 2; s2 < a.d; ++s2) {
+        idx[s2] = rem % a.n[s2];
+        rem /= a.n[s2];
+      }
+      float* u = ubuf[0];
+      float* un = ubuf[1];
+      if (a.d == 2) {
+        if (lane == 0) u[0] = 1.f;
+      } else {
+        const int s2 = a.d - 1, ra = a.r[s2];
+        for (int al = lane; al < ra; al += 32) u[al] = a.core[s2][al + (int64_t)ra * idx[s2]];
       }
       __syncwarp();
-      float* t = u;
-      u = un;
-      un = t;
+      for (int s2 = a.d - 2; s2 >= 2; --s2) {
+        const int ra = a.r[s2], rb = a.r[s2 + 1];
+        const float* G = a.core[s2] + (int64_t)ra * idx[s2];
+        const int64_t bstride = (int64_t)ra * a.n[s2];
+        for (int al = lane; al < ra; al += 32) {
+          float acc = 0.f;
+          for (int be = 0; be < rb; ++be) acc = fmaf(G[al + bstride * be], u[be], acc);
+          un[al] = acc;
+        }
+        __syncwarp();
+        for (int al = lane; al < ra; al += 32) u[al] = un[al];
+        __syncwarp();
+      }
     }
-    const int64_t base = f * n0;
+    __syncthreads();
+    // W(al, i1) = sum_be G_1(al, i1, be) u(be)
+    const float* g1 = a.core[1];
+    for (int q = threadIdx.x; q < r1 * (j1 - j0); q += blockDim.x) {
+      const int al = q % r1, i1 = j0 + q / r1;
+      float acc = 0.f;
+      for (int be = 0; be < r2; ++be) acc = fmaf(g1[al + (int64_t)r1 * (i1 + (int64_t)n1 * be)], ubuf[0][be], acc);
+      W[(size_t)al * a.i1chunk + (i1 - j0)] = acc;
+    }
+    __syncthreads();
+    const int64_t base = t * (int64_t)n0 * n1 + (int64_t)j0 * n0;
+    const int cnt = (j1 - j0) * n0;
     float fe = 0.f, fa = 0.f;
-    for (int i0 = lane; i0 < n0; i0 += 32) {
+    const int step_q = blockDim.x / n0, step_r = blockDim.x - step_q * n0;
+    int i1 = threadIdx.x / n0, i0 = threadIdx.x - (threadIdx.x / n0) * n0;
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x, i0 += step_r, i1 += step_q) {
+      if (i0 >= n0) {
+        i0 -= n0;
+        ++i1;
+      }
       float rec = 0.f;
-      for (int al = 0; al < r1; ++al) rec = fmaf(a.core[0][i0 + (int64_t)n0 * al], u[al], rec);
-      float x = err_elem<DT>(a, base + i0);
+      for (int al = 0; al < r1; ++al) rec = fmaf(g0[i0 + n0 * al], W[(size_t)al * a.i1chunk + i1], rec);
+      float x = err_elem<DT>(a.A, base + e);
       if (a.scales) x *= __ldg(a.scales + i0);
-      float dlt = x - rec;
-      fe = fmaf(dlt, dlt, fe);
+      const float dl = x - rec;
+      fe = fmaf(dl, dl, fe);
       fa = fmaf(x, x, fa);
     }
     e2 += fe;
-    a2 += fa;
-    __syncwarp();
+    x2 += fa;
+    __syncthreads();
   }
   for (int o = 16; o > 0; o >>= 1) {
     e2 += __shfl_xor_sync(0xffffffffu, e2, o);
-    a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+    x2 += __shfl_xor_sync(0xffffffffu, x2, o);
   }
   if (lane == 0) {
-    red[0][wib] = e2;
-    red[1][wib] = a2;
+    red[0][warp] = e2;
+    red[1][warp] = x2;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -517,16 +632,37 @@ int tt_launch_rel_error(tt_ctx* c, const void* A, const float* scales, float* co
   }
   for (int k = 0; k <= c->d; ++k) a.r[k] = c->r[k];
   a.d = c->d;
-  a.dtype = c->dtype;
-  a.M0 = c->M0;
   a.acc = c->d_err_acc;
+  a.slabs = c->N / (c->n[0] * c->n[1]);
+  // i_1 chunk: at most 16K entries per item and at least ~4 items per SM overall
+  int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(c->n[1], 16384 / std::max<int64_t>(1, c->n[0])));
+  while (chunk > 1 && a.slabs * ((c->n[1] + chunk - 1) / chunk) < 152 * 4) chunk = (chunk + 1) / 2;
+  a.i1chunk = (int)chunk;
+  a.nchunks = (int)((c->n[1] + chunk - 1) / chunk);
+  size_t smem = sizeof(float) * (size_t)c->r[1] * a.i1chunk;
+  const size_t g0sz = sizeof(float) * (size_t)c->n[0] * c->r[1];
+  a.g0_in_smem = (smem + g0sz <= 96 * 1024) ? 1 : 0;
+  if (a.g0_in_smem) smem += g0sz;
   TT_CUDA(c, cudaMemsetAsync(c->d_err_acc, 0, sizeof(double) * 2, c->stream));
-  int blocks = (int)std::min<int64_t>((c->M0 + 7) / 8, 152 * 16);
+  const int64_t items = a.slabs * a.nchunks;
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(items, 152 * 8));
   switch (c->dtype) {
-    case TT_F64: k_rel_error<TT_F64><<<blocks, 256, 0, c->stream>>>(a); break;
-    case TT_F32: k_rel_error<TT_F32><<<blocks, 256, 0, c->stream>>>(a); break;
-    case TT_BF16: k_rel_error<TT_BF16><<<blocks, 256, 0, c->stream>>>(a); break;
-    default: k_rel_error<TT_FP8E4M3><<<blocks, 256, 0, c->stream>>>(a); break;
+    case TT_F64:
+      TT_CUDA(c, cudaFuncSetAttribute(k_rel_error<TT_F64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_rel_error<TT_F64><<<blocks, 256, smem, c->stream>>>(a);
+      break;
+    case TT_F32:
+      TT_CUDA(c, cudaFuncSetAttribute(k_rel_error<TT_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_rel_error<TT_F32><<<blocks, 256, smem, c->stream>>>(a);
+      break;
+    case TT_BF16:
+      TT_CUDA(c, cudaFuncSetAttribute(k_rel_error<TT_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_rel_error<TT_BF16><<<blocks, 256, smem, c->stream>>>(a);
+      break;
+    default:
+      TT_CUDA(c, cudaFuncSetAttribute(k_rel_error<TT_FP8E4M3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_rel_error<TT_FP8E4M3><<<blocks, 256, smem, c->stream>>>(a);
+      break;
   }
   TT_LAUNCH(c, "k_rel_error");
   return TT_OK;
@@ -607,9 +743,8 @@ extern "C" int tt_prox_update_noalloc(const float* Y_dev, const float* SH_dev, f
   a.n = n;
   a.r0 = r0;
   a.r1 = r1;
-  const int budget = 48 * 1024;
-  a.chunk_rows = std::max(1, std::min(n, (budget - s * s) / s));
-  size_t smem = sizeof(float) * ((size_t)s * s + (size_t)a.chunk_rows * s);
+  a.chunk_rows = solve_chunk_rows(s, n);
+  size_t smem = solve_smem(s, a.chunk_rows);
   if (cudaFuncSetAttribute(k_prox_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return TT_ECUDA;
   k_prox_solve<<<1, 1024, smem, st>>>(a);
