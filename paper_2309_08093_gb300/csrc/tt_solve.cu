@@ -168,7 +168,8 @@ __global__ void __launch_bounds__(1024) k_prox_solve(SolveArgs a) {
   __syncthreads();
   double dsum = 0.0, nsum = 0.0;
   const int ZP = P;
-  for (int i0 = 0; i0 < a.n; i0 += a.chunk_rows) {
+  // each CTA (re)factorises M and solves its own slice of chunk_rows right-hand-side rows
+  for (int i0 = blockIdx.x * a.chunk_rows; i0 < a.n; i0 += gridDim.x * a.chunk_rows) {
     const int nr = min(a.chunk_rows, a.n - i0);
     for (int idx = t; idx < nr * s; idx += T) {
       const int i = idx / s, c = idx - i * s;
@@ -255,9 +256,9 @@ __global__ void __launch_bounds__(1024) k_prox_solve(SolveArgs a) {
   }
   double t1 = block_sum(dsum, red);
   double t2 = block_sum(nsum, red);
-  if (t == 0 && a.change) {
-    a.change[0] = t1;
-    a.change[1] = t2;
+  if (t == 0 && a.change) {  // slot zeroed by the host
+    atomicAdd(a.change, t1);
+    atomicAdd(a.change + 1, t2);
   }
 }
 
@@ -267,9 +268,9 @@ static size_t solve_smem(int s, int chunk_rows) {
 }
 
 static int solve_chunk_rows(int s, int n) {
-  // rows per chunk: at most 128 (rows x 32 block columns <= 4 items per thread of 1024) and
-  // within ~200 KB of shared memory
-  int rows = std::min(n, 128);
+  // rows per CTA: 16 (rows x 32 block columns <= 4 items per thread of 1024) and within
+  // ~200 KB of shared memory
+  int rows = std::min(n, 16);
   while (rows > 1 && solve_smem(s, rows) > 200 * 1024) rows = (rows + 1) / 2;
   return std::max(1, rows);
 }
@@ -303,7 +304,8 @@ int tt_launch_prox_update(tt_ctx* c, const float* Y, const float* SH, float* cor
   a.chunk_rows = solve_chunk_rows(s, n);
   size_t smem = solve_smem(s, a.chunk_rows);
   TT_CUDA(c, cudaFuncSetAttribute(k_prox_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_prox_solve<<<1, 1024, smem, c->stream>>>(a);
+  if (change_slot) TT_CUDA(c, cudaMemsetAsync(change_slot, 0, 2 * sizeof(double), c->stream));
+  k_prox_solve<<<(n + a.chunk_rows - 1) / a.chunk_rows, 1024, smem, c->stream>>>(a);
   TT_LAUNCH(c, "k_prox_solve");
   return TT_OK;
 }
@@ -401,21 +403,137 @@ __device__ void block_householder_qr(float* A, int m, int q, float* Rm, float* t
   }
 }
 
+// CholeskyQR2 of the m x q column-major matrix A (pitch lda) in shared memory: two passes of
+// W = A^T A (threads own (i, j, row-group) partial sums), W = R^T R (one warp, FP32 Cholesky),
+// A <- A R^{-1} (one thread per row). With rows >= q and a well-conditioned A the result is the
+// unique QR factorisation with positive diagonal; a non-positive or relatively tiny pivot
+// (rank deficiency, a wide matrix, a very ill-conditioned core) returns false and the caller
+// falls back to Householder. On success A holds Q and Rm (q x q row-major) holds R.
+__device__ bool block_cholqr2(float* A, int m, int q, int lda, float* Rm, float* W, float* Rp, int* flag) {
+  const int t = threadIdx.x, T = blockDim.x;
+  const int lane = t & 31, warp = t >> 5;
+  const int pairs = q * q;
+  const int G = max(1, min(32, T / max(1, pairs)));
+  for (int pass = 0; pass < 2; ++pass) {
+    // W = A^T A, partial sums over row groups
+    for (int idx = t; idx < pairs * G; idx += T) {
+      const int pr = idx % pairs, g = idx / pairs;
+      const int i = pr / q, j = pr - i * q;
+      float acc = 0.f;
+      if (j <= i)
+        for (int r = g; r < m; r += G) acc = fmaf(A[r + lda * i], A[r + lda * j], acc);
+      W[idx] = acc;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      // reduce the groups, then Cholesky W = L L^T (lower, row-major in Rp); R = L^T
+      for (int pr = lane; pr < pairs; pr += 32) {
+        float acc = 0.f;
+        for (int g = 0; g < G; ++g) acc += W[pr + pairs * g];
+        Rp[pr] = acc;
+      }
+      __syncwarp();
+      float dmax = 0.f;
+      for (int i = 0; i < q; ++i) dmax = fmaxf(dmax, Rp[i * q + i]);
+      int ok = (dmax > 0.f && isfinite(dmax)) ? 1 : 0;
+      for (int j = 0; j < q && ok; ++j) {
+        const float pj = Rp[j * q + j];
+        if (!(pj > 1e-6f * dmax) || !isfinite(pj)) {  // kappa(A) above ~1e3: use Householder
+          ok = 0;
+          break;
+        }
+        const float lj = sqrtf(pj);
+        __syncwarp();
+        for (int i = j + lane; i < q; i += 32) Rp[i * q + j] = (i == j) ? lj : Rp[i * q + j] / lj;
+        __syncwarp();
+        for (int i = j + 1 + lane; i < q; i += 32) {
+          const float lij = Rp[i * q + j];
+          for (int l = j + 1; l <= i; ++l) Rp[i * q + l] -= lij * Rp[l * q + j];
+        }
+        __syncwarp();
+      }
+      if (lane == 0) *flag = ok;
+    }
+    __syncthreads();
+    if (!*flag) return false;
+    // A <- A R^{-1} with R = L^T: row r solves x L^T = a_r (x_j = (a_j - sum_{l<j} x_l L[j][l]) / L[j][j])
+    for (int r = t; r < m; r += T) {
+      for (int j = 0; j < q; ++j) {
+        float v = A[r + lda * j];
+        for (int l = 0; l < j; ++l) v -= A[r + lda * l] * Rp[j * q + l];
+        A[r + lda * j] = v / Rp[j * q + j];
+      }
+    }
+    // R_total = R_pass * R_total  (R_pass = L^T upper)
+    if (warp == 1 || (T == 32 && warp == 0)) {
+      for (int pr = lane; pr < pairs; pr += 32) {
+        const int i = pr / q, j = pr - i * q;
+        float acc = 0.f;
+        if (pass == 0) {
+          acc = (j >= i) ? Rp[j * q + i] : 0.f;
+        } else {
+          for (int l = i; l <= j; ++l) acc = fmaf(Rp[l * q + i], Rm[l * q + j], acc);
+        }
+        W[pr] = acc;
+      }
+      __syncwarp();
+      for (int pr = lane; pr < pairs; pr += 32) Rm[pr] = W[pr];
+    }
+    __syncthreads();
+  }
+  return true;
+}
+
+// Shared-memory layout of the QR kernels: A (lda x q) | Rm (q x q) | tau (q) | colsc (4) |
+// W (max(q*q, 512)) | Rp (q*q). CholeskyQR2 is used for q <= 32; otherwise, or when it reports a
+// tiny pivot, Householder runs on a dense copy (pitch m) of the input.
+struct QrSmem {
+  float *A, *Rm, *tau, *colsc, *W, *Rp;
+  int lda;
+};
+__device__ QrSmem qr_layout(float* sm, int m, int q, int use_chol) {
+  QrSmem L;
+  L.lda = use_chol ? (m | 1) : m;
+  L.A = sm;
+  L.Rm = L.A + (int64_t)L.lda * q;
+  L.tau = L.Rm + q * q;
+  L.colsc = L.tau + q;
+  L.W = L.colsc + 4;
+  L.Rp = L.W + max(q * q, 512);
+  return L;
+}
+
 // G_k^L (m = r0 n rows, q = r1 cols) = Q R; G_k <- Q (zero-padded); G_{k+1} <- R G_{k+1}^R
 __global__ void __launch_bounds__(512) k_qr_left(float* core, float* next, int r0, int n, int r1,
-                                                 int ncols_next, const int* status) {
+                                                 int ncols_next, int use_chol, const int* status) {
   extern __shared__ float sm[];
+  __shared__ int flag;
   if (*status != 0) return;
   const int m = r0 * n, q = r1;
-  float* A = sm;
-  float* Rm = A + (int64_t)m * q;
-  float* tau = Rm + q * q;
-  float* colsc = tau + q;
-  for (int idx = threadIdx.x; idx < m * q; idx += blockDim.x) A[idx] = core[idx];
+  const QrSmem L = qr_layout(sm, m, q, use_chol);
+  bool ok = false;
+  if (use_chol && m >= q) {
+    for (int idx = threadIdx.x; idx < m * q; idx += blockDim.x) {
+      const int r = idx % m, j = idx / m;
+      L.A[r + L.lda * j] = core[idx];
+    }
+    __syncthreads();
+    ok = block_cholqr2(L.A, m, q, L.lda, L.Rm, L.W, L.Rp, &flag);
+    __syncthreads();
+    if (ok)
+      for (int idx = threadIdx.x; idx < m * q; idx += blockDim.x) {
+        const int r = idx % m, j = idx / m;
+        core[idx] = L.A[r + L.lda * j];
+      }
+  }
+  if (!ok) {  // Householder on a dense copy of the input (G_k^L is column-major, pitch m)
+    for (int idx = threadIdx.x; idx < m * q; idx += blockDim.x) L.A[idx] = core[idx];
+    __syncthreads();
+    block_householder_qr(L.A, m, q, L.Rm, L.tau, L.colsc);
+    const int p = min(m, q);
+    for (int idx = threadIdx.x; idx < m * q; idx += blockDim.x) core[idx] = (idx / m < p) ? L.A[idx] : 0.f;
+  }
   __syncthreads();
-  block_householder_qr(A, m, q, Rm, tau, colsc);
-  const int p = min(m, q);
-  for (int idx = threadIdx.x; idx < m * q; idx += blockDim.x) core[idx] = (idx / m < p) ? A[idx] : 0.f;
   // next^R is r1 x ncols_next column-major: column c holds r1 contiguous entries
   for (int cidx = threadIdx.x; cidx < ncols_next; cidx += blockDim.x) {
     float col[TT_MAX_S];
@@ -423,7 +541,7 @@ __global__ void __launch_bounds__(512) k_qr_left(float* core, float* next, int r
     for (int b = 0; b < r1; ++b) col[b] = g[b];
     for (int a2 = 0; a2 < r1; ++a2) {
       float acc = 0.f;
-      for (int b = a2; b < r1; ++b) acc = fmaf(Rm[a2 * q + b], col[b], acc);
+      for (int b = a2; b < r1; ++b) acc = fmaf(L.Rm[a2 * q + b], col[b], acc);
       g[a2] = acc;
     }
   }
@@ -431,55 +549,76 @@ __global__ void __launch_bounds__(512) k_qr_left(float* core, float* next, int r
 
 // (G_k^R)^T (m = n r1 rows, q = r0 cols) = Q R; G_k^R <- Q^T; G_{k-1}^L <- G_{k-1}^L R^T
 __global__ void __launch_bounds__(512) k_lq_right(float* prev, float* core, int r0, int n, int r1,
-                                                  int nrows_prev, const int* status) {
+                                                  int nrows_prev, int use_chol, const int* status) {
   extern __shared__ float sm[];
+  __shared__ int flag;
   if (*status != 0) return;
   const int m = n * r1, q = r0;
-  float* A = sm;
-  float* Rm = A + (int64_t)m * q;
-  float* tau = Rm + q * q;
-  float* colsc = tau + q;
-  for (int idx = threadIdx.x; idx < m * q; idx += blockDim.x) {
-    int i = idx % m, a2 = idx / m;
-    A[idx] = core[a2 + (int64_t)r0 * i];
+  const QrSmem L = qr_layout(sm, m, q, use_chol);
+  bool ok = false;
+  if (use_chol && m >= q) {
+    for (int idx = threadIdx.x; idx < m * q; idx += blockDim.x) {
+      const int i = idx % m, a2 = idx / m;
+      L.A[i + L.lda * a2] = core[a2 + (int64_t)r0 * i];
+    }
+    __syncthreads();
+    ok = block_cholqr2(L.A, m, q, L.lda, L.Rm, L.W, L.Rp, &flag);
+    __syncthreads();
+    if (ok)
+      for (int idx = threadIdx.x; idx < m * q; idx += blockDim.x) {
+        const int i = idx % m, a2 = idx / m;
+        core[a2 + (int64_t)r0 * i] = L.A[i + L.lda * a2];
+      }
+  }
+  if (!ok) {
+    for (int idx = threadIdx.x; idx < m * q; idx += blockDim.x) {
+      const int i = idx % m, a2 = idx / m;
+      L.A[idx] = core[a2 + (int64_t)r0 * i];  // dense, pitch m
+    }
+    __syncthreads();
+    block_householder_qr(L.A, m, q, L.Rm, L.tau, L.colsc);
+    const int p = min(m, q);
+    for (int idx = threadIdx.x; idx < m * q; idx += blockDim.x) {
+      const int i = idx % m, a2 = idx / m;
+      core[a2 + (int64_t)r0 * i] = (a2 < p) ? L.A[idx] : 0.f;
+    }
   }
   __syncthreads();
-  block_householder_qr(A, m, q, Rm, tau, colsc);
-  const int p = min(m, q);
-  for (int idx = threadIdx.x; idx < m * q; idx += blockDim.x) {
-    int i = idx % m, a2 = idx / m;
-    core[a2 + (int64_t)r0 * i] = (a2 < p) ? A[idx] : 0.f;
-  }
   // prev^L is nrows_prev x r0 column-major; row t: prev[t + nrows_prev * a]
   for (int t = threadIdx.x; t < nrows_prev; t += blockDim.x) {
     float row[TT_MAX_S];
     for (int a2 = 0; a2 < r0; ++a2) row[a2] = prev[t + (int64_t)nrows_prev * a2];
     for (int b = 0; b < r0; ++b) {
       float acc = 0.f;
-      for (int a2 = b; a2 < r0; ++a2) acc = fmaf(row[a2], Rm[b * q + a2], acc);  // (G R^T)[t, b]
+      for (int a2 = b; a2 < r0; ++a2) acc = fmaf(row[a2], L.Rm[b * q + a2], acc);  // (G R^T)[t, b]
       prev[t + (int64_t)nrows_prev * b] = acc;
     }
   }
 }
 
-static size_t qr_smem(int m, int q) { return sizeof(float) * ((size_t)m * q + (size_t)q * q + q + 4); }
+static size_t qr_smem(int m, int q, int use_chol) {
+  const size_t lda = use_chol ? (size_t)(m | 1) : (size_t)m;
+  return sizeof(float) * (lda * q + (size_t)q * q + q + 4 + (size_t)std::max(q * q, 512) + (size_t)q * q);
+}
 
 int tt_launch_qr_left(tt_ctx* c, float* core_k, float* core_k1, int k) {
   int r0 = c->r[k], n = (int)c->n[k], r1 = c->r[k + 1];
-  size_t smem = qr_smem(r0 * n, r1);
+  const int use_chol = (r1 <= 32) ? 1 : 0;
+  size_t smem = qr_smem(r0 * n, r1, use_chol);
   TT_CUDA(c, cudaFuncSetAttribute(k_qr_left, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int ncols = (int)(c->n[k + 1] * c->r[k + 2]);
-  k_qr_left<<<1, 512, smem, c->stream>>>(core_k, core_k1, r0, n, r1, ncols, c->d_status);
+  k_qr_left<<<1, 512, smem, c->stream>>>(core_k, core_k1, r0, n, r1, ncols, use_chol, c->d_status);
   TT_LAUNCH(c, "k_qr_left");
   return TT_OK;
 }
 
 int tt_launch_lq_right(tt_ctx* c, float* core_km1, float* core_k, int k) {
   int r0 = c->r[k], n = (int)c->n[k], r1 = c->r[k + 1];
-  size_t smem = qr_smem(n * r1, r0);
+  const int use_chol = (r0 <= 32) ? 1 : 0;
+  size_t smem = qr_smem(n * r1, r0, use_chol);
   TT_CUDA(c, cudaFuncSetAttribute(k_lq_right, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int nrows = (int)(c->r[k - 1] * c->n[k - 1]);
-  k_lq_right<<<1, 512, smem, c->stream>>>(core_km1, core_k, r0, n, r1, nrows, c->d_status);
+  k_lq_right<<<1, 512, smem, c->stream>>>(core_km1, core_k, r0, n, r1, nrows, use_chol, c->d_status);
   TT_LAUNCH(c, "k_lq_right");
   return TT_OK;
 }
@@ -525,22 +664,18 @@ __global__ void __launch_bounds__(256) k_rel_error(ErrArgs a) {
   __shared__ float ubuf[2][TT_MAX_S];
   __shared__ double red[2][8];
   const int n0 = (int)a.n[0], n1 = (int)a.n[1], r1 = a.r[1], r2 = a.r[2];
-  float* W = sm;                                   // r1 x i1chunk
-  float* G0 = sm + (size_t)r1 * a.i1chunk;         // n0 x r1 (optional)
+  const int WP = a.i1chunk;                        // W pitch (multiple of 4)
+  float* W = sm;                                   // r1 x WP
+  float* G0 = sm + (size_t)r1 * WP;                // r1 x n0 (G_0(0, i0, al) at al * n0 + i0)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const float* g0 = a.core[0];
-  if (a.g0_in_smem) {
-    for (int i = threadIdx.x; i < n0 * r1; i += blockDim.x) G0[i] = g0[i];
-    g0 = G0;
-  }
+  for (int i = threadIdx.x; i < n0 * r1; i += blockDim.x) G0[i] = a.core[0][i];
   double e2 = 0.0, x2 = 0.0;
   const int64_t items = a.slabs * a.nchunks;
   for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
     const int64_t t = it / a.nchunks;
     const int ch = (int)(it - t * a.nchunks);
     const int j0 = ch * a.i1chunk, j1 = min(n1, j0 + a.i1chunk);
-    // u = G_2(i_2) ... G_{d-1}(i_{d-1}) (r_2 entries); u = [1] when d == 2
-    if (warp == 0) {
+    if (warp == 0) {  // u = G_2(i_2) ... G_{d-1}(i_{d-1}), or [1] when d == 2
       int64_t idx[TT_MAX_D];
       int64_t rem = t;
       for (int s2 = 2; s2 < a.d; ++s2) {
@@ -571,32 +706,45 @@ __global__ void __launch_bounds__(256) k_rel_error(ErrArgs a) {
       }
     }
     __syncthreads();
-    // W(al, i1) = sum_be G_1(al, i1, be) u(be)
+    // W(al, i1) = sum_be G_1(al, i1, be) u(be), zero-padded to a multiple of 4 columns
     const float* g1 = a.core[1];
-    for (int q = threadIdx.x; q < r1 * (j1 - j0); q += blockDim.x) {
-      const int al = q % r1, i1 = j0 + q / r1;
+    const int wcols = (j1 - j0 + 3) & ~3;
+    for (int q = threadIdx.x; q < r1 * wcols; q += blockDim.x) {
+      const int al = q / wcols, c = q - al * wcols, i1 = j0 + c;
       float acc = 0.f;
-      for (int be = 0; be < r2; ++be) acc = fmaf(g1[al + (int64_t)r1 * (i1 + (int64_t)n1 * be)], ubuf[0][be], acc);
-      W[(size_t)al * a.i1chunk + (i1 - j0)] = acc;
+      if (i1 < j1)
+        for (int be = 0; be < r2; ++be) acc = fmaf(g1[al + (int64_t)r1 * (i1 + (int64_t)n1 * be)], ubuf[0][be], acc);
+      W[(size_t)al * WP + c] = acc;
     }
     __syncthreads();
+    // tiles of 4 consecutive i1 for one i0: one G0 load and one 16-byte W load per al feed 4 FMAs
     const int64_t base = t * (int64_t)n0 * n1 + (int64_t)j0 * n0;
-    const int cnt = (j1 - j0) * n0;
+    const int ngroups = wcols >> 2;
+    const int tiles = ngroups * n0;
     float fe = 0.f, fa = 0.f;
-    const int step_q = blockDim.x / n0, step_r = blockDim.x - step_q * n0;
-    int i1 = threadIdx.x / n0, i0 = threadIdx.x - (threadIdx.x / n0) * n0;
-    for (int e = threadIdx.x; e < cnt; e += blockDim.x, i0 += step_r, i1 += step_q) {
-      if (i0 >= n0) {
-        i0 -= n0;
-        ++i1;
+    for (int q = threadIdx.x; q < tiles; q += blockDim.x) {
+      const int gq = q / n0, i0 = q - gq * n0;
+      float r4[4] = {0.f, 0.f, 0.f, 0.f};
+      const float* wp = W + 4 * gq;
+      for (int al = 0; al < r1; ++al) {
+        const float g = G0[al * n0 + i0];
+        const float4 w4 = *reinterpret_cast<const float4*>(wp + (size_t)al * WP);
+        r4[0] = fmaf(g, w4.x, r4[0]);
+        r4[1] = fmaf(g, w4.y, r4[1]);
+        r4[2] = fmaf(g, w4.z, r4[2]);
+        r4[3] = fmaf(g, w4.w, r4[3]);
       }
-      float rec = 0.f;
-      for (int al = 0; al < r1; ++al) rec = fmaf(g0[i0 + n0 * al], W[(size_t)al * a.i1chunk + i1], rec);
-      float x = err_elem<DT>(a.A, base + e);
-      if (a.scales) x *= __ldg(a.scales + i0);
-      const float dl = x - rec;
-      fe = fmaf(dl, dl, fe);
-      fa = fmaf(x, x, fa);
+      const float sc = a.scales ? __ldg(a.scales + i0) : 1.f;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int i1 = 4 * gq + c;
+        if (j0 + i1 < j1) {
+          const float x = err_elem<DT>(a.A, base + (int64_t)i1 * n0 + i0) * sc;
+          const float dl = x - r4[c];
+          fe = fmaf(dl, dl, fe);
+          fa = fmaf(x, x, fa);
+        }
+      }
     }
     e2 += fe;
     x2 += fa;
@@ -634,15 +782,17 @@ int tt_launch_rel_error(tt_ctx* c, const void* A, const float* scales, float* co
   a.d = c->d;
   a.acc = c->d_err_acc;
   a.slabs = c->N / (c->n[0] * c->n[1]);
-  // i_1 chunk: at most 16K entries per item and at least ~4 items per SM overall
-  int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(c->n[1], 16384 / std::max<int64_t>(1, c->n[0])));
-  while (chunk > 1 && a.slabs * ((c->n[1] + chunk - 1) / chunk) < 152 * 4) chunk = (chunk + 1) / 2;
+  // i_1 chunk (multiple of 4): W (r1 x chunk) plus G_0 (r1 x n0) within ~200 KB, at most ~16K
+  // entries per item, and at least ~4 items per SM overall
+  const int64_t g0sz = (int64_t)c->n[0] * c->r[1];
+  int64_t chunk = std::max<int64_t>(4, std::min<int64_t>(c->n[1], 16384 / std::max<int64_t>(1, c->n[0])));
+  chunk = (chunk + 3) & ~3ll;
+  while (chunk > 4 && (int64_t)c->r[1] * chunk + g0sz > 50 * 1024) chunk -= 4;
+  while (chunk > 4 && a.slabs * ((c->n[1] + chunk - 1) / chunk) < 152 * 4) chunk = ((chunk / 2) + 3) & ~3ll;
   a.i1chunk = (int)chunk;
   a.nchunks = (int)((c->n[1] + chunk - 1) / chunk);
-  size_t smem = sizeof(float) * (size_t)c->r[1] * a.i1chunk;
-  const size_t g0sz = sizeof(float) * (size_t)c->n[0] * c->r[1];
-  a.g0_in_smem = (smem + g0sz <= 96 * 1024) ? 1 : 0;
-  if (a.g0_in_smem) smem += g0sz;
+  a.g0_in_smem = 1;
+  const size_t smem = sizeof(float) * ((size_t)c->r[1] * a.i1chunk + (size_t)g0sz);
   TT_CUDA(c, cudaMemsetAsync(c->d_err_acc, 0, sizeof(double) * 2, c->stream));
   const int64_t items = a.slabs * a.nchunks;
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(items, 152 * 8));
@@ -747,7 +897,7 @@ extern "C" int tt_prox_update_noalloc(const float* Y_dev, const float* SH_dev, f
   size_t smem = solve_smem(s, a.chunk_rows);
   if (cudaFuncSetAttribute(k_prox_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return TT_ECUDA;
-  k_prox_solve<<<1, 1024, smem, st>>>(a);
+  k_prox_solve<<<(n + a.chunk_rows - 1) / a.chunk_rows, 1024, smem, st>>>(a);
   if (cudaGetLastError() != cudaSuccess) return TT_ECUDA;
   int hst = 0;
   if (cudaMemcpyAsync(&hst, status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return TT_ECUDA;
