@@ -148,6 +148,19 @@ static FibreGeom fibre_geom(int64_t fiber_bytes, int VB) {
 // ---------------------------------------------------------------------------------------------
 // the gather kernel
 
+__device__ __forceinline__ void cp_async_vec(void* smem, const void* gmem, int bytes) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  if (bytes == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+  else if (bytes == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem));
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
 struct GArgs {
   const char* A;
   const float* scales;    // n0 FP8 scales or null
@@ -157,174 +170,186 @@ struct GArgs {
   const int32_t* ulist;   // distinct c values
   const int64_t* ustart;  // starts into plan (U + 1)
   const int32_t* ucount;  // U
-  float* Y;               // J x ncol column-major (zeroed by the host when k >= 1)
+  float* Y;               // J x ncol column-major, zeroed by the host
   int64_t col_fibres;     // fibre-index stride of the output column (stride_k / n0); 0 for mode 0
   int J, n0, ncol;
-  int C;                  // c groups per chunk
-  int pitch;              // row pitch of the Z chunk (odd)
-  int elem_bytes;
+  int nseg;               // c-segments per column (work items = ncol * nseg)
+  int segmax;             // capacity of the staged segment (c groups)
   FibreGeom fg;
 };
 
-template <int DT, int VB, int U, bool MODE0>
+// Bytes of the cp.async ring at the start of the gather kernel's shared memory (none when the
+// vectors are loaded synchronously). Used by the kernel and by the host-side size computation.
+__host__ __device__ constexpr size_t gather_ring_bytes(bool async, int nwarps, int stages, int vb) {
+  return async ? (size_t)nwarps * stages * 32 * vb : 0;
+}
+
+// One work item = a contiguous segment of c groups of one output column (mode 0: of Y_0's
+// rows). The item's fibres are split evenly over the (warp, fibre-slot) pairs; each lane keeps S
+// of its 16-byte fibre pieces in flight with cp.async (one commit group per fibre, the slot is
+// refilled as soon as it is consumed) and sums runs of equal c in registers. When a run ends:
+//   mode 0  : the finished row goes to Y_0 (plain store if the run lies inside this slot's range,
+//             atomic add otherwise);
+//   mode >= 1: coef(i0) * run is added into bucket (c + h_0(i0)) mod J of the CTA's column copy.
+template <int DT, int VB, int S, bool MODE0>
 __global__ void __launch_bounds__(256, 2) k_unfold_gather(GArgs a) {
+  constexpr bool ASYNC = VB >= 4;  // cp.async moves 4, 8 or 16 bytes; 1-2 byte vectors load directly
   constexpr int EPV = TtVec<DT, VB>::EPV;
-  extern __shared__ float sm[];
+  extern __shared__ __align__(16) unsigned char smraw[];
   const int J = a.J;
-  float* Ys = sm;                                       // J (k >= 1 only)
-  float* Zs = Ys + (MODE0 ? 0 : J);                     // C x pitch
-  float* coef = Zs + (size_t)a.C * a.pitch;             // n0
-  int* h0s = reinterpret_cast<int*>(coef + a.n0);       // n0
-  int* cvals = h0s + a.n0;                              // C
-  int64_t* cst = reinterpret_cast<int64_t*>(sm) + ((size_t)((MODE0 ? 0 : J) + a.C * a.pitch + 2 * a.n0 + a.C + 1) / 2);
   const int T = blockDim.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = T >> 5;
-  for (int i = threadIdx.x; i < a.n0; i += T) {
-    float cf = 1.f;
-    if (!MODE0 && __ldg(a.v0 + i) < 0) cf = -1.f;
-    if (a.scales) cf *= __ldg(a.scales + i);
-    coef[i] = cf;
-    h0s[i] = MODE0 ? 0 : __ldg(a.h0 + i);
-  }
-  const int64_t U_ = *a.ucount;
-  const int64_t total = U_ * a.ncol;
-  const int64_t lo = total * blockIdx.x / gridDim.x, hi = total * (blockIdx.x + 1) / gridDim.x;
+  unsigned char* ring = smraw;                                           // nw x S x 32 x VB
+  float* Ys = reinterpret_cast<float*>(ring + gather_ring_bytes(ASYNC, nw, S, VB));  // J (mode >= 1)
+  int* sstart = reinterpret_cast<int*>(Ys + (MODE0 ? 0 : J));           // segmax + 1 (relative)
+  int* scval = sstart + a.segmax + 1;                                    // segmax
+  const int U_ = *a.ucount;
   const int slot = lane / a.fg.lpf, posl = lane - slot * a.fg.lpf;
+  const bool slot_ok = slot < a.fg.fpi;
   const int nslots = nw * a.fg.fpi;
   const int gslot = warp * a.fg.fpi + slot;
-  const bool slot_ok = slot < a.fg.fpi;
-  int cur_col = -1;
-  for (int64_t p0 = lo; p0 < hi;) {
-    const int col = (int)(p0 / U_);
-    const int64_t u0 = p0 - (int64_t)col * U_;
-    const int64_t cend = min(hi, (int64_t)(col + 1) * U_);
-    const int nc = (int)((cend - p0) < (int64_t)a.C ? (cend - p0) : (int64_t)a.C);
-    if (!MODE0 && col != cur_col) {
-      if (cur_col >= 0) {  // flush the finished column
-        __syncthreads();
-        float* yc = a.Y + (int64_t)J * cur_col;
-        if ((J & 3) == 0) {
-          for (int b = threadIdx.x * 4; b < J; b += T * 4) {
-            float4 v4 = make_float4(Ys[b], Ys[b + 1], Ys[b + 2], Ys[b + 3]);
-            atomicAdd(reinterpret_cast<float4*>(yc + b), v4);
-          }
-        } else {
-          for (int b = threadIdx.x; b < J; b += T) atomicAdd(yc + b, Ys[b]);
-        }
-        __syncthreads();
-      }
+  unsigned char* myring = ring + ((size_t)warp * S * 32 + lane) * VB;
+  const int items = a.ncol * a.nseg;
+  for (int item = blockIdx.x; item < items; item += gridDim.x) {
+    const int col = item / a.nseg, seg = item - col * a.nseg;
+    const int ua = (int)((int64_t)U_ * seg / a.nseg), ub = (int)((int64_t)U_ * (seg + 1) / a.nseg);
+    const int nu = ub - ua;
+    if (nu <= 0) continue;
+    const int64_t e0 = __ldg(a.ustart + ua);
+    for (int i = threadIdx.x; i <= nu; i += T) {
+      sstart[i] = (int)(__ldg(a.ustart + ua + i) - e0);
+      if (i < nu) scval[i] = __ldg(a.ulist + ua + i);
+    }
+    if (!MODE0)
       for (int i = threadIdx.x; i < J; i += T) Ys[i] = 0.f;
-      cur_col = col;
-    }
-    for (int i = threadIdx.x; i < nc * a.pitch; i += T) Zs[i] = 0.f;
-    for (int i = threadIdx.x; i <= nc; i += T) {
-      cst[i] = __ldg(a.ustart + u0 + i);
-      if (i < nc) cvals[i] = __ldg(a.ulist + u0 + i);
-    }
     __syncthreads();
-    // ---- phase 1: Z rows of the chunk by fibre gathers
-    {
-      const int64_t e0 = cst[0], ne = cst[nc] - e0;
-      const int64_t sb = e0 + ne * gslot / nslots, se = e0 + ne * (gslot + 1) / nslots;
-      const int64_t colf = (int64_t)col * a.col_fibres;
-      if (slot_ok && sb < se) {
-        // run containing sb: largest cu with cst[cu] <= sb
-        int lo2 = 0, hi2 = nc;  // cst[lo2] <= sb < cst[hi2]
-        while (hi2 - lo2 > 1) {
-          const int mid = (lo2 + hi2) >> 1;
-          if (cst[mid] <= sb) lo2 = mid; else hi2 = mid;
+    const int ne = sstart[nu];
+    const int sb = (int)((int64_t)ne * gslot / nslots), se = (int)((int64_t)ne * (gslot + 1) / nslots);
+    const int64_t colf = (int64_t)col * a.col_fibres;
+    const uint32_t* plan = a.plan + e0;
+    if (slot_ok && sb < se) {
+      int lo2 = 0, hi2 = nu;  // run containing sb: sstart[lo2] <= sb < sstart[hi2]
+      while (hi2 - lo2 > 1) {
+        const int mid = (lo2 + hi2) >> 1;
+        if (sstart[mid] <= sb) lo2 = mid; else hi2 = mid;
+      }
+      const int count = se - sb;
+      for (int ch = 0; ch < a.fg.nchunk; ++ch) {
+        const int vpos = ch * 32 + posl;
+        const bool lane_ok = vpos < a.fg.vpf;
+        const int64_t vbyte = (int64_t)vpos * VB;
+        float coefr[EPV];
+        int h0r[EPV];
+#pragma unroll
+        for (int e = 0; e < EPV; ++e) {
+          const int i0 = vpos * EPV + e;
+          float cf = 1.f;
+          int hh = 0;
+          if (lane_ok) {
+            if (!MODE0 && __ldg(a.v0 + i0) < 0) cf = -1.f;
+            if (a.scales) cf *= __ldg(a.scales + i0);
+            if (!MODE0) hh = __ldg(a.h0 + i0);
+          }
+          coefr[e] = cf;
+          h0r[e] = hh;
         }
-        for (int ch = 0; ch < a.fg.nchunk; ++ch) {
-          const int vpos = ch * 32 + posl;
-          const bool lane_ok = vpos < a.fg.vpf;
-          const int64_t vbyte = (int64_t)vpos * VB;
-          int cu = lo2;
-          int64_t next_b = cst[cu + 1];
-          bool first_run = true;
-          float acc[EPV];
+        int cu = lo2;
+        int next_b = sstart[cu + 1];
+        bool first_run = true;
+        float acc[EPV];
+#pragma unroll
+        for (int e = 0; e < EPV; ++e) acc[e] = 0.f;
+        // flush of the run of group cu (shared with a neighbour slot when `shared`)
+        auto flush = [&](bool shared) {
+          if (lane_ok) {
+            const int cv = scval[cu];
+            if (MODE0) {
+#pragma unroll
+              for (int e = 0; e < EPV; ++e) {
+                float* dst = a.Y + cv + (int64_t)J * (vpos * EPV + e);
+                const float v = coefr[e] * acc[e];
+                if (shared) atomicAdd(dst, v); else *dst = v;
+              }
+            } else {
+#pragma unroll
+              for (int e = 0; e < EPV; ++e) atomicAdd(Ys + ((cv + h0r[e]) & (J - 1)), coefr[e] * acc[e]);
+            }
+          }
 #pragma unroll
           for (int e = 0; e < EPV; ++e) acc[e] = 0.f;
-          uint32_t wn[U];
+        };
+        // pipeline: slot q of the ring holds fibre j with j % S == q
+        uint32_t wcur[S], wnext[S];
 #pragma unroll
-          for (int q = 0; q < U; ++q) wn[q] = (sb + q < se) ? __ldg(a.plan + sb + q) : 0u;
-          for (int64_t j0 = sb; j0 < se; j0 += U) {
-            typename TtVec<DT, VB>::Raw v[U];
-            uint32_t w[U];
-#pragma unroll
-            for (int q = 0; q < U; ++q) {
-              w[q] = wn[q];
-              if (lane_ok && j0 + q < se) {
-                const int64_t fib = (int64_t)(w[q] & 0x7FFFFFFFu) + colf;
-                v[q] = TtVec<DT, VB>::load(a.A + fib * a.fg.fiber_bytes + vbyte);
-              } else {
-                v[q] = TtVec<DT, VB>::zero();
-              }
-            }
-#pragma unroll
-            for (int q = 0; q < U; ++q) wn[q] = (j0 + U + q < se) ? __ldg(a.plan + j0 + U + q) : 0u;
-#pragma unroll
-            for (int q = 0; q < U; ++q) {
-              const int64_t j = j0 + q;
-              if (j < se) {
-                if (j >= next_b) {  // the run of group cu ended: write it
-                  if (lane_ok) {
-                    float* z = Zs + (size_t)cu * a.pitch + vpos * EPV;
-                    if (first_run) {
-#pragma unroll
-                      for (int e = 0; e < EPV; ++e) atomicAdd(z + e, acc[e]);
-                    } else {
-#pragma unroll
-                      for (int e = 0; e < EPV; ++e) z[e] = acc[e];
-                    }
-                  }
-#pragma unroll
-                  for (int e = 0; e < EPV; ++e) acc[e] = 0.f;
-                  first_run = false;
-                  do {
-                    ++cu;
-                    next_b = cst[cu + 1];
-                  } while (j >= next_b);
-                }
-                TtVec<DT, VB>::fma_into(v[q], (w[q] >> 31) ? -1.f : 1.f, acc);
-              }
-            }
+        for (int q = 0; q < S; ++q) {
+          wcur[q] = (q < count) ? __ldg(plan + sb + q) : 0u;
+          if constexpr (ASYNC) {
+            if (lane_ok && q < count)
+              cp_async_vec(myring + (size_t)q * 32 * VB,
+                           a.A + ((int64_t)(wcur[q] & 0x7FFFFFFFu) + colf) * a.fg.fiber_bytes + vbyte, VB);
+            cp_async_commit();
           }
-          if (lane_ok) {  // the slot's last run may be shared with the next slot
-            float* z = Zs + (size_t)cu * a.pitch + vpos * EPV;
+          wnext[q] = (S + q < count) ? __ldg(plan + sb + S + q) : 0u;
+        }
+        for (int j0 = 0; j0 < count; j0 += S) {
 #pragma unroll
-            for (int e = 0; e < EPV; ++e) atomicAdd(z + e, acc[e]);
+          for (int q = 0; q < S; ++q) {
+            const int j = j0 + q;
+            if (j < count) {
+              typename TtVec<DT, VB>::Raw raw;
+              if constexpr (ASYNC) {
+                cp_async_wait<S - 1>();
+                if (lane_ok) {
+                  const uint32_t* src = reinterpret_cast<const uint32_t*>(myring + (size_t)q * 32 * VB);
+#pragma unroll
+                  for (int t2 = 0; t2 < TtVec<DT, VB>::W; ++t2) raw.w[t2] = src[t2];
+                } else {
+                  raw = TtVec<DT, VB>::zero();
+                }
+              } else {
+                raw = lane_ok ? TtVec<DT, VB>::load(a.A + ((int64_t)(wcur[q] & 0x7FFFFFFFu) + colf) * a.fg.fiber_bytes + vbyte)
+                              : TtVec<DT, VB>::zero();
+              }
+              const int jr = sb + j;  // position within the item
+              if (jr >= next_b) {
+                flush(first_run || (sstart[cu] < sb));
+                first_run = false;
+                do {
+                  ++cu;
+                  next_b = sstart[cu + 1];
+                } while (jr >= next_b);
+              }
+              TtVec<DT, VB>::fma_into(raw, (wcur[q] >> 31) ? -1.f : 1.f, acc);
+              // refill slot q with fibre j + S, prefetch the plan word of fibre j + 2S
+              const int jn = j + S;
+              if constexpr (ASYNC) {
+                if (lane_ok && jn < count)
+                  cp_async_vec(myring + (size_t)q * 32 * VB,
+                               a.A + ((int64_t)(wnext[q] & 0x7FFFFFFFu) + colf) * a.fg.fiber_bytes + vbyte, VB);
+                cp_async_commit();
+              }
+              wcur[q] = wnext[q];
+              wnext[q] = (jn + S < count) ? __ldg(plan + sb + jn + S) : 0u;
+            }
           }
         }
+        if constexpr (ASYNC) cp_async_wait<0>();
+        // last run: shared with the next slot unless it ends exactly at se
+        flush(first_run || sstart[cu] < sb || sstart[cu + 1] > se);
       }
     }
     __syncthreads();
-    // ---- phase 2
-    if (MODE0) {
-      // finished rows c of Y_0: Y_0[c + J i0] = scale(i0) * Z[c, i0] (consecutive c: coalesced)
-      for (int idx = threadIdx.x; idx < nc * a.n0; idx += T) {
-        const int ul = idx % nc, i0 = idx / nc;
-        a.Y[cvals[ul] + (int64_t)J * i0] = coef[i0] * Zs[(size_t)ul * a.pitch + i0];
+    if (!MODE0) {  // flush the column copy
+      float* yc = a.Y + (int64_t)J * col;
+      if ((J & 3) == 0) {
+        for (int b = threadIdx.x * 4; b < J; b += T * 4) {
+          const float4 v4 = make_float4(Ys[b], Ys[b + 1], Ys[b + 2], Ys[b + 3]);
+          if (v4.x != 0.f || v4.y != 0.f || v4.z != 0.f || v4.w != 0.f) atomicAdd(reinterpret_cast<float4*>(yc + b), v4);
+        }
+      } else {
+        for (int b = threadIdx.x; b < J; b += T) atomicAdd(yc + b, Ys[b]);
       }
-    } else {
-      for (int idx = threadIdx.x; idx < nc * a.n0; idx += T) {
-        const int ul = idx % nc, i0 = idx / nc;
-        const int b = (cvals[ul] + h0s[i0]) & (J - 1);
-        atomicAdd(Ys + b, coef[i0] * Zs[(size_t)ul * a.pitch + i0]);
-      }
-    }
-    __syncthreads();
-    p0 += nc;
-  }
-  if (!MODE0 && cur_col >= 0) {
-    __syncthreads();
-    float* yc = a.Y + (int64_t)J * cur_col;
-    if ((J & 3) == 0) {
-      for (int b = threadIdx.x * 4; b < J; b += T * 4) {
-        float4 v4 = make_float4(Ys[b], Ys[b + 1], Ys[b + 2], Ys[b + 3]);
-        atomicAdd(reinterpret_cast<float4*>(yc + b), v4);
-      }
-    } else {
-      for (int b = threadIdx.x; b < J; b += T) atomicAdd(yc + b, Ys[b]);
+      __syncthreads();
     }
   }
 }
@@ -338,15 +363,10 @@ static int pick_vb(int64_t fiber_bytes, uintptr_t base, int elem_bytes) {
   return elem_bytes;
 }
 
-static size_t gather_smem(int J, bool mode0, int C, int pitch, int n0) {
-  size_t words = (size_t)(mode0 ? 0 : J) + (size_t)C * pitch + 2 * (size_t)n0 + C + 1;
-  words = (words + 1) & ~(size_t)1;  // cst is 8-byte aligned
-  return words * 4 + sizeof(int64_t) * (C + 1);
-}
-
 template <int DT, int VB, bool MODE0>
 static int launch_gather_vb(tt_ctx* c, const void* A, const float* scales, int k, float* Y) {
-  constexpr int U = 8;
+  constexpr int S = 12;
+  constexpr int THREADS = 256;
   GArgs a;
   a.A = (const char*)A;
   a.scales = scales;
@@ -361,25 +381,26 @@ static int launch_gather_vb(tt_ctx* c, const void* A, const float* scales, int k
   a.n0 = (int)c->n[0];
   a.ncol = MODE0 ? 1 : (int)c->n[k];
   a.col_fibres = MODE0 ? 0 : c->stride[k] / c->n[0];
-  a.elem_bytes = TtElem<DT>::bytes;
   a.fg = fibre_geom((int64_t)c->n[0] * TtElem<DT>::bytes, VB);
-  a.pitch = (a.n0 % 2 == 0) ? a.n0 + 1 : a.n0;
-  // chunk size: aim at two CTAs per SM (about 105 KB of shared memory each)
-  const size_t target = 105 * 1024;
-  int C = 256;
-  while (C > 32 && gather_smem(c->J, MODE0, C, a.pitch, a.n0) > target) C -= 32;
-  while (C > 1 && gather_smem(c->J, MODE0, C, a.pitch, a.n0) > 220 * 1024) C >>= 1;
-  a.C = C;
-  const size_t smem = gather_smem(c->J, MODE0, C, a.pitch, a.n0);
-  if (smem > 220 * 1024) return tt_fail(c, TT_EINVAL, "gather kernel needs %zu bytes of shared memory", smem);
-  TT_CUDA(c, cudaMemsetAsync(Y, 0, sizeof(float) * c->J * c->n[k], c->stream));  // empty groups stay 0
-  TT_CUDA(c, cudaFuncSetAttribute(k_unfold_gather<DT, VB, U, MODE0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int per_sm = 1;
-  TT_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_unfold_gather<DT, VB, U, MODE0>, 256, smem));
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
-  const int blocks = std::max(1, sms * std::max(1, per_sm));
-  k_unfold_gather<DT, VB, U, MODE0><<<blocks, 256, smem, c->stream>>>(a);
+  // work items (column, c-segment): at most one per CTA slot (two CTAs per SM) when the columns
+  // allow it, so that every CTA gets the same amount of work; segments of at most 2048 c groups
+  const int slots = 2 * sms;
+  int nseg = std::max(1, slots / a.ncol);
+  nseg = std::max(nseg, (c->J + 2047) / 2048);
+  a.nseg = nseg;
+  a.segmax = (c->J + nseg - 1) / nseg + 1;
+  const size_t ring = gather_ring_bytes(VB >= 4, THREADS / 32, S, VB);
+  const size_t smem = ring + sizeof(float) * (MODE0 ? 0 : c->J) + sizeof(int) * (2 * (size_t)a.segmax + 1);
+  if (smem > 220 * 1024) return tt_fail(c, TT_EINVAL, "gather kernel needs %zu bytes of shared memory", smem);
+  TT_CUDA(c, cudaMemsetAsync(Y, 0, sizeof(float) * c->J * c->n[k], c->stream));  // empty groups stay 0
+  TT_CUDA(c, cudaFuncSetAttribute(k_unfold_gather<DT, VB, S, MODE0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 1;
+  TT_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_unfold_gather<DT, VB, S, MODE0>, THREADS, smem));
+  const int items = a.ncol * a.nseg;
+  const int blocks = std::max(1, std::min(items, sms * std::max(1, per_sm)));
+  k_unfold_gather<DT, VB, S, MODE0><<<blocks, THREADS, smem, c->stream>>>(a);
   TT_LAUNCH(c, "k_unfold_gather");
   return TT_OK;
 }
@@ -391,9 +412,9 @@ static int launch_gather(tt_ctx* c, const void* A, const float* scales, int k, f
   switch (vb) {
     case 16: return launch_gather_vb<DT, 16, MODE0>(c, A, scales, k, Y);
     case 8: return launch_gather_vb<DT, (EB <= 8 ? 8 : 16), MODE0>(c, A, scales, k, Y);
-    case 4: return launch_gather_vb<DT, (EB <= 4 ? 4 : EB), MODE0>(c, A, scales, k, Y);
-    case 2: return launch_gather_vb<DT, (EB <= 2 ? 2 : EB), MODE0>(c, A, scales, k, Y);
-    default: return launch_gather_vb<DT, EB, MODE0>(c, A, scales, k, Y);
+    case 4: return launch_gather_vb<DT, (EB <= 4 ? 4 : 16), MODE0>(c, A, scales, k, Y);
+    case 2: return launch_gather_vb<DT, (EB <= 2 ? 2 : 16), MODE0>(c, A, scales, k, Y);
+    default: return launch_gather_vb<DT, (EB <= 1 ? 1 : 16), MODE0>(c, A, scales, k, Y);
   }
 }
 
