@@ -74,67 +74,120 @@ int tt_ensure_tables(tt_ctx* c, uint64_t sweep) {
 struct RPlanArgs {
   int64_t n[TT_MAX_D];
   int64_t stride[TT_MAX_D];
+  int64_t fstride[TT_MAX_D];  // stride[s] / n[0]: mode-0 fibres per step of mode s (s >= 1)
   int64_t noff[TT_MAX_D + 1];
   int d, k, J;
   int64_t R;
 };
 
-__device__ __forceinline__ void rplan_entry(const RPlanArgs& a, const int32_t* __restrict__ h,
-                                            const int8_t* __restrict__ v, int64_t r, int* key, int* neg,
-                                            int64_t* off) {
-  int b = 0, sg = 0;
-  int64_t o = 0, rem = r;
-  for (int s = 1; s < a.d; ++s) {
-    if (s == a.k) continue;
-    int64_t i = rem % a.n[s];
-    rem /= a.n[s];
-    b += h[a.noff[s] + i];
-    sg ^= (v[a.noff[s] + i] < 0);
-    o += i * a.stride[s];
+// Mixed-radix counter over the rest modes of a plan (lowest mode fastest). A thread decomposes
+// its first fibre index and its stride once (divisions), then advances with digit additions and
+// carries only; hash, sign and offset are updated incrementally from per-digit table lookups.
+struct RestWalker {
+  int dig[TT_MAX_D];    // current digits, one per rest mode
+  int sdig[TT_MAX_D];   // digits of the stride
+  int nm;               // number of rest modes
+  int md[TT_MAX_D];     // mode of each digit
+  __device__ void init(const RPlanArgs& a, int64_t r, int64_t stride) {
+    nm = 0;
+    for (int s = 1; s < a.d; ++s)
+      if (s != a.k) md[nm++] = s;
+    int64_t rem = r, st = stride;
+    for (int q = 0; q < nm; ++q) {
+      const int64_t n = a.n[md[q]];
+      dig[q] = (int)(rem % n);
+      rem /= n;
+      sdig[q] = (int)(st % n);
+      st /= n;
+    }
   }
-  *key = b & (a.J - 1);
-  *neg = sg;
-  *off = o;
-}
+  __device__ void advance(const RPlanArgs& a) {
+    int carry = 0;
+    for (int q = 0; q < nm; ++q) {
+      const int n = (int)a.n[md[q]];
+      int x = dig[q] + sdig[q] + carry;
+      carry = 0;
+      while (x >= n) {
+        x -= n;
+        ++carry;
+      }
+      dig[q] = x;
+    }
+  }
+  __device__ void entry(const RPlanArgs& a, const int32_t* __restrict__ h, const int8_t* __restrict__ v,
+                        int* key, int* neg, int64_t* off) const {
+    int b = 0, sg = 0;
+    int64_t o = 0;
+    for (int q = 0; q < nm; ++q) {
+      const int s = md[q], i = dig[q];
+      b += h[a.noff[s] + i];
+      sg ^= (v[a.noff[s] + i] < 0);
+      o += (int64_t)i * a.fstride[s];
+    }
+    *key = b & (a.J - 1);
+    *neg = sg;
+    *off = o;  // mode-0 fibre index at i_k = 0
+  }
+};
 
+// Counting with a per-block shared-memory histogram (one global atomic per non-empty bucket and
+// block); fibres r of block b are the contiguous range [b*PB, (b+1)*PB).
+#define TT_PLAN_BLOCK 8192
 __global__ void k_rplan_count(RPlanArgs a, const int32_t* h, const int8_t* v, int32_t* count) {
-  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < a.R; r += (int64_t)gridDim.x * blockDim.x) {
+  extern __shared__ int hist[];
+  for (int i = threadIdx.x; i < a.J; i += blockDim.x) hist[i] = 0;
+  __syncthreads();
+  const int64_t r0 = (int64_t)blockIdx.x * TT_PLAN_BLOCK, r1 = min(a.R, r0 + TT_PLAN_BLOCK);
+  RestWalker wk;
+  wk.init(a, r0 + threadIdx.x, blockDim.x);
+  for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x, wk.advance(a)) {
     int key, neg;
     int64_t off;
-    rplan_entry(a, h, v, r, &key, &neg, &off);
-    atomicAdd(&count[key], 1);
+    wk.entry(a, h, v, &key, &neg, &off);
+    atomicAdd(&hist[key], 1);
   }
+  __syncthreads();
+  for (int i = threadIdx.x; i < a.J; i += blockDim.x)
+    if (hist[i]) atomicAdd(&count[i], hist[i]);
 }
 
-// exclusive scans of the counts and of the non-empty flags (one block of 1024 threads)
+// exclusive scans of the counts and of the non-empty flags (one block of 1024 threads,
+// warp-shuffle scans)
+__device__ __forceinline__ int64_t warp_incl_scan(int64_t x) {
+  const int lane = threadIdx.x & 31;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  return x;
+}
 __global__ void k_rplan_scan(int J, int64_t R, int32_t* count, int64_t* off, int32_t* ulist, int64_t* ustart,
                              int32_t* ucount) {
-  __shared__ int64_t part[1024];
-  __shared__ int upart[1024];
-  const int t = threadIdx.x;
+  __shared__ int64_t wsum[32], wun[32];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int per = (J + 1023) / 1024;
   const int lo = min(J, t * per), hi = min(J, (t + 1) * per);
-  int64_t s = 0;
-  int u = 0;
+  int64_t s = 0, u = 0;
   for (int i = lo; i < hi; ++i) {
     s += count[i];
     u += count[i] > 0;
   }
-  part[t] = s;
-  upart[t] = u;
-  __syncthreads();
-  for (int o = 1; o < 1024; o <<= 1) {
-    int64_t x = (t >= o) ? part[t - o] : 0;
-    int y = (t >= o) ? upart[t - o] : 0;
-    __syncthreads();
-    part[t] += x;
-    upart[t] += y;
-    __syncthreads();
+  const int64_t si = warp_incl_scan(s), ui = warp_incl_scan(u);
+  if (lane == 31) {
+    wsum[warp] = si;
+    wun[warp] = ui;
   }
-  int64_t base = part[t] - s;
-  int ub = upart[t] - u;
+  __syncthreads();
+  if (warp == 0) {
+    const int64_t a1 = warp_incl_scan(wsum[lane]), a2 = warp_incl_scan(wun[lane]);
+    wsum[lane] = a1;
+    wun[lane] = a2;
+  }
+  __syncthreads();
+  int64_t base = (warp ? wsum[warp - 1] : 0) + si - s;
+  int ub = (int)((warp ? wun[warp - 1] : 0) + ui - u);
   for (int i = lo; i < hi; ++i) {
-    int ci = count[i];
+    const int ci = count[i];
     off[i] = base;
     if (ci > 0) {
       ulist[ub] = i;
@@ -145,20 +198,39 @@ __global__ void k_rplan_scan(int J, int64_t R, int32_t* count, int64_t* off, int
     count[i] = 0;  // becomes the scatter cursor
   }
   if (t == 1023) {
-    off[J] = part[1023];
-    ustart[upart[1023]] = part[1023];
-    *ucount = upart[1023];
+    off[J] = wsum[31];
+    ustart[wun[31]] = wsum[31];
+    *ucount = (int32_t)wun[31];
   }
 }
 
+// Scatter: each block reserves, per non-empty bucket, a range of the bucket's slots with one
+// global atomic, then places its fibres with shared-memory cursors.
 __global__ void k_rplan_scatter(RPlanArgs a, const int32_t* h, const int8_t* v, const int64_t* off,
                                 int32_t* cursor, uint32_t* plan) {
-  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < a.R; r += (int64_t)gridDim.x * blockDim.x) {
+  extern __shared__ int hist[];
+  for (int i = threadIdx.x; i < a.J; i += blockDim.x) hist[i] = 0;
+  __syncthreads();
+  const int64_t r0 = (int64_t)blockIdx.x * TT_PLAN_BLOCK, r1 = min(a.R, r0 + TT_PLAN_BLOCK);
+  RestWalker wk;
+  wk.init(a, r0 + threadIdx.x, blockDim.x);
+  for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x, wk.advance(a)) {
     int key, neg;
     int64_t o;
-    rplan_entry(a, h, v, r, &key, &neg, &o);
-    int pos = atomicAdd(&cursor[key], 1);
-    plan[off[key] + pos] = (uint32_t)(o / a.n[0]) | ((uint32_t)neg << 31);  // fibre index | sign
+    wk.entry(a, h, v, &key, &neg, &o);
+    atomicAdd(&hist[key], 1);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < a.J; i += blockDim.x)
+    if (hist[i]) hist[i] = atomicAdd(&cursor[i], hist[i]);  // start of this block's slots
+  __syncthreads();
+  wk.init(a, r0 + threadIdx.x, blockDim.x);
+  for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x, wk.advance(a)) {
+    int key, neg;
+    int64_t o;
+    wk.entry(a, h, v, &key, &neg, &o);
+    const int pos = atomicAdd(&hist[key], 1);
+    plan[off[key] + pos] = (uint32_t)o | ((uint32_t)neg << 31);  // fibre index | sign
   }
 }
 
@@ -168,6 +240,7 @@ int tt_ensure_rplan(tt_ctx* c, int k) {
   for (int s = 0; s < c->d; ++s) {
     a.n[s] = c->n[s];
     a.stride[s] = c->stride[s];
+    a.fstride[s] = c->stride[s] / c->n[0];
   }
   for (int s = 0; s <= c->d; ++s) a.noff[s] = c->noff[s];
   a.d = c->d;
@@ -176,12 +249,17 @@ int tt_ensure_rplan(tt_ctx* c, int k) {
   a.R = c->R[k];
   int32_t* count = c->d_plan0_cursor;
   TT_CUDA(c, cudaMemsetAsync(count, 0, sizeof(int32_t) * c->J, c->stream));
-  int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((a.R + 255) / 256, 152 * 16));
-  k_rplan_count<<<blocks, 256, 0, c->stream>>>(a, c->d_h, c->d_v, count);
+  const int blocks = (int)std::max<int64_t>(1, (a.R + TT_PLAN_BLOCK - 1) / TT_PLAN_BLOCK);
+  const size_t hsm = sizeof(int) * c->J;
+  if (hsm > 48 * 1024) {
+    TT_CUDA(c, cudaFuncSetAttribute(k_rplan_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm));
+    TT_CUDA(c, cudaFuncSetAttribute(k_rplan_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm));
+  }
+  k_rplan_count<<<blocks, 512, hsm, c->stream>>>(a, c->d_h, c->d_v, count);
   TT_LAUNCH(c, "k_rplan_count");
   k_rplan_scan<<<1, 1024, 0, c->stream>>>(c->J, a.R, count, c->d_rtmp, c->d_ulist[k], c->d_ustart[k], c->d_ucount[k]);
   TT_LAUNCH(c, "k_rplan_scan");
-  k_rplan_scatter<<<blocks, 256, 0, c->stream>>>(a, c->d_h, c->d_v, c->d_rtmp, count, c->d_rplan[k]);
+  k_rplan_scatter<<<blocks, 512, hsm, c->stream>>>(a, c->d_h, c->d_v, c->d_rtmp, count, c->d_rplan[k]);
   TT_LAUNCH(c, "k_rplan_scatter");
   c->rplan_valid[k] = true;
   return TT_OK;

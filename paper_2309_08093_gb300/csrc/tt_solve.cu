@@ -413,23 +413,30 @@ __device__ bool block_cholqr2(float* A, int m, int q, int lda, float* Rm, float*
   const int t = threadIdx.x, T = blockDim.x;
   const int lane = t & 31, warp = t >> 5;
   const int pairs = q * q;
-  const int G = max(1, min(32, T / max(1, pairs)));
+  const int tri = q * (q + 1) / 2;  // lower-triangle pairs (i >= j), p = i (i + 1) / 2 + j
+  const int G = max(1, min(32, T / max(1, tri)));
   for (int pass = 0; pass < 2; ++pass) {
-    // W = A^T A, partial sums over row groups
-    for (int idx = t; idx < pairs * G; idx += T) {
-      const int pr = idx % pairs, g = idx / pairs;
-      const int i = pr / q, j = pr - i * q;
+    // W = A^T A on the lower triangle, partial sums over G row groups
+    for (int idx = t; idx < tri * G; idx += T) {
+      const int p = idx % tri, g = idx / tri;
+      int i = (int)((sqrtf(8.f * p + 1.f) - 1.f) * 0.5f);
+      while (i * (i + 1) / 2 > p) --i;
+      while ((i + 1) * (i + 2) / 2 <= p) ++i;
+      const int j = p - i * (i + 1) / 2;
       float acc = 0.f;
-      if (j <= i)
-        for (int r = g; r < m; r += G) acc = fmaf(A[r + lda * i], A[r + lda * j], acc);
+      for (int r = g; r < m; r += G) acc = fmaf(A[r + lda * i], A[r + lda * j], acc);
       W[idx] = acc;
     }
     __syncthreads();
     if (warp == 0) {
       // reduce the groups, then Cholesky W = L L^T (lower, row-major in Rp); R = L^T
       for (int pr = lane; pr < pairs; pr += 32) {
+        const int i = pr / q, j = pr - i * q;
         float acc = 0.f;
-        for (int g = 0; g < G; ++g) acc += W[pr + pairs * g];
+        if (j <= i) {
+          const int p = i * (i + 1) / 2 + j;
+          for (int g = 0; g < G; ++g) acc += W[p + tri * g];
+        }
         Rp[pr] = acc;
       }
       __syncwarp();
@@ -534,16 +541,23 @@ __global__ void __launch_bounds__(512) k_qr_left(float* core, float* next, int r
     for (int idx = threadIdx.x; idx < m * q; idx += blockDim.x) core[idx] = (idx / m < p) ? L.A[idx] : 0.f;
   }
   __syncthreads();
-  // next^R is r1 x ncols_next column-major: column c holds r1 contiguous entries
-  for (int cidx = threadIdx.x; cidx < ncols_next; cidx += blockDim.x) {
-    float col[TT_MAX_S];
-    float* g = next + (int64_t)cidx * r1;
-    for (int b = 0; b < r1; ++b) col[b] = g[b];
-    for (int a2 = 0; a2 < r1; ++a2) {
+  // G_{k+1}^R <- R G_{k+1}^R (r1 x ncols_next, column-major), staged through the free A region
+  // in pieces that fit it
+  const int64_t cap = (int64_t)L.lda * q;  // floats available in A
+  const int cols_per = (int)(cap / r1 > 1 ? cap / r1 : 1);
+  for (int c0 = 0; c0 < ncols_next; c0 += cols_per) {
+    const int nc = min(cols_per, ncols_next - c0);
+    float* g = next + (int64_t)c0 * r1;
+    for (int idx = threadIdx.x; idx < nc * r1; idx += blockDim.x) L.A[idx] = g[idx];
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nc * r1; idx += blockDim.x) {
+      const int cc = idx / r1, a2 = idx - cc * r1;
+      const float* col = L.A + (size_t)cc * r1;
       float acc = 0.f;
       for (int b = a2; b < r1; ++b) acc = fmaf(L.Rm[a2 * q + b], col[b], acc);
-      g[a2] = acc;
+      g[idx] = acc;
     }
+    __syncthreads();
   }
 }
 
@@ -584,15 +598,23 @@ __global__ void __launch_bounds__(512) k_lq_right(float* prev, float* core, int 
     }
   }
   __syncthreads();
-  // prev^L is nrows_prev x r0 column-major; row t: prev[t + nrows_prev * a]
-  for (int t = threadIdx.x; t < nrows_prev; t += blockDim.x) {
-    float row[TT_MAX_S];
-    for (int a2 = 0; a2 < r0; ++a2) row[a2] = prev[t + (int64_t)nrows_prev * a2];
-    for (int b = 0; b < r0; ++b) {
-      float acc = 0.f;
-      for (int a2 = b; a2 < r0; ++a2) acc = fmaf(row[a2], L.Rm[b * q + a2], acc);  // (G R^T)[t, b]
-      prev[t + (int64_t)nrows_prev * b] = acc;
+  // G_{k-1}^L <- G_{k-1}^L R^T (nrows_prev x r0, column-major), staged through the free A region
+  const int64_t cap = (int64_t)L.lda * q;
+  const int rows_per = (int)(cap / r0 > 1 ? cap / r0 : 1);
+  for (int t0 = 0; t0 < nrows_prev; t0 += rows_per) {
+    const int nr = min(rows_per, nrows_prev - t0);
+    for (int idx = threadIdx.x; idx < nr * r0; idx += blockDim.x) {
+      const int a2 = idx / nr, tt = idx - a2 * nr;
+      L.A[idx] = prev[t0 + tt + (int64_t)nrows_prev * a2];  // A[a2 * nr + tt]
     }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nr * r0; idx += blockDim.x) {
+      const int b = idx / nr, tt = idx - b * nr;
+      float acc = 0.f;
+      for (int a2 = b; a2 < r0; ++a2) acc = fmaf(L.A[a2 * nr + tt], L.Rm[b * q + a2], acc);  // (G R^T)[t, b]
+      prev[t0 + tt + (int64_t)nrows_prev * b] = acc;
+    }
+    __syncthreads();
   }
 }
 
@@ -658,6 +680,32 @@ __device__ __forceinline__ float err_elem(const void* A, int64_t idx) {
   return 0.f;
 }
 
+// four consecutive entries starting at a multiple of 4 (vector load in the storage type)
+template <int DT>
+__device__ __forceinline__ void err_load4(const void* A, int64_t idx, float* x) {
+  if constexpr (DT == TT_F32) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(A) + idx / 4);
+    x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+  } else if constexpr (DT == TT_F64) {
+    const double2 v0 = __ldg(reinterpret_cast<const double2*>(A) + idx / 2);
+    const double2 v1 = __ldg(reinterpret_cast<const double2*>(A) + idx / 2 + 1);
+    x[0] = (float)v0.x; x[1] = (float)v0.y; x[2] = (float)v1.x; x[3] = (float)v1.y;
+  } else if constexpr (DT == TT_BF16) {
+    const uint2 v = __ldg(reinterpret_cast<const uint2*>(A) + idx / 4);
+    x[0] = __uint_as_float(v.x << 16); x[1] = __uint_as_float(v.x & 0xFFFF0000u);
+    x[2] = __uint_as_float(v.y << 16); x[3] = __uint_as_float(v.y & 0xFFFF0000u);
+  } else {
+    const uint32_t v = __ldg(reinterpret_cast<const uint32_t*>(A) + idx / 4);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const uint32_t cc = (v >> (8 * c)) & 0xFFu;
+      const uint32_t sg = (cc & 0x80u) << 24, e = (cc >> 3) & 0xFu, mm = cc & 7u;
+      const float mag = e ? __uint_as_float(((e + 120u) << 23) | (mm << 20)) : (float)mm * 0.001953125f;
+      x[c] = __uint_as_float(__float_as_uint(mag) | sg);
+    }
+  }
+}
+
 template <int DT>
 __global__ void __launch_bounds__(256) k_rel_error(ErrArgs a) {
   extern __shared__ float sm[];
@@ -717,32 +765,73 @@ __global__ void __launch_bounds__(256) k_rel_error(ErrArgs a) {
       W[(size_t)al * WP + c] = acc;
     }
     __syncthreads();
-    // tiles of 4 consecutive i1 for one i0: one G0 load and one 16-byte W load per al feed 4 FMAs
+    // tiles of 4 consecutive i0 for one i1 (when n0 % 4 == 0): one vector load of A (issued before
+    // the reconstruction so its latency overlaps the FMAs), one 16-byte G_0 load and one broadcast
+    // W load per rank index feed 4 FMAs. Otherwise tiles of 4 consecutive i1 for one i0.
     const int64_t base = t * (int64_t)n0 * n1 + (int64_t)j0 * n0;
-    const int ngroups = wcols >> 2;
-    const int tiles = ngroups * n0;
     float fe = 0.f, fa = 0.f;
-    for (int q = threadIdx.x; q < tiles; q += blockDim.x) {
-      const int gq = q / n0, i0 = q - gq * n0;
-      float r4[4] = {0.f, 0.f, 0.f, 0.f};
-      const float* wp = W + 4 * gq;
-      for (int al = 0; al < r1; ++al) {
-        const float g = G0[al * n0 + i0];
-        const float4 w4 = *reinterpret_cast<const float4*>(wp + (size_t)al * WP);
-        r4[0] = fmaf(g, w4.x, r4[0]);
-        r4[1] = fmaf(g, w4.y, r4[1]);
-        r4[2] = fmaf(g, w4.z, r4[2]);
-        r4[3] = fmaf(g, w4.w, r4[3]);
-      }
-      const float sc = a.scales ? __ldg(a.scales + i0) : 1.f;
+    if ((n0 & 3) == 0) {
+      const int q4 = n0 >> 2;
+      const int tiles = q4 * (j1 - j0);
+      constexpr int UT = 4;  // tiles per thread in flight
+      for (int qb = threadIdx.x; qb < tiles; qb += UT * blockDim.x) {
+        float x[UT][4];
+        int i1s[UT], i0s[UT];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const int i1 = 4 * gq + c;
-        if (j0 + i1 < j1) {
-          const float x = err_elem<DT>(a.A, base + (int64_t)i1 * n0 + i0) * sc;
-          const float dl = x - r4[c];
-          fe = fmaf(dl, dl, fe);
-          fa = fmaf(x, x, fa);
+        for (int u = 0; u < UT; ++u) {
+          const int q = qb + u * blockDim.x;
+          i1s[u] = q / q4;
+          i0s[u] = (q - i1s[u] * q4) * 4;
+          if (q < tiles)
+            err_load4<DT>(a.A, base + (int64_t)i1s[u] * n0 + i0s[u], x[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < UT; ++u) {
+          if (qb + u * blockDim.x >= tiles) break;
+          const int i1 = i1s[u], i0 = i0s[u];
+          float r4[4] = {0.f, 0.f, 0.f, 0.f};
+          for (int al = 0; al < r1; ++al) {
+            const float4 g4 = *reinterpret_cast<const float4*>(G0 + al * n0 + i0);
+            const float w = W[(size_t)al * WP + i1];
+            r4[0] = fmaf(g4.x, w, r4[0]);
+            r4[1] = fmaf(g4.y, w, r4[1]);
+            r4[2] = fmaf(g4.z, w, r4[2]);
+            r4[3] = fmaf(g4.w, w, r4[3]);
+          }
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const float xv = a.scales ? x[u][c] * __ldg(a.scales + i0 + c) : x[u][c];
+            const float dl = xv - r4[c];
+            fe = fmaf(dl, dl, fe);
+            fa = fmaf(xv, xv, fa);
+          }
+        }
+      }
+    } else {
+      const int ngroups = wcols >> 2;
+      const int tiles = ngroups * n0;
+      for (int q = threadIdx.x; q < tiles; q += blockDim.x) {
+        const int gq = q / n0, i0 = q - gq * n0;
+        float r4[4] = {0.f, 0.f, 0.f, 0.f};
+        const float* wp = W + 4 * gq;
+        for (int al = 0; al < r1; ++al) {
+          const float g = G0[al * n0 + i0];
+          const float4 w4 = *reinterpret_cast<const float4*>(wp + (size_t)al * WP);
+          r4[0] = fmaf(g, w4.x, r4[0]);
+          r4[1] = fmaf(g, w4.y, r4[1]);
+          r4[2] = fmaf(g, w4.z, r4[2]);
+          r4[3] = fmaf(g, w4.w, r4[3]);
+        }
+        const float sc = a.scales ? __ldg(a.scales + i0) : 1.f;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int i1 = 4 * gq + c;
+          if (j0 + i1 < j1) {
+            const float x = err_elem<DT>(a.A, base + (int64_t)i1 * n0 + i0) * sc;
+            const float dl = x - r4[c];
+            fe = fmaf(dl, dl, fe);
+            fa = fmaf(x, x, fa);
+          }
         }
       }
     }
