@@ -40,6 +40,7 @@ def parse():
     ap.add_argument("--storage", default=None, help="override the workload's storage type")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-patterns", action="store_true", help="skip the BF16-form comparison")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--cpu-columns", type=int, default=0, help=argparse.SUPPRESS)
     return ap.parse_args()
@@ -204,6 +205,50 @@ def workload_config(w, storage):
 
 
 # ---------------------------------------------------------------------------------------------
+# precision pattern: the same workload with the tensor stored in BF16 (FP32 sketch accumulation,
+# FP32 Gram, FP32 factorisation), compared with the plain FP32 form at equal relative error
+
+def precision_pattern(w, p, dev, nsweeps):
+    import numpy as np
+    import torch
+    from paper_2309_08093_gb300 import lib, synth
+
+    stream = torch.cuda.current_stream()
+    A32 = lib.device_tensor(p.storage, "f32", device=dev)
+    ctx32 = lib.Context(w.dims, p.ranks, w.J, w.lam, p.sketch_seed, "f32")
+    forms = {"f32": (ctx32, A32)}
+    bits = synth.bf16_bits(np.asarray(p.storage, dtype=np.float32))
+    ctx16 = lib.Context(w.dims, p.ranks, w.J, w.lam, p.sketch_seed, "bf16")
+    forms["bf16"] = (ctx16, lib.device_tensor(bits, "bf16", device=dev))
+    out = {}
+    for name, (ctx, A) in forms.items():
+        cores = lib.device_cores(p.init_cores, device=dev)
+        errs, ms = [], 0.0
+        for t in range(nsweeps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.tt_prox_als_sweep(A, cores, 1, t, rel_change=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+            errs.append(ctx32.tt_rel_error(A32, cores))  # always against the FP32 tensor
+        out[name] = {"sweeps_per_s": nsweeps / (ms / 1e3), "rel_error_per_sweep": errs}
+    target = out["f32"]["rel_error_per_sweep"][-1] * (1 + 1e-3)
+    for name, r in out.items():
+        hit = next((i + 1 for i, e in enumerate(r["rel_error_per_sweep"]) if e <= target), None)
+        r["sweeps_to_tolerance"] = hit
+        r["sweeps_to_tolerance_per_s"] = (r["sweeps_per_s"] / hit) if hit else None
+        r["rel_error_final"] = r["rel_error_per_sweep"][-1]
+        r["rel_error_per_sweep"] = [round(e, 8) for e in r["rel_error_per_sweep"]]
+    for ctx, _ in forms.values():
+        ctx.close()
+    return {"tolerance": target, "sweeps": nsweeps,
+            "note": "sweeps timed with CUDA events (no relative error inside the timed sweeps); errors "
+                    "against the FP32 tensor; tolerance = FP32 form's final error x (1 + 1e-3)",
+            "forms": out}
+
+
+# ---------------------------------------------------------------------------------------------
 # GPU arm
 
 def main():
@@ -322,6 +367,8 @@ def main():
                        "note": "tt_prox_als_sweep_host: H2D copy of the tensor and cores, one sweep, the relative "
                                "error, D2H of the cores, rel-change and rel error; synchronised; wall clock"}
     ctx.close()
+    if rank == 0 and world == 1 and not args.no_patterns and storage == "f32":
+        line["patterns"] = {"precision": precision_pattern(w, p, dev, w.sweeps)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
             res = run_cpu_child(["--workload", args.workload] + (["--storage", args.storage] if args.storage else []))
