@@ -200,6 +200,29 @@ int tt_prox_als_sweep_host(tt_ctx* ctx, const void* A_host, const float* scales_
 int tt_prox_update_noalloc(const float* Y_dev, const float* SH_dev, float* core_dev, int J, int n,
                            int r0, int r1, double sigma, void* cuda_stream);
 
+/*
+ * Batched driver (the batching pattern: many tensors of different order, size, rank and sketch
+ * size swept together). tt_batch_init creates one context per tt_params entry (all validated as
+ * in tt_sketch_init) and a pool of streams. tt_batch_sweep runs `nsweeps` outer iterations of
+ * Algorithm 1 on every tensor i: A_dev[i] (storage of params[i]), scales_dev[i] (FP8 only; the
+ * array itself may be NULL when no tensor is FP8), cores_dev[i] (host array of params[i].d device
+ * core pointers, updated in place). One sweep of all tensors is captured once into a CUDA graph
+ * (tensors spread over the stream pool, forked from and joined to `cuda_stream`) and replayed
+ * with one graph launch per sweep; the graph is recaptured when any pointer changes. The first
+ * call also autotunes the unfold kernel of every tensor on its own data. Sweep t of the call uses
+ * hash draw first_sweep + t (or 0 with TT_FLAG_FIXED_SKETCH). Synchronises `cuda_stream`;
+ * returns TT_ENOTSPD etc. for the first tensor whose solve failed (tt_batch_last_error).
+ */
+typedef struct tt_batch tt_batch;
+int tt_batch_init(tt_batch** out, int count, const tt_params* params, void* cuda_stream);
+void tt_batch_destroy(tt_batch* b);
+const char* tt_batch_last_error(const tt_batch* b);
+int tt_batch_sweep(tt_batch* b, const void* const* A_dev, const float* const* scales_dev,
+                   float* const* const* cores_dev, int nsweeps, uint64_t first_sweep);
+/* Relative error of every tensor (as tt_rel_error) into out[count]; synchronises. */
+int tt_batch_rel_error(tt_batch* b, const void* const* A_dev, const float* const* scales_dev,
+                       float* const* const* cores_dev, double* out);
+
 /* Per-context counters for measurement (not part of the method). */
 typedef struct {
   double unfold_ms;          /* summed device time of the unfold-sketch kernels (CUDA events) */

@@ -103,7 +103,7 @@ extern "C" int tt_orthogonalize(tt_ctx* c, float* const* cores, int direction, i
 }
 
 // One outer iteration of Algorithm 1; change slots receive ||dG_k||^2, ||G_k||^2 per core.
-static int one_sweep(tt_ctx* c, const void* A, const float* scales, float* const* cores, uint64_t sweep,
+int tt_one_sweep(tt_ctx* c, const void* A, const float* scales, float* const* cores, uint64_t sweep,
                      double* change_slots) {
   const int d = c->d;
   for (int kk = d - 1; kk >= 1; --kk) TT_TRY(tt_launch_lq_right(c, cores[kk - 1], cores[kk], kk));
@@ -138,7 +138,7 @@ extern "C" int tt_prox_als_sweep(tt_ctx* c, const void* A, const float* scales, 
     const int nt = std::min(per_block, nsweeps - t0);
     for (int t = 0; t < nt; ++t) {
       double* slots = rel_change_out ? c->d_changes + (size_t)2 * c->d * t : nullptr;
-      TT_TRY(one_sweep(c, A, scales, cores, first_sweep + t0 + t, slots));
+      TT_TRY(tt_one_sweep(c, A, scales, cores, first_sweep + t0 + t, slots));
     }
     if (rel_change_out) {
       host.resize((size_t)2 * c->d * nt);

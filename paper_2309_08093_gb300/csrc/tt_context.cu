@@ -46,8 +46,31 @@ __global__ void k_gen_tables(uint64_t seed, uint64_t sweep, TabArgs a, int J, in
   v[g] = (wv >> 63) ? (int8_t)-1 : (int8_t)1;
 }
 
+__global__ void k_gen_tables_dev(uint64_t seed, const uint64_t* sweep_ptr, int fixed, TabArgs a, int J,
+                                 int32_t* h, int8_t* v) {
+  int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= a.noff[a.d]) return;
+  const uint64_t sweep = fixed ? 0ull : *sweep_ptr;
+  int k = 0;
+  while (g >= a.noff[k + 1]) ++k;
+  uint64_t i = (uint64_t)(g - a.noff[k]);
+  h[g] = (int32_t)(tt_word(seed, sweep, (uint64_t)k, 0ull, i) & (uint64_t)(J - 1));
+  v[g] = (tt_word(seed, sweep, (uint64_t)k, 1ull, i) >> 63) ? (int8_t)-1 : (int8_t)1;
+}
+
 int tt_ensure_tables(tt_ctx* c, uint64_t sweep) {
   if (c->user_tables) return TT_OK;
+  if (c->capture_mode) {  // sweep index read on the device at replay time
+    TabArgs a;
+    for (int k = 0; k <= c->d; ++k) a.noff[k] = c->noff[k];
+    a.d = c->d;
+    const int64_t total = c->noff[c->d];
+    k_gen_tables_dev<<<(int)((total + 255) / 256), 256, 0, c->stream>>>(
+        c->seed, c->d_sweep_ptr, (c->flags & TT_FLAG_FIXED_SKETCH) ? 1 : 0, a, c->J, c->d_h, c->d_v);
+    TT_LAUNCH(c, "k_gen_tables_dev");
+    for (int k = 0; k < TT_MAX_D; ++k) c->rplan_valid[k] = false;
+    return TT_OK;
+  }
   if (c->flags & TT_FLAG_FIXED_SKETCH) sweep = 0;
   if (c->tables_valid && c->tables_sweep == sweep) return TT_OK;
   TabArgs a;
@@ -235,7 +258,8 @@ __global__ void k_rplan_scatter(RPlanArgs a, const int32_t* h, const int8_t* v, 
 }
 
 int tt_ensure_rplan(tt_ctx* c, int k) {
-  if (c->rplan_valid[k]) return TT_OK;
+  if (c->rplan_valid[k] && !(c->capture_mode && !(c->flags & TT_FLAG_FIXED_SKETCH) && !c->user_tables))
+    return TT_OK;
   RPlanArgs a;
   for (int s = 0; s < c->d; ++s) {
     a.n[s] = c->n[s];

@@ -89,6 +89,15 @@ struct tt_ctx {
   int ev_used = 0;            // events in use
   int64_t prof_bytes = 0;
 
+  // graph-capture mode (batched driver): tables are drawn from the device sweep counter
+  // *d_sweep_ptr and the plans are rebuilt every sweep, with no host-side state checks.
+  bool capture_mode = false;
+  const uint64_t* d_sweep_ptr = nullptr;
+
+  // autotuned parameters of the unfold kernel per mode (0 = default)
+  int tune_seg_mult[TT_MAX_D] = {0};   // multiplier of the work-item count
+  int tune_cta_per_sm[TT_MAX_D] = {0}; // CTAs per SM (1 or 2)
+
   // host-buffer entry point staging (allocated on first use)
   void* d_A_stage = nullptr;
   float* d_scales_stage = nullptr;
@@ -145,6 +154,8 @@ int tt_launch_qr_left(tt_ctx* c, float* core_k, float* core_k1, int k);
 int tt_launch_lq_right(tt_ctx* c, float* core_km1, float* core_k, int k);
 int tt_launch_rel_error(tt_ctx* c, const void* A, const float* scales, float* const* cores);
 int tt_read_status(tt_ctx* c);
+int tt_one_sweep(tt_ctx* c, const void* A, const float* scales, float* const* cores, uint64_t sweep,
+                 double* change_slots);
 int tt_prof_begin(tt_ctx* c, int k);   // record a start event when profiling (returns TT_OK)
 int tt_prof_end(tt_ctx* c);
 int tt_elem_bytes(int dtype);

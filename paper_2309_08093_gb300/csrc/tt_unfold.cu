@@ -386,8 +386,10 @@ static int launch_gather_vb(tt_ctx* c, const void* A, const float* scales, int k
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
   // work items (column, c-segment): at most one per CTA slot (two CTAs per SM) when the columns
   // allow it, so that every CTA gets the same amount of work; segments of at most 2048 c groups
-  const int slots = 2 * sms;
+  const int cps = c->tune_cta_per_sm[k] ? c->tune_cta_per_sm[k] : 2;
+  const int slots = cps * sms;
   int nseg = std::max(1, slots / a.ncol);
+  if (c->tune_seg_mult[k]) nseg *= c->tune_seg_mult[k];
   nseg = std::max(nseg, (c->J + 2047) / 2048);
   a.nseg = nseg;
   a.segmax = (c->J + nseg - 1) / nseg + 1;
@@ -399,7 +401,7 @@ static int launch_gather_vb(tt_ctx* c, const void* A, const float* scales, int k
   int per_sm = 1;
   TT_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_unfold_gather<DT, VB, S, MODE0>, THREADS, smem));
   const int items = a.ncol * a.nseg;
-  const int blocks = std::max(1, std::min(items, sms * std::max(1, per_sm)));
+  const int blocks = std::max(1, std::min(items, sms * std::max(1, std::min(per_sm, cps))));
   k_unfold_gather<DT, VB, S, MODE0><<<blocks, THREADS, smem, c->stream>>>(a);
   TT_LAUNCH(c, "k_unfold_gather");
   return TT_OK;

@@ -23,7 +23,8 @@ TT_FLAG_FIXED_SKETCH = 1
 EXPORTS = ["tt_sketch_init", "tt_sketch_destroy", "tt_last_error", "tt_sketch_tables",
            "tt_sketch_set_tables", "tt_sketch_unfold", "tt_sketch_interface", "tt_prox_update",
            "tt_orthogonalize", "tt_prox_als_sweep", "tt_rel_error", "tt_prox_als_sweep_host",
-           "tt_profile_enable", "tt_profile_read", "tt_prox_update_noalloc"]
+           "tt_profile_enable", "tt_profile_read", "tt_prox_update_noalloc", "tt_batch_init",
+           "tt_batch_destroy", "tt_batch_last_error", "tt_batch_sweep", "tt_batch_rel_error"]
 
 
 class TtError(RuntimeError):
@@ -75,9 +76,17 @@ def load(path: str = LIB_PATH):
     L.tt_prox_update_noalloc.argtypes = [vp, vp, vp, i, i, i, i, ctypes.c_double, vp]
     L.tt_profile_enable.argtypes = [vp, i]
     L.tt_profile_read.argtypes = [vp, ctypes.POINTER(TtProfile)]
+    L.tt_batch_init.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(TtParams), vp]
+    L.tt_batch_destroy.argtypes = [vp]
+    L.tt_batch_destroy.restype = None
+    L.tt_batch_last_error.argtypes = [vp]
+    L.tt_batch_last_error.restype = ctypes.c_char_p
+    L.tt_batch_sweep.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), i, u64]
+    L.tt_batch_rel_error.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                     ctypes.POINTER(ctypes.c_double)]
     for name in EXPORTS:
         f = getattr(L, name)
-        if name not in ("tt_sketch_destroy", "tt_last_error"):
+        if name not in ("tt_sketch_destroy", "tt_last_error", "tt_batch_destroy", "tt_batch_last_error"):
             f.restype = ctypes.c_int
     _lib = L
     return L
@@ -207,6 +216,64 @@ def tt_prox_update_noalloc(Y, SH, core, J: int, n: int, r0: int, r1: int, sigma:
     stream = _current_stream() if stream is None else stream
     return L.tt_prox_update_noalloc(_ptr(Y), _ptr(SH), _ptr(core), int(J), int(n), int(r0), int(r1),
                                     float(sigma), stream)
+
+
+class Batch:
+    """Owns one tt_batch: many tensors, each given as a dict(dims, ranks, J, lam, seed, dtype)."""
+
+    def __init__(self, specs: Sequence[dict], stream=None):
+        self.lib = load()
+        self.specs = list(specs)
+        self.count = len(self.specs)
+        self._keep = []
+        params = (TtParams * self.count)()
+        for i, sp in enumerate(self.specs):
+            d = len(sp["dims"])
+            n = (ctypes.c_int64 * d)(*[int(x) for x in sp["dims"]])
+            r = (ctypes.c_int * (d + 1))(*[int(x) for x in sp["ranks"]])
+            self._keep += [n, r]
+            params[i] = TtParams(d, n, r, int(sp["J"]), float(sp["lam"]), int(sp["seed"]) & (2**64 - 1),
+                                 DTYPES[sp.get("dtype", "f32")], int(sp.get("flags", 0)))
+        self._params = params
+        self.b = ctypes.c_void_p()
+        stream = _current_stream() if stream is None else stream
+        rc = self.lib.tt_batch_init(ctypes.byref(self.b), self.count, params, stream)
+        if rc != TT_OK:
+            raise TtError(rc, "tt_batch_init failed (see stderr)")
+
+    def close(self):
+        if self.b:
+            self.lib.tt_batch_destroy(self.b)
+            self.b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _arrays(self, A_list, cores_list, scales_list):
+        A = _ptr_array(A_list)
+        S = _ptr_array(scales_list) if scales_list is not None else None
+        inner = [_ptr_array(c) for c in cores_list]
+        C = (ctypes.c_void_p * self.count)()
+        for i, arr in enumerate(inner):
+            C[i] = ctypes.cast(arr, ctypes.c_void_p)
+        return A, S, C, inner
+
+    def tt_batch_sweep(self, A_list, cores_list, nsweeps: int, first_sweep: int = 0, scales_list=None):
+        A, S, C, inner = self._arrays(A_list, cores_list, scales_list)
+        rc = self.lib.tt_batch_sweep(self.b, A, S, C, int(nsweeps), int(first_sweep))
+        if rc != TT_OK:
+            raise TtError(rc, self.lib.tt_batch_last_error(self.b).decode())
+
+    def tt_batch_rel_error(self, A_list, cores_list, scales_list=None):
+        A, S, C, inner = self._arrays(A_list, cores_list, scales_list)
+        out = (ctypes.c_double * self.count)()
+        rc = self.lib.tt_batch_rel_error(self.b, A, S, C, out)
+        if rc != TT_OK:
+            raise TtError(rc, self.lib.tt_batch_last_error(self.b).decode())
+        return list(out)
 
 
 # ---------------------------------------------------------------------------------------------

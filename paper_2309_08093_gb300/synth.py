@@ -253,3 +253,65 @@ def random_tensor(dims: Sequence[int], seed: int) -> np.ndarray:
 
 def random_tt(dims: Sequence[int], ranks: Sequence[int], seed: int, kind: str = "normal"):
     return random_cores(dims, ranks, np.random.default_rng([seed, STREAM_CORES]), kind)
+
+
+# ---------------------------------------------------------------------------------------------
+# batched workload: 256 tensors of order 3-4, mode sizes in [16, 128], TT ranks in [4, 12],
+# 1e-3 relative noise, J = next power of two >= 8 max_k r_{k-1} r_k; storage alternates FP32 / BF16
+
+def batched_specs(count: int = 256, seed: int = 20230919, dims_range=(16, 128), rank_range=(4, 12),
+                  storages=("f32", "bf16")):
+    """Shapes, ranks and sketch sizes of the batched workload (numpy RNG, fully determined by seed)."""
+    rng = np.random.default_rng([seed, 5])
+    specs = []
+    for i in range(count):
+        d = int(rng.integers(3, 5))
+        dims = [int(x) for x in rng.integers(dims_range[0], dims_range[1] + 1, size=d)]
+        ranks = [1] + [int(x) for x in rng.integers(rank_range[0], rank_range[1] + 1, size=d - 1)] + [1]
+        for k in range(1, d):
+            ranks[k] = min(ranks[k], int(np.prod(dims[:k])), int(np.prod(dims[k:])))
+        smax = max(ranks[k] * ranks[k + 1] for k in range(d))
+        J = 1
+        while J < 8 * smax:
+            J *= 2
+        specs.append({"dims": dims, "ranks": ranks, "J": J, "lam": 1e-3, "noise": 1e-3,
+                      "seed": int(rng.integers(0, 2**62)), "dtype": storages[i % len(storages)],
+                      "tensor_seed": int(seed * 1000 + i)})
+    return specs
+
+
+def batched_tensor_cpu(spec):
+    """Noisy tensor of one batched spec on the host (numpy, for small test batches)."""
+    cores = random_tt(spec["dims"], spec["ranks"], spec["tensor_seed"])
+    a = add_noise(contract_cores(cores), spec["noise"], np.random.default_rng([spec["tensor_seed"], STREAM_NOISE]))
+    init = random_cores(spec["dims"], spec["ranks"], np.random.default_rng([spec["tensor_seed"], STREAM_INIT]))
+    return a, init
+
+
+def batched_tensor_gpu(spec, device="cuda"):
+    """The same recipe generated on the device with torch (large batches): seeded numpy cores,
+    TT contraction in FP32 (TF32 disabled) and torch-generated Gaussian noise. Returns the flat
+    device tensor in memory order (mode 0 fastest) in the spec's storage type (BF16 by round to
+    nearest even from FP32) and the initial cores (numpy)."""
+    import torch
+
+    torch.backends.cuda.matmul.allow_tf32 = False
+    cores = random_tt(spec["dims"], spec["ranks"], spec["tensor_seed"])
+    q = None  # Q[beta, i] with i = linear index of the modes so far (first fastest)
+    for g in cores:
+        gt = torch.as_tensor(np.ascontiguousarray(g), dtype=torch.float32, device=device)
+        if q is None:
+            q = gt[0].transpose(0, 1).contiguous()  # (r1, n0)
+        else:
+            q = torch.einsum("aib,ax->bix", gt, q).reshape(gt.shape[2], -1)
+    t = q.reshape(-1)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(spec["tensor_seed"])
+    e = torch.randn(t.numel(), generator=gen, device=device, dtype=torch.float32)
+    a = t + (spec["noise"] * torch.linalg.vector_norm(t) / torch.linalg.vector_norm(e)) * e
+    if spec["dtype"] == "bf16":
+        a = a.to(torch.bfloat16)
+    elif spec["dtype"] != "f32":
+        raise ValueError("device generation covers f32 and bf16 storage")
+    init = random_cores(spec["dims"], spec["ranks"], np.random.default_rng([spec["tensor_seed"], STREAM_INIT]))
+    return a, init
