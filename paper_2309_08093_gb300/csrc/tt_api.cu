@@ -13,7 +13,7 @@ static int check_data(tt_ctx* c, const void* A, const float* scales) {
   return TT_OK;
 }
 
-static int check_cores(tt_ctx* c, float* const* cores) {
+int tt_check_cores(tt_ctx* c, float* const* cores) {
   if (!cores) return tt_fail(c, TT_EINVAL, "null core array");
   for (int k = 0; k < c->d; ++k)
     if (!cores[k]) return tt_fail(c, TT_EINVAL, "null core pointer %d", k);
@@ -30,16 +30,10 @@ int tt_read_status(tt_ctx* c) {
   return TT_OK;
 }
 
-static int reset_status(tt_ctx* c) {
+int tt_reset_status(tt_ctx* c) {
   TT_CUDA(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
   return TT_OK;
 }
-
-#define TT_TRY(x)            \
-  do {                       \
-    int _rc = (x);           \
-    if (_rc) return _rc;     \
-  } while (0)
 
 extern "C" int tt_sketch_unfold(tt_ctx* c, const void* A, const float* scales, int k, uint64_t sweep,
                                 float* const* Y) {
@@ -63,7 +57,7 @@ static int build_all_ghat(tt_ctx* c, float* const* cores) {
 
 extern "C" int tt_sketch_interface(tt_ctx* c, float* const* cores, int k, uint64_t sweep, float* SH) {
   if (!c) return TT_EINVAL;
-  TT_TRY(check_cores(c, cores));
+  TT_TRY(tt_check_cores(c, cores));
   if (!SH) return tt_fail(c, TT_EINVAL, "null output");
   if (k < 0 || k >= c->d) return tt_fail(c, TT_EINVAL, "mode %d outside [0, %d)", k, c->d);
   c->err.clear();
@@ -81,16 +75,16 @@ extern "C" int tt_prox_update(tt_ctx* c, const float* Y, const float* SH, float*
   if (!Y || !SH || !core) return tt_fail(c, TT_EINVAL, "null pointer");
   if (k < 0 || k >= c->d) return tt_fail(c, TT_EINVAL, "mode %d outside [0, %d)", k, c->d);
   c->err.clear();
-  TT_TRY(reset_status(c));
+  TT_TRY(tt_reset_status(c));
   TT_TRY(tt_launch_prox_update(c, Y, SH, core, k, nullptr));
   return tt_read_status(c);
 }
 
 extern "C" int tt_orthogonalize(tt_ctx* c, float* const* cores, int direction, int k) {
   if (!c) return TT_EINVAL;
-  TT_TRY(check_cores(c, cores));
+  TT_TRY(tt_check_cores(c, cores));
   c->err.clear();
-  TT_TRY(reset_status(c));
+  TT_TRY(tt_reset_status(c));
   if (direction == -1) {
     for (int kk = c->d - 1; kk >= 1; --kk) TT_TRY(tt_launch_lq_right(c, cores[kk - 1], cores[kk], kk));
   } else if (direction == 1) {
@@ -128,10 +122,10 @@ extern "C" int tt_prox_als_sweep(tt_ctx* c, const void* A, const float* scales, 
                                  int nsweeps, uint64_t first_sweep, double* rel_change_out) {
   if (!c) return TT_EINVAL;
   TT_TRY(check_data(c, A, scales));
-  TT_TRY(check_cores(c, cores));
+  TT_TRY(tt_check_cores(c, cores));
   if (nsweeps < 0) return tt_fail(c, TT_EINVAL, "nsweeps < 0");
   c->err.clear();
-  TT_TRY(reset_status(c));
+  TT_TRY(tt_reset_status(c));
   const int per_block = c->changes_cap / c->d;
   std::vector<double> host;
   for (int t0 = 0; t0 < nsweeps; t0 += per_block) {
@@ -167,7 +161,7 @@ extern "C" int tt_prox_als_sweep(tt_ctx* c, const void* A, const float* scales, 
 extern "C" int tt_rel_error(tt_ctx* c, const void* A, const float* scales, float* const* cores, double* out) {
   if (!c) return TT_EINVAL;
   TT_TRY(check_data(c, A, scales));
-  TT_TRY(check_cores(c, cores));
+  TT_TRY(tt_check_cores(c, cores));
   if (!out) return tt_fail(c, TT_EINVAL, "null output");
   c->err.clear();
   TT_TRY(tt_launch_rel_error(c, A, scales, cores));
@@ -195,7 +189,7 @@ extern "C" int tt_prox_als_sweep_host(tt_ctx* c, const void* A_host, const float
                                       double* rel_change_out, double* rel_error_out) {
   if (!c) return TT_EINVAL;
   TT_TRY(check_data(c, A_host, scales_host));
-  TT_TRY(check_cores(c, cores_host));
+  TT_TRY(tt_check_cores(c, cores_host));
   c->err.clear();
   const size_t abytes = (size_t)c->N * tt_elem_bytes(c->dtype);
   if (!c->d_A_stage) TT_CUDA(c, cudaMalloc(&c->d_A_stage, abytes));

@@ -154,6 +154,14 @@ int tt_launch_qr_left(tt_ctx* c, float* core_k, float* core_k1, int k);
 int tt_launch_lq_right(tt_ctx* c, float* core_km1, float* core_k, int k);
 int tt_launch_rel_error(tt_ctx* c, const void* A, const float* scales, float* const* cores);
 int tt_read_status(tt_ctx* c);
+int tt_reset_status(tt_ctx* c);
+int tt_check_cores(tt_ctx* c, float* const* cores);
+
+#define TT_TRY(x)            \
+  do {                       \
+    int _rc = (x);           \
+    if (_rc) return _rc;     \
+  } while (0)
 int tt_one_sweep(tt_ctx* c, const void* A, const float* scales, float* const* cores, uint64_t sweep,
                  double* change_slots);
 int tt_prof_begin(tt_ctx* c, int k);   // record a start event when profiling (returns TT_OK)

@@ -1,0 +1,824 @@
+// Learned warm start: the MLP's kernels and its C ABI (include/tt_warmstart.h).
+//
+//   k_gemm_tn<EPI>  : C = A B^T, A (M x K) and B (N x K) row-major BF16, one 128 x 128 tile per
+//                     CTA. Operands are staged by cp.async into shared memory in the canonical
+//                     no-swizzle K-major layout (8 x 16-byte core matrices); one thread issues
+//                     tcgen05.mma (kind::f16, BF16 x BF16 -> FP32) into a 128-column tensor-memory
+//                     accumulator; completion is signalled by tcgen05.commit on an mbarrier per
+//                     stage. Four stages: tile kt+2 loads while the MMAs of kt-1 and kt run. The
+//                     epilogue reads the accumulator with tcgen05.ld (warp w owns lanes 32w..32w+31)
+//                     and applies one of three fused epilogues:
+//                       EPI_F32   : C (+ bias) -> FP32
+//                       EPI_GELU  : Z = C + bias -> FP32 (kept for the backward pass),
+//                                   H = GELU(Z) -> BF16 row-major and BF16 transposed
+//                       EPI_DGELU : dZ = C * GELU'(Z) -> FP32, BF16 row-major, BF16 transposed
+//   k_input         : gather rows of X, round to BF16 (row-major and transposed), zero padding
+//   k_loss          : dY = 2 (Y - T) / (B out) and the squared-error sum (FP64)
+//   k_colsum        : bias gradients (column sums, fixed order)
+//   k_adam          : Adam update of FP32 masters, BF16 copies (and transposed copies)
+//
+// Padded shapes: in_p = roundup(in, 64), out_p = roundup(out, 64), batch rows padded to Bp =
+// roundup(batch, 64) inside the batch_max buffers. Padding entries of weights and inputs are zero
+// and receive zero gradients, so they stay zero.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <string>
+
+#include "../../include/tt_warmstart.h"
+
+namespace {
+
+typedef __nv_bfloat16 bf16;
+
+constexpr int GM = 128, GN = 128, GK = 64, GSTAGES = 4;
+constexpr int A_STAGE = GM * GK * 2;  // bytes per stage of A
+constexpr int B_STAGE = GN * GK * 2;
+constexpr int GEMM_SMEM = GSTAGES * (A_STAGE + B_STAGE) + 1024 + 128;
+constexpr uint32_t TMEM_COLS = 128;
+constexpr unsigned long long WAIT_NS = 2000000000ull;  // an mbarrier wait gives up after 2 s
+
+enum { EPI_F32 = 0, EPI_GELU = 1, EPI_DGELU = 2 };
+
+struct GemmArgs {
+  const bf16* A;
+  int lda;
+  const bf16* B;
+  int ldb;
+  int M, N, K;
+  // epilogue
+  const float* bias;  // per column (EPI_F32 optional, EPI_GELU required)
+  float* f32;         // FP32 output (C, Z or dZ)
+  int ldf;
+  const float* zin;   // EPI_DGELU: pre-activation Z, row stride ldf
+  bf16* hb;           // BF16 row-major output (EPI_GELU / EPI_DGELU)
+  int ldh;
+  bf16* ht;           // BF16 transposed output: ht[col * ldt + row]
+  int ldt;
+  int* err;           // device flag set to 1 when a bounded wait gave up
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// tcgen05 shared-memory matrix descriptor, no swizzle: start address, leading-dimension byte
+// offset (between core matrices adjacent in K), stride byte offset (between 8-row groups), the
+// fixed 0b001 field at bits 46-48, base offset 0, swizzle mode 0.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// Instruction descriptor of tcgen05.mma kind::f16: D FP32 (bits 4-5 = 1), A BF16 (bits 7-9 = 1),
+// B BF16 (bits 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at 24-28.
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(GN >> 3) << 17) |
+                           ((uint32_t)(GM >> 4) << 24);
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool valid) {
+  const int sz = valid ? 16 : 0;  // 0 = fill the 16 bytes with zeros, read nothing
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(sz)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t addr, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(addr), "r"(count) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t addr, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(addr), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Bounded wait for the completion of phase `parity`; false if it gave up.
+__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity) {
+  if (mbar_try(addr, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (global_ns() - t0 < WAIT_NS)
+    if (mbar_try(addr, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar)
+               : "memory");
+}
+
+// 32 consecutive accumulator columns of this thread's lane.
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+        "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+        "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+}
+
+__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad_f(float z) {
+  return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
+}
+
+// Stage one 128 x 64 BF16 tile (rows r0.., columns k0..k0+63 of a row-major matrix) into the
+// no-swizzle K-major layout: 16-byte chunk (row, c) at (row / 8) * 1024 + c * 128 + (row % 8) * 16.
+__device__ __forceinline__ void load_tile(uint32_t sbase, const bf16* M, int ld, int rows, int r0, int k0,
+                                          int tid) {
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int q = tid + 128 * j;
+    const int row = q >> 3, c = q & 7;
+    const int g = r0 + row;
+    const bool ok = g < rows;
+    const bf16* src = ok ? M + (int64_t)g * ld + k0 + c * 8 : M;
+    cp_async16(sbase + (uint32_t)((row >> 3) * 1024 + c * 128 + (row & 7) * 16), src, ok);
+  }
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(128, 1) k_gemm_tn(GemmArgs g) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + GSTAGES * A_STAGE;
+  uint64_t* mbar = (uint64_t*)(sB + GSTAGES * B_STAGE);
+  uint32_t* s_tmem = (uint32_t*)(mbar + GSTAGES);
+  volatile int* s_err = (volatile int*)(s_tmem + 2);  // two slots, alternating by iteration
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.y * GM, n0 = blockIdx.x * GN;
+  const int KT = g.K / GK;
+
+  if (tid == 0) {
+    for (int s = 0; s < GSTAGES; ++s) mbar_init(smem_u32(&mbar[s]), 1);
+    s_err[0] = 0;
+    s_err[1] = 0;
+    s_err[2] = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(s_tmem)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *s_tmem;
+  const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+
+  load_tile(a0, g.A, g.lda, g.M, m0, 0, tid);
+  load_tile(b0, g.B, g.ldb, g.N, n0, 0, tid);
+  cp_async_commit();
+  if (KT > 1) {
+    load_tile(a0 + A_STAGE, g.A, g.lda, g.M, m0, GK, tid);
+    load_tile(b0 + B_STAGE, g.B, g.ldb, g.N, n0, GK, tid);
+  }
+  cp_async_commit();
+
+  bool failed = false;
+  for (int kt = 0; kt < KT; ++kt) {
+    const int s = kt % GSTAGES;
+    cp_async_wait<1>();  // this thread's copies of tile kt have landed
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    if (tid == 0 && kt >= 2) {  // the stage about to be refilled was read by the MMAs of kt-2
+      const int t = kt - 2;
+      if (!mbar_wait(smem_u32(&mbar[t % GSTAGES]), (uint32_t)((t / GSTAGES) & 1))) s_err[kt & 1] = 1;
+    }
+    __syncthreads();
+    if (s_err[kt & 1]) {
+      failed = true;
+      break;
+    }
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t sa = a0 + s * A_STAGE, sb = b0 + s * B_STAGE;
+#pragma unroll
+      for (int kk = 0; kk < GK / 16; ++kk)
+        tc_mma(tmem, smem_desc(sa + kk * 256, 128, 1024), smem_desc(sb + kk * 256, 128, 1024), IDESC,
+               (kt > 0 || kk > 0) ? 1u : 0u);
+      tc_commit(smem_u32(&mbar[s]));
+    }
+    if (kt + 2 < KT) {
+      const int s2 = (kt + 2) % GSTAGES;
+      load_tile(a0 + s2 * A_STAGE, g.A, g.lda, g.M, m0, (kt + 2) * GK, tid);
+      load_tile(b0 + s2 * B_STAGE, g.B, g.ldb, g.N, n0, (kt + 2) * GK, tid);
+    }
+    cp_async_commit();
+  }
+  cp_async_wait<0>();
+  if (!failed) {
+    if (tid == 0) {
+      const int t = KT - 1;
+      if (!mbar_wait(smem_u32(&mbar[t % GSTAGES]), (uint32_t)((t / GSTAGES) & 1))) s_err[2] = 1;
+    }
+    __syncthreads();
+    failed = s_err[2] != 0;
+  }
+  tc_fence_after();
+
+  if (!failed) {
+    const int row = m0 + 32 * warp + lane;
+    const bool row_ok = row < g.M;
+    for (int c0 = 0; c0 < GN; c0 += 32) {
+      if (n0 + c0 >= g.N) break;  // uniform over the CTA
+      uint32_t r[32];
+      tc_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, r);
+      const int col0 = n0 + c0;
+      if (EPI == EPI_F32) {
+        if (row_ok) {
+          float* out = g.f32 + (int64_t)row * g.ldf + col0;
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (col0 + j < g.N) out[j] = __uint_as_float(r[j]) + (g.bias ? g.bias[col0 + j] : 0.0f);
+        }
+      } else {
+        // full 32-column chunks (N % 32 == 0 is checked on the host)
+        float v[32];
+        if (EPI == EPI_GELU) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]) + g.bias[col0 + j];
+          if (row_ok) {
+            float* zo = g.f32 + (int64_t)row * g.ldf + col0;
+#pragma unroll
+            for (int j = 0; j < 32; j += 4) *(float4*)(zo + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+          }
+#pragma unroll
+          for (int j = 0; j < 32; ++j) v[j] = gelu_f(v[j]);
+        } else {
+          float zz[32];
+          if (row_ok) {
+            const float* zi = g.zin + (int64_t)row * g.ldf + col0;
+#pragma unroll
+            for (int j = 0; j < 32; j += 4) {
+              const float4 q = *(const float4*)(zi + j);
+              zz[j] = q.x; zz[j + 1] = q.y; zz[j + 2] = q.z; zz[j + 3] = q.w;
+            }
+          } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) zz[j] = 0.0f;
+          }
+#pragma unroll
+          for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]) * gelu_grad_f(zz[j]);
+          if (row_ok) {
+            float* zo = g.f32 + (int64_t)row * g.ldf + col0;
+#pragma unroll
+            for (int j = 0; j < 32; j += 4) *(float4*)(zo + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+          }
+        }
+        if (row_ok) {
+          uint32_t pk[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+            pk[j] = *(const uint32_t*)&h2;
+          }
+          uint4* ho = (uint4*)(g.hb + (int64_t)row * g.ldh + col0);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) ho[j] = make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) g.ht[(int64_t)(col0 + j) * g.ldt + row] = __float2bfloat16_rn(v[j]);
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  if (failed && tid == 0 && g.err) atomicExch(g.err, 1);
+}
+
+// ---------------------------------------------------------------------------------------------
+// elementwise kernels
+
+// Rows of X (optionally gathered) -> BF16 row-major Xb (Bp x in_p) and transposed XbT
+// (in_p x ldt); rows >= batch and columns >= in are zero.
+__global__ void k_input(const float* __restrict__ X, int ldx, const int* __restrict__ rows, int batch, int in,
+                        int in_p, int Bp, bf16* __restrict__ Xb, bf16* __restrict__ XbT, int ldt) {
+  __shared__ float tile[32][33];
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    const int row = r0 + y, col = c0 + threadIdx.x;
+    float v = 0.0f;
+    if (row < batch && col < in) {
+      const int64_t src = rows ? (int64_t)rows[row] : (int64_t)row;
+      v = X[src * ldx + col];
+    }
+    if (row < Bp && col < in_p) Xb[(int64_t)row * in_p + col] = __float2bfloat16_rn(v);
+    tile[y][threadIdx.x] = v;
+  }
+  __syncthreads();
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    const int col = c0 + y, row = r0 + threadIdx.x;
+    if (col < in_p && row < Bp) XbT[(int64_t)col * ldt + row] = __float2bfloat16_rn(tile[threadIdx.x][y]);
+  }
+}
+
+// dY = 2 (Y - T) / (batch * out) for valid entries, 0 in the padding; the sum of (Y - T)^2 is
+// accumulated in FP64.
+__global__ void k_loss(const float* __restrict__ Y, int ldy, const float* __restrict__ T, int ldt_in,
+                       const int* __restrict__ rows, int batch, int out, int out_p, int Bp, float inv,
+                       float* __restrict__ dY, bf16* __restrict__ dYb, bf16* __restrict__ dYbT, int ldbt,
+                       double* __restrict__ loss) {
+  __shared__ float tile[32][33];
+  __shared__ double red[8];
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  double acc = 0.0;
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    const int row = r0 + y, col = c0 + threadIdx.x;
+    float d = 0.0f;
+    if (row < batch && col < out) {
+      const int64_t src = rows ? (int64_t)rows[row] : (int64_t)row;
+      const float res = Y[(int64_t)row * ldy + col] - T[src * ldt_in + col];
+      acc += (double)res * (double)res;
+      d = 2.0f * res * inv;
+    }
+    if (row < Bp && col < out_p) {
+      dY[(int64_t)row * out_p + col] = d;
+      dYb[(int64_t)row * out_p + col] = __float2bfloat16_rn(d);
+    }
+    tile[y][threadIdx.x] = d;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (threadIdx.x == 0) red[threadIdx.y] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    double s = 0.0;
+    for (int i = 0; i < (int)blockDim.y; ++i) s += red[i];
+    if (s != 0.0) atomicAdd(loss, s);
+  }
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    const int col = c0 + y, row = r0 + threadIdx.x;
+    if (col < out_p && row < Bp) dYbT[(int64_t)col * ldbt + row] = __float2bfloat16_rn(tile[threadIdx.x][y]);
+  }
+}
+
+// g[j] = sum_{row < rows} D[row * ld + j] (one thread per column, fixed order).
+__global__ void k_colsum(const float* __restrict__ D, int ld, int rows, int cols, float* __restrict__ g) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= cols) return;
+  float s = 0.0f;
+  for (int r = 0; r < rows; ++r) s += D[(int64_t)r * ld + j];
+  g[j] = s;
+}
+
+// Adam on a rows x cols FP32 matrix (row-major, leading dimension cols), then BF16 copies:
+// wb (row-major, optional) and wt (transposed, wt[c * rows + r], optional). pack_only skips the
+// update and only refreshes the copies.
+__global__ void k_adam(float* __restrict__ w, const float* __restrict__ gr, float* __restrict__ m,
+                       float* __restrict__ v, int rows, int cols, float lr, float b1, float b2, float eps,
+                       float c1, float c2, int pack_only, bf16* __restrict__ wb, bf16* __restrict__ wt) {
+  __shared__ float tile[32][33];
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    const int row = r0 + y, col = c0 + threadIdx.x;
+    float x = 0.0f;
+    if (row < rows && col < cols) {
+      const int64_t i = (int64_t)row * cols + col;
+      x = w[i];
+      if (!pack_only) {
+        const float gi = gr[i];
+        const float mi = b1 * m[i] + (1.0f - b1) * gi;
+        const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        const float mhat = mi / c1, vhat = vi / c2;
+        x = x - lr * mhat / (sqrtf(vhat) + eps);
+        w[i] = x;
+      }
+      if (wb) wb[i] = __float2bfloat16_rn(x);
+    }
+    tile[y][threadIdx.x] = x;
+  }
+  if (!wt) return;
+  __syncthreads();
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    const int col = c0 + y, row = r0 + threadIdx.x;
+    if (col < cols && row < rows) wt[(int64_t)col * rows + row] = __float2bfloat16_rn(tile[threadIdx.x][y]);
+  }
+}
+
+// Copy a rows x cols block between row-major matrices of different leading dimensions.
+__global__ void k_copy2d(const float* __restrict__ src, int lds, float* __restrict__ dst, int ldd, int rows,
+                         int cols) {
+  const int64_t total = (int64_t)rows * cols;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / cols, c = i % cols;
+    dst[r * ldd + c] = src[r * lds + c];
+  }
+}
+
+int roundup(int x, int m) { return (x + m - 1) / m * m; }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------------
+// the network object
+
+struct tt_mlp {
+  int in = 0, hid = 0, out = 0, bmax = 0;
+  int in_p = 0, out_p = 0, bmax_p = 0;
+  float lr = 0, b1 = 0, b2 = 0, eps = 0;
+  int t = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+
+  // FP32 masters (padded), Adam moments, gradients: index 0..5 = W1, b1, W2, b2, W3, b3
+  float* P[6] = {nullptr};
+  float* Mo[6] = {nullptr};
+  float* Vo[6] = {nullptr};
+  float* G[6] = {nullptr};
+  int prow[6] = {0}, pcol[6] = {0};  // padded shapes (rows x cols; biases 1 x len)
+  bf16 *W1b = nullptr, *W2b = nullptr, *W2t = nullptr, *W3b = nullptr, *W3t = nullptr;
+  // activations
+  bf16 *Xb = nullptr, *XbT = nullptr;
+  float *Z1 = nullptr, *Z2 = nullptr, *Y = nullptr, *dY = nullptr, *dZ1 = nullptr, *dZ2 = nullptr;
+  bf16 *H1b = nullptr, *H1t = nullptr, *H2b = nullptr, *H2t = nullptr;
+  bf16 *dYb = nullptr, *dYt = nullptr, *dZ1b = nullptr, *dZ1t = nullptr, *dZ2b = nullptr, *dZ2t = nullptr;
+  double* d_loss = nullptr;
+  int* d_err = nullptr;
+  int64_t launches = 0;
+};
+
+namespace {
+
+int mfail(tt_mlp* m, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (m) m->err = buf;
+  return code;
+}
+
+#define MLP_CUDA(m, call)                                                                  \
+  do {                                                                                     \
+    cudaError_t _e = (call);                                                               \
+    if (_e != cudaSuccess) return mfail(m, TT_ECUDA, "%s: %s", #call, cudaGetErrorString(_e)); \
+  } while (0)
+#define MLP_LAUNCH(m, what)                                                                  \
+  do {                                                                                       \
+    cudaError_t _e = cudaGetLastError();                                                     \
+    if (_e != cudaSuccess) return mfail(m, TT_ECUDA, "%s: %s", what, cudaGetErrorString(_e)); \
+    if (m) ++(m)->launches;                                                                  \
+  } while (0)
+#define MLP_TRY(x)              \
+  do {                          \
+    int _r = (x);               \
+    if (_r != TT_OK) return _r; \
+  } while (0)
+
+template <int EPI>
+int launch_gemm(tt_mlp* m, const GemmArgs& g, cudaStream_t s) {
+  static bool attr_done = false;  // per template instance; the attribute is per function
+  if (!attr_done) {
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_tn<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, GEMM_SMEM);
+    if (e != cudaSuccess) return mfail(m, TT_ECUDA, "gemm smem attribute: %s", cudaGetErrorString(e));
+    attr_done = true;
+  }
+  dim3 grid((g.N + GN - 1) / GN, (g.M + GM - 1) / GM);
+  k_gemm_tn<EPI><<<grid, 128, GEMM_SMEM, s>>>(g);
+  MLP_LAUNCH(m, "k_gemm_tn");
+  return TT_OK;
+}
+
+GemmArgs gemm_args(const bf16* A, int lda, const bf16* B, int ldb, int M, int N, int K, int* err) {
+  GemmArgs g{};
+  g.A = A; g.lda = lda; g.B = B; g.ldb = ldb; g.M = M; g.N = N; g.K = K; g.err = err;
+  return g;
+}
+
+int check_err_flag(tt_mlp* m) {
+  int h = 0;
+  MLP_CUDA(m, cudaMemcpyAsync(&h, m->d_err, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
+  MLP_CUDA(m, cudaStreamSynchronize(m->stream));
+  if (h) return mfail(m, TT_ETIMEOUT, "a bounded wait in the GEMM kernel gave up");
+  return TT_OK;
+}
+
+int pack_weights(tt_mlp* m) {
+  dim3 blk(32, 8);
+  bf16* wb[6] = {m->W1b, nullptr, m->W2b, nullptr, m->W3b, nullptr};
+  bf16* wt[6] = {nullptr, nullptr, m->W2t, nullptr, m->W3t, nullptr};
+  for (int i = 0; i < 6; i += 2) {
+    dim3 grid((m->pcol[i] + 31) / 32, (m->prow[i] + 31) / 32);
+    k_adam<<<grid, blk, 0, m->stream>>>(m->P[i], nullptr, nullptr, nullptr, m->prow[i], m->pcol[i], 0, 0, 0, 0, 1,
+                                        1, 1, wb[i], wt[i]);
+    MLP_LAUNCH(m, "k_adam(pack)");
+  }
+  return TT_OK;
+}
+
+// forward pass for `batch` rows; leaves Z1, Z2, H*, Y in the network's buffers
+int forward(tt_mlp* m, const float* X, int ldx, const int* rows, int batch) {
+  const int Bp = roundup(batch, 64);
+  {
+    dim3 grid((m->in_p + 31) / 32, (Bp + 31) / 32), blk(32, 8);
+    k_input<<<grid, blk, 0, m->stream>>>(X, ldx, rows, batch, m->in, m->in_p, Bp, m->Xb, m->XbT, m->bmax_p);
+    MLP_LAUNCH(m, "k_input");
+  }
+  GemmArgs g = gemm_args(m->Xb, m->in_p, m->W1b, m->in_p, Bp, m->hid, m->in_p, m->d_err);
+  g.bias = m->P[1]; g.f32 = m->Z1; g.ldf = m->hid; g.hb = m->H1b; g.ldh = m->hid; g.ht = m->H1t; g.ldt = m->bmax_p;
+  MLP_TRY(launch_gemm<EPI_GELU>(m, g, m->stream));
+  g = gemm_args(m->H1b, m->hid, m->W2b, m->hid, Bp, m->hid, m->hid, m->d_err);
+  g.bias = m->P[3]; g.f32 = m->Z2; g.ldf = m->hid; g.hb = m->H2b; g.ldh = m->hid; g.ht = m->H2t; g.ldt = m->bmax_p;
+  MLP_TRY(launch_gemm<EPI_GELU>(m, g, m->stream));
+  g = gemm_args(m->H2b, m->hid, m->W3b, m->hid, Bp, m->out_p, m->hid, m->d_err);
+  g.bias = m->P[5]; g.f32 = m->Y; g.ldf = m->out_p;
+  MLP_TRY(launch_gemm<EPI_F32>(m, g, m->stream));
+  return TT_OK;
+}
+
+// loss gradient and backward pass into m->G[*]
+int backward(tt_mlp* m, const float* T, int ldt, const int* rows, int batch) {
+  const int Bp = roundup(batch, 64);
+  MLP_CUDA(m, cudaMemsetAsync(m->d_loss, 0, sizeof(double), m->stream));
+  {
+    dim3 grid((m->out_p + 31) / 32, (Bp + 31) / 32), blk(32, 8);
+    const float inv = (float)(1.0 / ((double)batch * (double)m->out));
+    k_loss<<<grid, blk, 0, m->stream>>>(m->Y, m->out_p, T, ldt, rows, batch, m->out, m->out_p, Bp, inv, m->dY,
+                                        m->dYb, m->dYt, m->bmax_p, m->d_loss);
+    MLP_LAUNCH(m, "k_loss");
+  }
+  // dW3 = dY^T H2, db3 = colsum(dY)
+  GemmArgs g = gemm_args(m->dYt, m->bmax_p, m->H2t, m->bmax_p, m->out_p, m->hid, Bp, m->d_err);
+  g.f32 = m->G[4]; g.ldf = m->hid;
+  MLP_TRY(launch_gemm<EPI_F32>(m, g, m->stream));
+  k_colsum<<<(m->out_p + 255) / 256, 256, 0, m->stream>>>(m->dY, m->out_p, Bp, m->out_p, m->G[5]);
+  MLP_LAUNCH(m, "k_colsum");
+  // dZ2 = (dY W3) * GELU'(Z2)
+  g = gemm_args(m->dYb, m->out_p, m->W3t, m->out_p, Bp, m->hid, m->out_p, m->d_err);
+  g.f32 = m->dZ2; g.ldf = m->hid; g.zin = m->Z2; g.hb = m->dZ2b; g.ldh = m->hid; g.ht = m->dZ2t; g.ldt = m->bmax_p;
+  MLP_TRY(launch_gemm<EPI_DGELU>(m, g, m->stream));
+  // dW2 = dZ2^T H1, db2
+  g = gemm_args(m->dZ2t, m->bmax_p, m->H1t, m->bmax_p, m->hid, m->hid, Bp, m->d_err);
+  g.f32 = m->G[2]; g.ldf = m->hid;
+  MLP_TRY(launch_gemm<EPI_F32>(m, g, m->stream));
+  k_colsum<<<(m->hid + 255) / 256, 256, 0, m->stream>>>(m->dZ2, m->hid, Bp, m->hid, m->G[3]);
+  MLP_LAUNCH(m, "k_colsum");
+  // dZ1 = (dZ2 W2) * GELU'(Z1)
+  g = gemm_args(m->dZ2b, m->hid, m->W2t, m->hid, Bp, m->hid, m->hid, m->d_err);
+  g.f32 = m->dZ1; g.ldf = m->hid; g.zin = m->Z1; g.hb = m->dZ1b; g.ldh = m->hid; g.ht = m->dZ1t; g.ldt = m->bmax_p;
+  MLP_TRY(launch_gemm<EPI_DGELU>(m, g, m->stream));
+  // dW1 = dZ1^T X, db1
+  g = gemm_args(m->dZ1t, m->bmax_p, m->XbT, m->bmax_p, m->hid, m->in_p, Bp, m->d_err);
+  g.f32 = m->G[0]; g.ldf = m->in_p;
+  MLP_TRY(launch_gemm<EPI_F32>(m, g, m->stream));
+  k_colsum<<<(m->hid + 255) / 256, 256, 0, m->stream>>>(m->dZ1, m->hid, Bp, m->hid, m->G[1]);
+  MLP_LAUNCH(m, "k_colsum");
+  return TT_OK;
+}
+
+int check_batch(tt_mlp* m, const float* X, int ldx, int batch) {
+  if (!X) return mfail(m, TT_EINVAL, "null input");
+  if (batch < 1 || batch > m->bmax) return mfail(m, TT_EINVAL, "batch %d outside 1..%d", batch, m->bmax);
+  if (ldx < m->in) return mfail(m, TT_EINVAL, "ldx %d < in_dim %d", ldx, m->in);
+  return TT_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------------
+// C ABI
+
+extern "C" int tt_mlp_init(tt_mlp** out, const tt_mlp_params* p, void* cuda_stream) {
+  if (!out || !p) return TT_EINVAL;
+  *out = nullptr;
+  if (p->in_dim < 1 || p->in_dim > 65536 || p->hidden < 64 || p->hidden > 2048 || p->hidden % 64 != 0 ||
+      p->out_dim < 1 || p->out_dim > 262144 || p->batch_max < 1 || p->batch_max > 1024 || !(p->beta1 >= 0.0f) ||
+      !(p->beta1 < 1.0f) || !(p->beta2 >= 0.0f) || !(p->beta2 < 1.0f) || !(p->eps > 0.0f) || !std::isfinite(p->lr)) {
+    fprintf(stderr, "tt_mlp_init: invalid parameters\n");
+    return TT_EINVAL;
+  }
+  tt_mlp* m = new tt_mlp();
+  m->in = p->in_dim; m->hid = p->hidden; m->out = p->out_dim; m->bmax = p->batch_max;
+  m->in_p = roundup(m->in, 64); m->out_p = roundup(m->out, 64); m->bmax_p = roundup(m->bmax, 64);
+  m->lr = p->lr; m->b1 = p->beta1; m->b2 = p->beta2; m->eps = p->eps;
+  m->stream = (cudaStream_t)cuda_stream;
+  const int R[6] = {m->hid, 1, m->hid, 1, m->out_p, 1};
+  const int C[6] = {m->in_p, m->hid, m->hid, m->hid, m->hid, m->out_p};
+  auto fail = [&](const char* what) {
+    fprintf(stderr, "tt_mlp_init: allocation of %s failed\n", what);
+    tt_mlp_destroy(m);
+    return TT_ENOMEM;
+  };
+  for (int i = 0; i < 6; ++i) {
+    m->prow[i] = R[i];
+    m->pcol[i] = C[i];
+    const size_t bytes = (size_t)R[i] * C[i] * sizeof(float);
+    if (cudaMalloc(&m->P[i], bytes) != cudaSuccess || cudaMalloc(&m->Mo[i], bytes) != cudaSuccess ||
+        cudaMalloc(&m->Vo[i], bytes) != cudaSuccess || cudaMalloc(&m->G[i], bytes) != cudaSuccess)
+      return fail("parameters");
+    cudaMemset(m->P[i], 0, bytes);
+    cudaMemset(m->Mo[i], 0, bytes);
+    cudaMemset(m->Vo[i], 0, bytes);
+    cudaMemset(m->G[i], 0, bytes);
+  }
+  const size_t h = m->hid, ip = m->in_p, op = m->out_p, bp = m->bmax_p;
+  struct {
+    void** p;
+    size_t bytes;
+  } bufs[] = {{(void**)&m->W1b, h * ip * 2}, {(void**)&m->W2b, h * h * 2}, {(void**)&m->W2t, h * h * 2},
+              {(void**)&m->W3b, op * h * 2}, {(void**)&m->W3t, op * h * 2}, {(void**)&m->Xb, bp * ip * 2},
+              {(void**)&m->XbT, ip * bp * 2}, {(void**)&m->Z1, bp * h * 4}, {(void**)&m->Z2, bp * h * 4},
+              {(void**)&m->Y, bp * op * 4}, {(void**)&m->dY, bp * op * 4}, {(void**)&m->dZ1, bp * h * 4},
+              {(void**)&m->dZ2, bp * h * 4}, {(void**)&m->H1b, bp * h * 2}, {(void**)&m->H1t, h * bp * 2},
+              {(void**)&m->H2b, bp * h * 2}, {(void**)&m->H2t, h * bp * 2}, {(void**)&m->dYb, bp * op * 2},
+              {(void**)&m->dYt, op * bp * 2}, {(void**)&m->dZ1b, bp * h * 2}, {(void**)&m->dZ1t, h * bp * 2},
+              {(void**)&m->dZ2b, bp * h * 2}, {(void**)&m->dZ2t, h * bp * 2}, {(void**)&m->d_loss, 8},
+              {(void**)&m->d_err, 4}};
+  for (auto& b : bufs) {
+    if (cudaMalloc(b.p, b.bytes) != cudaSuccess) return fail("activations");
+    cudaMemset(*b.p, 0, b.bytes);
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) return fail("initialisation");
+  *out = m;
+  return TT_OK;
+}
+
+extern "C" int tt_mlp_destroy(tt_mlp* m) {
+  if (!m) return TT_OK;
+  if (m->stream) cudaStreamSynchronize(m->stream);
+  for (int i = 0; i < 6; ++i) {
+    cudaFree(m->P[i]); cudaFree(m->Mo[i]); cudaFree(m->Vo[i]); cudaFree(m->G[i]);
+  }
+  void* ps[] = {m->W1b, m->W2b, m->W2t, m->W3b, m->W3t, m->Xb, m->XbT, m->Z1, m->Z2, m->Y, m->dY, m->dZ1, m->dZ2,
+                m->H1b, m->H1t, m->H2b, m->H2t, m->dYb, m->dYt, m->dZ1b, m->dZ1t, m->dZ2b, m->dZ2t, m->d_loss,
+                m->d_err};
+  for (void* p : ps) cudaFree(p);
+  delete m;
+  return TT_OK;
+}
+
+extern "C" const char* tt_mlp_last_error(tt_mlp* m) { return m ? m->err.c_str() : "null network"; }
+
+extern "C" int tt_mlp_set_weights(tt_mlp* m, const float* W1, const float* b1, const float* W2, const float* b2,
+                                  const float* W3, const float* b3) {
+  if (!m) return TT_EINVAL;
+  if (!W1 || !b1 || !W2 || !b2 || !W3 || !b3) return mfail(m, TT_EINVAL, "null weight pointer");
+  const float* src[6] = {W1, b1, W2, b2, W3, b3};
+  const int rows[6] = {m->hid, 1, m->hid, 1, m->out, 1};
+  const int cols[6] = {m->in, m->hid, m->hid, m->hid, m->hid, m->out};
+  for (int i = 0; i < 6; ++i) {
+    const size_t bytes = (size_t)m->prow[i] * m->pcol[i] * sizeof(float);
+    MLP_CUDA(m, cudaMemsetAsync(m->P[i], 0, bytes, m->stream));
+    MLP_CUDA(m, cudaMemsetAsync(m->Mo[i], 0, bytes, m->stream));
+    MLP_CUDA(m, cudaMemsetAsync(m->Vo[i], 0, bytes, m->stream));
+    k_copy2d<<<256, 256, 0, m->stream>>>(src[i], cols[i], m->P[i], m->pcol[i], rows[i], cols[i]);
+    MLP_LAUNCH(m, "k_copy2d");
+  }
+  m->t = 0;
+  return pack_weights(m);
+}
+
+extern "C" int tt_mlp_get_weights(tt_mlp* m, float* W1, float* b1, float* W2, float* b2, float* W3, float* b3) {
+  if (!m) return TT_EINVAL;
+  if (!W1 || !b1 || !W2 || !b2 || !W3 || !b3) return mfail(m, TT_EINVAL, "null weight pointer");
+  float* dst[6] = {W1, b1, W2, b2, W3, b3};
+  const int rows[6] = {m->hid, 1, m->hid, 1, m->out, 1};
+  const int cols[6] = {m->in, m->hid, m->hid, m->hid, m->hid, m->out};
+  for (int i = 0; i < 6; ++i) {
+    k_copy2d<<<256, 256, 0, m->stream>>>(m->P[i], m->pcol[i], dst[i], cols[i], rows[i], cols[i]);
+    MLP_LAUNCH(m, "k_copy2d");
+  }
+  return TT_OK;
+}
+
+extern "C" int tt_mlp_forward(tt_mlp* m, const float* X, int ldx, const int* rows, int batch, float* Y, int ldy) {
+  if (!m) return TT_EINVAL;
+  MLP_TRY(check_batch(m, X, ldx, batch));
+  if (!Y || ldy < m->out) return mfail(m, TT_EINVAL, "bad output (ldy %d < out_dim %d or null)", ldy, m->out);
+  MLP_CUDA(m, cudaMemsetAsync(m->d_err, 0, sizeof(int), m->stream));
+  MLP_TRY(forward(m, X, ldx, rows, batch));
+  k_copy2d<<<256, 256, 0, m->stream>>>(m->Y, m->out_p, Y, ldy, batch, m->out);
+  MLP_LAUNCH(m, "k_copy2d");
+  return TT_OK;
+}
+
+extern "C" int tt_mlp_loss_grads(tt_mlp* m, const float* X, int ldx, const float* T, int ldt, const int* rows,
+                                 int batch, double* loss_out, float* gW1, float* gb1, float* gW2, float* gb2,
+                                 float* gW3, float* gb3) {
+  if (!m) return TT_EINVAL;
+  MLP_TRY(check_batch(m, X, ldx, batch));
+  if (!T || ldt < m->out) return mfail(m, TT_EINVAL, "bad targets (ldt %d < out_dim %d or null)", ldt, m->out);
+  MLP_CUDA(m, cudaMemsetAsync(m->d_err, 0, sizeof(int), m->stream));
+  MLP_TRY(forward(m, X, ldx, rows, batch));
+  MLP_TRY(backward(m, T, ldt, rows, batch));
+  float* dst[6] = {gW1, gb1, gW2, gb2, gW3, gb3};
+  const int r[6] = {m->hid, 1, m->hid, 1, m->out, 1};
+  const int c[6] = {m->in, m->hid, m->hid, m->hid, m->hid, m->out};
+  for (int i = 0; i < 6; ++i) {
+    if (!dst[i]) continue;
+    k_copy2d<<<256, 256, 0, m->stream>>>(m->G[i], m->pcol[i], dst[i], c[i], r[i], c[i]);
+    MLP_LAUNCH(m, "k_copy2d");
+  }
+  MLP_TRY(check_err_flag(m));
+  if (loss_out) {
+    double s = 0.0;
+    MLP_CUDA(m, cudaMemcpyAsync(&s, m->d_loss, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+    MLP_CUDA(m, cudaStreamSynchronize(m->stream));
+    *loss_out = s / ((double)batch * (double)m->out);
+  }
+  return TT_OK;
+}
+
+extern "C" int tt_mlp_train_step(tt_mlp* m, const float* X, int ldx, const float* T, int ldt, const int* rows,
+                                 int batch, double* loss_out) {
+  if (!m) return TT_EINVAL;
+  MLP_TRY(check_batch(m, X, ldx, batch));
+  if (!T || ldt < m->out) return mfail(m, TT_EINVAL, "bad targets (ldt %d < out_dim %d or null)", ldt, m->out);
+  MLP_CUDA(m, cudaMemsetAsync(m->d_err, 0, sizeof(int), m->stream));
+  MLP_TRY(forward(m, X, ldx, rows, batch));
+  MLP_TRY(backward(m, T, ldt, rows, batch));
+  m->t += 1;
+  const double c1 = 1.0 - std::pow((double)m->b1, (double)m->t);
+  const double c2 = 1.0 - std::pow((double)m->b2, (double)m->t);
+  bf16* wb[6] = {m->W1b, nullptr, m->W2b, nullptr, m->W3b, nullptr};
+  bf16* wt[6] = {nullptr, nullptr, m->W2t, nullptr, m->W3t, nullptr};
+  dim3 blk(32, 8);
+  for (int i = 0; i < 6; ++i) {
+    dim3 grid((m->pcol[i] + 31) / 32, (m->prow[i] + 31) / 32);
+    k_adam<<<grid, blk, 0, m->stream>>>(m->P[i], m->G[i], m->Mo[i], m->Vo[i], m->prow[i], m->pcol[i], m->lr, m->b1,
+                                        m->b2, m->eps, (float)c1, (float)c2, 0, wb[i], wt[i]);
+    MLP_LAUNCH(m, "k_adam");
+  }
+  if (loss_out) {
+    MLP_TRY(check_err_flag(m));
+    double s = 0.0;
+    MLP_CUDA(m, cudaMemcpyAsync(&s, m->d_loss, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+    MLP_CUDA(m, cudaStreamSynchronize(m->stream));
+    *loss_out = s / ((double)batch * (double)m->out);
+  }
+  return TT_OK;
+}
+
+extern "C" int tt_mlp_gemm_bf16(const uint16_t* A, int lda, const uint16_t* B, int ldb, int M, int N, int K,
+                                float* C, int ldc, int check, void* cuda_stream) {
+  if (!A || !B || !C || M < 1 || N < 1 || K < GK || K % GK != 0 || lda < K || ldb < K || lda % 8 != 0 ||
+      ldb % 8 != 0 || ldc < N || ((uintptr_t)A & 15) || ((uintptr_t)B & 15)) {
+    fprintf(stderr, "tt_mlp_gemm_bf16: invalid arguments\n");
+    return TT_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  static int* d_flag = nullptr;  // one flag for the standalone entry point
+  if (!d_flag && cudaMalloc(&d_flag, sizeof(int)) != cudaSuccess) return TT_ENOMEM;
+  if (cudaMemsetAsync(d_flag, 0, sizeof(int), s) != cudaSuccess) return TT_ECUDA;
+  GemmArgs g = gemm_args((const bf16*)A, lda, (const bf16*)B, ldb, M, N, K, d_flag);
+  g.f32 = C;
+  g.ldf = ldc;
+  int rc = launch_gemm<EPI_F32>(nullptr, g, s);
+  if (rc != TT_OK) return rc;
+  if (check) {
+    int h = 0;
+    if (cudaMemcpyAsync(&h, d_flag, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return TT_ECUDA;
+    if (h) return TT_ETIMEOUT;
+  }
+  return TT_OK;
+}

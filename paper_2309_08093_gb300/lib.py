@@ -24,7 +24,14 @@ EXPORTS = ["tt_sketch_init", "tt_sketch_destroy", "tt_last_error", "tt_sketch_ta
            "tt_sketch_set_tables", "tt_sketch_unfold", "tt_sketch_interface", "tt_prox_update",
            "tt_orthogonalize", "tt_prox_als_sweep", "tt_rel_error", "tt_prox_als_sweep_host",
            "tt_profile_enable", "tt_profile_read", "tt_prox_update_noalloc", "tt_batch_init",
-           "tt_batch_destroy", "tt_batch_last_error", "tt_batch_sweep", "tt_batch_rel_error"]
+           "tt_batch_destroy", "tt_batch_last_error", "tt_batch_sweep", "tt_batch_rel_error",
+           # learned warm start (include/tt_warmstart.h)
+           "tt_mlp_init", "tt_mlp_destroy", "tt_mlp_last_error", "tt_mlp_set_weights", "tt_mlp_get_weights",
+           "tt_mlp_forward", "tt_mlp_loss_grads", "tt_mlp_train_step", "tt_mlp_gemm_bf16",
+           "tt_ws_summary_dim", "tt_ws_core_dim", "tt_ws_summary", "tt_canonicalize", "tt_ws_pack",
+           "tt_ws_unpack"]
+_NOT_INT = {"tt_sketch_destroy", "tt_last_error", "tt_batch_destroy", "tt_batch_last_error", "tt_mlp_last_error",
+            "tt_ws_summary_dim", "tt_ws_core_dim"}
 
 
 class TtError(RuntimeError):
@@ -37,6 +44,12 @@ class TtProfile(ctypes.Structure):
     _fields_ = [("unfold_ms", ctypes.c_double), ("unfold_launches", ctypes.c_int64),
                 ("unfold_bytes", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
                 ("mode_ms", ctypes.c_double * 8), ("mode_launches", ctypes.c_int64 * 8)]
+
+
+class TtMlpParams(ctypes.Structure):
+    _fields_ = [("in_dim", ctypes.c_int), ("hidden", ctypes.c_int), ("out_dim", ctypes.c_int),
+                ("batch_max", ctypes.c_int), ("lr", ctypes.c_float), ("beta1", ctypes.c_float),
+                ("beta2", ctypes.c_float), ("eps", ctypes.c_float)]
 
 
 class TtParams(ctypes.Structure):
@@ -84,9 +97,28 @@ def load(path: str = LIB_PATH):
     L.tt_batch_sweep.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), i, u64]
     L.tt_batch_rel_error.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                      ctypes.POINTER(ctypes.c_double)]
+    f32p, dp, ip = vp, ctypes.POINTER(ctypes.c_double), vp
+    L.tt_mlp_init.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(TtMlpParams), vp]
+    L.tt_mlp_destroy.argtypes = [vp]
+    L.tt_mlp_last_error.argtypes = [vp]
+    L.tt_mlp_last_error.restype = ctypes.c_char_p
+    L.tt_mlp_set_weights.argtypes = [vp] + [f32p] * 6
+    L.tt_mlp_get_weights.argtypes = [vp] + [f32p] * 6
+    L.tt_mlp_forward.argtypes = [vp, f32p, i, ip, i, f32p, i]
+    L.tt_mlp_loss_grads.argtypes = [vp, f32p, i, f32p, i, ip, i, dp] + [f32p] * 6
+    L.tt_mlp_train_step.argtypes = [vp, f32p, i, f32p, i, ip, i, dp]
+    L.tt_mlp_gemm_bf16.argtypes = [vp, i, vp, i, i, i, i, f32p, i, i, vp]
+    L.tt_ws_summary_dim.argtypes = [vp, i]
+    L.tt_ws_summary_dim.restype = ctypes.c_int64
+    L.tt_ws_core_dim.argtypes = [vp]
+    L.tt_ws_core_dim.restype = ctypes.c_int64
+    L.tt_ws_summary.argtypes = [vp, ctypes.POINTER(vp), i, f32p, f32p]
+    L.tt_canonicalize.argtypes = [vp, ctypes.POINTER(vp)]
+    L.tt_ws_pack.argtypes = [vp, ctypes.POINTER(vp), f32p, f32p]
+    L.tt_ws_unpack.argtypes = [vp, f32p, f32p, ctypes.POINTER(vp)]
     for name in EXPORTS:
         f = getattr(L, name)
-        if name not in ("tt_sketch_destroy", "tt_last_error", "tt_batch_destroy", "tt_batch_last_error"):
+        if name not in _NOT_INT:
             f.restype = ctypes.c_int
     _lib = L
     return L
@@ -206,6 +238,98 @@ class Context:
         out = ctypes.c_double()
         self._check(self.lib.tt_rel_error(self.ctx, _ptr(A), _ptr(scales), _ptr_array(cores), ctypes.byref(out)))
         return out.value
+
+
+def _ctx_ws_methods():
+    """Warm-start entry points on a context (include/tt_warmstart.h)."""
+
+    def tt_ws_summary_dim(self, p: int) -> int:
+        return int(self.lib.tt_ws_summary_dim(self.ctx, int(p)))
+
+    def tt_ws_core_dim(self) -> int:
+        return int(self.lib.tt_ws_core_dim(self.ctx))
+
+    def tt_ws_summary(self, Y: Sequence, p: int, x, scale):
+        self._check(self.lib.tt_ws_summary(self.ctx, _ptr_array(Y), int(p), _ptr(x), _ptr(scale)))
+
+    def tt_canonicalize(self, cores: Sequence):
+        self._check(self.lib.tt_canonicalize(self.ctx, _ptr_array(cores)))
+
+    def tt_ws_pack(self, cores: Sequence, scale, y):
+        self._check(self.lib.tt_ws_pack(self.ctx, _ptr_array(cores), _ptr(scale), _ptr(y)))
+
+    def tt_ws_unpack(self, y, scale, cores: Sequence):
+        self._check(self.lib.tt_ws_unpack(self.ctx, _ptr(y), _ptr(scale), _ptr_array(cores)))
+
+    for f in (tt_ws_summary_dim, tt_ws_core_dim, tt_ws_summary, tt_canonicalize, tt_ws_pack, tt_ws_unpack):
+        setattr(Context, f.__name__, f)
+
+
+_ctx_ws_methods()
+
+
+class Mlp:
+    """Owns one tt_mlp (the warm-start network). Matrices are torch CUDA tensors, row-major FP32."""
+
+    def __init__(self, in_dim: int, hidden: int, out_dim: int, batch_max: int, lr: float = 1e-3,
+                 beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8, stream=None):
+        self.lib = load()
+        self.in_dim, self.hidden, self.out_dim, self.batch_max = in_dim, hidden, out_dim, batch_max
+        p = TtMlpParams(in_dim, hidden, out_dim, batch_max, lr, beta1, beta2, eps)
+        self.m = ctypes.c_void_p()
+        stream = _current_stream() if stream is None else stream
+        rc = self.lib.tt_mlp_init(ctypes.byref(self.m), ctypes.byref(p), stream)
+        if rc != TT_OK:
+            raise TtError(rc, "tt_mlp_init failed (see stderr)")
+
+    def close(self):
+        if self.m:
+            self.lib.tt_mlp_destroy(self.m)
+            self.m = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc: int):
+        if rc != TT_OK:
+            raise TtError(rc, self.lib.tt_mlp_last_error(self.m).decode())
+
+    def tt_mlp_set_weights(self, W1, b1, W2, b2, W3, b3):
+        self._check(self.lib.tt_mlp_set_weights(self.m, *[_ptr(t) for t in (W1, b1, W2, b2, W3, b3)]))
+
+    def tt_mlp_get_weights(self, W1, b1, W2, b2, W3, b3):
+        self._check(self.lib.tt_mlp_get_weights(self.m, *[_ptr(t) for t in (W1, b1, W2, b2, W3, b3)]))
+
+    def tt_mlp_forward(self, X, batch: int, Y, rows=None, ldx: Optional[int] = None, ldy: Optional[int] = None):
+        self._check(self.lib.tt_mlp_forward(self.m, _ptr(X), int(ldx or self.in_dim), _ptr(rows), int(batch),
+                                            _ptr(Y), int(ldy or self.out_dim)))
+
+    def tt_mlp_loss_grads(self, X, T, batch: int, grads=None, rows=None, ldx=None, ldt=None) -> float:
+        loss = ctypes.c_double(0.0)
+        g = [_ptr(t) for t in grads] if grads is not None else [None] * 6
+        self._check(self.lib.tt_mlp_loss_grads(self.m, _ptr(X), int(ldx or self.in_dim), _ptr(T),
+                                               int(ldt or self.out_dim), _ptr(rows), int(batch),
+                                               ctypes.byref(loss), *g))
+        return loss.value
+
+    def tt_mlp_train_step(self, X, T, batch: int, rows=None, ldx=None, ldt=None, want_loss: bool = False):
+        loss = ctypes.c_double(0.0)
+        self._check(self.lib.tt_mlp_train_step(self.m, _ptr(X), int(ldx or self.in_dim), _ptr(T),
+                                               int(ldt or self.out_dim), _ptr(rows), int(batch),
+                                               ctypes.byref(loss) if want_loss else None))
+        return loss.value if want_loss else None
+
+
+def tt_mlp_gemm_bf16(A, B, C, M: int, N: int, K: int, lda: int, ldb: int, ldc: int, check: bool = True,
+                     stream=None) -> int:
+    """C = A B^T on BF16 row-major device tensors (torch.bfloat16 or int16 views); returns the status."""
+    L = load()
+    stream = _current_stream() if stream is None else stream
+    return L.tt_mlp_gemm_bf16(_ptr(A), int(lda), _ptr(B), int(ldb), int(M), int(N), int(K), _ptr(C), int(ldc),
+                              1 if check else 0, stream)
 
 
 def tt_prox_update_noalloc(Y, SH, core, J: int, n: int, r0: int, r1: int, sigma: float, stream=None) -> int:

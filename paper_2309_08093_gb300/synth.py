@@ -315,3 +315,45 @@ def batched_tensor_gpu(spec, device="cuda"):
         raise ValueError("device generation covers f32 and bf16 storage")
     init = random_cores(spec["dims"], spec["ranks"], np.random.default_rng([spec["tensor_seed"], STREAM_INIT]))
     return a, init
+
+
+# ---------------------------------------------------------------------------------------------
+# learned warm start: a family of order-4 tensors with smooth (cumulative-sum) TT cores and 1%
+# noise, one member per seed; plus the seeded initial weights of the network
+
+def warmstart_spec(dims=(256, 256, 3, 128), ranks=(1, 20, 3, 20, 1), J=2048, lam=1e-3, noise=1e-2):
+    return {"dims": list(dims), "ranks": list(ranks), "J": J, "lam": lam, "noise": noise, "dtype": "f32"}
+
+
+def warmstart_tensor_gpu(spec, tensor_seed: int, device="cuda"):
+    """One member of the family on the device: seeded cumsum cores (numpy), their FP32 TT
+    contraction (TF32 off), Gaussian noise at spec['noise'] relative Frobenius norm (torch,
+    seeded). Returns (A, T, init) with A the noisy and T the noise-free flat FP32 tensor (mode 0
+    fastest) and init the seeded N(0,1) random initial cores (numpy)."""
+    import torch
+
+    torch.backends.cuda.matmul.allow_tf32 = False
+    dims, ranks = spec["dims"], spec["ranks"]
+    cores = random_cores(dims, ranks, np.random.default_rng([tensor_seed, STREAM_CORES]), "cumsum")
+    q = None
+    for g in cores:
+        gt = torch.as_tensor(np.ascontiguousarray(g), dtype=torch.float32, device=device)
+        q = gt[0].transpose(0, 1).contiguous() if q is None else torch.einsum("aib,ax->bix", gt, q).reshape(gt.shape[2], -1)
+    t = q.reshape(-1)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(tensor_seed) & (2**63 - 1))
+    e = torch.randn(t.numel(), generator=gen, device=device, dtype=torch.float32)
+    a = t + (spec["noise"] * torch.linalg.vector_norm(t) / torch.linalg.vector_norm(e)) * e
+    init = random_cores(dims, ranks, np.random.default_rng([tensor_seed, STREAM_INIT]), "normal")
+    return a, t, init
+
+
+def mlp_init(in_dim: int, hidden: int, out_dim: int, seed: int):
+    """Seeded initial weights of the in -> hidden -> hidden -> out network (numpy FP32, row-major):
+    hidden layers N(0, 2 / fan_in) (He et al., 2015), output layer N(0, 1 / fan_in), zero biases."""
+    rng = np.random.default_rng([seed, 11])
+    f32 = np.float32
+    W1 = (rng.standard_normal((hidden, in_dim)) * np.sqrt(2.0 / in_dim)).astype(f32)
+    W2 = (rng.standard_normal((hidden, hidden)) * np.sqrt(2.0 / hidden)).astype(f32)
+    W3 = (rng.standard_normal((out_dim, hidden)) * np.sqrt(1.0 / hidden)).astype(f32)
+    return [W1, np.zeros(hidden, f32), W2, np.zeros(hidden, f32), W3, np.zeros(out_dim, f32)]

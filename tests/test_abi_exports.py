@@ -1,5 +1,5 @@
 """The C-ABI library builds for sm_103a, loads, and exports every function that
-include/tt_sketch.h declares (no compute calls: CPU only)."""
+include/*.h declares (no compute calls: CPU only)."""
 import ctypes
 import os
 import re
@@ -16,7 +16,7 @@ def _declared():
         if fn.endswith(".h"):
             src = open(os.path.join(ROOT, "include", fn)).read()
             src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-            names |= set(re.findall(r"^\s*(?:int|void|const char\*)\s+(tt_\w+)\s*\(", src, flags=re.M))
+            names |= set(re.findall(r"^\s*(?:int64_t|int|void|const char\*)\s+(tt_\w+)\s*\(", src, flags=re.M))
     return names
 
 

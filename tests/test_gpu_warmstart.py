@@ -1,0 +1,268 @@
+"""Learned warm start on the GPU against the warm-start oracle: network gradients and Adam steps,
+the sketch summary, the right-canonical gauge, target packing, and the gain of the trained
+network over random initialisation on a reduced member of the smooth-core tensor family."""
+import math
+
+import numpy as np
+import pytest
+
+import tt_oracle as O
+import tt_warmstart as W
+from paper_2309_08093_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2309_08093_gb300 import build as _build  # noqa: E402
+
+_build.build()
+from paper_2309_08093_gb300 import lib  # noqa: E402
+
+NAMES = ("W1", "b1", "W2", "b2", "W3", "b3")
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.ravel(a - b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
+
+
+def _net_case(n_in, hid, n_out, batch, seed, lr=1e-3):
+    rng = np.random.default_rng(seed)
+    P = dict(zip(NAMES, synth.mlp_init(n_in, hid, n_out, seed)))
+    for k in ("b1", "b2", "b3"):
+        P[k] = (0.1 * rng.standard_normal(P[k].shape)).astype(np.float32)
+    X = rng.standard_normal((batch, n_in)).astype(np.float32)
+    T = (0.5 * rng.standard_normal((batch, n_out))).astype(np.float32)
+    net = lib.Mlp(n_in, hid, n_out, batch, lr=lr)
+    net.tt_mlp_set_weights(*[_dev(P[k]) for k in NAMES])
+    return net, P, X, T
+
+
+def _gpu_grads(net, Xd, Td, batch, P):
+    g = [torch.zeros(P[k].shape, device="cuda") for k in NAMES]
+    loss = net.tt_mlp_loss_grads(Xd, Td, batch, g)
+    return loss, {k: t.cpu().numpy().astype(np.float64) for k, t in zip(NAMES, g)}
+
+
+@pytest.mark.parametrize("n_in,hid,n_out,batch,exact", [(100, 64, 70, 37, False), (64, 128, 64, 64, False),
+                                                        (5144, 512, 23220, 16, False), (100, 64, 70, 37, True)])
+def test_gradients_match_oracle(n_in, hid, n_out, batch, exact):
+    """The oracle rounds the same GEMM operands to BF16, so the two sides differ by FP32
+    accumulation order (over K up to 23220 terms), erf/exp rounding, and the BF16 rounding flips
+    these cause: an activation whose FP32 value lies within the accumulation error of a BF16
+    rounding boundary rounds the other way on one side (2^-8 relative in that element). With
+    generic operands a few flips per layer are expected: bounds 3e-3 relative Frobenius error per
+    gradient and 2e-4 on the loss. With dyadic operands (integer inputs, weights and biases
+    multiples of 1/16) on a small network the first layer's sums are exact in FP32 and the other
+    accumulations short, flips become rare, and the bound is 1e-5. (On the full-size network the
+    23220-term backward sums bring the flips back.)"""
+    net, P, X, T = _net_case(n_in, hid, n_out, batch, 21 + n_in)
+    if exact:
+        rng = np.random.default_rng(99)
+        X = rng.integers(-2, 3, size=X.shape).astype(np.float32)
+        for k in NAMES:
+            scale = 1.0 / math.sqrt(P[k].shape[-1]) if k.startswith("W") else 0.1
+            P[k] = (np.round(rng.standard_normal(P[k].shape) * scale * 16) / 16).astype(np.float32)
+        net.tt_mlp_set_weights(*[_dev(P[k]) for k in NAMES])
+    loss, g = _gpu_grads(net, _dev(X), _dev(T), batch, P)
+    P64 = {k: v.astype(np.float64) for k, v in P.items()}
+    l_ref, g_ref, _ = W.mlp_loss_grads(P64, X.astype(np.float64), T.astype(np.float64), bf16=True)
+    errs = {k: _rel(g[k], g_ref[k]) for k in NAMES}
+    print(f"\nshape {(n_in, hid, n_out, batch)} exact={exact}: loss rel err {abs(loss - l_ref) / l_ref:.2e}, "
+          "gradients " + ", ".join(f"{k} {e:.2e}" for k, e in errs.items()))
+    tol_l, tol_g = (1e-5, 1e-5) if exact else (2e-4, 3e-3)
+    assert abs(loss - l_ref) <= tol_l * l_ref
+    for k in NAMES:
+        assert errs[k] <= tol_g, (k, errs[k])
+    net.close()
+
+
+def test_row_gather_matches_contiguous_rows():
+    net, P, X, T = _net_case(96, 64, 80, 50, 5)
+    rows = np.random.default_rng(3).permutation(50)[:20].astype(np.int32)
+    l1 = net.tt_mlp_loss_grads(_dev(X), _dev(T), 20, rows=torch.from_numpy(rows).cuda())
+    l2 = net.tt_mlp_loss_grads(_dev(X[rows]), _dev(T[rows]), 20)
+    assert abs(l1 - l2) <= 1e-12 * l2
+    Y = torch.zeros(20, 80, device="cuda")
+    net.tt_mlp_forward(_dev(X[rows]), 20, Y)
+    ref, _ = W.mlp_forward({k: v.astype(np.float64) for k, v in P.items()}, X[rows].astype(np.float64), bf16=True)
+    assert _rel(Y.cpu().numpy(), ref) <= 1e-5
+    net.close()
+
+
+def test_adam_steps_match_oracle():
+    """Two training steps: the update of every parameter equals the oracle's Adam applied to the
+    network's own gradients (which the gradient test pins), up to FP32 rounding."""
+    lr = 1e-3
+    net, P, X, T = _net_case(100, 64, 70, 37, 9, lr=lr)
+    Xd, Td = _dev(X), _dev(T)
+    cur = {k: v.astype(np.float64) for k, v in P.items()}
+    m = {k: np.zeros_like(v) for k, v in cur.items()}
+    v = {k: np.zeros_like(x) for k, x in cur.items()}
+    for t in (1, 2):
+        _, g = _gpu_grads(net, Xd, Td, 37, P)
+        net.tt_mlp_train_step(Xd, Td, 37)
+        for k in NAMES:
+            cur[k], m[k], v[k] = W.adam_step(cur[k], g[k], m[k], v[k], t, lr, 0.9, 0.999, 1e-8)
+    out = [torch.zeros(P[k].shape, device="cuda") for k in NAMES]
+    net.tt_mlp_get_weights(*out)
+    for k, o in zip(NAMES, out):
+        got = o.cpu().numpy().astype(np.float64)
+        assert np.all(np.abs(got - cur[k]) <= 2.0 ** -22 * np.abs(cur[k]) + 1e-3 * lr), k
+    net.close()
+
+
+def test_training_reduces_loss():
+    net, P, X, T = _net_case(128, 256, 96, 256, 17, lr=2e-3)
+    Xd, Td = _dev(X), _dev(T)
+    first = net.tt_mlp_train_step(Xd, Td, 256, want_loss=True)
+    for _ in range(200):
+        net.tt_mlp_train_step(Xd, Td, 256)
+    last = net.tt_mlp_train_step(Xd, Td, 256, want_loss=True)
+    assert last < 0.1 * first, (first, last)
+    net.close()
+
+
+# ---------------------------------------------------------------------------------------------
+# summary, gauge, packing
+
+
+def test_summary_matches_oracle():
+    dims, ranks, J, seed, p = (12, 10, 8), (1, 3, 3, 1), 64, 41, 5
+    A64 = synth.quantize(synth.random_tensor(dims, 4), "f32")[2]
+    flat = np.asarray(A64, dtype=np.float32).ravel(order="F")
+    ctx = lib.Context(dims, ranks, J, 1e-3, seed, "f32")
+    Y = [torch.zeros(J * n, device="cuda") for n in dims]
+    ctx.tt_sketch_unfold(lib.device_tensor(flat, "f32"), -1, 0, Y)
+    x = torch.zeros(ctx.tt_ws_summary_dim(p), device="cuda")
+    s = torch.zeros(1, device="cuda")
+    ctx.tt_ws_summary(Y, p, x, s)
+    hs, vs = O.draw_sketch(seed, 0, dims, J)
+    x_ref, s_ref = W.ws_summary([O.sketch_unfolding(A64, hs, vs, J, k) for k in range(3)], p)
+    assert _rel(x.cpu().numpy(), x_ref) <= 1e-5
+    assert abs(float(s.item()) - s_ref) <= 1e-5 * s_ref
+    ctx.close()
+
+
+@pytest.mark.parametrize("dims,ranks", [((5, 6, 3, 4), (1, 4, 3, 4, 1)), ((5, 4, 1, 6), (1, 4, 2, 4, 1)),
+                                        ((24, 24, 3, 24), (1, 20, 3, 20, 1)), ((7, 9, 11), (1, 5, 6, 1))])
+def test_canonicalize_matches_oracle(dims, ranks):
+    rng = np.random.default_rng(sum(dims))
+    cs = [rng.standard_normal((ranks[k], dims[k], ranks[k + 1])).astype(np.float32).astype(np.float64)
+          for k in range(len(dims))]
+    ctx = lib.Context(dims, ranks, 64, 1e-3, 1, "f32")
+    dc = lib.device_cores(cs)
+    ctx.tt_canonicalize(dc)
+    got = lib.host_cores(dc, ranks, dims)
+    ref = W.canonicalize_right(cs)
+    for k in range(len(dims)):
+        scale = max(np.linalg.norm(ref[k]), 1e-30)
+        assert np.linalg.norm(got[k] - ref[k]) <= 1e-4 * scale, (k, np.linalg.norm(got[k] - ref[k]) / scale)
+    assert _rel(O.tt_full(got), O.tt_full(cs)) <= 1e-5
+    ctx.close()
+
+
+def test_pack_unpack_match_oracle():
+    dims, ranks = (7, 6, 3, 5), (1, 4, 3, 4, 1)
+    rng = np.random.default_rng(2)
+    cs = [rng.standard_normal((ranks[k], dims[k], ranks[k + 1])).astype(np.float32).astype(np.float64)
+          for k in range(4)]
+    ctx = lib.Context(dims, ranks, 64, 1e-3, 1, "f32")
+    y = torch.zeros(ctx.tt_ws_core_dim(), device="cuda")
+    s = torch.tensor([2.5], device="cuda")
+    ctx.tt_ws_pack(lib.device_cores(cs), s, y)
+    assert _rel(y.cpu().numpy(), W.ws_targets(cs, 2.5)) <= 1e-6
+    back = lib.device_cores([np.zeros_like(c) for c in cs])
+    ctx.tt_ws_unpack(y, s, back)
+    for a, b in zip(lib.host_cores(back, ranks, dims), cs):
+        assert _rel(a, b) <= 1e-6
+    ctx.close()
+
+
+# ---------------------------------------------------------------------------------------------
+# the gain of the trained network
+
+SUMMARY_SWEEP = 1 << 40  # the draw of the summary sketch: fixed, distinct from the sweeps' draws
+
+
+def _solve_targets(ctx, spec, seeds, p, nsw):
+    """(summary, target) pairs produced by the method: summary of the fixed summary sketch, then
+    nsw TT-TS sweeps from random cores, right-canonical gauge, packed target."""
+    dims = spec["dims"]
+    X = torch.zeros(len(seeds), ctx.tt_ws_summary_dim(p), device="cuda")
+    T = torch.zeros(len(seeds), ctx.tt_ws_core_dim(), device="cuda")
+    S = torch.zeros(len(seeds), device="cuda")
+    Y = [torch.zeros(spec["J"] * n, device="cuda") for n in dims]
+    for i, sd in enumerate(seeds):
+        A, _, init = synth.warmstart_tensor_gpu(spec, sd)
+        ctx.tt_sketch_unfold(A, -1, SUMMARY_SWEEP, Y)
+        ctx.tt_ws_summary(Y, p, X[i], S[i:i + 1])
+        cores = lib.device_cores(init)
+        ctx.tt_prox_als_sweep(A, cores, nsw, 0, rel_change=False)
+        ctx.tt_canonicalize(cores)
+        ctx.tt_ws_pack(cores, S[i:i + 1], T[i])
+    return X, T
+
+
+def _sweeps_to(ctx, A, Tn, cores, tol, max_sweeps):
+    errs = []
+    for t in range(max_sweeps):
+        ctx.tt_prox_als_sweep(A, cores, 1, t, rel_change=False)
+        errs.append(ctx.tt_rel_error(Tn, cores))
+    hit = next((i + 1 for i, e in enumerate(errs) if e <= tol), max_sweeps + 1)
+    return hit, errs
+
+
+def test_warm_start_beats_random_init():
+    """Reduced member of the family (64 x 64 x 3 x 32, ranks (1, 8, 3, 8, 1), J = 512, 1% noise):
+    1024 method-generated solves, the network trained on the GPU, then 12 held-out tensors swept
+    from the network's cores and from random cores. Error is measured against the noise-free
+    tensor (1e-2 = recovered to the noise level)."""
+    spec = synth.warmstart_spec(dims=(64, 64, 3, 32), ranks=(1, 8, 3, 8, 1), J=512)
+    p = 8
+    ctx = lib.Context(spec["dims"], spec["ranks"], spec["J"], spec["lam"], 1234, "f32")
+    X, T = _solve_targets(ctx, spec, list(range(1000, 2024)), p, 4)
+    n_in, n_out = X.shape[1], T.shape[1]
+    net = lib.Mlp(n_in, 512, n_out, 128, lr=1e-3)
+    net.tt_mlp_set_weights(*[_dev(w) for w in synth.mlp_init(n_in, 512, n_out, 7)])
+    rng = np.random.default_rng(5)
+    losses = []
+    for ep in range(60):
+        perm = torch.from_numpy(rng.permutation(X.shape[0]).astype(np.int32)).cuda()
+        for b in range(0, X.shape[0], 128):
+            want = (b == 0)
+            l = net.tt_mlp_train_step(X, T, 128, rows=perm[b:b + 128], want_loss=want)
+            if want:
+                losses.append(l)
+    assert losses[-1] < 0.5 * losses[0], losses
+    hits_w, hits_r, e1_w, e1_r = [], [], [], []
+    Y = [torch.zeros(spec["J"] * n, device="cuda") for n in spec["dims"]]
+    x = torch.zeros(1, n_in, device="cuda")
+    s = torch.zeros(1, device="cuda")
+    yo = torch.zeros(1, n_out, device="cuda")
+    for sd in range(50000, 50012):
+        A, Tn, init = synth.warmstart_tensor_gpu(spec, sd)
+        h, e = _sweeps_to(ctx, A, Tn, lib.device_cores(init), 1e-2, 6)
+        hits_r.append(h)
+        e1_r.append(e[0])
+        ctx.tt_sketch_unfold(A, -1, SUMMARY_SWEEP, Y)
+        ctx.tt_ws_summary(Y, p, x[0], s)
+        net.tt_mlp_forward(x, 1, yo)
+        cores = lib.device_cores(init)  # overwritten by the network's cores
+        ctx.tt_ws_unpack(yo[0], s, cores)
+        h, e = _sweeps_to(ctx, A, Tn, cores, 1e-2, 6)
+        hits_w.append(h)
+        e1_w.append(e[0])
+    print(f"\nwarm start: sweeps to 1e-2 warm {hits_w} (mean {np.mean(hits_w):.2f}) random {hits_r} "
+          f"(mean {np.mean(hits_r):.2f}); error after one sweep warm median {np.median(e1_w):.3e} random "
+          f"{np.median(e1_r):.3e}; loss {losses[0]:.4f} -> {losses[-1]:.4f}")
+    assert np.mean(hits_w) < np.mean(hits_r)
+    assert np.median(e1_w) < 0.5 * np.median(e1_r)
+    net.close()
+    ctx.close()
