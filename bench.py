@@ -40,7 +40,10 @@ def parse():
     ap.add_argument("--storage", default=None, help="override the workload's storage type")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-patterns", action="store_true", help="skip the BF16-form comparison")
+    ap.add_argument("--no-patterns", action="store_true", help="skip the precision/batched/warm-start patterns")
+    ap.add_argument("--only-pattern", default=None, choices=["precision", "batched", "warmstart"],
+                    help="run one pattern and print its JSON")
+    ap.add_argument("--ws-train", type=int, default=10240, help="warm-start training solves")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--cpu-columns", type=int, default=0, help=argparse.SUPPRESS)
     return ap.parse_args()
@@ -292,6 +295,151 @@ def batched_pattern(dev, nsweeps=10, count=256):
 
 
 # ---------------------------------------------------------------------------------------------
+# learned-warm-start pattern: the network (summary of the data sketch -> initial cores) trained
+# on method-generated solves of the 256 x 256 x 3 x 128 smooth-core family, then held-out tensors
+# swept from its cores and from random cores until the error against the noise-free tensor is
+# <= 1e-2
+
+WS_SUMMARY_SWEEP = 0  # the summary uses sweep 0's draw (fixed for a fixed seed); the first sweep reuses its plans
+
+
+def warmstart_pattern(dev, n_train=10240, n_eval=32, p=8, train_sweeps=4, epochs=40, mb=256, group=256,
+                      tol=1e-2, max_sweeps=8):
+    import numpy as np
+    import torch
+    from paper_2309_08093_gb300 import lib, synth
+
+    spec = synth.warmstart_spec()
+    dims, ranks, J = spec["dims"], spec["ranks"], spec["J"]
+    stream = torch.cuda.current_stream()
+    ctx = lib.Context(dims, ranks, J, spec["lam"], 1234, "f32")
+    n_in, n_out = ctx.tt_ws_summary_dim(p), ctx.tt_ws_core_dim()
+    n_train = (n_train + group - 1) // group * group
+    X = torch.zeros(n_train, n_in, device=dev)
+    T = torch.zeros(n_train, n_out, device=dev)
+    S = torch.zeros(n_train, device=dev)
+    Y = [torch.zeros(J * n, device=dev) for n in dims]
+    bspecs = [{"dims": dims, "ranks": ranks, "J": J, "lam": spec["lam"], "seed": 5000 + i, "dtype": "f32"}
+              for i in range(group)]
+    batch = lib.Batch(bspecs)
+    t0 = time.perf_counter()
+    for g0 in range(0, n_train, group):
+        As, cores = [], []
+        for i in range(g0, g0 + group):
+            A, _, init = synth.warmstart_tensor_gpu(spec, 100000 + i, device=dev)
+            ctx.tt_sketch_unfold(A, -1, WS_SUMMARY_SWEEP, Y)
+            ctx.tt_ws_summary(Y, p, X[i], S[i:i + 1])
+            As.append(A)
+            cores.append(lib.device_cores(init, device=dev))
+        batch.tt_batch_sweep(As, cores, train_sweeps, 0)
+        for j, i in enumerate(range(g0, g0 + group)):
+            ctx.tt_canonicalize(cores[j])
+            ctx.tt_ws_pack(cores[j], S[i:i + 1], T[i])
+        del As, cores
+    torch.cuda.synchronize()
+    datagen_s = time.perf_counter() - t0
+    batch.close()
+    torch.cuda.empty_cache()
+
+    net = lib.Mlp(n_in, 512, n_out, mb, lr=1e-3)
+    net.tt_mlp_set_weights(*[torch.from_numpy(w).to(dev) for w in synth.mlp_init(n_in, 512, n_out, 7)])
+    rng = np.random.default_rng(5)
+    losses, steps = [], 0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    train_ms = 0.0
+    for ep in range(epochs):
+        perm = torch.from_numpy(rng.permutation(n_train).astype(np.int32)).to(dev)
+        e0.record(stream)
+        for b in range(0, n_train - mb + 1, mb):
+            net.tt_mlp_train_step(X, T, mb, rows=perm[b:b + mb])
+            steps += 1
+        e1.record(stream)
+        torch.cuda.synchronize()
+        train_ms += e0.elapsed_time(e1)
+        if ep in (0, epochs - 1):
+            losses.append(net.tt_mlp_loss_grads(X, T, mb, rows=perm[:mb]))
+    flops_per_step = 2.0 * mb * (net.in_dim * 512 + 512 * 512 + 512 * n_out) * 3 - 2.0 * mb * net.in_dim * 512
+
+    def sweeps(A, Tn, cores, Ygiven=None):
+        """Sweeps until the error against the noise-free tensor is <= tol; the first sweep uses
+        the given sketches when the warm start already computed them (Y_k do not depend on the
+        cores). Returns the sweep count (None if not reached) and the device time of each sweep."""
+        errs, ms = [], []
+        for t in range(max_sweeps):
+            e0.record(stream)
+            if t == 0 and Ygiven is not None:
+                ctx.tt_prox_als_sweep_sketched(Ygiven, cores, 0)
+            else:
+                ctx.tt_prox_als_sweep(A, cores, 1, t, rel_change=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            errs.append(ctx.tt_rel_error(Tn, cores))
+            if errs[-1] <= tol:
+                break
+        return (len(errs) if errs[-1] <= tol else None), ms
+
+    res = {"random": [], "warm": []}
+    tt = {"random": [], "warm": []}
+    sweep_ms, first_ms, init_ms, parts = [], {"random": [], "warm": []}, [], []
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    x1 = torch.zeros(1, n_in, device=dev)
+    s1 = torch.zeros(1, device=dev)
+    y1 = torch.zeros(1, n_out, device=dev)
+    for e in range(n_eval):
+        A, Tn, init = synth.warmstart_tensor_gpu(spec, 900000 + e, device=dev)
+        h, ms = sweeps(A, Tn, lib.device_cores(init, device=dev))
+        res["random"].append(h)
+        tt["random"].append(sum(ms) if h else None)
+        first_ms["random"].append(ms[0])
+        sweep_ms += ms[1:]
+        cores = lib.device_cores(init, device=dev)
+        ev[0].record(stream)
+        ctx.tt_sketch_unfold(A, -1, WS_SUMMARY_SWEEP, Y)
+        ev[1].record(stream)
+        ctx.tt_ws_summary(Y, p, x1[0], s1)
+        ev[2].record(stream)
+        net.tt_mlp_forward(x1, 1, y1)
+        ev[3].record(stream)
+        ctx.tt_ws_unpack(y1[0], s1, cores)
+        ev[4].record(stream)
+        torch.cuda.synchronize()
+        init_ms.append(ev[0].elapsed_time(ev[4]))
+        parts.append([ev[i].elapsed_time(ev[i + 1]) for i in range(4)])
+        h, ms = sweeps(A, Tn, cores, Ygiven=Y)
+        res["warm"].append(h)
+        tt["warm"].append(init_ms[-1] + sum(ms) if h else None)
+        first_ms["warm"].append(ms[0])
+        sweep_ms += ms[1:]
+    net.close()
+    ctx.close()
+    t_sweep = float(np.median(sweep_ms))
+    t_init = float(np.median(init_ms))
+    out = {"workload": f"{'x'.join(map(str, dims))} FP32, TT ranks {ranks}, cumsum cores, 1% noise, J={J}",
+           "train_solves": n_train, "train_sweeps_per_solve": train_sweeps, "datagen_s": datagen_s,
+           "summary_width": n_in, "network": f"{n_in} -> 512 -> 512 -> {n_out}, GELU, BF16 tcgen05 GEMMs",
+           "train_steps": steps, "minibatch": mb, "train_ms": train_ms,
+           "train_tflops": flops_per_step * steps / (train_ms * 1e-3) / 1e12,
+           "loss_first_epoch": losses[0], "loss_last_epoch": losses[-1],
+           "eval_tensors": n_eval, "tolerance": tol,
+           "tolerance_note": "relative error against the noise-free tensor (1% noise: recovered to the noise level)",
+           "sweep_ms_median": t_sweep, "warm_init_ms_median": t_init,
+           "first_sweep_ms_median": {k: float(np.median(v)) for k, v in first_ms.items()},
+           "warm_init_parts_ms": dict(zip(["summary_unfold", "summary", "mlp_forward", "unpack"],
+                                          [float(x) for x in np.median(np.array(parts), axis=0)])),
+           "note": "warm form: the summary's sketches are the first sweep's data sketches (same draw), so the "
+                   "first sweep runs on them (tt_prox_als_sweep_sketched); times are CUDA-event sums per tensor"}
+    for k, hits in res.items():
+        ok = [h for h in hits if h is not None]
+        times = [t for t in tt[k] if t is not None]
+        mean_t = float(np.mean(times)) if times else None
+        out[k] = {"sweeps_to_tolerance": hits, "mean_sweeps": float(np.mean(ok)) if ok else None,
+                  "reached": len(ok), "time_to_tolerance_ms_mean": mean_t,
+                  "solves_per_s": (1e3 / mean_t) if mean_t else None}
+    return out
+
+
+# ---------------------------------------------------------------------------------------------
 # GPU arm
 
 def main():
@@ -308,6 +456,22 @@ def main():
 
     import numpy as np
     import torch
+
+    if args.only_pattern:
+        torch.cuda.set_device(0)
+        dev = torch.device("cuda", 0)
+        from paper_2309_08093_gb300 import build, synth
+
+        build.build()
+        if args.only_pattern == "batched":
+            out = batched_pattern(dev)
+        elif args.only_pattern == "warmstart":
+            out = warmstart_pattern(dev, n_train=args.ws_train)
+        else:
+            w = synth.WORKLOADS[args.workload]
+            out = precision_pattern(w, synth.make_problem(w, storage="f32"), dev, w.sweeps)
+        print(json.dumps({"pattern": args.only_pattern, **out}), flush=True)
+        return
 
     dist = None
     if world > 1:
@@ -414,6 +578,8 @@ def main():
         line["patterns"] = {"precision": precision_pattern(w, p, dev, w.sweeps)}
         torch.cuda.empty_cache()
         line["patterns"]["batched"] = batched_pattern(dev)
+        torch.cuda.empty_cache()
+        line["patterns"]["warmstart"] = warmstart_pattern(dev, n_train=args.ws_train)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
             res = run_cpu_child(["--workload", args.workload] + (["--storage", args.storage] if args.storage else []))

@@ -160,6 +160,17 @@ int tt_prox_als_sweep(tt_ctx* ctx, const void* A_dev, const float* scales_dev,
                       double* rel_change_out);
 
 /*
+ * One sweep of Algorithm 1 (draw `sweep`) whose data sketches are given: Y_dev[k] must hold
+ * Y_k = S A_(k)^T for that draw, as tt_sketch_unfold(ctx, A, scales, -1, sweep, Y_dev) returns
+ * them (J x n[k] column-major). The sketches of a sweep do not depend on the cores, so computing
+ * them beforehand and reusing them is exact; the tensor itself is not read. Used when the
+ * sketches were already computed for another purpose (the warm start's summary). Synchronises;
+ * returns as tt_prox_als_sweep.
+ */
+int tt_prox_als_sweep_sketched(tt_ctx* ctx, float* const* Y_dev, float* const* cores_dev,
+                               uint64_t sweep);
+
+/*
  * Relative error ||A - [[G_1, ..., G_d]]||_F / ||A||_F (Sec. 5) with FP64 accumulation.
  * Reads every entry of A once; synchronises and writes *out on the host.
  */

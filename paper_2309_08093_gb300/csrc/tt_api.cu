@@ -98,7 +98,7 @@ extern "C" int tt_orthogonalize(tt_ctx* c, float* const* cores, int direction, i
 
 // One outer iteration of Algorithm 1; change slots receive ||dG_k||^2, ||G_k||^2 per core.
 int tt_one_sweep(tt_ctx* c, const void* A, const float* scales, float* const* cores, uint64_t sweep,
-                     double* change_slots) {
+                     double* change_slots, float* const* Ygiven) {
   const int d = c->d;
   for (int kk = d - 1; kk >= 1; --kk) TT_TRY(tt_launch_lq_right(c, cores[kk - 1], cores[kk], kk));
   TT_TRY(tt_ensure_tables(c, sweep));
@@ -107,8 +107,10 @@ int tt_one_sweep(tt_ctx* c, const void* A, const float* scales, float* const* co
   TT_TRY(tt_launch_prefix_reset(c));
   for (int k = 0; k < d; ++k) {
     TT_TRY(tt_launch_interface_from_chain(c, k, c->d_SH));
-    TT_TRY(tt_launch_unfold(c, A, scales, k, c->d_Y));
-    TT_TRY(tt_launch_prox_update(c, c->d_Y, c->d_SH, cores[k], k, change_slots ? change_slots + 2 * k : nullptr));
+    const float* Yk = c->d_Y;
+    if (Ygiven) Yk = Ygiven[k];  // the sketches do not depend on the cores: computed beforehand
+    else TT_TRY(tt_launch_unfold(c, A, scales, k, c->d_Y));
+    TT_TRY(tt_launch_prox_update(c, Yk, c->d_SH, cores[k], k, change_slots ? change_slots + 2 * k : nullptr));
     if (k < d - 1) {
       TT_TRY(tt_launch_qr_left(c, cores[k], cores[k + 1], k));
       TT_TRY(tt_launch_core_fft(c, cores[k], k));
@@ -116,6 +118,18 @@ int tt_one_sweep(tt_ctx* c, const void* A, const float* scales, float* const* co
     }
   }
   return TT_OK;
+}
+
+extern "C" int tt_prox_als_sweep_sketched(tt_ctx* c, float* const* Y, float* const* cores, uint64_t sweep) {
+  if (!c) return TT_EINVAL;
+  if (!Y) return tt_fail(c, TT_EINVAL, "null sketch array");
+  for (int k = 0; k < c->d; ++k)
+    if (!Y[k]) return tt_fail(c, TT_EINVAL, "null sketch pointer %d", k);
+  TT_TRY(tt_check_cores(c, cores));
+  c->err.clear();
+  TT_TRY(tt_reset_status(c));
+  TT_TRY(tt_one_sweep(c, nullptr, nullptr, cores, sweep, nullptr, Y));
+  return tt_read_status(c);
 }
 
 extern "C" int tt_prox_als_sweep(tt_ctx* c, const void* A, const float* scales, float* const* cores,

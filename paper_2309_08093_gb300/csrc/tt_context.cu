@@ -297,7 +297,7 @@ int tt_ensure_plan0(tt_ctx* c) { return tt_ensure_rplan(c, 0); }
 static void free_all(tt_ctx* c) {
   void* ps[] = {c->d_h, c->d_v, c->d_plan0, c->d_plan0_off, c->d_plan0_cursor, c->d_ghat,
                 c->d_twiddle, c->d_suffix, c->d_prefix, c->d_prefix_tmp, c->d_SH, c->d_Y,
-                c->d_gram, c->d_core_old, c->d_changes, c->d_status, c->d_err_acc};
+                c->d_gram, c->d_core_old, c->d_changes, c->d_status, c->d_err_acc, c->d_ws_acc};
   for (void* p : ps)
     if (p) cudaFree(p);
   if (c->d_A_stage) cudaFree(c->d_A_stage);
@@ -401,6 +401,7 @@ extern "C" int tt_sketch_init(tt_ctx** out, const tt_params* p, void* stream) {
   A((void**)&c->d_changes, sizeof(double) * 2 * c->changes_cap);
   A((void**)&c->d_status, sizeof(int));
   A((void**)&c->d_err_acc, sizeof(double) * 4);
+  A((void**)&c->d_ws_acc, sizeof(double) * 2);
   if (e != cudaSuccess) {
     free_all(c);
     fprintf(stderr, "tt_sketch_init: cudaMalloc: %s\n", cudaGetErrorString(e));

@@ -79,6 +79,7 @@ struct tt_ctx {
   double* d_changes = nullptr; // per (sweep, k): ||dG||^2, ||G||^2
   int* d_status = nullptr;     // device error flag (0 = ok, else TT_E* code)
   double* d_err_acc = nullptr; // rel-error accumulators (2 doubles)
+  double* d_ws_acc = nullptr;  // warm-start summary accumulators (2 doubles)
   int changes_cap = 0;
 
   // measurement counters (tt_profile_*)
@@ -163,7 +164,7 @@ int tt_check_cores(tt_ctx* c, float* const* cores);
     if (_rc) return _rc;     \
   } while (0)
 int tt_one_sweep(tt_ctx* c, const void* A, const float* scales, float* const* cores, uint64_t sweep,
-                 double* change_slots);
+                 double* change_slots, float* const* Ygiven = nullptr);
 int tt_prof_begin(tt_ctx* c, int k);   // record a start event when profiling (returns TT_OK)
 int tt_prof_end(tt_ctx* c);
 int tt_elem_bytes(int dtype);

@@ -24,6 +24,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -60,6 +61,8 @@ struct GemmArgs {
   bf16* ht;           // BF16 transposed output: ht[col * ldt + row]
   int ldt;
   int* err;           // device flag set to 1 when a bounded wait gave up
+  int kchunk;         // split-K: columns of K per blockIdx.z (multiple of GK)
+  int64_t slab;       // split-K: element offset between the FP32 outputs of consecutive splits
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -190,7 +193,8 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tn(GemmArgs g) {
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m0 = blockIdx.y * GM, n0 = blockIdx.x * GN;
-  const int KT = g.K / GK;
+  const int kbeg = blockIdx.z * g.kchunk;
+  const int KT = (min(g.K, kbeg + g.kchunk) - kbeg) / GK;
 
   if (tid == 0) {
     for (int s = 0; s < GSTAGES; ++s) mbar_init(smem_u32(&mbar[s]), 1);
@@ -210,12 +214,12 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tn(GemmArgs g) {
   const uint32_t tmem = *s_tmem;
   const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
 
-  load_tile(a0, g.A, g.lda, g.M, m0, 0, tid);
-  load_tile(b0, g.B, g.ldb, g.N, n0, 0, tid);
+  load_tile(a0, g.A, g.lda, g.M, m0, kbeg, tid);
+  load_tile(b0, g.B, g.ldb, g.N, n0, kbeg, tid);
   cp_async_commit();
   if (KT > 1) {
-    load_tile(a0 + A_STAGE, g.A, g.lda, g.M, m0, GK, tid);
-    load_tile(b0 + B_STAGE, g.B, g.ldb, g.N, n0, GK, tid);
+    load_tile(a0 + A_STAGE, g.A, g.lda, g.M, m0, kbeg + GK, tid);
+    load_tile(b0 + B_STAGE, g.B, g.ldb, g.N, n0, kbeg + GK, tid);
   }
   cp_async_commit();
 
@@ -244,8 +248,8 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tn(GemmArgs g) {
     }
     if (kt + 2 < KT) {
       const int s2 = (kt + 2) % GSTAGES;
-      load_tile(a0 + s2 * A_STAGE, g.A, g.lda, g.M, m0, (kt + 2) * GK, tid);
-      load_tile(b0 + s2 * B_STAGE, g.B, g.ldb, g.N, n0, (kt + 2) * GK, tid);
+      load_tile(a0 + s2 * A_STAGE, g.A, g.lda, g.M, m0, kbeg + (kt + 2) * GK, tid);
+      load_tile(b0 + s2 * B_STAGE, g.B, g.ldb, g.N, n0, kbeg + (kt + 2) * GK, tid);
     }
     cp_async_commit();
   }
@@ -270,7 +274,7 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tn(GemmArgs g) {
       const int col0 = n0 + c0;
       if (EPI == EPI_F32) {
         if (row_ok) {
-          float* out = g.f32 + (int64_t)row * g.ldf + col0;
+          float* out = g.f32 + blockIdx.z * g.slab + (int64_t)row * g.ldf + col0;
 #pragma unroll
           for (int j = 0; j < 32; ++j)
             if (col0 + j < g.N) out[j] = __uint_as_float(r[j]) + (g.bias ? g.bias[col0 + j] : 0.0f);
@@ -330,6 +334,40 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tn(GemmArgs g) {
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
   if (failed && tid == 0 && g.err) atomicExch(g.err, 1);
+}
+
+// Split-K epilogue: v = sum of the nsplit FP32 partial products (fixed order), then the fused
+// epilogue of EPI as in k_gemm_tn. 32 x 32 tiles; transposed BF16 stores go through shared memory.
+template <int EPI>
+__global__ void k_splitk_epi(const float* __restrict__ ws, int nsplit, int64_t slab, GemmArgs g) {
+  __shared__ float tile[32][33];
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    const int row = r0 + y, col = c0 + threadIdx.x;
+    float v = 0.0f;
+    if (row < g.M && col < g.N) {
+      for (int z = 0; z < nsplit; ++z) v += ws[z * slab + (int64_t)row * g.N + col];
+      if (EPI == EPI_F32) {
+        g.f32[(int64_t)row * g.ldf + col] = v + (g.bias ? g.bias[col] : 0.0f);
+      } else if (EPI == EPI_GELU) {
+        const float z = v + g.bias[col];
+        g.f32[(int64_t)row * g.ldf + col] = z;
+        v = gelu_f(z);
+        g.hb[(int64_t)row * g.ldh + col] = __float2bfloat16_rn(v);
+      } else {
+        v = v * gelu_grad_f(g.zin[(int64_t)row * g.ldf + col]);
+        g.f32[(int64_t)row * g.ldf + col] = v;
+        g.hb[(int64_t)row * g.ldh + col] = __float2bfloat16_rn(v);
+      }
+    }
+    tile[y][threadIdx.x] = v;
+  }
+  if (EPI == EPI_F32) return;
+  __syncthreads();
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    const int col = c0 + y, row = r0 + threadIdx.x;
+    if (col < g.N && row < g.M) g.ht[(int64_t)col * g.ldt + row] = __float2bfloat16_rn(tile[threadIdx.x][y]);
+  }
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -481,6 +519,8 @@ struct tt_mlp {
   bf16 *dYb = nullptr, *dYt = nullptr, *dZ1b = nullptr, *dZ1t = nullptr, *dZ2b = nullptr, *dZ2t = nullptr;
   double* d_loss = nullptr;
   int* d_err = nullptr;
+  float* ws = nullptr;      // split-K partial products
+  int64_t ws_cap = 0;       // floats
   int64_t launches = 0;
 };
 
@@ -514,22 +554,56 @@ int mfail(tt_mlp* m, int code, const char* fmt, ...) {
   } while (0)
 
 template <int EPI>
-int launch_gemm(tt_mlp* m, const GemmArgs& g, cudaStream_t s) {
+int launch_tiles(tt_mlp* m, const GemmArgs& g, int nsplit, cudaStream_t s) {
   static bool attr_done = false;  // per template instance; the attribute is per function
   if (!attr_done) {
     cudaError_t e = cudaFuncSetAttribute(k_gemm_tn<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, GEMM_SMEM);
     if (e != cudaSuccess) return mfail(m, TT_ECUDA, "gemm smem attribute: %s", cudaGetErrorString(e));
     attr_done = true;
   }
-  dim3 grid((g.N + GN - 1) / GN, (g.M + GM - 1) / GM);
+  dim3 grid((g.N + GN - 1) / GN, (g.M + GM - 1) / GM, nsplit);
   k_gemm_tn<EPI><<<grid, 128, GEMM_SMEM, s>>>(g);
   MLP_LAUNCH(m, "k_gemm_tn");
+  return TT_OK;
+}
+
+// Number of K splits: enough CTAs to cover the SMs when the tile grid is small, at least four
+// K tiles per split, at most 32 splits, and partial products that fit the workspace.
+int choose_split(int M, int N, int K, int64_t cap) {
+  const int tiles = ((M + GM - 1) / GM) * ((N + GN - 1) / GN);
+  const int KT = K / GK;
+  if (tiles >= 100 || KT < 8) return 1;
+  int s = std::min(KT / 4, (148 + tiles - 1) / tiles);
+  s = std::min(s, 32);
+  while (s > 1 && (int64_t)s * M * N > cap) --s;
+  return std::max(s, 1);
+}
+
+template <int EPI>
+int launch_gemm(tt_mlp* m, const GemmArgs& g, cudaStream_t s) {
+  const int split = m ? choose_split(g.M, g.N, g.K, m->ws_cap) : 1;
+  if (split <= 1) return launch_tiles<EPI>(m, g, 1, s);
+  const int KT = g.K / GK;
+  const int kchunk = ((KT + split - 1) / split) * GK;
+  const int nsplit = (g.K + kchunk - 1) / kchunk;
+  GemmArgs p = g;
+  p.kchunk = kchunk;
+  p.slab = (int64_t)g.M * g.N;
+  p.f32 = m->ws;
+  p.ldf = g.N;
+  p.bias = nullptr;
+  MLP_TRY(launch_tiles<EPI_F32>(m, p, nsplit, s));
+  dim3 grid((g.N + 31) / 32, (g.M + 31) / 32), blk(32, 8);
+  k_splitk_epi<EPI><<<grid, blk, 0, s>>>(m->ws, nsplit, p.slab, g);
+  MLP_LAUNCH(m, "k_splitk_epi");
   return TT_OK;
 }
 
 GemmArgs gemm_args(const bf16* A, int lda, const bf16* B, int ldb, int M, int N, int K, int* err) {
   GemmArgs g{};
   g.A = A; g.lda = lda; g.B = B; g.ldb = ldb; g.M = M; g.N = N; g.K = K; g.err = err;
+  g.kchunk = K;
+  g.slab = 0;
   return g;
 }
 
@@ -671,7 +745,8 @@ extern "C" int tt_mlp_init(tt_mlp** out, const tt_mlp_params* p, void* cuda_stre
               {(void**)&m->H2b, bp * h * 2}, {(void**)&m->H2t, h * bp * 2}, {(void**)&m->dYb, bp * op * 2},
               {(void**)&m->dYt, op * bp * 2}, {(void**)&m->dZ1b, bp * h * 2}, {(void**)&m->dZ1t, h * bp * 2},
               {(void**)&m->dZ2b, bp * h * 2}, {(void**)&m->dZ2t, h * bp * 2}, {(void**)&m->d_loss, 8},
-              {(void**)&m->d_err, 4}};
+              {(void**)&m->d_err, 4}, {(void**)&m->ws, (size_t)32 * bp * h * 4}};
+  m->ws_cap = (int64_t)32 * bp * h;
   for (auto& b : bufs) {
     if (cudaMalloc(b.p, b.bytes) != cudaSuccess) return fail("activations");
     cudaMemset(*b.p, 0, b.bytes);
@@ -689,7 +764,7 @@ extern "C" int tt_mlp_destroy(tt_mlp* m) {
   }
   void* ps[] = {m->W1b, m->W2b, m->W2t, m->W3b, m->W3t, m->Xb, m->XbT, m->Z1, m->Z2, m->Y, m->dY, m->dZ1, m->dZ2,
                 m->H1b, m->H1t, m->H2b, m->H2t, m->dYb, m->dYt, m->dZ1b, m->dZ1t, m->dZ2b, m->dZ2t, m->d_loss,
-                m->d_err};
+                m->d_err, m->ws};
   for (void* p : ps) cudaFree(p);
   delete m;
   return TT_OK;

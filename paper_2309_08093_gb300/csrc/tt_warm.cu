@@ -1,7 +1,7 @@
 // Learned warm start: the network's input and output on a TT-TS context (include/tt_warmstart.h).
 //
-//   k_ws_summary  : rows 0..p-1 of every data sketch Y_k, normalised by their root mean square,
-//                   and ||Y_0||_F (one CTA, FP64 reductions)
+//   k_ws_summary_sums / k_ws_summary_write : rows 0..p-1 of every data sketch Y_k, normalised
+//                   by their root mean square, and ||Y_0||_F (grid-wide FP64 sums, then the writes)
 //   k_canon_step  : one step k of the right-to-left SVD pass of the right-canonical gauge
 //                   (one CTA): C = G_k^R G_k^R^T in FP64, eigen-decomposition of C by parallel
 //                   cyclic Jacobi rotations (Golub and Van Loan, Matrix Computations, Sec. 8.5:
@@ -10,6 +10,8 @@
 //                   G_{k-1} <- G_{k-1} x_3 (U S)
 //   k_ws_pack / k_ws_unpack : cores <-> network target vector
 #include <math.h>
+
+#include <algorithm>
 
 #include "../../include/tt_warmstart.h"
 #include "tt_internal.cuh"
@@ -50,39 +52,53 @@ struct SummaryArgs {
   int64_t n[TT_MAX_D];
   int64_t xoff[TT_MAX_D + 1];
   int d, J, p;
+  int64_t y0_vec4;  // entries of Y_0 read as float4 (0 when Y_0 is not 16-byte aligned)
   float* x;
   float* scale;
 };
 
-__global__ void __launch_bounds__(1024) k_ws_summary(SummaryArgs a) {
+__device__ __forceinline__ float summary_value(const SummaryArgs& a, int64_t e) {
+  int k = 0;
+  while (e >= a.xoff[k + 1]) ++k;
+  const int64_t loc = e - a.xoff[k];
+  return a.Y[k][(loc / a.p) * a.J + loc % a.p];
+}
+
+// acc[0] += sum of squares of the summary entries, acc[1] += ||Y_0||_F^2 (grid-wide, FP64)
+__global__ void __launch_bounds__(256) k_ws_summary_sums(SummaryArgs a, double* __restrict__ acc) {
   __shared__ double red[32];
   const int64_t total = a.xoff[a.d];
-  double ss = 0.0;
-  for (int64_t e = threadIdx.x; e < total; e += blockDim.x) {
-    int k = 0;
-    while (e >= a.xoff[k + 1]) ++k;
-    const int64_t loc = e - a.xoff[k];
-    const int64_t i = loc / a.p, b = loc % a.p;
-    const double v = a.Y[k][i * a.J + b];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double ss = 0.0, y0 = 0.0;
+  for (int64_t e = t0; e < total; e += stride) {
+    const double v = summary_value(a, e);
     ss += v * v;
   }
-  double y0 = 0.0;
-  const int64_t n0 = a.n[0] * a.J;
-  for (int64_t e = threadIdx.x; e < n0; e += blockDim.x) {
+  const float4* Y0 = (const float4*)a.Y[0];
+  const int64_t n4 = a.y0_vec4;
+  for (int64_t e = t0; e < n4; e += stride) {
+    const float4 q = Y0[e];
+    y0 += (double)q.x * q.x + (double)q.y * q.y + (double)q.z * q.z + (double)q.w * q.w;
+  }
+  for (int64_t e = 4 * n4 + t0; e < a.n[0] * a.J; e += stride) {
     const double v = a.Y[0][e];
     y0 += v * v;
   }
   ss = block_sum(ss, red);
   y0 = block_sum(y0, red);
-  const double inv = ss > 0.0 ? 1.0 / sqrt(ss / (double)total) : 0.0;
-  for (int64_t e = threadIdx.x; e < total; e += blockDim.x) {
-    int k = 0;
-    while (e >= a.xoff[k + 1]) ++k;
-    const int64_t loc = e - a.xoff[k];
-    const int64_t i = loc / a.p, b = loc % a.p;
-    a.x[e] = (float)((double)a.Y[k][i * a.J + b] * inv);
+  if (threadIdx.x == 0) {
+    if (ss != 0.0) atomicAdd(&acc[0], ss);
+    if (y0 != 0.0) atomicAdd(&acc[1], y0);
   }
-  if (threadIdx.x == 0) *a.scale = (float)sqrt(y0);
+}
+
+__global__ void __launch_bounds__(256) k_ws_summary_write(SummaryArgs a, const double* __restrict__ acc) {
+  const int64_t total = a.xoff[a.d];
+  const double inv = acc[0] > 0.0 ? 1.0 / sqrt(acc[0] / (double)total) : 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
+    a.x[e] = (float)((double)summary_value(a, e) * inv);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *a.scale = (float)sqrt(acc[1]);
 }
 
 // One step of the right-to-left SVD pass at core k: W = G_k^R (r x m, element (a, c) at
@@ -301,6 +317,7 @@ extern "C" int tt_ws_summary(tt_ctx* c, float* const* Y, int p, float* x, float*
   a.p = p;
   a.x = x;
   a.scale = scale;
+  a.y0_vec4 = ((uintptr_t)Y[0] & 15) ? 0 : (c->n[0] * c->J) / 4;
   a.xoff[0] = 0;
   for (int k = 0; k < c->d; ++k) {
     if (!Y[k]) return tt_fail(c, TT_EINVAL, "null sketch pointer %d", k);
@@ -308,8 +325,14 @@ extern "C" int tt_ws_summary(tt_ctx* c, float* const* Y, int p, float* x, float*
     a.n[k] = c->n[k];
     a.xoff[k + 1] = a.xoff[k] + (int64_t)p * c->n[k];
   }
-  k_ws_summary<<<1, 1024, 0, c->stream>>>(a);
-  TT_LAUNCH(c, "k_ws_summary");
+  int dev = 0, sms = 0;
+  TT_CUDA(c, cudaGetDevice(&dev));
+  TT_CUDA(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  TT_CUDA(c, cudaMemsetAsync(c->d_ws_acc, 0, 2 * sizeof(double), c->stream));
+  k_ws_summary_sums<<<sms, 256, 0, c->stream>>>(a, c->d_ws_acc);
+  TT_LAUNCH(c, "k_ws_summary_sums");
+  k_ws_summary_write<<<(unsigned)std::min<int64_t>(sms, (a.xoff[a.d] + 255) / 256), 256, 0, c->stream>>>(a, c->d_ws_acc);
+  TT_LAUNCH(c, "k_ws_summary_write");
   return TT_OK;
 }
 

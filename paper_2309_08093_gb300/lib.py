@@ -25,6 +25,7 @@ EXPORTS = ["tt_sketch_init", "tt_sketch_destroy", "tt_last_error", "tt_sketch_ta
            "tt_orthogonalize", "tt_prox_als_sweep", "tt_rel_error", "tt_prox_als_sweep_host",
            "tt_profile_enable", "tt_profile_read", "tt_prox_update_noalloc", "tt_batch_init",
            "tt_batch_destroy", "tt_batch_last_error", "tt_batch_sweep", "tt_batch_rel_error",
+           "tt_prox_als_sweep_sketched",
            # learned warm start (include/tt_warmstart.h)
            "tt_mlp_init", "tt_mlp_destroy", "tt_mlp_last_error", "tt_mlp_set_weights", "tt_mlp_get_weights",
            "tt_mlp_forward", "tt_mlp_loss_grads", "tt_mlp_train_step", "tt_mlp_gemm_bf16",
@@ -84,6 +85,7 @@ def load(path: str = LIB_PATH):
     L.tt_orthogonalize.argtypes = [vp, ctypes.POINTER(vp), i, i]
     L.tt_prox_als_sweep.argtypes = [vp, vp, vp, ctypes.POINTER(vp), i, u64, ctypes.POINTER(ctypes.c_double)]
     L.tt_rel_error.argtypes = [vp, vp, vp, ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_double)]
+    L.tt_prox_als_sweep_sketched.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), u64]
     L.tt_prox_als_sweep_host.argtypes = [vp, vp, vp, ctypes.POINTER(vp), i, u64, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_double)]
     L.tt_prox_update_noalloc.argtypes = [vp, vp, vp, i, i, i, i, ctypes.c_double, vp]
@@ -252,6 +254,9 @@ def _ctx_ws_methods():
     def tt_ws_summary(self, Y: Sequence, p: int, x, scale):
         self._check(self.lib.tt_ws_summary(self.ctx, _ptr_array(Y), int(p), _ptr(x), _ptr(scale)))
 
+    def tt_prox_als_sweep_sketched(self, Y: Sequence, cores: Sequence, sweep: int):
+        self._check(self.lib.tt_prox_als_sweep_sketched(self.ctx, _ptr_array(Y), _ptr_array(cores), int(sweep)))
+
     def tt_canonicalize(self, cores: Sequence):
         self._check(self.lib.tt_canonicalize(self.ctx, _ptr_array(cores)))
 
@@ -261,7 +266,8 @@ def _ctx_ws_methods():
     def tt_ws_unpack(self, y, scale, cores: Sequence):
         self._check(self.lib.tt_ws_unpack(self.ctx, _ptr(y), _ptr(scale), _ptr_array(cores)))
 
-    for f in (tt_ws_summary_dim, tt_ws_core_dim, tt_ws_summary, tt_canonicalize, tt_ws_pack, tt_ws_unpack):
+    for f in (tt_ws_summary_dim, tt_ws_core_dim, tt_ws_summary, tt_prox_als_sweep_sketched, tt_canonicalize,
+              tt_ws_pack, tt_ws_unpack):
         setattr(Context, f.__name__, f)
 
 
