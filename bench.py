@@ -279,6 +279,20 @@ def batched_pattern(dev, nsweeps=10, count=256):
     ms = e0.elapsed_time(e1)
     errs = batch.tt_batch_rel_error(As, cores)
     batch.close()
+    # the same sweeps one tensor at a time (a context per tensor, its own launches, no graph)
+    ctxs = [lib.Context(sp["dims"], sp["ranks"], sp["J"], sp["lam"], sp["seed"], sp["dtype"]) for sp in specs]
+    for c, a, cs in zip(ctxs, As, cores):
+        c.tt_prox_als_sweep(a, cs, 1, 100, rel_change=False)  # warm: plans, tables
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for t in range(2):
+        for c, a, cs in zip(ctxs, As, cores):
+            c.tt_prox_als_sweep(a, cs, 1, 101 + t, rel_change=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    loop_ms = e0.elapsed_time(e1) / 2
+    for c in ctxs:
+        c.close()
     esz = {"f32": 4, "bf16": 2}
     tensor_bytes = sum(int(a.numel()) * esz[sp["dtype"]] for a, sp in zip(As, specs))
     unfold_bytes = sum(int(a.numel()) * esz[sp["dtype"]] * len(sp["dims"]) for a, sp in zip(As, specs))
@@ -286,6 +300,8 @@ def batched_pattern(dev, nsweeps=10, count=256):
     errs_sorted = sorted(errs)
     return {"tensors": count, "tensor_gb": tensor_bytes / 1e9, "sweeps": nsweeps,
             "tensor_sweeps_per_s": count / sweep_s, "ms_per_batched_sweep": sweep_s * 1e3,
+            "ms_per_sweep_one_tensor_at_a_time": loop_ms,
+            "tensor_sweeps_per_s_one_tensor_at_a_time": count / (loop_ms * 1e-3),
             "unfold_read_gbs_lower_bound": unfold_bytes / sweep_s / 1e9,
             "setup_s": setup_s,
             "rel_error_median": errs_sorted[len(errs) // 2], "rel_error_max": errs_sorted[-1],
