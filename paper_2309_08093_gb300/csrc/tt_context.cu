@@ -153,16 +153,50 @@ struct RestWalker {
   }
 };
 
-// Counting with a per-block shared-memory histogram (one global atomic per non-empty bucket and
-// block); fibres r of block b are the contiguous range [b*PB, (b+1)*PB).
-#define TT_PLAN_BLOCK 8192
-__global__ void k_rplan_count(RPlanArgs a, const int32_t* h, const int8_t* v, int32_t* count) {
+// Plans of all modes are built together (the hashes of a sweep are known at its start): one
+// launch counts, one scans, one scatters, over a grid that concatenates the blocks of every mode.
+// Modes with few rest fibres (R <= 8 J) use global atomics per fibre; the others a per-block
+// shared-memory histogram (one global atomic per non-empty bucket and block).
+#define TT_PLAN_BLOCK 8192  // fibres per block in histogram mode
+struct RPlanAll {
+  RPlanArgs m[TT_MAX_D];
+  int64_t bstart[TT_MAX_D + 1];  // first block of each mode
+  int pb[TT_MAX_D];              // fibres per block
+  int direct[TT_MAX_D];          // 1: global atomics, no shared histogram
+  int d;
+};
+struct RPlanOut {
+  int32_t* ulist[TT_MAX_D];
+  int64_t* ustart[TT_MAX_D];
+  int32_t* ucount[TT_MAX_D];
+  uint32_t* plan[TT_MAX_D];
+};
+
+__device__ __forceinline__ int plan_mode(const RPlanAll& P) {
+  int m = 0;
+  while (m + 1 < P.d && (int64_t)blockIdx.x >= P.bstart[m + 1]) ++m;
+  return m;
+}
+
+__global__ void k_rplan_count(RPlanAll P, const int32_t* h, const int8_t* v, int32_t* count) {
   extern __shared__ int hist[];
-  for (int i = threadIdx.x; i < a.J; i += blockDim.x) hist[i] = 0;
-  __syncthreads();
-  const int64_t r0 = (int64_t)blockIdx.x * TT_PLAN_BLOCK, r1 = min(a.R, r0 + TT_PLAN_BLOCK);
+  const int m = plan_mode(P);
+  const RPlanArgs& a = P.m[m];
+  const int64_t r0 = ((int64_t)blockIdx.x - P.bstart[m]) * P.pb[m], r1 = min(a.R, r0 + P.pb[m]);
+  int32_t* cnt = count + (int64_t)m * a.J;
   RestWalker wk;
   wk.init(a, r0 + threadIdx.x, blockDim.x);
+  if (P.direct[m]) {
+    for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x, wk.advance(a)) {
+      int key, neg;
+      int64_t off;
+      wk.entry(a, h, v, &key, &neg, &off);
+      atomicAdd(&cnt[key], 1);
+    }
+    return;
+  }
+  for (int i = threadIdx.x; i < a.J; i += blockDim.x) hist[i] = 0;
+  __syncthreads();
   for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x, wk.advance(a)) {
     int key, neg;
     int64_t off;
@@ -171,11 +205,11 @@ __global__ void k_rplan_count(RPlanArgs a, const int32_t* h, const int8_t* v, in
   }
   __syncthreads();
   for (int i = threadIdx.x; i < a.J; i += blockDim.x)
-    if (hist[i]) atomicAdd(&count[i], hist[i]);
+    if (hist[i]) atomicAdd(&cnt[i], hist[i]);
 }
 
-// exclusive scans of the counts and of the non-empty flags (one block of 1024 threads,
-// warp-shuffle scans)
+// exclusive scans of the counts and of the non-empty flags (one block of 1024 threads per mode,
+// warp-shuffle scans); the counts become the scatter cursors
 __device__ __forceinline__ int64_t warp_incl_scan(int64_t x) {
   const int lane = threadIdx.x & 31;
   for (int o = 1; o < 32; o <<= 1) {
@@ -184,9 +218,11 @@ __device__ __forceinline__ int64_t warp_incl_scan(int64_t x) {
   }
   return x;
 }
-__global__ void k_rplan_scan(int J, int64_t R, int32_t* count, int64_t* off, int32_t* ulist, int64_t* ustart,
-                             int32_t* ucount) {
+__global__ void k_rplan_scan(int J, int32_t* count_all, int64_t* off_all, RPlanOut o) {
   __shared__ int64_t wsum[32], wun[32];
+  const int m = blockIdx.x;
+  int32_t* count = count_all + (int64_t)m * J;
+  int64_t* off = off_all + (int64_t)m * (J + 1);
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int per = (J + 1023) / 1024;
   const int lo = min(J, t * per), hi = min(J, (t + 1) * per);
@@ -213,34 +249,50 @@ __global__ void k_rplan_scan(int J, int64_t R, int32_t* count, int64_t* off, int
     const int ci = count[i];
     off[i] = base;
     if (ci > 0) {
-      ulist[ub] = i;
-      ustart[ub] = base;
+      o.ulist[m][ub] = i;
+      o.ustart[m][ub] = base;
       ++ub;
     }
     base += ci;
-    count[i] = 0;  // becomes the scatter cursor
+    count[i] = 0;
   }
   if (t == 1023) {
     off[J] = wsum[31];
-    ustart[wun[31]] = wsum[31];
-    *ucount = (int32_t)wun[31];
+    o.ustart[m][wun[31]] = wsum[31];
+    *o.ucount[m] = (int32_t)wun[31];
   }
 }
 
-// Scatter: each block reserves, per non-empty bucket, a range of the bucket's slots with one
-// global atomic, then places its fibres with shared-memory cursors.
-__global__ void k_rplan_scatter(RPlanArgs a, const int32_t* h, const int8_t* v, const int64_t* off,
-                                int32_t* cursor, uint32_t* plan) {
+// Scatter: a histogram-mode block reserves, per non-empty bucket, a range of the bucket's slots
+// with one global atomic, then places its fibres with shared-memory cursors; a direct-mode block
+// takes one global cursor increment per fibre.
+__global__ void k_rplan_scatter(RPlanAll P, const int32_t* h, const int8_t* v, const int64_t* off_all,
+                                int32_t* cursor_all, RPlanOut o) {
   extern __shared__ int hist[];
-  for (int i = threadIdx.x; i < a.J; i += blockDim.x) hist[i] = 0;
-  __syncthreads();
-  const int64_t r0 = (int64_t)blockIdx.x * TT_PLAN_BLOCK, r1 = min(a.R, r0 + TT_PLAN_BLOCK);
+  const int m = plan_mode(P);
+  const RPlanArgs& a = P.m[m];
+  const int64_t r0 = ((int64_t)blockIdx.x - P.bstart[m]) * P.pb[m], r1 = min(a.R, r0 + P.pb[m]);
+  int32_t* cursor = cursor_all + (int64_t)m * a.J;
+  const int64_t* off = off_all + (int64_t)m * (a.J + 1);
+  uint32_t* plan = o.plan[m];
   RestWalker wk;
   wk.init(a, r0 + threadIdx.x, blockDim.x);
+  if (P.direct[m]) {
+    for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x, wk.advance(a)) {
+      int key, neg;
+      int64_t ofs;
+      wk.entry(a, h, v, &key, &neg, &ofs);
+      const int pos = atomicAdd(&cursor[key], 1);
+      plan[off[key] + pos] = (uint32_t)ofs | ((uint32_t)neg << 31);
+    }
+    return;
+  }
+  for (int i = threadIdx.x; i < a.J; i += blockDim.x) hist[i] = 0;
+  __syncthreads();
   for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x, wk.advance(a)) {
     int key, neg;
-    int64_t o;
-    wk.entry(a, h, v, &key, &neg, &o);
+    int64_t ofs;
+    wk.entry(a, h, v, &key, &neg, &ofs);
     atomicAdd(&hist[key], 1);
   }
   __syncthreads();
@@ -250,42 +302,58 @@ __global__ void k_rplan_scatter(RPlanArgs a, const int32_t* h, const int8_t* v, 
   wk.init(a, r0 + threadIdx.x, blockDim.x);
   for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x, wk.advance(a)) {
     int key, neg;
-    int64_t o;
-    wk.entry(a, h, v, &key, &neg, &o);
+    int64_t ofs;
+    wk.entry(a, h, v, &key, &neg, &ofs);
     const int pos = atomicAdd(&hist[key], 1);
-    plan[off[key] + pos] = (uint32_t)o | ((uint32_t)neg << 31);  // fibre index | sign
+    plan[off[key] + pos] = (uint32_t)ofs | ((uint32_t)neg << 31);  // fibre index | sign
   }
 }
 
+// Plans of every mode for the current tables. In graph-capture mode with per-sweep draws the
+// plans are rebuilt at the sweep's first data sketch (mode 0) and reused by the other modes.
 int tt_ensure_rplan(tt_ctx* c, int k) {
-  if (c->rplan_valid[k] && !(c->capture_mode && !(c->flags & TT_FLAG_FIXED_SKETCH) && !c->user_tables))
-    return TT_OK;
-  RPlanArgs a;
-  for (int s = 0; s < c->d; ++s) {
-    a.n[s] = c->n[s];
-    a.stride[s] = c->stride[s];
-    a.fstride[s] = c->stride[s] / c->n[0];
+  const bool redraw = c->capture_mode && !(c->flags & TT_FLAG_FIXED_SKETCH) && !c->user_tables;
+  if (redraw ? k != 0 : c->rplan_valid[k]) return TT_OK;
+  RPlanAll P;
+  RPlanOut o;
+  P.d = c->d;
+  P.bstart[0] = 0;
+  for (int m = 0; m < c->d; ++m) {
+    RPlanArgs& a = P.m[m];
+    for (int s = 0; s < c->d; ++s) {
+      a.n[s] = c->n[s];
+      a.stride[s] = c->stride[s];
+      a.fstride[s] = c->stride[s] / c->n[0];
+    }
+    for (int s = 0; s <= c->d; ++s) a.noff[s] = c->noff[s];
+    a.d = c->d;
+    a.k = m;
+    a.J = c->J;
+    a.R = c->R[m];
+    P.direct[m] = a.R <= 8 * (int64_t)c->J;
+    P.pb[m] = P.direct[m] ? 1024
+                          : (int)std::max<int64_t>(2 * (int64_t)c->J, std::min<int64_t>(TT_PLAN_BLOCK, (a.R + 303) / 304));
+    P.bstart[m + 1] = P.bstart[m] + std::max<int64_t>(1, (a.R + P.pb[m] - 1) / P.pb[m]);
+    o.ulist[m] = c->d_ulist[m];
+    o.ustart[m] = c->d_ustart[m];
+    o.ucount[m] = c->d_ucount[m];
+    o.plan[m] = c->d_rplan[m];
   }
-  for (int s = 0; s <= c->d; ++s) a.noff[s] = c->noff[s];
-  a.d = c->d;
-  a.k = k;
-  a.J = c->J;
-  a.R = c->R[k];
   int32_t* count = c->d_plan0_cursor;
-  TT_CUDA(c, cudaMemsetAsync(count, 0, sizeof(int32_t) * c->J, c->stream));
-  const int blocks = (int)std::max<int64_t>(1, (a.R + TT_PLAN_BLOCK - 1) / TT_PLAN_BLOCK);
+  TT_CUDA(c, cudaMemsetAsync(count, 0, sizeof(int32_t) * c->J * c->d, c->stream));
   const size_t hsm = sizeof(int) * c->J;
   if (hsm > 48 * 1024) {
     TT_CUDA(c, cudaFuncSetAttribute(k_rplan_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm));
     TT_CUDA(c, cudaFuncSetAttribute(k_rplan_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm));
   }
-  k_rplan_count<<<blocks, 512, hsm, c->stream>>>(a, c->d_h, c->d_v, count);
+  const int blocks = (int)P.bstart[c->d];
+  k_rplan_count<<<blocks, 512, hsm, c->stream>>>(P, c->d_h, c->d_v, count);
   TT_LAUNCH(c, "k_rplan_count");
-  k_rplan_scan<<<1, 1024, 0, c->stream>>>(c->J, a.R, count, c->d_rtmp, c->d_ulist[k], c->d_ustart[k], c->d_ucount[k]);
+  k_rplan_scan<<<c->d, 1024, 0, c->stream>>>(c->J, count, c->d_rtmp, o);
   TT_LAUNCH(c, "k_rplan_scan");
-  k_rplan_scatter<<<blocks, 512, hsm, c->stream>>>(a, c->d_h, c->d_v, c->d_rtmp, count, c->d_rplan[k]);
+  k_rplan_scatter<<<blocks, 512, hsm, c->stream>>>(P, c->d_h, c->d_v, c->d_rtmp, count, o);
   TT_LAUNCH(c, "k_rplan_scatter");
-  c->rplan_valid[k] = true;
+  for (int m = 0; m < c->d; ++m) c->rplan_valid[m] = true;
   return TT_OK;
 }
 
@@ -297,7 +365,7 @@ int tt_ensure_plan0(tt_ctx* c) { return tt_ensure_rplan(c, 0); }
 static void free_all(tt_ctx* c) {
   void* ps[] = {c->d_h, c->d_v, c->d_plan0, c->d_plan0_off, c->d_plan0_cursor, c->d_ghat,
                 c->d_twiddle, c->d_suffix, c->d_prefix, c->d_prefix_tmp, c->d_SH, c->d_Y,
-                c->d_gram, c->d_core_old, c->d_changes, c->d_status, c->d_err_acc, c->d_ws_acc};
+                c->d_gram, c->d_core_old, c->d_changes, c->d_status, c->d_err_acc, c->d_ws_acc, c->d_rint, c->d_slab_u};
   for (void* p : ps)
     if (p) cudaFree(p);
   if (c->d_A_stage) cudaFree(c->d_A_stage);
@@ -379,8 +447,8 @@ extern "C" int tt_sketch_init(tt_ctx** out, const tt_params* p, void* stream) {
   };
   A((void**)&c->d_h, sizeof(int32_t) * c->noff[c->d]);
   A((void**)&c->d_v, sizeof(int8_t) * c->noff[c->d]);
-  A((void**)&c->d_plan0_cursor, sizeof(int32_t) * c->J);
-  A((void**)&c->d_rtmp, sizeof(int64_t) * (c->J + 1));
+  A((void**)&c->d_plan0_cursor, sizeof(int32_t) * c->J * c->d);
+  A((void**)&c->d_rtmp, sizeof(int64_t) * (c->J + 1) * c->d);
   for (int k = 0; k < c->d; ++k) {
     c->R[k] = c->N / (c->n[0] * (k == 0 ? 1 : c->n[k]));
     A((void**)&c->d_rplan[k], sizeof(uint32_t) * c->R[k]);
@@ -402,6 +470,12 @@ extern "C" int tt_sketch_init(tt_ctx** out, const tt_params* p, void* stream) {
   A((void**)&c->d_status, sizeof(int));
   A((void**)&c->d_err_acc, sizeof(double) * 4);
   A((void**)&c->d_ws_acc, sizeof(double) * 2);
+  // streaming relative error (n_0 % 4 == 0, n_0 <= 1024, G_0 within 48 KB of shared memory)
+  c->rint_r1p = (c->r[1] + 3) & ~3;
+  if (c->n[0] % 4 == 0 && c->n[0] <= 1024 && (int64_t)c->rint_r1p * c->n[0] * 4 <= 48 * 1024) {
+    A((void**)&c->d_rint, sizeof(float) * (size_t)(c->N / c->n[0]) * c->rint_r1p);
+    A((void**)&c->d_slab_u, sizeof(float) * (size_t)(c->N / (c->n[0] * c->n[1])) * c->r[2]);
+  }
   if (e != cudaSuccess) {
     free_all(c);
     fprintf(stderr, "tt_sketch_init: cudaMalloc: %s\n", cudaGetErrorString(e));

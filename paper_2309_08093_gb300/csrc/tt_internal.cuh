@@ -46,7 +46,7 @@ struct tt_ctx {
   int64_t M0 = 0;              // number of mode-0 fibers, N / n_0
   uint32_t* d_plan0 = nullptr; // M0 entries: fiber index | sign in bit 31 (sorted by row)
   int64_t* d_plan0_off = nullptr;  // J + 1 row offsets into d_plan0
-  int32_t* d_plan0_cursor = nullptr;  // J scatter cursors
+  int32_t* d_plan0_cursor = nullptr;  // d x J plan counts / scatter cursors (one row per mode)
   bool plan0_valid = false;
 
   // mode-k plans: mode-0 fibres of the modes other than 0 and k ("rest" fibres r), grouped by
@@ -57,7 +57,7 @@ struct tt_ctx {
   int32_t* d_ulist[TT_MAX_D] = {nullptr};   // distinct c values (J entries max)
   int64_t* d_ustart[TT_MAX_D] = {nullptr};  // J + 1 starts into d_rplan[k]
   int32_t* d_ucount[TT_MAX_D] = {nullptr};  // number of distinct c values (device scalar)
-  int64_t* d_rtmp = nullptr;                 // J + 1 scratch offsets for the plan build
+  int64_t* d_rtmp = nullptr;                 // d x (J + 1) bucket offsets of the plan build
   bool rplan_valid[TT_MAX_D] = {false};
   float* d_Ypart = nullptr;                  // unused placeholder
 
@@ -80,6 +80,9 @@ struct tt_ctx {
   int* d_status = nullptr;     // device error flag (0 = ok, else TT_E* code)
   double* d_err_acc = nullptr; // rel-error accumulators (2 doubles)
   double* d_ws_acc = nullptr;  // warm-start summary accumulators (2 doubles)
+  float* d_rint = nullptr;     // right interfaces of the mode-0 fibres (N / n_0 x rint_r1p), rel error
+  int rint_r1p = 0;            // r_1 rounded up to a multiple of 4
+  float* d_slab_u = nullptr;   // u_t = G_2(i_2)...G_{d-1}(i_{d-1}) per slab (N / (n_0 n_1) x r_2), rel error
   int changes_cap = 0;
 
   // measurement counters (tt_profile_*)

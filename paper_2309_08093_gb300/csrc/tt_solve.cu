@@ -7,7 +7,9 @@
 //   k_prox_solve  : Cholesky M = L L^T and the two triangular solves, one CTA (s <= 160)
 //   k_qr_left     : Householder QR of G_k^L, G_k <- Q, G_{k+1} <- R G_{k+1}^R
 //   k_lq_right    : the same on (G_k^R)^T: G_k^R <- Q^T, G_{k-1}^L <- G_{k-1}^L R^T
-//   k_rel_error   : ||A - [[G]]||_F^2 and ||A||_F^2, one warp per mode-0 fibre
+//   k_slab_u, k_rint, k_rel_error_stream : ||A - [[G]]||_F^2 and ||A||_F^2: right interfaces of
+//                   all mode-0 fibres, then one cp.async-pipelined pass over A in memory order
+//   k_rel_error   : the same for other shapes (n_0 % 4 != 0 or n_0 > 1024), slab by slab
 #include <stdio.h>
 
 #include <algorithm>
@@ -859,6 +861,241 @@ __global__ void __launch_bounds__(256) k_rel_error(ErrArgs a) {
   }
 }
 
+// Right interface of every mode-0 fibre f = i_1 + n_1 t (t = slab index over modes 2..d-1):
+// R[f * r1p + al] = (G_1(i_1) u_t)[al], zero for r1 <= al < r1p, with
+// u_t = G_2(i_2) ... G_{d-1}(i_{d-1}) (r_2 values; [1] when d == 2). k_slab_u forms u_t (one
+// thread per slab), k_rint one output per thread (coalesced writes).
+__global__ void __launch_bounds__(256) k_slab_u(ErrArgs a, float* __restrict__ Uo) {
+  const int r2 = a.r[2];
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < a.slabs; t += (int64_t)gridDim.x * blockDim.x) {
+    float u[TT_MAX_S], un[TT_MAX_S];
+    if (a.d == 2) {
+      u[0] = 1.f;
+    } else {
+      int64_t idx[TT_MAX_D];
+      int64_t rem = t;
+      for (int s2 = 2; s2 < a.d; ++s2) {
+        idx[s2] = rem % a.n[s2];
+        rem /= a.n[s2];
+      }
+      const int s2 = a.d - 1, ra = a.r[s2];
+      for (int al = 0; al < ra; ++al) u[al] = a.core[s2][al + (int64_t)ra * idx[s2]];
+      for (int s3 = a.d - 2; s3 >= 2; --s3) {
+        const int rA = a.r[s3], rB = a.r[s3 + 1];
+        const float* G = a.core[s3] + (int64_t)rA * idx[s3];
+        const int64_t bstride = (int64_t)rA * a.n[s3];
+        for (int al = 0; al < rA; ++al) {
+          float acc = 0.f;
+          for (int be = 0; be < rB; ++be) acc = fmaf(G[al + bstride * be], u[be], acc);
+          un[al] = acc;
+        }
+        for (int al = 0; al < rA; ++al) u[al] = un[al];
+      }
+    }
+    for (int be = 0; be < r2; ++be) Uo[t * r2 + be] = u[be];
+  }
+}
+
+__global__ void __launch_bounds__(256) k_rint(ErrArgs a, const float* __restrict__ Uv, float* __restrict__ R, int r1p) {
+  __shared__ float u[TT_MAX_S];
+  const int n1 = (int)a.n[1], r1 = a.r[1], r2 = a.r[2];
+  const int per = n1 * r1p;  // outputs of one slab (al fastest: G_1 reads and R writes contiguous)
+  const float* g1 = a.core[1];
+  for (int64_t t = blockIdx.x; t < a.slabs; t += gridDim.x) {
+    for (int be = threadIdx.x; be < r2; be += blockDim.x) u[be] = Uv[t * r2 + be];
+    __syncthreads();
+    float* out = R + t * (int64_t)per;
+    for (int ol = threadIdx.x; ol < per; ol += blockDim.x) {
+      const int i1 = ol / r1p, al = ol - i1 * r1p;
+      float acc = 0.f;
+      if (al < r1)
+        for (int be = 0; be < r2; ++be) acc = fmaf(__ldg(g1 + al + r1 * (i1 + n1 * be)), u[be], acc);
+      out[ol] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+template <int DT>
+struct ElemSize {
+  static constexpr int value = DT == TT_F64 ? 8 : DT == TT_F32 ? 4 : DT == TT_BF16 ? 2 : 1;
+};
+
+__device__ __forceinline__ void cpa16(uint32_t dst, const void* src, int bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+}
+
+// four consecutive entries from shared memory (storage type DT, 4-entry aligned)
+template <int DT>
+__device__ __forceinline__ void smem_load4(const unsigned char* p, float* x) {
+  if constexpr (DT == TT_F32) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+  } else if constexpr (DT == TT_F64) {
+    const double2 v0 = *reinterpret_cast<const double2*>(p), v1 = *reinterpret_cast<const double2*>(p + 16);
+    x[0] = (float)v0.x; x[1] = (float)v0.y; x[2] = (float)v1.x; x[3] = (float)v1.y;
+  } else if constexpr (DT == TT_BF16) {
+    const uint2 v = *reinterpret_cast<const uint2*>(p);
+    x[0] = __uint_as_float(v.x << 16); x[1] = __uint_as_float(v.x & 0xFFFF0000u);
+    x[2] = __uint_as_float(v.y << 16); x[3] = __uint_as_float(v.y & 0xFFFF0000u);
+  } else {
+    const uint32_t v = *reinterpret_cast<const uint32_t*>(p);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const uint32_t cc = (v >> (8 * c)) & 0xFFu;
+      const uint32_t sg = (cc & 0x80u) << 24, e = (cc >> 3) & 0xFu, mm = cc & 7u;
+      const float mag = e ? __uint_as_float(((e + 120u) << 23) | (mm << 20)) : (float)mm * 0.001953125f;
+      x[c] = __uint_as_float(__float_as_uint(mag) | sg);
+    }
+  }
+}
+
+constexpr int REL_U = 8;  // fibres per thread per tile
+
+// ||A - [[G]]||^2 and ||A||^2 by streaming A in memory order. A tile is FT = P * REL_U consecutive
+// mode-0 fibres (FT * n_0 entries, contiguous) with their rows of R; tiles are staged into shared
+// memory by cp.async, double-buffered, so the next tile is in flight while this one is reduced.
+// Thread (q, p) owns entries 4q..4q+3 of the tile's fibres p + P u; the reconstruction is
+// G_0 (shared, float4 along i_0) times the fibre's R row (shared, float4 broadcast).
+// Needs n_0 % 4 == 0 and n_0 <= 1024.
+template <int DT>
+__global__ void __launch_bounds__(256, 2) k_rel_error_stream(const void* __restrict__ A, const float* __restrict__ scales,
+                                                          const float* __restrict__ g0, const float* __restrict__ R,
+                                                          int n0, int r1, int r1p, int64_t M0, double* acc) {
+  constexpr int ES = ElemSize<DT>::value;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ double red[2][8];
+  const int Q = n0 >> 2, P = blockDim.x / Q, FT = P * REL_U;
+  float* G0 = reinterpret_cast<float*>(smraw);  // r1p x n0, rows >= r1 zero
+  unsigned char* bufA = smraw + (size_t)r1p * n0 * 4;
+  const int tileA = FT * n0 * ES;               // bytes (a multiple of 16)
+  float* bufR = reinterpret_cast<float*>(bufA + 2 * (size_t)tileA);
+  const int tileR = FT * r1p;                   // floats
+  for (int i = threadIdx.x; i < r1p * n0; i += blockDim.x) G0[i] = i < r1 * n0 ? g0[i] : 0.f;
+  const int qi = threadIdx.x % Q, pi = threadIdx.x / Q;
+  const bool active = pi < P;
+  float sc[4] = {1.f, 1.f, 1.f, 1.f};
+  if (scales && active)
+    for (int c = 0; c < 4; ++c) sc[c] = __ldg(scales + 4 * qi + c);
+  const int64_t ntiles = (M0 + FT - 1) / FT;
+  auto issue = [&](int64_t tile, int b) {
+    const int64_t f0 = tile * FT;
+    const int nf = (int)min((int64_t)FT, M0 - f0);
+    const unsigned char* src = reinterpret_cast<const unsigned char*>(A) + f0 * n0 * ES;
+    const int bytes = nf * n0 * ES;
+    const uint32_t dA = (uint32_t)__cvta_generic_to_shared(bufA + (size_t)b * tileA);
+    for (int c = threadIdx.x; c * 16 < bytes; c += blockDim.x) cpa16(dA + 16 * c, src + 16 * c, min(16, bytes - 16 * c));
+    const float* srcR = R + f0 * r1p;
+    const int bytesR = nf * r1p * 4;
+    const uint32_t dR = (uint32_t)__cvta_generic_to_shared(bufR + (size_t)b * tileR);
+    for (int c = threadIdx.x; c * 16 < bytesR; c += blockDim.x) cpa16(dR + 16 * c, srcR + 4 * c, 16);
+  };
+  double e2 = 0.0, x2 = 0.0;
+  int64_t tile = blockIdx.x;
+  if (tile < ntiles) issue(tile, 0);
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  for (int b = 0; tile < ntiles; tile += gridDim.x, b ^= 1) {
+    if (tile + gridDim.x < ntiles) issue(tile + gridDim.x, b ^ 1);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    __syncthreads();
+    const int64_t f0 = tile * FT;
+    const unsigned char* tA = bufA + (size_t)b * tileA;
+    const float* tR = bufR + (size_t)b * tileR;
+    float fe = 0.f, fa = 0.f;
+    if (active) {
+      // fibres innermost: every G_0 float4 read from shared memory serves REL_U fibres
+      float x[REL_U][4], r4[REL_U][4];
+#pragma unroll
+      for (int u = 0; u < REL_U; ++u) {
+        smem_load4<DT>(tA + ((size_t)(pi + P * u) * n0 + 4 * qi) * ES, x[u]);
+        r4[u][0] = r4[u][1] = r4[u][2] = r4[u][3] = 0.f;
+      }
+      for (int al0 = 0; al0 < r1p; al0 += 4) {
+        float4 w[REL_U];
+#pragma unroll
+        for (int u = 0; u < REL_U; ++u) w[u] = *reinterpret_cast<const float4*>(tR + (size_t)(pi + P * u) * r1p + al0);
+#pragma unroll
+        for (int aa = 0; aa < 4; ++aa) {
+          const float4 g4 = *reinterpret_cast<const float4*>(G0 + (al0 + aa) * n0 + 4 * qi);
+#pragma unroll
+          for (int u = 0; u < REL_U; ++u) {
+            const float ww = aa == 0 ? w[u].x : aa == 1 ? w[u].y : aa == 2 ? w[u].z : w[u].w;
+            r4[u][0] = fmaf(g4.x, ww, r4[u][0]);
+            r4[u][1] = fmaf(g4.y, ww, r4[u][1]);
+            r4[u][2] = fmaf(g4.z, ww, r4[u][2]);
+            r4[u][3] = fmaf(g4.w, ww, r4[u][3]);
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < REL_U; ++u) {
+        if (f0 + pi + P * u >= M0) continue;  // past the last fibre (stale buffer entries)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const float xv = x[u][c] * sc[c];
+          const float dl = xv - r4[u][c];
+          fe = fmaf(dl, dl, fe);
+          fa = fmaf(xv, xv, fa);
+        }
+      }
+    }
+    e2 += fe;
+    x2 += fa;
+    __syncthreads();  // buffer b is refilled by the next iteration's issue
+  }
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) {
+    e2 += __shfl_xor_sync(0xffffffffu, e2, o);
+    x2 += __shfl_xor_sync(0xffffffffu, x2, o);
+  }
+  if (lane == 0) {
+    red[0][warp] = e2;
+    red[1][warp] = x2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t1 = 0.0, t2 = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      t1 += red[0][w];
+      t2 += red[1][w];
+    }
+    atomicAdd(acc, t1);
+    atomicAdd(acc + 1, t2);
+  }
+}
+
+// shared memory of k_rel_error_stream for this context (0 if the shape does not fit)
+static size_t rel_stream_smem(const tt_ctx* c, int es) {
+  const int64_t n0 = c->n[0];
+  if (n0 % 4 != 0 || n0 > 1024) return 0;
+  const int64_t Q = n0 / 4, P = 256 / Q, FT = P * REL_U;
+  const size_t bytes = (size_t)c->rint_r1p * n0 * 4 + 2 * (size_t)FT * n0 * es + 2 * (size_t)FT * c->rint_r1p * 4;
+  return bytes <= 200 * 1024 ? bytes : 0;
+}
+
+template <int DT>
+static int launch_rel_stream(tt_ctx* c, const void* A, const float* scales, const float* g0, size_t smem) {
+  static bool attr = false;
+  if (!attr) {
+    TT_CUDA(c, cudaFuncSetAttribute(k_rel_error_stream<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    attr = true;
+  }
+  int per_sm = 0, dev = 0, sms = 0;
+  TT_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rel_error_stream<DT>, 256, smem));
+  TT_CUDA(c, cudaGetDevice(&dev));
+  TT_CUDA(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int64_t M0 = c->N / c->n[0];
+  const int64_t Q = c->n[0] / 4, FT = (256 / Q) * REL_U;
+  const int64_t ntiles = (M0 + FT - 1) / FT;
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)std::max(1, per_sm) * sms));
+  k_rel_error_stream<DT><<<blocks, 256, smem, c->stream>>>(A, scales, g0, c->d_rint, (int)c->n[0], c->r[1],
+                                                          c->rint_r1p, M0, c->d_err_acc);
+  TT_LAUNCH(c, "k_rel_error_stream");
+  return TT_OK;
+}
+
 int tt_launch_rel_error(tt_ctx* c, const void* A, const float* scales, float* const* cores) {
   ErrArgs a;
   a.A = A;
@@ -883,6 +1120,22 @@ int tt_launch_rel_error(tt_ctx* c, const void* A, const float* scales, float* co
   a.g0_in_smem = 1;
   const size_t smem = sizeof(float) * ((size_t)c->r[1] * a.i1chunk + (size_t)g0sz);
   TT_CUDA(c, cudaMemsetAsync(c->d_err_acc, 0, sizeof(double) * 2, c->stream));
+  const int es = c->dtype == TT_F64 ? 8 : c->dtype == TT_F32 ? 4 : c->dtype == TT_BF16 ? 2 : 1;
+  const size_t ssm = c->d_rint ? rel_stream_smem(c, es) : 0;
+  if (ssm) {  // streaming form: right interfaces first, then one pass over A in memory order
+    const int ublocks = (int)std::max<int64_t>(1, std::min<int64_t>((a.slabs + 255) / 256, 4096));
+    k_slab_u<<<ublocks, 256, 0, c->stream>>>(a, c->d_slab_u);
+    TT_LAUNCH(c, "k_slab_u");
+    const int rblocks = (int)std::max<int64_t>(1, std::min<int64_t>(a.slabs, 152 * 8));
+    k_rint<<<rblocks, 256, 0, c->stream>>>(a, c->d_slab_u, c->d_rint, c->rint_r1p);
+    TT_LAUNCH(c, "k_rint");
+    switch (c->dtype) {
+      case TT_F64: return launch_rel_stream<TT_F64>(c, A, scales, cores[0], ssm);
+      case TT_F32: return launch_rel_stream<TT_F32>(c, A, scales, cores[0], ssm);
+      case TT_BF16: return launch_rel_stream<TT_BF16>(c, A, scales, cores[0], ssm);
+      default: return launch_rel_stream<TT_FP8E4M3>(c, A, scales, cores[0], ssm);
+    }
+  }
   const int64_t items = a.slabs * a.nchunks;
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(items, 152 * 8));
   switch (c->dtype) {

@@ -122,27 +122,47 @@ struct TtVec {
   }
 };
 
-// Vector geometry of a fibre: VB-byte loads, vpf vectors per fibre, lanes per fibre slot and
-// fibre slots per warp (several short fibres share one warp instruction).
+// Vector geometry of a fibre: VB-byte loads, vpf vectors per fibre, m vectors per lane, lanes per
+// fibre slot and fibre slots per warp (several short fibres share one warp instruction). Vector v
+// of a fibre is read by lane posl of its slot as (chunk ch, sub-vector mm) with
+// v = ch * lpf * m + mm * lpf + posl, so each of a lane's m loads is coalesced across the slot.
 struct FibreGeom {
   int64_t fiber_bytes;
-  int vpf, lpf, fpi, nchunk;
+  int vpf, lpf, fpi, nchunk, m;
 };
 
-static FibreGeom fibre_geom(int64_t fiber_bytes, int VB) {
+static FibreGeom fibre_geom(int64_t fiber_bytes, int VB, int M) {
   FibreGeom g;
   g.fiber_bytes = fiber_bytes;
+  g.m = M;
   g.vpf = (int)(fiber_bytes / VB);
-  if (g.vpf <= 32) {
-    g.lpf = g.vpf;
-    g.fpi = 32 / g.vpf;
+  const int lanes = (g.vpf + M - 1) / M;
+  if (lanes <= 32) {
+    g.lpf = lanes;
+    g.fpi = 32 / lanes;
     g.nchunk = 1;
   } else {
     g.lpf = 32;
     g.fpi = 1;
-    g.nchunk = (g.vpf + 31) / 32;
+    g.nchunk = (g.vpf + 32 * M - 1) / (32 * M);
   }
   return g;
+}
+
+// vectors per lane for a fibre of vpf 16-byte vectors: the most fibre slots per warp (fewest warp
+// instructions per fibre), ties to the smaller m; at most 16 elements per lane (registers)
+static int pick_m(int vpf, int epv) {
+  int best = 1, best_fpi = 0;
+  for (int M : {1, 2, 4}) {
+    if (M * epv > 16) break;
+    const int lanes = (vpf + M - 1) / M;
+    const int fpi = lanes <= 32 ? 32 / lanes : 0;
+    if (fpi > best_fpi) {
+      best = M;
+      best_fpi = fpi;
+    }
+  }
+  return best;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -186,29 +206,31 @@ __host__ __device__ constexpr size_t gather_ring_bytes(bool async, int nwarps, i
 
 // One work item = a contiguous segment of c groups of one output column (mode 0: of Y_0's
 // rows). The item's fibres are split evenly over the (warp, fibre-slot) pairs; each lane keeps S
-// of its 16-byte fibre pieces in flight with cp.async (one commit group per fibre, the slot is
+// fibres of M VB-byte pieces in flight with cp.async (one commit group per fibre, the stage is
 // refilled as soon as it is consumed) and sums runs of equal c in registers. When a run ends:
 //   mode 0  : the finished row goes to Y_0 (plain store if the run lies inside this slot's range,
 //             atomic add otherwise);
 //   mode >= 1: coef(i0) * run is added into bucket (c + h_0(i0)) mod J of the CTA's column copy.
-template <int DT, int VB, int S, bool MODE0>
+template <int DT, int VB, int S, int M, bool MODE0>
 __global__ void __launch_bounds__(256, 2) k_unfold_gather(GArgs a) {
   constexpr bool ASYNC = VB >= 4;  // cp.async moves 4, 8 or 16 bytes; 1-2 byte vectors load directly
+  static_assert(ASYNC || M == 1, "direct loads use one vector per lane");
   constexpr int EPV = TtVec<DT, VB>::EPV;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int J = a.J;
   const int T = blockDim.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = T >> 5;
-  unsigned char* ring = smraw;                                           // nw x S x 32 x VB
-  float* Ys = reinterpret_cast<float*>(ring + gather_ring_bytes(ASYNC, nw, S, VB));  // J (mode >= 1)
+  unsigned char* ring = smraw;                                           // nw x S x M x 32 x VB
+  float* Ys = reinterpret_cast<float*>(ring + gather_ring_bytes(ASYNC, nw, S * M, VB));  // J (mode >= 1)
   int* sstart = reinterpret_cast<int*>(Ys + (MODE0 ? 0 : J));           // segmax + 1 (relative)
   int* scval = sstart + a.segmax + 1;                                    // segmax
   const int U_ = *a.ucount;
-  const int slot = lane / a.fg.lpf, posl = lane - slot * a.fg.lpf;
+  const int lpf = a.fg.lpf;
+  const int slot = lane / lpf, posl = lane - slot * lpf;
   const bool slot_ok = slot < a.fg.fpi;
   const int nslots = nw * a.fg.fpi;
   const int gslot = warp * a.fg.fpi + slot;
-  unsigned char* myring = ring + ((size_t)warp * S * 32 + lane) * VB;
+  unsigned char* myring = ring + ((size_t)warp * S * M * 32 + lane) * VB;
   const int items = a.ncol * a.nseg;
   for (int item = blockIdx.x; item < items; item += gridDim.x) {
     const int col = item / a.nseg, seg = item - col * a.nseg;
@@ -225,7 +247,7 @@ __global__ void __launch_bounds__(256, 2) k_unfold_gather(GArgs a) {
     __syncthreads();
     const int ne = sstart[nu];
     const int sb = (int)((int64_t)ne * gslot / nslots), se = (int)((int64_t)ne * (gslot + 1) / nslots);
-    const int64_t colf = (int64_t)col * a.col_fibres;
+    const char* Acol = a.A + (int64_t)col * a.col_fibres * a.fg.fiber_bytes;
     const uint32_t* plan = a.plan + e0;
     if (slot_ok && sb < se) {
       int lo2 = 0, hi2 = nu;  // run containing sb: sstart[lo2] <= sb < sstart[hi2]
@@ -235,58 +257,73 @@ __global__ void __launch_bounds__(256, 2) k_unfold_gather(GArgs a) {
       }
       const int count = se - sb;
       for (int ch = 0; ch < a.fg.nchunk; ++ch) {
-        const int vpos = ch * 32 + posl;
-        const bool lane_ok = vpos < a.fg.vpf;
-        const int64_t vbyte = (int64_t)vpos * VB;
-        float coefr[EPV];
-        int h0r[EPV];
+        int vpos[M];
+        bool vok[M];
+        float coefr[M][EPV];
+        int h0r[M][EPV];
 #pragma unroll
-        for (int e = 0; e < EPV; ++e) {
-          const int i0 = vpos * EPV + e;
-          float cf = 1.f;
-          int hh = 0;
-          if (lane_ok) {
-            if (!MODE0 && __ldg(a.v0 + i0) < 0) cf = -1.f;
-            if (a.scales) cf *= __ldg(a.scales + i0);
-            if (!MODE0) hh = __ldg(a.h0 + i0);
+        for (int mm = 0; mm < M; ++mm) {
+          vpos[mm] = ch * lpf * M + mm * lpf + posl;
+          vok[mm] = vpos[mm] < a.fg.vpf;
+#pragma unroll
+          for (int e = 0; e < EPV; ++e) {
+            const int i0 = vpos[mm] * EPV + e;
+            float cf = 1.f;
+            int hh = 0;
+            if (vok[mm]) {
+              if (!MODE0 && __ldg(a.v0 + i0) < 0) cf = -1.f;
+              if (a.scales) cf *= __ldg(a.scales + i0);
+              if (!MODE0) hh = __ldg(a.h0 + i0);
+            }
+            coefr[mm][e] = cf;
+            h0r[mm][e] = hh;
           }
-          coefr[e] = cf;
-          h0r[e] = hh;
         }
+        const char* Alane[M];
+#pragma unroll
+        for (int mm = 0; mm < M; ++mm) Alane[mm] = Acol + (int64_t)vpos[mm] * VB;
         int cu = lo2;
         int next_b = sstart[cu + 1];
         bool first_run = true;
-        float acc[EPV];
+        float acc[M][EPV];
 #pragma unroll
-        for (int e = 0; e < EPV; ++e) acc[e] = 0.f;
+        for (int mm = 0; mm < M; ++mm)
+#pragma unroll
+          for (int e = 0; e < EPV; ++e) acc[mm][e] = 0.f;
         // flush of the run of group cu (shared with a neighbour slot when `shared`)
         auto flush = [&](bool shared) {
-          if (lane_ok) {
-            const int cv = scval[cu];
-            if (MODE0) {
+          const int cv = scval[cu];
 #pragma unroll
-              for (int e = 0; e < EPV; ++e) {
-                float* dst = a.Y + cv + (int64_t)J * (vpos * EPV + e);
-                const float v = coefr[e] * acc[e];
-                if (shared) atomicAdd(dst, v); else *dst = v;
+          for (int mm = 0; mm < M; ++mm) {
+            if (vok[mm]) {
+              if (MODE0) {
+#pragma unroll
+                for (int e = 0; e < EPV; ++e) {
+                  float* dst = a.Y + cv + (int64_t)J * (vpos[mm] * EPV + e);
+                  const float v = coefr[mm][e] * acc[mm][e];
+                  if (shared) atomicAdd(dst, v); else *dst = v;
+                }
+              } else {
+#pragma unroll
+                for (int e = 0; e < EPV; ++e) atomicAdd(Ys + ((cv + h0r[mm][e]) & (J - 1)), coefr[mm][e] * acc[mm][e]);
               }
-            } else {
-#pragma unroll
-              for (int e = 0; e < EPV; ++e) atomicAdd(Ys + ((cv + h0r[e]) & (J - 1)), coefr[e] * acc[e]);
             }
-          }
 #pragma unroll
-          for (int e = 0; e < EPV; ++e) acc[e] = 0.f;
+            for (int e = 0; e < EPV; ++e) acc[mm][e] = 0.f;
+          }
         };
-        // pipeline: slot q of the ring holds fibre j with j % S == q
+        // pipeline: stage q of the ring holds fibre j with j % S == q (M pieces per lane)
         uint32_t wcur[S], wnext[S];
 #pragma unroll
         for (int q = 0; q < S; ++q) {
           wcur[q] = (q < count) ? __ldg(plan + sb + q) : 0u;
           if constexpr (ASYNC) {
-            if (lane_ok && q < count)
-              cp_async_vec(myring + (size_t)q * 32 * VB,
-                           a.A + ((int64_t)(wcur[q] & 0x7FFFFFFFu) + colf) * a.fg.fiber_bytes + vbyte, VB);
+            if (q < count) {
+              const int64_t fo = (int64_t)(wcur[q] & 0x7FFFFFFFu) * a.fg.fiber_bytes;
+#pragma unroll
+              for (int mm = 0; mm < M; ++mm)
+                if (vok[mm]) cp_async_vec(myring + (size_t)(q * M + mm) * 32 * VB, Alane[mm] + fo, VB);
+            }
             cp_async_commit();
           }
           wnext[q] = (S + q < count) ? __ldg(plan + sb + S + q) : 0u;
@@ -296,19 +333,27 @@ __global__ void __launch_bounds__(256, 2) k_unfold_gather(GArgs a) {
           for (int q = 0; q < S; ++q) {
             const int j = j0 + q;
             if (j < count) {
-              typename TtVec<DT, VB>::Raw raw;
+              typename TtVec<DT, VB>::Raw raw[M];
               if constexpr (ASYNC) {
                 cp_async_wait<S - 1>();
-                if (lane_ok) {
-                  const uint32_t* src = reinterpret_cast<const uint32_t*>(myring + (size_t)q * 32 * VB);
 #pragma unroll
-                  for (int t2 = 0; t2 < TtVec<DT, VB>::W; ++t2) raw.w[t2] = src[t2];
-                } else {
-                  raw = TtVec<DT, VB>::zero();
+                for (int mm = 0; mm < M; ++mm) {
+                  if (vok[mm]) {
+                    const unsigned char* src = myring + (size_t)(q * M + mm) * 32 * VB;
+                    if constexpr (VB == 16) {
+                      const uint4 w4 = *reinterpret_cast<const uint4*>(src);
+                      raw[mm].w[0] = w4.x; raw[mm].w[1] = w4.y; raw[mm].w[2] = w4.z; raw[mm].w[3] = w4.w;
+                    } else {
+#pragma unroll
+                      for (int t2 = 0; t2 < TtVec<DT, VB>::W; ++t2) raw[mm].w[t2] = reinterpret_cast<const uint32_t*>(src)[t2];
+                    }
+                  } else {
+                    raw[mm] = TtVec<DT, VB>::zero();
+                  }
                 }
               } else {
-                raw = lane_ok ? TtVec<DT, VB>::load(a.A + ((int64_t)(wcur[q] & 0x7FFFFFFFu) + colf) * a.fg.fiber_bytes + vbyte)
-                              : TtVec<DT, VB>::zero();
+                raw[0] = vok[0] ? TtVec<DT, VB>::load(Alane[0] + (int64_t)(wcur[q] & 0x7FFFFFFFu) * a.fg.fiber_bytes)
+                                : TtVec<DT, VB>::zero();
               }
               const int jr = sb + j;  // position within the item
               if (jr >= next_b) {
@@ -319,13 +364,18 @@ __global__ void __launch_bounds__(256, 2) k_unfold_gather(GArgs a) {
                   next_b = sstart[cu + 1];
                 } while (jr >= next_b);
               }
-              TtVec<DT, VB>::fma_into(raw, (wcur[q] >> 31) ? -1.f : 1.f, acc);
-              // refill slot q with fibre j + S, prefetch the plan word of fibre j + 2S
+              const float sg = (wcur[q] >> 31) ? -1.f : 1.f;
+#pragma unroll
+              for (int mm = 0; mm < M; ++mm) TtVec<DT, VB>::fma_into(raw[mm], sg, acc[mm]);
+              // refill stage q with fibre j + S, prefetch the plan word of fibre j + 2S
               const int jn = j + S;
               if constexpr (ASYNC) {
-                if (lane_ok && jn < count)
-                  cp_async_vec(myring + (size_t)q * 32 * VB,
-                               a.A + ((int64_t)(wnext[q] & 0x7FFFFFFFu) + colf) * a.fg.fiber_bytes + vbyte, VB);
+                if (jn < count) {
+                  const int64_t fo = (int64_t)(wnext[q] & 0x7FFFFFFFu) * a.fg.fiber_bytes;
+#pragma unroll
+                  for (int mm = 0; mm < M; ++mm)
+                    if (vok[mm]) cp_async_vec(myring + (size_t)(q * M + mm) * 32 * VB, Alane[mm] + fo, VB);
+                }
                 cp_async_commit();
               }
               wcur[q] = wnext[q];
@@ -363,9 +413,9 @@ static int pick_vb(int64_t fiber_bytes, uintptr_t base, int elem_bytes) {
   return elem_bytes;
 }
 
-template <int DT, int VB, bool MODE0>
-static int launch_gather_vb(tt_ctx* c, const void* A, const float* scales, int k, float* Y) {
-  constexpr int S = 12;
+template <int DT, int VB, int M, bool MODE0>
+static int launch_gather_vbm(tt_ctx* c, const void* A, const float* scales, int k, float* Y) {
+  constexpr int S = 12 / M;  // fibres in flight per lane: S * M pieces of VB bytes
   constexpr int THREADS = 256;
   GArgs a;
   a.A = (const char*)A;
@@ -381,7 +431,7 @@ static int launch_gather_vb(tt_ctx* c, const void* A, const float* scales, int k
   a.n0 = (int)c->n[0];
   a.ncol = MODE0 ? 1 : (int)c->n[k];
   a.col_fibres = MODE0 ? 0 : c->stride[k] / c->n[0];
-  a.fg = fibre_geom((int64_t)c->n[0] * TtElem<DT>::bytes, VB);
+  a.fg = fibre_geom((int64_t)c->n[0] * TtElem<DT>::bytes, VB, M);
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
   // work items (column, c-segment): at most one per CTA slot (two CTAs per SM) when the columns
@@ -393,18 +443,33 @@ static int launch_gather_vb(tt_ctx* c, const void* A, const float* scales, int k
   nseg = std::max(nseg, (c->J + 2047) / 2048);
   a.nseg = nseg;
   a.segmax = (c->J + nseg - 1) / nseg + 1;
-  const size_t ring = gather_ring_bytes(VB >= 4, THREADS / 32, S, VB);
+  const size_t ring = gather_ring_bytes(VB >= 4, THREADS / 32, S * M, VB);
   const size_t smem = ring + sizeof(float) * (MODE0 ? 0 : c->J) + sizeof(int) * (2 * (size_t)a.segmax + 1);
   if (smem > 220 * 1024) return tt_fail(c, TT_EINVAL, "gather kernel needs %zu bytes of shared memory", smem);
   TT_CUDA(c, cudaMemsetAsync(Y, 0, sizeof(float) * c->J * c->n[k], c->stream));  // empty groups stay 0
-  TT_CUDA(c, cudaFuncSetAttribute(k_unfold_gather<DT, VB, S, MODE0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  TT_CUDA(c, cudaFuncSetAttribute(k_unfold_gather<DT, VB, S, M, MODE0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 1;
-  TT_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_unfold_gather<DT, VB, S, MODE0>, THREADS, smem));
+  TT_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_unfold_gather<DT, VB, S, M, MODE0>, THREADS, smem));
   const int items = a.ncol * a.nseg;
   const int blocks = std::max(1, std::min(items, sms * std::max(1, std::min(per_sm, cps))));
-  k_unfold_gather<DT, VB, S, MODE0><<<blocks, THREADS, smem, c->stream>>>(a);
+  k_unfold_gather<DT, VB, S, M, MODE0><<<blocks, THREADS, smem, c->stream>>>(a);
   TT_LAUNCH(c, "k_unfold_gather");
   return TT_OK;
+}
+
+template <int DT, int VB, bool MODE0>
+static int launch_gather_vb(tt_ctx* c, const void* A, const float* scales, int k, float* Y) {
+  // Several fibres per warp pay off in mode 0, whose runs are long (one flush per row); in modes
+  // >= 1 a run is a few fibres and the fibre slots of a warp would flush divergently.
+  if constexpr (VB == 16 && MODE0) {
+    switch (pick_m((int)(c->n[0] * TtElem<DT>::bytes / 16), TtVec<DT, 16>::EPV)) {
+      case 4: return launch_gather_vbm<DT, 16, 4, MODE0>(c, A, scales, k, Y);
+      case 2: return launch_gather_vbm<DT, 16, 2, MODE0>(c, A, scales, k, Y);
+      default: return launch_gather_vbm<DT, 16, 1, MODE0>(c, A, scales, k, Y);
+    }
+  } else {
+    return launch_gather_vbm<DT, VB, 1, MODE0>(c, A, scales, k, Y);
+  }
 }
 
 template <int DT, bool MODE0>
