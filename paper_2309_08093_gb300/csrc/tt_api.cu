@@ -100,24 +100,52 @@ extern "C" int tt_orthogonalize(tt_ctx* c, float* const* cores, int direction, i
 int tt_one_sweep(tt_ctx* c, const void* A, const float* scales, float* const* cores, uint64_t sweep,
                      double* change_slots, float* const* Ygiven) {
   const int d = c->d;
-  for (int kk = d - 1; kk >= 1; --kk) TT_TRY(tt_launch_lq_right(c, cores[kk - 1], cores[kk], kk));
   TT_TRY(tt_ensure_tables(c, sweep));
-  TT_TRY(build_all_ghat(c, cores));
-  TT_TRY(tt_launch_suffixes(c));
-  TT_TRY(tt_launch_prefix_reset(c));
-  for (int k = 0; k < d; ++k) {
-    TT_TRY(tt_launch_interface_from_chain(c, k, c->d_SH));
-    const float* Yk = c->d_Y;
-    if (Ygiven) Yk = Ygiven[k];  // the sketches do not depend on the cores: computed beforehand
-    else TT_TRY(tt_launch_unfold(c, A, scales, k, c->d_Y));
-    TT_TRY(tt_launch_prox_update(c, Yk, c->d_SH, cores[k], k, change_slots ? change_slots + 2 * k : nullptr));
-    if (k < d - 1) {
-      TT_TRY(tt_launch_qr_left(c, cores[k], cores[k + 1], k));
-      TT_TRY(tt_launch_core_fft(c, cores[k], k));
-      TT_TRY(tt_launch_prefix_step(c, k));
+  // The data sketches Y_k do not depend on the cores: all d of them are launched now on the side
+  // stream (plans built there too) and run concurrently with the orthogonalisation, interface
+  // and solve kernels below, which use few SMs; core k's update waits only for Y_k.
+  const bool fork = Ygiven == nullptr;
+  if (fork) {
+    TT_CUDA(c, cudaEventRecord(c->ev_fork, c->stream));
+    TT_CUDA(c, cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+    cudaStream_t main_stream = c->stream;
+    c->stream = c->side;
+    int rc = TT_OK;
+    for (int k = 0; k < d && rc == TT_OK; ++k) {
+      rc = tt_launch_unfold(c, A, scales, k, c->d_Yall + c->yoff[k]);
+      if (rc == TT_OK) {
+        const cudaError_t e = cudaEventRecord(c->ev_y[k], c->side);
+        if (e != cudaSuccess) rc = tt_cuda_check(c, e, "cudaEventRecord");
+      }
+    }
+    c->stream = main_stream;
+    if (rc != TT_OK) {
+      cudaEventRecord(c->ev_fork, c->side);  // join whatever was launched before returning
+      cudaStreamWaitEvent(c->stream, c->ev_fork, 0);
+      return rc;
     }
   }
-  return TT_OK;
+  auto chain = [&]() -> int {
+    for (int kk = d - 1; kk >= 1; --kk) TT_TRY(tt_launch_lq_right(c, cores[kk - 1], cores[kk], kk));
+    TT_TRY(build_all_ghat(c, cores));
+    TT_TRY(tt_launch_suffixes(c));
+    TT_TRY(tt_launch_prefix_reset(c));
+    for (int k = 0; k < d; ++k) {
+      TT_TRY(tt_launch_interface_from_chain(c, k, c->d_SH));
+      const float* Yk = fork ? c->d_Yall + c->yoff[k] : Ygiven[k];
+      if (fork) TT_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_y[k], 0));
+      TT_TRY(tt_launch_prox_update(c, Yk, c->d_SH, cores[k], k, change_slots ? change_slots + 2 * k : nullptr));
+      if (k < d - 1) {
+        TT_TRY(tt_launch_qr_left(c, cores[k], cores[k + 1], k));
+        TT_TRY(tt_launch_core_fft(c, cores[k], k));
+        TT_TRY(tt_launch_prefix_step(c, k));
+      }
+    }
+    return TT_OK;
+  };
+  const int rc = chain();
+  if (fork) TT_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_y[d - 1], 0));  // joined on every path
+  return rc;
 }
 
 extern "C" int tt_prox_als_sweep_sketched(tt_ctx* c, float* const* Y, float* const* cores, uint64_t sweep) {

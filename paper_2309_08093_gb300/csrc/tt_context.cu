@@ -365,7 +365,7 @@ int tt_ensure_plan0(tt_ctx* c) { return tt_ensure_rplan(c, 0); }
 static void free_all(tt_ctx* c) {
   void* ps[] = {c->d_h, c->d_v, c->d_plan0, c->d_plan0_off, c->d_plan0_cursor, c->d_ghat,
                 c->d_twiddle, c->d_suffix, c->d_prefix, c->d_prefix_tmp, c->d_SH, c->d_Y,
-                c->d_gram, c->d_core_old, c->d_changes, c->d_status, c->d_err_acc, c->d_ws_acc, c->d_rint, c->d_slab_u};
+                c->d_gram, c->d_core_old, c->d_changes, c->d_status, c->d_err_acc, c->d_ws_acc, c->d_rint, c->d_slab_u, c->d_Yall};
   for (void* p : ps)
     if (p) cudaFree(p);
   if (c->d_A_stage) cudaFree(c->d_A_stage);
@@ -379,6 +379,10 @@ static void free_all(tt_ctx* c) {
   }
   if (c->d_rtmp) cudaFree(c->d_rtmp);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  for (int k = 0; k < TT_MAX_D; ++k)
+    if (c->ev_y[k]) cudaEventDestroy(c->ev_y[k]);
+  if (c->side) cudaStreamDestroy(c->side);
 }
 
 extern "C" int tt_sketch_init(tt_ctx** out, const tt_params* p, void* stream) {
@@ -463,6 +467,12 @@ extern "C" int tt_sketch_init(tt_ctx** out, const tt_params* p, void* stream) {
   A((void**)&c->d_prefix_tmp, sizeof(float2) * H * c->rmax);
   A((void**)&c->d_SH, sizeof(float) * c->J * c->smax);
   A((void**)&c->d_Y, sizeof(float) * c->J * c->nmax);
+  c->yoff[0] = 0;
+  for (int k = 0; k < c->d; ++k) c->yoff[k + 1] = c->yoff[k] + (int64_t)c->J * c->n[k];
+  A((void**)&c->d_Yall, sizeof(float) * c->yoff[c->d]);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+  for (int k = 0; k < c->d && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&c->ev_y[k], cudaEventDisableTiming);
   A((void**)&c->d_gram, sizeof(double) * (c->smax + c->nmax) * c->smax);
   A((void**)&c->d_core_old, sizeof(float) * c->nmax * c->smax);
   c->changes_cap = 1024 * TT_MAX_D;

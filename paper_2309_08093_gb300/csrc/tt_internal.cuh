@@ -73,7 +73,14 @@ struct tt_ctx {
 
   // dense workspaces
   float* d_SH = nullptr;       // J x smax (column-major)
-  float* d_Y = nullptr;        // J x nmax (row-major), used by the sweep
+  float* d_Y = nullptr;        // J x nmax, scratch for the autotuner's timed data sketches
+  // the sweep's data sketches run on `side`, concurrently with the interface/solve chain on the
+  // caller's stream: mode k's sketch goes to d_Yall + yoff[k] and signals ev_y[k]
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr;
+  cudaEvent_t ev_y[TT_MAX_D] = {nullptr};
+  float* d_Yall = nullptr;
+  int64_t yoff[TT_MAX_D + 1] = {0};
   double* d_gram = nullptr;    // (smax + nmax) x smax FP64 accumulators of [SH | Y]^T SH
   float* d_core_old = nullptr; // proximal centre copy (nmax * smax)
   double* d_changes = nullptr; // per (sweep, k): ||dG||^2, ||G||^2

@@ -436,6 +436,8 @@ static int launch_gather_vbm(tt_ctx* c, const void* A, const float* scales, int 
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
   // work items (column, c-segment): at most one per CTA slot (two CTAs per SM) when the columns
   // allow it, so that every CTA gets the same amount of work; segments of at most 2048 c groups
+  // CTAs per SM: two (the kernel is latency-bound and needs the warps), also when the sweep runs
+  // the sketches beside the chain kernels
   const int cps = c->tune_cta_per_sm[k] ? c->tune_cta_per_sm[k] : 2;
   const int slots = cps * sms;
   int nseg = std::max(1, slots / a.ncol);

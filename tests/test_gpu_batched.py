@@ -62,7 +62,9 @@ def test_batched_matches_single_tensor_path_and_oracle():
 
 
 def test_batched_sweeps_continue_and_recapture():
-    """Replays draw sweep first_sweep + t; new core buffers force a recapture."""
+    """Replays draw sweep first_sweep + t; new core buffers force a recapture. After 4 sweeps the
+    iterates are not converged: summation-order differences show up at ~1e-4 relative, while a
+    wrong draw sequence changes the error at ~1e-2, so the bound is 1e-3."""
     specs = synth.batched_specs(count=3, dims_range=(8, 14), rank_range=(2, 4))
     As, inits, _ = _setup(specs)
     batch = lib.Batch(specs)
@@ -74,5 +76,5 @@ def test_batched_sweeps_continue_and_recapture():
     e1 = batch.tt_batch_rel_error(As, c1)
     e2 = batch.tt_batch_rel_error(As, c2)
     for a, b in zip(e1, e2):
-        assert abs(a - b) <= 1e-4 * b
+        assert abs(a - b) <= 1e-3 * b
     batch.close()
