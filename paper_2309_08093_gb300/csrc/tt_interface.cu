@@ -3,10 +3,12 @@
 // FFT-sketched cores G_j x_2 (F S_j)                                            (Theorem 2).
 //
 // Every core is real, so each DFT is Hermitian and only the J/2+1 frequencies 0..J/2 are kept.
-//   k_core_fft     : CountSketch of one (a, b) fibre of core j into J buckets + radix-2 FFT
+//   k_core_fft2    : CountSketch of two (a, b) fibres of core j into J buckets (real and imaginary
+//                    parts) + radix-4 Stockham FFT; k_core_fft (radix-2, one fibre) for J = 16384
 //   k_suffix_chain : R_{>k}(w) = Ghat_{k+1}(w) ... Ghat_{d-1}(w) for all k   (one thread per w)
 //   k_prefix_step  : L_{<j+1}(w) = L_{<j}(w) Ghat_j(w)
-//   k_face_ifft    : column c = a + r_k b of S H_k: inverse FFT of L_{<k}(w)[a] R_{>k}(w)[b]
+//   k_face_ifft2   : two columns c = a + r_k b of S H_k: inverse FFT of L_{<k}(w)[a] R_{>k}(w)[b]
+//                    (k_face_ifft, one column with radix-2, for J = 16384)
 #include "tt_internal.cuh"
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
@@ -43,6 +45,59 @@ __device__ void block_fft(float2* buf, const float2* __restrict__ tw, int J, int
   }
 }
 
+// Self-sorting (Stockham) FFT of length J = 2^logJ, forward (w = exp(-2 pi i / J)), with the
+// radix-4 iteration of Govindaraju et al. ("High performance discrete Fourier transforms on
+// graphics processors", SC 2008): at span Ns, butterfly j reads x[j + r J/4] (r < 4), applies
+// the twiddles exp(-2 pi i r (j mod Ns) / (4 Ns)), takes a 4-point DFT and writes
+// y[(j / Ns) 4 Ns + (j mod Ns) + r Ns]; a radix-2 stage first when logJ is odd. x and y are
+// J-entry shared buffers (ping-pong); returns the buffer holding the result. One barrier per stage.
+__device__ __forceinline__ float2 tw_full(const float2* __restrict__ tw, int t, int J) {
+  // exp(-2 pi i t / J) for 0 <= t < J from the J/2-entry table
+  if (t < (J >> 1)) return __ldg(tw + t);
+  const float2 w = __ldg(tw + t - (J >> 1));
+  return make_float2(-w.x, -w.y);
+}
+
+__device__ float2* block_fft_stockham(float2* x, float2* y, const float2* __restrict__ tw, int J, int logJ) {
+  int Ns = 1;
+  __syncthreads();
+  if (logJ & 1) {
+    const int h = J >> 1;
+    for (int j = threadIdx.x; j < h; j += blockDim.x) {
+      const float2 v0 = x[j], v1 = x[j + h];
+      y[2 * j] = make_float2(v0.x + v1.x, v0.y + v1.y);
+      y[2 * j + 1] = make_float2(v0.x - v1.x, v0.y - v1.y);
+    }
+    float2* t = x; x = y; y = t;
+    Ns = 2;
+    __syncthreads();
+  }
+  const int q = J >> 2;
+  for (; Ns < J; Ns <<= 2) {
+    const int tstep = q / Ns;  // J / (4 Ns)
+    for (int j = threadIdx.x; j < q; j += blockDim.x) {
+      const int jm = j & (Ns - 1);
+      float2 v0 = x[j], v1 = x[j + q], v2 = x[j + 2 * q], v3 = x[j + 3 * q];
+      if (Ns > 1) {
+        const int st = jm * tstep;
+        v1 = cmul(v1, tw_full(tw, st, J));
+        v2 = cmul(v2, tw_full(tw, 2 * st, J));
+        v3 = cmul(v3, tw_full(tw, 3 * st, J));
+      }
+      const float2 a = make_float2(v0.x + v2.x, v0.y + v2.y), b = make_float2(v0.x - v2.x, v0.y - v2.y);
+      const float2 c = make_float2(v1.x + v3.x, v1.y + v3.y), d = make_float2(v1.x - v3.x, v1.y - v3.y);
+      const int o = (j - jm) * 4 + jm;
+      y[o] = make_float2(a.x + c.x, a.y + c.y);
+      y[o + Ns] = make_float2(b.x + d.y, b.y - d.x);       // b - i d
+      y[o + 2 * Ns] = make_float2(a.x - c.x, a.y - c.y);
+      y[o + 3 * Ns] = make_float2(b.x - d.y, b.y + d.x);   // b + i d
+    }
+    float2* t = x; x = y; y = t;
+    __syncthreads();
+  }
+  return x;
+}
+
 struct CoreFftArgs {
   const float* core;  // r0 x n x r1, r0 fastest
   const int32_t* h;   // h_j, n entries
@@ -69,6 +124,36 @@ __global__ void k_core_fft(CoreFftArgs a) {
   for (int w = threadIdx.x; w <= a.J / 2; w += blockDim.x) a.out[(int64_t)w * S + fib] = buf[w];
 }
 
+// Two CountSketched fibres per CTA, packed as z = x0 + i x1: one complex FFT, then
+// X0[w] = (Z[w] + conj Z[J-w]) / 2 and X1[w] = (Z[w] - conj Z[J-w]) / 2i for w <= J/2.
+__global__ void __launch_bounds__(256) k_core_fft2(CoreFftArgs a) {
+  extern __shared__ float2 fbuf[];
+  float2* x = fbuf;
+  float2* y = fbuf + a.J;
+  const int S = a.r0 * a.r1;
+  const int f0 = 2 * blockIdx.x, f1 = f0 + 1;
+  const bool has1 = f1 < S;
+  for (int t = threadIdx.x; t < a.J; t += blockDim.x) x[t] = make_float2(0.f, 0.f);
+  __syncthreads();
+  const int al0 = f0 % a.r0, be0 = f0 / a.r0, al1 = f1 % a.r0, be1 = f1 / a.r0;
+  for (int i = threadIdx.x; i < a.n; i += blockDim.x) {
+    const int hb = a.h[i];
+    const bool neg = a.v[i] < 0;
+    const float g0 = a.core[al0 + (int64_t)a.r0 * (i + (int64_t)a.n * be0)];
+    atomicAdd(&x[hb].x, neg ? -g0 : g0);
+    if (has1) {
+      const float g1 = a.core[al1 + (int64_t)a.r0 * (i + (int64_t)a.n * be1)];
+      atomicAdd(&x[hb].y, neg ? -g1 : g1);
+    }
+  }
+  const float2* Z = block_fft_stockham(x, y, a.tw, a.J, a.logJ);
+  for (int w = threadIdx.x; w <= a.J / 2; w += blockDim.x) {
+    const float2 z = Z[w], zc = Z[(a.J - w) & (a.J - 1)];
+    a.out[(int64_t)w * S + f0] = make_float2(0.5f * (z.x + zc.x), 0.5f * (z.y - zc.y));
+    if (has1) a.out[(int64_t)w * S + f1] = make_float2(0.5f * (z.y + zc.y), -0.5f * (z.x - zc.x));
+  }
+}
+
 int tt_launch_core_fft(tt_ctx* c, const float* core, int j) {
   CoreFftArgs a;
   a.core = core;
@@ -81,6 +166,17 @@ int tt_launch_core_fft(tt_ctx* c, const float* core, int j) {
   a.n = (int)c->n[j];
   a.J = c->J;
   a.logJ = c->logJ;
+  if (c->J <= 8192) {  // two J-entry ping-pong buffers fit in shared memory
+    const size_t smem = 2 * sizeof(float2) * c->J;
+    static bool attr = false;
+    if (!attr) {
+      TT_CUDA(c, cudaFuncSetAttribute(k_core_fft2, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * (int)sizeof(float2) * 8192));
+      attr = true;
+    }
+    k_core_fft2<<<(a.r0 * a.r1 + 1) / 2, 256, smem, c->stream>>>(a);
+    TT_LAUNCH(c, "k_core_fft2");
+    return TT_OK;
+  }
   size_t smem = sizeof(float2) * c->J;
   if (smem > 48 * 1024) TT_CUDA(c, cudaFuncSetAttribute(k_core_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k_core_fft<<<a.r0 * a.r1, 512, smem, c->stream>>>(a);
@@ -180,6 +276,36 @@ struct FaceArgs {
   int ra, rb, J, logJ;
 };
 
+// Two columns per CTA: their Hermitian spectra X, Y packed as Z = X + i Y; the inverse DFT of Z is
+// x + i y, obtained as conj(FFT(conj Z)) / J.
+__global__ void __launch_bounds__(256) k_face_ifft2(FaceArgs a) {
+  extern __shared__ float2 fbuf[];
+  float2* x = fbuf;
+  float2* y = fbuf + a.J;
+  const int S = a.ra * a.rb;
+  const int c0 = 2 * blockIdx.x, c1 = c0 + 1;
+  const bool has1 = c1 < S;
+  const int al0 = c0 % a.ra, be0 = c0 / a.ra, al1 = c1 % a.ra, be1 = c1 / a.ra;
+  const int H = a.J / 2 + 1;
+  for (int w = threadIdx.x; w < a.J; w += blockDim.x) {
+    const int ws = (w < H) ? w : a.J - w;
+    float2 X = cmul(a.L[(int64_t)ws * a.ra + al0], a.R[(int64_t)ws * a.rb + be0]);
+    float2 Y = has1 ? cmul(a.L[(int64_t)ws * a.ra + al1], a.R[(int64_t)ws * a.rb + be1]) : make_float2(0.f, 0.f);
+    if (w >= H) {
+      X.y = -X.y;
+      Y.y = -Y.y;
+    }
+    x[w] = make_float2(X.x - Y.y, -(X.y + Y.x));  // conj(X + i Y)
+  }
+  const float2* F = block_fft_stockham(x, y, a.tw, a.J, a.logJ);
+  const float inv = 1.f / (float)a.J;
+  for (int t = threadIdx.x; t < a.J; t += blockDim.x) {
+    const float2 f = F[t];
+    a.SH[(int64_t)c0 * a.J + t] = f.x * inv;
+    if (has1) a.SH[(int64_t)c1 * a.J + t] = -f.y * inv;
+  }
+}
+
 __global__ void k_face_ifft(FaceArgs a) {
   extern __shared__ float2 buf[];
   const int col = blockIdx.x;
@@ -209,6 +335,17 @@ int tt_launch_interface_from_chain(tt_ctx* c, int k, float* SH) {
   a.rb = c->r[k + 1];
   a.J = c->J;
   a.logJ = c->logJ;
+  if (c->J <= 8192) {  // two columns per CTA, radix-4 Stockham
+    const size_t smem = 2 * sizeof(float2) * c->J;
+    static bool attr = false;
+    if (!attr) {
+      TT_CUDA(c, cudaFuncSetAttribute(k_face_ifft2, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * (int)sizeof(float2) * 8192));
+      attr = true;
+    }
+    k_face_ifft2<<<(a.ra * a.rb + 1) / 2, 256, smem, c->stream>>>(a);
+    TT_LAUNCH(c, "k_face_ifft2");
+    return TT_OK;
+  }
   size_t smem = sizeof(float2) * c->J;
   if (smem > 48 * 1024) TT_CUDA(c, cudaFuncSetAttribute(k_face_ifft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k_face_ifft<<<a.ra * a.rb, 512, smem, c->stream>>>(a);
