@@ -26,6 +26,8 @@ struct GramArgs {
   int J, s, n, kchunk;
 };
 
+// Software-pipelined: the next 32-wide k tile is loaded into registers (read-only loads, all
+// issued before any use) while the current tile is multiplied from shared memory.
 __global__ void __launch_bounds__(256) k_gram(GramArgs a) {
   __shared__ float X[32][33];
   __shared__ float B[32][33];
@@ -34,23 +36,36 @@ __global__ void __launch_bounds__(256) k_gram(GramArgs a) {
   const int kb = blockIdx.z * a.kchunk, ke = min(a.J, kb + a.kchunk);
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // 16 x 16 threads, 2 x 2 outputs each
   float acc[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
-  for (int b0 = kb; b0 < ke; b0 += 32) {
-    for (int idx = threadIdx.x; idx < 32 * 32; idx += 256) {
-      int kk = idx & 31, cc = idx >> 5;
-      int b = b0 + kk;
-      int gr = r0 + cc, gc = c0 + cc;
+  float xr[4], br[4];
+  auto load = [&](int b0) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int idx = threadIdx.x + 256 * u;
+      const int kk = idx & 31, cc = idx >> 5;
+      const int b = b0 + kk;
+      const int gr = r0 + cc, gc = c0 + cc;
       float xv = 0.f, bv = 0.f;
       if (b < ke) {
         if (gr < a.s)
-          xv = a.SH[(int64_t)gr * a.J + b];
+          xv = __ldg(a.SH + (int64_t)gr * a.J + b);
         else if (gr < rows)
-          xv = a.Y[(int64_t)(gr - a.s) * a.J + b];
-        if (gc < a.s) bv = a.SH[(int64_t)gc * a.J + b];
+          xv = __ldg(a.Y + (int64_t)(gr - a.s) * a.J + b);
+        if (gc < a.s) bv = __ldg(a.SH + (int64_t)gc * a.J + b);
       }
-      X[kk][cc] = xv;
-      B[kk][cc] = bv;
+      xr[u] = xv;
+      br[u] = bv;
+    }
+  };
+  if (kb < ke) load(kb);
+  for (int b0 = kb; b0 < ke; b0 += 32) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int idx = threadIdx.x + 256 * u;
+      X[idx & 31][idx >> 5] = xr[u];
+      B[idx & 31][idx >> 5] = br[u];
     }
     __syncthreads();
+    if (b0 + 32 < ke) load(b0 + 32);  // in flight during the FMAs below
 #pragma unroll 8
     for (int kk = 0; kk < 32; ++kk) {
       float x0 = X[kk][ty], x1 = X[kk][ty + 16];
@@ -118,11 +133,18 @@ __global__ void __launch_bounds__(1024) k_prox_solve(SolveArgs a) {
   const int t = threadIdx.x, T = blockDim.x;
   const int lane = t & 31, warp = t >> 5;
   if (*a.status != 0) return;
-  for (int idx = t; idx < s * s; idx += T) {
-    const int i = idx / s, j = idx - i * s;
-    double m = a.C[idx];
-    if (i == j) m += a.sigma;
-    M[i * P + j] = (float)m;
+  for (int b0 = t; b0 < s * s; b0 += 4 * T) {  // four independent loads in flight per thread
+    double v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = (b0 + u * T < s * s) ? __ldg(a.C + b0 + u * T) : 0.0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int idx = b0 + u * T;
+      if (idx < s * s) {
+        const int i = idx / s, j = idx - i * s;
+        M[i * P + j] = (float)(i == j ? v[u] + a.sigma : v[u]);
+      }
+    }
   }
   if (t == 0) bad = 0;
   __syncthreads();
@@ -512,6 +534,27 @@ __device__ QrSmem qr_layout(float* sm, int m, int q, int use_chol) {
   return L;
 }
 
+// Copy `total` floats from global into shared memory with UB independent loads in flight per
+// thread: the loads of a batch are issued before any of its stores (a plain copy loop waits for
+// each global load in turn). src(idx) / dst(idx) give the source and destination addresses.
+template <typename Src, typename Dst>
+__device__ __forceinline__ void stage_batched(int total, Src src, Dst dst) {
+  constexpr int UB = 8;
+  for (int b0 = threadIdx.x; b0 < total; b0 += UB * blockDim.x) {
+    float v[UB];
+#pragma unroll
+    for (int u = 0; u < UB; ++u) {
+      const int idx = b0 + u * blockDim.x;
+      v[u] = idx < total ? *src(idx) : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < UB; ++u) {
+      const int idx = b0 + u * blockDim.x;
+      if (idx < total) *dst(idx) = v[u];
+    }
+  }
+}
+
 // G_k^L (m = r0 n rows, q = r1 cols) = Q R; G_k <- Q (zero-padded); G_{k+1} <- R G_{k+1}^R
 __global__ void __launch_bounds__(512) k_qr_left(float* core, float* next, int r0, int n, int r1,
                                                  int ncols_next, int use_chol, const int* status) {
@@ -522,10 +565,8 @@ __global__ void __launch_bounds__(512) k_qr_left(float* core, float* next, int r
   const QrSmem L = qr_layout(sm, m, q, use_chol);
   bool ok = false;
   if (use_chol && m >= q) {
-    for (int idx = threadIdx.x; idx < m * q; idx += blockDim.x) {
-      const int r = idx % m, j = idx / m;
-      L.A[r + L.lda * j] = core[idx];
-    }
+    stage_batched(m * q, [&](int idx) { return core + idx; },
+                  [&](int idx) { return L.A + (idx % m) + (int64_t)L.lda * (idx / m); });
     __syncthreads();
     ok = block_cholqr2(L.A, m, q, L.lda, L.Rm, L.W, L.Rp, &flag);
     __syncthreads();
@@ -536,7 +577,7 @@ __global__ void __launch_bounds__(512) k_qr_left(float* core, float* next, int r
       }
   }
   if (!ok) {  // Householder on a dense copy of the input (G_k^L is column-major, pitch m)
-    for (int idx = threadIdx.x; idx < m * q; idx += blockDim.x) L.A[idx] = core[idx];
+    stage_batched(m * q, [&](int idx) { return core + idx; }, [&](int idx) { return L.A + idx; });
     __syncthreads();
     block_householder_qr(L.A, m, q, L.Rm, L.tau, L.colsc);
     const int p = min(m, q);
@@ -550,7 +591,7 @@ __global__ void __launch_bounds__(512) k_qr_left(float* core, float* next, int r
   for (int c0 = 0; c0 < ncols_next; c0 += cols_per) {
     const int nc = min(cols_per, ncols_next - c0);
     float* g = next + (int64_t)c0 * r1;
-    for (int idx = threadIdx.x; idx < nc * r1; idx += blockDim.x) L.A[idx] = g[idx];
+    stage_batched(nc * r1, [&](int idx) { return g + idx; }, [&](int idx) { return L.A + idx; });
     __syncthreads();
     for (int idx = threadIdx.x; idx < nc * r1; idx += blockDim.x) {
       const int cc = idx / r1, a2 = idx - cc * r1;
@@ -573,10 +614,8 @@ __global__ void __launch_bounds__(512) k_lq_right(float* prev, float* core, int 
   const QrSmem L = qr_layout(sm, m, q, use_chol);
   bool ok = false;
   if (use_chol && m >= q) {
-    for (int idx = threadIdx.x; idx < m * q; idx += blockDim.x) {
-      const int i = idx % m, a2 = idx / m;
-      L.A[i + L.lda * a2] = core[a2 + (int64_t)r0 * i];
-    }
+    stage_batched(m * q, [&](int idx) { return core + (idx / m) + (int64_t)r0 * (idx % m); },
+                  [&](int idx) { return L.A + (idx % m) + (int64_t)L.lda * (idx / m); });
     __syncthreads();
     ok = block_cholqr2(L.A, m, q, L.lda, L.Rm, L.W, L.Rp, &flag);
     __syncthreads();
@@ -587,10 +626,8 @@ __global__ void __launch_bounds__(512) k_lq_right(float* prev, float* core, int 
       }
   }
   if (!ok) {
-    for (int idx = threadIdx.x; idx < m * q; idx += blockDim.x) {
-      const int i = idx % m, a2 = idx / m;
-      L.A[idx] = core[a2 + (int64_t)r0 * i];  // dense, pitch m
-    }
+    stage_batched(m * q, [&](int idx) { return core + (idx / m) + (int64_t)r0 * (idx % m); },
+                  [&](int idx) { return L.A + idx; });  // dense, pitch m
     __syncthreads();
     block_householder_qr(L.A, m, q, L.Rm, L.tau, L.colsc);
     const int p = min(m, q);
@@ -605,10 +642,8 @@ __global__ void __launch_bounds__(512) k_lq_right(float* prev, float* core, int 
   const int rows_per = (int)(cap / r0 > 1 ? cap / r0 : 1);
   for (int t0 = 0; t0 < nrows_prev; t0 += rows_per) {
     const int nr = min(rows_per, nrows_prev - t0);
-    for (int idx = threadIdx.x; idx < nr * r0; idx += blockDim.x) {
-      const int a2 = idx / nr, tt = idx - a2 * nr;
-      L.A[idx] = prev[t0 + tt + (int64_t)nrows_prev * a2];  // A[a2 * nr + tt]
-    }
+    stage_batched(nr * r0, [&](int idx) { return prev + t0 + (idx % nr) + (int64_t)nrows_prev * (idx / nr); },
+                  [&](int idx) { return L.A + idx; });  // A[a2 * nr + tt]
     __syncthreads();
     for (int idx = threadIdx.x; idx < nr * r0; idx += blockDim.x) {
       const int b = idx / nr, tt = idx - b * nr;
