@@ -97,8 +97,8 @@ extern "C" int tt_orthogonalize(tt_ctx* c, float* const* cores, int direction, i
 }
 
 // One outer iteration of Algorithm 1; change slots receive ||dG_k||^2, ||G_k||^2 per core.
-int tt_one_sweep(tt_ctx* c, const void* A, const float* scales, float* const* cores, uint64_t sweep,
-                     double* change_slots, float* const* Ygiven) {
+static int sweep_body(tt_ctx* c, const void* A, const float* scales, float* const* cores, uint64_t sweep,
+                      double* change_slots, float* const* Ygiven) {
   const int d = c->d;
   TT_TRY(tt_ensure_tables(c, sweep));
   // The data sketches Y_k do not depend on the cores: all d of them are launched now on the side
@@ -110,6 +110,7 @@ int tt_one_sweep(tt_ctx* c, const void* A, const float* scales, float* const* co
     TT_CUDA(c, cudaStreamWaitEvent(c->side, c->ev_fork, 0));
     cudaStream_t main_stream = c->stream;
     c->stream = c->side;
+    c->in_sweep = true;
     int rc = TT_OK;
     for (int k = 0; k < d && rc == TT_OK; ++k) {
       rc = tt_launch_unfold(c, A, scales, k, c->d_Yall + c->yoff[k]);
@@ -119,6 +120,7 @@ int tt_one_sweep(tt_ctx* c, const void* A, const float* scales, float* const* co
       }
     }
     c->stream = main_stream;
+    c->in_sweep = false;
     if (rc != TT_OK) {
       cudaEventRecord(c->ev_fork, c->side);  // join whatever was launched before returning
       cudaStreamWaitEvent(c->stream, c->ev_fork, 0);
@@ -145,6 +147,21 @@ int tt_one_sweep(tt_ctx* c, const void* A, const float* scales, float* const* co
   };
   const int rc = chain();
   if (fork) TT_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_y[d - 1], 0));  // joined on every path
+  return rc;
+}
+
+// One outer iteration of Algorithm 1 on the context's high-priority stream, ordered after the
+// caller's stream and joined back into it on every return path.
+int tt_one_sweep(tt_ctx* c, const void* A, const float* scales, float* const* cores, uint64_t sweep,
+                 double* change_slots, float* const* Ygiven) {
+  cudaStream_t caller = c->stream;
+  TT_CUDA(c, cudaEventRecord(c->ev_in, caller));
+  TT_CUDA(c, cudaStreamWaitEvent(c->hi, c->ev_in, 0));
+  c->stream = c->hi;
+  const int rc = sweep_body(c, A, scales, cores, sweep, change_slots, Ygiven);
+  c->stream = caller;
+  TT_CUDA(c, cudaEventRecord(c->ev_out, c->hi));
+  TT_CUDA(c, cudaStreamWaitEvent(caller, c->ev_out, 0));
   return rc;
 }
 

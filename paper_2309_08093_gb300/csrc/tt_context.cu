@@ -383,6 +383,9 @@ static void free_all(tt_ctx* c) {
   for (int k = 0; k < TT_MAX_D; ++k)
     if (c->ev_y[k]) cudaEventDestroy(c->ev_y[k]);
   if (c->side) cudaStreamDestroy(c->side);
+  if (c->hi) cudaStreamDestroy(c->hi);
+  if (c->ev_in) cudaEventDestroy(c->ev_in);
+  if (c->ev_out) cudaEventDestroy(c->ev_out);
 }
 
 extern "C" int tt_sketch_init(tt_ctx** out, const tt_params* p, void* stream) {
@@ -471,6 +474,13 @@ extern "C" int tt_sketch_init(tt_ctx** out, const tt_params* p, void* stream) {
   for (int k = 0; k < c->d; ++k) c->yoff[k + 1] = c->yoff[k] + (int64_t)c->J * c->n[k];
   A((void**)&c->d_Yall, sizeof(float) * c->yoff[c->d]);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) {
+    int least = 0, greatest = 0;
+    e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->hi, cudaStreamNonBlocking, greatest);
+  }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
   for (int k = 0; k < c->d && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&c->ev_y[k], cudaEventDisableTiming);
   A((void**)&c->d_gram, sizeof(double) * (c->smax + c->nmax) * c->smax);

@@ -77,6 +77,11 @@ struct tt_ctx {
   // the sweep's data sketches run on `side`, concurrently with the interface/solve chain on the
   // caller's stream: mode k's sketch goes to d_Yall + yoff[k] and signals ev_y[k]
   cudaStream_t side = nullptr;
+  // the chain itself runs on `hi`, a highest-priority stream forked from (and joined back to) the
+  // caller's stream, so that its small kernels get SM slots ahead of the data-sketch CTAs
+  cudaStream_t hi = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  bool in_sweep = false;       // data sketches launched inside a sweep: finer work items
   cudaEvent_t ev_fork = nullptr;
   cudaEvent_t ev_y[TT_MAX_D] = {nullptr};
   float* d_Yall = nullptr;

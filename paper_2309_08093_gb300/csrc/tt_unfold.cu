@@ -442,6 +442,7 @@ static int launch_gather_vbm(tt_ctx* c, const void* A, const float* scales, int 
   const int slots = cps * sms;
   int nseg = std::max(1, slots / a.ncol);
   if (c->tune_seg_mult[k]) nseg *= c->tune_seg_mult[k];
+  else if (c->in_sweep) nseg *= 4;  // beside the chain: short CTAs free SM slots often
   nseg = std::max(nseg, (c->J + 2047) / 2048);
   a.nseg = nseg;
   a.segmax = (c->J + nseg - 1) / nseg + 1;
@@ -453,7 +454,11 @@ static int launch_gather_vbm(tt_ctx* c, const void* A, const float* scales, int 
   int per_sm = 1;
   TT_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_unfold_gather<DT, VB, S, M, MODE0>, THREADS, smem));
   const int items = a.ncol * a.nseg;
-  const int blocks = std::max(1, std::min(items, sms * std::max(1, std::min(per_sm, cps))));
+  // one CTA per item inside a sweep (the scheduler hands freed slots to the high-priority chain
+  // first); otherwise at most one wave
+  const int blocks = (c->in_sweep && !c->tune_seg_mult[k])
+                         ? std::max(1, items)
+                         : std::max(1, std::min(items, sms * std::max(1, std::min(per_sm, cps))));
   k_unfold_gather<DT, VB, S, M, MODE0><<<blocks, THREADS, smem, c->stream>>>(a);
   TT_LAUNCH(c, "k_unfold_gather");
   return TT_OK;
