@@ -137,7 +137,7 @@ def cpu_sample_main(args):
 
     w = synth.WORKLOADS[args.workload]
     p = synth.make_problem(w, storage=args.storage)
-    if args.cpu_columns <= 0:
+    if args.cpu_columns == 0:  # (negative: the reference arm's automatic sample size)
         t = time.perf_counter()
         O.tt_ts_sweep(p.tensor, p.init_cores, p.sketch_seed, 0, w.J, w.lam)
         dt = time.perf_counter() - t
