@@ -175,6 +175,22 @@ def run_cpu_child(extra):
     return json.loads(p.stdout.strip().splitlines()[-1])
 
 
+def max_over_ranks(ms, dist, dev):
+    """Timed-region length of the slowest rank (every rank gets it); ms itself on one process."""
+    if dist is None:
+        return ms
+    import torch
+
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(world, steps, max_ms):
+    """Whole-job sweeps/s: every rank sweeps its own replica `steps` times within max_ms."""
+    return world * steps / (max_ms / 1e3)
+
+
 def reference_main(args, rank, world):
     if rank != 0:
         return
@@ -553,12 +569,8 @@ def main():
     del Yiso
     clocks.stop()
     clk = clocks.summary(t_wall0, t_wall1)
-    ms = e0.elapsed_time(e1)
-    if dist:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    sweeps_per_s = world * args.steps / (ms / 1e3)
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
+    sweeps_per_s = replica_throughput(world, args.steps, ms)
 
     hbm, peak_kind = peaks()
     unfold_avg_ms = prof["unfold_ms"] / max(1, prof["unfold_launches"])
