@@ -41,7 +41,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-patterns", action="store_true", help="skip the precision/batched/warm-start patterns")
-    ap.add_argument("--only-pattern", default=None, choices=["precision", "batched", "warmstart"],
+    ap.add_argument("--only-pattern", default=None, choices=["precision", "batched", "warmstart", "gemm"],
                     help="run one pattern and print its JSON")
     ap.add_argument("--ws-train", type=int, default=10240, help="warm-start training solves")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
@@ -326,6 +326,45 @@ def batched_pattern(dev, nsweeps=10, count=256):
                     "the sweep included"}
 
 
+def bf16_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured"
+    except Exception:
+        return 1900.0, "fallback"
+
+
+def gemm_pattern(dev, reps=10):
+    """The network's tcgen05 GEMM (C = A B^T, BF16 in, FP32 accumulators in tensor memory) timed
+    alone with CUDA events: a large square problem and the warm-start network's training shapes."""
+    import torch
+    from paper_2309_08093_gb300 import lib
+
+    peak, kind = bf16_peak()
+    stream = torch.cuda.current_stream()
+    out = {"peak_tflops": peak, "peak_kind": kind, "shapes": {}}
+    for M, N, K in [(8192, 8192, 8192), (256, 23232, 512), (23232, 512, 256), (256, 512, 5184)]:
+        A = torch.randn(M, K, device=dev).to(torch.bfloat16)
+        B = torch.randn(N, K, device=dev).to(torch.bfloat16)
+        C = torch.empty(M, N, device=dev)
+        for _ in range(3):
+            lib.tt_mlp_gemm_bf16(A, B, C, M, N, K, K, K, N, check=False)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            lib.tt_mlp_gemm_bf16(A, B, C, M, N, K, K, K, N, check=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        tf = 2.0 * M * N * K / (ms * 1e-3) / 1e12
+        out["shapes"][f"{M}x{N}x{K}"] = {"ms": ms, "tflops": tf, "frac": tf / peak}
+        del A, B, C
+    out["note"] = ("one kernel per call, no split-K (the network splits K for its small-M shapes); "
+                   "frac against the measured cuBLAS BF16 burst peak")
+    return out
+
+
 # ---------------------------------------------------------------------------------------------
 # learned-warm-start pattern: the network (summary of the data sketch -> initial cores) trained
 # on method-generated solves of the 256 x 256 x 3 x 128 smooth-core family, then held-out tensors
@@ -499,6 +538,8 @@ def main():
             out = batched_pattern(dev)
         elif args.only_pattern == "warmstart":
             out = warmstart_pattern(dev, n_train=args.ws_train)
+        elif args.only_pattern == "gemm":
+            out = gemm_pattern(dev)
         else:
             w = synth.WORKLOADS[args.workload]
             out = precision_pattern(w, synth.make_problem(w, storage="f32"), dev, w.sweeps)
@@ -632,6 +673,8 @@ def main():
         line["patterns"]["batched"] = batched_pattern(dev)
         torch.cuda.empty_cache()
         line["patterns"]["warmstart"] = warmstart_pattern(dev, n_train=args.ws_train)
+        torch.cuda.empty_cache()
+        line["patterns"]["gemm"] = gemm_pattern(dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
             res = run_cpu_child(["--workload", args.workload] + (["--storage", args.storage] if args.storage else []))

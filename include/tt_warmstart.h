@@ -91,7 +91,7 @@ int tt_mlp_train_step(tt_mlp* m, const float* X_dev, int ldx, const float* T_dev
  * The network's GEMM on its own: C (M x N, FP32, row stride ldc) = A (M x K) B (N x K)^T with A
  * and B row-major BF16 (raw 16-bit patterns, row strides lda, ldb). K must be a multiple of 64;
  * lda and ldb multiples of 8 and every row 16-byte aligned; M, N >= 1. One tcgen05 kernel:
- * 128 x 128 tiles, FP32 accumulators in tensor memory. Asynchronous on `cuda_stream`; returns
+ * 128 x 256 tiles, FP32 accumulators in tensor memory. Asynchronous on `cuda_stream`; returns
  * TT_ETIMEOUT (after synchronising) only if a bounded wait inside the kernel gave up, which the
  * call checks when `check` is non-zero.
  */

@@ -1,9 +1,9 @@
 // Learned warm start: the MLP's kernels and its C ABI (include/tt_warmstart.h).
 //
-//   k_gemm_tn<EPI>  : C = A B^T, A (M x K) and B (N x K) row-major BF16, one 128 x 128 tile per
+//   k_gemm_tn<EPI>  : C = A B^T, A (M x K) and B (N x K) row-major BF16, one 128 x 256 tile per
 //                     CTA. Operands are staged by cp.async into shared memory in the canonical
 //                     no-swizzle K-major layout (8 x 16-byte core matrices); one thread issues
-//                     tcgen05.mma (kind::f16, BF16 x BF16 -> FP32) into a 128-column tensor-memory
+//                     tcgen05.mma (kind::f16, BF16 x BF16 -> FP32) into a 256-column tensor-memory
 //                     accumulator; completion is signalled by tcgen05.commit on an mbarrier per
 //                     stage. Four stages: tile kt+2 loads while the MMAs of kt-1 and kt run. The
 //                     epilogue reads the accumulator with tcgen05.ld (warp w owns lanes 32w..32w+31)
@@ -36,11 +36,12 @@ namespace {
 
 typedef __nv_bfloat16 bf16;
 
-constexpr int GM = 128, GN = 128, GK = 64, GSTAGES = 4;
+constexpr int GM = 128, GK = 64, GSTAGES = 4;  // tile N (BN) is 128 or 256, per launch
 constexpr int A_STAGE = GM * GK * 2;  // bytes per stage of A
-constexpr int B_STAGE = GN * GK * 2;
-constexpr int GEMM_SMEM = GSTAGES * (A_STAGE + B_STAGE) + 1024 + 128;
-constexpr uint32_t TMEM_COLS = 128;
+template <int BN>
+constexpr int b_stage() { return BN * GK * 2; }
+template <int BN>
+constexpr int gemm_smem() { return GSTAGES * (A_STAGE + b_stage<BN>()) + 1024 + 128; }
 constexpr unsigned long long WAIT_NS = 2000000000ull;  // an mbarrier wait gives up after 2 s
 
 enum { EPI_F32 = 0, EPI_GELU = 1, EPI_DGELU = 2 };
@@ -82,8 +83,10 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
 
 // Instruction descriptor of tcgen05.mma kind::f16: D FP32 (bits 4-5 = 1), A BF16 (bits 7-9 = 1),
 // B BF16 (bits 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at 24-28.
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(GN >> 3) << 17) |
-                           ((uint32_t)(GM >> 4) << 24);
+template <int BN>
+constexpr uint32_t idesc() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(GM >> 4) << 24);
+}
 
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool valid) {
   const int sz = valid ? 16 : 0;  // 0 = fill the 16 bytes with zeros, read nothing
@@ -166,12 +169,13 @@ __device__ __forceinline__ float gelu_grad_f(float z) {
   return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
 }
 
-// Stage one 128 x 64 BF16 tile (rows r0.., columns k0..k0+63 of a row-major matrix) into the
+// Stage one ROWS x 64 BF16 tile (rows r0.., columns k0..k0+63 of a row-major matrix) into the
 // no-swizzle K-major layout: 16-byte chunk (row, c) at (row / 8) * 1024 + c * 128 + (row % 8) * 16.
+template <int ROWS>
 __device__ __forceinline__ void load_tile(uint32_t sbase, const bf16* M, int ld, int rows, int r0, int k0,
                                           int tid) {
 #pragma unroll
-  for (int j = 0; j < 8; ++j) {
+  for (int j = 0; j < ROWS / 16; ++j) {
     const int q = tid + 128 * j;
     const int row = q >> 3, c = q & 7;
     const int g = r0 + row;
@@ -181,8 +185,10 @@ __device__ __forceinline__ void load_tile(uint32_t sbase, const bf16* M, int ld,
   }
 }
 
-template <int EPI>
+template <int EPI, int BN>
 __global__ void __launch_bounds__(128, 1) k_gemm_tn(GemmArgs g) {
+  constexpr int B_STAGE = b_stage<BN>();
+  constexpr uint32_t TMEM_COLS = BN;  // the 128 x BN FP32 accumulator
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = smem;
@@ -192,7 +198,7 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tn(GemmArgs g) {
   volatile int* s_err = (volatile int*)(s_tmem + 2);  // two slots, alternating by iteration
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int m0 = blockIdx.y * GM, n0 = blockIdx.x * GN;
+  const int m0 = blockIdx.y * GM, n0 = blockIdx.x * BN;
   const int kbeg = blockIdx.z * g.kchunk;
   const int KT = (min(g.K, kbeg + g.kchunk) - kbeg) / GK;
 
@@ -214,12 +220,12 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tn(GemmArgs g) {
   const uint32_t tmem = *s_tmem;
   const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
 
-  load_tile(a0, g.A, g.lda, g.M, m0, kbeg, tid);
-  load_tile(b0, g.B, g.ldb, g.N, n0, kbeg, tid);
+  load_tile<GM>(a0, g.A, g.lda, g.M, m0, kbeg, tid);
+  load_tile<BN>(b0, g.B, g.ldb, g.N, n0, kbeg, tid);
   cp_async_commit();
   if (KT > 1) {
-    load_tile(a0 + A_STAGE, g.A, g.lda, g.M, m0, kbeg + GK, tid);
-    load_tile(b0 + B_STAGE, g.B, g.ldb, g.N, n0, kbeg + GK, tid);
+    load_tile<GM>(a0 + A_STAGE, g.A, g.lda, g.M, m0, kbeg + GK, tid);
+    load_tile<BN>(b0 + B_STAGE, g.B, g.ldb, g.N, n0, kbeg + GK, tid);
   }
   cp_async_commit();
 
@@ -242,14 +248,14 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tn(GemmArgs g) {
       const uint32_t sa = a0 + s * A_STAGE, sb = b0 + s * B_STAGE;
 #pragma unroll
       for (int kk = 0; kk < GK / 16; ++kk)
-        tc_mma(tmem, smem_desc(sa + kk * 256, 128, 1024), smem_desc(sb + kk * 256, 128, 1024), IDESC,
+        tc_mma(tmem, smem_desc(sa + kk * 256, 128, 1024), smem_desc(sb + kk * 256, 128, 1024), idesc<BN>(),
                (kt > 0 || kk > 0) ? 1u : 0u);
       tc_commit(smem_u32(&mbar[s]));
     }
     if (kt + 2 < KT) {
       const int s2 = (kt + 2) % GSTAGES;
-      load_tile(a0 + s2 * A_STAGE, g.A, g.lda, g.M, m0, kbeg + (kt + 2) * GK, tid);
-      load_tile(b0 + s2 * B_STAGE, g.B, g.ldb, g.N, n0, kbeg + (kt + 2) * GK, tid);
+      load_tile<GM>(a0 + s2 * A_STAGE, g.A, g.lda, g.M, m0, kbeg + (kt + 2) * GK, tid);
+      load_tile<BN>(b0 + s2 * B_STAGE, g.B, g.ldb, g.N, n0, kbeg + (kt + 2) * GK, tid);
     }
     cp_async_commit();
   }
@@ -267,7 +273,7 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tn(GemmArgs g) {
   if (!failed) {
     const int row = m0 + 32 * warp + lane;
     const bool row_ok = row < g.M;
-    for (int c0 = 0; c0 < GN; c0 += 32) {
+    for (int c0 = 0; c0 < BN; c0 += 32) {
       if (n0 + c0 >= g.N) break;  // uniform over the CTA
       uint32_t r[32];
       tc_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, r);
@@ -553,24 +559,33 @@ int mfail(tt_mlp* m, int code, const char* fmt, ...) {
     if (_r != TT_OK) return _r; \
   } while (0)
 
-template <int EPI>
-int launch_tiles(tt_mlp* m, const GemmArgs& g, int nsplit, cudaStream_t s) {
+template <int EPI, int BN>
+int launch_tiles_bn(tt_mlp* m, const GemmArgs& g, int nsplit, cudaStream_t s) {
   static bool attr_done = false;  // per template instance; the attribute is per function
   if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(k_gemm_tn<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, GEMM_SMEM);
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_tn<EPI, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, gemm_smem<BN>());
     if (e != cudaSuccess) return mfail(m, TT_ECUDA, "gemm smem attribute: %s", cudaGetErrorString(e));
     attr_done = true;
   }
-  dim3 grid((g.N + GN - 1) / GN, (g.M + GM - 1) / GM, nsplit);
-  k_gemm_tn<EPI><<<grid, 128, GEMM_SMEM, s>>>(g);
+  dim3 grid((g.N + BN - 1) / BN, (g.M + GM - 1) / GM, nsplit);
+  k_gemm_tn<EPI, BN><<<grid, 128, gemm_smem<BN>(), s>>>(g);
   MLP_LAUNCH(m, "k_gemm_tn");
   return TT_OK;
+}
+
+// 128 x 256 tiles when that still gives every SM a CTA (fewer operand re-reads per FLOP),
+// 128 x 128 otherwise
+template <int EPI>
+int launch_tiles(tt_mlp* m, const GemmArgs& g, int nsplit, cudaStream_t s) {
+  const int64_t wide = (int64_t)((g.N + 255) / 256) * ((g.M + GM - 1) / GM) * nsplit;
+  if (wide >= 148) return launch_tiles_bn<EPI, 256>(m, g, nsplit, s);
+  return launch_tiles_bn<EPI, 128>(m, g, nsplit, s);
 }
 
 // Number of K splits: enough CTAs to cover the SMs when the tile grid is small, at least four
 // K tiles per split, at most 32 splits, and partial products that fit the workspace.
 int choose_split(int M, int N, int K, int64_t cap) {
-  const int tiles = ((M + GM - 1) / GM) * ((N + GN - 1) / GN);
+  const int tiles = ((M + GM - 1) / GM) * ((N + 127) / 128);
   const int KT = K / GK;
   if (tiles >= 100 || KT < 8) return 1;
   int s = std::min(KT / 4, (148 + tiles - 1) / tiles);

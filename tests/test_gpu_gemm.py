@@ -16,7 +16,9 @@ from paper_2309_08093_gb300 import lib  # noqa: E402
 
 
 @pytest.mark.parametrize("M,N,K,pad", [(128, 128, 64, 0), (200, 300, 192, 8), (256, 512, 1024, 0),
-                                       (1, 7, 64, 0), (130, 129, 320, 16), (384, 256, 4096, 0)])
+                                       (1, 7, 64, 0), (130, 129, 320, 16), (384, 256, 4096, 0),
+                                       # enough 128 x 256 tiles for the wide-tile kernel (one per SM)
+                                       (2048, 2560, 128, 0), (2000, 2600, 192, 8)])
 def test_gemm_bf16_tn_matches_fp64(M, N, K, pad):
     g = torch.Generator(device="cuda")
     g.manual_seed(M * 7919 + N * 31 + K)
