@@ -20,6 +20,8 @@
 // Padded shapes: in_p = roundup(in, 64), out_p = roundup(out, 64), batch rows padded to Bp =
 // roundup(batch, 64) inside the batch_max buffers. Padding entries of weights and inputs are zero
 // and receive zero gradients, so they stay zero.
+#include <cuda.h>  // CUtensorMap (the encoder is fetched through the runtime: no libcuda link)
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -81,22 +83,38 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
   return d;
 }
 
+// The same for the 128-byte swizzled K-major layout that TMA writes with SWIZZLE_128B: rows of
+// 128 bytes (64 BF16 of K) whose 16-byte chunks are permuted by row mod 8, 8-row atoms 1024 bytes
+// apart (stride byte offset), leading-dimension offset unused (encoded as 16 bytes), swizzle mode 2
+// at bits 61-63. The 16-element K steps of one atom advance the start address by 32 bytes; every
+// atom starts on a 1024-byte boundary (base offset 0).
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t addr, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(addr), "r"(bytes) : "memory");
+}
+
+// 2-D tiled TMA load of the box at (x = K column, y = row) into shared memory; completion is
+// counted on the mbarrier (complete_tx). x is a multiple of 64 BF16 (128 bytes).
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* tm, int x, int y, uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(mbar)
+      : "memory");
+}
+
 // Instruction descriptor of tcgen05.mma kind::f16: D FP32 (bits 4-5 = 1), A BF16 (bits 7-9 = 1),
 // B BF16 (bits 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at 24-28.
 template <int BN>
 constexpr uint32_t idesc() {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(GM >> 4) << 24);
-}
-
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool valid) {
-  const int sz = valid ? 16 : 0;  // 0 = fill the 16 bytes with zeros, read nothing
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(sz)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
 __device__ __forceinline__ void mbar_init(uint32_t addr, uint32_t count) {
@@ -169,33 +187,20 @@ __device__ __forceinline__ float gelu_grad_f(float z) {
   return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
 }
 
-// Stage one ROWS x 64 BF16 tile (rows r0.., columns k0..k0+63 of a row-major matrix) into the
-// no-swizzle K-major layout: 16-byte chunk (row, c) at (row / 8) * 1024 + c * 128 + (row % 8) * 16.
-template <int ROWS>
-__device__ __forceinline__ void load_tile(uint32_t sbase, const bf16* M, int ld, int rows, int r0, int k0,
-                                          int tid) {
-#pragma unroll
-  for (int j = 0; j < ROWS / 16; ++j) {
-    const int q = tid + 128 * j;
-    const int row = q >> 3, c = q & 7;
-    const int g = r0 + row;
-    const bool ok = g < rows;
-    const bf16* src = ok ? M + (int64_t)g * ld + k0 + c * 8 : M;
-    cp_async16(sbase + (uint32_t)((row >> 3) * 1024 + c * 128 + (row & 7) * 16), src, ok);
-  }
-}
-
 template <int EPI, int BN>
-__global__ void __launch_bounds__(128, 1) k_gemm_tn(GemmArgs g) {
+__global__ void __launch_bounds__(128, 1) k_gemm_tn(const __grid_constant__ CUtensorMap tmA,
+                                                    const __grid_constant__ CUtensorMap tmB, GemmArgs g) {
   constexpr int B_STAGE = b_stage<BN>();
   constexpr uint32_t TMEM_COLS = BN;  // the 128 x BN FP32 accumulator
+  constexpr uint32_t STAGE_BYTES = A_STAGE + B_STAGE;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = smem;
   uint8_t* sB = smem + GSTAGES * A_STAGE;
-  uint64_t* mbar = (uint64_t*)(sB + GSTAGES * B_STAGE);
-  uint32_t* s_tmem = (uint32_t*)(mbar + GSTAGES);
-  volatile int* s_err = (volatile int*)(s_tmem + 2);  // two slots, alternating by iteration
+  uint64_t* full = (uint64_t*)(sB + GSTAGES * B_STAGE);  // TMA bytes of a stage have landed
+  uint64_t* empty = full + GSTAGES;                        // the MMAs reading a stage are done
+  uint32_t* s_tmem = (uint32_t*)(empty + GSTAGES);
+  volatile int* s_err = (volatile int*)(s_tmem + 2);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m0 = blockIdx.y * GM, n0 = blockIdx.x * BN;
@@ -203,10 +208,12 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tn(GemmArgs g) {
   const int KT = (min(g.K, kbeg + g.kchunk) - kbeg) / GK;
 
   if (tid == 0) {
-    for (int s = 0; s < GSTAGES; ++s) mbar_init(smem_u32(&mbar[s]), 1);
-    s_err[0] = 0;
-    s_err[1] = 0;
-    s_err[2] = 0;
+    for (int s = 0; s < GSTAGES; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
+    *s_err = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(s_tmem)),
@@ -220,54 +227,42 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tn(GemmArgs g) {
   const uint32_t tmem = *s_tmem;
   const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
 
-  load_tile<GM>(a0, g.A, g.lda, g.M, m0, kbeg, tid);
-  load_tile<BN>(b0, g.B, g.ldb, g.N, n0, kbeg, tid);
-  cp_async_commit();
-  if (KT > 1) {
-    load_tile<GM>(a0 + A_STAGE, g.A, g.lda, g.M, m0, kbeg + GK, tid);
-    load_tile<BN>(b0 + B_STAGE, g.B, g.ldb, g.N, n0, kbeg + GK, tid);
-  }
-  cp_async_commit();
-
-  bool failed = false;
-  for (int kt = 0; kt < KT; ++kt) {
-    const int s = kt % GSTAGES;
-    cp_async_wait<1>();  // this thread's copies of tile kt have landed
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    if (tid == 0 && kt >= 2) {  // the stage about to be refilled was read by the MMAs of kt-2
-      const int t = kt - 2;
-      if (!mbar_wait(smem_u32(&mbar[t % GSTAGES]), (uint32_t)((t / GSTAGES) & 1))) s_err[kt & 1] = 1;
-    }
-    __syncthreads();
-    if (s_err[kt & 1]) {
-      failed = true;
-      break;
-    }
-    if (tid == 0) {
+  // One thread is producer and MMA issuer: tiles go in flight up to GSTAGES ahead; after the MMAs
+  // of tile kt are issued, the stage of tile kt-1 is refilled once those MMAs have released it.
+  if (tid == 0) {
+    auto load = [&](int t) {
+      const int s = t % GSTAGES;
+      const uint32_t fb = smem_u32(&full[s]);
+      mbar_expect_tx(fb, STAGE_BYTES);
+      tma_load_2d(a0 + s * A_STAGE, &tmA, kbeg + t * GK, m0, fb);
+      tma_load_2d(b0 + s * B_STAGE, &tmB, kbeg + t * GK, n0, fb);
+    };
+    for (int t = 0; t < GSTAGES && t < KT; ++t) load(t);
+    int err = 0;
+    for (int kt = 0; kt < KT; ++kt) {
+      const int s = kt % GSTAGES;
+      if (!mbar_wait(smem_u32(&full[s]), (uint32_t)((kt / GSTAGES) & 1))) { err = 1; break; }
       tc_fence_after();
       const uint32_t sa = a0 + s * A_STAGE, sb = b0 + s * B_STAGE;
 #pragma unroll
       for (int kk = 0; kk < GK / 16; ++kk)
-        tc_mma(tmem, smem_desc(sa + kk * 256, 128, 1024), smem_desc(sb + kk * 256, 128, 1024), idesc<BN>(),
+        tc_mma(tmem, smem_desc_sw128(sa + kk * 32), smem_desc_sw128(sb + kk * 32), idesc<BN>(),
                (kt > 0 || kk > 0) ? 1u : 0u);
-      tc_commit(smem_u32(&mbar[s]));
+      tc_commit(smem_u32(&empty[s]));
+      const int t = kt - 1 + GSTAGES;  // refill the stage of tile kt-1
+      if (kt >= 1 && t < KT) {
+        if (!mbar_wait(smem_u32(&empty[(kt - 1) % GSTAGES]), (uint32_t)(((kt - 1) / GSTAGES) & 1))) { err = 1; break; }
+        load(t);
+      }
     }
-    if (kt + 2 < KT) {
-      const int s2 = (kt + 2) % GSTAGES;
-      load_tile<GM>(a0 + s2 * A_STAGE, g.A, g.lda, g.M, m0, kbeg + (kt + 2) * GK, tid);
-      load_tile<BN>(b0 + s2 * B_STAGE, g.B, g.ldb, g.N, n0, kbeg + (kt + 2) * GK, tid);
+    if (!err && KT > 0) {
+      const int t = KT - 1;  // the last commit covers every earlier MMA of this thread
+      if (!mbar_wait(smem_u32(&empty[t % GSTAGES]), (uint32_t)((t / GSTAGES) & 1))) err = 1;
     }
-    cp_async_commit();
+    *s_err = err;
   }
-  cp_async_wait<0>();
-  if (!failed) {
-    if (tid == 0) {
-      const int t = KT - 1;
-      if (!mbar_wait(smem_u32(&mbar[t % GSTAGES]), (uint32_t)((t / GSTAGES) & 1))) s_err[2] = 1;
-    }
-    __syncthreads();
-    failed = s_err[2] != 0;
-  }
+  __syncthreads();
+  const bool failed = *s_err != 0;
   tc_fence_after();
 
   if (!failed) {
@@ -559,6 +554,35 @@ int mfail(tt_mlp* m, int code, const char* fmt, ...) {
     if (_r != TT_OK) return _r; \
   } while (0)
 
+// cuTensorMapEncodeTiled, fetched once through the runtime (the library does not link libcuda)
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+// Tensor map of a row-major BF16 matrix (rows x K, row stride ld elements): boxes of 64 K columns
+// (128 bytes, the swizzle span) by box_rows rows, 128-byte swizzle, rows past the end read as 0.
+int make_tmap(tt_mlp* m, CUtensorMap* tm, const bf16* base, int rows, int K, int ld, int box_rows) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return mfail(m, TT_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(bf16)};
+  const cuuint32_t box[2] = {(cuuint32_t)GK, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)base, dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return mfail(m, TT_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return TT_OK;
+}
+
 template <int EPI, int BN>
 int launch_tiles_bn(tt_mlp* m, const GemmArgs& g, int nsplit, cudaStream_t s) {
   static bool attr_done = false;  // per template instance; the attribute is per function
@@ -567,8 +591,11 @@ int launch_tiles_bn(tt_mlp* m, const GemmArgs& g, int nsplit, cudaStream_t s) {
     if (e != cudaSuccess) return mfail(m, TT_ECUDA, "gemm smem attribute: %s", cudaGetErrorString(e));
     attr_done = true;
   }
+  CUtensorMap tmA, tmB;
+  MLP_TRY(make_tmap(m, &tmA, g.A, g.M, g.K, g.lda, GM));
+  MLP_TRY(make_tmap(m, &tmB, g.B, g.N, g.K, g.ldb, BN));
   dim3 grid((g.N + BN - 1) / BN, (g.M + GM - 1) / GM, nsplit);
-  k_gemm_tn<EPI, BN><<<grid, 128, gemm_smem<BN>(), s>>>(g);
+  k_gemm_tn<EPI, BN><<<grid, 128, gemm_smem<BN>(), s>>>(tmA, tmB, g);
   MLP_LAUNCH(m, "k_gemm_tn");
   return TT_OK;
 }
