@@ -956,9 +956,6 @@ struct ElemSize {
   static constexpr int value = DT == TT_F64 ? 8 : DT == TT_F32 ? 4 : DT == TT_BF16 ? 2 : 1;
 };
 
-__device__ __forceinline__ void cpa16(uint32_t dst, const void* src, int bytes) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
-}
 
 // four consecutive entries from shared memory (storage type DT, 4-entry aligned)
 template <int DT>
@@ -985,11 +982,36 @@ __device__ __forceinline__ void smem_load4(const unsigned char* p, float* x) {
   }
 }
 
-constexpr int REL_U = 8;  // fibres per thread per tile
+constexpr int REL_U = 8;   // fibres per thread per tile
+constexpr int REL_NS = 3;  // tiles in flight per CTA
+
+__device__ __forceinline__ bool rel_mbar_try(uint32_t addr, uint32_t parity) {
+  uint32_t ok;
+  asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+               : "=r"(ok) : "r"(addr), "r"(parity) : "memory");
+  return ok != 0;
+}
+// bounded wait (2 s by %globaltimer) for the completion of phase `parity`
+__device__ __forceinline__ bool rel_mbar_wait(uint32_t addr, uint32_t parity) {
+  if (rel_mbar_try(addr, parity)) return true;
+  unsigned long long t0, t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  do {
+    if (rel_mbar_try(addr, parity)) return true;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  } while (t - t0 < 2000000000ull);
+  return false;
+}
+// 1-D bulk copy global -> shared (16-byte aligned, a multiple of 16 bytes), counted on an mbarrier
+__device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(mbar) : "memory");
+}
 
 // ||A - [[G]]||^2 and ||A||^2 by streaming A in memory order. A tile is FT = P * REL_U consecutive
-// mode-0 fibres (FT * n_0 entries, contiguous) with their rows of R; tiles are staged into shared
-// memory by cp.async, double-buffered, so the next tile is in flight while this one is reduced.
+// mode-0 fibres (FT * n_0 entries, contiguous) with their rows of R; one thread moves each tile
+// into shared memory with two bulk copies (cp.async.bulk, counted on the buffer's mbarrier),
+// REL_NS tiles in flight per CTA, while the CTA reduces the oldest one.
 // Thread (q, p) owns entries 4q..4q+3 of the tile's fibres p + P u; the reconstruction is
 // G_0 (shared, float4 along i_0) times the fibre's R row (shared, float4 broadcast).
 // Needs n_0 % 4 == 0 and n_0 <= 1024.
@@ -1004,8 +1026,9 @@ __global__ void __launch_bounds__(256, 2) k_rel_error_stream(const void* __restr
   float* G0 = reinterpret_cast<float*>(smraw);  // r1p x n0, rows >= r1 zero
   unsigned char* bufA = smraw + (size_t)r1p * n0 * 4;
   const int tileA = FT * n0 * ES;               // bytes (a multiple of 16)
-  float* bufR = reinterpret_cast<float*>(bufA + 2 * (size_t)tileA);
+  float* bufR = reinterpret_cast<float*>(bufA + REL_NS * (size_t)tileA);
   const int tileR = FT * r1p;                   // floats
+  uint64_t* mb = reinterpret_cast<uint64_t*>(bufR + REL_NS * (size_t)tileR);  // one per buffer
   for (int i = threadIdx.x; i < r1p * n0; i += blockDim.x) G0[i] = i < r1 * n0 ? g0[i] : 0.f;
   const int qi = threadIdx.x % Q, pi = threadIdx.x / Q;
   const bool active = pi < P;
@@ -1013,27 +1036,39 @@ __global__ void __launch_bounds__(256, 2) k_rel_error_stream(const void* __restr
   if (scales && active)
     for (int c = 0; c < 4; ++c) sc[c] = __ldg(scales + 4 * qi + c);
   const int64_t ntiles = (M0 + FT - 1) / FT;
+  // thread 0: both bulk copies of a tile on the buffer's mbarrier; the bytes of a partial last
+  // tile past the last multiple of 16 are copied by plain loads (read after a CTA barrier)
   auto issue = [&](int64_t tile, int b) {
     const int64_t f0 = tile * FT;
     const int nf = (int)min((int64_t)FT, M0 - f0);
     const unsigned char* src = reinterpret_cast<const unsigned char*>(A) + f0 * n0 * ES;
-    const int bytes = nf * n0 * ES;
-    const uint32_t dA = (uint32_t)__cvta_generic_to_shared(bufA + (size_t)b * tileA);
-    for (int c = threadIdx.x; c * 16 < bytes; c += blockDim.x) cpa16(dA + 16 * c, src + 16 * c, min(16, bytes - 16 * c));
-    const float* srcR = R + f0 * r1p;
-    const int bytesR = nf * r1p * 4;
-    const uint32_t dR = (uint32_t)__cvta_generic_to_shared(bufR + (size_t)b * tileR);
-    for (int c = threadIdx.x; c * 16 < bytesR; c += blockDim.x) cpa16(dR + 16 * c, srcR + 4 * c, 16);
+    const uint32_t bytes = (uint32_t)nf * n0 * ES, bulk = bytes & ~15u;
+    const uint32_t bytesR = (uint32_t)nf * r1p * 4;
+    unsigned char* dA = bufA + (size_t)b * tileA;
+    const uint32_t m = (uint32_t)__cvta_generic_to_shared(&mb[b]);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(m), "r"(bulk + bytesR) : "memory");
+    if (bulk) bulk_copy((uint32_t)__cvta_generic_to_shared(dA), src, bulk, m);
+    bulk_copy((uint32_t)__cvta_generic_to_shared(bufR + (size_t)b * tileR), R + f0 * r1p, bytesR, m);
+    for (uint32_t t2 = bulk; t2 < bytes; ++t2) dA[t2] = src[t2];
   };
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < REL_NS; ++i)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"((uint32_t)__cvta_generic_to_shared(&mb[i])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    for (int i = 0; i < REL_NS - 1; ++i)
+      if (blockIdx.x + (int64_t)i * gridDim.x < ntiles) issue(blockIdx.x + (int64_t)i * gridDim.x, i);
+  }
+  __syncthreads();
   double e2 = 0.0, x2 = 0.0;
-  int64_t tile = blockIdx.x;
-  if (tile < ntiles) issue(tile, 0);
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
-  for (int b = 0; tile < ntiles; tile += gridDim.x, b ^= 1) {
-    if (tile + gridDim.x < ntiles) issue(tile + gridDim.x, b ^ 1);
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-    asm volatile("cp.async.wait_group 1;\n" ::: "memory");
-    __syncthreads();
+  bool timed_out = false;
+  int it = 0;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+    const int b = it % REL_NS;
+    if (threadIdx.x == 0) {  // tile it + REL_NS - 1 goes into the buffer read in iteration it - 1
+      const int64_t nx = tile + (int64_t)(REL_NS - 1) * gridDim.x;
+      if (nx < ntiles) issue(nx, (it + REL_NS - 1) % REL_NS);
+    }
+    if (!rel_mbar_wait((uint32_t)__cvta_generic_to_shared(&mb[b]), (uint32_t)((it / REL_NS) & 1))) timed_out = true;
     const int64_t f0 = tile * FT;
     const unsigned char* tA = bufA + (size_t)b * tileA;
     const float* tR = bufR + (size_t)b * tileR;
@@ -1079,7 +1114,7 @@ __global__ void __launch_bounds__(256, 2) k_rel_error_stream(const void* __restr
     x2 += fa;
     __syncthreads();  // buffer b is refilled by the next iteration's issue
   }
-  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  if (timed_out) e2 = __longlong_as_double(0x7ff8000000000000ll);  // a wait gave up: the result reads NaN
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int o = 16; o > 0; o >>= 1) {
     e2 += __shfl_xor_sync(0xffffffffu, e2, o);
@@ -1106,7 +1141,8 @@ static size_t rel_stream_smem(const tt_ctx* c, int es) {
   const int64_t n0 = c->n[0];
   if (n0 % 4 != 0 || n0 > 1024) return 0;
   const int64_t Q = n0 / 4, P = 256 / Q, FT = P * REL_U;
-  const size_t bytes = (size_t)c->rint_r1p * n0 * 4 + 2 * (size_t)FT * n0 * es + 2 * (size_t)FT * c->rint_r1p * 4;
+  const size_t bytes = (size_t)c->rint_r1p * n0 * 4 + REL_NS * (size_t)FT * n0 * es +
+                       REL_NS * (size_t)FT * c->rint_r1p * 4 + REL_NS * sizeof(uint64_t);
   return bytes <= 200 * 1024 ? bytes : 0;
 }
 
