@@ -483,7 +483,7 @@ extern "C" int tt_sketch_init(tt_ctx** out, const tt_params* p, void* stream) {
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
   for (int k = 0; k < c->d && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&c->ev_y[k], cudaEventDisableTiming);
-  A((void**)&c->d_gram, sizeof(double) * (c->smax + c->nmax) * c->smax);
+  A((void**)&c->d_gram, sizeof(float) * (c->smax + c->nmax) * c->smax);
   A((void**)&c->d_core_old, sizeof(float) * c->nmax * c->smax);
   c->changes_cap = 1024 * TT_MAX_D;
   A((void**)&c->d_changes, sizeof(double) * 2 * c->changes_cap);

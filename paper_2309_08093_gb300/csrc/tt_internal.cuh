@@ -86,7 +86,7 @@ struct tt_ctx {
   cudaEvent_t ev_y[TT_MAX_D] = {nullptr};
   float* d_Yall = nullptr;
   int64_t yoff[TT_MAX_D + 1] = {0};
-  double* d_gram = nullptr;    // (smax + nmax) x smax FP64 accumulators of [SH | Y]^T SH
+  float* d_gram = nullptr;     // (smax + nmax) x smax FP32 accumulators of [SH | Y]^T SH
   float* d_core_old = nullptr; // proximal centre copy (nmax * smax)
   double* d_changes = nullptr; // per (sweep, k): ||dG||^2, ||G||^2
   int* d_status = nullptr;     // device error flag (0 = ok, else TT_E* code)

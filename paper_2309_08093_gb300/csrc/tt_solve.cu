@@ -3,12 +3,16 @@
 // plus the QR / LQ orthogonalisation steps of Algorithm 1 and the relative error of Sec. 5.
 //
 //   k_gram        : [S H_k | Y_k]^T (S H_k) with FP32 products summed in FP32 over K-chunks of
-//                   256 rows and in FP64 across chunks (split-K, FP64 atomics)
-//   k_prox_solve  : Cholesky M = L L^T and the two triangular solves, one CTA (s <= 160)
-//   k_qr_left     : Householder QR of G_k^L, G_k <- Q, G_{k+1} <- R G_{k+1}^R
+//                   256 rows and across chunks (split-K, FP32 atomics)
+//   k_prox_solve  : Gauss-Jordan elimination of [M | B^T] in registers, one barrier per pivot,
+//                   one CTA per chunk of right-hand-side rows (s <= 160)
+//   k_qr_left_rows, k_lq_right_rows : CholeskyQR2 with rows in registers (rank <= 16), then
+//                   G_k <- Q and R absorbed into the neighbour (prefetched during the QR)
+//   k_qr_left     : the same for larger ranks (Gram in shared memory), Householder fallback:
+//                   G_k^L = Q R, G_k <- Q, G_{k+1} <- R G_{k+1}^R
 //   k_lq_right    : the same on (G_k^R)^T: G_k^R <- Q^T, G_{k-1}^L <- G_{k-1}^L R^T
 //   k_slab_u, k_rint, k_rel_error_stream : ||A - [[G]]||_F^2 and ||A||_F^2: right interfaces of
-//                   all mode-0 fibres, then one cp.async-pipelined pass over A in memory order
+//                   all mode-0 fibres, then one pass over A in memory order (bulk copies)
 //   k_rel_error   : the same for other shapes (n_0 % 4 != 0 or n_0 > 1024), slab by slab
 #include <stdio.h>
 
@@ -16,13 +20,23 @@
 
 #include "tt_internal.cuh"
 
+// 4-byte asynchronous copies global -> shared (cp.async), committed and awaited by group
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 // ---------------------------------------------------------------------------------------------
 // Gram and right-hand side
 
 struct GramArgs {
   const float* SH;  // J x s column-major
   const float* Y;   // J x n column-major
-  double* C;        // (s + n) x s row-major accumulators (zeroed by the caller)
+  float* C;         // accumulators (zeroed by the caller): s x s Gram, then the s x n RHS
+                    // (SH^T Y, row-major) -- both row-major
   int J, s, n, kchunk;
 };
 
@@ -82,7 +96,10 @@ __global__ void __launch_bounds__(256) k_gram(GramArgs a) {
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
       int gr = r0 + ty + 16 * i, gc = c0 + tx + 16 * j;
-      if (gr < rows && gc < a.s) atomicAdd(a.C + (int64_t)gr * a.s + gc, (double)acc[i][j]);
+      if (gr < a.s && gc < a.s)
+        atomicAdd(a.C + (int64_t)gr * a.s + gc, acc[i][j]);
+      else if (gr < rows && gc < a.s)  // right-hand side stored transposed: s x n
+        atomicAdd(a.C + (int64_t)a.s * a.s + (int64_t)gc * a.n + (gr - a.s), acc[i][j]);
     }
 }
 
@@ -90,7 +107,7 @@ __global__ void __launch_bounds__(256) k_gram(GramArgs a) {
 // Cholesky + triangular solves, one CTA
 
 struct SolveArgs {
-  const double* C;  // (s + n) x s: rows [0, s) = SH^T SH, rows [s, s+n) = Y^T SH
+  const float* C;   // s x s Gram SH^T SH, then s x n SH^T Y (both row-major)
   float* core;      // r0 x n x r1 (read: proximal centre; written: update)
   double* change;   // [0] += ||G_new - G_old||^2, [1] += ||G_new||^2 (may be null)
   int* status;
@@ -99,211 +116,197 @@ struct SolveArgs {
   int chunk_rows;
 };
 
-__device__ double block_sum(double v, double* sh) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  __syncthreads();
-  if (l == 0) sh[w] = v;
-  __syncthreads();
-  double t = 0.0;
-  if (threadIdx.x < 32) {
-    t = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+// Gauss-Jordan elimination without pivoting of the s x (s + nr) array W = [M | B_c^T], where B_c
+// holds the nr right-hand-side rows of this CTA's chunk. Step j divides row j by its pivot
+// W[j][j] (the D of M = L D L^T: positive exactly when M is SPD) and subtracts W[i][j] times it
+// from every other row i; after s steps the first s columns are the identity and
+// X_c[r][i] = W[i][s + r]. W lives in registers: thread (ty, tx) of a TY x 32 layout owns
+// W[ty + TY a][tx + 32 b]. A warp needs column j only for its own rows, so lane j % 32 hands it
+// over by shuffles; the normalised row j is published through shared memory by its warp at the
+// end of step j - 1: one barrier per step. Steps run in groups of TY (template recursion over
+// the group G): row j is then register block G of warp j - TY G and column j register block
+// TY G / 32 of lane j % 32, both compile-time, so no register is ever selected by a runtime
+// index. Column blocks wholly left of the group's pivots are dead and skipped.
+template <int TY, int RA, int CB, int G>
+__device__ __forceinline__ void gj_publish_row(float (&w)[RA][CB], int jn, float* rowb, int* bad, int ty, int tx) {
+  constexpr int CN = (TY * G) / 32;  // column block of pivots TY G .. TY G + TY - 1
+  if (ty == jn - TY * G) {           // the warp that owns row jn (register block G)
+    const float p = __shfl_sync(0xffffffffu, w[G][CN], jn & 31);
+    if (tx == 0 && (!(p > 0.f) || !isfinite(p))) atomicCAS(bad, 0, isfinite(p) ? TT_ENOTSPD : TT_ENONFINITE);
+    const float ip = 1.f / p;
+#pragma unroll
+    for (int cb = 0; cb < CB; ++cb) {
+      const float v = w[G][cb] * ip;
+      w[G][cb] = v;
+      rowb[tx + 32 * cb] = v;
+    }
   }
-  return t;  // valid in thread 0
 }
 
-// Factorisation M = L D L^T (unit lower L, D > 0 -- the Cholesky factor is L D^{1/2}) with one
-// barrier per column: thread (ty, tx) of a 32 x 32 tiling owns the entries (i, l), i = ty mod 32,
-// l = tx mod 32, of the trailing triangle. The solve X M = B runs as three passes over blocks of
-// 32 columns: Y L^T = B (forward), V = Y D^{-1}, X L = V (backward). Within a pass each block
-// is a parallel GEMM update with the finished blocks followed by a multiplication with the
-// inverse of the block's unit-triangular diagonal part (inverted up front, one warp per block).
-#define TT_SB 32
-__global__ void __launch_bounds__(1024) k_prox_solve(SolveArgs a) {
-  extern __shared__ float sm[];
-  __shared__ int bad;
-  __shared__ double red[32];
-  const int s = a.s;
-  const int P = s | 1;                         // odd pitch: column walks hit distinct banks
-  const int nb = (s + TT_SB - 1) / TT_SB;
-  float* M = sm;                               // s x P: L below the diagonal, D on it
-  float* Tinv = M + (size_t)s * P;             // nb blocks of 32 x 33: inverses of diagonal blocks
-  float* Z = Tinv + (size_t)nb * TT_SB * (TT_SB + 1);  // chunk_rows x P right-hand sides
-  const int t = threadIdx.x, T = blockDim.x;
-  const int lane = t & 31, warp = t >> 5;
-  if (*a.status != 0) return;
-  for (int b0 = t; b0 < s * s; b0 += 4 * T) {  // four independent loads in flight per thread
-    double v[4];
+template <int TY, int RA, int CB, int G>
+__device__ __forceinline__ void gj_groups(float (&w)[RA][CB], int s, float (*rowbuf)[CB * 32], int* bad, int& bs,
+                                          int ty, int tx) {
+  if constexpr (G < RA) {
+    constexpr int CN = (TY * G) / 32;  // column block of this group's pivots = first live block
+    const int j0 = TY * G;
+    if (j0 >= s) return;
+    const int jend = min(TY, s - j0);
+    for (int jj = 0; jj < jend; ++jj) {
+      const int jl = (j0 + jj) & 31;  // the lane that holds column j
+      float f[RA], rv[CB];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) v[u] = (b0 + u * T < s * s) ? __ldg(a.C + b0 + u * T) : 0.0;
+      for (int ra = 0; ra < RA; ++ra) f[ra] = __shfl_sync(0xffffffffu, w[ra][CN], jl);
+      if (ty == jj) f[G] = 0.f;  // row j itself (already normalised) is left alone
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int idx = b0 + u * T;
-      if (idx < s * s) {
-        const int i = idx / s, j = idx - i * s;
-        M[i * P + j] = (float)(i == j ? v[u] + a.sigma : v[u]);
+      for (int cb = CN; cb < CB; ++cb) rv[cb] = rowbuf[bs][tx + 32 * cb];
+#pragma unroll
+      for (int cb = CN; cb < CB; ++cb)
+#pragma unroll
+        for (int ra = 0; ra < RA; ++ra) w[ra][cb] = fmaf(-f[ra], rv[cb], w[ra][cb]);
+      const int jn = j0 + jj + 1;
+      if (jn < s) {
+        if (jj + 1 < TY)
+          gj_publish_row<TY, RA, CB, G>(w, jn, rowbuf[bs ^ 1], bad, ty, tx);
+        else if constexpr (G + 1 < RA)
+          gj_publish_row<TY, RA, CB, G + 1>(w, jn, rowbuf[bs ^ 1], bad, ty, tx);
       }
+      __syncthreads();
+      bs ^= 1;
+    }
+    gj_groups<TY, RA, CB, G + 1>(w, s, rowbuf, bad, bs, ty, tx);
+  }
+}
+
+template <int TY, int RA, int CB>
+__global__ void __launch_bounds__(TY * 32) k_prox_solve(SolveArgs a) {
+  constexpr int T = TY * 32;
+  __shared__ __align__(16) float rowbuf[2][CB * 32];
+  __shared__ float gsm[RA * TY][33];  // this chunk of G_{k(2)}^T: proximal centre, then the update
+  __shared__ float red[2][TY];
+  __shared__ int bad;
+  const int t = threadIdx.x, tx = t & 31, ty = t >> 5;
+  const int s = a.s, r0 = a.r0, n = a.n;
+  const int i0 = blockIdx.x * a.chunk_rows;
+  const int nr = min(a.chunk_rows, n - i0);
+  const int ncol = s + nr;
+  const float sigma = (float)a.sigma;
+  if (*a.status != 0) return;
+  // M and the transposed right-hand side: unconditional loads (clamped addresses) so that many
+  // are in flight at once; row-major rows of both are read along the lanes
+  float w[RA][CB];
+#pragma unroll
+  for (int ra = 0; ra < RA; ++ra) {
+    const int ic = min(ty + TY * ra, s - 1);
+#pragma unroll
+    for (int cb = 0; cb < CB; ++cb) {
+      const int l = tx + 32 * cb;
+      const int r = min(max(l - s, 0), nr - 1);
+      const int64_t ci = (l < s) ? (int64_t)ic * s + l : (int64_t)s * s + (int64_t)ic * n + i0 + r;
+      w[ra][cb] = __ldg(a.C + ci);
     }
   }
+  // the chunk's proximal centre, coalesced and asynchronous: gsm[al + r0 be][r] = G(al, i0 + r, be)
+  const int rn = r0 * nr;
+  for (int idx = t; idx < s * nr; idx += T) {
+    const int be = idx / rn, rem = idx - be * rn, r = rem / r0, al = rem - r * r0;
+    cp_async4(&gsm[al + r0 * be][r], a.core + al + (int64_t)r0 * ((i0 + r) + (int64_t)n * be));
+  }
+  cp_async_commit();
   if (t == 0) bad = 0;
+  cp_async_wait<0>();
   __syncthreads();
-  const int ty = t >> 5, tx = t & 31;  // 32 x 32 tiling (T = 1024)
-  for (int j = 0; j < s; ++j) {
-    const float p = M[j * P + j];
-    if (!(p > 0.f) || !isfinite(p)) {
-      if (t == 0) bad = isfinite(p) ? TT_ENOTSPD : TT_ENONFINITE;
-      break;
+#pragma unroll
+  for (int ra = 0; ra < RA; ++ra) {
+    const int i = ty + TY * ra;
+#pragma unroll
+    for (int cb = 0; cb < CB; ++cb) {
+      const int l = tx + 32 * cb;
+      const bool in = i < s && l < ncol;
+      float v = w[ra][cb];
+      if (l == i) v += sigma;
+      if (in && l >= s) v = fmaf(sigma, gsm[i][l - s], v);
+      w[ra][cb] = in ? v : 0.f;
     }
-    const float ip = 1.f / p;
-    for (int i = j + 1 + ((ty - (j + 1)) % 32 + 32) % 32; i < s; i += 32) {
-      const float mij = M[i * P + j] * ip;
-      for (int l = j + 1 + ((tx - (j + 1)) % 32 + 32) % 32; l <= i; l += 32) M[i * P + l] -= mij * M[l * P + j];
-    }
-    __syncthreads();
   }
+  gj_publish_row<TY, RA, CB, 0>(w, 0, rowbuf[0], &bad, ty, tx);
   __syncthreads();
-  if (bad) {
+  int bs = 0;
+  gj_groups<TY, RA, CB, 0>(w, s, rowbuf, &bad, bs, ty, tx);
+  if (bad) {  // read after the last step's barrier: the same value in every thread
     if (t == 0) atomicCAS(a.status, 0, bad);
     return;
   }
-  // L[i][j] = M[i][j] / D[j]  (i > j)
-  for (int idx = t; idx < s * s; idx += T) {
-    const int i = idx / s, j = idx - i * s;
-    if (i > j) M[i * P + j] /= M[j * P + j];
-  }
-  __syncthreads();
-  // inverses of the unit lower diagonal blocks (warp b inverts block b; lane c = column c)
-  for (int b = warp; b < nb; b += T / 32) {
-    const int c0 = b * TT_SB, w = min(TT_SB, s - c0);
-    float* Tb = Tinv + (size_t)b * TT_SB * (TT_SB + 1);
-    if (lane < w) {
-      float x[TT_SB];
+  // change sums against the proximal centre, the update into gsm, then coalesced stores
+  float dsum = 0.f, nsum = 0.f;
 #pragma unroll
-      for (int i = 0; i < TT_SB; ++i) x[i] = 0.f;
-      for (int i = lane; i < w; ++i) {
-        float v = (i == lane) ? 1.f : 0.f;
-        for (int l = lane; l < i; ++l) v -= M[(c0 + i) * P + c0 + l] * x[l];
-        x[i] = v;
-      }
-      for (int i = 0; i < w; ++i) Tb[i * (TT_SB + 1) + lane] = x[i];  // Tb = (L_bb)^{-1}, row i col lane
+  for (int ra = 0; ra < RA; ++ra) {
+    const int i = ty + TY * ra;
+    if (i >= s) continue;
+#pragma unroll
+    for (int cb = 0; cb < CB; ++cb) {
+      const int l = tx + 32 * cb;
+      if (l < s || l >= ncol) continue;
+      const float nw = w[ra][cb], d = nw - gsm[i][l - s];
+      dsum = fmaf(d, d, dsum);
+      nsum = fmaf(nw, nw, nsum);
+      gsm[i][l - s] = nw;
+    }
+  }
+  if (a.change) {  // slot zeroed by the host
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
+      nsum += __shfl_xor_sync(0xffffffffu, nsum, o);
+    }
+    if (tx == 0) {
+      red[0][ty] = dsum;
+      red[1][ty] = nsum;
     }
   }
   __syncthreads();
-  double dsum = 0.0, nsum = 0.0;
-  const int ZP = P;
-  // each CTA (re)factorises M and solves its own slice of chunk_rows right-hand-side rows
-  for (int i0 = blockIdx.x * a.chunk_rows; i0 < a.n; i0 += gridDim.x * a.chunk_rows) {
-    const int nr = min(a.chunk_rows, a.n - i0);
-    for (int idx = t; idx < nr * s; idx += T) {
-      const int i = idx / s, c = idx - i * s;
-      const int al = c % a.r0, be = c / a.r0;
-      const float g = a.core[al + (int64_t)a.r0 * ((i0 + i) + (int64_t)a.n * be)];
-      Z[i * ZP + c] = (float)(a.C[(int64_t)(s + i0 + i) * s + c] + a.sigma * (double)g);
-    }
-    __syncthreads();
-    // forward: Y L^T = B. Block b: Z[:, blk] -= Z[:, <c0] L[blk, <c0]^T, then Z[:, blk] <- Z[:, blk] Tb^T
-    for (int b = 0; b < nb; ++b) {
-      const int c0 = b * TT_SB, w = min(TT_SB, s - c0);
-      for (int idx = t; idx < nr * w; idx += T) {
-        const int r = idx / w, jj = idx - r * w;
-        float acc = Z[r * ZP + c0 + jj];
-        for (int l = 0; l < c0; ++l) acc -= Z[r * ZP + l] * M[(c0 + jj) * P + l];
-        Z[r * ZP + c0 + jj] = acc;
-      }
-      __syncthreads();
-      const float* Tb = Tinv + (size_t)b * TT_SB * (TT_SB + 1);
-      float tmp[4];
-      int cntq = 0;
-      for (int idx = t; idx < nr * w; idx += T) {  // y_blk = z_blk (Tb)^T: y_j = sum_{l<=j} Tb[j][l] z_l
-        const int r = idx / w, jj = idx - r * w;
-        float acc = 0.f;
-        for (int l = 0; l <= jj; ++l) acc += Tb[jj * (TT_SB + 1) + l] * Z[r * ZP + c0 + l];
-        if (cntq < 4) tmp[cntq] = acc;
-        ++cntq;
-      }
-      __syncthreads();
-      cntq = 0;
-      for (int idx = t; idx < nr * w; idx += T) {
-        const int r = idx / w, jj = idx - r * w;
-        if (cntq < 4) Z[r * ZP + c0 + jj] = tmp[cntq];
-        ++cntq;
-      }
-      __syncthreads();
-    }
-    // V = Y D^{-1}
-    for (int idx = t; idx < nr * s; idx += T) {
-      const int r = idx / s, c = idx - r * s;
-      Z[r * ZP + c] /= M[c * P + c];
-    }
-    __syncthreads();
-    // backward: X L = V. Block b (last first): Z[:, blk] -= Z[:, >=c1] L[>=c1, blk], then
-    // Z[:, blk] <- Z[:, blk] Tb  (x_j = sum_{i>=j} z_i Tb[i][j])
-    for (int b = nb - 1; b >= 0; --b) {
-      const int c0 = b * TT_SB, w = min(TT_SB, s - c0), c1 = c0 + w;
-      for (int idx = t; idx < nr * w; idx += T) {
-        const int r = idx / w, jj = idx - r * w;
-        float acc = Z[r * ZP + c0 + jj];
-        for (int i = c1; i < s; ++i) acc -= Z[r * ZP + i] * M[i * P + c0 + jj];
-        Z[r * ZP + c0 + jj] = acc;
-      }
-      __syncthreads();
-      const float* Tb = Tinv + (size_t)b * TT_SB * (TT_SB + 1);
-      float tmp[4];
-      int cntq = 0;
-      for (int idx = t; idx < nr * w; idx += T) {
-        const int r = idx / w, jj = idx - r * w;
-        float acc = 0.f;
-        for (int i = jj; i < w; ++i) acc += Z[r * ZP + c0 + i] * Tb[i * (TT_SB + 1) + jj];
-        if (cntq < 4) tmp[cntq] = acc;
-        ++cntq;
-      }
-      __syncthreads();
-      cntq = 0;
-      for (int idx = t; idx < nr * w; idx += T) {
-        const int r = idx / w, jj = idx - r * w;
-        if (cntq < 4) Z[r * ZP + c0 + jj] = tmp[cntq];
-        ++cntq;
-      }
-      __syncthreads();
-    }
-    for (int idx = t; idx < nr * s; idx += T) {
-      const int i = idx / s, c = idx - i * s;
-      const int al = c % a.r0, be = c / a.r0;
-      const int64_t off = al + (int64_t)a.r0 * ((i0 + i) + (int64_t)a.n * be);
-      const float old = a.core[off], nw = Z[i * ZP + c];
-      dsum += (double)(nw - old) * (double)(nw - old);
-      nsum += (double)nw * (double)nw;
-      a.core[off] = nw;
-    }
-    __syncthreads();
+  for (int idx = t; idx < s * nr; idx += T) {
+    const int be = idx / rn, rem = idx - be * rn, r = rem / r0, al = rem - r * r0;
+    a.core[al + (int64_t)r0 * ((i0 + r) + (int64_t)n * be)] = gsm[al + r0 * be][r];
   }
-  double t1 = block_sum(dsum, red);
-  double t2 = block_sum(nsum, red);
-  if (t == 0 && a.change) {  // slot zeroed by the host
-    atomicAdd(a.change, t1);
-    atomicAdd(a.change + 1, t2);
+  if (a.change && t == 0) {
+    float t1 = 0.f, t2 = 0.f;
+    for (int u = 0; u < TY; ++u) {
+      t1 += red[0][u];
+      t2 += red[1][u];
+    }
+    atomicAdd(a.change, (double)t1);
+    atomicAdd(a.change + 1, (double)t2);
   }
 }
 
-static size_t solve_smem(int s, int chunk_rows) {
-  const int P = s | 1, nb = (s + TT_SB - 1) / TT_SB;
-  return sizeof(float) * ((size_t)s * P + (size_t)nb * TT_SB * (TT_SB + 1) + (size_t)chunk_rows * P);
-}
+// Register shapes of the solve (TY x 32 threads, RA row blocks of TY, CB column blocks of 32):
+// the first that holds s rows and s + 1 columns; its spare columns carry right-hand-side rows.
+struct SolveShape {
+  int ty, ra, cb;
+};
+static const SolveShape kSolveShapes[] = {{8, 4, 2}, {8, 14, 4}, {16, 10, 6}};
 
-static int solve_chunk_rows(int s, int n) {
-  // rows per CTA: 16 (rows x 32 block columns <= 4 items per thread of 1024) and within
-  // ~200 KB of shared memory
-  int rows = std::min(n, 16);
-  while (rows > 1 && solve_smem(s, rows) > 200 * 1024) rows = (rows + 1) / 2;
-  return std::max(1, rows);
+static cudaError_t launch_prox_solve(SolveArgs a, cudaStream_t st) {
+  for (const SolveShape& sh : kSolveShapes) {
+    if (a.s > sh.ty * sh.ra || a.s + 1 > 32 * sh.cb) continue;
+    a.chunk_rows = std::max(1, std::min(a.n, std::min(32, 32 * sh.cb - a.s)));
+    const int grid = (a.n + a.chunk_rows - 1) / a.chunk_rows;
+    if (sh.ra == 4)
+      k_prox_solve<8, 4, 2><<<grid, 256, 0, st>>>(a);
+    else if (sh.ra == 14)
+      k_prox_solve<8, 14, 4><<<grid, 256, 0, st>>>(a);
+    else
+      k_prox_solve<16, 10, 6><<<grid, 512, 0, st>>>(a);
+    return cudaGetLastError();
+  }
+  return cudaErrorInvalidValue;  // s above TT_MAX_S, rejected at context creation
 }
 
 int tt_launch_prox_update(tt_ctx* c, const float* Y, const float* SH, float* core, int k,
                           double* change_slot) {
   const int s = c->r[k] * c->r[k + 1];
   const int n = (int)c->n[k];
-  TT_CUDA(c, cudaMemsetAsync(c->d_gram, 0, sizeof(double) * (s + n) * s, c->stream));
+  TT_CUDA(c, cudaMemsetAsync(c->d_gram, 0, sizeof(float) * (s + n) * s, c->stream));
   GramArgs g;
   g.SH = SH;
   g.Y = Y;
@@ -325,11 +328,8 @@ int tt_launch_prox_update(tt_ctx* c, const float* Y, const float* SH, float* cor
   a.n = n;
   a.r0 = c->r[k];
   a.r1 = c->r[k + 1];
-  a.chunk_rows = solve_chunk_rows(s, n);
-  size_t smem = solve_smem(s, a.chunk_rows);
-  TT_CUDA(c, cudaFuncSetAttribute(k_prox_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   if (change_slot) TT_CUDA(c, cudaMemsetAsync(change_slot, 0, 2 * sizeof(double), c->stream));
-  k_prox_solve<<<(n + a.chunk_rows - 1) / a.chunk_rows, 1024, smem, c->stream>>>(a);
+  TT_CUDA(c, launch_prox_solve(a, c->stream));
   TT_LAUNCH(c, "k_prox_solve");
   return TT_OK;
 }
@@ -655,6 +655,368 @@ __global__ void __launch_bounds__(512) k_lq_right(float* prev, float* core, int 
   }
 }
 
+// ---------------------------------------------------------------------------------------------
+// CholeskyQR2 with rows in registers, for q <= 16 columns (Q = q rounded up to 4, 8, 12 or 16),
+// 256 threads. A (m x Q, row-major, pitch QP) is in shared memory; thread t owns rows t, t + 256,
+// ... Per pass: every thread sums the outer products a a^T of its rows (Q (Q+1) / 2 packed
+// lower-triangle values in registers); each warp folds its 32 copies with a reduce-scatter of
+// shuffles (each step halves the values a lane holds), the 8 warp sums are added in a fixed
+// order; every thread then factors W = L L^T itself (FP32 Cholesky, so no further barrier) and
+// replaces each of its rows a by the solution x of x L^T = a. Padded columns (q <= j < Q) are
+// zero and get a unit pivot, so they stay zero. A pivot <= 1e-6 times the largest diagonal entry
+// of W (condition number above ~1e3, rank deficiency) returns false: the caller falls back to
+// Householder. On success Rm (q x q row-major) holds R = L_2^T L_1^T.
+
+constexpr int QR_T = 256;
+
+template <int Q>
+struct QrShape {
+  static constexpr int QP = (Q % 8 == 0) ? Q + 4 : Q;  // row pitch: conflict-free 16-byte loads
+  static constexpr int V = Q * (Q + 1) / 2;            // packed lower triangle, p = i (i+1)/2 + j
+};
+
+// Sum v[0..V) over the 32 lanes of a warp; on return lane `lane` holds the sums of the packed
+// indices base + k, k < kept (written to out[base + k] for base + k < V).
+// One step of the fold: N values per lane become H = (N + 1) / 2; a lane with the OFF bit set
+// keeps the upper half (and adds H to its base index), its partner the lower half. `cnt` counts
+// the leading slots that hold real indices; the rest are zero padding (odd N), which must not be
+// stored: their index belongs to another lane.
+template <int N, int OFF, int V>
+__device__ __forceinline__ void warp_fold_step(float (&v)[V], int lane, int& base, int& cnt) {
+  constexpr int H = (N + 1) / 2;
+  const bool up = (lane & OFF) != 0;
+#pragma unroll
+  for (int k = 0; k < H; ++k) {
+    const float lo = v[k];
+    const float hi = (H + k < N) ? v[H + k] : 0.f;
+    const float got = __shfl_xor_sync(0xffffffffu, up ? lo : hi, OFF);
+    v[k] = (up ? hi : lo) + got;
+  }
+  if (up) {
+    base += H;
+    cnt = max(cnt - H, 0);
+  } else {
+    cnt = min(cnt, H);
+  }
+}
+
+// Sum v[0..V) over the 32 lanes of a warp (a reduce-scatter: 5 steps, each halving the values a
+// lane holds) and store the sums to out[0..V): lane `lane` ends with indices base + k.
+template <int V>
+__device__ __forceinline__ void warp_fold_store(float (&v)[V], float* out) {
+  const int lane = threadIdx.x & 31;
+  int base = 0, cnt = V;
+  constexpr int N1 = (V + 1) / 2, N2 = (N1 + 1) / 2, N3 = (N2 + 1) / 2, N4 = (N3 + 1) / 2, N5 = (N4 + 1) / 2;
+  warp_fold_step<V, 16>(v, lane, base, cnt);
+  warp_fold_step<N1, 8>(v, lane, base, cnt);
+  warp_fold_step<N2, 4>(v, lane, base, cnt);
+  warp_fold_step<N3, 2>(v, lane, base, cnt);
+  warp_fold_step<N4, 1>(v, lane, base, cnt);
+#pragma unroll
+  for (int k = 0; k < N5; ++k)
+    if (k < cnt) out[base + k] = v[k];
+}
+
+template <int Q>
+__device__ __forceinline__ void qr_load_row(const float* As, int r, float (&a)[Q]) {
+  const float4* p = reinterpret_cast<const float4*>(As + (size_t)r * QrShape<Q>::QP);
+#pragma unroll
+  for (int u = 0; u < Q / 4; ++u) {
+    const float4 x = p[u];
+    a[4 * u] = x.x;
+    a[4 * u + 1] = x.y;
+    a[4 * u + 2] = x.z;
+    a[4 * u + 3] = x.w;
+  }
+}
+
+template <int Q>
+__device__ __forceinline__ void qr_store_row(float* As, int r, const float (&a)[Q]) {
+  float4* p = reinterpret_cast<float4*>(As + (size_t)r * QrShape<Q>::QP);
+#pragma unroll
+  for (int u = 0; u < Q / 4; ++u) p[u] = make_float4(a[4 * u], a[4 * u + 1], a[4 * u + 2], a[4 * u + 3]);
+}
+
+// Shared scratch of cholqr2_rows: part (8 x V) | Wsum (V) | Ls (2 x V)
+template <int Q>
+__device__ bool cholqr2_rows(float* As, int m, int q, float* scratch, float* Rm) {
+  constexpr int V = QrShape<Q>::V;
+  float* part = scratch;
+  float* Wsum = part + 8 * V;
+  float* Ls = Wsum + V;
+  const int t = threadIdx.x, warp = t >> 5;
+  for (int pass = 0; pass < 2; ++pass) {
+    float acc[V];
+#pragma unroll
+    for (int p = 0; p < V; ++p) acc[p] = 0.f;
+    for (int r = t; r < m; r += QR_T) {
+      float a[Q];
+      qr_load_row<Q>(As, r, a);
+#pragma unroll
+      for (int i = 0; i < Q; ++i)
+#pragma unroll
+        for (int j = 0; j < Q; ++j)
+          if (j <= i) acc[i * (i + 1) / 2 + j] = fmaf(a[i], a[j], acc[i * (i + 1) / 2 + j]);
+    }
+    warp_fold_store<V>(acc, part + warp * V);
+    __syncthreads();
+    if (t < V) {
+      float sum = 0.f;
+#pragma unroll
+      for (int u = 0; u < QR_T / 32; ++u) sum += part[u * V + t];
+      Wsum[t] = sum;
+    }
+    __syncthreads();
+    float L[V], dinv[Q];
+    float dmax = 0.f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) dmax = fmaxf(dmax, i < q ? Wsum[i * (i + 1) / 2 + i] : 0.f);
+    bool ok = dmax > 0.f && isfinite(dmax);
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+      const int pj = j * (j + 1) / 2;
+      float d = (j < q) ? Wsum[pj + j] : 1.f;
+#pragma unroll
+      for (int l = 0; l < Q; ++l)
+        if (l < j) d = fmaf(-L[pj + l], L[pj + l], d);
+      if (j < q && (!(d > 1e-6f * dmax) || !isfinite(d))) ok = false;
+      const float ljj = sqrtf(fmaxf(d, 1e-30f));
+      L[pj + j] = ljj;
+      dinv[j] = 1.f / ljj;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        if (i <= j) continue;
+        const int pi = i * (i + 1) / 2;
+        float v = (i < q && j < q) ? Wsum[pi + j] : 0.f;
+#pragma unroll
+        for (int l = 0; l < Q; ++l)
+          if (l < j) v = fmaf(-L[pi + l], L[pj + l], v);
+        L[pi + j] = v * dinv[j];
+      }
+    }
+    if (!ok) return false;  // the same values in every thread: a uniform exit
+    for (int r = t; r < m; r += QR_T) {
+      float a[Q];
+      qr_load_row<Q>(As, r, a);
+#pragma unroll
+      for (int j = 0; j < Q; ++j) {
+        const int pj = j * (j + 1) / 2;
+        float v = a[j];
+#pragma unroll
+        for (int l = 0; l < Q; ++l)
+          if (l < j) v = fmaf(-a[l], L[pj + l], v);
+        a[j] = v * dinv[j];
+      }
+      qr_store_row<Q>(As, r, a);
+    }
+    if (t == 0) {
+#pragma unroll
+      for (int p = 0; p < V; ++p) Ls[pass * V + p] = L[p];
+    }
+  }
+  __syncthreads();
+  // R = R_2 R_1, R_p = L_p^T: R[i][j] = sum_{l = i..j} L_2[l][i] L_1[j][l]
+  for (int e = t; e < q * q; e += QR_T) {
+    const int i = e / q, j = e - i * q;
+    float acc = 0.f;
+    for (int l = i; l <= j; ++l) acc = fmaf(Ls[V + l * (l + 1) / 2 + i], Ls[j * (j + 1) / 2 + l], acc);
+    Rm[e] = acc;
+  }
+  __syncthreads();
+  return true;
+}
+
+
+// Shared-memory layout of k_qr_left_rows / k_lq_right_rows (floats): As (m x QP) | NX (the
+// neighbour core, when prefetched) | scratch (8 V + 3 V) | Rm (q x q) | tau (Q) | colsc (4)
+template <int Q>
+static size_t qr_rows_smem(int m, int64_t nx) {
+  constexpr int V = QrShape<Q>::V;
+  return sizeof(float) * ((size_t)m * QrShape<Q>::QP + (size_t)nx + 11 * V + Q * Q + Q + 4);
+}
+
+// G_k^L (m = r0 n rows, q = r1 <= Q cols) = Q R; G_k <- Q; G_{k+1} <- R G_{k+1}^R. The
+// neighbour G_{k+1} (r1 x ncols_next) is prefetched with cp.async while the QR runs when
+// `prefetch` is set (the launcher reserved room for it).
+template <int Q>
+__global__ void __launch_bounds__(QR_T, 1) k_qr_left_rows(float* core, float* next, int r0, int n, int r1,
+                                                      int ncols_next, int prefetch, const int* status) {
+  extern __shared__ __align__(16) float sm[];
+  constexpr int QP = QrShape<Q>::QP, V = QrShape<Q>::V;
+  if (*status != 0) return;
+  const int m = r0 * n, q = r1, t = threadIdx.x;
+  const int64_t nx = prefetch ? (int64_t)r1 * ncols_next : 0;
+  float* As = sm;
+  float* NX = As + (size_t)m * QP;
+  float* scratch = NX + nx;
+  float* Rm = scratch + 11 * V;
+  float* tau = Rm + Q * Q;
+  float* colsc = tau + Q;
+  bool ok = false;
+  if (m >= q) {
+    for (int j = 0; j < q; ++j)  // G_k^L column-major -> rows
+      for (int r = t; r < m; r += QR_T) cp_async4(As + (size_t)r * QP + j, core + (size_t)j * m + r);
+  }
+  cp_async_commit();  // group 0: the matrix (empty when m < q)
+  for (int64_t idx = t; idx < nx; idx += QR_T) cp_async4(NX + idx, next + idx);
+  cp_async_commit();  // group 1: the neighbour core
+  if (m >= q) {
+    for (int r = t; r < m; r += QR_T)  // zero padding columns
+#pragma unroll
+      for (int j = 0; j < QP; ++j)
+        if (j >= q) As[(size_t)r * QP + j] = 0.f;
+    cp_async_wait<1>();
+    __syncthreads();
+    ok = cholqr2_rows<Q>(As, m, q, scratch, Rm);
+    if (ok)
+      for (int j = 0; j < q; ++j)
+        for (int r = t; r < m; r += QR_T) core[(size_t)j * m + r] = As[(size_t)r * QP + j];
+  }
+  cp_async_wait<0>();
+  __syncthreads();
+  if (!ok) {  // Householder on a dense column-major copy (pitch m)
+    stage_batched(m * q, [&](int idx) { return core + idx; }, [&](int idx) { return As + idx; });
+    __syncthreads();
+    block_householder_qr(As, m, q, Rm, tau, colsc);
+    const int p = min(m, q);
+    for (int idx = t; idx < m * q; idx += QR_T) core[idx] = (idx / m < p) ? As[idx] : 0.f;
+    __syncthreads();
+  }
+  // G_{k+1}^R <- R G_{k+1}^R (r1 x ncols_next, column-major): one thread per column, the upper
+  // triangle of R in registers
+  float R[QrShape<Q>::V];
+#pragma unroll
+  for (int a2 = 0; a2 < Q; ++a2)
+#pragma unroll
+    for (int b = 0; b < Q; ++b)
+      if (b >= a2) R[b * (b + 1) / 2 + a2] = (a2 < q && b < q) ? Rm[a2 * q + b] : 0.f;
+  for (int cc = t; cc < ncols_next; cc += QR_T) {
+    float x[Q];
+    const float* src = prefetch ? NX + (size_t)cc * r1 : next + (size_t)cc * r1;
+#pragma unroll
+    for (int b = 0; b < Q; ++b) x[b] = b < q ? src[b] : 0.f;
+#pragma unroll
+    for (int a2 = 0; a2 < Q; ++a2) {
+      if (a2 >= q) break;
+      float acc = 0.f;
+#pragma unroll
+      for (int b = 0; b < Q; ++b)
+        if (b >= a2) acc = fmaf(R[b * (b + 1) / 2 + a2], x[b], acc);
+      next[(size_t)cc * r1 + a2] = acc;
+    }
+  }
+}
+
+// (G_k^R)^T (m = n r1 rows, q = r0 <= Q cols) = Q R; G_k^R <- Q^T; G_{k-1}^L <- G_{k-1}^L R^T.
+// The neighbour G_{k-1} (nrows_prev x r0) is prefetched as in k_qr_left_rows.
+template <int Q>
+__global__ void __launch_bounds__(QR_T, 1) k_lq_right_rows(float* prev, float* core, int r0, int n, int r1,
+                                                       int nrows_prev, int prefetch, const int* status) {
+  extern __shared__ __align__(16) float sm[];
+  constexpr int QP = QrShape<Q>::QP, V = QrShape<Q>::V;
+  if (*status != 0) return;
+  const int m = n * r1, q = r0, t = threadIdx.x;
+  const int64_t nx = prefetch ? (int64_t)nrows_prev * r0 : 0;
+  float* As = sm;
+  float* NX = As + (size_t)m * QP;
+  float* scratch = NX + nx;
+  float* Rm = scratch + 11 * V;
+  float* tau = Rm + Q * Q;
+  float* colsc = tau + Q;
+  bool ok = false;
+  if (m >= q) {
+    for (int i = t; i < m; i += QR_T)  // row i of (G_k^R)^T = core[q i .. q i + q)
+#pragma unroll
+      for (int a2 = 0; a2 < Q; ++a2)
+        if (a2 < q) cp_async4(As + (size_t)i * QP + a2, core + (size_t)i * q + a2);
+  }
+  cp_async_commit();  // group 0: the matrix (empty when m < q)
+  for (int64_t idx = t; idx < nx; idx += QR_T) cp_async4(NX + idx, prev + idx);
+  cp_async_commit();  // group 1: the neighbour core
+  if (m >= q) {
+    for (int r = t; r < m; r += QR_T)  // zero padding columns
+#pragma unroll
+      for (int j = 0; j < QP; ++j)
+        if (j >= q) As[(size_t)r * QP + j] = 0.f;
+    cp_async_wait<1>();
+    __syncthreads();
+    ok = cholqr2_rows<Q>(As, m, q, scratch, Rm);
+    if (ok)
+      for (int i = t; i < m; i += QR_T)
+#pragma unroll
+        for (int a2 = 0; a2 < Q; ++a2)
+          if (a2 < q) core[(size_t)i * q + a2] = As[(size_t)i * QP + a2];
+  }
+  cp_async_wait<0>();
+  __syncthreads();
+  if (!ok) {
+    stage_batched(m * q, [&](int idx) { return core + (idx / m) + (int64_t)r0 * (idx % m); },
+                  [&](int idx) { return As + idx; });  // dense, pitch m
+    __syncthreads();
+    block_householder_qr(As, m, q, Rm, tau, colsc);
+    const int p = min(m, q);
+    for (int idx = t; idx < m * q; idx += QR_T) {
+      const int i = idx % m, a2 = idx / m;
+      core[a2 + (int64_t)r0 * i] = (a2 < p) ? As[idx] : 0.f;
+    }
+    __syncthreads();
+  }
+  // G_{k-1}^L <- G_{k-1}^L R^T (nrows_prev x r0, column-major): one thread per row, the upper
+  // triangle of R in registers
+  float R[QrShape<Q>::V];
+#pragma unroll
+  for (int b = 0; b < Q; ++b)
+#pragma unroll
+    for (int a2 = 0; a2 < Q; ++a2)
+      if (a2 >= b) R[a2 * (a2 + 1) / 2 + b] = (a2 < q && b < q) ? Rm[b * q + a2] : 0.f;
+  for (int tt = t; tt < nrows_prev; tt += QR_T) {
+    float x[Q];
+    const float* src = prefetch ? NX : prev;
+#pragma unroll
+    for (int a2 = 0; a2 < Q; ++a2) x[a2] = a2 < q ? src[tt + (size_t)nrows_prev * a2] : 0.f;
+#pragma unroll
+    for (int b = 0; b < Q; ++b) {
+      if (b >= q) break;
+      float acc = 0.f;
+#pragma unroll
+      for (int a2 = 0; a2 < Q; ++a2)
+        if (a2 >= b) acc = fmaf(x[a2], R[a2 * (a2 + 1) / 2 + b], acc);
+      prev[tt + (size_t)nrows_prev * b] = acc;
+    }
+  }
+}
+
+// Launch a rows kernel for q <= 16 when its shared memory fits; false = use the generic kernels.
+template <int Q, bool LEFT>
+static bool launch_qr_rows_q(float* a0, float* a1, int r0, int n, int r1, int nbr, int m, int64_t nx,
+                             const int* status, cudaStream_t st, cudaError_t* err) {
+  size_t smem = qr_rows_smem<Q>(m, nx);
+  int prefetch = 1;
+  if (smem > 200 * 1024) {
+    prefetch = 0;
+    smem = qr_rows_smem<Q>(m, 0);
+    if (smem > 200 * 1024) return false;
+  }
+  auto kern = LEFT ? k_qr_left_rows<Q> : k_lq_right_rows<Q>;
+  *err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (*err != cudaSuccess) return true;
+  kern<<<1, QR_T, smem, st>>>(a0, a1, r0, n, r1, nbr, prefetch, status);
+  *err = cudaGetLastError();
+  return true;
+}
+
+template <bool LEFT>
+static bool launch_qr_rows(float* a0, float* a1, int r0, int n, int r1, int nbr, const int* status,
+                           cudaStream_t st, cudaError_t* err) {
+  const int q = LEFT ? r1 : r0, m = LEFT ? r0 * n : n * r1;
+  const int64_t nx = (int64_t)nbr * q;
+  if (q <= 4) return launch_qr_rows_q<4, LEFT>(a0, a1, r0, n, r1, nbr, m, nx, status, st, err);
+  if (q <= 8) return launch_qr_rows_q<8, LEFT>(a0, a1, r0, n, r1, nbr, m, nx, status, st, err);
+  if (q <= 12) return launch_qr_rows_q<12, LEFT>(a0, a1, r0, n, r1, nbr, m, nx, status, st, err);
+  if (q <= 16) return launch_qr_rows_q<16, LEFT>(a0, a1, r0, n, r1, nbr, m, nx, status, st, err);
+  return false;
+}
+
 static size_t qr_smem(int m, int q, int use_chol) {
   const size_t lda = use_chol ? (size_t)(m | 1) : (size_t)m;
   return sizeof(float) * (lda * q + (size_t)q * q + q + 4 + (size_t)std::max(q * q, 512) + (size_t)q * q);
@@ -662,10 +1024,16 @@ static size_t qr_smem(int m, int q, int use_chol) {
 
 int tt_launch_qr_left(tt_ctx* c, float* core_k, float* core_k1, int k) {
   int r0 = c->r[k], n = (int)c->n[k], r1 = c->r[k + 1];
+  int ncols = (int)(c->n[k + 1] * c->r[k + 2]);
+  cudaError_t e = cudaSuccess;
+  if (launch_qr_rows<true>(core_k, core_k1, r0, n, r1, ncols, c->d_status, c->stream, &e)) {
+    TT_CUDA(c, e);
+    TT_LAUNCH(c, "k_qr_left_rows");
+    return TT_OK;
+  }
   const int use_chol = (r1 <= 32) ? 1 : 0;
   size_t smem = qr_smem(r0 * n, r1, use_chol);
   TT_CUDA(c, cudaFuncSetAttribute(k_qr_left, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int ncols = (int)(c->n[k + 1] * c->r[k + 2]);
   k_qr_left<<<1, 512, smem, c->stream>>>(core_k, core_k1, r0, n, r1, ncols, use_chol, c->d_status);
   TT_LAUNCH(c, "k_qr_left");
   return TT_OK;
@@ -673,10 +1041,16 @@ int tt_launch_qr_left(tt_ctx* c, float* core_k, float* core_k1, int k) {
 
 int tt_launch_lq_right(tt_ctx* c, float* core_km1, float* core_k, int k) {
   int r0 = c->r[k], n = (int)c->n[k], r1 = c->r[k + 1];
+  int nrows = (int)(c->r[k - 1] * c->n[k - 1]);
+  cudaError_t e = cudaSuccess;
+  if (launch_qr_rows<false>(core_km1, core_k, r0, n, r1, nrows, c->d_status, c->stream, &e)) {
+    TT_CUDA(c, e);
+    TT_LAUNCH(c, "k_lq_right_rows");
+    return TT_OK;
+  }
   const int use_chol = (r0 <= 32) ? 1 : 0;
   size_t smem = qr_smem(n * r1, r0, use_chol);
   TT_CUDA(c, cudaFuncSetAttribute(k_lq_right, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int nrows = (int)(c->r[k - 1] * c->n[k - 1]);
   k_lq_right<<<1, 512, smem, c->stream>>>(core_km1, core_k, r0, n, r1, nrows, use_chol, c->d_status);
   TT_LAUNCH(c, "k_lq_right");
   return TT_OK;
@@ -1234,7 +1608,7 @@ int tt_launch_rel_error(tt_ctx* c, const void* A, const float* scales, float* co
 // ---------------------------------------------------------------------------------------------
 // Allocation-free variant of the proximal update (see tt_prox_update_noalloc in tt_sketch.h).
 //
-// Its only scratch -- the FP64 accumulators of [SH | Y]^T SH and the status word -- lives in the
+// Its only scratch -- the FP32 accumulators of [SH | Y]^T SH and the status word -- lives in the
 // file-scope array below, sized for s = r0*r1 <= 160 and n <= 1024. Every GPU that loads the
 // library holds these ~1.5 MB until the process exits. In host code `g_noalloc_scratch` only
 // names a host-side stand-in, so the device address is looked up once per device with
@@ -1280,10 +1654,10 @@ extern "C" int tt_prox_update_noalloc(const float* Y_dev, const float* SH_dev, f
   void* base = nullptr;
   int rc = noalloc_scratch(&base);
   if (rc) return rc;
-  double* gram = (double*)base;
-  int* status = (int*)(gram + TT_NOALLOC_GRAM);
+  float* gram = (float*)base;
+  int* status = (int*)((double*)base + TT_NOALLOC_GRAM);
   // the array keeps the previous call's contents: clear the accumulators and the status word
-  if (cudaMemsetAsync(gram, 0, sizeof(double) * (size_t)(s + n) * s, st) != cudaSuccess) return TT_ECUDA;
+  if (cudaMemsetAsync(gram, 0, sizeof(float) * (size_t)(s + n) * s, st) != cudaSuccess) return TT_ECUDA;
   if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return TT_ECUDA;
   GramArgs g;
   g.SH = SH_dev;
@@ -1306,12 +1680,7 @@ extern "C" int tt_prox_update_noalloc(const float* Y_dev, const float* SH_dev, f
   a.n = n;
   a.r0 = r0;
   a.r1 = r1;
-  a.chunk_rows = solve_chunk_rows(s, n);
-  size_t smem = solve_smem(s, a.chunk_rows);
-  if (cudaFuncSetAttribute(k_prox_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-    return TT_ECUDA;
-  k_prox_solve<<<(n + a.chunk_rows - 1) / a.chunk_rows, 1024, smem, st>>>(a);
-  if (cudaGetLastError() != cudaSuccess) return TT_ECUDA;
+  if (launch_prox_solve(a, st) != cudaSuccess) return TT_ECUDA;
   int hst = 0;
   if (cudaMemcpyAsync(&hst, status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return TT_ECUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return TT_ECUDA;

@@ -217,7 +217,8 @@ def test_prox_update_not_spd_leaves_core():
 # a7-a8: orthogonalisation
 
 @pytest.mark.parametrize("dims,ranks", [((6, 7, 5, 4), (1, 3, 4, 2, 1)), ((256, 256, 3, 128), (1, 20, 3, 20, 1)),
-                                        ((10, 12, 3, 9), (1, 8, 3, 8, 1)), ((40, 40, 40), (1, 8, 8, 1))])
+                                        ((10, 12, 3, 9), (1, 8, 3, 8, 1)), ((40, 40, 40), (1, 8, 8, 1)),
+                                        ((30, 24, 20, 16), (1, 10, 12, 10, 1)), ((32, 20, 18), (1, 16, 9, 1))])
 def test_orthogonalization_parity(dims, ranks):
     cores = synth.random_tt(dims, ranks, 31)
     c32 = [np.asarray(g, np.float32).astype(np.float64) for g in cores]
@@ -235,6 +236,32 @@ def test_orthogonalization_parity(dims, ranks):
         assert rel(got[k], ref[k]) <= 1e-4, (k, rel(got[k], ref[k]))
         assert rel(got[k + 1], ref[k + 1]) <= 1e-4
     assert rel(O.tt_full(got), O.tt_full(c32)) <= 1e-5
+    ctx.close()
+
+
+@pytest.mark.parametrize("case", ["rank_deficient", "wide"])
+def test_orthogonalization_fallback(case):
+    """CholeskyQR2 gives way to Householder when G_k^L is rank deficient (a repeated column) or
+    wider than tall; either way [[G]] is unchanged and G_k^L gets orthonormal columns (zero
+    columns past its row count in the wide case)."""
+    if case == "rank_deficient":
+        dims, ranks = (9, 7, 6), (1, 5, 6, 1)
+    else:
+        dims, ranks = (2, 3, 6), (1, 2, 8, 1)
+    cores = synth.random_tt(dims, ranks, 41)
+    if case == "rank_deficient":
+        cores[1][:, :, 4] = cores[1][:, :, 1]
+    c32 = [np.asarray(g, np.float32).astype(np.float64) for g in cores]
+    ctx = lib.Context(dims, ranks, 64, 1e-3, 5, "f32")
+    dc = lib.device_cores(cores)
+    ctx.tt_orthogonalize(dc, +1, 1)
+    got = lib.host_cores(dc, ranks, dims)
+    assert rel(O.tt_full(got), O.tt_full(c32)) <= 1e-5
+    m, q = ranks[1] * dims[1], ranks[2]
+    GL = got[1].reshape(m, q, order="F")
+    p = min(m, q)
+    assert np.allclose(GL[:, :p].T @ GL[:, :p], np.eye(p), atol=1e-5)
+    assert np.all(GL[:, p:] == 0)
     ctx.close()
 
 
