@@ -50,10 +50,7 @@ extern "C" int tt_sketch_unfold(tt_ctx* c, const void* A, const float* scales, i
   return TT_OK;
 }
 
-static int build_all_ghat(tt_ctx* c, float* const* cores) {
-  for (int j = 0; j < c->d; ++j) TT_TRY(tt_launch_core_fft(c, cores[j], j));
-  return TT_OK;
-}
+static int build_all_ghat(tt_ctx* c, float* const* cores) { return tt_launch_core_ffts(c, cores); }
 
 extern "C" int tt_sketch_interface(tt_ctx* c, float* const* cores, int k, uint64_t sweep, float* SH) {
   if (!c) return TT_EINVAL;

@@ -2,11 +2,14 @@
 // with F S_{<k} G_{<k} and F S_{>k} G_{>k}^T formed by slice-wise products of the
 // FFT-sketched cores G_j x_2 (F S_j)                                            (Theorem 2).
 //
-// Every core is real, so each DFT is Hermitian and only the J/2+1 frequencies 0..J/2 are kept.
-//   k_core_fft2    : CountSketch of two (a, b) fibres of core j into J buckets (real and imaginary
-//                    parts) + radix-4 Stockham FFT; k_core_fft (radix-2, one fibre) for J = 16384
+// Every core is real, so each DFT is Hermitian and only the H = J/2+1 frequencies 0..J/2 are
+// kept. Spectra are stored rank-major with the frequency fastest -- Ghat_j[(a + r_j b) H + w],
+// R_{>k}[b H + w], L_{<k}[a H + w] -- so that every kernel below reads and writes them coalesced.
+//   k_core_fft2    : CountSketch of two (a, b) fibres of a core into J buckets (real and imaginary
+//                    parts) + radix-4 Stockham FFT, the fibres of several cores in one launch;
+//                    k_core_fft (radix-2, one fibre) for J = 16384
 //   k_suffix_chain : R_{>k}(w) = Ghat_{k+1}(w) ... Ghat_{d-1}(w) for all k   (one thread per w)
-//   k_prefix_step  : L_{<j+1}(w) = L_{<j}(w) Ghat_j(w)
+//   k_prefix_step  : L_{<j+1}(w) = L_{<j}(w) Ghat_j(w)                      (one thread per w, b)
 //   k_face_ifft2   : two columns c = a + r_k b of S H_k: inverse FFT of L_{<k}(w)[a] R_{>k}(w)[b]
 //                    (k_face_ifft, one column with radix-2, for J = 16384)
 #include "tt_internal.cuh"
@@ -51,14 +54,26 @@ __device__ void block_fft(float2* buf, const float2* __restrict__ tw, int J, int
 // the twiddles exp(-2 pi i r (j mod Ns) / (4 Ns)), takes a 4-point DFT and writes
 // y[(j / Ns) 4 Ns + (j mod Ns) + r Ns]; a radix-2 stage first when logJ is odd. x and y are
 // J-entry shared buffers (ping-pong); returns the buffer holding the result. One barrier per stage.
-__device__ __forceinline__ float2 tw_full(const float2* __restrict__ tw, int t, int J) {
-  // exp(-2 pi i t / J) for 0 <= t < J from the J/2-entry table
-  if (t < (J >> 1)) return __ldg(tw + t);
-  const float2 w = __ldg(tw + t - (J >> 1));
+__device__ __forceinline__ float2 tw_full(const float2* tw, int t, int J) {
+  // exp(-2 pi i t / J) for 0 <= t < J from the J/2-entry table (in shared memory)
+  if (t < (J >> 1)) return tw[t];
+  const float2 w = tw[t - (J >> 1)];
   return make_float2(-w.x, -w.y);
 }
 
-__device__ float2* block_fft_stockham(float2* x, float2* y, const float2* __restrict__ tw, int J, int logJ) {
+// Copy the J/2-entry twiddle table into shared memory (asynchronously; the caller's first
+// barrier after the FFT inputs are staged makes it visible).
+__device__ __forceinline__ void stage_twiddles(float2* tws, const float2* __restrict__ tw, int J) {
+  for (int t = threadIdx.x; t < (J >> 1); t += blockDim.x) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(tws + t);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(tw + t) : "memory");
+  }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void wait_twiddles() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// tw: the twiddle table in shared memory (stage_twiddles + wait_twiddles before the call)
+__device__ float2* block_fft_stockham(float2* x, float2* y, const float2* tw, int J, int logJ) {
   int Ns = 1;
   __syncthreads();
   if (logJ & 1) {
@@ -98,91 +113,126 @@ __device__ float2* block_fft_stockham(float2* x, float2* y, const float2* __rest
   return x;
 }
 
+// The fibres (a, b) of up to TT_MAX_D cores: core q owns fibre pairs [pair0[q], pair0[q + 1]).
 struct CoreFftArgs {
-  const float* core;  // r0 x n x r1, r0 fastest
-  const int32_t* h;   // h_j, n entries
-  const int8_t* v;
+  const float* core[TT_MAX_D];  // r0 x n x r1, r0 fastest
+  const int32_t* h[TT_MAX_D];   // h_j, n entries
+  const int8_t* v[TT_MAX_D];
+  float2* out[TT_MAX_D];        // (r0 r1) x H, frequency fastest
+  int r0[TT_MAX_D], r1[TT_MAX_D], n[TT_MAX_D];
+  int pair0[TT_MAX_D + 1];
+  int ncores;
   const float2* tw;
-  float2* out;        // (J/2+1) x (r0 r1), frequency-major
-  int r0, r1, n, J, logJ;
+  int J, logJ;
 };
 
-__global__ void k_core_fft(CoreFftArgs a) {
+__device__ __forceinline__ int fft_core_of(const CoreFftArgs& a, int pair) {
+  int q = 0;
+  while (q + 1 < a.ncores && pair >= a.pair0[q + 1]) ++q;
+  return q;
+}
+
+__global__ void k_core_fft(CoreFftArgs a) {  // one fibre per CTA (pair0 counts fibres here)
   extern __shared__ float2 buf[];
-  const int fib = blockIdx.x;  // a + r0 * b
-  const int al = fib % a.r0, be = fib / a.r0;
+  const int q = fft_core_of(a, blockIdx.x);
+  const int fib = blockIdx.x - a.pair0[q];  // a + r0 * b
+  const int r0 = a.r0[q], n = a.n[q];
+  const int al = fib % r0, be = fib / r0;
   for (int t = threadIdx.x; t < a.J; t += blockDim.x) buf[t] = make_float2(0.f, 0.f);
   __syncthreads();
-  for (int i = threadIdx.x; i < a.n; i += blockDim.x) {
-    float g = a.core[al + (int64_t)a.r0 * (i + (int64_t)a.n * be)];
-    float s = a.v[i] < 0 ? -g : g;
-    atomicAdd(&buf[a.h[i]].x, s);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    float g = a.core[q][al + (int64_t)r0 * (i + (int64_t)n * be)];
+    float s = a.v[q][i] < 0 ? -g : g;
+    atomicAdd(&buf[a.h[q][i]].x, s);
   }
   __syncthreads();
   block_fft(buf, a.tw, a.J, a.logJ);
-  const int S = a.r0 * a.r1;
-  for (int w = threadIdx.x; w <= a.J / 2; w += blockDim.x) a.out[(int64_t)w * S + fib] = buf[w];
+  const int H = a.J / 2 + 1;
+  for (int w = threadIdx.x; w < H; w += blockDim.x) a.out[q][(int64_t)fib * H + w] = buf[w];
 }
 
 // Two CountSketched fibres per CTA, packed as z = x0 + i x1: one complex FFT, then
 // X0[w] = (Z[w] + conj Z[J-w]) / 2 and X1[w] = (Z[w] - conj Z[J-w]) / 2i for w <= J/2.
-__global__ void __launch_bounds__(256) k_core_fft2(CoreFftArgs a) {
+__global__ void __launch_bounds__(512) k_core_fft2(CoreFftArgs a) {
   extern __shared__ float2 fbuf[];
   float2* x = fbuf;
   float2* y = fbuf + a.J;
-  const int S = a.r0 * a.r1;
-  const int f0 = 2 * blockIdx.x, f1 = f0 + 1;
+  float2* tws = fbuf + 2 * a.J;
+  stage_twiddles(tws, a.tw, a.J);
+  const int q = fft_core_of(a, blockIdx.x);
+  const int r0 = a.r0[q], n = a.n[q], S = r0 * a.r1[q];
+  const int f0 = 2 * (blockIdx.x - a.pair0[q]), f1 = f0 + 1;
   const bool has1 = f1 < S;
   for (int t = threadIdx.x; t < a.J; t += blockDim.x) x[t] = make_float2(0.f, 0.f);
   __syncthreads();
-  const int al0 = f0 % a.r0, be0 = f0 / a.r0, al1 = f1 % a.r0, be1 = f1 / a.r0;
-  for (int i = threadIdx.x; i < a.n; i += blockDim.x) {
-    const int hb = a.h[i];
-    const bool neg = a.v[i] < 0;
-    const float g0 = a.core[al0 + (int64_t)a.r0 * (i + (int64_t)a.n * be0)];
+  const int al0 = f0 % r0, be0 = f0 / r0, al1 = f1 % r0, be1 = f1 / r0;
+  const float* core = a.core[q];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int hb = a.h[q][i];
+    const bool neg = a.v[q][i] < 0;
+    const float g0 = core[al0 + (int64_t)r0 * (i + (int64_t)n * be0)];
     atomicAdd(&x[hb].x, neg ? -g0 : g0);
     if (has1) {
-      const float g1 = a.core[al1 + (int64_t)a.r0 * (i + (int64_t)a.n * be1)];
+      const float g1 = core[al1 + (int64_t)r0 * (i + (int64_t)n * be1)];
       atomicAdd(&x[hb].y, neg ? -g1 : g1);
     }
   }
-  const float2* Z = block_fft_stockham(x, y, a.tw, a.J, a.logJ);
-  for (int w = threadIdx.x; w <= a.J / 2; w += blockDim.x) {
+  wait_twiddles();
+  const float2* Z = block_fft_stockham(x, y, tws, a.J, a.logJ);
+  const int H = a.J / 2 + 1;
+  float2* o0 = a.out[q] + (int64_t)f0 * H;
+  for (int w = threadIdx.x; w < H; w += blockDim.x) {
     const float2 z = Z[w], zc = Z[(a.J - w) & (a.J - 1)];
-    a.out[(int64_t)w * S + f0] = make_float2(0.5f * (z.x + zc.x), 0.5f * (z.y - zc.y));
-    if (has1) a.out[(int64_t)w * S + f1] = make_float2(0.5f * (z.y + zc.y), -0.5f * (z.x - zc.x));
+    o0[w] = make_float2(0.5f * (z.x + zc.x), 0.5f * (z.y - zc.y));
+    if (has1) o0[H + w] = make_float2(0.5f * (z.y + zc.y), -0.5f * (z.x - zc.x));
   }
 }
 
-int tt_launch_core_fft(tt_ctx* c, const float* core, int j) {
+// FFT sketches of cores j0 .. j1-1 in one launch
+static int launch_core_ffts(tt_ctx* c, float* const* cores, int j0, int j1) {
   CoreFftArgs a;
-  a.core = core;
-  a.h = c->d_h + c->noff[j];
-  a.v = c->d_v + c->noff[j];
+  const bool two = c->J <= 8192;  // two J-entry ping-pong buffers fit in shared memory
+  a.ncores = j1 - j0;
+  a.pair0[0] = 0;
+  for (int q = 0; q < a.ncores; ++q) {
+    const int j = j0 + q;
+    a.core[q] = cores[q];
+    a.h[q] = c->d_h + c->noff[j];
+    a.v[q] = c->d_v + c->noff[j];
+    a.out[q] = c->d_ghat + c->ghat_off[j];
+    a.r0[q] = c->r[j];
+    a.r1[q] = c->r[j + 1];
+    a.n[q] = (int)c->n[j];
+    const int S = a.r0[q] * a.r1[q];
+    a.pair0[q + 1] = a.pair0[q] + (two ? (S + 1) / 2 : S);
+  }
   a.tw = c->d_twiddle;
-  a.out = c->d_ghat + c->ghat_off[j];
-  a.r0 = c->r[j];
-  a.r1 = c->r[j + 1];
-  a.n = (int)c->n[j];
   a.J = c->J;
   a.logJ = c->logJ;
-  if (c->J <= 8192) {  // two J-entry ping-pong buffers fit in shared memory
-    const size_t smem = 2 * sizeof(float2) * c->J;
+  if (two) {
+    const size_t smem = sizeof(float2) * (2 * c->J + c->J / 2);  // ping-pong buffers + twiddles
     static bool attr = false;
     if (!attr) {
-      TT_CUDA(c, cudaFuncSetAttribute(k_core_fft2, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * (int)sizeof(float2) * 8192));
+      TT_CUDA(c, cudaFuncSetAttribute(k_core_fft2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(float2) * (2 * 8192 + 4096)));
       attr = true;
     }
-    k_core_fft2<<<(a.r0 * a.r1 + 1) / 2, 256, smem, c->stream>>>(a);
+    k_core_fft2<<<a.pair0[a.ncores], 512, smem, c->stream>>>(a);
     TT_LAUNCH(c, "k_core_fft2");
     return TT_OK;
   }
   size_t smem = sizeof(float2) * c->J;
   if (smem > 48 * 1024) TT_CUDA(c, cudaFuncSetAttribute(k_core_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_core_fft<<<a.r0 * a.r1, 512, smem, c->stream>>>(a);
+  k_core_fft<<<a.pair0[a.ncores], 512, smem, c->stream>>>(a);
   TT_LAUNCH(c, "k_core_fft");
   return TT_OK;
 }
+
+int tt_launch_core_fft(tt_ctx* c, const float* core, int j) {
+  float* cs[1] = {const_cast<float*>(core)};
+  return launch_core_ffts(c, cs, j, j + 1);
+}
+
+int tt_launch_core_ffts(tt_ctx* c, float* const* cores) { return launch_core_ffts(c, cores, 0, c->d); }
 
 // ---------------------------------------------------------------------------------------------
 // chain products (slice-wise products of Theorem 2), one thread per frequency
@@ -196,21 +246,37 @@ struct ChainArgs {
   int d, H;
 };
 
+// Block (32 frequencies) x (min(max rank, 32) rows): thread (w, y) forms R_{>k}[al][w] for
+// al = y, y + blockDim.y, ... and k = d-2 .. 0; the rows of R_{>k+1} it reads were written by
+// its own block before the barrier.
 __global__ void k_suffix_chain(ChainArgs a) {
-  int w = blockIdx.x * blockDim.x + threadIdx.x;
-  if (w >= a.H) return;
-  // R_{>d-1} = [1]
-  a.suffix[a.suffix_off[a.d - 1] + w] = make_float2(1.f, 0.f);
+  const int w = blockIdx.x * 32 + threadIdx.x;
+  const bool live = w < a.H;
+  const int64_t H = a.H;
+  if (live && threadIdx.y == 0) a.suffix[a.suffix_off[a.d - 1] + w] = make_float2(1.f, 0.f);  // R_{>d-1} = [1]
+  __syncthreads();
+  constexpr int U = 8;
   for (int k = a.d - 2; k >= 0; --k) {
     const int ra = a.r[k + 1], rb = a.r[k + 2];
-    const float2* G = a.ghat + a.ghat_off[k + 1] + (int64_t)w * ra * rb;  // Ghat_{k+1}(w), (a + ra b)
-    const float2* Rn = a.suffix + a.suffix_off[k + 1] + (int64_t)w * rb;
-    float2* R = a.suffix + a.suffix_off[k] + (int64_t)w * ra;
-    for (int al = 0; al < ra; ++al) {
+    for (int al = threadIdx.y; live && al < ra; al += blockDim.y) {
+      const float2* G = a.ghat + a.ghat_off[k + 1] + (int64_t)al * H + w;  // Ghat_{k+1}[(al + ra b) H + w]
+      const float2* Rn = a.suffix + a.suffix_off[k + 1] + w;
       float2 acc = make_float2(0.f, 0.f);
-      for (int be = 0; be < rb; ++be) acc = cfma(G[al + ra * be], Rn[be], acc);
-      R[al] = acc;
+      for (int b0 = 0; b0 < rb; b0 += U) {
+        float2 g[U], rn[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int be = min(b0 + u, rb - 1);
+          g[u] = G[(int64_t)ra * be * H];
+          rn[u] = Rn[(int64_t)be * H];
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (b0 + u < rb) acc = cfma(g[u], rn[u], acc);
+      }
+      a.suffix[a.suffix_off[k] + (int64_t)al * H + w] = acc;
     }
+    __syncthreads();
   }
 }
 
@@ -225,7 +291,9 @@ int tt_launch_suffixes(tt_ctx* c) {
   a.suffix = c->d_suffix;
   a.d = c->d;
   a.H = c->J / 2 + 1;
-  k_suffix_chain<<<(a.H + 127) / 128, 128, 0, c->stream>>>(a);
+  int rmax = 1;
+  for (int k = 1; k < c->d; ++k) rmax = std::max(rmax, c->r[k]);
+  k_suffix_chain<<<(a.H + 31) / 32, dim3(32, std::min(rmax, 32)), 0, c->stream>>>(a);
   TT_LAUNCH(c, "k_suffix_chain");
   return TT_OK;
 }
@@ -242,24 +310,34 @@ int tt_launch_prefix_reset(tt_ctx* c) {
   return TT_OK;
 }
 
-// L_new(w)[b] = sum_a L(w)[a] Ghat_j(w)[a + ra b]; L has ra = r[j] entries per frequency
+// L_new(w)[b] = sum_a L(w)[a] Ghat_j(w)[a + ra b]; L has ra = r[j] entries per frequency. One
+// thread per (w, b): b = blockIdx.y.
 __global__ void k_prefix_step(const float2* __restrict__ L, const float2* __restrict__ G, float2* Ln,
-                              int ra, int rb, int H) {
-  int w = blockIdx.x * blockDim.x + threadIdx.x;
+                              int ra, int H) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x, be = blockIdx.y;
   if (w >= H) return;
-  const float2* Lw = L + (int64_t)w * ra;
-  const float2* Gw = G + (int64_t)w * ra * rb;
-  for (int be = 0; be < rb; ++be) {
-    float2 acc = make_float2(0.f, 0.f);
-    for (int al = 0; al < ra; ++al) acc = cfma(Lw[al], Gw[al + ra * be], acc);
-    Ln[(int64_t)w * rb + be] = acc;
+  constexpr int U = 8;  // loads in flight together
+  float2 acc = make_float2(0.f, 0.f);
+  const float2* Gb = G + (int64_t)ra * be * H + w;
+  for (int a0 = 0; a0 < ra; a0 += U) {
+    float2 l[U], g[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int al = min(a0 + u, ra - 1);
+      l[u] = __ldg(L + (int64_t)al * H + w);
+      g[u] = __ldg(Gb + (int64_t)al * H);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (a0 + u < ra) acc = cfma(l[u], g[u], acc);
   }
+  Ln[(int64_t)be * H + w] = acc;
 }
 
 int tt_launch_prefix_step(tt_ctx* c, int j) {
   int H = c->J / 2 + 1;
-  k_prefix_step<<<(H + 127) / 128, 128, 0, c->stream>>>(c->d_prefix, c->d_ghat + c->ghat_off[j],
-                                                        c->d_prefix_tmp, c->r[j], c->r[j + 1], H);
+  dim3 grid((H + 127) / 128, c->r[j + 1]);
+  k_prefix_step<<<grid, 128, 0, c->stream>>>(c->d_prefix, c->d_ghat + c->ghat_off[j], c->d_prefix_tmp, c->r[j], H);
   TT_LAUNCH(c, "k_prefix_step");
   std::swap(c->d_prefix, c->d_prefix_tmp);
   return TT_OK;
@@ -269,8 +347,8 @@ int tt_launch_prefix_step(tt_ctx* c, int j) {
 // face-split + inverse FFT: one CTA per column c = a + r_k b of S H_k
 
 struct FaceArgs {
-  const float2* L;  // H x ra (prefix L_{<k})
-  const float2* R;  // H x rb (suffix R_{>k})
+  const float2* L;  // ra x H (prefix L_{<k})
+  const float2* R;  // rb x H (suffix R_{>k})
   const float2* tw;
   float* SH;        // J x (ra rb), column-major
   int ra, rb, J, logJ;
@@ -282,22 +360,42 @@ __global__ void __launch_bounds__(256) k_face_ifft2(FaceArgs a) {
   extern __shared__ float2 fbuf[];
   float2* x = fbuf;
   float2* y = fbuf + a.J;
+  float2* tws = fbuf + 2 * a.J;
+  stage_twiddles(tws, a.tw, a.J);
   const int S = a.ra * a.rb;
   const int c0 = 2 * blockIdx.x, c1 = c0 + 1;
   const bool has1 = c1 < S;
-  const int al0 = c0 % a.ra, be0 = c0 / a.ra, al1 = c1 % a.ra, be1 = c1 / a.ra;
+  const int al0 = c0 % a.ra, be0 = c0 / a.ra, al1 = has1 ? c1 % a.ra : al0, be1 = has1 ? c1 / a.ra : be0;
   const int H = a.J / 2 + 1;
-  for (int w = threadIdx.x; w < a.J; w += blockDim.x) {
-    const int ws = (w < H) ? w : a.J - w;
-    float2 X = cmul(a.L[(int64_t)ws * a.ra + al0], a.R[(int64_t)ws * a.rb + be0]);
-    float2 Y = has1 ? cmul(a.L[(int64_t)ws * a.ra + al1], a.R[(int64_t)ws * a.rb + be1]) : make_float2(0.f, 0.f);
-    if (w >= H) {
-      X.y = -X.y;
-      Y.y = -Y.y;
+  const float2 *L0 = a.L + (int64_t)al0 * H, *R0 = a.R + (int64_t)be0 * H;
+  const float2 *L1 = a.L + (int64_t)al1 * H, *R1 = a.R + (int64_t)be1 * H;
+  constexpr int U = 4;  // frequencies per thread whose loads are in flight together
+  for (int w0 = threadIdx.x; w0 < a.J; w0 += U * blockDim.x) {
+    float2 l0[U], r0[U], l1[U], r1[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int w = min(w0 + u * (int)blockDim.x, a.J - 1);
+      const int ws = (w < H) ? w : a.J - w;
+      l0[u] = __ldg(L0 + ws);
+      r0[u] = __ldg(R0 + ws);
+      l1[u] = __ldg(L1 + ws);
+      r1[u] = __ldg(R1 + ws);
     }
-    x[w] = make_float2(X.x - Y.y, -(X.y + Y.x));  // conj(X + i Y)
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int w = w0 + u * blockDim.x;
+      if (w >= a.J) break;
+      float2 X = cmul(l0[u], r0[u]);
+      float2 Y = has1 ? cmul(l1[u], r1[u]) : make_float2(0.f, 0.f);
+      if (w >= H) {
+        X.y = -X.y;
+        Y.y = -Y.y;
+      }
+      x[w] = make_float2(X.x - Y.y, -(X.y + Y.x));  // conj(X + i Y)
+    }
   }
-  const float2* F = block_fft_stockham(x, y, a.tw, a.J, a.logJ);
+  wait_twiddles();
+  const float2* F = block_fft_stockham(x, y, tws, a.J, a.logJ);
   const float inv = 1.f / (float)a.J;
   for (int t = threadIdx.x; t < a.J; t += blockDim.x) {
     const float2 f = F[t];
@@ -315,7 +413,7 @@ __global__ void k_face_ifft(FaceArgs a) {
   // X[w] = conj(X[J - w]) above; forward FFT of conj(X) then real part / J = inverse DFT.
   for (int w = threadIdx.x; w < a.J; w += blockDim.x) {
     int ws = (w < H) ? w : a.J - w;
-    float2 x = cmul(a.L[(int64_t)ws * a.ra + al], a.R[(int64_t)ws * a.rb + be]);
+    float2 x = cmul(a.L[(int64_t)al * H + ws], a.R[(int64_t)be * H + ws]);
     if (w >= H) x.y = -x.y;
     buf[w] = make_float2(x.x, -x.y);
   }
@@ -336,10 +434,10 @@ int tt_launch_interface_from_chain(tt_ctx* c, int k, float* SH) {
   a.J = c->J;
   a.logJ = c->logJ;
   if (c->J <= 8192) {  // two columns per CTA, radix-4 Stockham
-    const size_t smem = 2 * sizeof(float2) * c->J;
+    const size_t smem = sizeof(float2) * (2 * c->J + c->J / 2);  // ping-pong buffers + twiddles
     static bool attr = false;
     if (!attr) {
-      TT_CUDA(c, cudaFuncSetAttribute(k_face_ifft2, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * (int)sizeof(float2) * 8192));
+      TT_CUDA(c, cudaFuncSetAttribute(k_face_ifft2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(float2) * (2 * 8192 + 4096)));
       attr = true;
     }
     k_face_ifft2<<<(a.ra * a.rb + 1) / 2, 256, smem, c->stream>>>(a);

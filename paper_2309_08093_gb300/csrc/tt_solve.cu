@@ -40,67 +40,95 @@ struct GramArgs {
   int J, s, n, kchunk;
 };
 
-// Software-pipelined: the next 32-wide k tile is loaded into registers (read-only loads, all
-// issued before any use) while the current tile is multiplied from shared memory.
+// CTA tile of 64 x 64 entries of [S H_k | Y_k]^T (S H_k) over one K-chunk; 256 threads with 4 x 4
+// entries each. K-steps of 16 rows are staged through shared memory as [k][column], so that a
+// thread reads its 4 rows and 4 columns with two 16-byte loads per k (8 FMAs per load); the next
+// step's global loads (16 bytes per thread and operand when VEC: J % 16 == 0 and aligned bases;
+// else 4 bounds-checked scalars) are in flight while the current step is multiplied. Chunks are
+// summed with FP32 atomics.
+template <bool VEC>
 __global__ void __launch_bounds__(256) k_gram(GramArgs a) {
-  __shared__ float X[32][33];
-  __shared__ float B[32][33];
+  __shared__ __align__(16) float Xs[16][68];
+  __shared__ __align__(16) float Bs[16][68];
+  const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
   const int rows = a.s + a.n;
-  const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+  const int r0 = blockIdx.x * 64, c0 = blockIdx.y * 64;
   const int kb = blockIdx.z * a.kchunk, ke = min(a.J, kb + a.kchunk);
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // 16 x 16 threads, 2 x 2 outputs each
-  float acc[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+  // loader: tile column lc = t / 4, k offset 4 (t % 4) within the step
+  const int lc = t >> 2, lk = (t & 3) * 4;
+  const int gr = r0 + lc, gc = c0 + lc;
+  const float* xcol = gr < a.s ? a.SH + (int64_t)gr * a.J : (gr < rows ? a.Y + (int64_t)(gr - a.s) * a.J : nullptr);
+  const float* bcol = gc < a.s ? a.SH + (int64_t)gc * a.J : nullptr;
   float xr[4], br[4];
-  auto load = [&](int b0) {
+  auto load = [&](int k0) {
+    if constexpr (VEC) {
+      const float4 xv = xcol ? __ldg(reinterpret_cast<const float4*>(xcol + k0 + lk)) : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 bv = bcol ? __ldg(reinterpret_cast<const float4*>(bcol + k0 + lk)) : make_float4(0.f, 0.f, 0.f, 0.f);
+      xr[0] = xv.x, xr[1] = xv.y, xr[2] = xv.z, xr[3] = xv.w;
+      br[0] = bv.x, br[1] = bv.y, br[2] = bv.z, br[3] = bv.w;
+    } else {
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int idx = threadIdx.x + 256 * u;
-      const int kk = idx & 31, cc = idx >> 5;
-      const int b = b0 + kk;
-      const int gr = r0 + cc, gc = c0 + cc;
-      float xv = 0.f, bv = 0.f;
-      if (b < ke) {
-        if (gr < a.s)
-          xv = __ldg(a.SH + (int64_t)gr * a.J + b);
-        else if (gr < rows)
-          xv = __ldg(a.Y + (int64_t)(gr - a.s) * a.J + b);
-        if (gc < a.s) bv = __ldg(a.SH + (int64_t)gc * a.J + b);
+      for (int e = 0; e < 4; ++e) {
+        const bool in = k0 + lk + e < ke;
+        xr[e] = (xcol && in) ? __ldg(xcol + k0 + lk + e) : 0.f;
+        br[e] = (bcol && in) ? __ldg(bcol + k0 + lk + e) : 0.f;
       }
-      xr[u] = xv;
-      br[u] = bv;
     }
   };
-  if (kb < ke) load(kb);
-  for (int b0 = kb; b0 < ke; b0 += 32) {
+  float acc[4][4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int idx = threadIdx.x + 256 * u;
-      X[idx & 31][idx >> 5] = xr[u];
-      B[idx & 31][idx >> 5] = br[u];
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  if (kb < ke) load(kb);
+  for (int k0 = kb; k0 < ke; k0 += 16) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      Xs[lk + e][lc] = xr[e];
+      Bs[lk + e][lc] = br[e];
     }
     __syncthreads();
-    if (b0 + 32 < ke) load(b0 + 32);  // in flight during the FMAs below
-#pragma unroll 8
-    for (int kk = 0; kk < 32; ++kk) {
-      float x0 = X[kk][ty], x1 = X[kk][ty + 16];
-      float y0 = B[kk][tx], y1 = B[kk][tx + 16];
-      acc[0][0] = fmaf(x0, y0, acc[0][0]);
-      acc[0][1] = fmaf(x0, y1, acc[0][1]);
-      acc[1][0] = fmaf(x1, y0, acc[1][0]);
-      acc[1][1] = fmaf(x1, y1, acc[1][1]);
+    if (k0 + 16 < ke) load(k0 + 16);  // in flight during the FMAs below
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      const float4 xv = *reinterpret_cast<const float4*>(&Xs[kk][ty * 4]);
+      const float4 bv = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
+      const float xa[4] = {xv.x, xv.y, xv.z, xv.w}, ba[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(xa[i], ba[j], acc[i][j]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < 2; ++i)
+  for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      int gr = r0 + ty + 16 * i, gc = c0 + tx + 16 * j;
-      if (gr < a.s && gc < a.s)
-        atomicAdd(a.C + (int64_t)gr * a.s + gc, acc[i][j]);
-      else if (gr < rows && gc < a.s)  // right-hand side stored transposed: s x n
-        atomicAdd(a.C + (int64_t)a.s * a.s + (int64_t)gc * a.n + (gr - a.s), acc[i][j]);
+    for (int j = 0; j < 4; ++j) {
+      const int row = r0 + ty * 4 + i, col = c0 + tx * 4 + j;
+      if (col >= a.s || row >= rows) continue;
+      if (row < a.s)
+        atomicAdd(a.C + (int64_t)row * a.s + col, acc[i][j]);
+      else  // right-hand side stored transposed: s x n
+        atomicAdd(a.C + (int64_t)a.s * a.s + (int64_t)col * a.n + (row - a.s), acc[i][j]);
     }
+}
+
+// Gram + right-hand side (C zeroed by the caller), any J >= 1.
+static cudaError_t launch_gram(GramArgs g, cudaStream_t st) {
+  const int mt = (g.s + g.n + 63) / 64, nt = (g.s + 63) / 64;
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+  // K-chunks: about two CTAs per SM in all, each at least 64 rows of K
+  const int ksplit = std::max(1, std::min(g.J / 64, (2 * sms + mt * nt - 1) / (mt * nt)));
+  g.kchunk = ((g.J + ksplit - 1) / ksplit + 15) & ~15;
+  dim3 grid(mt, nt, (g.J + g.kchunk - 1) / g.kchunk);
+  const bool vec = g.J % 16 == 0 && ((reinterpret_cast<uintptr_t>(g.SH) | reinterpret_cast<uintptr_t>(g.Y)) & 15) == 0;
+  if (vec)
+    k_gram<true><<<grid, 256, 0, st>>>(g);
+  else
+    k_gram<false><<<grid, 256, 0, st>>>(g);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -314,9 +342,7 @@ int tt_launch_prox_update(tt_ctx* c, const float* Y, const float* SH, float* cor
   g.J = c->J;
   g.s = s;
   g.n = n;
-  g.kchunk = std::max(32, std::min(256, c->J));
-  dim3 grid((s + n + 31) / 32, (s + 31) / 32, (c->J + g.kchunk - 1) / g.kchunk);
-  k_gram<<<grid, 256, 0, c->stream>>>(g);
+  TT_CUDA(c, launch_gram(g, c->stream));
   TT_LAUNCH(c, "k_gram");
   SolveArgs a;
   a.C = c->d_gram;
@@ -1666,10 +1692,7 @@ extern "C" int tt_prox_update_noalloc(const float* Y_dev, const float* SH_dev, f
   g.J = J;
   g.s = s;
   g.n = n;
-  g.kchunk = std::max(32, std::min(256, J));
-  dim3 grid((s + n + 31) / 32, (s + 31) / 32, (J + g.kchunk - 1) / g.kchunk);
-  k_gram<<<grid, 256, 0, st>>>(g);
-  if (cudaGetLastError() != cudaSuccess) return TT_ECUDA;
+  if (launch_gram(g, st) != cudaSuccess) return TT_ECUDA;
   SolveArgs a;
   a.C = gram;
   a.core = core_dev;
