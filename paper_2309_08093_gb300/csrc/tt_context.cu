@@ -364,7 +364,7 @@ int tt_ensure_plan0(tt_ctx* c) { return tt_ensure_rplan(c, 0); }
 
 static void free_all(tt_ctx* c) {
   void* ps[] = {c->d_h, c->d_v, c->d_plan0, c->d_plan0_off, c->d_plan0_cursor, c->d_ghat,
-                c->d_twiddle, c->d_suffix, c->d_prefix, c->d_prefix_tmp, c->d_SH, c->d_Y,
+                c->d_twiddle, c->d_twstage, c->d_suffix, c->d_prefix, c->d_prefix_tmp, c->d_SH, c->d_Y,
                 c->d_gram, c->d_core_old, c->d_changes, c->d_status, c->d_err_acc, c->d_ws_acc, c->d_rint, c->d_slab_u, c->d_Yall};
   for (void* p : ps)
     if (p) cudaFree(p);
@@ -465,6 +465,7 @@ extern "C" int tt_sketch_init(tt_ctx** out, const tt_params* p, void* stream) {
   }
   A((void**)&c->d_ghat, sizeof(float2) * c->ghat_off[c->d]);
   A((void**)&c->d_twiddle, sizeof(float2) * (c->J / 2));
+  A((void**)&c->d_twstage, sizeof(float2) * c->J);
   A((void**)&c->d_suffix, sizeof(float2) * c->suffix_off[c->d]);
   A((void**)&c->d_prefix, sizeof(float2) * H * c->rmax);
   A((void**)&c->d_prefix_tmp, sizeof(float2) * H * c->rmax);
@@ -509,6 +510,20 @@ extern "C" int tt_sketch_init(tt_ctx** out, const tt_params* p, void* stream) {
     tw[t] = make_float2((float)std::cos(ang), (float)std::sin(ang));
   }
   e = cudaMemcpyAsync(c->d_twiddle, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice, c->stream);
+  // per-stage tables of the radix-4 Stockham FFT: spans Ns = Ns0, 4 Ns0, ... < J (Ns0 = 2 after
+  // the radix-2 stage of an odd log J), entries exp(-2 pi i r m / (4 Ns)) at [off + 3 m + r - 1]
+  std::vector<float2> tws(c->J, make_float2(1.f, 0.f));
+  {
+    size_t off = 0;
+    for (int Ns = (c->logJ & 1) ? 2 : 1; Ns < c->J; Ns *= 4)
+      for (int m = 0; m < Ns; ++m, off += 3)
+        for (int r = 1; r <= 3; ++r) {
+          const double ang = -2.0 * M_PI * (double)r * (double)m / (4.0 * (double)Ns);
+          tws[off + r - 1] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+        }
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->d_twstage, tws.data(), sizeof(float2) * tws.size(), cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) {

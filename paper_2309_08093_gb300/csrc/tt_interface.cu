@@ -54,26 +54,9 @@ __device__ void block_fft(float2* buf, const float2* __restrict__ tw, int J, int
 // the twiddles exp(-2 pi i r (j mod Ns) / (4 Ns)), takes a 4-point DFT and writes
 // y[(j / Ns) 4 Ns + (j mod Ns) + r Ns]; a radix-2 stage first when logJ is odd. x and y are
 // J-entry shared buffers (ping-pong); returns the buffer holding the result. One barrier per stage.
-__device__ __forceinline__ float2 tw_full(const float2* tw, int t, int J) {
-  // exp(-2 pi i t / J) for 0 <= t < J from the J/2-entry table (in shared memory)
-  if (t < (J >> 1)) return tw[t];
-  const float2 w = tw[t - (J >> 1)];
-  return make_float2(-w.x, -w.y);
-}
-
-// Copy the J/2-entry twiddle table into shared memory (asynchronously; the caller's first
-// barrier after the FFT inputs are staged makes it visible).
-__device__ __forceinline__ void stage_twiddles(float2* tws, const float2* __restrict__ tw, int J) {
-  for (int t = threadIdx.x; t < (J >> 1); t += blockDim.x) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(tws + t);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(tw + t) : "memory");
-  }
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
-}
-__device__ __forceinline__ void wait_twiddles() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-
-// tw: the twiddle table in shared memory (stage_twiddles + wait_twiddles before the call)
-__device__ float2* block_fft_stockham(float2* x, float2* y, const float2* tw, int J, int logJ) {
+// twst: the per-stage twiddle tables (tt_ctx::d_twstage): span Ns reads exp(-2 pi i r m / (4 Ns))
+// at [off + 3 m + r - 1], consecutive butterflies consecutive entries.
+__device__ float2* block_fft_stockham(float2* x, float2* y, const float2* __restrict__ twst, int J, int logJ) {
   int Ns = 1;
   __syncthreads();
   if (logJ & 1) {
@@ -87,17 +70,17 @@ __device__ float2* block_fft_stockham(float2* x, float2* y, const float2* tw, in
     Ns = 2;
     __syncthreads();
   }
+  int off = 0;
   const int q = J >> 2;
-  for (; Ns < J; Ns <<= 2) {
-    const int tstep = q / Ns;  // J / (4 Ns)
+  for (; Ns < J; off += 3 * Ns, Ns <<= 2) {
     for (int j = threadIdx.x; j < q; j += blockDim.x) {
       const int jm = j & (Ns - 1);
       float2 v0 = x[j], v1 = x[j + q], v2 = x[j + 2 * q], v3 = x[j + 3 * q];
       if (Ns > 1) {
-        const int st = jm * tstep;
-        v1 = cmul(v1, tw_full(tw, st, J));
-        v2 = cmul(v2, tw_full(tw, 2 * st, J));
-        v3 = cmul(v3, tw_full(tw, 3 * st, J));
+        const float2* w = twst + off + 3 * jm;
+        v1 = cmul(v1, __ldg(w));
+        v2 = cmul(v2, __ldg(w + 1));
+        v3 = cmul(v3, __ldg(w + 2));
       }
       const float2 a = make_float2(v0.x + v2.x, v0.y + v2.y), b = make_float2(v0.x - v2.x, v0.y - v2.y);
       const float2 c = make_float2(v1.x + v3.x, v1.y + v3.y), d = make_float2(v1.x - v3.x, v1.y - v3.y);
@@ -122,7 +105,8 @@ struct CoreFftArgs {
   int r0[TT_MAX_D], r1[TT_MAX_D], n[TT_MAX_D];
   int pair0[TT_MAX_D + 1];
   int ncores;
-  const float2* tw;
+  const float2* tw;    // J/2 twiddles (radix-2 path)
+  const float2* twst;  // per-stage twiddles (Stockham path)
   int J, logJ;
 };
 
@@ -157,8 +141,6 @@ __global__ void __launch_bounds__(512) k_core_fft2(CoreFftArgs a) {
   extern __shared__ float2 fbuf[];
   float2* x = fbuf;
   float2* y = fbuf + a.J;
-  float2* tws = fbuf + 2 * a.J;
-  stage_twiddles(tws, a.tw, a.J);
   const int q = fft_core_of(a, blockIdx.x);
   const int r0 = a.r0[q], n = a.n[q], S = r0 * a.r1[q];
   const int f0 = 2 * (blockIdx.x - a.pair0[q]), f1 = f0 + 1;
@@ -177,8 +159,7 @@ __global__ void __launch_bounds__(512) k_core_fft2(CoreFftArgs a) {
       atomicAdd(&x[hb].y, neg ? -g1 : g1);
     }
   }
-  wait_twiddles();
-  const float2* Z = block_fft_stockham(x, y, tws, a.J, a.logJ);
+  const float2* Z = block_fft_stockham(x, y, a.twst, a.J, a.logJ);
   const int H = a.J / 2 + 1;
   float2* o0 = a.out[q] + (int64_t)f0 * H;
   for (int w = threadIdx.x; w < H; w += blockDim.x) {
@@ -207,13 +188,14 @@ static int launch_core_ffts(tt_ctx* c, float* const* cores, int j0, int j1) {
     a.pair0[q + 1] = a.pair0[q] + (two ? (S + 1) / 2 : S);
   }
   a.tw = c->d_twiddle;
+  a.twst = c->d_twstage;
   a.J = c->J;
   a.logJ = c->logJ;
   if (two) {
-    const size_t smem = sizeof(float2) * (2 * c->J + c->J / 2);  // ping-pong buffers + twiddles
+    const size_t smem = 2 * sizeof(float2) * c->J;  // ping-pong buffers
     static bool attr = false;
     if (!attr) {
-      TT_CUDA(c, cudaFuncSetAttribute(k_core_fft2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(float2) * (2 * 8192 + 4096)));
+      TT_CUDA(c, cudaFuncSetAttribute(k_core_fft2, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * (int)sizeof(float2) * 8192));
       attr = true;
     }
     k_core_fft2<<<a.pair0[a.ncores], 512, smem, c->stream>>>(a);
@@ -350,6 +332,7 @@ struct FaceArgs {
   const float2* L;  // ra x H (prefix L_{<k})
   const float2* R;  // rb x H (suffix R_{>k})
   const float2* tw;
+  const float2* twst;
   float* SH;        // J x (ra rb), column-major
   int ra, rb, J, logJ;
 };
@@ -360,8 +343,6 @@ __global__ void __launch_bounds__(256) k_face_ifft2(FaceArgs a) {
   extern __shared__ float2 fbuf[];
   float2* x = fbuf;
   float2* y = fbuf + a.J;
-  float2* tws = fbuf + 2 * a.J;
-  stage_twiddles(tws, a.tw, a.J);
   const int S = a.ra * a.rb;
   const int c0 = 2 * blockIdx.x, c1 = c0 + 1;
   const bool has1 = c1 < S;
@@ -394,8 +375,7 @@ __global__ void __launch_bounds__(256) k_face_ifft2(FaceArgs a) {
       x[w] = make_float2(X.x - Y.y, -(X.y + Y.x));  // conj(X + i Y)
     }
   }
-  wait_twiddles();
-  const float2* F = block_fft_stockham(x, y, tws, a.J, a.logJ);
+  const float2* F = block_fft_stockham(x, y, a.twst, a.J, a.logJ);
   const float inv = 1.f / (float)a.J;
   for (int t = threadIdx.x; t < a.J; t += blockDim.x) {
     const float2 f = F[t];
@@ -428,16 +408,17 @@ int tt_launch_interface_from_chain(tt_ctx* c, int k, float* SH) {
   a.L = c->d_prefix;
   a.R = c->d_suffix + c->suffix_off[k];
   a.tw = c->d_twiddle;
+  a.twst = c->d_twstage;
   a.SH = SH;
   a.ra = c->r[k];
   a.rb = c->r[k + 1];
   a.J = c->J;
   a.logJ = c->logJ;
   if (c->J <= 8192) {  // two columns per CTA, radix-4 Stockham
-    const size_t smem = sizeof(float2) * (2 * c->J + c->J / 2);  // ping-pong buffers + twiddles
+    const size_t smem = 2 * sizeof(float2) * c->J;  // ping-pong buffers
     static bool attr = false;
     if (!attr) {
-      TT_CUDA(c, cudaFuncSetAttribute(k_face_ifft2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(float2) * (2 * 8192 + 4096)));
+      TT_CUDA(c, cudaFuncSetAttribute(k_face_ifft2, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * (int)sizeof(float2) * 8192));
       attr = true;
     }
     k_face_ifft2<<<(a.ra * a.rb + 1) / 2, 256, smem, c->stream>>>(a);

@@ -65,6 +65,7 @@ struct tt_ctx {
   float2* d_ghat = nullptr;
   int64_t ghat_off[TT_MAX_D + 1];
   float2* d_twiddle = nullptr;   // J/2 twiddles exp(-2 pi i t / J)
+  float2* d_twstage = nullptr;   // radix-4 stage twiddles exp(-2 pi i r m / (4 Ns)), per stage [m][r-1]
   float2* d_suffix = nullptr;    // for each k: (J/2+1) x r[k+1] complex (suffix R_{>k})
   int64_t suffix_off[TT_MAX_D + 1];
   float2* d_prefix = nullptr;    // (J/2+1) x rmax complex: prefix L_{<k}

@@ -1331,6 +1331,49 @@ __global__ void __launch_bounds__(256) k_slab_u(ErrArgs a, float* __restrict__ U
   }
 }
 
+// The same right interfaces with G_1 in registers: a CTA takes a run of slabs; thread x owns the
+// output positions ol = x + blockDim.x k (k < RINT_KP; ol = i_1 r1p + al) of every slab of the
+// run and keeps their G_1(al, i_1, :) entries (RB >= r_2 of them) in registers, so each output
+// costs r_2 FMAs with u_t broadcast from shared memory; the stores of a slab are contiguous.
+constexpr int RINT_KP = 4;
+template <int RB>
+__global__ void __launch_bounds__(512, 1) k_rint_reg(ErrArgs a, const float* __restrict__ Uv, float* __restrict__ R,
+                                                   int r1p, int slabs_per_cta) {
+  extern __shared__ float us[];  // slabs_per_cta x r_2
+  const int n1 = (int)a.n[1], r1 = a.r[1], r2 = a.r[2];
+  const int per = n1 * r1p;
+  const int64_t t0 = (int64_t)blockIdx.x * slabs_per_cta;
+  if (t0 >= a.slabs) return;
+  const int nsl = (int)min((int64_t)slabs_per_cta, a.slabs - t0);
+  for (int e = threadIdx.x; e < nsl * r2; e += blockDim.x) us[e] = Uv[t0 * r2 + e];
+  const float* g1 = a.core[1];
+  float g[RINT_KP][RB];
+#pragma unroll
+  for (int k = 0; k < RINT_KP; ++k) {
+    const int ol = threadIdx.x + blockDim.x * k;
+    const int i1 = ol / r1p, al = ol - i1 * r1p;
+    const bool valid = ol < per && al < r1;
+#pragma unroll
+    for (int be = 0; be < RB; ++be)
+      g[k][be] = (valid && be < r2) ? __ldg(g1 + al + r1 * (i1 + n1 * be)) : 0.f;
+  }
+  __syncthreads();
+  for (int sl = 0; sl < nsl; ++sl) {
+    float u[RB];
+#pragma unroll
+    for (int be = 0; be < RB; ++be) u[be] = be < r2 ? us[sl * r2 + be] : 0.f;
+    float* out = R + (t0 + sl) * (int64_t)per;
+#pragma unroll
+    for (int k = 0; k < RINT_KP; ++k) {
+      const int ol = threadIdx.x + blockDim.x * k;
+      float acc = 0.f;
+#pragma unroll
+      for (int be = 0; be < RB; ++be) acc = fmaf(g[k][be], u[be], acc);
+      if (ol < per) out[ol] = acc;
+    }
+  }
+}
+
 __global__ void __launch_bounds__(256) k_rint(ErrArgs a, const float* __restrict__ Uv, float* __restrict__ R, int r1p) {
   __shared__ float u[TT_MAX_S];
   const int n1 = (int)a.n[1], r1 = a.r[1], r2 = a.r[2];
@@ -1597,9 +1640,29 @@ int tt_launch_rel_error(tt_ctx* c, const void* A, const float* scales, float* co
     const int ublocks = (int)std::max<int64_t>(1, std::min<int64_t>((a.slabs + 255) / 256, 4096));
     k_slab_u<<<ublocks, 256, 0, c->stream>>>(a, c->d_slab_u);
     TT_LAUNCH(c, "k_slab_u");
-    const int rblocks = (int)std::max<int64_t>(1, std::min<int64_t>(a.slabs, 152 * 8));
-    k_rint<<<rblocks, 256, 0, c->stream>>>(a, c->d_slab_u, c->d_rint, c->rint_r1p);
-    TT_LAUNCH(c, "k_rint");
+    const int per = (int)c->n[1] * c->rint_r1p;
+    const int r2 = c->r[2];
+    const int rthreads = ((per + RINT_KP - 1) / RINT_KP + 31) & ~31;
+    if (rthreads <= 512 && r2 <= 16) {  // G_1 entries in registers
+      int sms = 152;
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+      const int spc = (int)std::max<int64_t>(1, (a.slabs + 4 * sms - 1) / (4 * sms));
+      const int rgrid = (int)((a.slabs + spc - 1) / spc);
+      const size_t rsm = sizeof(float) * (size_t)spc * r2;
+      if (r2 <= 4)
+        k_rint_reg<4><<<rgrid, rthreads, rsm, c->stream>>>(a, c->d_slab_u, c->d_rint, c->rint_r1p, spc);
+      else if (r2 <= 8)
+        k_rint_reg<8><<<rgrid, rthreads, rsm, c->stream>>>(a, c->d_slab_u, c->d_rint, c->rint_r1p, spc);
+      else if (r2 <= 12)
+        k_rint_reg<12><<<rgrid, rthreads, rsm, c->stream>>>(a, c->d_slab_u, c->d_rint, c->rint_r1p, spc);
+      else
+        k_rint_reg<16><<<rgrid, rthreads, rsm, c->stream>>>(a, c->d_slab_u, c->d_rint, c->rint_r1p, spc);
+      TT_LAUNCH(c, "k_rint_reg");
+    } else {
+      const int rblocks = (int)std::max<int64_t>(1, std::min<int64_t>(a.slabs, 152 * 8));
+      k_rint<<<rblocks, 256, 0, c->stream>>>(a, c->d_slab_u, c->d_rint, c->rint_r1p);
+      TT_LAUNCH(c, "k_rint");
+    }
     switch (c->dtype) {
       case TT_F64: return launch_rel_stream<TT_F64>(c, A, scales, cores[0], ssm);
       case TT_F32: return launch_rel_stream<TT_F32>(c, A, scales, cores[0], ssm);
