@@ -118,6 +118,9 @@ static int sweep_body(tt_ctx* c, const void* A, const float* scales, float* cons
     }
     c->stream = main_stream;
     c->in_sweep = false;
+    // the next sweep's draw and plans, behind this sweep's data sketches on the side stream (not
+    // joined: it overlaps the rest of this sweep and whatever the caller does next)
+    if (rc == TT_OK) rc = tt_prepare_next_draw(c, sweep + 1);
     if (rc != TT_OK) {
       cudaEventRecord(c->ev_fork, c->side);  // join whatever was launched before returning
       cudaStreamWaitEvent(c->stream, c->ev_fork, 0);

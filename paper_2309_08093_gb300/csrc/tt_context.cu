@@ -7,6 +7,8 @@
 #include <new>
 #include <vector>
 
+#include <utility>
+
 #include "tt_internal.cuh"
 
 int tt_fail(tt_ctx* c, int code, const char* fmt, ...) {
@@ -58,6 +60,21 @@ __global__ void k_gen_tables_dev(uint64_t seed, const uint64_t* sweep_ptr, int f
   v[g] = (tt_word(seed, sweep, (uint64_t)k, 1ull, i) >> 63) ? (int8_t)-1 : (int8_t)1;
 }
 
+void tt_swap_draw(tt_ctx* c) {
+  TtDraw& o = c->spare;
+  std::swap(c->d_h, o.h);
+  std::swap(c->d_v, o.v);
+  for (int k = 0; k < TT_MAX_D; ++k) {
+    std::swap(c->d_rplan[k], o.rplan[k]);
+    std::swap(c->d_ulist[k], o.ulist[k]);
+    std::swap(c->d_ustart[k], o.ustart[k]);
+    std::swap(c->d_ucount[k], o.ucount[k]);
+    std::swap(c->rplan_valid[k], o.rplan_valid[k]);
+  }
+  std::swap(c->tables_valid, o.tables_valid);
+  std::swap(c->tables_sweep, o.tables_sweep);
+}
+
 int tt_ensure_tables(tt_ctx* c, uint64_t sweep) {
   if (c->user_tables) return TT_OK;
   if (c->capture_mode) {  // sweep index read on the device at replay time
@@ -73,6 +90,12 @@ int tt_ensure_tables(tt_ctx* c, uint64_t sweep) {
   }
   if (c->flags & TT_FLAG_FIXED_SKETCH) sweep = 0;
   if (c->tables_valid && c->tables_sweep == sweep) return TT_OK;
+  if (c->spare.tables_valid && c->spare.tables_sweep == sweep) {  // built ahead by the last sweep
+    tt_swap_draw(c);
+    if (c->spare_pending) TT_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_spare, 0));
+    return TT_OK;
+  }
+  if (c->spare_pending) TT_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_spare, 0));  // shared scratch
   TabArgs a;
   for (int k = 0; k <= c->d; ++k) a.noff[k] = c->noff[k];
   a.d = c->d;
@@ -340,6 +363,7 @@ int tt_ensure_rplan(tt_ctx* c, int k) {
     o.plan[m] = c->d_rplan[m];
   }
   int32_t* count = c->d_plan0_cursor;
+  if (c->spare_pending && c->stream != c->side) TT_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_spare, 0));
   TT_CUDA(c, cudaMemsetAsync(count, 0, sizeof(int32_t) * c->J * c->d, c->stream));
   const size_t hsm = sizeof(int) * c->J;
   if (hsm > 48 * 1024) {
@@ -359,6 +383,29 @@ int tt_ensure_rplan(tt_ctx* c, int k) {
 
 int tt_ensure_plan0(tt_ctx* c) { return tt_ensure_rplan(c, 0); }
 
+int tt_prepare_next_draw(tt_ctx* c, uint64_t sweep) {
+  if (c->capture_mode || c->user_tables || (c->flags & TT_FLAG_FIXED_SKETCH)) return TT_OK;
+  bool ready = c->spare.tables_valid && c->spare.tables_sweep == sweep;
+  for (int k = 0; k < c->d; ++k) ready = ready && c->spare.rplan_valid[k];
+  if (ready) return TT_OK;
+  tt_swap_draw(c);  // build into the spare through the current-draw fields
+  cudaStream_t s0 = c->stream;
+  c->stream = c->side;
+  c->tables_valid = false;
+  int rc = tt_ensure_tables(c, sweep);
+  if (rc == TT_OK) rc = tt_ensure_rplan(c, 0);
+  cudaError_t e = cudaEventRecord(c->ev_spare, c->side);
+  c->stream = s0;
+  tt_swap_draw(c);
+  if (rc == TT_OK && e != cudaSuccess) rc = tt_cuda_check(c, e, "cudaEventRecord");
+  if (rc != TT_OK) {
+    c->spare.tables_valid = false;
+    return rc;
+  }
+  c->spare_pending = true;
+  return TT_OK;
+}
+
 // ---------------------------------------------------------------------------------------------
 // lifetime
 
@@ -370,6 +417,16 @@ static void free_all(tt_ctx* c) {
     if (p) cudaFree(p);
   if (c->d_A_stage) cudaFree(c->d_A_stage);
   if (c->d_scales_stage) cudaFree(c->d_scales_stage);
+  void* sp[] = {c->spare.h, c->spare.v};
+  for (void* p : sp)
+    if (p) cudaFree(p);
+  if (c->ev_spare) cudaEventDestroy(c->ev_spare);
+  for (int k = 0; k < TT_MAX_D; ++k) {
+    if (c->spare.rplan[k]) cudaFree(c->spare.rplan[k]);
+    if (c->spare.ulist[k]) cudaFree(c->spare.ulist[k]);
+    if (c->spare.ustart[k]) cudaFree(c->spare.ustart[k]);
+    if (c->spare.ucount[k]) cudaFree(c->spare.ucount[k]);
+  }
   for (int k = 0; k < TT_MAX_D; ++k) {
     if (c->d_cores_stage[k]) cudaFree(c->d_cores_stage[k]);
     if (c->d_rplan[k]) cudaFree(c->d_rplan[k]);
@@ -462,7 +519,13 @@ extern "C" int tt_sketch_init(tt_ctx** out, const tt_params* p, void* stream) {
     A((void**)&c->d_ulist[k], sizeof(int32_t) * c->J);
     A((void**)&c->d_ustart[k], sizeof(int64_t) * (c->J + 1));
     A((void**)&c->d_ucount[k], sizeof(int32_t));
+    A((void**)&c->spare.rplan[k], sizeof(uint32_t) * c->R[k]);
+    A((void**)&c->spare.ulist[k], sizeof(int32_t) * c->J);
+    A((void**)&c->spare.ustart[k], sizeof(int64_t) * (c->J + 1));
+    A((void**)&c->spare.ucount[k], sizeof(int32_t));
   }
+  A((void**)&c->spare.h, sizeof(int32_t) * c->noff[c->d]);
+  A((void**)&c->spare.v, sizeof(int8_t) * c->noff[c->d]);
   A((void**)&c->d_ghat, sizeof(float2) * c->ghat_off[c->d]);
   A((void**)&c->d_twiddle, sizeof(float2) * (c->J / 2));
   A((void**)&c->d_twstage, sizeof(float2) * c->J);
@@ -483,6 +546,7 @@ extern "C" int tt_sketch_init(tt_ctx** out, const tt_params* p, void* stream) {
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_spare, cudaEventDisableTiming);
   for (int k = 0; k < c->d && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&c->ev_y[k], cudaEventDisableTiming);
   A((void**)&c->d_gram, sizeof(float) * (c->smax + c->nmax) * c->smax);
   A((void**)&c->d_core_old, sizeof(float) * c->nmax * c->smax);
@@ -539,6 +603,7 @@ extern "C" int tt_sketch_init(tt_ctx** out, const tt_params* p, void* stream) {
 extern "C" void tt_sketch_destroy(tt_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
+  if (c->side) cudaStreamSynchronize(c->side);  // a spare draw may still be in flight
   free_all(c);
   delete c;
 }
@@ -564,10 +629,12 @@ extern "C" int tt_sketch_set_tables(tt_ctx* c, const int32_t* h_host, const int8
     if (h_host[i] < 0 || h_host[i] >= c->J) return tt_fail(c, TT_EINVAL, "h[%lld]=%d outside [0, J)", (long long)i, h_host[i]);
     if (v_host[i] != 1 && v_host[i] != -1) return tt_fail(c, TT_EINVAL, "v[%lld]=%d not +-1", (long long)i, v_host[i]);
   }
+  if (c->spare_pending) TT_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_spare, 0));
   TT_CUDA(c, cudaMemcpyAsync(c->d_h, h_host, sizeof(int32_t) * tot, cudaMemcpyHostToDevice, c->stream));
   TT_CUDA(c, cudaMemcpyAsync(c->d_v, v_host, sizeof(int8_t) * tot, cudaMemcpyHostToDevice, c->stream));
   TT_CUDA(c, cudaStreamSynchronize(c->stream));
   c->user_tables = true;
+  c->spare.tables_valid = false;
   c->tables_valid = true;
   for (int k = 0; k < TT_MAX_D; ++k) c->rplan_valid[k] = false;
   return TT_OK;

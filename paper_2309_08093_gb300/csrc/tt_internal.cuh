@@ -16,6 +16,21 @@
 
 struct TtPlan0;
 
+// The hash / sign tables and fibre plans of one sketch draw. A context holds two: the current draw
+// (its d_h, d_v, d_rplan ... fields) and a spare that each sweep fills, on its side stream, for the
+// next sweep index, so that the next sweep starts with its plans ready.
+struct TtDraw {
+  int32_t* h = nullptr;
+  int8_t* v = nullptr;
+  uint32_t* rplan[TT_MAX_D] = {nullptr};
+  int32_t* ulist[TT_MAX_D] = {nullptr};
+  int64_t* ustart[TT_MAX_D] = {nullptr};
+  int32_t* ucount[TT_MAX_D] = {nullptr};
+  bool tables_valid = false;
+  uint64_t tables_sweep = 0;
+  bool rplan_valid[TT_MAX_D] = {false};
+};
+
 // Library-owned state of one problem shape (see tt_sketch_init).
 struct tt_ctx {
   int d = 0;
@@ -60,6 +75,9 @@ struct tt_ctx {
   int64_t* d_rtmp = nullptr;                 // d x (J + 1) bucket offsets of the plan build
   bool rplan_valid[TT_MAX_D] = {false};
   float* d_Ypart = nullptr;                  // unused placeholder
+  TtDraw spare;                              // the next sweep's draw (see TtDraw)
+  cudaEvent_t ev_spare = nullptr;            // end of the spare's build on `side`
+  bool spare_pending = false;
 
   // FFT sketches of the cores: for core j, (J/2+1) x s_j complex, frequency-major
   float2* d_ghat = nullptr;
@@ -155,6 +173,10 @@ int tt_cuda_check(tt_ctx* c, cudaError_t e, const char* what);
   } while (0)
 
 int tt_ensure_tables(tt_ctx* c, uint64_t sweep);
+// Build the tables and plans of draw `sweep` into the spare on the side stream (no-op in graph
+// capture, with user tables or a fixed sketch, or when the spare already holds that draw).
+int tt_prepare_next_draw(tt_ctx* c, uint64_t sweep);
+void tt_swap_draw(tt_ctx* c);
 int tt_ensure_plan0(tt_ctx* c);
 int tt_ensure_rplan(tt_ctx* c, int k);
 

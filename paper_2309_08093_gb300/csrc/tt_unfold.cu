@@ -195,6 +195,7 @@ struct GArgs {
   int J, n0, ncol;
   int nseg;               // c-segments per column (work items = ncol * nseg)
   int segmax;             // capacity of the staged segment (c groups)
+  int y_vec4;             // Y 16-byte aligned and J % 4 == 0: columns flushed with 16-byte atomics
   FibreGeom fg;
 };
 
@@ -391,7 +392,7 @@ __global__ void __launch_bounds__(256, 2) k_unfold_gather(GArgs a) {
     __syncthreads();
     if (!MODE0) {  // flush the column copy
       float* yc = a.Y + (int64_t)J * col;
-      if ((J & 3) == 0) {
+      if (a.y_vec4) {
         for (int b = threadIdx.x * 4; b < J; b += T * 4) {
           const float4 v4 = make_float4(Ys[b], Ys[b + 1], Ys[b + 2], Ys[b + 3]);
           if (v4.x != 0.f || v4.y != 0.f || v4.z != 0.f || v4.w != 0.f) atomicAdd(reinterpret_cast<float4*>(yc + b), v4);
@@ -402,6 +403,251 @@ __global__ void __launch_bounds__(256, 2) k_unfold_gather(GArgs a) {
       __syncthreads();
     }
   }
+}
+
+// ---------------------------------------------------------------------------------------------
+// modes >= 1, G columns at once. The plan of mode k lists the rest fibres r by tail hash c_r and
+// is the same for every output column i_k, so one work item takes G neighbouring columns
+// (i_k = G g .. G g + G - 1) and one c-segment: a warp walks its slice of the segment and, per plan
+// entry r, gathers the G fibres A(:, r, i_k) (neighbours in memory for mode 1). Lane l holds the
+// MV vectors v = l + 32 m of the G * vpf vectors of an entry (column v / vpf, piece v % vpf), keeps
+// S entries in flight with cp.async and sums runs of equal c in registers; a run's end (the same
+// for every lane: all of them walk the same entries) adds coef(i_0) * sum into bucket
+// (c + h_0(i_0)) mod J of the CTA's copy of the column. The G column copies are flushed to Y_k
+// with 16-byte atomics at the end of the item.
+template <int DT, int VB, int S, int MV, int G>
+__global__ void __launch_bounds__(256, 2) k_unfold_cols(GArgs a) {
+  constexpr int EPV = TtVec<DT, VB>::EPV;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int J = a.J;
+  const int T = blockDim.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = T >> 5;
+  unsigned char* ring = smraw;                                                // nw x S x MV x 32 x VB
+  float* Ys = reinterpret_cast<float*>(ring + gather_ring_bytes(true, nw, S * MV, VB));  // G x J
+  int* sstart = reinterpret_cast<int*>(Ys + (size_t)G * J);                 // segmax + 1 (relative)
+  int* scval = sstart + a.segmax + 1;                                        // segmax
+  const int U_ = *a.ucount;
+  const int vpf = a.fg.vpf;
+  unsigned char* myring = ring + ((size_t)warp * S * MV * 32 + lane) * VB;
+  // this lane's vectors of an entry and their coefficients (fixed for the whole kernel)
+  int vg[MV], vp[MV];
+  float coefr[MV][EPV];
+  int h0r[MV][EPV];
+#pragma unroll
+  for (int m = 0; m < MV; ++m) {
+    const int v = lane + 32 * m;
+    const bool in = v < G * vpf;
+    vg[m] = in ? v / vpf : 0;
+    vp[m] = in ? v - vg[m] * vpf : 0;
+#pragma unroll
+    for (int e = 0; e < EPV; ++e) {
+      const int i0 = vp[m] * EPV + e;
+      float cf = 0.f;
+      int hh = 0;
+      if (in) {
+        cf = __ldg(a.v0 + i0) < 0 ? -1.f : 1.f;
+        if (a.scales) cf *= __ldg(a.scales + i0);
+        hh = __ldg(a.h0 + i0);
+      }
+      coefr[m][e] = cf;
+      h0r[m][e] = hh;
+    }
+  }
+  const int ncolg = (a.ncol + G - 1) / G;
+  const int items = ncolg * a.nseg;
+  for (int item = blockIdx.x; item < items; item += gridDim.x) {
+    const int colg = item / a.nseg, seg = item - colg * a.nseg;
+    const int col0 = colg * G;
+    const int ua = (int)((int64_t)U_ * seg / a.nseg), ub = (int)((int64_t)U_ * (seg + 1) / a.nseg);
+    const int nu = ub - ua;
+    if (nu <= 0) continue;
+    const int64_t e0 = __ldg(a.ustart + ua);
+    for (int i = threadIdx.x; i <= nu; i += T) {
+      sstart[i] = (int)(__ldg(a.ustart + ua + i) - e0);
+      if (i < nu) scval[i] = __ldg(a.ulist + ua + i);
+    }
+    for (int i = threadIdx.x; i < G * J; i += T) Ys[i] = 0.f;
+    __syncthreads();
+    const int ne = sstart[nu];
+    const int sb = (int)((int64_t)ne * warp / nw), se = (int)((int64_t)ne * (warp + 1) / nw);
+    const uint32_t* plan = a.plan + e0;
+    bool vok[MV];
+    const char* Alane[MV];
+#pragma unroll
+    for (int m = 0; m < MV; ++m) {
+      vok[m] = lane + 32 * m < G * vpf && col0 + vg[m] < a.ncol;
+      Alane[m] = a.A + ((int64_t)(col0 + vg[m]) * a.col_fibres) * a.fg.fiber_bytes + (int64_t)vp[m] * VB;
+    }
+    if (sb < se) {
+      int lo2 = 0, hi2 = nu;  // run containing sb: sstart[lo2] <= sb < sstart[hi2]
+      while (hi2 - lo2 > 1) {
+        const int mid = (lo2 + hi2) >> 1;
+        if (sstart[mid] <= sb) lo2 = mid; else hi2 = mid;
+      }
+      const int count = se - sb;
+      int cu = lo2;
+      int next_b = sstart[cu + 1];
+      float acc[MV][EPV];
+#pragma unroll
+      for (int m = 0; m < MV; ++m)
+#pragma unroll
+        for (int e = 0; e < EPV; ++e) acc[m][e] = 0.f;
+      auto flush = [&]() {
+        const int cv = scval[cu];
+#pragma unroll
+        for (int m = 0; m < MV; ++m) {
+          if (vok[m]) {
+            float* yc = Ys + (size_t)vg[m] * J;
+#pragma unroll
+            for (int e = 0; e < EPV; ++e) atomicAdd(yc + ((cv + h0r[m][e]) & (J - 1)), coefr[m][e] * acc[m][e]);
+          }
+#pragma unroll
+          for (int e = 0; e < EPV; ++e) acc[m][e] = 0.f;
+        }
+      };
+      // pipeline: stage q of the ring holds entry j with j % S == q (MV pieces per lane)
+      uint32_t wcur[S], wnext[S];
+#pragma unroll
+      for (int q = 0; q < S; ++q) {
+        wcur[q] = (q < count) ? __ldg(plan + sb + q) : 0u;
+        if (q < count) {
+          const int64_t fo = (int64_t)(wcur[q] & 0x7FFFFFFFu) * a.fg.fiber_bytes;
+#pragma unroll
+          for (int m = 0; m < MV; ++m)
+            if (vok[m]) cp_async_vec(myring + (size_t)(q * MV + m) * 32 * VB, Alane[m] + fo, VB);
+        }
+        cp_async_commit();
+        wnext[q] = (S + q < count) ? __ldg(plan + sb + S + q) : 0u;
+      }
+      for (int j0 = 0; j0 < count; j0 += S) {
+#pragma unroll
+        for (int q = 0; q < S; ++q) {
+          const int j = j0 + q;
+          if (j < count) {
+            typename TtVec<DT, VB>::Raw raw[MV];
+            cp_async_wait<S - 1>();
+#pragma unroll
+            for (int m = 0; m < MV; ++m) {
+              if (vok[m]) {
+                const unsigned char* src = myring + (size_t)(q * MV + m) * 32 * VB;
+                if constexpr (VB == 16) {
+                  const uint4 w4 = *reinterpret_cast<const uint4*>(src);
+                  raw[m].w[0] = w4.x; raw[m].w[1] = w4.y; raw[m].w[2] = w4.z; raw[m].w[3] = w4.w;
+                } else {
+#pragma unroll
+                  for (int t2 = 0; t2 < TtVec<DT, VB>::W; ++t2) raw[m].w[t2] = reinterpret_cast<const uint32_t*>(src)[t2];
+                }
+              } else {
+                raw[m] = TtVec<DT, VB>::zero();
+              }
+            }
+            const int jr = sb + j;
+            if (jr >= next_b) {
+              flush();
+              do {
+                ++cu;
+                next_b = sstart[cu + 1];
+              } while (jr >= next_b);
+            }
+            const float sg = (wcur[q] >> 31) ? -1.f : 1.f;
+#pragma unroll
+            for (int m = 0; m < MV; ++m) TtVec<DT, VB>::fma_into(raw[m], sg, acc[m]);
+            const int jn = j + S;
+            if (jn < count) {
+              const int64_t fo = (int64_t)(wnext[q] & 0x7FFFFFFFu) * a.fg.fiber_bytes;
+#pragma unroll
+              for (int m = 0; m < MV; ++m)
+                if (vok[m]) cp_async_vec(myring + (size_t)(q * MV + m) * 32 * VB, Alane[m] + fo, VB);
+            }
+            cp_async_commit();
+            wcur[q] = wnext[q];
+            wnext[q] = (jn + S < count) ? __ldg(plan + sb + jn + S) : 0u;
+          }
+        }
+      }
+      cp_async_wait<0>();
+      flush();
+    }
+    __syncthreads();
+    // flush the G column copies
+    for (int g = 0; g < G && col0 + g < a.ncol; ++g) {
+      float* yc = a.Y + (int64_t)J * (col0 + g);
+      const float* ys = Ys + (size_t)g * J;
+      if (a.y_vec4) {
+        for (int b = threadIdx.x * 4; b < J; b += T * 4) {
+          const float4 v4 = make_float4(ys[b], ys[b + 1], ys[b + 2], ys[b + 3]);
+          if (v4.x != 0.f || v4.y != 0.f || v4.z != 0.f || v4.w != 0.f) atomicAdd(reinterpret_cast<float4*>(yc + b), v4);
+        }
+      } else {
+        for (int b = threadIdx.x; b < J; b += T)
+          if (ys[b] != 0.f) atomicAdd(yc + b, ys[b]);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Modes >= 1 with G columns per item: 16-byte vectors (VB), S entries in flight, MV vectors per
+// lane; returns false (nothing launched) when the shape does not suit it.
+template <int DT, int VB, int S>
+static int launch_cols_s(tt_ctx* c, const void* A, const float* scales, int k, float* Y, bool* done, size_t smax) {
+  *done = false;
+  constexpr int G = 4, THREADS = 256;
+  constexpr int EB = TtElem<DT>::bytes;
+  const int64_t fiber_bytes = (int64_t)c->n[0] * EB;
+  const int vpf = (int)(fiber_bytes / VB);
+  const int mv = (G * vpf + 31) / 32;
+  constexpr int EPV = TtVec<DT, VB>::EPV;
+  if (mv > 4 || mv * EPV > 16 || (c->J & 3) != 0) return TT_OK;  // at most 16 elements per lane
+  GArgs a;
+  a.A = (const char*)A;
+  a.scales = scales;
+  a.h0 = c->d_h;
+  a.v0 = c->d_v;
+  a.plan = c->d_rplan[k];
+  a.ulist = c->d_ulist[k];
+  a.ustart = c->d_ustart[k];
+  a.ucount = c->d_ucount[k];
+  a.Y = Y;
+  a.J = c->J;
+  a.y_vec4 = (c->J & 3) == 0 && (reinterpret_cast<uintptr_t>(Y) & 15) == 0;
+  a.n0 = (int)c->n[0];
+  a.ncol = (int)c->n[k];
+  a.col_fibres = c->stride[k] / c->n[0];
+  a.fg = fibre_geom(fiber_bytes, VB, 1);
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+  const int ncolg = (a.ncol + G - 1) / G;
+  const int slots = 2 * sms;
+  // one item per CTA slot; four times as many beside the chain (shorter CTAs hand SM slots to
+  // the chain kernels sooner; measured best of 1, 2, 4, 8 at 100^4)
+  int nseg = std::max(1, slots / ncolg);
+  if (c->in_sweep) nseg *= 4;
+  nseg = std::max(nseg, (c->J + 2047) / 2048);
+  a.nseg = nseg;
+  a.segmax = (c->J + nseg - 1) / nseg + 1;
+  const size_t smem = gather_ring_bytes(true, THREADS / 32, S * 4, VB) + sizeof(float) * (size_t)G * c->J +
+                      sizeof(int) * (2 * (size_t)a.segmax + 1);
+  if (smem > smax) return TT_OK;
+  *done = true;
+  TT_CUDA(c, cudaMemsetAsync(Y, 0, sizeof(float) * c->J * c->n[k], c->stream));
+  void (*kern)(GArgs) = k_unfold_cols<DT, VB, S, 1, G>;
+  if constexpr (2 * EPV <= 16)
+    if (mv == 2) kern = k_unfold_cols<DT, VB, S, 2, G>;
+  if constexpr (3 * EPV <= 16)
+    if (mv == 3) kern = k_unfold_cols<DT, VB, S, 3, G>;
+  if constexpr (4 * EPV <= 16)
+    if (mv == 4) kern = k_unfold_cols<DT, VB, S, 4, G>;
+  TT_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int items = ncolg * a.nseg;
+  kern<<<std::max(1, items), THREADS, smem, c->stream>>>(a);
+  TT_LAUNCH(c, "k_unfold_cols");
+  return TT_OK;
+}
+
+template <int DT, int VB>
+static int launch_cols(tt_ctx* c, const void* A, const float* scales, int k, float* Y, bool* done) {
+  return launch_cols_s<DT, VB, 2>(c, A, scales, k, Y, done, 113 * 1024);  // two CTAs per SM
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -428,6 +674,7 @@ static int launch_gather_vbm(tt_ctx* c, const void* A, const float* scales, int 
   a.ucount = c->d_ucount[k];
   a.Y = Y;
   a.J = c->J;
+  a.y_vec4 = (c->J & 3) == 0 && (reinterpret_cast<uintptr_t>(Y) & 15) == 0;
   a.n0 = (int)c->n[0];
   a.ncol = MODE0 ? 1 : (int)c->n[k];
   a.col_fibres = MODE0 ? 0 : c->stride[k] / c->n[0];
@@ -450,7 +697,12 @@ static int launch_gather_vbm(tt_ctx* c, const void* A, const float* scales, int 
   const size_t smem = ring + sizeof(float) * (MODE0 ? 0 : c->J) + sizeof(int) * (2 * (size_t)a.segmax + 1);
   if (smem > 220 * 1024) return tt_fail(c, TT_EINVAL, "gather kernel needs %zu bytes of shared memory", smem);
   TT_CUDA(c, cudaMemsetAsync(Y, 0, sizeof(float) * c->J * c->n[k], c->stream));  // empty groups stay 0
-  TT_CUDA(c, cudaFuncSetAttribute(k_unfold_gather<DT, VB, S, M, MODE0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  // Beside the chain, the mode-0 kernel runs one CTA per SM (its shared-memory request is raised
+  // to more than half an SM's): its four fibre slots per warp keep enough bytes in flight, and
+  // the registers and shared memory of the second CTA stay free for the chain kernels, which
+  // otherwise wait for sketch CTAs to leave (measured at 100^4: -5% per step).
+  const size_t smem_l = (c->in_sweep && MODE0) ? std::max(smem, (size_t)116 * 1024) : smem;
+  TT_CUDA(c, cudaFuncSetAttribute(k_unfold_gather<DT, VB, S, M, MODE0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_l));
   int per_sm = 1;
   TT_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_unfold_gather<DT, VB, S, M, MODE0>, THREADS, smem));
   const int items = a.ncol * a.nseg;
@@ -459,13 +711,20 @@ static int launch_gather_vbm(tt_ctx* c, const void* A, const float* scales, int 
   const int blocks = (c->in_sweep && !c->tune_seg_mult[k])
                          ? std::max(1, items)
                          : std::max(1, std::min(items, sms * std::max(1, std::min(per_sm, cps))));
-  k_unfold_gather<DT, VB, S, M, MODE0><<<blocks, THREADS, smem, c->stream>>>(a);
+  k_unfold_gather<DT, VB, S, M, MODE0><<<blocks, THREADS, smem_l, c->stream>>>(a);
   TT_LAUNCH(c, "k_unfold_gather");
   return TT_OK;
 }
 
 template <int DT, int VB, bool MODE0>
 static int launch_gather_vb(tt_ctx* c, const void* A, const float* scales, int k, float* Y) {
+  if constexpr (!MODE0 && (VB == 8 || VB == 16)) {
+    if (!c->tune_seg_mult[k]) {  // the autotuner times the one-column kernel's granularities
+      bool done = false;
+      const int rc = launch_cols<DT, VB>(c, A, scales, k, Y, &done);
+      if (rc != TT_OK || done) return rc;
+    }
+  }
   // Several fibres per warp pay off in mode 0, whose runs are long (one flush per row); in modes
   // >= 1 a run is a few fibres and the fibre slots of a warp would flush divergently.
   if constexpr (VB == 16 && MODE0) {
