@@ -26,6 +26,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "ALS sweeps/s + unfold-sketch HBM GB/s at equal rel. error vs plain FP32 GPU"
+# DRAM bytes (read + write) per data-sketch launch from an ncu capture of the current kernels,
+# per (workload, storage); the roofline reports null for anything not captured.
+UNFOLD_TRAFFIC = {("order4-100-r10", "f32"): 429.5e6}
 UNIT = "sweeps/s"
 DEFAULT_WORKLOAD = "order4-100-r10"
 
@@ -623,7 +626,7 @@ def main():
     iso_ms = prof_iso["unfold_ms"] / max(1, prof_iso["unfold_launches"])
     iso_bytes = prof_iso["unfold_bytes"] / max(1, prof_iso["unfold_launches"])
     iso_ach = iso_bytes / (iso_ms * 1e-3) / 1e9
-    iso = {"kernel": "k_unfold_gather alone (tt_sketch_unfold, all modes, 10 draws, after the timed region)",
+    iso = {"kernel": "data sketch kernels alone (tt_sketch_unfold, all modes, 10 draws, after the timed region)",
            "bound": "hbm", "achieved": iso_ach, "peak": hbm, "unit": "GB/s", "frac": iso_ach / hbm,
            "avg_launch_ms": iso_ms, "bytes_per_launch": iso_bytes,
            "per_mode_gbs": [(iso_bytes / (m / n * 1e-3) / 1e9) if n else None
@@ -635,9 +638,14 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": storage, "data": "synthetic",
                 "config": workload_config(w, storage),
                 "rel_error_after": err,
-                "roofline": {"kernel": "unfold sketch (k_unfold_mode0 + k_unfold_col)", "bound": "hbm",
+                "roofline": {"kernel": "data sketch (k_unfold_gather mode 0 + k_unfold_cols modes >= 1)",
+                             "bound": "hbm",
                              "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                             "peak_kind": peak_kind, "traffic": None,
+                             "peak_kind": peak_kind,
+                             "traffic": UNFOLD_TRAFFIC.get((args.workload, storage)),
+                             "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum per launch, mean over the "
+                                             "four modes of one sweep (in-sweep launch shapes), from one ncu capture of "
+                                             "these kernel versions; null for workloads not captured",
                              "bytes_per_launch": bytes_per_launch, "avg_launch_ms": unfold_avg_ms,
                              "per_mode_gbs": mode_gbs,
                              "share_of_step": prof["unfold_ms"] / ms,
