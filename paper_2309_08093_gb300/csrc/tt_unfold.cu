@@ -149,7 +149,7 @@ static FibreGeom fibre_geom(int64_t fiber_bytes, int VB, int M) {
   return g;
 }
 
-// vectors per lane for a fibre of vpf 16-byte vectors: the most fibre slots per warp (fewest warp
+// vectors per lane for a fibre of vpf VB-byte vectors: the most fibre slots per warp (fewest warp
 // instructions per fibre), ties to the smaller m; at most 16 elements per lane (registers)
 static int pick_m(int vpf, int epv) {
   int best = 1, best_fpi = 0;
@@ -697,11 +697,13 @@ static int launch_gather_vbm(tt_ctx* c, const void* A, const float* scales, int 
   const size_t smem = ring + sizeof(float) * (MODE0 ? 0 : c->J) + sizeof(int) * (2 * (size_t)a.segmax + 1);
   if (smem > 220 * 1024) return tt_fail(c, TT_EINVAL, "gather kernel needs %zu bytes of shared memory", smem);
   TT_CUDA(c, cudaMemsetAsync(Y, 0, sizeof(float) * c->J * c->n[k], c->stream));  // empty groups stay 0
-  // Beside the chain, the mode-0 kernel runs one CTA per SM (its shared-memory request is raised
-  // to more than half an SM's): its four fibre slots per warp keep enough bytes in flight, and
-  // the registers and shared memory of the second CTA stay free for the chain kernels, which
-  // otherwise wait for sketch CTAs to leave (measured at 100^4: -5% per step).
-  const size_t smem_l = (c->in_sweep && MODE0) ? std::max(smem, (size_t)116 * 1024) : smem;
+  // Beside the chain of a single-tensor sweep, the mode-0 kernel with packed fibres (four or more
+  // slots per warp) runs one CTA per SM (its shared-memory request is raised to more than half an
+  // SM's): the packed slots keep enough bytes in flight, and the registers and shared memory of
+  // the second CTA stay free for the chain kernels, which otherwise wait for sketch CTAs to leave
+  // (measured at 100^4: -5% per step). Not in graph capture, where other tensors share the SMs.
+  const bool one_cta = c->in_sweep && !c->capture_mode && MODE0 && a.fg.fpi >= 4;
+  const size_t smem_l = one_cta ? std::max(smem, (size_t)116 * 1024) : smem;
   TT_CUDA(c, cudaFuncSetAttribute(k_unfold_gather<DT, VB, S, M, MODE0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_l));
   int per_sm = 1;
   TT_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_unfold_gather<DT, VB, S, M, MODE0>, THREADS, smem));
@@ -727,12 +729,14 @@ static int launch_gather_vb(tt_ctx* c, const void* A, const float* scales, int k
   }
   // Several fibres per warp pay off in mode 0, whose runs are long (one flush per row); in modes
   // >= 1 a run is a few fibres and the fibre slots of a warp would flush divergently.
-  if constexpr (VB == 16 && MODE0) {
-    switch (pick_m((int)(c->n[0] * TtElem<DT>::bytes / 16), TtVec<DT, 16>::EPV)) {
-      case 4: return launch_gather_vbm<DT, 16, 4, MODE0>(c, A, scales, k, Y);
-      case 2: return launch_gather_vbm<DT, 16, 2, MODE0>(c, A, scales, k, Y);
-      default: return launch_gather_vbm<DT, 16, 1, MODE0>(c, A, scales, k, Y);
-    }
+  if constexpr ((VB == 16 || VB == 8) && MODE0) {
+    constexpr int EPV = TtVec<DT, VB>::EPV;  // pick_m keeps M * EPV <= 16: only those are compiled
+    const int m = pick_m((int)(c->n[0] * TtElem<DT>::bytes / VB), EPV);
+    if constexpr (4 * EPV <= 16)
+      if (m == 4) return launch_gather_vbm<DT, VB, 4, MODE0>(c, A, scales, k, Y);
+    if constexpr (2 * EPV <= 16)
+      if (m == 2) return launch_gather_vbm<DT, VB, 2, MODE0>(c, A, scales, k, Y);
+    return launch_gather_vbm<DT, VB, 1, MODE0>(c, A, scales, k, Y);
   } else {
     return launch_gather_vbm<DT, VB, 1, MODE0>(c, A, scales, k, Y);
   }
