@@ -9,6 +9,18 @@
 
 #include "../../include/tt_sketch.h"
 
+// Two FP32 FMAs in one instruction (fma.rn.f32x2, sm_100 and later): d.x = a.x * b.x + c.x and
+// d.y = a.y * b.y + c.y, each rounded once to nearest, i.e. exactly what two fmaf calls give.
+__device__ __forceinline__ float2 tt_ffma2(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+      "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+
 #define TT_MAX_D 8
 #define TT_MAX_S 160      // largest r[k]*r[k+1] handled by the dense solve kernels
 #define TT_MAX_J 16384

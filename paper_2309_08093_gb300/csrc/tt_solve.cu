@@ -93,11 +93,15 @@ __global__ void __launch_bounds__(256) k_gram(GramArgs a) {
     for (int kk = 0; kk < 16; ++kk) {
       const float4 xv = *reinterpret_cast<const float4*>(&Xs[kk][ty * 4]);
       const float4 bv = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
-      const float xa[4] = {xv.x, xv.y, xv.z, xv.w}, ba[4] = {bv.x, bv.y, bv.z, bv.w};
+      const float xa[4] = {xv.x, xv.y, xv.z, xv.w};
+      const float2 blo = make_float2(bv.x, bv.y), bhi = make_float2(bv.z, bv.w);
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(xa[i], ba[j], acc[i][j]);
+      for (int i = 0; i < 4; ++i) {  // pairs of outputs per fma.rn.f32x2
+        const float2 x2 = make_float2(xa[i], xa[i]);
+        const float2 lo = tt_ffma2(x2, blo, make_float2(acc[i][0], acc[i][1]));
+        const float2 hi = tt_ffma2(x2, bhi, make_float2(acc[i][2], acc[i][3]));
+        acc[i][0] = lo.x, acc[i][1] = lo.y, acc[i][2] = hi.x, acc[i][3] = hi.y;
+      }
     }
     __syncthreads();
   }
@@ -186,11 +190,25 @@ __device__ __forceinline__ void gj_groups(float (&w)[RA][CB], int s, float (*row
       for (int ra = 0; ra < RA; ++ra) f[ra] = __shfl_sync(0xffffffffu, w[ra][CN], jl);
       if (ty == jj) f[G] = 0.f;  // row j itself (already normalised) is left alone
 #pragma unroll
-      for (int cb = CN; cb < CB; ++cb) rv[cb] = rowbuf[bs][tx + 32 * cb];
+      for (int cb = CN & ~1; cb < CB; ++cb) rv[cb] = rowbuf[bs][tx + 32 * cb];
+      // pairs of column blocks per fma.rn.f32x2 (a dead block left of CN may be updated too: it
+      // is never read again)
+      constexpr int CP = CN & ~1;
 #pragma unroll
-      for (int cb = CN; cb < CB; ++cb)
+      for (int cb = CP; cb < CB; cb += 2) {
+        if (cb + 1 < CB) {
 #pragma unroll
-        for (int ra = 0; ra < RA; ++ra) w[ra][cb] = fmaf(-f[ra], rv[cb], w[ra][cb]);
+          for (int ra = 0; ra < RA; ++ra) {
+            const float2 d = tt_ffma2(make_float2(-f[ra], -f[ra]), make_float2(rv[cb], rv[cb + 1]),
+                                      make_float2(w[ra][cb], w[ra][cb + 1]));
+            w[ra][cb] = d.x;
+            w[ra][cb + 1] = d.y;
+          }
+        } else {
+#pragma unroll
+          for (int ra = 0; ra < RA; ++ra) w[ra][cb] = fmaf(-f[ra], rv[cb], w[ra][cb]);
+        }
+      }
       const int jn = j0 + jj + 1;
       if (jn < s) {
         if (jj + 1 < TY)
@@ -1518,11 +1536,13 @@ __global__ void __launch_bounds__(256, 2) k_rel_error_stream(const void* __restr
     float fe = 0.f, fa = 0.f;
     if (active) {
       // fibres innermost: every G_0 float4 read from shared memory serves REL_U fibres
-      float x[REL_U][4], r4[REL_U][4];
+      // the reconstruction in pairs of entries: one fma.rn.f32x2 per two FMAs
+      float x[REL_U][4];
+      float2 r2[REL_U][2];
 #pragma unroll
       for (int u = 0; u < REL_U; ++u) {
         smem_load4<DT>(tA + ((size_t)(pi + P * u) * n0 + 4 * qi) * ES, x[u]);
-        r4[u][0] = r4[u][1] = r4[u][2] = r4[u][3] = 0.f;
+        r2[u][0] = r2[u][1] = make_float2(0.f, 0.f);
       }
       for (int al0 = 0; al0 < r1p; al0 += 4) {
         float4 w[REL_U];
@@ -1531,27 +1551,30 @@ __global__ void __launch_bounds__(256, 2) k_rel_error_stream(const void* __restr
 #pragma unroll
         for (int aa = 0; aa < 4; ++aa) {
           const float4 g4 = *reinterpret_cast<const float4*>(G0 + (al0 + aa) * n0 + 4 * qi);
+          const float2 glo = make_float2(g4.x, g4.y), ghi = make_float2(g4.z, g4.w);
 #pragma unroll
           for (int u = 0; u < REL_U; ++u) {
             const float ww = aa == 0 ? w[u].x : aa == 1 ? w[u].y : aa == 2 ? w[u].z : w[u].w;
-            r4[u][0] = fmaf(g4.x, ww, r4[u][0]);
-            r4[u][1] = fmaf(g4.y, ww, r4[u][1]);
-            r4[u][2] = fmaf(g4.z, ww, r4[u][2]);
-            r4[u][3] = fmaf(g4.w, ww, r4[u][3]);
+            const float2 w2 = make_float2(ww, ww);
+            r2[u][0] = tt_ffma2(glo, w2, r2[u][0]);
+            r2[u][1] = tt_ffma2(ghi, w2, r2[u][1]);
           }
         }
       }
+      float2 fe2 = make_float2(0.f, 0.f), fa2 = make_float2(0.f, 0.f);
 #pragma unroll
       for (int u = 0; u < REL_U; ++u) {
         if (f0 + pi + P * u >= M0) continue;  // past the last fibre (stale buffer entries)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const float xv = x[u][c] * sc[c];
-          const float dl = xv - r4[u][c];
-          fe = fmaf(dl, dl, fe);
-          fa = fmaf(xv, xv, fa);
+        for (int h = 0; h < 2; ++h) {
+          const float2 xv = make_float2(x[u][2 * h] * sc[2 * h], x[u][2 * h + 1] * sc[2 * h + 1]);
+          const float2 dl = make_float2(xv.x - r2[u][h].x, xv.y - r2[u][h].y);
+          fe2 = tt_ffma2(dl, dl, fe2);
+          fa2 = tt_ffma2(xv, xv, fa2);
         }
       }
+      fe = fe2.x + fe2.y;
+      fa = fa2.x + fa2.y;
     }
     e2 += fe;
     x2 += fa;

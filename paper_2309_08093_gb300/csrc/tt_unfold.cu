@@ -102,7 +102,15 @@ struct TtVec {
   // acc[e] += s * element e
   __device__ static void fma_into(const Raw& r, float s, float* acc) {
     const uint32_t* w = r.w;
-    if constexpr (DT == TT_F32) {
+    if constexpr (DT == TT_F32 && EPV % 2 == 0) {  // pairs of entries: one fma.rn.f32x2 each
+#pragma unroll
+      for (int e = 0; e < EPV; e += 2) {
+        const float2 d = tt_ffma2(make_float2(s, s), make_float2(__uint_as_float(w[e]), __uint_as_float(w[e + 1])),
+                                  make_float2(acc[e], acc[e + 1]));
+        acc[e] = d.x;
+        acc[e + 1] = d.y;
+      }
+    } else if constexpr (DT == TT_F32) {
 #pragma unroll
       for (int e = 0; e < EPV; ++e) acc[e] = fmaf(s, __uint_as_float(w[e]), acc[e]);
     } else if constexpr (DT == TT_F64) {
@@ -111,10 +119,15 @@ struct TtVec {
         unsigned long long b = ((unsigned long long)w[2 * e + 1] << 32) | w[2 * e];
         acc[e] = fmaf(s, (float)__longlong_as_double((long long)b), acc[e]);
       }
-    } else if constexpr (DT == TT_BF16) {
+    } else if constexpr (DT == TT_BF16) {  // a 32-bit word holds two entries: one fma.rn.f32x2
 #pragma unroll
-      for (int e = 0; e < EPV; ++e)
-        acc[e] = fmaf(s, __uint_as_float(((w[e >> 1] >> (16 * (e & 1))) & 0xFFFFu) << 16), acc[e]);
+      for (int e = 0; e < EPV; e += 2) {
+        const uint32_t ww = w[e >> 1];
+        const float2 d = tt_ffma2(make_float2(s, s), make_float2(__uint_as_float(ww << 16), __uint_as_float(ww & 0xFFFF0000u)),
+                                  make_float2(acc[e], acc[e + 1]));
+        acc[e] = d.x;
+        acc[e + 1] = d.y;
+      }
     } else {
 #pragma unroll
       for (int e = 0; e < EPV; ++e) acc[e] = fmaf(s, tt_fp8_e4m3((w[e >> 2] >> (8 * (e & 3))) & 0xFFu), acc[e]);
