@@ -672,9 +672,10 @@ static int pick_vb(int64_t fiber_bytes, uintptr_t base, int elem_bytes) {
   return elem_bytes;
 }
 
-template <int DT, int VB, int M, bool MODE0>
+// S fibres in flight per slot (S * M pieces of VB bytes per lane); ONE_CTA: the in-sweep mode-0
+// shape that runs one CTA per SM beside the chain
+template <int DT, int VB, int M, bool MODE0, int S = 12 / M, bool ONE_CTA = false>
 static int launch_gather_vbm(tt_ctx* c, const void* A, const float* scales, int k, float* Y) {
-  constexpr int S = 12 / M;  // fibres in flight per lane: S * M pieces of VB bytes
   constexpr int THREADS = 256;
   GArgs a;
   a.A = (const char*)A;
@@ -710,13 +711,13 @@ static int launch_gather_vbm(tt_ctx* c, const void* A, const float* scales, int 
   const size_t smem = ring + sizeof(float) * (MODE0 ? 0 : c->J) + sizeof(int) * (2 * (size_t)a.segmax + 1);
   if (smem > 220 * 1024) return tt_fail(c, TT_EINVAL, "gather kernel needs %zu bytes of shared memory", smem);
   TT_CUDA(c, cudaMemsetAsync(Y, 0, sizeof(float) * c->J * c->n[k], c->stream));  // empty groups stay 0
-  // Beside the chain of a single-tensor sweep, the mode-0 kernel with packed fibres (four or more
-  // slots per warp) runs one CTA per SM (its shared-memory request is raised to more than half an
-  // SM's): the packed slots keep enough bytes in flight, and the registers and shared memory of
-  // the second CTA stay free for the chain kernels, which otherwise wait for sketch CTAs to leave
-  // (measured at 100^4: -5% per step). Not in graph capture, where other tensors share the SMs.
-  const bool one_cta = c->in_sweep && !c->capture_mode && MODE0 && a.fg.fpi >= 4;
-  const size_t smem_l = one_cta ? std::max(smem, (size_t)116 * 1024) : smem;
+  // ONE_CTA: beside the chain of a single-tensor sweep, the mode-0 kernel with packed fibres (four
+  // or more slots per warp) runs one CTA per SM (its shared-memory request is raised to more than
+  // half an SM's): the packed slots keep enough bytes in flight, and the registers and shared
+  // memory of the second CTA stay free for the chain kernels, which otherwise wait for sketch CTAs
+  // to leave (measured at 100^4: -5% per step). Not in graph capture, where other tensors share
+  // the SMs.
+  const size_t smem_l = ONE_CTA ? std::max(smem, (size_t)116 * 1024) : smem;
   TT_CUDA(c, cudaFuncSetAttribute(k_unfold_gather<DT, VB, S, M, MODE0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_l));
   int per_sm = 1;
   TT_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_unfold_gather<DT, VB, S, M, MODE0>, THREADS, smem));
@@ -745,8 +746,16 @@ static int launch_gather_vb(tt_ctx* c, const void* A, const float* scales, int k
   if constexpr ((VB == 16 || VB == 8) && MODE0) {
     constexpr int EPV = TtVec<DT, VB>::EPV;  // pick_m keeps M * EPV <= 16: only those are compiled
     const int m = pick_m((int)(c->n[0] * TtElem<DT>::bytes / VB), EPV);
-    if constexpr (4 * EPV <= 16)
-      if (m == 4) return launch_gather_vbm<DT, VB, 4, MODE0>(c, A, scales, k, Y);
+    if constexpr (4 * EPV <= 16) {
+      if (m == 4) {
+        const FibreGeom fg = fibre_geom((int64_t)c->n[0] * TtElem<DT>::bytes, VB, 4);
+        // beside the chain of a single-tensor sweep: one CTA per SM with six fibres in flight per
+        // slot instead of three (measured at 100^4: sweep 671 -> 655 us; 4 stages: 661 us)
+        if (c->in_sweep && !c->capture_mode && fg.fpi >= 4)
+          return launch_gather_vbm<DT, VB, 4, MODE0, 6, true>(c, A, scales, k, Y);
+        return launch_gather_vbm<DT, VB, 4, MODE0>(c, A, scales, k, Y);
+      }
+    }
     if constexpr (2 * EPV <= 16)
       if (m == 2) return launch_gather_vbm<DT, VB, 2, MODE0>(c, A, scales, k, Y);
     return launch_gather_vbm<DT, VB, 1, MODE0>(c, A, scales, k, Y);
