@@ -60,8 +60,7 @@ extern "C" int tt_sketch_interface(tt_ctx* c, float* const* cores, int k, uint64
   c->err.clear();
   TT_TRY(tt_ensure_tables(c, sweep));
   TT_TRY(build_all_ghat(c, cores));
-  TT_TRY(tt_launch_suffixes(c));
-  TT_TRY(tt_launch_prefix_reset(c));
+  TT_TRY(tt_launch_suffixes(c));  // also restarts the prefix chain
   for (int j = 0; j < k; ++j) TT_TRY(tt_launch_prefix_step(c, j));
   TT_TRY(tt_launch_interface_from_chain(c, k, SH));
   return TT_OK;
@@ -83,7 +82,7 @@ extern "C" int tt_orthogonalize(tt_ctx* c, float* const* cores, int direction, i
   c->err.clear();
   TT_TRY(tt_reset_status(c));
   if (direction == -1) {
-    for (int kk = c->d - 1; kk >= 1; --kk) TT_TRY(tt_launch_lq_right(c, cores[kk - 1], cores[kk], kk));
+    TT_TRY(tt_launch_lq_sweep(c, cores));
   } else if (direction == 1) {
     if (k < 0 || k >= c->d - 1) return tt_fail(c, TT_EINVAL, "QR step needs 0 <= k < d-1 (k=%d)", k);
     TT_TRY(tt_launch_qr_left(c, cores[k], cores[k + 1], k));
@@ -128,15 +127,17 @@ static int sweep_body(tt_ctx* c, const void* A, const float* scales, float* cons
     }
   }
   auto chain = [&]() -> int {
-    for (int kk = d - 1; kk >= 1; --kk) TT_TRY(tt_launch_lq_right(c, cores[kk - 1], cores[kk], kk));
+    TT_TRY(tt_launch_lq_sweep(c, cores));
     TT_TRY(build_all_ghat(c, cores));
-    TT_TRY(tt_launch_suffixes(c));
-    TT_TRY(tt_launch_prefix_reset(c));
+    TT_TRY(tt_launch_suffixes(c));  // also restarts the prefix chain
     for (int k = 0; k < d; ++k) {
-      TT_TRY(tt_launch_interface_from_chain(c, k, c->d_SH));
+      // the interface kernel also zeroes the Gram accumulators of this core's update
+      const int64_t sk = (int64_t)c->r[k] * c->r[k + 1];
+      TT_TRY(tt_launch_interface_from_chain(c, k, c->d_SH, c->d_gram, (sk + c->n[k]) * sk));
       const float* Yk = fork ? c->d_Yall + c->yoff[k] : Ygiven[k];
       if (fork) TT_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_y[k], 0));
-      TT_TRY(tt_launch_prox_update(c, Yk, c->d_SH, cores[k], k, change_slots ? change_slots + 2 * k : nullptr));
+      TT_TRY(tt_launch_prox_update(c, Yk, c->d_SH, cores[k], k, change_slots ? change_slots + 2 * k : nullptr,
+                                   true));
       if (k < d - 1) {
         TT_TRY(tt_launch_qr_left(c, cores[k], cores[k + 1], k));
         TT_TRY(tt_launch_core_fft(c, cores[k], k));

@@ -8,7 +8,7 @@
 //   k_core_fft2    : CountSketch of two (a, b) fibres of a core into J buckets (real and imaginary
 //                    parts) + radix-4 Stockham FFT, the fibres of several cores in one launch;
 //                    k_core_fft (radix-2, one fibre) for J = 16384
-//   k_suffix_chain : R_{>k}(w) = Ghat_{k+1}(w) ... Ghat_{d-1}(w) for all k   (one thread per w)
+//   k_suffix_chain : R_{>k}(w) = Ghat_{k+1}(w) ... Ghat_{d-1}(w) for all k, and L_{<0} = 1
 //   k_prefix_step  : L_{<j+1}(w) = L_{<j}(w) Ghat_j(w)                      (one thread per w, b)
 //   k_face_ifft2   : two columns c = a + r_k b of S H_k: inverse FFT of L_{<k}(w)[a] R_{>k}(w)[b]
 //                    (k_face_ifft, one column with radix-2, for J = 16384)
@@ -222,6 +222,7 @@ int tt_launch_core_ffts(tt_ctx* c, float* const* cores) { return launch_core_fft
 struct ChainArgs {
   const float2* ghat;
   int64_t ghat_off[TT_MAX_D + 1];
+  float2* prefix;  // L_{<0} = [1] is written here too (the prefix chain restarts with the suffixes)
   float2* suffix;
   int64_t suffix_off[TT_MAX_D + 1];
   int r[TT_MAX_D + 1];
@@ -235,7 +236,10 @@ __global__ void k_suffix_chain(ChainArgs a) {
   const int w = blockIdx.x * 32 + threadIdx.x;
   const bool live = w < a.H;
   const int64_t H = a.H;
-  if (live && threadIdx.y == 0) a.suffix[a.suffix_off[a.d - 1] + w] = make_float2(1.f, 0.f);  // R_{>d-1} = [1]
+  if (live && threadIdx.y == 0) {
+    a.suffix[a.suffix_off[a.d - 1] + w] = make_float2(1.f, 0.f);  // R_{>d-1} = [1]
+    a.prefix[w] = make_float2(1.f, 0.f);                          // L_{<0} = [1]
+  }
   __syncthreads();
   constexpr int U = 8;
   for (int k = a.d - 2; k >= 0; --k) {
@@ -271,24 +275,13 @@ int tt_launch_suffixes(tt_ctx* c) {
     a.r[k] = c->r[k];
   }
   a.suffix = c->d_suffix;
+  a.prefix = c->d_prefix;
   a.d = c->d;
   a.H = c->J / 2 + 1;
   int rmax = 1;
   for (int k = 1; k < c->d; ++k) rmax = std::max(rmax, c->r[k]);
   k_suffix_chain<<<(a.H + 31) / 32, dim3(32, std::min(rmax, 32)), 0, c->stream>>>(a);
   TT_LAUNCH(c, "k_suffix_chain");
-  return TT_OK;
-}
-
-__global__ void k_prefix_reset(float2* L, int H) {
-  int w = blockIdx.x * blockDim.x + threadIdx.x;
-  if (w < H) L[w] = make_float2(1.f, 0.f);
-}
-
-int tt_launch_prefix_reset(tt_ctx* c) {
-  int H = c->J / 2 + 1;
-  k_prefix_reset<<<(H + 127) / 128, 128, 0, c->stream>>>(c->d_prefix, H);
-  TT_LAUNCH(c, "k_prefix_reset");
   return TT_OK;
 }
 
@@ -333,14 +326,22 @@ struct FaceArgs {
   const float2* R;  // rb x H (suffix R_{>k})
   const float2* tw;
   const float2* twst;
+  float* zero;      // zeroed by the grid on the side (the Gram accumulators of the next kernel)
+  int64_t nzero;
   float* SH;        // J x (ra rb), column-major
   int ra, rb, J, logJ;
 };
 
 // Two columns per CTA: their Hermitian spectra X, Y packed as Z = X + i Y; the inverse DFT of Z is
 // x + i y, obtained as conj(FFT(conj Z)) / J.
+__device__ __forceinline__ void face_zero(const FaceArgs& a) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.nzero; i += (int64_t)gridDim.x * blockDim.x)
+    a.zero[i] = 0.f;
+}
+
 __global__ void __launch_bounds__(256) k_face_ifft2(FaceArgs a) {
   extern __shared__ float2 fbuf[];
+  face_zero(a);
   float2* x = fbuf;
   float2* y = fbuf + a.J;
   const int S = a.ra * a.rb;
@@ -386,6 +387,7 @@ __global__ void __launch_bounds__(256) k_face_ifft2(FaceArgs a) {
 
 __global__ void k_face_ifft(FaceArgs a) {
   extern __shared__ float2 buf[];
+  face_zero(a);
   const int col = blockIdx.x;
   const int al = col % a.ra, be = col / a.ra;
   const int H = a.J / 2 + 1;
@@ -403,8 +405,10 @@ __global__ void k_face_ifft(FaceArgs a) {
   for (int t = threadIdx.x; t < a.J; t += blockDim.x) a.SH[(int64_t)col * a.J + t] = buf[t].x * inv;
 }
 
-int tt_launch_interface_from_chain(tt_ctx* c, int k, float* SH) {
+int tt_launch_interface_from_chain(tt_ctx* c, int k, float* SH, float* zero, int64_t nzero) {
   FaceArgs a;
+  a.zero = zero;
+  a.nzero = zero ? nzero : 0;
   a.L = c->d_prefix;
   a.R = c->d_suffix + c->suffix_off[k];
   a.tw = c->d_twiddle;

@@ -197,13 +197,15 @@ int tt_launch_unfold(tt_ctx* c, const void* A, const float* scales, int k, float
 int tt_launch_core_fft(tt_ctx* c, const float* core, int j);
 int tt_launch_core_ffts(tt_ctx* c, float* const* cores);  // all d cores, one launch
 int tt_launch_suffixes(tt_ctx* c);
-int tt_launch_prefix_reset(tt_ctx* c);
 int tt_launch_prefix_step(tt_ctx* c, int j);
-int tt_launch_interface_from_chain(tt_ctx* c, int k, float* SH);
+// S H_k from the prefix and suffix chains; `zero` (nzero floats, optional) is zeroed on the side
+int tt_launch_interface_from_chain(tt_ctx* c, int k, float* SH, float* zero = nullptr, int64_t nzero = 0);
 int tt_launch_prox_update(tt_ctx* c, const float* Y, const float* SH, float* core, int k,
-                          double* change_slot);
+                          double* change_slot,
+                          bool gram_zeroed = false);  // gram_zeroed: d_gram already zero
 int tt_launch_qr_left(tt_ctx* c, float* core_k, float* core_k1, int k);
 int tt_launch_lq_right(tt_ctx* c, float* core_km1, float* core_k, int k);
+int tt_launch_lq_sweep(tt_ctx* c, float* const* cores);  // all right-to-left steps
 int tt_launch_rel_error(tt_ctx* c, const void* A, const float* scales, float* const* cores);
 int tt_read_status(tt_ctx* c);
 int tt_reset_status(tt_ctx* c);

@@ -349,10 +349,10 @@ static cudaError_t launch_prox_solve(SolveArgs a, cudaStream_t st) {
 }
 
 int tt_launch_prox_update(tt_ctx* c, const float* Y, const float* SH, float* core, int k,
-                          double* change_slot) {
+                          double* change_slot, bool gram_zeroed) {
   const int s = c->r[k] * c->r[k + 1];
   const int n = (int)c->n[k];
-  TT_CUDA(c, cudaMemsetAsync(c->d_gram, 0, sizeof(float) * (s + n) * s, c->stream));
+  if (!gram_zeroed) TT_CUDA(c, cudaMemsetAsync(c->d_gram, 0, sizeof(float) * (s + n) * s, c->stream));
   GramArgs g;
   g.SH = SH;
   g.Y = Y;
@@ -954,11 +954,9 @@ __global__ void __launch_bounds__(QR_T, 1) k_qr_left_rows(float* core, float* ne
 // (G_k^R)^T (m = n r1 rows, q = r0 <= Q cols) = Q R; G_k^R <- Q^T; G_{k-1}^L <- G_{k-1}^L R^T.
 // The neighbour G_{k-1} (nrows_prev x r0) is prefetched as in k_qr_left_rows.
 template <int Q>
-__global__ void __launch_bounds__(QR_T, 1) k_lq_right_rows(float* prev, float* core, int r0, int n, int r1,
-                                                       int nrows_prev, int prefetch, const int* status) {
-  extern __shared__ __align__(16) float sm[];
+__device__ void lq_right_body(float* sm, float* prev, float* core, int r0, int n, int r1, int nrows_prev,
+                              int prefetch) {
   constexpr int QP = QrShape<Q>::QP, V = QrShape<Q>::V;
-  if (*status != 0) return;
   const int m = n * r1, q = r0, t = threadIdx.x;
   const int64_t nx = prefetch ? (int64_t)nrows_prev * r0 : 0;
   float* As = sm;
@@ -1030,6 +1028,60 @@ __global__ void __launch_bounds__(QR_T, 1) k_lq_right_rows(float* prev, float* c
   }
 }
 
+template <int Q>
+__global__ void __launch_bounds__(QR_T, 1) k_lq_right_rows(float* prev, float* core, int r0, int n, int r1,
+                                                       int nrows_prev, int prefetch, const int* status) {
+  extern __shared__ __align__(16) float sm[];
+  if (*status != 0) return;
+  lq_right_body<Q>(sm, prev, core, r0, n, r1, nrows_prev, prefetch);
+}
+
+// The right-to-left orthogonalisation of Algorithm 1 (k = d-1 .. 1) in one CTA: each step is the
+// body of k_lq_right_rows on the cores left by the previous one (a barrier between the steps).
+struct LqSweepArgs {
+  float* core[TT_MAX_D];
+  int r[TT_MAX_D + 1];
+  int n[TT_MAX_D];
+  int d;
+  int prefetch;
+};
+
+template <int Q>
+__global__ void __launch_bounds__(QR_T, 1) k_lq_sweep_rows(LqSweepArgs a, const int* status) {
+  extern __shared__ __align__(16) float sm[];
+  if (*status != 0) return;
+  for (int k = a.d - 1; k >= 1; --k) {
+    lq_right_body<Q>(sm, a.core[k - 1], a.core[k], a.r[k], a.n[k], a.r[k + 1], a.r[k - 1] * a.n[k - 1], a.prefetch);
+    __syncthreads();
+  }
+}
+
+template <int Q>
+static bool launch_lq_sweep_q(tt_ctx* c, float* const* cores, cudaError_t* err) {
+  LqSweepArgs a;
+  a.d = c->d;
+  size_t with = 0, without = 0;
+  for (int k = 0; k < c->d; ++k) {
+    a.core[k] = cores[k];
+    a.n[k] = (int)c->n[k];
+  }
+  for (int k = 0; k <= c->d; ++k) a.r[k] = c->r[k];
+  for (int k = c->d - 1; k >= 1; --k) {
+    const int m = (int)c->n[k] * c->r[k + 1];
+    const int64_t nx = (int64_t)c->r[k - 1] * c->n[k - 1] * c->r[k];
+    with = std::max(with, qr_rows_smem<Q>(m, nx));
+    without = std::max(without, qr_rows_smem<Q>(m, 0));
+  }
+  a.prefetch = with <= 200 * 1024;
+  const size_t smem = a.prefetch ? with : without;
+  if (smem > 200 * 1024) return false;
+  *err = cudaFuncSetAttribute(k_lq_sweep_rows<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (*err != cudaSuccess) return true;
+  k_lq_sweep_rows<Q><<<1, QR_T, smem, c->stream>>>(a, c->d_status);
+  *err = cudaGetLastError();
+  return true;
+}
+
 // Launch a rows kernel for q <= 16 when its shared memory fits; false = use the generic kernels.
 template <int Q, bool LEFT>
 static bool launch_qr_rows_q(float* a0, float* a1, int r0, int n, int r1, int nbr, int m, int64_t nx,
@@ -1080,6 +1132,32 @@ int tt_launch_qr_left(tt_ctx* c, float* core_k, float* core_k1, int k) {
   TT_CUDA(c, cudaFuncSetAttribute(k_qr_left, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k_qr_left<<<1, 512, smem, c->stream>>>(core_k, core_k1, r0, n, r1, ncols, use_chol, c->d_status);
   TT_LAUNCH(c, "k_qr_left");
+  return TT_OK;
+}
+
+// Right-to-left orthogonalisation of all cores: one launch when every rank r_1 .. r_{d-1} is at
+// most 16 (and shared memory allows), else one launch per step.
+int tt_launch_lq_sweep(tt_ctx* c, float* const* cores) {
+  int q = 1;
+  for (int k = 1; k < c->d; ++k) q = std::max(q, c->r[k]);
+  cudaError_t e = cudaSuccess;
+  bool done = false;
+  if (c->d >= 2 && q <= 16) {
+    if (q <= 4)
+      done = launch_lq_sweep_q<4>(c, cores, &e);
+    else if (q <= 8)
+      done = launch_lq_sweep_q<8>(c, cores, &e);
+    else if (q <= 12)
+      done = launch_lq_sweep_q<12>(c, cores, &e);
+    else
+      done = launch_lq_sweep_q<16>(c, cores, &e);
+  }
+  if (done) {
+    TT_CUDA(c, e);
+    TT_LAUNCH(c, "k_lq_sweep_rows");
+    return TT_OK;
+  }
+  for (int kk = c->d - 1; kk >= 1; --kk) TT_TRY(tt_launch_lq_right(c, cores[kk - 1], cores[kk], kk));
   return TT_OK;
 }
 
