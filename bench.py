@@ -571,6 +571,10 @@ def main():
     scales = torch.tensor(p.scales, device=dev) if p.scales is not None else None
     cores = lib.device_cores(p.init_cores, device=dev)
 
+    # One sweep of Algorithm 1, then the relative error of the updated cores. Two calls (two
+    # synchronisations): measured 772 us per step, against 797 us for the single
+    # tt_prox_als_sweep_monitored call, whose relative error then overlaps the next draw's plan
+    # build on the side stream.
     def step(t):
         ctx.tt_prox_als_sweep(A, cores, 1, t, scales=scales, rel_change=False)
         return ctx.tt_rel_error(A, cores, scales=scales)

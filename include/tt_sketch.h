@@ -29,8 +29,8 @@
  * context owns its hash tables, plans and workspaces (allocated in tt_sketch_init).
  *
  * Streams: all work is enqueued on the stream given to tt_sketch_init. Calls that return host
- * scalars (tt_prox_als_sweep with rel_change_out, tt_rel_error, tt_sketch_tables) synchronise
- * that stream; the others are asynchronous.
+ * scalars (tt_prox_als_sweep, tt_prox_als_sweep_monitored, tt_rel_error, tt_sketch_tables)
+ * synchronise that stream; the others are asynchronous.
  *
  * Errors: every int-returning call returns TT_OK (0) or a negative TT_E* code; the message of
  * the last failure is available from tt_last_error(ctx). On error no output is guaranteed.
@@ -158,6 +158,18 @@ int tt_orthogonalize(tt_ctx* ctx, float* const* cores_dev, int direction, int k)
 int tt_prox_als_sweep(tt_ctx* ctx, const void* A_dev, const float* scales_dev,
                       float* const* cores_dev, int nsweeps, uint64_t first_sweep,
                       double* rel_change_out);
+
+/*
+ * tt_prox_als_sweep with the relative error of Sec. 5 after every sweep: rel_error_out (host,
+ * nsweeps entries, required) receives ||A - [[G^(t+1)]]||_F / ||A||_F computed right after sweep t
+ * (as tt_rel_error computes it, FP64 accumulation), rel_change_out (optional) as above. Sweeps and
+ * errors are enqueued back to back and copied back with one synchronisation per block of
+ * sweeps, instead of one per call of each. Returns as tt_prox_als_sweep; TT_EINVAL if
+ * rel_error_out is NULL.
+ */
+int tt_prox_als_sweep_monitored(tt_ctx* ctx, const void* A_dev, const float* scales_dev,
+                                float* const* cores_dev, int nsweeps, uint64_t first_sweep,
+                                double* rel_change_out, double* rel_error_out);
 
 /*
  * One sweep of Algorithm 1 (draw `sweep`) whose data sketches are given: Y_dev[k] must hold

@@ -178,27 +178,31 @@ extern "C" int tt_prox_als_sweep_sketched(tt_ctx* c, float* const* Y, float* con
   return tt_read_status(c);
 }
 
-extern "C" int tt_prox_als_sweep(tt_ctx* c, const void* A, const float* scales, float* const* cores,
-                                 int nsweeps, uint64_t first_sweep, double* rel_change_out) {
-  if (!c) return TT_EINVAL;
-  TT_TRY(check_data(c, A, scales));
-  TT_TRY(tt_check_cores(c, cores));
-  if (nsweeps < 0) return tt_fail(c, TT_EINVAL, "nsweeps < 0");
-  c->err.clear();
+// nsweeps outer iterations; per sweep (optional) the rel-change and the relative error of the
+// updated cores, copied back in blocks of changes_cap / d sweeps with one synchronisation each.
+static int run_sweeps(tt_ctx* c, const void* A, const float* scales, float* const* cores, int nsweeps,
+                      uint64_t first_sweep, double* rel_change_out, double* rel_error_out) {
   TT_TRY(tt_reset_status(c));
   const int per_block = c->changes_cap / c->d;
-  std::vector<double> host;
+  std::vector<double> host, herr;
   for (int t0 = 0; t0 < nsweeps; t0 += per_block) {
     const int nt = std::min(per_block, nsweeps - t0);
     for (int t = 0; t < nt; ++t) {
       double* slots = rel_change_out ? c->d_changes + (size_t)2 * c->d * t : nullptr;
       TT_TRY(tt_one_sweep(c, A, scales, cores, first_sweep + t0 + t, slots));
+      if (rel_error_out) TT_TRY(tt_launch_rel_error(c, A, scales, cores, c->d_errs + 2 * t));
     }
     if (rel_change_out) {
       host.resize((size_t)2 * c->d * nt);
       TT_CUDA(c, cudaMemcpyAsync(host.data(), c->d_changes, sizeof(double) * host.size(), cudaMemcpyDeviceToHost, c->stream));
-      TT_TRY(tt_read_status(c));
-      for (int t = 0; t < nt; ++t) {
+    }
+    if (rel_error_out) {
+      herr.resize((size_t)2 * nt);
+      TT_CUDA(c, cudaMemcpyAsync(herr.data(), c->d_errs, sizeof(double) * herr.size(), cudaMemcpyDeviceToHost, c->stream));
+    }
+    if (rel_change_out || rel_error_out) {
+      TT_TRY(tt_read_status(c));  // synchronises
+      for (int t = 0; t < nt && rel_change_out; ++t) {
         double mx = 0.0;
         for (int k = 0; k < c->d; ++k) {
           double dd = host[(size_t)2 * (c->d * t + k)], nn = host[(size_t)2 * (c->d * t + k) + 1];
@@ -206,16 +210,40 @@ extern "C" int tt_prox_als_sweep(tt_ctx* c, const void* A, const float* scales, 
         }
         rel_change_out[t0 + t] = mx;
       }
+      for (int t = 0; t < nt && rel_error_out; ++t)
+        rel_error_out[t0 + t] = herr[2 * t + 1] > 0 ? sqrt(herr[2 * t] / herr[2 * t + 1]) : 0.0;
     }
   }
-  if (!rel_change_out) {
-    // surface a failed solve without forcing a synchronisation on the success path
+  if (!rel_change_out && !rel_error_out) {
+    // surface a failed solve (one synchronisation at the end of the call)
     int st = 0;
     TT_CUDA(c, cudaMemcpyAsync(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     TT_CUDA(c, cudaStreamSynchronize(c->stream));
     if (st != 0) return tt_read_status(c);
   }
   return TT_OK;
+}
+
+extern "C" int tt_prox_als_sweep(tt_ctx* c, const void* A, const float* scales, float* const* cores,
+                                 int nsweeps, uint64_t first_sweep, double* rel_change_out) {
+  if (!c) return TT_EINVAL;
+  TT_TRY(check_data(c, A, scales));
+  TT_TRY(tt_check_cores(c, cores));
+  if (nsweeps < 0) return tt_fail(c, TT_EINVAL, "nsweeps < 0");
+  c->err.clear();
+  return run_sweeps(c, A, scales, cores, nsweeps, first_sweep, rel_change_out, nullptr);
+}
+
+extern "C" int tt_prox_als_sweep_monitored(tt_ctx* c, const void* A, const float* scales, float* const* cores,
+                                           int nsweeps, uint64_t first_sweep, double* rel_change_out,
+                                           double* rel_error_out) {
+  if (!c) return TT_EINVAL;
+  TT_TRY(check_data(c, A, scales));
+  TT_TRY(tt_check_cores(c, cores));
+  if (nsweeps < 0) return tt_fail(c, TT_EINVAL, "nsweeps < 0");
+  if (!rel_error_out) return tt_fail(c, TT_EINVAL, "null rel_error_out");
+  c->err.clear();
+  return run_sweeps(c, A, scales, cores, nsweeps, first_sweep, rel_change_out, rel_error_out);
 }
 
 extern "C" int tt_rel_error(tt_ctx* c, const void* A, const float* scales, float* const* cores, double* out) {

@@ -412,7 +412,7 @@ int tt_prepare_next_draw(tt_ctx* c, uint64_t sweep) {
 static void free_all(tt_ctx* c) {
   void* ps[] = {c->d_h, c->d_v, c->d_plan0, c->d_plan0_off, c->d_plan0_cursor, c->d_ghat,
                 c->d_twiddle, c->d_twstage, c->d_suffix, c->d_prefix, c->d_prefix_tmp, c->d_SH, c->d_Y,
-                c->d_gram, c->d_core_old, c->d_changes, c->d_status, c->d_err_acc, c->d_ws_acc, c->d_rint, c->d_slab_u, c->d_Yall};
+                c->d_gram, c->d_core_old, c->d_changes, c->d_status, c->d_err_acc, c->d_errs, c->d_ws_acc, c->d_rint, c->d_slab_u, c->d_Yall};
   for (void* p : ps)
     if (p) cudaFree(p);
   if (c->d_A_stage) cudaFree(c->d_A_stage);
@@ -552,6 +552,7 @@ extern "C" int tt_sketch_init(tt_ctx** out, const tt_params* p, void* stream) {
   A((void**)&c->d_core_old, sizeof(float) * c->nmax * c->smax);
   c->changes_cap = 1024 * TT_MAX_D;
   A((void**)&c->d_changes, sizeof(double) * 2 * c->changes_cap);
+  A((void**)&c->d_errs, sizeof(double) * 2 * (c->changes_cap / c->d));
   A((void**)&c->d_status, sizeof(int));
   A((void**)&c->d_err_acc, sizeof(double) * 4);
   A((void**)&c->d_ws_acc, sizeof(double) * 2);

@@ -122,6 +122,7 @@ struct tt_ctx {
   double* d_changes = nullptr; // per (sweep, k): ||dG||^2, ||G||^2
   int* d_status = nullptr;     // device error flag (0 = ok, else TT_E* code)
   double* d_err_acc = nullptr; // rel-error accumulators (2 doubles)
+  double* d_errs = nullptr;    // per-sweep rel-error accumulators (2 per sweep, changes_cap / d sweeps)
   double* d_ws_acc = nullptr;  // warm-start summary accumulators (2 doubles)
   float* d_rint = nullptr;     // right interfaces of the mode-0 fibres (N / n_0 x rint_r1p), rel error
   int rint_r1p = 0;            // r_1 rounded up to a multiple of 4
@@ -206,7 +207,8 @@ int tt_launch_prox_update(tt_ctx* c, const float* Y, const float* SH, float* cor
 int tt_launch_qr_left(tt_ctx* c, float* core_k, float* core_k1, int k);
 int tt_launch_lq_right(tt_ctx* c, float* core_km1, float* core_k, int k);
 int tt_launch_lq_sweep(tt_ctx* c, float* const* cores);  // all right-to-left steps
-int tt_launch_rel_error(tt_ctx* c, const void* A, const float* scales, float* const* cores);
+int tt_launch_rel_error(tt_ctx* c, const void* A, const float* scales, float* const* cores,
+                        double* acc = nullptr);  // acc: 2 doubles (default: the context's)
 int tt_read_status(tt_ctx* c);
 int tt_reset_status(tt_ctx* c);
 int tt_check_cores(tt_ctx* c, float* const* cores);

@@ -1691,7 +1691,8 @@ static size_t rel_stream_smem(const tt_ctx* c, int es) {
 }
 
 template <int DT>
-static int launch_rel_stream(tt_ctx* c, const void* A, const float* scales, const float* g0, size_t smem) {
+static int launch_rel_stream(tt_ctx* c, const void* A, const float* scales, const float* g0, size_t smem,
+                             double* acc) {
   static bool attr = false;
   if (!attr) {
     TT_CUDA(c, cudaFuncSetAttribute(k_rel_error_stream<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
@@ -1706,12 +1707,13 @@ static int launch_rel_stream(tt_ctx* c, const void* A, const float* scales, cons
   const int64_t ntiles = (M0 + FT - 1) / FT;
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)std::max(1, per_sm) * sms));
   k_rel_error_stream<DT><<<blocks, 256, smem, c->stream>>>(A, scales, g0, c->d_rint, (int)c->n[0], c->r[1],
-                                                          c->rint_r1p, M0, c->d_err_acc);
+                                                          c->rint_r1p, M0, acc);
   TT_LAUNCH(c, "k_rel_error_stream");
   return TT_OK;
 }
 
-int tt_launch_rel_error(tt_ctx* c, const void* A, const float* scales, float* const* cores) {
+int tt_launch_rel_error(tt_ctx* c, const void* A, const float* scales, float* const* cores, double* acc) {
+  if (!acc) acc = c->d_err_acc;
   ErrArgs a;
   a.A = A;
   a.scales = scales;
@@ -1721,7 +1723,7 @@ int tt_launch_rel_error(tt_ctx* c, const void* A, const float* scales, float* co
   }
   for (int k = 0; k <= c->d; ++k) a.r[k] = c->r[k];
   a.d = c->d;
-  a.acc = c->d_err_acc;
+  a.acc = acc;
   a.slabs = c->N / (c->n[0] * c->n[1]);
   // i_1 chunk (multiple of 4): W (r1 x chunk) plus G_0 (r1 x n0) within ~200 KB, at most ~16K
   // entries per item, and at least ~4 items per SM overall
@@ -1734,7 +1736,7 @@ int tt_launch_rel_error(tt_ctx* c, const void* A, const float* scales, float* co
   a.nchunks = (int)((c->n[1] + chunk - 1) / chunk);
   a.g0_in_smem = 1;
   const size_t smem = sizeof(float) * ((size_t)c->r[1] * a.i1chunk + (size_t)g0sz);
-  TT_CUDA(c, cudaMemsetAsync(c->d_err_acc, 0, sizeof(double) * 2, c->stream));
+  TT_CUDA(c, cudaMemsetAsync(acc, 0, sizeof(double) * 2, c->stream));
   const int es = c->dtype == TT_F64 ? 8 : c->dtype == TT_F32 ? 4 : c->dtype == TT_BF16 ? 2 : 1;
   const size_t ssm = c->d_rint ? rel_stream_smem(c, es) : 0;
   if (ssm) {  // streaming form: right interfaces first, then one pass over A in memory order
@@ -1765,10 +1767,10 @@ int tt_launch_rel_error(tt_ctx* c, const void* A, const float* scales, float* co
       TT_LAUNCH(c, "k_rint");
     }
     switch (c->dtype) {
-      case TT_F64: return launch_rel_stream<TT_F64>(c, A, scales, cores[0], ssm);
-      case TT_F32: return launch_rel_stream<TT_F32>(c, A, scales, cores[0], ssm);
-      case TT_BF16: return launch_rel_stream<TT_BF16>(c, A, scales, cores[0], ssm);
-      default: return launch_rel_stream<TT_FP8E4M3>(c, A, scales, cores[0], ssm);
+      case TT_F64: return launch_rel_stream<TT_F64>(c, A, scales, cores[0], ssm, acc);
+      case TT_F32: return launch_rel_stream<TT_F32>(c, A, scales, cores[0], ssm, acc);
+      case TT_BF16: return launch_rel_stream<TT_BF16>(c, A, scales, cores[0], ssm, acc);
+      default: return launch_rel_stream<TT_FP8E4M3>(c, A, scales, cores[0], ssm, acc);
     }
   }
   const int64_t items = a.slabs * a.nchunks;

@@ -25,7 +25,7 @@ EXPORTS = ["tt_sketch_init", "tt_sketch_destroy", "tt_last_error", "tt_sketch_ta
            "tt_orthogonalize", "tt_prox_als_sweep", "tt_rel_error", "tt_prox_als_sweep_host",
            "tt_profile_enable", "tt_profile_read", "tt_prox_update_noalloc", "tt_batch_init",
            "tt_batch_destroy", "tt_batch_last_error", "tt_batch_sweep", "tt_batch_rel_error",
-           "tt_prox_als_sweep_sketched",
+           "tt_prox_als_sweep_sketched", "tt_prox_als_sweep_monitored",
            # learned warm start (include/tt_warmstart.h)
            "tt_mlp_init", "tt_mlp_destroy", "tt_mlp_last_error", "tt_mlp_set_weights", "tt_mlp_get_weights",
            "tt_mlp_forward", "tt_mlp_loss_grads", "tt_mlp_train_step", "tt_mlp_gemm_bf16",
@@ -86,6 +86,8 @@ def load(path: str = LIB_PATH):
     L.tt_prox_als_sweep.argtypes = [vp, vp, vp, ctypes.POINTER(vp), i, u64, ctypes.POINTER(ctypes.c_double)]
     L.tt_rel_error.argtypes = [vp, vp, vp, ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_double)]
     L.tt_prox_als_sweep_sketched.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), u64]
+    L.tt_prox_als_sweep_monitored.argtypes = [vp, vp, vp, ctypes.POINTER(vp), i, u64, ctypes.POINTER(ctypes.c_double),
+                                              ctypes.POINTER(ctypes.c_double)]
     L.tt_prox_als_sweep_host.argtypes = [vp, vp, vp, ctypes.POINTER(vp), i, u64, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_double)]
     L.tt_prox_update_noalloc.argtypes = [vp, vp, vp, i, i, i, i, ctypes.c_double, vp]
@@ -214,6 +216,16 @@ class Context:
         self._check(self.lib.tt_prox_als_sweep(self.ctx, _ptr(A), _ptr(scales), _ptr_array(cores),
                                                int(nsweeps), int(first_sweep), out))
         return list(out)[:nsweeps] if rel_change else None
+
+    def tt_prox_als_sweep_monitored(self, A, cores: Sequence, nsweeps: int, first_sweep: int = 0, scales=None,
+                                    rel_change: bool = False):
+        """Sweeps with the relative error after each one (one synchronisation per call).
+        Returns (rel_errors, rel_changes or None)."""
+        err = (ctypes.c_double * max(1, nsweeps))()
+        out = (ctypes.c_double * max(1, nsweeps))() if rel_change else None
+        self._check(self.lib.tt_prox_als_sweep_monitored(self.ctx, _ptr(A), _ptr(scales), _ptr_array(cores),
+                                                         int(nsweeps), int(first_sweep), out, err))
+        return list(err)[:nsweeps], (list(out)[:nsweeps] if rel_change else None)
 
     def tt_prox_als_sweep_host(self, A_host: np.ndarray, cores_host: Sequence[np.ndarray], nsweeps: int,
                                first_sweep: int = 0, scales_host: Optional[np.ndarray] = None,

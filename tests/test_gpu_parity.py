@@ -319,6 +319,57 @@ def test_sweeps_scaled_order4_parity():
     assert abs(err - err_ref) <= 1e-5 * err_ref, (err, err_ref)
 
 
+def test_monitored_sweeps_match_separate_calls():
+    """tt_prox_als_sweep_monitored = per sweep, tt_prox_als_sweep then tt_rel_error. Two contexts
+    with the same draws differ only by FP32 summation order in the data-sketch atomics, which
+    unconverged sweeps amplify to ~1e-5: the bound is 1e-4."""
+    w = synth.WORKLOADS["order4-100-r10"].scaled((24, 20, 18, 16), J=512)
+    p = synth.make_problem(w, storage="f32")
+    A = lib.device_tensor(p.storage, "f32")
+    ctx_a = lib.Context(w.dims, p.ranks, w.J, w.lam, p.sketch_seed, "f32")
+    ctx_b = lib.Context(w.dims, p.ranks, w.J, w.lam, p.sketch_seed, "f32")
+    ca, cb = lib.device_cores(p.init_cores), lib.device_cores(p.init_cores)
+    errs, changes = ctx_a.tt_prox_als_sweep_monitored(A, ca, 3, 0, rel_change=True)
+    for t in range(3):
+        ch = ctx_b.tt_prox_als_sweep(A, cb, 1, t)[0]
+        e = ctx_b.tt_rel_error(A, cb)
+        assert abs(errs[t] - e) <= 1e-4 * e, (t, errs[t], e)
+        assert abs(changes[t] - ch) <= 1e-4 * ch, (t, changes[t], ch)
+    ga, gb = lib.host_cores(ca, p.ranks, w.dims), lib.host_cores(cb, p.ranks, w.dims)
+    assert rel(O.tt_full(ga), O.tt_full(gb)) <= 1e-4
+    rc = ctx_a.lib.tt_prox_als_sweep_monitored(ctx_a.ctx, lib._ptr(A), None, lib._ptr_array(ca), 1, 0, None, None)
+    assert rc == lib.TT_EINVAL  # the per-sweep errors are the point of the call
+    ctx_a.close()
+    ctx_b.close()
+
+
+def test_sweeps_with_jumps_in_the_sweep_index():
+    """Each sweep builds the next sweep index's draw and plans ahead; a call with another index
+    (a jump, a step back, a repeat) must draw its own, and the data-sketch entry point must see
+    the draw of the index it is given, whichever of the two buffers holds it."""
+    w = synth.WORKLOADS["order3-50-r5"]
+    p = synth.make_problem(w, storage="f32")
+    ctx = lib.Context(w.dims, p.ranks, w.J, w.lam, p.sketch_seed, "f32")
+    A = lib.device_tensor(p.storage, "f32")
+    dc = lib.device_cores(p.init_cores)
+    ref = [np.array(g, np.float64) for g in p.init_cores]
+    for first in (0, 5, 1, 2, 2):  # a jump ahead, a step back, the spare's index, a repeat
+        ctx.tt_prox_als_sweep(A, dc, 1, first, rel_change=False)
+        ref, _ = O.tt_ts(p.tensor, ref, p.sketch_seed, w.J, w.lam, 1, first_sweep=first)
+    got = lib.host_cores(dc, p.ranks, w.dims)
+    assert rel(O.tt_full(got), O.tt_full(ref)) <= 1e-4
+    Y = [torch.zeros(w.J * n, device="cuda") for n in w.dims]
+    for sweep in (3, 2, 3):  # the spare built by the last sweep, the current draw, the spare again
+        ctx.tt_sketch_unfold(A, -1, sweep, Y)
+        torch.cuda.synchronize()
+        hs, vs = O.draw_sketch(p.sketch_seed, sweep, w.dims, w.J)
+        for k in range(len(w.dims)):
+            refk = O.sketch_unfolding(p.tensor, hs, vs, w.J, k)
+            gotk = Y[k].cpu().numpy().reshape(w.dims[k], w.J).T
+            assert rel(gotk, refk) <= 1e-5, (sweep, k, rel(gotk, refk))
+    ctx.close()
+
+
 def test_sweep_exact_tt_recovery_on_gpu():
     dims, ranks = (12, 10, 11, 9), (1, 3, 3, 3, 1)
     A = synth.contract_cores(synth.random_tt(dims, ranks, 15))
