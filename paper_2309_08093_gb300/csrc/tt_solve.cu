@@ -797,10 +797,17 @@ __device__ bool cholqr2_rows(float* As, int m, int q, float* scratch, float* Rm)
       float a[Q];
       qr_load_row<Q>(As, r, a);
 #pragma unroll
-      for (int i = 0; i < Q; ++i)
+      for (int i = 0; i < Q; ++i) {  // row i of the packed triangle: pairs (j, j+1) per fma.rn.f32x2
+        const int pi = i * (i + 1) / 2;
+        const float2 ai = make_float2(a[i], a[i]);
 #pragma unroll
-        for (int j = 0; j < Q; ++j)
-          if (j <= i) acc[i * (i + 1) / 2 + j] = fmaf(a[i], a[j], acc[i * (i + 1) / 2 + j]);
+        for (int j = 0; j + 1 <= i; j += 2) {
+          const float2 d = tt_ffma2(ai, make_float2(a[j], a[j + 1]), make_float2(acc[pi + j], acc[pi + j + 1]));
+          acc[pi + j] = d.x;
+          acc[pi + j + 1] = d.y;
+        }
+        if ((i & 1) == 0) acc[pi + i] = fmaf(a[i], a[i], acc[pi + i]);  // odd count: the diagonal alone
+      }
     }
     warp_fold_store<V>(acc, part + warp * V);
     __syncthreads();
@@ -934,6 +941,9 @@ __global__ void __launch_bounds__(QR_T, 1) k_qr_left_rows(float* core, float* ne
 #pragma unroll
     for (int b = 0; b < Q; ++b)
       if (b >= a2) R[b * (b + 1) / 2 + a2] = (a2 < q && b < q) ? Rm[a2 * q + b] : 0.f;
+  // with the neighbour prefetched, each thread overwrites its own columns of the shared copy and
+  // the CTA then stores the copy with coalesced writes (columns are r1 floats apart)
+  float* dstc = prefetch ? NX : next;
   for (int cc = t; cc < ncols_next; cc += QR_T) {
     float x[Q];
     const float* src = prefetch ? NX + (size_t)cc * r1 : next + (size_t)cc * r1;
@@ -946,8 +956,13 @@ __global__ void __launch_bounds__(QR_T, 1) k_qr_left_rows(float* core, float* ne
 #pragma unroll
       for (int b = 0; b < Q; ++b)
         if (b >= a2) acc = fmaf(R[b * (b + 1) / 2 + a2], x[b], acc);
-      next[(size_t)cc * r1 + a2] = acc;
+      dstc[(size_t)cc * r1 + a2] = acc;
     }
+  }
+  if (prefetch) {
+    __syncthreads();
+    const int64_t nx = (int64_t)r1 * ncols_next;
+    for (int64_t idx = t; idx < nx; idx += QR_T) next[idx] = NX[idx];
   }
 }
 
