@@ -153,145 +153,69 @@ struct SolveArgs {
 // W[j][j] (the D of M = L D L^T: positive exactly when M is SPD) and subtracts W[i][j] times it
 // from every other row i; after s steps the first s columns are the identity and
 // X_c[r][i] = W[i][s + r]. W lives in registers: thread (ty, tx) of a TY x 32 layout owns
-// W[ty + TY a][tx + 32 b]. Pivots go in pairs (j, j+1), one barrier per pair: before a pair the
-// owners publish in shared memory row j normalised and row j+1 as it stands; every thread then
-// forms, for its own columns, row j+1 after step j and normalised by its pivot
-// p' = W[j+1][j+1] - W[j+1][j] r_j[j+1], takes columns j and j+1 of its own rows from the owning
-// lanes by shuffles, and applies both steps at once:
-//     W[i] -= W[i][j] r_j + (W[i][j+1] - W[i][j] r_j[j+1]) r_{j+1}   (i != j+1; W[j][j] := 0),
-// while row j+1 becomes r_{j+1}. A last unpaired pivot takes a single step. Steps run in groups of
-// TY (TY even, so pairs never straddle groups; template recursion over the group G): row j is then
-// register block G of warp j - TY G and column j register block TY G / 32 of lane j % 32, both
-// compile-time, so no register is ever selected by a runtime index. Column blocks wholly left of
-// the group's pivots are dead and skipped.
-
-// Publish the next unit: row jn normalised into rb0 and, for a pair, row jn + 1 as it stands
-// into rb1 (GN: the group of row jn).
-template <int TY, int RA, int CB, int GN>
-__device__ __forceinline__ void gj_pub(float (&w)[RA][CB], int jn, bool pair, float* rb0, float* rb1, int* bad,
-                                       int ty, int tx) {
-  constexpr int CNN = (TY * GN) / 32;
-  if (ty == jn - TY * GN) {
-    const float p = __shfl_sync(0xffffffffu, w[GN][CNN], jn & 31);
+// W[ty + TY a][tx + 32 b]. A warp needs column j only for its own rows, so lane j % 32 hands it
+// over by shuffles; the normalised row j is published through shared memory by its warp at the
+// end of step j - 1: one barrier per step. Steps run in groups of TY (template recursion over
+// the group G): row j is then register block G of warp j - TY G and column j register block
+// TY G / 32 of lane j % 32, both compile-time, so no register is ever selected by a runtime
+// index. Column blocks wholly left of the group's pivots are dead and skipped.
+template <int TY, int RA, int CB, int G>
+__device__ __forceinline__ void gj_publish_row(float (&w)[RA][CB], int jn, float* rowb, int* bad, int ty, int tx) {
+  constexpr int CN = (TY * G) / 32;  // column block of pivots TY G .. TY G + TY - 1
+  if (ty == jn - TY * G) {           // the warp that owns row jn (register block G)
+    const float p = __shfl_sync(0xffffffffu, w[G][CN], jn & 31);
     if (tx == 0 && (!(p > 0.f) || !isfinite(p))) atomicCAS(bad, 0, isfinite(p) ? TT_ENOTSPD : TT_ENONFINITE);
     const float ip = 1.f / p;
 #pragma unroll
     for (int cb = 0; cb < CB; ++cb) {
-      const float v = w[GN][cb] * ip;
-      w[GN][cb] = v;
-      rb0[tx + 32 * cb] = v;
-    }
-  }
-  if (pair && ty == jn + 1 - TY * GN) {
-#pragma unroll
-    for (int cb = 0; cb < CB; ++cb) rb1[tx + 32 * cb] = w[GN][cb];
-  }
-}
-
-// One pivot pair on the live column blocks (a dead block left of CN may be updated too: it is never
-// read again). Per column: r_{j+1} = (W[j+1] - a1 r_j) / p' and r_j' = r_j - b0 r_{j+1} (row j
-// after both steps); then W[i] -= f_i r_j' + g_i r_{j+1} with f_i = W[i][j], g_i = W[i][j+1] as
-// they stood before the pair (f_j = 0, g_j = r_j[j+1] = b0), pairs of blocks per fma.rn.f32x2.
-// Row j+1 (register block G of warp own1) becomes r_{j+1}.
-template <int RA, int CB, int CN, int G>
-__device__ __forceinline__ void gj_pair_update(float (&w)[RA][CB], const float (&f)[RA], const float (&g)[RA],
-                                               const float* r0b, const float* r1b, float a1, float b0, float ipp,
-                                               bool own1, int tx) {
-  constexpr int CP = CN & ~1;
-#pragma unroll
-  for (int cb = CP; cb < CB; cb += 2) {
-    if (cb + 1 < CB) {
-      const float x0a = r0b[tx + 32 * cb], x0b = r0b[tx + 32 * (cb + 1)];
-      const float x1a = fmaf(-a1, x0a, r1b[tx + 32 * cb]) * ipp;
-      const float x1b = fmaf(-a1, x0b, r1b[tx + 32 * (cb + 1)]) * ipp;
-      const float ya = fmaf(-b0, x1a, x0a), yb = fmaf(-b0, x1b, x0b);
-#pragma unroll
-      for (int ra = 0; ra < RA; ++ra) {
-        float2 d = tt_ffma2(make_float2(-f[ra], -f[ra]), make_float2(ya, yb), make_float2(w[ra][cb], w[ra][cb + 1]));
-        d = tt_ffma2(make_float2(-g[ra], -g[ra]), make_float2(x1a, x1b), d);
-        w[ra][cb] = d.x;
-        w[ra][cb + 1] = d.y;
-      }
-      if (own1) {
-        w[G][cb] = x1a;
-        w[G][cb + 1] = x1b;
-      }
-    } else {
-      const float x0a = r0b[tx + 32 * cb];
-      const float x1a = fmaf(-a1, x0a, r1b[tx + 32 * cb]) * ipp;
-      const float ya = fmaf(-b0, x1a, x0a);
-#pragma unroll
-      for (int ra = 0; ra < RA; ++ra) w[ra][cb] = fmaf(-g[ra], x1a, fmaf(-f[ra], ya, w[ra][cb]));
-      if (own1) w[G][cb] = x1a;
-    }
-  }
-}
-
-// A single step on the live column blocks: W[i] -= f_i r_j (f_j = 0).
-template <int RA, int CB, int CN>
-__device__ __forceinline__ void gj_single_update(float (&w)[RA][CB], const float (&f)[RA], const float* r0b, int tx) {
-  constexpr int CP = CN & ~1;
-#pragma unroll
-  for (int cb = CP; cb < CB; cb += 2) {
-    if (cb + 1 < CB) {
-      const float xa = r0b[tx + 32 * cb], xb = r0b[tx + 32 * (cb + 1)];
-#pragma unroll
-      for (int ra = 0; ra < RA; ++ra) {
-        const float2 d =
-            tt_ffma2(make_float2(-f[ra], -f[ra]), make_float2(xa, xb), make_float2(w[ra][cb], w[ra][cb + 1]));
-        w[ra][cb] = d.x;
-        w[ra][cb + 1] = d.y;
-      }
-    } else {
-      const float xa = r0b[tx + 32 * cb];
-#pragma unroll
-      for (int ra = 0; ra < RA; ++ra) w[ra][cb] = fmaf(-f[ra], xa, w[ra][cb]);
+      const float v = w[G][cb] * ip;
+      w[G][cb] = v;
+      rowb[tx + 32 * cb] = v;
     }
   }
 }
 
 template <int TY, int RA, int CB, int G>
-__device__ __forceinline__ void gj_groups(float (&w)[RA][CB], int s, float (*rowbuf)[2][CB * 32], int* bad, int& bs,
+__device__ __forceinline__ void gj_groups(float (&w)[RA][CB], int s, float (*rowbuf)[CB * 32], int* bad, int& bs,
                                           int ty, int tx) {
   if constexpr (G < RA) {
     constexpr int CN = (TY * G) / 32;  // column block of this group's pivots = first live block
-    constexpr int CP = CN & ~1;
     const int j0 = TY * G;
     if (j0 >= s) return;
     const int jend = min(TY, s - j0);
-    for (int jj = 0; jj + 1 < jend; jj += 2) {
-      const int j = j0 + jj;
-      const float* r0b = rowbuf[bs][0];
-      const float* r1b = rowbuf[bs][1];
-      float f[RA], g[RA];
+    for (int jj = 0; jj < jend; ++jj) {
+      const int jl = (j0 + jj) & 31;  // the lane that holds column j
+      float f[RA], rv[CB];
 #pragma unroll
-      for (int ra = 0; ra < RA; ++ra) {
-        f[ra] = __shfl_sync(0xffffffffu, w[ra][CN], j & 31);
-        g[ra] = __shfl_sync(0xffffffffu, w[ra][CN], (j + 1) & 31);
+      for (int ra = 0; ra < RA; ++ra) f[ra] = __shfl_sync(0xffffffffu, w[ra][CN], jl);
+      if (ty == jj) f[G] = 0.f;  // row j itself (already normalised) is left alone
+#pragma unroll
+      for (int cb = CN & ~1; cb < CB; ++cb) rv[cb] = rowbuf[bs][tx + 32 * cb];
+      // pairs of column blocks per fma.rn.f32x2 (a dead block left of CN may be updated too: it
+      // is never read again)
+      constexpr int CP = CN & ~1;
+#pragma unroll
+      for (int cb = CP; cb < CB; cb += 2) {
+        if (cb + 1 < CB) {
+#pragma unroll
+          for (int ra = 0; ra < RA; ++ra) {
+            const float2 d = tt_ffma2(make_float2(-f[ra], -f[ra]), make_float2(rv[cb], rv[cb + 1]),
+                                      make_float2(w[ra][cb], w[ra][cb + 1]));
+            w[ra][cb] = d.x;
+            w[ra][cb + 1] = d.y;
+          }
+        } else {
+#pragma unroll
+          for (int ra = 0; ra < RA; ++ra) w[ra][cb] = fmaf(-f[ra], rv[cb], w[ra][cb]);
+        }
       }
-      const float a1 = r1b[j], b0 = r0b[j + 1], c1 = r1b[j + 1];  // W[j+1][j], r_j[j+1], W[j+1][j+1]
-      const float pp = fmaf(-a1, b0, c1);                          // pivot j+1 after step j
-      if (tx == 0 && ty == 0 && (!(pp > 0.f) || !isfinite(pp))) atomicCAS(bad, 0, isfinite(pp) ? TT_ENOTSPD : TT_ENONFINITE);
-      const float ipp = 1.f / pp;
-      if (ty == jj) f[G] = 0.f;  // row j (normalised) takes step j+1 only
-      gj_pair_update<RA, CB, CN, G>(w, f, g, r0b, r1b, a1, b0, ipp, ty == jj + 1, tx);
-      const int jn = j + 2;
+      const int jn = j0 + jj + 1;
       if (jn < s) {
-        if (jj + 2 < TY)
-          gj_pub<TY, RA, CB, G>(w, jn, jj + 3 < jend, rowbuf[bs ^ 1][0], rowbuf[bs ^ 1][1], bad, ty, tx);
+        if (jj + 1 < TY)
+          gj_publish_row<TY, RA, CB, G>(w, jn, rowbuf[bs ^ 1], bad, ty, tx);
         else if constexpr (G + 1 < RA)
-          gj_pub<TY, RA, CB, G + 1>(w, jn, s - jn >= 2, rowbuf[bs ^ 1][0], rowbuf[bs ^ 1][1], bad, ty, tx);
+          gj_publish_row<TY, RA, CB, G + 1>(w, jn, rowbuf[bs ^ 1], bad, ty, tx);
       }
-      __syncthreads();
-      bs ^= 1;
-    }
-    if (jend & 1) {  // the last pivot (s - 1), unpaired: one single step
-      const int j = j0 + jend - 1;
-      float f[RA];
-#pragma unroll
-      for (int ra = 0; ra < RA; ++ra) f[ra] = __shfl_sync(0xffffffffu, w[ra][CN], j & 31);
-      if (ty == jend - 1) f[G] = 0.f;
-      gj_single_update<RA, CB, CN>(w, f, rowbuf[bs][0], tx);
       __syncthreads();
       bs ^= 1;
     }
@@ -300,9 +224,9 @@ __device__ __forceinline__ void gj_groups(float (&w)[RA][CB], int s, float (*row
 }
 
 template <int TY, int RA, int CB>
-__global__ void __launch_bounds__(TY * 32, 1) k_prox_solve(SolveArgs a) {
+__global__ void __launch_bounds__(TY * 32) k_prox_solve(SolveArgs a) {
   constexpr int T = TY * 32;
-  __shared__ __align__(16) float rowbuf[2][2][CB * 32];  // [parity][row j normalised | row j+1]
+  __shared__ __align__(16) float rowbuf[2][CB * 32];
   __shared__ float gsm[RA * TY][33];  // this chunk of G_{k(2)}^T: proximal centre, then the update
   __shared__ float red[2][TY];
   __shared__ int bad;
@@ -350,7 +274,7 @@ __global__ void __launch_bounds__(TY * 32, 1) k_prox_solve(SolveArgs a) {
       w[ra][cb] = in ? v : 0.f;
     }
   }
-  gj_pub<TY, RA, CB, 0>(w, 0, s >= 2, rowbuf[0][0], rowbuf[0][1], &bad, ty, tx);
+  gj_publish_row<TY, RA, CB, 0>(w, 0, rowbuf[0], &bad, ty, tx);
   __syncthreads();
   int bs = 0;
   gj_groups<TY, RA, CB, 0>(w, s, rowbuf, &bad, bs, ty, tx);
