@@ -1446,17 +1446,18 @@ __global__ void __launch_bounds__(256) k_slab_u(ErrArgs a, float* __restrict__ U
 // output positions ol = x + blockDim.x k (k < RINT_KP; ol = i_1 r1p + al) of every slab of the
 // run and keeps their G_1(al, i_1, :) entries (RB >= r_2 of them) in registers, so each output
 // costs r_2 FMAs with u_t broadcast from shared memory; the stores of a slab are contiguous.
+// The CTA first forms the u_t of its own slabs, one level (core) at a time with its threads over
+// (slab, entry) pairs: entry al of G_s(i_s) u takes r_{s+1} loads issued in batches of eight; the
+// vectors pass through shared memory.
 constexpr int RINT_KP = 4;
 template <int RB>
-__global__ void __launch_bounds__(512, 1) k_rint_reg(ErrArgs a, const float* __restrict__ Uv, float* __restrict__ R,
-                                                   int r1p, int slabs_per_cta) {
-  extern __shared__ float us[];  // slabs_per_cta x r_2
+__global__ void __launch_bounds__(512, 1) k_rint_reg(ErrArgs a, float* __restrict__ R, int r1p, int slabs_per_cta) {
+  extern __shared__ float us[];  // slabs_per_cta x r_2, then two slabs_per_cta x max(r_2..r_{d-1}) buffers
   const int n1 = (int)a.n[1], r1 = a.r[1], r2 = a.r[2];
   const int per = n1 * r1p;
   const int64_t t0 = (int64_t)blockIdx.x * slabs_per_cta;
   if (t0 >= a.slabs) return;
   const int nsl = (int)min((int64_t)slabs_per_cta, a.slabs - t0);
-  for (int e = threadIdx.x; e < nsl * r2; e += blockDim.x) us[e] = Uv[t0 * r2 + e];
   const float* g1 = a.core[1];
   float g[RINT_KP][RB];
 #pragma unroll
@@ -1467,6 +1468,50 @@ __global__ void __launch_bounds__(512, 1) k_rint_reg(ErrArgs a, const float* __r
 #pragma unroll
     for (int be = 0; be < RB; ++be)
       g[k][be] = (valid && be < r2) ? __ldg(g1 + al + r1 * (i1 + n1 * be)) : 0.f;
+  }
+  if (a.d == 2) {
+    for (int sl = threadIdx.x; sl < nsl; sl += blockDim.x) us[sl] = 1.f;
+  } else {  // u_t level by level, the CTA's threads over (slab, entry) pairs
+    int rmax = 1;
+    for (int q = 2; q < a.d; ++q) rmax = max(rmax, a.r[q]);
+    float* bufs[2] = {us + slabs_per_cta * r2, us + slabs_per_cta * (r2 + rmax)};
+    int64_t stride = 1;  // prod_{2 <= q < s} n_q for the mode s of the level
+    for (int q = 2; q < a.d - 1; ++q) stride *= a.n[q];
+    const int sl1 = a.d - 1, rl = a.r[sl1];  // the last core: u = G_{d-1}(:, i_{d-1}, 0)
+    float* cur = sl1 == 2 ? us : bufs[0];
+    const int pc = sl1 == 2 ? r2 : rmax;
+    for (int e = threadIdx.x; e < nsl * rl; e += blockDim.x) {
+      const int sl = e / rl, al = e - sl * rl;
+      const int64_t i = ((t0 + sl) / stride) % a.n[sl1];
+      cur[sl * pc + al] = __ldg(a.core[sl1] + al + (int64_t)rl * i);
+    }
+    int pcur = pc;
+    for (int s3 = a.d - 2; s3 >= 2; --s3) {
+      __syncthreads();
+      stride /= a.n[s3];
+      const int rA = a.r[s3], rB = a.r[s3 + 1];
+      const int64_t bstride = (int64_t)rA * a.n[s3];
+      float* nxt = s3 == 2 ? us : (cur == bufs[0] ? bufs[1] : bufs[0]);
+      const int pn = s3 == 2 ? r2 : rmax;
+      for (int e = threadIdx.x; e < nsl * rA; e += blockDim.x) {
+        const int sl = e / rA, al = e - sl * rA;
+        const int64_t i = ((t0 + sl) / stride) % a.n[s3];
+        const float* G = a.core[s3] + al + (int64_t)rA * i;
+        const float* uc = cur + sl * pcur;
+        float acc = 0.f;
+        for (int be0 = 0; be0 < rB; be0 += 8) {  // eight loads in flight per batch
+          float gv[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) gv[q] = be0 + q < rB ? __ldg(G + bstride * (be0 + q)) : 0.f;
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            if (be0 + q < rB) acc = fmaf(gv[q], uc[be0 + q], acc);
+        }
+        nxt[sl * pn + al] = acc;
+      }
+      cur = nxt;
+      pcur = pn;
+    }
   }
   __syncthreads();
   for (int sl = 0; sl < nsl; ++sl) {
@@ -1755,28 +1800,34 @@ int tt_launch_rel_error(tt_ctx* c, const void* A, const float* scales, float* co
   const int es = c->dtype == TT_F64 ? 8 : c->dtype == TT_F32 ? 4 : c->dtype == TT_BF16 ? 2 : 1;
   const size_t ssm = c->d_rint ? rel_stream_smem(c, es) : 0;
   if (ssm) {  // streaming form: right interfaces first, then one pass over A in memory order
-    const int ublocks = (int)std::max<int64_t>(1, std::min<int64_t>((a.slabs + 255) / 256, 4096));
-    k_slab_u<<<ublocks, 256, 0, c->stream>>>(a, c->d_slab_u);
-    TT_LAUNCH(c, "k_slab_u");
     const int per = (int)c->n[1] * c->rint_r1p;
     const int r2 = c->r[2];
     const int rthreads = ((per + RINT_KP - 1) / RINT_KP + 31) & ~31;
-    if (rthreads <= 512 && r2 <= 16) {  // G_1 entries in registers
+    if (rthreads <= 512 && r2 <= 16) {  // G_1 entries in registers, u_t formed in the same kernel
       int sms = 152;
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
-      const int spc = (int)std::max<int64_t>(1, (a.slabs + 4 * sms - 1) / (4 * sms));
+      // one slab run per SM (one CTA fits per SM: a single wave pays the G_1 and u_t prologue once
+      // per SM); a run's u_t and the two level buffers within the default 48 KB of shared memory
+      int rmax = 1;
+      for (int q = 2; q < c->d; ++q) rmax = std::max(rmax, c->r[q]);
+      const int64_t per_slab = r2 + (c->d > 2 ? 2 * rmax : 0);
+      const int64_t spc_max = std::max<int64_t>(1, 12 * 1024 / per_slab);
+      const int spc = (int)std::min(spc_max, std::max<int64_t>(1, (a.slabs + sms - 1) / sms));
       const int rgrid = (int)((a.slabs + spc - 1) / spc);
-      const size_t rsm = sizeof(float) * (size_t)spc * r2;
+      const size_t rsm = sizeof(float) * (size_t)spc * per_slab;
       if (r2 <= 4)
-        k_rint_reg<4><<<rgrid, rthreads, rsm, c->stream>>>(a, c->d_slab_u, c->d_rint, c->rint_r1p, spc);
+        k_rint_reg<4><<<rgrid, rthreads, rsm, c->stream>>>(a, c->d_rint, c->rint_r1p, spc);
       else if (r2 <= 8)
-        k_rint_reg<8><<<rgrid, rthreads, rsm, c->stream>>>(a, c->d_slab_u, c->d_rint, c->rint_r1p, spc);
+        k_rint_reg<8><<<rgrid, rthreads, rsm, c->stream>>>(a, c->d_rint, c->rint_r1p, spc);
       else if (r2 <= 12)
-        k_rint_reg<12><<<rgrid, rthreads, rsm, c->stream>>>(a, c->d_slab_u, c->d_rint, c->rint_r1p, spc);
+        k_rint_reg<12><<<rgrid, rthreads, rsm, c->stream>>>(a, c->d_rint, c->rint_r1p, spc);
       else
-        k_rint_reg<16><<<rgrid, rthreads, rsm, c->stream>>>(a, c->d_slab_u, c->d_rint, c->rint_r1p, spc);
+        k_rint_reg<16><<<rgrid, rthreads, rsm, c->stream>>>(a, c->d_rint, c->rint_r1p, spc);
       TT_LAUNCH(c, "k_rint_reg");
     } else {
+      const int ublocks = (int)std::max<int64_t>(1, std::min<int64_t>((a.slabs + 255) / 256, 4096));
+      k_slab_u<<<ublocks, 256, 0, c->stream>>>(a, c->d_slab_u);
+      TT_LAUNCH(c, "k_slab_u");
       const int rblocks = (int)std::max<int64_t>(1, std::min<int64_t>(a.slabs, 152 * 8));
       k_rint<<<rblocks, 256, 0, c->stream>>>(a, c->d_slab_u, c->d_rint, c->rint_r1p);
       TT_LAUNCH(c, "k_rint");

@@ -270,7 +270,8 @@ def test_orthogonalization_fallback(case):
 
 @pytest.mark.parametrize("dims,ranks,storage", [((20, 18, 16), (1, 4, 5, 1), "f32"), ((9, 8, 7, 6), (1, 3, 4, 2, 1), "f64"),
                                                 ((33, 17, 9, 5), (1, 3, 3, 3, 1), "bf16"), ((40, 12, 10, 6), (1, 2, 3, 2, 1), "fp8"),
-                                                ((64, 48), (1, 7, 1), "f32")])
+                                                ((64, 48), (1, 7, 1), "f32"), ((12, 5, 4, 3, 3), (1, 3, 4, 3, 2, 1), "f32"),
+                                                ((8, 6, 10, 40), (1, 2, 4, 36, 1), "f32")])
 def test_rel_error_parity(dims, ranks, storage):
     true = synth.random_tt(dims, ranks, 3)
     a = synth.add_noise(synth.contract_cores(true), 0.05, np.random.default_rng(4))
