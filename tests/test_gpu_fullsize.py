@@ -1,6 +1,8 @@
-"""Parity at the full size of the order-4 100^4 workload (J = 4096, TT ranks (1,10,10,10,1),
-lambda = 1e-3): the 400 MB FP32 tensor the benchmark streams, in the launch configuration it
-times, against the CPU FP64 oracle on the same seeded tensor, initial cores and draws.
+"""Parity at full size against the CPU FP64 oracle on the same seeded tensor, initial cores and
+draws.
+
+Order-4 100^4 workload (J = 4096, TT ranks (1,10,10,10,1), lambda = 1e-3): the 400 MB FP32
+tensor the benchmark streams, in the launch configuration it times.
 
 - One sweep of Algorithm 1 through tt_prox_als_sweep_monitored, the benchmark's call (its data
   sketches then run in their in-sweep launch shapes beside the chain kernels): every entry of
@@ -10,6 +12,13 @@ times, against the CPU FP64 oracle on the same seeded tensor, initial cores and 
 - The data sketches alone (tt_sketch_unfold, the launch shapes of the isolated roofline), FP32
   and BF16 storage: sampled columns Y_k[:, i_k] of every mode, first, middle and last index,
   against the oracle's column by definition (1e-5 relative per column).
+
+Order-5 40^5 workload (J = 8192, TT ranks (1,8,8,8,8,1) with 0.8^k-decaying cores, 1e-3 noise),
+stored BF16 and FP8-E4M3 with per-mode-1-slice scales: one sweep through the same call against the
+oracle's sweep on the same quantised tensor (1e-4 per core), the reported error against the
+oracle's error of the same cores (1e-5), and the error against the unquantised FP64 tensor within
+2 delta + 1e-4 of the oracle's FP64 sweep (delta = ||A_q - A|| / ||A||: the best-approximation
+error moves by at most delta when A is replaced by A_q).
 """
 import numpy as np
 import pytest
@@ -83,3 +92,40 @@ def test_full_size_data_sketch_columns(problem, storage):
             got = Yk[ik * W.J:(ik + 1) * W.J]  # column-major J x n_k
             assert rel(got, ref) <= 1e-5, (storage, k, ik, rel(got, ref))
     ctx.close()
+
+
+W5 = synth.WORKLOADS["order5-40-r8"]
+
+
+@pytest.fixture(scope="module")
+def problem5():
+    p = synth.make_problem(W5, storage="f64")
+    ref64, _ = O.tt_ts(p.tensor, p.init_cores, p.sketch_seed, W5.J, W5.lam, 1)
+    return p, O.rel_error(p.tensor, ref64)
+
+
+@pytest.mark.parametrize("storage", ["bf16", "fp8"])
+def test_full_size_order5_sweep_matches_oracle(problem5, storage):
+    p, e_64 = problem5
+    a64 = p.tensor
+    assert a64.size == 40 ** 5
+    flat, scales, exact_q = synth.quantize(a64, storage)
+    delta = rel(exact_q, a64)
+    ctx = lib.Context(W5.dims, p.ranks, W5.J, W5.lam, p.sketch_seed, storage)
+    A = lib.device_tensor(flat, storage)
+    sd = torch.tensor(scales, device="cuda") if scales is not None else None
+    dc = lib.device_cores(p.init_cores)
+    errs, _ = ctx.tt_prox_als_sweep_monitored(A, dc, 1, 0, scales=sd)
+    got = lib.host_cores(dc, p.ranks, W5.dims)
+    ctx.close()
+    del A
+    ref_q, _ = O.tt_ts(exact_q, p.init_cores, p.sketch_seed, W5.J, W5.lam, 1)
+    for k in range(W5.d):
+        assert rel(got[k], ref_q[k]) <= 1e-4, (storage, k, rel(got[k], ref_q[k]))
+    got64 = [np.asarray(g, np.float32).astype(np.float64) for g in got]
+    e_q = O.rel_error(exact_q, got64)
+    assert abs(errs[0] - e_q) <= 1e-5 * e_q, (errs[0], e_q)
+    e_gpu = O.rel_error(a64, got64)
+    print(f"\n{storage}: delta={delta:.3e} rel error vs FP64 tensor after one sweep: gpu={e_gpu:.6e} "
+          f"oracle(fp64)={e_64:.6e}")
+    assert abs(e_gpu - e_64) <= 2 * delta + 1e-4
