@@ -19,11 +19,18 @@ oracle's sweep on the same quantised tensor (1e-4 per core), the reported error 
 oracle's error of the same cores (1e-5), and the error against the unquantised FP64 tensor within
 2 delta + 1e-4 of the oracle's FP64 sweep (delta = ||A_q - A|| / ||A||: the best-approximation
 error moves by at most delta when A is replaced by A_q).
+
+Warm-start family member 256 x 256 x 3 x 128 (J = 2048, TT ranks (1,20,3,20,1), cumulative-sum
+cores, 1% noise; the CPU recipe of the family): the sketch summary the network reads (p = 8 bucket
+rows per mode) against the oracle's summary of its own data sketches (1e-5), one sweep against
+the oracle's (1e-4 per core, error 1e-5), then the right-canonical gauge of the swept cores and
+their packed targets against the warm-start oracle (1e-4 per core relative to its norm, 1e-5).
 """
 import numpy as np
 import pytest
 
 import tt_oracle as O
+import tt_warmstart as WS
 from paper_2309_08093_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -129,3 +136,46 @@ def test_full_size_order5_sweep_matches_oracle(problem5, storage):
     print(f"\n{storage}: delta={delta:.3e} rel error vs FP64 tensor after one sweep: gpu={e_gpu:.6e} "
           f"oracle(fp64)={e_64:.6e}")
     assert abs(e_gpu - e_64) <= 2 * delta + 1e-4
+
+
+WW = synth.WORKLOADS["order4-256x256x3x128-r20"]
+
+
+def test_full_size_warmstart_member():
+    p = synth.make_problem(WW)
+    dims, J = WW.dims, WW.J
+    ctx = lib.Context(dims, p.ranks, J, WW.lam, p.sketch_seed, "f32")
+    A = lib.device_tensor(p.storage, "f32")
+    # the summary of sweep 0's data sketches
+    Y = [torch.zeros(J * n, device="cuda") for n in dims]
+    ctx.tt_sketch_unfold(A, -1, 0, Y)
+    x = torch.zeros(ctx.tt_ws_summary_dim(8), device="cuda")
+    sc = torch.zeros(1, device="cuda")
+    ctx.tt_ws_summary(Y, 8, x, sc)
+    hs, vs = O.draw_sketch(p.sketch_seed, 0, dims, J)
+    x_ref, s_ref = WS.ws_summary([O.sketch_unfolding(p.tensor, hs, vs, J, k) for k in range(WW.d)], 8)
+    assert x.numel() == 8 * sum(dims)
+    assert rel(x.cpu().numpy(), x_ref) <= 1e-5
+    assert abs(float(sc.item()) - s_ref) <= 1e-5 * s_ref
+    # one sweep
+    dc = lib.device_cores(p.init_cores)
+    errs, _ = ctx.tt_prox_als_sweep_monitored(A, dc, 1, 0)
+    got = lib.host_cores(dc, p.ranks, dims)
+    ref, _ = O.tt_ts(p.tensor, p.init_cores, p.sketch_seed, J, WW.lam, 1)
+    for k in range(WW.d):
+        assert rel(got[k], ref[k]) <= 1e-4, (k, rel(got[k], ref[k]))
+    got64 = [np.asarray(g, np.float32).astype(np.float64) for g in got]
+    e_ref = O.rel_error(p.tensor, got64)
+    assert abs(errs[0] - e_ref) <= 1e-5 * e_ref, (errs[0], e_ref)
+    # gauge and targets
+    ctx.tt_canonicalize(dc)
+    can = lib.host_cores(dc, p.ranks, dims)
+    can_ref = WS.canonicalize_right(got64)
+    for k in range(WW.d):
+        scale = max(np.linalg.norm(can_ref[k]), 1e-30)
+        assert np.linalg.norm(can[k] - can_ref[k]) <= 1e-4 * scale, k
+    y = torch.zeros(ctx.tt_ws_core_dim(), device="cuda")
+    ctx.tt_ws_pack(dc, sc, y)
+    canc = [np.asarray(g, np.float32).astype(np.float64) for g in can]
+    assert rel(y.cpu().numpy(), WS.ws_targets(canc, float(sc.item()))) <= 1e-5
+    ctx.close()
