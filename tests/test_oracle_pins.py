@@ -153,10 +153,23 @@ def test_left_right_unfold_index_formula():
         assert R[a, i + 3 * b] == G[a, i, b]
 
 
+@pytest.mark.parametrize("J", [45, 150, 1000])
+def test_hash_tables_distribution_any_sketch_size(J):
+    """The same uniformity for sketch sizes that are not powers of two (h = word mod J)."""
+    n = J * 200
+    hs, vs = O.draw_sketch(777, 3, [n], J)
+    assert hs[0].min() >= 0 and hs[0].max() < J
+    counts = np.bincount(hs[0], minlength=J)
+    chi2 = ((counts - n / J) ** 2 / (n / J)).sum()
+    assert chi2 < J + 6 * math.sqrt(2 * J)
+    assert abs(vs[0].sum()) < 6 * math.sqrt(n)
+
+
 # ---------------------------------------------------------------------------------------------
 # part (a): Y_k = S A_(k)^T
 
-@pytest.mark.parametrize("dims,J", [((3, 4, 5), 8), ((2, 3, 2, 4), 16), ((5, 2), 4), ((4, 3, 2, 2, 3), 32)])
+@pytest.mark.parametrize("dims,J", [((3, 4, 5), 8), ((2, 3, 2, 4), 16), ((5, 2), 4), ((4, 3, 2, 2, 3), 32),
+                                    ((3, 4, 5), 7), ((2, 3, 2, 4), 45)])
 def test_data_sketch_definition_vs_dense(dims, J):
     rng = _rng(sum(dims) + J)
     A = synth.random_tensor(dims, J)
@@ -210,7 +223,8 @@ def test_mixed_product_rule():
 
 
 @pytest.mark.parametrize("dims,ranks,J", [((3, 4, 2), (1, 2, 3, 1), 8), ((2, 3, 4, 3), (1, 2, 2, 3, 1), 16),
-                                          ((4, 2, 3, 2, 3), (1, 3, 2, 2, 2, 1), 16), ((5, 4), (1, 3, 1), 4)])
+                                          ((4, 2, 3, 2, 3), (1, 3, 2, 2, 2, 1), 16), ((5, 4), (1, 3, 1), 4),
+                                          ((3, 4, 2), (1, 2, 3, 1), 9), ((2, 3, 4, 3), (1, 2, 2, 3, 1), 15)])
 def test_interface_sketch_three_routes(dims, ranks, J):
     rng = _rng(len(dims) * 31 + J)
     cores = synth.random_tt(dims, ranks, J)
