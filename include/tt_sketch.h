@@ -16,7 +16,9 @@
  *   - Y_k (sketch of the mode-k unfolding) is FP32, J x n[k], column-major: Y_k[b + J*i];
  *   - S H_k is FP32, J x s_k with s_k = r[k]*r[k+1], column-major: SH[b + J*c] with column
  *     c = a + r[k]*b' (a indexes r[k], b' indexes r[k+1]; matches G_{k(2)}, Sec. 3).
- *   - The sketch size m of the paper is J; J must be a power of two, 2 <= J <= 16384.
+ *   - The sketch size m of the paper is J: any integer in [2, 8192], or a power of two up to
+ *     16384. Powers of two use radix-4 / radix-2 FFTs; other sizes (the paper's m = 45, 150,
+ *     200, 1000, 2000 of Sec. 5) use direct DFTs of O(J^2) work per transform.
  *
  * Hash/sign draws (Sec. 2.2, Eqs. (eqn_h), (eqn_v)): per sweep t and mode k the library draws
  *   h_k(i) = word(seed, t, k, 0, i) mod J,  v_k(i) = 1 - 2 * (word(seed, t, k, 1, i) >> 63),
@@ -69,7 +71,7 @@ typedef struct {
   const int64_t* n;   /* host array of d mode sizes, each >= 1 */
   const int* r;       /* host array of d+1 TT ranks, r[0] = r[d] = 1, each >= 1;
                          r[k]*r[k+1] <= 160 and r[k]*n[k]*r[k+1] <= 40000 (in-CTA solves) */
-  int J;              /* sketch size m (power of two, 2..16384) */
+  int J;              /* sketch size m: 2..8192, or a power of two up to 16384 */
   double lambda;      /* proximal weight sigma >= 0 of Eq. (lrtt_sub_prox) */
   uint64_t seed;      /* seed of the hash/sign draws */
   int dtype;          /* TT_F64, TT_F32, TT_BF16 or TT_FP8E4M3: storage type of A */

@@ -44,7 +44,7 @@ __global__ void k_gen_tables(uint64_t seed, uint64_t sweep, TabArgs a, int J, in
   uint64_t i = (uint64_t)(g - a.noff[k]);
   uint64_t wh = tt_word(seed, sweep, (uint64_t)k, 0ull, i);
   uint64_t wv = tt_word(seed, sweep, (uint64_t)k, 1ull, i);
-  h[g] = (int32_t)(wh & (uint64_t)(J - 1));
+  h[g] = (int32_t)((J & (J - 1)) == 0 ? (wh & (uint64_t)(J - 1)) : wh % (uint64_t)J);
   v[g] = (wv >> 63) ? (int8_t)-1 : (int8_t)1;
 }
 
@@ -56,7 +56,8 @@ __global__ void k_gen_tables_dev(uint64_t seed, const uint64_t* sweep_ptr, int f
   int k = 0;
   while (g >= a.noff[k + 1]) ++k;
   uint64_t i = (uint64_t)(g - a.noff[k]);
-  h[g] = (int32_t)(tt_word(seed, sweep, (uint64_t)k, 0ull, i) & (uint64_t)(J - 1));
+  const uint64_t wh = tt_word(seed, sweep, (uint64_t)k, 0ull, i);
+  h[g] = (int32_t)((J & (J - 1)) == 0 ? (wh & (uint64_t)(J - 1)) : wh % (uint64_t)J);
   v[g] = (tt_word(seed, sweep, (uint64_t)k, 1ull, i) >> 63) ? (int8_t)-1 : (int8_t)1;
 }
 
@@ -170,7 +171,7 @@ struct RestWalker {
       sg ^= (v[a.noff[s] + i] < 0);
       o += (int64_t)i * a.fstride[s];
     }
-    *key = b & (a.J - 1);
+    *key = (a.J & (a.J - 1)) == 0 ? (b & (a.J - 1)) : b % a.J;
     *neg = sg;
     *off = o;  // mode-0 fibre index at i_k = 0
   }
@@ -460,7 +461,8 @@ extern "C" int tt_sketch_init(tt_ctx** out, const tt_params* p, void* stream) {
   };
   if (p->d < 2 || p->d > TT_MAX_D) return bad("d must be in [2, 8]", p->d);
   if (!p->n || !p->r) return bad("null n or r", 0);
-  if (p->J < 2 || p->J > TT_MAX_J || (p->J & (p->J - 1))) return bad("J must be a power of two in [2, 16384]", p->J);
+  if (p->J < 2 || p->J > TT_MAX_J) return bad("J must be in [2, 16384]", p->J);
+  if ((p->J & (p->J - 1)) && p->J > 8192) return bad("J above 8192 must be a power of two", p->J);
   if (!(p->lambda >= 0.0) || !std::isfinite(p->lambda)) return bad("lambda must be finite and >= 0", 0);
   if (p->dtype < TT_F64 || p->dtype > TT_FP8E4M3) return bad("unknown dtype", p->dtype);
   if (p->r[0] != 1 || p->r[p->d] != 1) return bad("r[0] and r[d] must be 1", 0);
@@ -468,6 +470,7 @@ extern "C" int tt_sketch_init(tt_ctx** out, const tt_params* p, void* stream) {
   c->J = p->J;
   c->logJ = 0;
   while ((1 << c->logJ) < c->J) ++c->logJ;
+  if ((1 << c->logJ) != c->J) c->logJ = -1;  // not a power of two: direct DFTs
   c->lambda = p->lambda;
   c->seed = p->seed;
   c->dtype = p->dtype;
@@ -529,7 +532,7 @@ extern "C" int tt_sketch_init(tt_ctx** out, const tt_params* p, void* stream) {
   A((void**)&c->spare.h, sizeof(int32_t) * c->noff[c->d]);
   A((void**)&c->spare.v, sizeof(int8_t) * c->noff[c->d]);
   A((void**)&c->d_ghat, sizeof(float2) * c->ghat_off[c->d]);
-  A((void**)&c->d_twiddle, sizeof(float2) * (c->J / 2));
+  A((void**)&c->d_twiddle, sizeof(float2) * c->J);
   A((void**)&c->d_twstage, sizeof(float2) * c->J);
   A((void**)&c->d_suffix, sizeof(float2) * c->suffix_off[c->d]);
   A((void**)&c->d_prefix, sizeof(float2) * H * c->rmax);
@@ -570,9 +573,10 @@ extern "C" int tt_sketch_init(tt_ctx** out, const tt_params* p, void* stream) {
     delete c;
     return e == cudaErrorMemoryAllocation ? TT_ENOMEM : TT_ECUDA;
   }
-  // FFT twiddles exp(-2 pi i t / J), t < J/2, evaluated in double on the host
-  std::vector<float2> tw(c->J / 2);
-  for (int t = 0; t < c->J / 2; ++t) {
+  // twiddles exp(-2 pi i t / J), t < J (the radix-2 FFT reads t < J/2, the direct DFT all),
+  // evaluated in double on the host
+  std::vector<float2> tw(c->J);
+  for (int t = 0; t < c->J; ++t) {
     double ang = -2.0 * M_PI * (double)t / (double)c->J;
     tw[t] = make_float2((float)std::cos(ang), (float)std::sin(ang));
   }
@@ -580,7 +584,7 @@ extern "C" int tt_sketch_init(tt_ctx** out, const tt_params* p, void* stream) {
   // per-stage tables of the radix-4 Stockham FFT: spans Ns = Ns0, 4 Ns0, ... < J (Ns0 = 2 after
   // the radix-2 stage of an odd log J), entries exp(-2 pi i r m / (4 Ns)) at [off + 3 m + r - 1]
   std::vector<float2> tws(c->J, make_float2(1.f, 0.f));
-  {
+  if (c->logJ >= 0) {
     size_t off = 0;
     for (int Ns = (c->logJ & 1) ? 2 : 1; Ns < c->J; Ns *= 4)
       for (int m = 0; m < Ns; ++m, off += 3)

@@ -56,9 +56,37 @@ __device__ void block_fft(float2* buf, const float2* __restrict__ tw, int J, int
 // J-entry shared buffers (ping-pong); returns the buffer holding the result. One barrier per stage.
 // twst: the per-stage twiddle tables (tt_ctx::d_twstage): span Ns reads exp(-2 pi i r m / (4 Ns))
 // at [off + 3 m + r - 1], consecutive butterflies consecutive entries.
+// Direct DFT of any length J, for the sketch sizes that are not powers of two (logJ < 0): y[w] =
+// sum_t x[t] tw[(t w) mod J] with tw[m] = exp(-2 pi i m / J), m < J; (t w) mod J is carried along t
+// by one add and one conditional subtract. O(J^2) work: these are the paper's small sketch sizes.
+__device__ float2* block_dft(const float2* x, float2* y, const float2* __restrict__ tw, int J) {
+  for (int w = threadIdx.x; w < J; w += blockDim.x) {
+    float2 s0 = make_float2(0.f, 0.f), s1 = make_float2(0.f, 0.f);  // even and odd t
+    int m = 0;
+    int t = 0;
+    for (; t + 1 < J; t += 2) {
+      const float2 x0 = x[t], w0 = __ldg(tw + m);
+      m = tt_modj(m + w, J);
+      const float2 x1 = x[t + 1], w1 = __ldg(tw + m);
+      m = tt_modj(m + w, J);
+      s0 = make_float2(fmaf(x0.x, w0.x, fmaf(-x0.y, w0.y, s0.x)), fmaf(x0.x, w0.y, fmaf(x0.y, w0.x, s0.y)));
+      s1 = make_float2(fmaf(x1.x, w1.x, fmaf(-x1.y, w1.y, s1.x)), fmaf(x1.x, w1.y, fmaf(x1.y, w1.x, s1.y)));
+    }
+    if (t < J) {
+      const float2 x0 = x[t], w0 = __ldg(tw + m);
+      s0 = make_float2(fmaf(x0.x, w0.x, fmaf(-x0.y, w0.y, s0.x)), fmaf(x0.x, w0.y, fmaf(x0.y, w0.x, s0.y)));
+    }
+    y[w] = make_float2(s0.x + s1.x, s0.y + s1.y);
+  }
+  __syncthreads();
+  return y;
+}
+
+// For logJ < 0 the call is a direct DFT (block_dft) with twst the J-entry table tw.
 __device__ float2* block_fft_stockham(float2* x, float2* y, const float2* __restrict__ twst, int J, int logJ) {
   int Ns = 1;
   __syncthreads();
+  if (logJ < 0) return block_dft(x, y, twst, J);
   if (logJ & 1) {
     const int h = J >> 1;
     for (int j = threadIdx.x; j < h; j += blockDim.x) {
@@ -163,7 +191,7 @@ __global__ void __launch_bounds__(512) k_core_fft2(CoreFftArgs a) {
   const int H = a.J / 2 + 1;
   float2* o0 = a.out[q] + (int64_t)f0 * H;
   for (int w = threadIdx.x; w < H; w += blockDim.x) {
-    const float2 z = Z[w], zc = Z[(a.J - w) & (a.J - 1)];
+    const float2 z = Z[w], zc = Z[w ? a.J - w : 0];
     o0[w] = make_float2(0.5f * (z.x + zc.x), 0.5f * (z.y - zc.y));
     if (has1) o0[H + w] = make_float2(0.5f * (z.y + zc.y), -0.5f * (z.x - zc.x));
   }
@@ -188,7 +216,7 @@ static int launch_core_ffts(tt_ctx* c, float* const* cores, int j0, int j1) {
     a.pair0[q + 1] = a.pair0[q] + (two ? (S + 1) / 2 : S);
   }
   a.tw = c->d_twiddle;
-  a.twst = c->d_twstage;
+  a.twst = c->logJ >= 0 ? c->d_twstage : c->d_twiddle;  // per-stage tables, or the DFT table
   a.J = c->J;
   a.logJ = c->logJ;
   if (two) {
@@ -412,7 +440,7 @@ int tt_launch_interface_from_chain(tt_ctx* c, int k, float* SH, float* zero, int
   a.L = c->d_prefix;
   a.R = c->d_suffix + c->suffix_off[k];
   a.tw = c->d_twiddle;
-  a.twst = c->d_twstage;
+  a.twst = c->logJ >= 0 ? c->d_twstage : c->d_twiddle;  // per-stage tables, or the DFT table
   a.SH = SH;
   a.ra = c->r[k];
   a.rb = c->r[k + 1];

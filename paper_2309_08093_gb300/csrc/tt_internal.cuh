@@ -24,6 +24,9 @@ __device__ __forceinline__ float2 tt_ffma2(float2 a, float2 b, float2 c) {
 #define TT_MAX_D 8
 #define TT_MAX_S 160      // largest r[k]*r[k+1] handled by the dense solve kernels
 #define TT_MAX_J 16384
+
+// (a + b) mod J for bucket indices a, b < J (any J)
+__host__ __device__ __forceinline__ int tt_modj(int x, int J) { return x >= J ? x - J : x; }
 #define TT_MAX_N 65536    // largest single mode size
 
 struct TtPlan0;
@@ -48,7 +51,7 @@ struct tt_ctx {
   int d = 0;
   int64_t n[TT_MAX_D] = {0};
   int r[TT_MAX_D + 1] = {0};
-  int J = 0, logJ = 0;
+  int J = 0, logJ = 0;  // logJ = -1 when J is not a power of two
   double lambda = 0.0;
   uint64_t seed = 0;
   int dtype = TT_F32;

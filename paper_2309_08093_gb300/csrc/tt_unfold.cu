@@ -319,7 +319,7 @@ __global__ void __launch_bounds__(256, 2) k_unfold_gather(GArgs a) {
                 }
               } else {
 #pragma unroll
-                for (int e = 0; e < EPV; ++e) atomicAdd(Ys + ((cv + h0r[mm][e]) & (J - 1)), coefr[mm][e] * acc[mm][e]);
+                for (int e = 0; e < EPV; ++e) atomicAdd(Ys + tt_modj(cv + h0r[mm][e], J), coefr[mm][e] * acc[mm][e]);
               }
             }
 #pragma unroll
@@ -512,7 +512,7 @@ __global__ void __launch_bounds__(256, 2) k_unfold_cols(GArgs a) {
           if (vok[m]) {
             float* yc = Ys + (size_t)vg[m] * J;
 #pragma unroll
-            for (int e = 0; e < EPV; ++e) atomicAdd(yc + ((cv + h0r[m][e]) & (J - 1)), coefr[m][e] * acc[m][e]);
+            for (int e = 0; e < EPV; ++e) atomicAdd(yc + tt_modj(cv + h0r[m][e], J), coefr[m][e] * acc[m][e]);
           }
 #pragma unroll
           for (int e = 0; e < EPV; ++e) acc[m][e] = 0.f;

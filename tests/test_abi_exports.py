@@ -63,7 +63,8 @@ def test_init_rejects_bad_parameters(libpath):
         ctx = ctypes.c_void_p()
         return L.tt_sketch_init(ctypes.byref(ctx), ctypes.byref(p), None)
 
-    assert init((4, 5, 6), (1, 2, 2, 1), 12) == lib.TT_EINVAL       # J not a power of two
+    assert init((4, 5, 6), (1, 2, 2, 1), 12000) == lib.TT_EINVAL    # above 8192, not a power of two
+    assert init((4, 5, 6), (1, 2, 2, 1), 1) == lib.TT_EINVAL        # J < 2
     assert init((4, 5, 6), (1, 2, 2, 1), 32768) == lib.TT_EINVAL    # J too large
     assert init((4, 5, 6), (2, 2, 2, 1), 16) == lib.TT_EINVAL       # r[0] != 1
     assert init((4,), (1, 1), 16) == lib.TT_EINVAL                  # d < 2

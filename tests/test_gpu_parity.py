@@ -51,7 +51,9 @@ def split_tables(h, v, dims):
                                                ((100, 100, 100, 100), 4096, 7, 19),
                                                ((3, 1, 7), 2, 2**63 + 5, 3),
                                                ((40,) * 5, 8192, 123, 2**40 + 1),
-                                               ((256, 256, 3, 128), 16384, 0, 0)])
+                                               ((256, 256, 3, 128), 16384, 0, 0),
+                                               ((50, 50, 50), 150, 11, 2), ((40,) * 4, 2000, 5, 1),
+                                               ((3, 1, 7), 3, 9, 0), ((10,) * 6, 45, 2**62 + 1, 7)])
 def test_tables_bit_exact(dims, J, seed, sweep):
     ranks = (1,) + (1,) * (len(dims) - 1) + (1,)
     ctx = lib.Context(dims, ranks, J, 1e-3, seed, "f32")
@@ -95,7 +97,10 @@ def test_worked_example_on_gpu():
 CASES_A = [((7, 5, 9), 64, "f32"), ((3, 5, 7, 2), 16, "f32"), ((50, 50, 50), 1024, "f64"),
            ((33, 17, 9, 5), 512, "bf16"), ((40, 12, 10, 6), 256, "fp8"), ((64, 3, 1, 20), 128, "f32"),
            ((1, 6, 8), 32, "f32"), ((100, 30, 20), 4096, "f32"), ((130, 7, 11), 2, "f32"),
-           ((300, 4, 5), 16384, "bf16"), ((12, 10, 8, 6, 4), 8192, "bf16"), ((41, 23, 6), 256, "f32")]
+           ((300, 4, 5), 16384, "bf16"), ((12, 10, 8, 6, 4), 8192, "bf16"), ((41, 23, 6), 256, "f32"),
+           # sketch sizes that are not powers of two (the paper's m of Sec. 5)
+           ((7, 5, 9), 45, "f32"), ((20, 18, 16), 150, "bf16"), ((16, 12, 10, 8), 1000, "f32"),
+           ((33, 17, 9, 5), 200, "fp8"), ((12, 10, 8), 2000, "f64"), ((10,) * 6, 45, "f32")]
 
 
 def _data(dims, storage, seed):
@@ -149,7 +154,11 @@ def test_unfold_sketch_rejects_bad_calls():
 CASES_B = [((6, 5, 7), (1, 2, 3, 1), 32), ((4, 3, 5, 6), (1, 3, 4, 2, 1), 64), ((9, 8), (1, 4, 1), 16),
            ((20, 30, 25, 10), (1, 4, 5, 3, 1), 256), ((50, 50, 50), (1, 5, 5, 1), 1024),
            ((10, 12, 3, 9), (1, 8, 3, 8, 1), 2048), ((7, 7, 7, 7, 7), (1, 3, 3, 3, 3, 1), 4096),
-           ((5, 6, 4), (1, 2, 2, 1), 2), ((30, 20, 10), (1, 12, 10, 1), 16384)]
+           ((5, 6, 4), (1, 2, 2, 1), 2), ((30, 20, 10), (1, 12, 10, 1), 16384),
+           # sketch sizes that are not powers of two: direct DFTs
+           ((6, 5, 7), (1, 2, 3, 1), 45), ((10, 12, 3, 9), (1, 8, 3, 8, 1), 2000),
+           ((20, 30, 25, 10), (1, 4, 5, 3, 1), 150), ((9, 8), (1, 4, 1), 3), ((50, 50, 50), (1, 5, 5, 1), 1000),
+           ((10,) * 6, (1, 5, 5, 5, 5, 5, 1), 200)]
 
 
 @pytest.mark.parametrize("dims,ranks,J", CASES_B)
@@ -177,7 +186,8 @@ def test_interface_sketch_parity(dims, ranks, J):
 
 @pytest.mark.parametrize("J,n,r0,r1,sigma", [(256, 7, 3, 4, 1e-3), (4096, 100, 10, 10, 1e-3), (2048, 256, 1, 20, 0.5),
                                              (1024, 50, 5, 5, 0.0), (8192, 40, 8, 8, 1e-3), (512, 128, 12, 12, 1e-3),
-                                             (64, 3, 1, 1, 2.0)])
+                                             (64, 3, 1, 1, 2.0), (45, 7, 3, 4, 1e-3), (1000, 100, 10, 10, 1e-3),
+                                             (150, 10, 5, 5, 1e-3)])
 def test_prox_update_parity(J, n, r0, r1, sigma):
     rng = np.random.default_rng(J + n)
     s = r0 * r1
@@ -318,6 +328,40 @@ def test_sweeps_scaled_order4_parity():
     p, got, err, changes, ref, ref_changes = _run_sweeps(w, "f32", 4)
     err_ref = O.rel_error(p.tensor, ref)
     assert abs(err - err_ref) <= 1e-5 * err_ref, (err, err_ref)
+
+
+@pytest.mark.parametrize("dims,ranks,J,nsw", [((10,) * 6, (1, 5, 5, 5, 5, 5, 1), 45, 1),
+                                              ((10,) * 6, (1, 5, 5, 5, 5, 5, 1), 150, 1),
+                                              ((30, 28, 26), (1, 4, 4, 1), 200, 3), ((12, 10, 8), (1, 3, 3, 1), 1000, 3)])
+def test_sweeps_non_power_of_two_sketch_sizes(dims, ranks, J, nsw):
+    """Whole sweeps at sketch sizes that are not powers of two, among them the shape of the
+    paper's first synthetic experiment (order 6, n = 10, ranks 5, m = 45 and 150; Sec. 5). With
+    25 unknowns per core and 45 or 150 sketch rows the iteration is far from converged and
+    amplifies rounding: the FP64 oracle itself moves its result after one sweep by 69x (m = 45)
+    and 12x (m = 150) a 1e-7 relative perturbation of the initial cores, and after three sweeps
+    by 2.3e5x and 650x. So the order-6 cases take one sweep, and the bound on the reconstructed
+    tensor is 1e-4 plus the oracle's own change under a 1e-6 perturbation (about ten FP32 ulps);
+    the relative error of the GPU's cores keeps 1e-5."""
+    cores = synth.random_tt(dims, ranks, 3)
+    a = synth.add_noise(synth.contract_cores(cores), 1e-2, np.random.default_rng(8))
+    flat, _, exact = synth.quantize(a, "f32")
+    init = synth.random_tt(dims, ranks, 9)
+    ctx = lib.Context(dims, ranks, J, 1e-3, 31, "f32")
+    A = lib.device_tensor(flat, "f32")
+    dc = lib.device_cores(init)
+    ctx.tt_prox_als_sweep(A, dc, nsw, 0, rel_change=False)
+    err = ctx.tt_rel_error(A, dc)
+    got = lib.host_cores(dc, ranks, dims)
+    ctx.close()
+    ref, _ = O.tt_ts(exact, init, 31, J, 1e-3, nsw)
+    xi = np.random.default_rng(1)
+    pert = [g * (1.0 + 1e-6 * xi.standard_normal(g.shape)) for g in init]
+    ref_p, _ = O.tt_ts(exact, pert, 31, J, 1e-3, nsw)
+    full_ref = O.tt_full(ref)
+    tol = 1e-4 + rel(O.tt_full(ref_p), full_ref)
+    assert rel(O.tt_full(got), full_ref) <= tol, (rel(O.tt_full(got), full_ref), tol)
+    e_ref = O.rel_error(exact, [np.asarray(g, np.float32).astype(np.float64) for g in got])
+    assert abs(err - e_ref) <= 1e-5 * e_ref, (err, e_ref)
 
 
 def test_monitored_sweeps_match_separate_calls():
