@@ -27,11 +27,12 @@ the oracle's (1e-4 per core, error 1e-5), then the right-canonical gauge of the 
 their packed targets against the warm-start oracle (1e-4 per core relative to its norm, 1e-5).
 
 Batched workload (256 tensors of order 3-4, modes 16-128, ranks 4-12, FP32 and BF16 storage,
-12.2 GB): two batched sweeps (the capture and one graph replay, the launch the benchmark times)
-against the single-tensor path on every tensor (relative error; the two differ only by FP32
-summation order, which unconverged sweeps amplify: 1e-4 + 1e-7), and against the oracle's two
-sweeps on the three smallest tensors and the median one (the reconstructed tensor, 1e-4; the
-relative error of the same cores, 1e-5 + 1e-7).
+12.2 GB): ten batched sweeps (the capture and nine graph replays, as the benchmark times them),
+converged to the noise floor, against the single-tensor path on every tensor (relative error; the
+two differ only by FP32 summation order: 1e-4 + 1e-7; after two unconverged sweeps that order
+alone moved tensor 0 by 1.1e-4), and against the oracle's ten sweeps on the three smallest
+tensors and the median one (the reconstructed tensor, 1e-4; the relative error of the same cores,
+1e-5 + 1e-7).
 """
 import numpy as np
 import pytest
@@ -199,14 +200,14 @@ def test_full_size_batched_workload():
     cores_b = [lib.device_cores(c) for c in inits]
     batch = lib.Batch(specs)
     batch.tt_batch_sweep(As, cores_b, 1, 0)  # autotune, capture, first sweep
-    batch.tt_batch_sweep(As, cores_b, 1, 1)  # graph replay
+    batch.tt_batch_sweep(As, cores_b, 9, 1)  # graph replays
     errs_b = batch.tt_batch_rel_error(As, cores_b)
     batch.close()
     bad = []
     for i, sp in enumerate(specs):
         ctx = lib.Context(sp["dims"], sp["ranks"], sp["J"], sp["lam"], sp["seed"], sp["dtype"])
         cs = lib.device_cores(inits[i])
-        ctx.tt_prox_als_sweep(As[i], cs, 2, 0, rel_change=False)
+        ctx.tt_prox_als_sweep(As[i], cs, 10, 0, rel_change=False)
         e = ctx.tt_rel_error(As[i], cs)
         ctx.close()
         if not abs(errs_b[i] - e) <= 1e-4 * e + 1e-7:
@@ -217,7 +218,7 @@ def test_full_size_batched_workload():
     for i in order[:3] + [order[len(order) // 2]]:
         sp = specs[i]
         exact = As[i].float().cpu().numpy().astype(np.float64).reshape(sp["dims"], order="F")
-        ref, _ = O.tt_ts(exact, inits[i], sp["seed"], sp["J"], sp["lam"], 2)
+        ref, _ = O.tt_ts(exact, inits[i], sp["seed"], sp["J"], sp["lam"], 10)
         got = [np.asarray(g, np.float32).astype(np.float64)
                for g in lib.host_cores(cores_b[i], sp["ranks"], sp["dims"])]
         assert rel(O.tt_full(got), O.tt_full(ref)) <= 1e-4, (i, sp["dims"], sp["ranks"])
