@@ -233,6 +233,27 @@ def sketch_unfolding_column(A: np.ndarray, hs, vs, J: int, k: int, ik: int) -> n
     return np.bincount(bucket.ravel(), weights=(sign * sub).ravel(), minlength=J)
 
 
+def sketch_unfolding_coo(idx: np.ndarray, vals: np.ndarray, dims: Sequence[int], hs, vs, J: int,
+                         k: int) -> np.ndarray:
+    """Y_k = S A_(k)^T for a sparse A given as coordinates (Sec. 3, the discussion after Theorem
+    3: for sparse A the sketch of the unfolding costs O(nnz)). idx is d x nnz (0-based indices,
+    idx[s, e] = i_s of entry e), vals the nnz values; repeated coordinates add up. Entry e adds
+    prod_{s != k} v_s(i_s) * val_e to Y_k[(sum_{s != k} h_s(i_s)) mod J, i_k], which is the
+    definition of Eqs. (eqn_h), (eqn_v) restricted to the nonzeros."""
+    d = len(dims)
+    idx = np.asarray(idx, dtype=np.int64)
+    vals = np.asarray(vals, dtype=np.float64)
+    bucket = np.zeros(vals.shape[0], dtype=np.int64)
+    sign = np.ones(vals.shape[0])
+    for s in range(d):
+        if s != k:
+            bucket += hs[s][idx[s]]
+            sign *= vs[s][idx[s]]
+    Y = np.zeros((J, dims[k]))
+    np.add.at(Y, (bucket % J, idx[k]), sign * vals)
+    return Y
+
+
 def sketch_unfolding(A: np.ndarray, hs, vs, J: int, k: int) -> np.ndarray:
     """Y_k = S A_(k)^T (J x n_k), every column by its definition (Alg. 1, 'compute S A_(k)^T')."""
     return np.stack([sketch_unfolding_column(A, hs, vs, J, k, i) for i in range(A.shape[k])], axis=1)

@@ -180,6 +180,27 @@ def test_data_sketch_definition_vs_dense(dims, J):
         assert np.allclose(Y, O.sketch_unfolding_dense(A, hs, vs, J, k), atol=1e-13)
 
 
+@pytest.mark.parametrize("dims,J,density", [((5, 4, 6), 8, 0.3), ((3, 4, 2, 5), 45, 0.2), ((6, 7), 16, 1.0)])
+def test_coo_sketch_equals_dense_definition(dims, J, density):
+    """The coordinate form on the nonzeros of a sparse tensor (with repeated coordinates, whose
+    values add up) equals the dense definition on the densified tensor, and an empty list gives 0."""
+    rng = _rng(len(dims) * 7 + J)
+    hs, vs = _rand_tables(rng, dims, J)
+    A = synth.random_tensor(dims, J) * (rng.random(dims) < density)
+    nz = np.nonzero(A)
+    idx = np.stack(nz)
+    vals = A[nz]
+    # split every value into two repeated coordinates
+    idx2 = np.concatenate([idx, idx], axis=1)
+    vals2 = np.concatenate([0.25 * vals, 0.75 * vals])
+    for k in range(len(dims)):
+        dense = O.sketch_unfolding(A, hs, vs, J, k)
+        assert np.allclose(O.sketch_unfolding_coo(idx, vals, dims, hs, vs, J, k), dense, atol=1e-13)
+        assert np.allclose(O.sketch_unfolding_coo(idx2, vals2, dims, hs, vs, J, k), dense, atol=1e-13)
+        empty = O.sketch_unfolding_coo(np.zeros((len(dims), 0), np.int64), np.zeros(0), dims, hs, vs, J, k)
+        assert empty.shape == (J, dims[k]) and not empty.any()
+
+
 def test_data_sketch_injective_hash_is_a_transpose():
     """With J = n_2, h_2 a permutation and v = +1, S is a permutation and Y_1 = P A^T."""
     A = synth.random_tensor((6, 7), 11)
