@@ -119,6 +119,21 @@ int tt_sketch_unfold(tt_ctx* ctx, const void* A_dev, const float* scales_dev, in
                      uint64_t sweep, float* const* Y_dev);
 
 /*
+ * Part (a) for a sparse tensor in coordinate form, at O(nnz) cost (Sec. 3, the discussion after
+ * Theorem 3). The context's dtype is not used: values are FP32.
+ *   idx_dev : device int32 array of d x nnz indices, mode-major: idx_dev[s*nnz + e] = i_s of
+ *             entry e (0-based);
+ *   val_dev : device FP32 array of the nnz values; repeated coordinates add up;
+ *   nnz     : number of entries (>= 0; idx_dev and val_dev may be NULL when it is 0);
+ *   k, sweep, Y_dev : as tt_sketch_unfold (each requested Y_k is zeroed, then accumulated).
+ * Entries with an index outside [0, n[s]) are skipped and the call returns TT_EINVAL. The call
+ * reads the device status back, so it synchronises. Followed by tt_prox_als_sweep_sketched with
+ * the same sweep, it gives a sweep of Algorithm 1 on the sparse tensor.
+ */
+int tt_sketch_unfold_coo(tt_ctx* ctx, const int32_t* idx_dev, const float* val_dev, int64_t nnz,
+                         int k, uint64_t sweep, float* const* Y_dev);
+
+/*
  * Part (b): S H_k with H_k = G_{>k}^T kron G_{<k}, computed as
  * F^{-1}[(F S_{>k} G_{>k}^T) face-split (F S_{<k} G_{<k})] (Theorem 1) with the two factors
  * formed by slice-wise products of the FFT-sketched cores (Theorem 2).

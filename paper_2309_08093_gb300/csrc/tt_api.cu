@@ -50,6 +50,24 @@ extern "C" int tt_sketch_unfold(tt_ctx* c, const void* A, const float* scales, i
   return TT_OK;
 }
 
+extern "C" int tt_sketch_unfold_coo(tt_ctx* c, const int32_t* idx, const float* val, int64_t nnz, int k,
+                                    uint64_t sweep, float* const* Y) {
+  if (!c) return TT_EINVAL;
+  if (nnz < 0) return tt_fail(c, TT_EINVAL, "nnz < 0");
+  if (nnz > 0 && (!idx || !val)) return tt_fail(c, TT_EINVAL, "null coordinates or values");
+  if (!Y) return tt_fail(c, TT_EINVAL, "null output array");
+  if (k < -1 || k >= c->d) return tt_fail(c, TT_EINVAL, "mode %d outside [-1, %d)", k, c->d);
+  for (int kk = 0; kk < c->d; ++kk)
+    if ((k == -1 || k == kk) && !Y[kk]) return tt_fail(c, TT_EINVAL, "null output for mode %d", kk);
+  c->err.clear();
+  TT_TRY(tt_ensure_tables(c, sweep));
+  TT_TRY(tt_reset_status(c));
+  TT_TRY(tt_launch_unfold_coo(c, idx, val, nnz, k, Y));
+  const int rc = tt_read_status(c);  // synchronises
+  if (rc == TT_EINVAL) return tt_fail(c, TT_EINVAL, "a coordinate lies outside its mode size (entry skipped)");
+  return rc;
+}
+
 static int build_all_ghat(tt_ctx* c, float* const* cores) { return tt_launch_core_ffts(c, cores); }
 
 extern "C" int tt_sketch_interface(tt_ctx* c, float* const* cores, int k, uint64_t sweep, float* SH) {

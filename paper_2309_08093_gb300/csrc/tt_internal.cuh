@@ -198,6 +198,7 @@ int tt_ensure_rplan(tt_ctx* c, int k);
 
 // kernels' host entry points (one translation unit each)
 int tt_launch_unfold(tt_ctx* c, const void* A, const float* scales, int k, float* Y);
+int tt_launch_unfold_coo(tt_ctx* c, const int32_t* idx, const float* val, int64_t nnz, int k, float* const* Y);
 int tt_launch_core_fft(tt_ctx* c, const float* core, int j);
 int tt_launch_core_ffts(tt_ctx* c, float* const* cores);  // all d cores, one launch
 int tt_launch_suffixes(tt_ctx* c);

@@ -783,6 +783,94 @@ static int unfold_dt(tt_ctx* c, const void* A, const float* scales, int k, float
   return launch_gather<DT, false>(c, A, scales, k, Y);
 }
 
+// ---------------------------------------------------------------------------------------------
+// sparse tensors in coordinate form (Sec. 3, the discussion after Theorem 3: for sparse A the
+// sketch of the unfolding costs O(nnz)). Entry e, with indices i_s = idx[s nnz + e] and value
+// val[e], adds prod_{s != k} v_s(i_s) val[e] to Y_k[(sum_{s != k} h_s(i_s)) mod J, i_k] for every
+// requested mode k. One thread per entry (grid-stride): the index loads of a warp are coalesced
+// (mode-major indices), the hash and sign lookups hit the small per-mode tables, and the adds are
+// FP32 atomics into the J x n_k sketches (L2-resident at the sizes of interest). The per-mode
+// values live in registers: the loops over modes run to TT_MAX_D with a predicate. An index
+// outside [0, n_s) skips its entry and raises TT_EINVAL in the device status.
+
+struct CooArgs {
+  const int32_t* idx;
+  const float* val;
+  int64_t nnz;
+  int d, J;
+  const int32_t* h;
+  const int8_t* v;
+  int64_t noff[TT_MAX_D + 1];
+  int64_t n[TT_MAX_D];
+  float* Y[TT_MAX_D];  // null: mode not requested
+  int* status;
+};
+
+__global__ void __launch_bounds__(256) k_unfold_coo(CooArgs a) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < a.nnz; e += (int64_t)gridDim.x * blockDim.x) {
+    int ii[TT_MAX_D], hh[TT_MAX_D];
+    bool ng[TT_MAX_D];
+    int H = 0;
+    bool neg = false, bad = false;
+#pragma unroll
+    for (int s = 0; s < TT_MAX_D; ++s) {
+      ii[s] = 0;
+      hh[s] = 0;
+      ng[s] = false;
+      if (s < a.d) {
+        const int i = __ldg(a.idx + (int64_t)s * a.nnz + e);
+        if (i < 0 || i >= a.n[s]) {
+          bad = true;
+        } else {
+          ii[s] = i;
+          hh[s] = __ldg(a.h + a.noff[s] + i);
+          ng[s] = __ldg(a.v + a.noff[s] + i) < 0;
+          H += hh[s];
+          neg ^= ng[s];
+        }
+      }
+    }
+    if (bad) {
+      atomicCAS(a.status, 0, TT_EINVAL);
+      continue;
+    }
+    const float x = __ldg(a.val + e);
+#pragma unroll
+    for (int k = 0; k < TT_MAX_D; ++k) {
+      if (k < a.d && a.Y[k]) {
+        int b = H - hh[k];  // sum over s != k: below (d - 1) J
+        while (b >= a.J) b -= a.J;
+        atomicAdd(a.Y[k] + b + (int64_t)a.J * ii[k], (neg != ng[k]) ? -x : x);
+      }
+    }
+  }
+}
+
+int tt_launch_unfold_coo(tt_ctx* c, const int32_t* idx, const float* val, int64_t nnz, int k, float* const* Y) {
+  CooArgs a;
+  a.idx = idx;
+  a.val = val;
+  a.nnz = nnz;
+  a.d = c->d;
+  a.J = c->J;
+  a.h = c->d_h;
+  a.v = c->d_v;
+  a.status = c->d_status;
+  for (int s = 0; s <= c->d; ++s) a.noff[s] = c->noff[s];
+  for (int s = 0; s < TT_MAX_D; ++s) {
+    a.n[s] = s < c->d ? c->n[s] : 1;
+    a.Y[s] = (s < c->d && (k == -1 || k == s)) ? Y[s] : nullptr;
+    if (a.Y[s]) TT_CUDA(c, cudaMemsetAsync(a.Y[s], 0, sizeof(float) * (size_t)c->J * c->n[s], c->stream));
+  }
+  if (nnz == 0) return TT_OK;
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+  const int64_t blocks = std::min<int64_t>((nnz + 255) / 256, (int64_t)sms * 8);
+  k_unfold_coo<<<(int)blocks, 256, 0, c->stream>>>(a);
+  TT_LAUNCH(c, "k_unfold_coo");
+  return TT_OK;
+}
+
 int tt_launch_unfold(tt_ctx* c, const void* A, const float* scales, int k, float* Y) {
   int rc = tt_ensure_rplan(c, k);  // plan build is not part of the timed kernel
   if (rc) return rc;

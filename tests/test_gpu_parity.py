@@ -135,6 +135,85 @@ def test_unfold_sketch_parity(dims, J, storage):
     ctx.close()
 
 
+@pytest.mark.parametrize("dims,J,density", [((30, 20, 10), 1024, 0.05), ((12, 10, 8, 6), 150, 0.2),
+                                            ((100, 100, 100), 4096, 0.01), ((9, 8, 7, 6, 5), 45, 0.1)])
+def test_unfold_coo_parity(dims, J, density):
+    """Sparse tensors in coordinate form (with repeated coordinates) against the oracle's dense
+    definition on the densified tensor, every mode and one mode alone; an empty list gives zeros."""
+    seed = 300 + J
+    rng = np.random.default_rng(seed)
+    A = synth.random_tensor(dims, seed) * (rng.random(dims) < density)
+    A = np.asarray(A, np.float32).astype(np.float64)
+    nz = np.nonzero(A)
+    idx = np.stack(nz).astype(np.int32)
+    vals = A[nz]
+    half = idx.shape[1] // 2  # the first half of the entries repeated with their value split
+    idx2 = np.concatenate([idx, idx[:, :half]], axis=1)
+    vals2 = np.concatenate([np.where(np.arange(vals.size) < half, 0.5 * vals, vals), 0.5 * vals[:half]])
+    nnz = idx2.shape[1]
+    perm = rng.permutation(nnz)  # arbitrary entry order
+    idx_d = torch.from_numpy(np.ascontiguousarray(idx2[:, perm])).cuda()
+    val_d = torch.from_numpy(vals2[perm].astype(np.float32)).cuda()
+    ranks = (1,) * (len(dims) + 1)
+    ctx = lib.Context(dims, ranks, J, 1e-3, seed, "f32")
+    Y = [torch.full((J * n,), 7.0, device="cuda") for n in dims]  # overwritten
+    ctx.tt_sketch_unfold_coo(idx_d, val_d, nnz, -1, 2, Y)
+    hs, vs = O.draw_sketch(seed, 2, dims, J)
+    for k in range(len(dims)):
+        got = Y[k].cpu().numpy().reshape(dims[k], J).T
+        ref = O.sketch_unfolding(A, hs, vs, J, k)
+        assert rel(got, ref) <= TOL, (k, rel(got, ref))
+    Y1 = [None] * len(dims)
+    Y1[1] = torch.zeros(J * dims[1], device="cuda")
+    ctx.tt_sketch_unfold_coo(idx_d, val_d, nnz, 1, 2, Y1)
+    assert rel(Y1[1].cpu().numpy().reshape(dims[1], J).T, O.sketch_unfolding(A, hs, vs, J, 1)) <= TOL
+    Y[0].fill_(3.0)
+    ctx.tt_sketch_unfold_coo(None, None, 0, 0, 2, Y)
+    assert not Y[0].any()
+    ctx.close()
+
+
+def test_unfold_coo_rejects_bad_coordinates():
+    dims = (4, 5, 6)
+    ctx = lib.Context(dims, (1, 1, 1, 1), 16, 1e-3, 1, "f32")
+    Y = [torch.zeros(16 * n, device="cuda") for n in dims]
+    idx = torch.tensor([[0, 3], [1, 5], [2, 0]], dtype=torch.int32, device="cuda")  # i_1 = 5 >= n_1
+    val = torch.ones(2, device="cuda")
+    with pytest.raises(lib.TtError) as e:
+        ctx.tt_sketch_unfold_coo(idx, val, 2, -1, 0, Y)
+    assert e.value.code == lib.TT_EINVAL
+    # the valid entry was still added, the bad one skipped
+    hs, vs = O.draw_sketch(1, 0, dims, 16)
+    A = np.zeros(dims)
+    A[0, 1, 2] = 1.0
+    assert rel(Y[0].cpu().numpy().reshape(dims[0], 16).T, O.sketch_unfolding(A, hs, vs, 16, 0)) <= TOL
+    with pytest.raises(lib.TtError):
+        ctx.tt_sketch_unfold_coo(idx, val, -1, -1, 0, Y)
+    ctx.close()
+
+
+def test_sparse_sweep_equals_dense_sweep():
+    """A sweep on the coordinate-form sketches (tt_sketch_unfold_coo + tt_prox_als_sweep_sketched)
+    equals the ordinary sweep on the densified tensor (the same draw)."""
+    dims, ranks, J = (20, 18, 16, 14), (1, 4, 5, 4, 1), 512
+    rng = np.random.default_rng(5)
+    A = np.asarray(synth.random_tensor(dims, 5) * (rng.random(dims) < 0.1), np.float32)
+    nz = np.nonzero(A)
+    idx_d = torch.from_numpy(np.stack(nz).astype(np.int32)).cuda()
+    val_d = torch.from_numpy(A[nz]).cuda()
+    init = synth.random_tt(dims, ranks, 6)
+    ctx = lib.Context(dims, ranks, J, 1e-3, 77, "f32")
+    c_dense, c_sparse = lib.device_cores(init), lib.device_cores(init)
+    ctx.tt_prox_als_sweep(lib.device_tensor(A.ravel(order="F"), "f32"), c_dense, 1, 4, rel_change=False)
+    Y = [torch.zeros(J * n, device="cuda") for n in dims]
+    ctx.tt_sketch_unfold_coo(idx_d, val_d, idx_d.shape[1], -1, 4, Y)
+    ctx.tt_prox_als_sweep_sketched(Y, c_sparse, 4)
+    a = O.tt_full(lib.host_cores(c_dense, ranks, dims))
+    b = O.tt_full(lib.host_cores(c_sparse, ranks, dims))
+    assert rel(b, a) <= 1e-4, rel(b, a)
+    ctx.close()
+
+
 def test_unfold_sketch_rejects_bad_calls():
     ctx = lib.Context((4, 5, 6), (1, 1, 1, 1), 16, 1e-3, 1, "f32")
     A = torch.zeros(120, device="cuda")
