@@ -357,3 +357,32 @@ def mlp_init(in_dim: int, hidden: int, out_dim: int, seed: int):
     W2 = (rng.standard_normal((hidden, hidden)) * np.sqrt(2.0 / hidden)).astype(f32)
     W3 = (rng.standard_normal((out_dim, hidden)) * np.sqrt(1.0 / hidden)).astype(f32)
     return [W1, np.zeros(hidden, f32), W2, np.zeros(hidden, f32), W3, np.zeros(out_dim, f32)]
+
+
+# ---------------------------------------------------------------------------------------------
+# the paper's synthetic experiments (Sec. 5), formula-generated
+
+def paper_tt_tensor(sd: float, seed: int, dims=(10,) * 6, rank: int = 5):
+    """First synthetic experiment: a sixth-order 10 x ... x 10 tensor in TT format with equal
+    ranks and N(0,1) core entries, plus Gaussian noise of standard deviation sd (absolute).
+    Returns the noisy tensor (Fortran order, float64)."""
+    ranks = (1,) + (rank,) * (len(dims) - 1) + (1,)
+    t = contract_cores(random_tt(dims, ranks, seed))
+    return t + sd * np.random.default_rng([seed, STREAM_NOISE]).standard_normal(t.shape)
+
+
+def paper_function_tensor(name: str, dims=(10,) * 6):
+    """Second experiment: a one-dimensional function sampled at prod(dims) equispaced points and
+    reshaped column-major (first index fastest) into a tensor: 'sinc' = sin(pi x)/(pi x) on
+    [-5, 5] (the normalised sinc of the MATLAB the paper used, numpy's sinc), 'osc' =
+    sin(4/x) cos(x^2) on [0, 1] (first point excluded: x > 0)."""
+    npts = int(np.prod(dims))
+    if name == "sinc":
+        x = np.linspace(-5.0, 5.0, npts)
+        y = np.sinc(x)
+    elif name == "osc":
+        x = np.linspace(0.0, 1.0, npts + 1)[1:]
+        y = np.sin(4.0 / x) * np.cos(x * x)
+    else:
+        raise ValueError(name)
+    return y.reshape(dims, order="F")
