@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-patterns", action="store_true", help="skip the precision/batched/warm-start patterns")
-    ap.add_argument("--only-pattern", default=None, choices=["precision", "batched", "warmstart", "gemm"],
+    ap.add_argument("--only-pattern", default=None, choices=["precision", "batched", "warmstart", "gemm", "sparse"],
                     help="run one pattern and print its JSON")
     ap.add_argument("--ws-train", type=int, default=10240, help="warm-start training solves")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
@@ -368,6 +368,41 @@ def gemm_pattern(dev, reps=10):
     return out
 
 
+def sparse_pattern(dev, nnz=20_000_000, reps=10):
+    """The data sketch of a sparse tensor in coordinate form (tt_sketch_unfold_coo, all four
+    modes) on the 100^4 shape at J = 4096: nnz uniformly random coordinates (20% of the entries,
+    repeats allowed) with N(0,1) values, seeded, device-resident. One draw (fixed sweep index)
+    for all timed calls; each call zeroes the four sketches, runs one kernel and reads the device
+    status back (a synchronisation, inside the timed region)."""
+    import torch
+    from paper_2309_08093_gb300 import lib
+
+    dims, J = (100, 100, 100, 100), 4096
+    g = torch.Generator(device=dev)
+    g.manual_seed(20230921)
+    idx = torch.randint(0, 100, (4, nnz), generator=g, device=dev, dtype=torch.int32)
+    val = torch.randn(nnz, generator=g, device=dev)
+    ctx = lib.Context(dims, (1, 10, 10, 10, 1), J, 1e-3, 5, "f32")
+    Y = [torch.zeros(J * n, device=dev) for n in dims]
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        ctx.tt_sketch_unfold_coo(idx, val, nnz, -1, 3, Y)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        ctx.tt_sketch_unfold_coo(idx, val, nnz, -1, 3, Y)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    ctx.close()
+    in_bytes = nnz * (4 * 4 + 4)
+    return {"shape": "100^4", "nnz": nnz, "J": J, "ms_per_call": ms, "entries_per_s": nnz / (ms * 1e-3),
+            "input_gbs": in_bytes / (ms * 1e-3) / 1e9, "atomic_adds_per_s": 4 * nnz / (ms * 1e-3),
+            "note": "k_unfold_coo: one thread per entry, four FP32 atomics into L2-resident sketches "
+                    "(6.5 MB per mode); input GB/s counts the int32 indices and FP32 values read"}
+
+
 # ---------------------------------------------------------------------------------------------
 # learned-warm-start pattern: the network (summary of the data sketch -> initial cores) trained
 # on method-generated solves of the 256 x 256 x 3 x 128 smooth-core family, then held-out tensors
@@ -543,6 +578,8 @@ def main():
             out = warmstart_pattern(dev, n_train=args.ws_train)
         elif args.only_pattern == "gemm":
             out = gemm_pattern(dev)
+        elif args.only_pattern == "sparse":
+            out = sparse_pattern(dev)
         else:
             w = synth.WORKLOADS[args.workload]
             out = precision_pattern(w, synth.make_problem(w, storage="f32"), dev, w.sweeps)
@@ -684,6 +721,7 @@ def main():
         line["patterns"]["warmstart"] = warmstart_pattern(dev, n_train=args.ws_train)
         torch.cuda.empty_cache()
         line["patterns"]["gemm"] = gemm_pattern(dev)
+        line["patterns"]["sparse"] = sparse_pattern(dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
             res = run_cpu_child(["--workload", args.workload] + (["--storage", args.storage] if args.storage else []))
