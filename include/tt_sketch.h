@@ -70,7 +70,9 @@ typedef struct {
   int d;              /* order of the tensor, 2 <= d <= 8 */
   const int64_t* n;   /* host array of d mode sizes, each >= 1 */
   const int* r;       /* host array of d+1 TT ranks, r[0] = r[d] = 1, each >= 1;
-                         r[k]*r[k+1] <= 160 and r[k]*n[k]*r[k+1] <= 40000 (in-CTA solves) */
+                         each r[k] <= 160, r[k]*r[k+1] <= 512 (up to 160 by Gauss-Jordan in
+                         registers, above by a one-CTA Cholesky needing 4 s (n[k] + 33) bytes of
+                         shared memory <= 227 KB), r[k]*n[k]*r[k+1] <= 40000 (in-CTA QR) */
   int J;              /* sketch size m: 2..8192, or a power of two up to 16384 */
   double lambda;      /* proximal weight sigma >= 0 of Eq. (lrtt_sub_prox) */
   uint64_t seed;      /* seed of the hash/sign draws */

@@ -495,7 +495,10 @@ extern "C" int tt_sketch_init(tt_ctx** out, const tt_params* p, void* stream) {
   }
   for (int k = 0; k < c->d; ++k) {
     int s = c->r[k] * c->r[k + 1];
-    if (s > TT_MAX_S) return bad("r[k]*r[k+1] exceeds 160", s);
+    if (s > TT_MAX_S_LARGE) return bad("r[k]*r[k+1] exceeds 512", s);
+    if (s > TT_MAX_S && (p->n[k] > 100000 || tt_large_solve_smem(s, (int)p->n[k]) > 227 * 1024))
+      return bad("r[k]*r[k+1]*(n[k]+33) too large for the one-CTA Cholesky solve", s);
+    if (p->r[k] > TT_MAX_S) return bad("a TT rank exceeds 160", p->r[k]);
     c->smax = std::max(c->smax, s);
     // QR/LQ working sets (see tt_solve.cu): rows x cols floats in shared memory
     int64_t ql = (int64_t)c->r[k] * c->n[k] * c->r[k + 1];

@@ -22,7 +22,9 @@ __device__ __forceinline__ float2 tt_ffma2(float2 a, float2 b, float2 c) {
 }
 
 #define TT_MAX_D 8
-#define TT_MAX_S 160      // largest r[k]*r[k+1] handled by the dense solve kernels
+#define TT_MAX_S 160      // largest r[k]*r[k+1] of the register solve (and largest single rank)
+#define TT_MAX_S_LARGE 512  // largest r[k]*r[k+1] of the one-CTA Cholesky solve
+size_t tt_large_solve_smem(int s, int n);  // its shared memory for s unknowns, n right-hand sides
 #define TT_MAX_J 16384
 
 // (a + b) mod J for bucket indices a, b < J (any J)

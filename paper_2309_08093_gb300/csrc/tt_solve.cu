@@ -348,6 +348,135 @@ static cudaError_t launch_prox_solve(SolveArgs a, cudaStream_t st) {
   return cudaErrorInvalidValue;  // s above TT_MAX_S, rejected at context creation
 }
 
+// Large systems (TT_MAX_S < s <= TT_MAX_S_LARGE): one CTA of 1024 threads factors
+// M + sigma I = L L^T (Cholesky, right-looking by 32-column panels) and solves for all n
+// right-hand sides. A panel (rows p0..s-1, 32 columns) is staged in shared memory, factored there
+// column by column, written back over the Gram (L2-resident) and applied to the trailing lower
+// triangle; while it is in shared memory it also carries out its part of the forward substitution
+// L Z = B^T + sigma G_c on Z (s x n, shared). The back substitution L^T X^T = Z then walks row
+// blocks of L from the bottom, staged in shared memory. A non-positive or non-finite pivot raises
+// the status (TT_ENOTSPD / TT_ENONFINITE) and leaves the core unchanged. Shared memory:
+// 4 (33 s + s n) bytes.
+constexpr int LS_NB = 32, LS_P = 33;
+__global__ void __launch_bounds__(1024) k_prox_solve_large(SolveArgs a) {
+  extern __shared__ float lsm[];
+  __shared__ int bad;
+  const int s = a.s, n = a.n, r0 = a.r0;
+  const int t = threadIdx.x, T = blockDim.x;
+  float* P = lsm;                       // panel, rows x LS_P
+  float* Z = lsm + (size_t)s * LS_P;    // s x n right-hand sides, then solutions
+  float* M = const_cast<float*>(a.C);   // factored in place (recomputed by every update)
+  const float* BT = a.C + (size_t)s * s;
+  const float sigma = (float)a.sigma;
+  if (*a.status != 0) return;
+  if (t == 0) bad = 0;
+  for (int e = t; e < s * n; e += T) {  // Z = B^T + sigma G_c
+    const int i = e / n, r = e - i * n;
+    const int be = i / r0, al = i - be * r0;
+    Z[e] = fmaf(sigma, a.core[al + (int64_t)r0 * (r + (int64_t)n * be)], BT[e]);
+  }
+  __syncthreads();
+  for (int p0 = 0; p0 < s; p0 += LS_NB) {
+    const int pb = min(LS_NB, s - p0), rows = s - p0;
+    for (int e = t; e < rows * LS_NB; e += T) {
+      const int i = e / LS_NB, c = e - i * LS_NB;
+      float v = 0.f;
+      if (c < pb && i >= c) v = M[(size_t)(p0 + i) * s + p0 + c] + (i == c ? sigma : 0.f);
+      P[i * LS_P + c] = v;
+    }
+    __syncthreads();
+    for (int c = 0; c < pb; ++c) {
+      const float d = P[c * LS_P + c];
+      if (!(d > 0.f) || !isfinite(d)) {
+        if (t == 0) bad = isfinite(d) ? TT_ENOTSPD : TT_ENONFINITE;
+        break;  // every thread reads the same d
+      }
+      const float l = sqrtf(d), il = 1.f / l;
+      __syncthreads();  // everyone has read d before column c changes
+      for (int i = c + t; i < rows; i += T) P[i * LS_P + c] = i == c ? l : P[i * LS_P + c] * il;
+      __syncthreads();
+      for (int e = t; e < rows * LS_NB; e += T) {  // the panel's columns right of c
+        const int i = e / LS_NB, c2 = e - i * LS_NB;
+        if (c2 > c && c2 < pb && i >= c2) P[i * LS_P + c2] = fmaf(-P[i * LS_P + c], P[c2 * LS_P + c], P[i * LS_P + c2]);
+      }
+      // forward substitution of this column: Z[p0 + c] /= l, then the rows below it
+      for (int r = t; r < n; r += T) Z[(size_t)(p0 + c) * n + r] *= il;
+      __syncthreads();
+      for (int e = t; e < (rows - c - 1) * n; e += T) {
+        const int i = c + 1 + e / n, r = e % n;
+        Z[(size_t)(p0 + i) * n + r] = fmaf(-P[i * LS_P + c], Z[(size_t)(p0 + c) * n + r], Z[(size_t)(p0 + i) * n + r]);
+      }
+      __syncthreads();
+    }
+    __syncthreads();
+    if (bad) break;  // read after a barrier: the same value in every thread
+    for (int e = t; e < rows * LS_NB; e += T) {  // L back over the Gram
+      const int i = e / LS_NB, c = e - i * LS_NB;
+      if (c < pb && i >= c) M[(size_t)(p0 + i) * s + p0 + c] = P[i * LS_P + c];
+    }
+    const int tr = rows - pb;  // trailing lower triangle: M[i][k] -= sum_c L[i][c] L[k][c]
+    for (int e = t; e < tr * tr; e += T) {
+      const int i = e / tr, kk = e - i * tr;
+      if (kk > i) continue;
+      const float* pi = P + (pb + i) * LS_P;
+      const float* pk = P + (pb + kk) * LS_P;
+      float acc = 0.f;
+      for (int c = 0; c < pb; ++c) acc = fmaf(pi[c], pk[c], acc);
+      float* m = M + (size_t)(p0 + pb + i) * s + p0 + pb + kk;
+      *m -= acc;
+    }
+    __syncthreads();
+  }
+  if (bad) {
+    if (t == 0) atomicCAS(a.status, 0, bad);
+    return;
+  }
+  // back substitution L^T X^T = Z, row blocks of L from the bottom (rows b0..b0+pb-1, columns
+  // 0..b0+pb-1 staged as pb x (b0 + pb))
+  for (int b0 = ((s - 1) / LS_NB) * LS_NB; b0 >= 0; b0 -= LS_NB) {
+    const int pb = min(LS_NB, s - b0), w = b0 + pb;
+    for (int e = t; e < pb * w; e += T) {
+      const int j = e / w, i = e - j * w;
+      P[e] = i <= b0 + j ? M[(size_t)(b0 + j) * s + i] : 0.f;
+    }
+    __syncthreads();
+    for (int j = pb - 1; j >= 0; --j) {
+      const float* Lj = P + (size_t)j * w;  // row b0 + j of L
+      const float il = 1.f / Lj[b0 + j];
+      for (int r = t; r < n; r += T) Z[(size_t)(b0 + j) * n + r] *= il;
+      __syncthreads();
+      for (int e = t; e < (b0 + j) * n; e += T) {
+        const int i = e / n, r = e - i * n;
+        Z[e] = fmaf(-Lj[i], Z[(size_t)(b0 + j) * n + r], Z[e]);
+      }
+      __syncthreads();
+    }
+  }
+  // the update into the core, with the change sums against the proximal centre
+  float dsum = 0.f, nsum = 0.f;
+  for (int e = t; e < s * n; e += T) {
+    const int i = e / n, r = e - i * n;
+    const int be = i / r0, al = i - be * r0;
+    float* g = a.core + al + (int64_t)r0 * (r + (int64_t)n * be);
+    const float nw = Z[e], dd = nw - *g;
+    dsum = fmaf(dd, dd, dsum);
+    nsum = fmaf(nw, nw, nsum);
+    *g = nw;
+  }
+  if (a.change) {
+    for (int o = 16; o > 0; o >>= 1) {
+      dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
+      nsum += __shfl_xor_sync(0xffffffffu, nsum, o);
+    }
+    if ((t & 31) == 0) {
+      atomicAdd(a.change, (double)dsum);
+      atomicAdd(a.change + 1, (double)nsum);
+    }
+  }
+}
+
+size_t tt_large_solve_smem(int s, int n) { return sizeof(float) * ((size_t)s * LS_P + (size_t)s * n); }
+
 int tt_launch_prox_update(tt_ctx* c, const float* Y, const float* SH, float* core, int k,
                           double* change_slot, bool gram_zeroed) {
   const int s = c->r[k] * c->r[k + 1];
@@ -373,6 +502,13 @@ int tt_launch_prox_update(tt_ctx* c, const float* Y, const float* SH, float* cor
   a.r0 = c->r[k];
   a.r1 = c->r[k + 1];
   if (change_slot) TT_CUDA(c, cudaMemsetAsync(change_slot, 0, 2 * sizeof(double), c->stream));
+  if (s > TT_MAX_S) {  // Cholesky in one CTA (sizes checked at context creation)
+    const size_t smem = tt_large_solve_smem(s, n);
+    TT_CUDA(c, cudaFuncSetAttribute(k_prox_solve_large, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_prox_solve_large<<<1, 1024, smem, c->stream>>>(a);
+    TT_LAUNCH(c, "k_prox_solve_large");
+    return TT_OK;
+  }
   TT_CUDA(c, launch_prox_solve(a, c->stream));
   TT_LAUNCH(c, "k_prox_solve");
   return TT_OK;

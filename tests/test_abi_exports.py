@@ -70,4 +70,6 @@ def test_init_rejects_bad_parameters(libpath):
     assert init((4,), (1, 1), 16) == lib.TT_EINVAL                  # d < 2
     assert init((4, 5, 6), (1, 2, 2, 1), 16, lam=-1.0) == lib.TT_EINVAL
     assert init((4, 5, 6), (1, 2, 2, 1), 16, dtype=7) == lib.TT_EINVAL
-    assert init((4, 5, 6), (1, 20, 20, 1), 16) == lib.TT_EINVAL     # r_k r_{k+1} > 160
+    assert init((4, 5, 6), (1, 30, 20, 1), 16) == lib.TT_EINVAL     # r_k r_{k+1} > 512
+    assert init((4, 500, 6), (1, 4, 100, 1), 16) == lib.TT_EINVAL   # s = 400 with n = 500: no room
+    assert init((200, 5, 6), (1, 200, 2, 1), 16) == lib.TT_EINVAL   # a rank above 160

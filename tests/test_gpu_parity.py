@@ -266,7 +266,9 @@ def test_interface_sketch_parity(dims, ranks, J):
 @pytest.mark.parametrize("J,n,r0,r1,sigma", [(256, 7, 3, 4, 1e-3), (4096, 100, 10, 10, 1e-3), (2048, 256, 1, 20, 0.5),
                                              (1024, 50, 5, 5, 0.0), (8192, 40, 8, 8, 1e-3), (512, 128, 12, 12, 1e-3),
                                              (64, 3, 1, 1, 2.0), (45, 7, 3, 4, 1e-3), (1000, 100, 10, 10, 1e-3),
-                                             (150, 10, 5, 5, 1e-3)])
+                                             (150, 10, 5, 5, 1e-3),
+                                             # s > 160: the one-CTA Cholesky solve
+                                             (2048, 10, 20, 20, 0.5), (1024, 30, 12, 16, 1e-3), (4096, 50, 16, 30, 1e-3)])
 def test_prox_update_parity(J, n, r0, r1, sigma):
     rng = np.random.default_rng(J + n)
     s = r0 * r1
@@ -289,14 +291,19 @@ def test_prox_update_parity(J, n, r0, r1, sigma):
     ctx.close()
 
 
-def test_prox_update_not_spd_leaves_core():
-    ctx = lib.Context((6, 4, 3), (1, 2, 2, 1), 32, 0.0, 5, "f32")
-    Yd = torch.randn(32, 6, device="cuda")
-    SHd = torch.zeros(32 * 2, device="cuda")
-    core = torch.randn(12, device="cuda")
+@pytest.mark.parametrize("dims,ranks,k", [((6, 4, 3), (1, 2, 2, 1), 0), ((5, 10, 3), (1, 20, 20, 1), 1)])
+def test_prox_update_not_spd_leaves_core(dims, ranks, k):
+    """sigma = 0 and a zero sketched interface: the register solve (s = 2) and the Cholesky solve
+    (s = 400) both refuse the singular Gram and leave the core as it was."""
+    J = 512
+    ctx = lib.Context(dims, ranks, J, 0.0, 5, "f32")
+    s, n = ranks[k] * ranks[k + 1], dims[k]
+    Yd = torch.randn(J, n, device="cuda")
+    SHd = torch.zeros(J * s, device="cuda")
+    core = torch.randn(s * n, device="cuda")
     before = core.clone()
     with pytest.raises(lib.TtError) as e:
-        ctx.tt_prox_update(Yd, SHd, core, 0)
+        ctx.tt_prox_update(Yd, SHd, core, k)
     assert e.value.code == lib.TT_ENOTSPD
     assert torch.equal(core, before)
     ctx.close()
@@ -439,6 +446,27 @@ def test_sweeps_non_power_of_two_sketch_sizes(dims, ranks, J, nsw):
     full_ref = O.tt_full(ref)
     tol = 1e-4 + rel(O.tt_full(ref_p), full_ref)
     assert rel(O.tt_full(got), full_ref) <= tol, (rel(O.tt_full(got), full_ref), tol)
+    e_ref = O.rel_error(exact, [np.asarray(g, np.float32).astype(np.float64) for g in got])
+    assert abs(err - e_ref) <= 1e-5 * e_ref, (err, e_ref)
+
+
+def test_sweeps_with_large_cores():
+    """Cores with r_k r_{k+1} = 180 > 160 unknowns (the Cholesky solve) in whole sweeps: the
+    tensor after two sweeps against the oracle's (1e-4) and its relative error (1e-5)."""
+    dims, ranks, J = (6, 8, 8, 6), (1, 6, 30, 6, 1), 1024
+    cores = synth.random_tt(dims, ranks, 21)
+    a = synth.add_noise(synth.contract_cores(cores), 1e-2, np.random.default_rng(22))
+    flat, _, exact = synth.quantize(a, "f32")
+    init = synth.random_tt(dims, ranks, 23)
+    ctx = lib.Context(dims, ranks, J, 1e-3, 41, "f32")
+    A = lib.device_tensor(flat, "f32")
+    dc = lib.device_cores(init)
+    ctx.tt_prox_als_sweep(A, dc, 2, 0, rel_change=False)
+    err = ctx.tt_rel_error(A, dc)
+    got = lib.host_cores(dc, ranks, dims)
+    ctx.close()
+    ref, _ = O.tt_ts(exact, init, 41, J, 1e-3, 2)
+    assert rel(O.tt_full(got), O.tt_full(ref)) <= 1e-4, rel(O.tt_full(got), O.tt_full(ref))
     e_ref = O.rel_error(exact, [np.asarray(g, np.float32).astype(np.float64) for g in got])
     assert abs(err - e_ref) <= 1e-5 * e_ref, (err, e_ref)
 
