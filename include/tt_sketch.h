@@ -148,7 +148,8 @@ int tt_sketch_interface(tt_ctx* ctx, float* const* cores_dev, int k, uint64_t sw
 /*
  * Part (c): the proximal update of core k by Eq. (ite) (read with S^T S):
  *   G_{k(2)} <- (Y_k^T SH_k + sigma G_{k(2)}) (SH_k^T SH_k + sigma I)^{-1},
- * solved through a Cholesky factorisation. Y_dev: J x n[k] column-major; SH_dev: J x s_k
+ * solved by Gauss-Jordan elimination in registers (s_k <= 160; its pivots are the D of L D L^T)
+ * or a blocked Cholesky factorisation in one CTA (s_k <= 512). Y_dev: J x n[k] column-major; SH_dev: J x s_k
  * column-major; core_dev is read (proximal centre) and overwritten with the update.
  * Returns TT_ENOTSPD if the Gram matrix is not positive definite (then core_dev is unchanged).
  * Synchronises the stream (the status is read back).
