@@ -210,6 +210,18 @@ int tt_rel_error(tt_ctx* ctx, const void* A_dev, const float* scales_dev,
                  float* const* cores_dev, double* out);
 
 /*
+ * The same relative error for a sparse tensor in coordinate form (idx_dev, val_dev, nnz as in
+ * tt_sketch_unfold_coo, but the coordinates must be distinct: ||A||^2 is summed entry by entry,
+ * so a repeated coordinate would count its parts' squares instead of its sum's):
+ * ||A - X||^2 = ||A||^2 - 2 <A, X> +
+ * ||X||^2, every term in FP64 (X at each nonzero from the cores, ||X||^2 from their Gram chain).
+ * Costs O(nnz sum_k r_k r_{k+1} + sum_k n_k r_k^2 r_{k+1}). Ranks up to 32 (else TT_EINVAL);
+ * an index outside [0, n[s]) skips its entry and returns TT_EINVAL. Synchronises.
+ */
+int tt_rel_error_coo(tt_ctx* ctx, const int32_t* idx_dev, const float* val_dev, int64_t nnz,
+                     float* const* cores_dev, double* out);
+
+/*
  * The same sweeps on HOST buffers: A_host (the dense tensor in the context's storage type,
  * layout as above), scales_host (FP8 only, else NULL) and the d FP32 cores (host array of host
  * pointers, updated in place). Each call copies the inputs to library-owned device buffers

@@ -264,6 +264,26 @@ extern "C" int tt_prox_als_sweep_monitored(tt_ctx* c, const void* A, const float
   return run_sweeps(c, A, scales, cores, nsweeps, first_sweep, rel_change_out, rel_error_out);
 }
 
+extern "C" int tt_rel_error_coo(tt_ctx* c, const int32_t* idx, const float* val, int64_t nnz,
+                                float* const* cores, double* out) {
+  if (!c) return TT_EINVAL;
+  if (nnz < 0) return tt_fail(c, TT_EINVAL, "nnz < 0");
+  if (nnz > 0 && (!idx || !val)) return tt_fail(c, TT_EINVAL, "null coordinates or values");
+  TT_TRY(tt_check_cores(c, cores));
+  if (!out) return tt_fail(c, TT_EINVAL, "null output");
+  c->err.clear();
+  TT_TRY(tt_reset_status(c));
+  TT_TRY(tt_launch_rel_error_coo(c, idx, val, nnz, cores));
+  double h[3];
+  TT_CUDA(c, cudaMemcpyAsync(h, c->d_err_acc, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  const int rc = tt_read_status(c);  // synchronises
+  if (rc == TT_EINVAL) return tt_fail(c, TT_EINVAL, "a coordinate lies outside its mode size (entry skipped)");
+  TT_TRY(rc);
+  const double e2 = h[0] - 2.0 * h[1] + h[2];
+  *out = h[0] > 0 ? sqrt(std::max(0.0, e2) / h[0]) : 0.0;
+  return TT_OK;
+}
+
 extern "C" int tt_rel_error(tt_ctx* c, const void* A, const float* scales, float* const* cores, double* out) {
   if (!c) return TT_EINVAL;
   TT_TRY(check_data(c, A, scales));

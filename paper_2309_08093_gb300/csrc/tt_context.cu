@@ -415,7 +415,7 @@ int tt_prepare_next_draw(tt_ctx* c, uint64_t sweep) {
 static void free_all(tt_ctx* c) {
   void* ps[] = {c->d_h, c->d_v, c->d_plan0, c->d_plan0_off, c->d_plan0_cursor, c->d_ghat,
                 c->d_twiddle, c->d_twstage, c->d_suffix, c->d_prefix, c->d_prefix_tmp, c->d_SH, c->d_Y,
-                c->d_gram, c->d_core_old, c->d_changes, c->d_status, c->d_err_acc, c->d_errs, c->d_ws_acc, c->d_rint, c->d_slab_u, c->d_Yall};
+                c->d_gram, c->d_core_old, c->d_changes, c->d_status, c->d_err_acc, c->d_errs, c->d_ws_acc, c->d_rint, c->d_slab_u, c->d_Yall, c->d_xgram};
   for (void* p : ps)
     if (p) cudaFree(p);
   if (c->d_A_stage) cudaFree(c->d_A_stage);
@@ -563,6 +563,7 @@ extern "C" int tt_sketch_init(tt_ctx** out, const tt_params* p, void* stream) {
   A((void**)&c->d_errs, sizeof(double) * 2 * (c->changes_cap / c->d));
   A((void**)&c->d_status, sizeof(int));
   A((void**)&c->d_err_acc, sizeof(double) * 4);
+  A((void**)&c->d_xgram, sizeof(double) * 2 * 32 * 32);
   A((void**)&c->d_ws_acc, sizeof(double) * 2);
   // streaming relative error (n_0 % 4 == 0, n_0 <= 1024, G_0 within 48 KB of shared memory)
   c->rint_r1p = (c->r[1] + 3) & ~3;

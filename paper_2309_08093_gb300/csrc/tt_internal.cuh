@@ -132,6 +132,7 @@ struct tt_ctx {
   float* d_rint = nullptr;     // right interfaces of the mode-0 fibres (N / n_0 x rint_r1p), rel error
   int rint_r1p = 0;            // r_1 rounded up to a multiple of 4
   float* d_slab_u = nullptr;   // u_t = G_2(i_2)...G_{d-1}(i_{d-1}) per slab (N / (n_0 n_1) x r_2), rel error
+  double* d_xgram = nullptr;   // two 32 x 32 FP64 Gram matrices of the sparse relative error
   int changes_cap = 0;
 
   // measurement counters (tt_profile_*)
@@ -201,6 +202,8 @@ int tt_ensure_rplan(tt_ctx* c, int k);
 // kernels' host entry points (one translation unit each)
 int tt_launch_unfold(tt_ctx* c, const void* A, const float* scales, int k, float* Y);
 int tt_launch_unfold_coo(tt_ctx* c, const int32_t* idx, const float* val, int64_t nnz, int k, float* const* Y);
+// d_err_acc[0..2] = sum val^2, sum val X(i), ||X||^2 of a sparse tensor in coordinate form
+int tt_launch_rel_error_coo(tt_ctx* c, const int32_t* idx, const float* val, int64_t nnz, float* const* cores);
 int tt_launch_core_fft(tt_ctx* c, const float* core, int j);
 int tt_launch_core_ffts(tt_ctx* c, float* const* cores);  // all d cores, one launch
 int tt_launch_suffixes(tt_ctx* c);

@@ -2077,3 +2077,149 @@ extern "C" int tt_prox_update_noalloc(const float* Y_dev, const float* SH_dev, f
   if (cudaStreamSynchronize(st) != cudaSuccess) return TT_ECUDA;
   return hst;  // TT_OK, TT_ENOTSPD or TT_ENONFINITE
 }
+
+// ---------------------------------------------------------------------------------------------
+// Relative error of a sparse tensor in coordinate form (Sec. 5's relative error; the nonzeros of
+// the discussion after Theorem 3): ||A - X||^2 = ||A||^2 - 2 <A, X> + ||X||^2 with
+// X = [[G_0, ..., G_{d-1}]]. The expanded form cancels (about four digits at a 1% residual), so
+// every term is formed in FP64: X at each nonzero by the chain of slice products
+// G_0(i_0) G_1(i_1) ... G_{d-1}(i_{d-1}) (one thread per entry, the row vector in registers: the
+// loops over ranks run to RB with a predicate), and ||X||^2 by the Gram chain
+// Gamma_0 = 1, Gamma_{k+1} = sum_i G_k(i)^T Gamma_k G_k(i) (one CTA per slice i, FP64 atomics).
+// Ranks up to 32; the coordinates must be distinct (||A||^2 is summed entry by entry). An index
+// outside [0, n_s) skips its entry and raises TT_EINVAL.
+
+struct CooErrArgs {
+  const int32_t* idx;
+  const float* val;
+  int64_t nnz;
+  int d;
+  const float* core[TT_MAX_D];
+  int64_t n[TT_MAX_D];
+  int r[TT_MAX_D + 1];
+  double* acc;  // [0] += sum val^2, [1] += sum val X(i)
+  int* status;
+};
+
+template <int RB>
+__global__ void __launch_bounds__(256) k_coo_inner(CooErrArgs a) {
+  double sa = 0.0, sx = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < a.nnz; e += (int64_t)gridDim.x * blockDim.x) {
+    double u[RB], w[RB];
+#pragma unroll
+    for (int b = 0; b < RB; ++b) u[b] = b == 0 ? 1.0 : 0.0;  // r_0 = 1
+    bool bad = false;
+    for (int k = 0; k < a.d; ++k) {
+      const int i = __ldg(a.idx + (int64_t)k * a.nnz + e);
+      if (i < 0 || i >= a.n[k]) {
+        bad = true;
+        break;
+      }
+      const int ra = a.r[k], rb = a.r[k + 1];
+      const float* G = a.core[k] + (int64_t)ra * i;
+      const int64_t bstride = (int64_t)ra * a.n[k];
+#pragma unroll
+      for (int b = 0; b < RB; ++b) {
+        double acc = 0.0;
+        if (b < rb) {
+#pragma unroll
+          for (int c = 0; c < RB; ++c)
+            if (c < ra) acc = fma(u[c], (double)__ldg(G + c + bstride * b), acc);
+        }
+        w[b] = acc;
+      }
+#pragma unroll
+      for (int b = 0; b < RB; ++b) u[b] = w[b];
+    }
+    if (bad) {
+      atomicCAS(a.status, 0, TT_EINVAL);
+      continue;
+    }
+    const double v = (double)__ldg(a.val + e);
+    sa = fma(v, v, sa);
+    sx = fma(v, u[0], sx);  // r_d = 1
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    sa += __shfl_xor_sync(0xffffffffu, sa, o);
+    sx += __shfl_xor_sync(0xffffffffu, sx, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(a.acc, sa);
+    atomicAdd(a.acc + 1, sx);
+  }
+}
+
+// Gamma_out += G(i)^T Gamma_in G(i) for the slice i = blockIdx.x of a ra x n x rb core
+// (Gamma_in ra x ra, Gamma_out rb x rb, row-major, FP64)
+__global__ void __launch_bounds__(256) k_tt_gram_step(const float* __restrict__ G, int n, int ra, int rb,
+                                                      const double* __restrict__ Gin, double* Gout) {
+  extern __shared__ double gsd[];
+  double* S = gsd;            // the slice, S[a + ra b]
+  double* T = gsd + ra * rb;  // Gamma_in S, same layout
+  const int i = blockIdx.x;
+  for (int e = threadIdx.x; e < ra * rb; e += blockDim.x) {
+    const int al = e % ra, b = e / ra;
+    S[e] = (double)G[al + (int64_t)ra * (i + (int64_t)n * b)];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < ra * rb; e += blockDim.x) {
+    const int al = e % ra, b = e / ra;
+    double acc = 0.0;
+    for (int c = 0; c < ra; ++c) acc = fma(Gin[al * ra + c], S[c + ra * b], acc);
+    T[e] = acc;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < rb * rb; e += blockDim.x) {
+    const int b1 = e / rb, b2 = e - b1 * rb;
+    double acc = 0.0;
+    for (int al = 0; al < ra; ++al) acc = fma(S[al + ra * b1], T[al + ra * b2], acc);
+    atomicAdd(Gout + e, acc);
+  }
+}
+
+__global__ void k_set_one(double* p) { *p = 1.0; }
+
+int tt_launch_rel_error_coo(tt_ctx* c, const int32_t* idx, const float* val, int64_t nnz, float* const* cores) {
+  int rmax = 1;
+  for (int k = 0; k <= c->d; ++k) rmax = std::max(rmax, c->r[k]);
+  if (rmax > 32) return tt_fail(c, TT_EINVAL, "the sparse relative error supports ranks up to 32");
+  CooErrArgs a;
+  a.idx = idx;
+  a.val = val;
+  a.nnz = nnz;
+  a.d = c->d;
+  for (int k = 0; k < c->d; ++k) {
+    a.core[k] = cores[k];
+    a.n[k] = c->n[k];
+  }
+  for (int k = 0; k <= c->d; ++k) a.r[k] = c->r[k];
+  a.acc = c->d_err_acc;
+  a.status = c->d_status;
+  TT_CUDA(c, cudaMemsetAsync(c->d_err_acc, 0, sizeof(double) * 3, c->stream));
+  if (nnz > 0) {
+    int sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+    const int blocks = (int)std::min<int64_t>((nnz + 255) / 256, (int64_t)sms * 8);
+    if (rmax <= 8)
+      k_coo_inner<8><<<blocks, 256, 0, c->stream>>>(a);
+    else if (rmax <= 16)
+      k_coo_inner<16><<<blocks, 256, 0, c->stream>>>(a);
+    else
+      k_coo_inner<32><<<blocks, 256, 0, c->stream>>>(a);
+    TT_LAUNCH(c, "k_coo_inner");
+  }
+  double* g[2] = {c->d_xgram, c->d_xgram + 32 * 32};
+  k_set_one<<<1, 1, 0, c->stream>>>(g[0]);  // Gamma_0 = 1 (r_0 = 1)
+  TT_LAUNCH(c, "k_set_one");
+  for (int k = 0; k < c->d; ++k) {
+    const int ra = c->r[k], rb = c->r[k + 1];
+    double* gin = g[k & 1];
+    double* gout = g[(k + 1) & 1];
+    TT_CUDA(c, cudaMemsetAsync(gout, 0, sizeof(double) * rb * rb, c->stream));
+    k_tt_gram_step<<<(int)c->n[k], 256, sizeof(double) * 2 * ra * rb, c->stream>>>(cores[k], (int)c->n[k], ra, rb,
+                                                                                    gin, gout);
+    TT_LAUNCH(c, "k_tt_gram_step");
+  }
+  TT_CUDA(c, cudaMemcpyAsync(c->d_err_acc + 2, g[c->d & 1], sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  return TT_OK;
+}

@@ -21,7 +21,7 @@ TT_OK, TT_EINVAL, TT_ENOMEM, TT_ECUDA, TT_ENOTSPD, TT_ETIMEOUT, TT_ENONFINITE = 
 TT_FLAG_FIXED_SKETCH = 1
 
 EXPORTS = ["tt_sketch_init", "tt_sketch_destroy", "tt_last_error", "tt_sketch_tables",
-           "tt_sketch_set_tables", "tt_sketch_unfold", "tt_sketch_unfold_coo", "tt_sketch_interface", "tt_prox_update",
+           "tt_sketch_set_tables", "tt_sketch_unfold", "tt_sketch_unfold_coo", "tt_rel_error_coo", "tt_sketch_interface", "tt_prox_update",
            "tt_orthogonalize", "tt_prox_als_sweep", "tt_rel_error", "tt_prox_als_sweep_host",
            "tt_profile_enable", "tt_profile_read", "tt_prox_update_noalloc", "tt_batch_init",
            "tt_batch_destroy", "tt_batch_last_error", "tt_batch_sweep", "tt_batch_rel_error",
@@ -81,6 +81,7 @@ def load(path: str = LIB_PATH):
     L.tt_sketch_set_tables.argtypes = [vp, vp, vp]
     L.tt_sketch_unfold.argtypes = [vp, vp, vp, i, u64, ctypes.POINTER(vp)]
     L.tt_sketch_unfold_coo.argtypes = [vp, vp, vp, ctypes.c_int64, i, u64, ctypes.POINTER(vp)]
+    L.tt_rel_error_coo.argtypes = [vp, vp, vp, ctypes.c_int64, ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_double)]
     L.tt_sketch_interface.argtypes = [vp, ctypes.POINTER(vp), i, u64, vp]
     L.tt_prox_update.argtypes = [vp, vp, vp, vp, i]
     L.tt_orthogonalize.argtypes = [vp, ctypes.POINTER(vp), i, i]
@@ -207,6 +208,12 @@ class Context:
         arr = _ptr_array(Y)
         self._check(self.lib.tt_sketch_unfold_coo(self.ctx, _ptr(idx), _ptr(val), int(nnz), int(k), int(sweep),
                                                   arr))
+
+    def tt_rel_error_coo(self, idx, val, nnz: int, cores: Sequence) -> float:
+        out = ctypes.c_double()
+        self._check(self.lib.tt_rel_error_coo(self.ctx, _ptr(idx), _ptr(val), int(nnz), _ptr_array(cores),
+                                              ctypes.byref(out)))
+        return out.value
 
     def tt_sketch_interface(self, cores: Sequence, k: int, sweep: int, SH):
         self._check(self.lib.tt_sketch_interface(self.ctx, _ptr_array(cores), int(k), int(sweep), _ptr(SH)))

@@ -382,6 +382,68 @@ def test_rel_error_parity(dims, ranks, storage):
     ctx.close()
 
 
+@pytest.mark.parametrize("dims,ranks,density", [((12, 10, 8, 6), (1, 3, 4, 2, 1), 0.1), ((20, 18, 16), (1, 12, 20, 1), 0.05),
+                                                ((9, 8, 7, 6, 5), (1, 4, 5, 6, 3, 1), 0.2), ((40, 30), (1, 32, 1), 0.3)])
+def test_rel_error_coo_parity(dims, ranks, density):
+    """The sparse relative error (coordinate form, distinct coordinates in shuffled order) against
+    the oracle's relative error of the densified tensor. Every term is FP64 on FP32 inputs:
+    bound 1e-8."""
+    rng = np.random.default_rng(sum(dims))
+    A = np.asarray(synth.random_tensor(dims, 4) * (rng.random(dims) < density), np.float32).astype(np.float64)
+    est = synth.random_tt(dims, ranks, 5)
+    c32 = [np.asarray(g, np.float32).astype(np.float64) for g in est]
+    nz = np.nonzero(A)
+    idx = np.stack(nz).astype(np.int32)
+    vals = A[nz]
+    perm = rng.permutation(vals.size)
+    idx2, vals2 = np.ascontiguousarray(idx[:, perm]), vals[perm]
+    ctx = lib.Context(dims, ranks, 64, 1e-3, 5, "f32")
+    e = ctx.tt_rel_error_coo(torch.from_numpy(idx2).cuda(), torch.from_numpy(vals2.astype(np.float32)).cuda(),
+                             idx2.shape[1], lib.device_cores(est))
+    ref = O.rel_error(A, c32)
+    assert abs(e - ref) <= 1e-8 * ref, (e, ref)
+    ctx.close()
+
+
+def test_rel_error_coo_small_residual():
+    """Every entry listed, A = X + 1e-4 relative noise: the expanded form cancels about eight
+    digits, which FP64 keeps (1e-6 against the oracle); the dense call agrees to 1e-5."""
+    dims, ranks = (16, 14, 12, 10), (1, 4, 5, 3, 1)
+    est = synth.random_tt(dims, ranks, 8)
+    c32 = [np.asarray(g, np.float32).astype(np.float64) for g in est]
+    X = O.tt_full(c32)
+    A = np.asarray(X + 1e-4 * np.linalg.norm(X) / np.sqrt(X.size) * np.random.default_rng(9).standard_normal(X.shape),
+                   np.float32).astype(np.float64)
+    idx = np.stack(np.unravel_index(np.arange(A.size), dims, order="F")).astype(np.int32)
+    vals = A.ravel(order="F")
+    ctx = lib.Context(dims, ranks, 64, 1e-3, 5, "f32")
+    dc = lib.device_cores(est)
+    e = ctx.tt_rel_error_coo(torch.from_numpy(idx).cuda(), torch.from_numpy(vals.astype(np.float32)).cuda(), A.size, dc)
+    ref = O.rel_error(A, c32)
+    assert abs(e - ref) <= 1e-6 * ref, (e, ref)
+    e_dense = ctx.tt_rel_error(lib.device_tensor(vals.astype(np.float32), "f32"), dc)
+    assert abs(e_dense - ref) <= 1e-5 * ref, (e_dense, ref)
+    ctx.close()
+
+
+def test_rel_error_coo_rejects():
+    ctx = lib.Context((5, 40, 3), (1, 5, 40, 1), 64, 1e-3, 5, "f32")  # a rank above 32
+    est = synth.random_tt((5, 40, 3), (1, 5, 40, 1), 1)
+    idx = torch.zeros(3, 1, dtype=torch.int32, device="cuda")
+    val = torch.ones(1, device="cuda")
+    with pytest.raises(lib.TtError) as e:
+        ctx.tt_rel_error_coo(idx, val, 1, lib.device_cores(est))
+    assert e.value.code == lib.TT_EINVAL
+    ctx.close()
+    ctx = lib.Context((5, 4, 3), (1, 2, 2, 1), 64, 1e-3, 5, "f32")
+    est = synth.random_tt((5, 4, 3), (1, 2, 2, 1), 1)
+    idx = torch.tensor([[0], [4], [0]], dtype=torch.int32, device="cuda")  # i_1 = 4 >= n_1
+    with pytest.raises(lib.TtError) as e:
+        ctx.tt_rel_error_coo(idx, val, 1, lib.device_cores(est))
+    assert e.value.code == lib.TT_EINVAL
+    ctx.close()
+
+
 # ---------------------------------------------------------------------------------------------
 # whole sweeps (Algorithm 1)
 
