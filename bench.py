@@ -9,7 +9,7 @@ Cholesky update and the QR step, then the relative error (one more read of the t
 
 Prints ONE JSON line (rank 0). `--impl reference` times the CPU FP64 oracle instead.
 Under torchrun (N > 1) every rank runs an independent replica (the single-tensor path has no
-data-parallel split without a collective; see DESIGN.md) and rank 0 reports the aggregate.
+data-parallel split without a collective) and rank 0 reports the aggregate.
 """
 from __future__ import annotations
 
