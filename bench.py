@@ -5,7 +5,7 @@ One step = one outer iteration (sweep) of Algorithm 1 on the order-4 100^4 FP32 
 (TT ranks (1,10,10,10,1), 1e-2 relative noise, J = 4096, lambda = 1e-3): right-to-left
 orthogonalisation, a fresh TensorSketch draw, for every core the FFT interface sketch, the
 data sketch of the unfolding (a full read of the 400 MB tensor per core), the proximal
-Cholesky update and the QR step, then the relative error (one more read of the tensor).
+update of Eq. (ite) and the QR step, then the relative error (one more read of the tensor).
 
 Prints ONE JSON line (rank 0). `--impl reference` times the CPU FP64 oracle instead.
 Under torchrun (N > 1) every rank runs an independent replica (the single-tensor path has no
