@@ -54,3 +54,25 @@ def test_reference_arm_runs_on_rank_zero_only():
     class Args:
         workload = "order3-50-r5"
     assert bench.reference_main(Args(), rank=1, world=2) is None  # returns before any work
+
+
+def test_reference_arm_prints_the_contract_line():
+    """Rank 0 of the reference arm (the CPU FP64 oracle) prints one JSON line with the contract's
+    keys; its step time and its throughput describe the same step (one sweep)."""
+    import json
+    import subprocess
+
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "0", "--workload", "order3-50-r5"], capture_output=True, text=True,
+                         timeout=300, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["unit"] == "sweeps/s" and d["higher_is_better"] is True
+    assert d["value"] > 0 and abs(d["value"] * d["ms_per_step"] - 1000.0) <= 1e-6 * 1000.0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
