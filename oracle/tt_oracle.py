@@ -364,11 +364,25 @@ class NotSPD(Exception):
     pass
 
 
+# Eq. (ite) needs M SPD, which Alg. 1 guarantees through sigma > 0; Sec. 5 also runs sigma = 0,
+# where the sketched Gram can be singular (for instance when two indices of a mode whose core is
+# square share a bucket, S H_k loses rank). Reading taken: a Cholesky pivot L_jj^2 at or below
+# PIVOT_TOL times the largest diagonal entry of M means M is singular to the precision of its
+# inputs, and the update is refused.
+PIVOT_TOL = 1e-10
+
+
 def cholesky_lower(M: np.ndarray) -> np.ndarray:
+    """Lower Cholesky factor of M, refusing (NotSPD) a factorization that fails or whose smallest
+    pivot L_jj^2 is at most PIVOT_TOL * max_i M_ii."""
     try:
-        return np.linalg.cholesky(M)
+        L = np.linalg.cholesky(M)
     except np.linalg.LinAlgError as e:
         raise NotSPD(str(e))
+    piv = np.diag(L) ** 2
+    if piv.size and piv.min() <= PIVOT_TOL * np.max(np.diag(M)):
+        raise NotSPD(f"pivot ratio {piv.min() / np.max(np.diag(M)):.3e} <= {PIVOT_TOL:g}")
+    return L
 
 
 def prox_update(Yk: np.ndarray, SHk: np.ndarray, Gk: np.ndarray, sigma: float) -> np.ndarray:

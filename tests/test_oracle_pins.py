@@ -311,6 +311,62 @@ def test_prox_update_sigma_zero_singular_raises():
         O.prox_update(Y, SH, np.zeros((1, 2, 3)), 0.0)
 
 
+def test_prox_update_refuses_numerically_singular_grams():
+    """Two equal columns of S H_k, or a column within 1e-9 of the span of the others, make M
+    singular to working precision (pivot ratios near 1e-16 and 1e-18): refused at sigma = 0,
+    accepted with sigma > 0. A system with cond(M) = 1e8 is kept and equals lstsq."""
+    rng = _rng(23)
+    J, n = 60, 5
+    Y = rng.standard_normal((J, n))
+    G = rng.standard_normal((2, n, 3))
+    base = rng.standard_normal((J, 6))
+    dup = base.copy()
+    dup[:, 4] = dup[:, 1]
+    near = base.copy()
+    near[:, 5] = base[:, :5] @ rng.standard_normal(5) + 1e-9 * rng.standard_normal(J)
+    for SH in (dup, near):
+        with pytest.raises(O.NotSPD):
+            O.prox_update(Y, SH, G, 0.0)
+        a = O.prox_update(Y, SH, G, 0.5)
+        assert np.allclose(a, O.prox_update_augmented(Y, SH, G, 0.5), atol=1e-9)
+    U, _ = np.linalg.qr(rng.standard_normal((J, 6)))
+    V, _ = np.linalg.qr(rng.standard_normal((6, 6)))
+    SH = U @ np.diag(np.logspace(0, -4, 6)) @ V.T  # cond(SH) = 1e4, cond(M) = 1e8
+    X, *_ = np.linalg.lstsq(SH, Y, rcond=None)
+    got = O.mode2_unfold(O.prox_update(Y, SH, G, 0.0)).T
+    assert np.linalg.norm(got - X) <= 1e-6 * np.linalg.norm(X)
+
+
+def test_sigma_zero_gram_is_singular_after_a_collision_in_a_square_last_core():
+    """The last core G_{d-1} (r_{d-1} x n_{d-1} x 1) is square when n_{d-1} = r_{d-1}. For
+    k = d-2 the sketched right interface is the CountSketch of that core's right unfolding
+    (Theorem 2 with one factor); two indices sharing a bucket add two of its rows, so S H_{d-2}
+    loses r_{d-2} columns of rank (checked by SVD) and the sigma = 0 Gram of Eq. (ite) is
+    singular: the oracle refuses it. Distinct buckets keep full rank and the update goes through."""
+    dims, ranks = (3, 5, 4), (1, 3, 4, 1)
+    cores = synth.random_tt(dims, ranks, 31)
+    A = synth.random_tensor(dims, 32)
+    J, k = 16, 1
+    vs = [np.ones(3), np.array([1.0, -1.0, 1.0, 1.0, -1.0]), np.array([1.0, -1.0, -1.0, 1.0])]
+    for h2, singular in (([0, 3, 3, 9], True), ([0, 3, 6, 9], False)):  # h_0 + h_2 distinct in the second
+        hs = [np.array([0, 1, 2]), np.array([3, 1, 4, 1, 5]), np.array(h2)]
+        SH = O.sketch_interface_dense(cores, hs, vs, J, k)
+        Y = O.sketch_unfolding(A, hs, vs, J, k)
+        sv = np.linalg.svd(SH, compute_uv=False)
+        s = ranks[k] * ranks[k + 1]
+        rank = int(np.sum(sv > 1e-12 * sv[0]))
+        if singular:
+            assert rank == s - ranks[k]
+            with pytest.raises(O.NotSPD):
+                O.prox_update(Y, SH, cores[k], 0.0)
+        else:
+            assert rank == s
+            X, *_ = np.linalg.lstsq(SH, Y, rcond=None)
+            got = O.mode2_unfold(O.prox_update(Y, SH, cores[k], 0.0)).T
+            assert np.linalg.norm(got - X) <= 1e-8 * np.linalg.norm(X)
+        O.prox_update(Y, SH, cores[k], 0.5)  # the proximal term keeps M SPD
+
+
 def test_identity_sketch_reduces_to_exact_prox_als():
     """m = prod_{i!=k} n_i, injective hash, v = +1: S is a permutation, so (ite) equals the exact
     proximal update of Eq. (lrtt_sub_prox)."""
