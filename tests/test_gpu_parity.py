@@ -1,7 +1,11 @@
 """GPU parity: the CUDA library (called through the C ABI) against the CPU FP64 oracle on the
 same seeded inputs and hash draws. Floating-point outputs are compared in relative Frobenius
-norm (sums in different orders; buckets with cancellation make element-wise relative error
-meaningless). Tolerance 1e-5 for FP32 work; integer tables bit-exact."""
+norm (sums in different orders) and, for the data and interface sketches, entry by entry
+against a bound that any summation order meets: for Y_k, 1e-5 of (the largest |entry| plus the
+sum of |terms| of the bucket), so a dropped or mis-signed term of a small bucket still fails;
+for S H_k, 1e-5 of each column's largest |entry|. Buckets with cancellation make a plain
+element-wise relative error meaningless. Tolerance 1e-5 for FP32 work; integer tables
+bit-exact."""
 import numpy as np
 import pytest
 
@@ -122,10 +126,15 @@ def test_unfold_sketch_parity(dims, J, storage):
         ctx.tt_sketch_unfold(Ad, -1, sweep, Y, scales=sd)
         torch.cuda.synchronize()
         hs, vs = O.draw_sketch(seed, sweep, dims, J)
+        ones = [np.ones_like(v) for v in vs]
         for k in range(len(dims)):
             ref = O.sketch_unfolding(exact, hs, vs, J, k)
             got = Y[k].cpu().numpy().reshape(dims[k], J).T  # column-major J x n_k
             assert rel(got, ref) <= TOL, (k, rel(got, ref))
+            # entrywise: the sum of |terms| of each bucket (the sketch of |A| with unit signs)
+            # bounds what any FP32 summation order can move it by
+            mass = O.sketch_unfolding(np.abs(exact), hs, ones, J, k)
+            assert np.all(np.abs(got - ref) <= TOL * (np.abs(ref).max() + mass)), k
     # single-mode call writes only that mode
     Y1 = [None] * len(dims)
     Y1[1] = torch.zeros(J * dims[1], device="cuda")
@@ -257,6 +266,9 @@ def test_interface_sketch_parity(dims, ranks, J):
             got = SH.cpu().numpy().reshape(s, J).T
             ref = O.sketch_interface_fft(c32, hs, vs, J, k)
             assert rel(got, ref) <= TOL, (k, rel(got, ref))
+            # entrywise, column by column (columns of S H_k differ in scale)
+            colmax = np.abs(ref).max(axis=0, keepdims=True)
+            assert np.all(np.abs(got - ref) <= TOL * colmax + 1e-30), (k, np.max(np.abs(got - ref) / colmax))
     ctx.close()
 
 

@@ -432,6 +432,35 @@ def test_exact_tt_is_a_fixed_point():
         assert rc < 1e-10
 
 
+def test_rel_change_by_hand_on_a_two_by_two_matrix():
+    """One sweep on A = [[3, 1], [1, 2]] with rank-1 cores g0 = (1, 0), g1 = (1, 1), sigma = 1/2,
+    and a draw whose hashes are injective at J = 2, so that S is a signed permutation and
+    S^T S = I. Worked by hand:
+      right-to-left orthogonalisation: q1 = g1 / |g1|, centre c0 = |g1| g0;
+      core 0: (S H_0)^T (S H_0) = 1, Y_0^T S H_0 = A S^T S q1 = A q1, so
+              G0 = (A q1 + sigma c0) / (1 + sigma); QR: q0 = G0 / |G0|, centre c1 = |G0| q1;
+      core 1: G1 = (A^T q0 + sigma c1) / (1 + sigma);
+      rel-change (Sec. 5) = max(|G0 - c0| / |G0|, |G1 - c1| / |G1|), each over the NEW core's norm."""
+    A = np.array([[3.0, 1.0], [1.0, 2.0]])
+    g0, g1, sigma, J = np.array([1.0, 0.0]), np.array([1.0, 1.0]), 0.5, 2
+    seed = next(sd for sd in range(1000)
+                if all(len(set(h.tolist())) == 2 for h in O.draw_sketch(sd, 0, (2, 2), J)[0]))
+    q1 = g1 / np.linalg.norm(g1)
+    c0 = np.linalg.norm(g1) * g0
+    G0 = (A @ q1 + sigma * c0) / (1 + sigma)
+    q0 = G0 / np.linalg.norm(G0)
+    c1 = np.linalg.norm(G0) * q1
+    G1 = (A.T @ q0 + sigma * c1) / (1 + sigma)
+    ch = max(np.linalg.norm(G0 - c0) / np.linalg.norm(G0), np.linalg.norm(G1 - c1) / np.linalg.norm(G1))
+    cores = [g0.reshape(1, 2, 1), g1.reshape(1, 2, 1)]
+    new, rc = O.tt_ts_sweep(A, cores, seed, 0, J, sigma)
+    assert abs(rc - ch) <= 1e-12, (rc, ch)
+    assert np.allclose(new[0].ravel(), q0, atol=1e-12) and np.allclose(new[1].ravel(), G1, atol=1e-12)
+    # the normalisation matters here: over the old cores' norms the value differs
+    wrong = max(np.linalg.norm(G0 - c0) / np.linalg.norm(c0), np.linalg.norm(G1 - c1) / np.linalg.norm(c1))
+    assert abs(wrong - ch) > 1e-2
+
+
 def test_exact_recovery_from_random_init():
     dims, ranks = (8, 9, 7, 8), (1, 3, 3, 3, 1)
     A = O.tt_full(synth.random_tt(dims, ranks, 15))
