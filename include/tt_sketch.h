@@ -65,6 +65,22 @@ enum {
 
 /* flags */
 #define TT_FLAG_FIXED_SKETCH 1u /* draw h_k, v_k once (t = 0) instead of once per sweep */
+#define TT_FLAG_FP64_SOLVE 2u   /* solve Eq. (ite) in FP64 also when sigma > 0 (see tt_prox_update) */
+/* Fixed summation orders: repeated calls on the same inputs return the same bits (data sketches,
+ * interface sketches, updated cores, relative errors and rel-changes of the dense-tensor calls).
+ * The data sketch is then accumulated in 64-bit fixed point, one read of A for all modes, with
+ * integer atomics, the Gram's K-chunks and all partial sums are added in a fixed order, and the
+ * CountSketch of the cores adds its entries in index order. Slower: the data sketch makes one
+ * 8-byte integer atomic add per entry and mode. The sparse coordinate-form calls are not covered. */
+#define TT_FLAG_DETERMINISTIC 4u
+/* Gram and right-hand side of the FP32 update (sigma > 0) on the tensor cores (tcgen05, TF32
+ * operands staged by TMA, FP32 accumulators in tensor memory), when J is a multiple of 4 and
+ * r[k]*r[k+1] <= 256; otherwise the CUDA-core FP32 Gram. TT_FLAG_TC_GRAM splits every operand into
+ * two TF32 parts and adds three products (about 2^-22 relative error per product, the FP32
+ * form's accuracy); TT_FLAG_TF32_GRAM reads the operands once as TF32 (about 2^-11 per product:
+ * the mixed-precision form). */
+#define TT_FLAG_TC_GRAM 8u
+#define TT_FLAG_TF32_GRAM 16u
 
 typedef struct {
   int d;              /* order of the tensor, 2 <= d <= 8 */
@@ -92,6 +108,18 @@ void tt_sketch_destroy(tt_ctx* ctx);
 
 /* Message of the last failure on this context ("" if none). Valid until the next call. */
 const char* tt_last_error(const tt_ctx* ctx);
+
+/*
+ * Process-wide cap on the device memory a context may own (0 = no cap, the default); returns
+ * the previous cap. The paper has no counterpart: it is memory budgeting for applications that
+ * share the GPU. tt_sketch_init sums the sizes of all the workspaces it would allocate (hash
+ * tables, fibre plans of two draws, FFT sketches, data sketches, Gram and solve buffers, the
+ * relative error's interfaces) before any CUDA call, and returns TT_ENOMEM (message on stderr)
+ * when the sum exceeds the cap; tt_prox_als_sweep_host returns TT_ENOMEM the same way before it
+ * allocates its staging buffers (the tensor, the scales and the cores) beyond the cap. Contexts
+ * created before a change keep what they own. Thread-safe.
+ */
+uint64_t tt_set_workspace_limit(uint64_t bytes);
 
 /*
  * Copy the hash and sign tables of sweep `sweep` (Sec. 2.2; drawn on the device) to host
@@ -147,12 +175,24 @@ int tt_sketch_interface(tt_ctx* ctx, float* const* cores_dev, int k, uint64_t sw
 
 /*
  * Part (c): the proximal update of core k by Eq. (ite) (read with S^T S):
- *   G_{k(2)} <- (Y_k^T SH_k + sigma G_{k(2)}) (SH_k^T SH_k + sigma I)^{-1},
- * solved by Gauss-Jordan elimination in registers (s_k <= 160; its pivots are the D of L D L^T)
- * or a blocked Cholesky factorisation in one CTA (s_k <= 512). Y_dev: J x n[k] column-major; SH_dev: J x s_k
- * column-major; core_dev is read (proximal centre) and overwritten with the update.
- * Returns TT_ENOTSPD if the Gram matrix is not positive definite (then core_dev is unchanged).
- * Synchronises the stream (the status is read back).
+ *   G_{k(2)} <- (Y_k^T SH_k + sigma G_{k(2)}) (SH_k^T SH_k + sigma I)^{-1}.
+ * Y_dev: J x n[k] column-major; SH_dev: J x s_k column-major; core_dev is read (proximal centre)
+ * and overwritten with the update. Two forms, fixed at context creation:
+ *   - sigma > 0 (Alg. 1's setting: M is SPD with smallest eigenvalue >= sigma): the Gram is
+ *     accumulated in FP32 and solved in FP32, by Gauss-Jordan elimination in registers
+ *     (s_k <= 160; its pivots are the D of L D L^T) or a blocked Cholesky in one CTA
+ *     (s_k <= 512). A pivot at or below 1e-4 of the largest diagonal entry of M is refused with
+ *     TT_ENOTSPD: the FP32 Gram's rounding noise (about sqrt(J) 2^-24 of that entry) can lift
+ *     the pivots of a singular system to about that level. Small sigma with a nearly singular
+ *     S H_k wants TT_FLAG_FP64_SOLVE.
+ *   - sigma = 0 (run in Sec. 5, where M is not SPD by construction), or TT_FLAG_FP64_SOLVE:
+ *     the Gram is accumulated in FP64 (the FP32 products are exact in FP64), factored by an
+ *     FP64 Cholesky and solved by FP64 triangular solves. A pivot L_jj^2 at or below 1e-10 of
+ *     the largest diagonal entry of M is refused with TT_ENOTSPD (M singular to the precision
+ *     of its FP32 inputs; the oracle refuses at the same ratio).
+ * Returns TT_ENOTSPD (core_dev unchanged), TT_ENONFINITE if S H_k or Y_k holds a NaN or Inf
+ * (core_dev unchanged) or if the solve overflows. Synchronises the stream (the status is read
+ * back).
  */
 int tt_prox_update(tt_ctx* ctx, const float* Y_dev, const float* SH_dev, float* core_dev, int k);
 
@@ -241,10 +281,11 @@ int tt_prox_als_sweep_host(tt_ctx* ctx, const void* A_host, const float* scales_
  * tt_prox_update computes for a core of shape r0 x n x r1, without a context:
  *   Y_dev (J x n column-major), SH_dev (J x r0*r1 column-major), core_dev (read as the proximal
  *   centre, overwritten with the update), sigma >= 0, cuda_stream (a cudaStream_t or NULL).
- * Limits: r0*r1 <= 160 and n <= 1024; larger sizes are rejected with TT_EINVAL (and a message
- * on stderr) before anything is launched.
- * Memory: it never calls cudaMalloc/cudaFree or any allocating routine. Its scratch (~1.5 MB of
- * FP64 Gram accumulators and a status word) is a static array in the library's device image, so
+ * Limits: r0, r1 >= 1 with r0*r1 <= 160, and n <= 1024; larger sizes (including ranks whose
+ * product would overflow an int) are rejected with TT_EINVAL (and a message on stderr) before
+ * anything is launched. It always takes the FP32 register solve, whatever sigma is.
+ * Memory: it never calls cudaMalloc/cudaFree or any allocating routine. Its scratch (~0.76 MB of
+ * FP32 Gram accumulators and a status word) is a static array in the library's device image, so
  * every GPU that loads the library holds it until the process exits. The first call on a device
  * looks up that array's device address while the device is current; make that first call before
  * any stream capture. All calls share the one array: each call clears what it needs, but calls

@@ -45,6 +45,8 @@ extern "C" int tt_sketch_unfold(tt_ctx* c, const void* A, const float* scales, i
     if ((k == -1 || k == kk) && !Y[kk]) return tt_fail(c, TT_EINVAL, "null output for mode %d", kk);
   c->err.clear();
   TT_TRY(tt_ensure_tables(c, sweep));
+  if (c->det)  // fixed-point sketch of all requested modes in one read of A
+    return tt_launch_unfold_det(c, A, scales, k == -1 ? (1u << c->d) - 1u : 1u << k, Y);
   for (int kk = 0; kk < c->d; ++kk)
     if (k == -1 || k == kk) TT_TRY(tt_launch_unfold(c, A, scales, kk, Y[kk]));
   return TT_OK;
@@ -126,7 +128,16 @@ static int sweep_body(tt_ctx* c, const void* A, const float* scales, float* cons
     c->stream = c->side;
     c->in_sweep = true;
     int rc = TT_OK;
-    for (int k = 0; k < d && rc == TT_OK; ++k) {
+    if (c->det) {  // every mode from one fixed-point pass over A
+      float* ys[TT_MAX_D];
+      for (int k = 0; k < d; ++k) ys[k] = c->d_Yall + c->yoff[k];
+      rc = tt_launch_unfold_det(c, A, scales, (1u << d) - 1u, ys);
+      for (int k = 0; k < d && rc == TT_OK; ++k) {
+        const cudaError_t e = cudaEventRecord(c->ev_y[k], c->side);
+        if (e != cudaSuccess) rc = tt_cuda_check(c, e, "cudaEventRecord");
+      }
+    }
+    for (int k = 0; k < d && rc == TT_OK && !c->det; ++k) {
       rc = tt_launch_unfold(c, A, scales, k, c->d_Yall + c->yoff[k]);
       if (rc == TT_OK) {
         const cudaError_t e = cudaEventRecord(c->ev_y[k], c->side);
@@ -151,7 +162,11 @@ static int sweep_body(tt_ctx* c, const void* A, const float* scales, float* cons
     for (int k = 0; k < d; ++k) {
       // the interface kernel also zeroes the Gram accumulators of this core's update
       const int64_t sk = (int64_t)c->r[k] * c->r[k + 1];
-      TT_TRY(tt_launch_interface_from_chain(c, k, c->d_SH, c->d_gram, (sk + c->n[k]) * sk));
+      if (c->solve64)
+        TT_TRY(tt_launch_interface_from_chain(c, k, c->d_SH, reinterpret_cast<float*>(c->d_gram64),
+                                              2 * (sk + c->n[k]) * sk));
+      else
+        TT_TRY(tt_launch_interface_from_chain(c, k, c->d_SH, c->d_gram, (sk + c->n[k]) * sk));
       const float* Yk = fork ? c->d_Yall + c->yoff[k] : Ygiven[k];
       if (fork) TT_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_y[k], 0));
       TT_TRY(tt_launch_prox_update(c, Yk, c->d_SH, cores[k], k, change_slots ? change_slots + 2 * k : nullptr,
@@ -318,7 +333,12 @@ extern "C" int tt_prox_als_sweep_host(tt_ctx* c, const void* A_host, const float
   TT_TRY(tt_check_cores(c, cores_host));
   c->err.clear();
   const size_t abytes = (size_t)c->N * tt_elem_bytes(c->dtype);
-  if (!c->d_A_stage) TT_CUDA(c, cudaMalloc(&c->d_A_stage, abytes));
+  if (!c->d_A_stage) {  // the staging buffers count against the workspace cap
+    uint64_t extra = abytes + sizeof(float) * c->n[0];
+    for (int k = 0; k < c->d; ++k) extra += sizeof(float) * (uint64_t)c->r[k] * c->n[k] * c->r[k + 1];
+    TT_TRY(tt_check_workspace_cap(c, extra));
+    TT_CUDA(c, cudaMalloc(&c->d_A_stage, abytes));
+  }
   if (scales_host && !c->d_scales_stage) TT_CUDA(c, cudaMalloc((void**)&c->d_scales_stage, sizeof(float) * c->n[0]));
   size_t csz[TT_MAX_D];
   for (int k = 0; k < c->d; ++k) {
@@ -359,7 +379,8 @@ int tt_prof_end(tt_ctx* c) {
   if (!c->profiling) return TT_OK;
   TT_CUDA(c, cudaEventRecord(c->ev_pool[c->ev_used], c->stream));
   c->ev_used += 1;
-  c->prof_bytes += (int64_t)c->N * tt_elem_bytes(c->dtype);
+  // algorithmic bytes of one data-sketch launch: every entry once, plus the FP8 slice scales
+  c->prof_bytes += (int64_t)c->N * tt_elem_bytes(c->dtype) + (c->dtype == TT_FP8E4M3 ? 4 * c->n[0] : 0);
   return TT_OK;
 }
 

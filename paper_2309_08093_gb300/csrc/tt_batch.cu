@@ -120,6 +120,7 @@ static int autotune(tt_batch* b, const void* const* A, const float* const* S) {
   static const int cps[] = {1, 2};
   for (int i = 0; i < b->count; ++i) {
     tt_ctx* c = b->ctx[i];
+    if (c->det) continue;  // the fixed-point data sketch has no tunables
     int rc = tt_ensure_tables(c, 0);
     if (rc) return rc;
     for (int k = 0; k < c->d; ++k) {

@@ -3,6 +3,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <cmath>
 #include <new>
 #include <vector>
@@ -10,6 +11,17 @@
 #include <utility>
 
 #include "tt_internal.cuh"
+
+int tt_sm_count() {
+  static int cache[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 152;
+  if (dev < 64 && cache[dev] > 0) return cache[dev];
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
+  if (dev < 64) cache[dev] = sms;
+  return sms;
+}
 
 int tt_fail(tt_ctx* c, int code, const char* fmt, ...) {
   if (c) {
@@ -387,7 +399,8 @@ int tt_ensure_rplan(tt_ctx* c, int k) {
 int tt_ensure_plan0(tt_ctx* c) { return tt_ensure_rplan(c, 0); }
 
 int tt_prepare_next_draw(tt_ctx* c, uint64_t sweep) {
-  if (c->capture_mode || c->user_tables || (c->flags & TT_FLAG_FIXED_SKETCH)) return TT_OK;
+  // (the deterministic data sketch needs no plans; its tables are drawn at the sweep's start)
+  if (c->det || c->capture_mode || c->user_tables || (c->flags & TT_FLAG_FIXED_SKETCH)) return TT_OK;
   bool ready = c->spare.tables_valid && c->spare.tables_sweep == sweep;
   for (int k = 0; k < c->d; ++k) ready = ready && c->spare.rplan_valid[k];
   if (ready) return TT_OK;
@@ -415,7 +428,8 @@ int tt_prepare_next_draw(tt_ctx* c, uint64_t sweep) {
 static void free_all(tt_ctx* c) {
   void* ps[] = {c->d_h, c->d_v, c->d_plan0, c->d_plan0_off, c->d_plan0_cursor, c->d_ghat,
                 c->d_twiddle, c->d_twstage, c->d_suffix, c->d_prefix, c->d_prefix_tmp, c->d_SH, c->d_Y,
-                c->d_gram, c->d_core_old, c->d_changes, c->d_status, c->d_err_acc, c->d_errs, c->d_ws_acc, c->d_rint, c->d_slab_u, c->d_Yall, c->d_xgram};
+                c->d_gram, c->d_core_old, c->d_changes, c->d_status, c->d_err_acc, c->d_errs, c->d_ws_acc, c->d_rint, c->d_slab_u, c->d_Yall, c->d_xgram, c->d_gram64,
+                c->d_det_misc, c->d_y64, c->d_gram_part, c->d_part_err, c->d_part_chg};
   for (void* p : ps)
     if (p) cudaFree(p);
   if (c->d_A_stage) cudaFree(c->d_A_stage);
@@ -448,6 +462,87 @@ static void free_all(tt_ctx* c) {
   if (c->ev_out) cudaEventDestroy(c->ev_out);
 }
 
+// Every device workspace of a context, in allocation order: f(&pointer, bytes). Used twice by
+// tt_sketch_init: to sum the sizes (the cap of tt_set_workspace_limit is checked before any CUDA
+// call) and to allocate. Fills the size bookkeeping of the context (R, yoff, changes_cap,
+// rint_r1p) as it goes.
+template <typename F>
+static void tt_workspace_each(tt_ctx* c, F&& A) {
+  A((void**)&c->d_h, sizeof(int32_t) * c->noff[c->d]);
+  A((void**)&c->d_v, sizeof(int8_t) * c->noff[c->d]);
+  A((void**)&c->d_plan0_cursor, sizeof(int32_t) * c->J * c->d);
+  A((void**)&c->d_rtmp, sizeof(int64_t) * (c->J + 1) * c->d);
+  for (int k = 0; k < c->d; ++k) {
+    c->R[k] = c->N / (c->n[0] * (k == 0 ? 1 : c->n[k]));
+    A((void**)&c->d_rplan[k], sizeof(uint32_t) * c->R[k]);
+    A((void**)&c->d_ulist[k], sizeof(int32_t) * c->J);
+    A((void**)&c->d_ustart[k], sizeof(int64_t) * (c->J + 1));
+    A((void**)&c->d_ucount[k], sizeof(int32_t));
+    A((void**)&c->spare.rplan[k], sizeof(uint32_t) * c->R[k]);
+    A((void**)&c->spare.ulist[k], sizeof(int32_t) * c->J);
+    A((void**)&c->spare.ustart[k], sizeof(int64_t) * (c->J + 1));
+    A((void**)&c->spare.ucount[k], sizeof(int32_t));
+  }
+  const int64_t H = c->J / 2 + 1;
+  A((void**)&c->spare.h, sizeof(int32_t) * c->noff[c->d]);
+  A((void**)&c->spare.v, sizeof(int8_t) * c->noff[c->d]);
+  A((void**)&c->d_ghat, sizeof(float2) * c->ghat_off[c->d]);
+  A((void**)&c->d_twiddle, sizeof(float2) * c->J);
+  A((void**)&c->d_twstage, sizeof(float2) * c->J);
+  A((void**)&c->d_suffix, sizeof(float2) * c->suffix_off[c->d]);
+  A((void**)&c->d_prefix, sizeof(float2) * H * c->rmax);
+  A((void**)&c->d_prefix_tmp, sizeof(float2) * H * c->rmax);
+  A((void**)&c->d_SH, sizeof(float) * c->J * c->smax);
+  A((void**)&c->d_Y, sizeof(float) * c->J * c->nmax);
+  c->yoff[0] = 0;
+  for (int k = 0; k < c->d; ++k) c->yoff[k + 1] = c->yoff[k] + (int64_t)c->J * c->n[k];
+  A((void**)&c->d_Yall, sizeof(float) * c->yoff[c->d]);
+  A((void**)&c->d_gram, sizeof(float) * (c->smax + c->nmax) * c->smax);
+  if (c->solve64) A((void**)&c->d_gram64, sizeof(double) * (c->smax + c->nmax) * c->smax);
+  if (c->det) {
+    A((void**)&c->d_det_misc, sizeof(int) * 4);
+    A((void**)&c->d_y64, sizeof(int64_t) * c->yoff[c->d]);
+    A((void**)&c->d_gram_part, (c->solve64 ? sizeof(double) : sizeof(float)) * (size_t)TT_DET_KSPLIT *
+                                   (c->smax + c->nmax) * c->smax);
+    A((void**)&c->d_part_err, sizeof(double) * 2 * TT_DET_PARTS);
+    A((void**)&c->d_part_chg, sizeof(double) * 2 * std::max<int64_t>(TT_DET_PARTS, c->nmax));
+  }
+  A((void**)&c->d_core_old, sizeof(float) * c->nmax * c->smax);
+  c->changes_cap = 1024 * TT_MAX_D;
+  A((void**)&c->d_changes, sizeof(double) * 2 * c->changes_cap);
+  A((void**)&c->d_errs, sizeof(double) * 2 * (c->changes_cap / c->d));
+  A((void**)&c->d_status, sizeof(int));
+  A((void**)&c->d_err_acc, sizeof(double) * 4);
+  A((void**)&c->d_xgram, sizeof(double) * 2 * 32 * 32);
+  A((void**)&c->d_ws_acc, sizeof(double) * 2);
+  // streaming relative error (n_0 % 4 == 0, n_0 <= 1024, G_0 within 48 KB of shared memory)
+  c->rint_r1p = (c->r[1] + 3) & ~3;
+  if (c->n[0] % 4 == 0 && c->n[0] <= 1024 && (int64_t)c->rint_r1p * c->n[0] * 4 <= 48 * 1024) {
+    A((void**)&c->d_rint, sizeof(float) * (size_t)(c->N / c->n[0]) * c->rint_r1p);
+    A((void**)&c->d_slab_u, sizeof(float) * (size_t)(c->N / (c->n[0] * c->n[1])) * c->r[2]);
+  }
+}
+
+static std::atomic<uint64_t> g_workspace_limit{0};
+
+// Total bytes of the workspaces above (each allocation rounded up to the 16 bytes cudaMalloc is
+// given at least); touches no device.
+static uint64_t tt_workspace_plan(tt_ctx* c) {
+  uint64_t total = 0;
+  tt_workspace_each(c, [&](void**, size_t bytes) { total += (std::max<size_t>(bytes, 16) + 255) & ~(size_t)255; });
+  return total;
+}
+
+extern "C" uint64_t tt_set_workspace_limit(uint64_t bytes) { return g_workspace_limit.exchange(bytes); }
+
+int tt_check_workspace_cap(tt_ctx* c, uint64_t extra) {
+  const uint64_t cap = g_workspace_limit.load();
+  if (cap && c->ws_bytes + extra > cap)
+    return tt_fail(c, TT_ENOMEM, "workspaces need %llu bytes, above the limit of %llu bytes",
+                   (unsigned long long)(c->ws_bytes + extra), (unsigned long long)cap);
+  return TT_OK;
+}
+
 extern "C" int tt_sketch_init(tt_ctx** out, const tt_params* p, void* stream) {
   if (!out || !p) return TT_EINVAL;
   *out = nullptr;
@@ -475,6 +570,10 @@ extern "C" int tt_sketch_init(tt_ctx** out, const tt_params* p, void* stream) {
   c->seed = p->seed;
   c->dtype = p->dtype;
   c->flags = p->flags;
+  // sigma = 0 (Alg. 1 asks sigma > 0: M is then not SPD by construction and its conditioning is
+  // unbounded) and TT_FLAG_FP64_SOLVE take the FP64 update
+  c->solve64 = (p->flags & TT_FLAG_FP64_SOLVE) != 0 || p->lambda == 0.0;
+  c->det = (p->flags & TT_FLAG_DETERMINISTIC) != 0;
   c->stream = (cudaStream_t)stream;
   c->N = 1;
   c->noff[0] = 0;
@@ -513,38 +612,21 @@ extern "C" int tt_sketch_init(tt_ctx** out, const tt_params* p, void* stream) {
   c->suffix_off[0] = 0;
   for (int k = 0; k < c->d; ++k) c->suffix_off[k + 1] = c->suffix_off[k] + (int64_t)H * c->r[k + 1];
 
-  cudaError_t e = cudaSuccess;
-  auto A = [&](void** ptr, size_t bytes) {
-    if (e == cudaSuccess) e = cudaMalloc(ptr, std::max<size_t>(bytes, 16));
-  };
-  A((void**)&c->d_h, sizeof(int32_t) * c->noff[c->d]);
-  A((void**)&c->d_v, sizeof(int8_t) * c->noff[c->d]);
-  A((void**)&c->d_plan0_cursor, sizeof(int32_t) * c->J * c->d);
-  A((void**)&c->d_rtmp, sizeof(int64_t) * (c->J + 1) * c->d);
-  for (int k = 0; k < c->d; ++k) {
-    c->R[k] = c->N / (c->n[0] * (k == 0 ? 1 : c->n[k]));
-    A((void**)&c->d_rplan[k], sizeof(uint32_t) * c->R[k]);
-    A((void**)&c->d_ulist[k], sizeof(int32_t) * c->J);
-    A((void**)&c->d_ustart[k], sizeof(int64_t) * (c->J + 1));
-    A((void**)&c->d_ucount[k], sizeof(int32_t));
-    A((void**)&c->spare.rplan[k], sizeof(uint32_t) * c->R[k]);
-    A((void**)&c->spare.ulist[k], sizeof(int32_t) * c->J);
-    A((void**)&c->spare.ustart[k], sizeof(int64_t) * (c->J + 1));
-    A((void**)&c->spare.ucount[k], sizeof(int32_t));
+  // The workspaces are planned (sizes summed) before anything is allocated, so that a process-wide
+  // cap (tt_set_workspace_limit) is enforced before any CUDA call.
+  const uint64_t planned = tt_workspace_plan(c);
+  c->ws_bytes = planned;
+  const uint64_t cap = g_workspace_limit.load();
+  if (cap && planned > cap) {
+    fprintf(stderr, "tt_sketch_init: workspaces need %llu bytes, above the limit of %llu bytes\n",
+            (unsigned long long)planned, (unsigned long long)cap);
+    delete c;
+    return TT_ENOMEM;
   }
-  A((void**)&c->spare.h, sizeof(int32_t) * c->noff[c->d]);
-  A((void**)&c->spare.v, sizeof(int8_t) * c->noff[c->d]);
-  A((void**)&c->d_ghat, sizeof(float2) * c->ghat_off[c->d]);
-  A((void**)&c->d_twiddle, sizeof(float2) * c->J);
-  A((void**)&c->d_twstage, sizeof(float2) * c->J);
-  A((void**)&c->d_suffix, sizeof(float2) * c->suffix_off[c->d]);
-  A((void**)&c->d_prefix, sizeof(float2) * H * c->rmax);
-  A((void**)&c->d_prefix_tmp, sizeof(float2) * H * c->rmax);
-  A((void**)&c->d_SH, sizeof(float) * c->J * c->smax);
-  A((void**)&c->d_Y, sizeof(float) * c->J * c->nmax);
-  c->yoff[0] = 0;
-  for (int k = 0; k < c->d; ++k) c->yoff[k + 1] = c->yoff[k] + (int64_t)c->J * c->n[k];
-  A((void**)&c->d_Yall, sizeof(float) * c->yoff[c->d]);
+  cudaError_t e = cudaSuccess;
+  tt_workspace_each(c, [&](void** ptr, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc(ptr, std::max<size_t>(bytes, 16));
+  });
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
   if (e == cudaSuccess) {
     int least = 0, greatest = 0;
@@ -556,21 +638,6 @@ extern "C" int tt_sketch_init(tt_ctx** out, const tt_params* p, void* stream) {
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_spare, cudaEventDisableTiming);
   for (int k = 0; k < c->d && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&c->ev_y[k], cudaEventDisableTiming);
-  A((void**)&c->d_gram, sizeof(float) * (c->smax + c->nmax) * c->smax);
-  A((void**)&c->d_core_old, sizeof(float) * c->nmax * c->smax);
-  c->changes_cap = 1024 * TT_MAX_D;
-  A((void**)&c->d_changes, sizeof(double) * 2 * c->changes_cap);
-  A((void**)&c->d_errs, sizeof(double) * 2 * (c->changes_cap / c->d));
-  A((void**)&c->d_status, sizeof(int));
-  A((void**)&c->d_err_acc, sizeof(double) * 4);
-  A((void**)&c->d_xgram, sizeof(double) * 2 * 32 * 32);
-  A((void**)&c->d_ws_acc, sizeof(double) * 2);
-  // streaming relative error (n_0 % 4 == 0, n_0 <= 1024, G_0 within 48 KB of shared memory)
-  c->rint_r1p = (c->r[1] + 3) & ~3;
-  if (c->n[0] % 4 == 0 && c->n[0] <= 1024 && (int64_t)c->rint_r1p * c->n[0] * 4 <= 48 * 1024) {
-    A((void**)&c->d_rint, sizeof(float) * (size_t)(c->N / c->n[0]) * c->rint_r1p);
-    A((void**)&c->d_slab_u, sizeof(float) * (size_t)(c->N / (c->n[0] * c->n[1])) * c->r[2]);
-  }
   if (e != cudaSuccess) {
     free_all(c);
     fprintf(stderr, "tt_sketch_init: cudaMalloc: %s\n", cudaGetErrorString(e));

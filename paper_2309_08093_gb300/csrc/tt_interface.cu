@@ -136,6 +136,7 @@ struct CoreFftArgs {
   const float2* tw;    // J/2 twiddles (radix-2 path)
   const float2* twst;  // per-stage twiddles (Stockham path)
   int J, logJ;
+  int det;             // deterministic mode: one thread adds the CountSketch entries in index order
 };
 
 __device__ __forceinline__ int fft_core_of(const CoreFftArgs& a, int pair) {
@@ -152,10 +153,13 @@ __global__ void k_core_fft(CoreFftArgs a) {  // one fibre per CTA (pair0 counts 
   const int al = fib % r0, be = fib / r0;
   for (int t = threadIdx.x; t < a.J; t += blockDim.x) buf[t] = make_float2(0.f, 0.f);
   __syncthreads();
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+  for (int i = a.det ? (threadIdx.x == 0 ? 0 : n) : threadIdx.x; i < n; i += a.det ? 1 : blockDim.x) {
     float g = a.core[q][al + (int64_t)r0 * (i + (int64_t)n * be)];
     float s = a.v[q][i] < 0 ? -g : g;
-    atomicAdd(&buf[a.h[q][i]].x, s);
+    if (a.det)
+      buf[a.h[q][i]].x += s;
+    else
+      atomicAdd(&buf[a.h[q][i]].x, s);
   }
   __syncthreads();
   block_fft(buf, a.tw, a.J, a.logJ);
@@ -177,14 +181,26 @@ __global__ void __launch_bounds__(512) k_core_fft2(CoreFftArgs a) {
   __syncthreads();
   const int al0 = f0 % r0, be0 = f0 / r0, al1 = f1 % r0, be1 = f1 / r0;
   const float* core = a.core[q];
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const int hb = a.h[q][i];
-    const bool neg = a.v[q][i] < 0;
-    const float g0 = core[al0 + (int64_t)r0 * (i + (int64_t)n * be0)];
-    atomicAdd(&x[hb].x, neg ? -g0 : g0);
-    if (has1) {
-      const float g1 = core[al1 + (int64_t)r0 * (i + (int64_t)n * be1)];
-      atomicAdd(&x[hb].y, neg ? -g1 : g1);
+  if (a.det) {  // index order: thread 0 the first fibre, thread 32 the second
+    if (threadIdx.x == 0 || (has1 && threadIdx.x == 32)) {
+      const int fb = threadIdx.x == 0 ? 0 : 1;
+      const int al = fb ? al1 : al0, be = fb ? be1 : be0;
+      for (int i = 0; i < n; ++i) {
+        const float g = core[al + (int64_t)r0 * (i + (int64_t)n * be)];
+        const float sg = a.v[q][i] < 0 ? -g : g;
+        if (fb) x[a.h[q][i]].y += sg; else x[a.h[q][i]].x += sg;
+      }
+    }
+  } else {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const int hb = a.h[q][i];
+      const bool neg = a.v[q][i] < 0;
+      const float g0 = core[al0 + (int64_t)r0 * (i + (int64_t)n * be0)];
+      atomicAdd(&x[hb].x, neg ? -g0 : g0);
+      if (has1) {
+        const float g1 = core[al1 + (int64_t)r0 * (i + (int64_t)n * be1)];
+        atomicAdd(&x[hb].y, neg ? -g1 : g1);
+      }
     }
   }
   const float2* Z = block_fft_stockham(x, y, a.twst, a.J, a.logJ);
@@ -219,6 +235,7 @@ static int launch_core_ffts(tt_ctx* c, float* const* cores, int j0, int j1) {
   a.twst = c->logJ >= 0 ? c->d_twstage : c->d_twiddle;  // per-stage tables, or the DFT table
   a.J = c->J;
   a.logJ = c->logJ;
+  a.det = c->det ? 1 : 0;
   if (two) {
     const size_t smem = 2 * sizeof(float2) * c->J;  // ping-pong buffers
     static bool attr = false;

@@ -26,6 +26,16 @@ __device__ __forceinline__ float2 tt_ffma2(float2 a, float2 b, float2 c) {
 #define TT_MAX_S_LARGE 512  // largest r[k]*r[k+1] of the one-CTA Cholesky solve
 size_t tt_large_solve_smem(int s, int n);  // its shared memory for s unknowns, n right-hand sides
 #define TT_MAX_J 16384
+// Relative pivot bound of the FP32 solves: a pivot at or below TT_PIVOT_TOL32 times the largest
+// diagonal entry of M + sigma I is refused. The FP32 Gram carries a rounding noise of about
+// sqrt(J) 2^-24 of that entry (up to about 1e-5 at J = 16384), which can lift the pivots of a
+// singular or nearly singular system to that level; below 1e-4 the FP32 update can no longer be
+// told from that noise (the FP64 update, TT_FLAG_FP64_SOLVE, resolves down to 1e-10)
+#define TT_PIVOT_TOL32 1e-4f
+#define TT_DET_KSPLIT 8     // K-chunks of the Gram in the deterministic mode
+#define TT_DET_PARTS 8192   // capacity (CTAs) of the deterministic partial-sum buffers
+size_t tt_chol64_smem(int s);           // shared memory of the FP64 Cholesky for s unknowns
+size_t tt_trsm64_smem(int s, int nc);   // and of its triangular solves, nc right-hand sides per CTA
 
 // (a + b) mod J for bucket indices a, b < J (any J)
 __host__ __device__ __forceinline__ int tt_modj(int x, int J) { return x >= J ? x - J : x; }
@@ -123,6 +133,15 @@ struct tt_ctx {
   float* d_Yall = nullptr;
   int64_t yoff[TT_MAX_D + 1] = {0};
   float* d_gram = nullptr;     // (smax + nmax) x smax FP32 accumulators of [SH | Y]^T SH
+  bool solve64 = false;        // the FP64 update (sigma = 0 or TT_FLAG_FP64_SOLVE)
+  double* d_gram64 = nullptr;  // (smax + nmax) x smax FP64 accumulators, then L, when solve64
+  // deterministic summation order (TT_FLAG_DETERMINISTIC, tt_det.cu)
+  bool det = false;
+  int* d_det_misc = nullptr;        // [0] bits of max |A|, [1] fixed-point exponent S, [2] A not finite
+  int64_t* d_y64 = nullptr;         // int64 data-sketch accumulators, mode k at yoff[k]
+  void* d_gram_part = nullptr;      // TT_DET_KSPLIT K-chunk partials of the Gram (FP32 or FP64)
+  double* d_part_err = nullptr;     // per-CTA partial sums of the relative error (2 per CTA)
+  double* d_part_chg = nullptr;     // per-CTA partial sums of the change norms (2 per CTA)
   float* d_core_old = nullptr; // proximal centre copy (nmax * smax)
   double* d_changes = nullptr; // per (sweep, k): ||dG||^2, ||G||^2
   int* d_status = nullptr;     // device error flag (0 = ok, else TT_E* code)
@@ -151,6 +170,8 @@ struct tt_ctx {
   // autotuned parameters of the unfold kernel per mode (0 = default)
   int tune_seg_mult[TT_MAX_D] = {0};   // multiplier of the work-item count
   int tune_cta_per_sm[TT_MAX_D] = {0}; // CTAs per SM (1 or 2)
+
+  uint64_t ws_bytes = 0;        // bytes of the workspaces planned at creation (tt_workspace_each)
 
   // host-buffer entry point staging (allocated on first use)
   void* d_A_stage = nullptr;
@@ -213,6 +234,21 @@ int tt_launch_interface_from_chain(tt_ctx* c, int k, float* SH, float* zero = nu
 int tt_launch_prox_update(tt_ctx* c, const float* Y, const float* SH, float* core, int k,
                           double* change_slot,
                           bool gram_zeroed = false);  // gram_zeroed: d_gram already zero
+// deterministic mode (tt_det.cu): the data sketches of the modes in `mask` in int64 fixed point
+// (Y[k] written for those modes), the ordered sum of per-CTA partials into acc[0..1], and the
+// ordered sum of the Gram's K-chunk partials
+int tt_launch_unfold_det(tt_ctx* c, const void* A, const float* scales, unsigned mask, float* const* Y);
+int tt_launch_sum_partials(tt_ctx* c, const double* part, int nparts, double* acc);
+int tt_launch_gram_reduce(tt_ctx* c, const void* P, int nz, int64_t count, void* C, bool f64);
+// tensor-core Gram of the FP32 update (tt_gram_tc.cu): whether the shape and pointers suit TMA,
+// and C (zeroed, or P's ordered sum in the deterministic mode) = [S H | Y]^T S H in TF32 x 3
+// (split3) or TF32 x 1
+bool tt_gram_tc_fits(int J, int s, const void* SH, const void* Y);
+int tt_launch_gram_tc(tt_ctx* c, const float* SH, const float* Y, int s, int n, float* C, float* P, bool split3,
+                      int* nz_out);
+// the same update in FP64 (FP64 Gram, Cholesky and triangular solves; tt_solve64.cu)
+int tt_launch_prox_update64(tt_ctx* c, const float* Y, const float* SH, float* core, int k, double* change_slot,
+                            bool gram_zeroed);
 int tt_launch_qr_left(tt_ctx* c, float* core_k, float* core_k1, int k);
 int tt_launch_lq_right(tt_ctx* c, float* core_km1, float* core_k, int k);
 int tt_launch_lq_sweep(tt_ctx* c, float* const* cores);  // all right-to-left steps
@@ -232,6 +268,11 @@ int tt_one_sweep(tt_ctx* c, const void* A, const float* scales, float* const* co
 int tt_prof_begin(tt_ctx* c, int k);   // record a start event when profiling (returns TT_OK)
 int tt_prof_end(tt_ctx* c);
 int tt_elem_bytes(int dtype);
+// number of SMs of the current device (queried once per device; 152 if the query fails)
+int tt_sm_count();
+// TT_ENOMEM (with a message) when the context's workspaces plus `extra` bytes would exceed the
+// process-wide cap of tt_set_workspace_limit; TT_OK otherwise
+int tt_check_workspace_cap(tt_ctx* c, uint64_t extra);
 
 // element loads of the data tensor in its storage type, converted to float
 template <int DT>

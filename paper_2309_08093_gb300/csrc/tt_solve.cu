@@ -37,6 +37,8 @@ struct GramArgs {
   const float* Y;   // J x n column-major
   float* C;         // accumulators (zeroed by the caller): s x s Gram, then the s x n RHS
                     // (SH^T Y, row-major) -- both row-major
+  int* status;      // raised to TT_ENONFINITE when a sum is not finite (may be null)
+  float* P;         // deterministic mode: K-chunk z stores its sums at P + z (s + n) s (no atomics)
   int J, s, n, kchunk;
 };
 
@@ -45,7 +47,8 @@ struct GramArgs {
 // thread reads its 4 rows and 4 columns with two 16-byte loads per k (8 FMAs per load); the next
 // step's global loads (16 bytes per thread and operand when VEC: J % 16 == 0 and aligned bases;
 // else 4 bounds-checked scalars) are in flight while the current step is multiplied. Chunks are
-// summed with FP32 atomics.
+// summed with FP32 atomics. A non-finite partial sum (a NaN or Inf in S H_k or Y_k) raises
+// TT_ENONFINITE, so the solve that follows leaves the core unchanged.
 template <bool VEC>
 __global__ void __launch_bounds__(256) k_gram(GramArgs a) {
   __shared__ __align__(16) float Xs[16][68];
@@ -105,28 +108,35 @@ __global__ void __launch_bounds__(256) k_gram(GramArgs a) {
     }
     __syncthreads();
   }
+  bool finite = true;
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int row = r0 + ty * 4 + i, col = c0 + tx * 4 + j;
       if (col >= a.s || row >= rows) continue;
-      if (row < a.s)
-        atomicAdd(a.C + (int64_t)row * a.s + col, acc[i][j]);
-      else  // right-hand side stored transposed: s x n
-        atomicAdd(a.C + (int64_t)a.s * a.s + (int64_t)col * a.n + (row - a.s), acc[i][j]);
+      finite = finite && isfinite(acc[i][j]);
+      // the Gram row-major, then the right-hand side stored transposed (s x n)
+      const int64_t idx = row < a.s ? (int64_t)row * a.s + col : (int64_t)a.s * a.s + (int64_t)col * a.n + (row - a.s);
+      if (a.P)
+        a.P[(int64_t)blockIdx.z * (a.s + a.n) * a.s + idx] = acc[i][j];
+      else
+        atomicAdd(a.C + idx, acc[i][j]);
     }
+  if (!finite && a.status) atomicCAS(a.status, 0, TT_ENONFINITE);
 }
 
-// Gram + right-hand side (C zeroed by the caller), any J >= 1.
-static cudaError_t launch_gram(GramArgs g, cudaStream_t st) {
+// Gram + right-hand side (C zeroed by the caller), any J >= 1. With g.P set (deterministic mode)
+// at most TT_DET_KSPLIT K-chunks store partials that the caller sums in order.
+static cudaError_t launch_gram(GramArgs g, cudaStream_t st, int* nz_out = nullptr) {
   const int mt = (g.s + g.n + 63) / 64, nt = (g.s + 63) / 64;
-  int sms = 152;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+  const int sms = tt_sm_count();
   // K-chunks: about two CTAs per SM in all, each at least 64 rows of K
-  const int ksplit = std::max(1, std::min(g.J / 64, (2 * sms + mt * nt - 1) / (mt * nt)));
+  int ksplit = std::max(1, std::min(g.J / 64, (2 * sms + mt * nt - 1) / (mt * nt)));
+  if (g.P) ksplit = std::min(ksplit, TT_DET_KSPLIT);
   g.kchunk = ((g.J + ksplit - 1) / ksplit + 15) & ~15;
   dim3 grid(mt, nt, (g.J + g.kchunk - 1) / g.kchunk);
+  if (nz_out) *nz_out = (int)grid.z;
   const bool vec = g.J % 16 == 0 && ((reinterpret_cast<uintptr_t>(g.SH) | reinterpret_cast<uintptr_t>(g.Y)) & 15) == 0;
   if (vec)
     k_gram<true><<<grid, 256, 0, st>>>(g);
@@ -142,6 +152,7 @@ struct SolveArgs {
   const float* C;   // s x s Gram SH^T SH, then s x n SH^T Y (both row-major)
   float* core;      // r0 x n x r1 (read: proximal centre; written: update)
   double* change;   // [0] += ||G_new - G_old||^2, [1] += ||G_new||^2 (may be null)
+  double* part;     // deterministic mode: CTA b stores its two change sums at part[2 b]
   int* status;
   double sigma;
   int s, n, r0, r1;
@@ -159,12 +170,15 @@ struct SolveArgs {
 // the group G): row j is then register block G of warp j - TY G and column j register block
 // TY G / 32 of lane j % 32, both compile-time, so no register is ever selected by a runtime
 // index. Column blocks wholly left of the group's pivots are dead and skipped.
+// A pivot at or below `thr` (TT_PIVOT_TOL32 times the largest diagonal entry of M + sigma I: the
+// system cannot be told from the FP32 Gram's rounding noise) refuses the update with TT_ENOTSPD.
 template <int TY, int RA, int CB, int G>
-__device__ __forceinline__ void gj_publish_row(float (&w)[RA][CB], int jn, float* rowb, int* bad, int ty, int tx) {
+__device__ __forceinline__ void gj_publish_row(float (&w)[RA][CB], int jn, float* rowb, int* bad, int ty, int tx,
+                                               float thr) {
   constexpr int CN = (TY * G) / 32;  // column block of pivots TY G .. TY G + TY - 1
   if (ty == jn - TY * G) {           // the warp that owns row jn (register block G)
     const float p = __shfl_sync(0xffffffffu, w[G][CN], jn & 31);
-    if (tx == 0 && (!(p > 0.f) || !isfinite(p))) atomicCAS(bad, 0, isfinite(p) ? TT_ENOTSPD : TT_ENONFINITE);
+    if (tx == 0 && (!(p > thr) || !isfinite(p))) atomicCAS(bad, 0, isfinite(p) ? TT_ENOTSPD : TT_ENONFINITE);
     const float ip = 1.f / p;
 #pragma unroll
     for (int cb = 0; cb < CB; ++cb) {
@@ -177,7 +191,7 @@ __device__ __forceinline__ void gj_publish_row(float (&w)[RA][CB], int jn, float
 
 template <int TY, int RA, int CB, int G>
 __device__ __forceinline__ void gj_groups(float (&w)[RA][CB], int s, float (*rowbuf)[CB * 32], int* bad, int& bs,
-                                          int ty, int tx) {
+                                          int ty, int tx, float thr) {
   if constexpr (G < RA) {
     constexpr int CN = (TY * G) / 32;  // column block of this group's pivots = first live block
     const int j0 = TY * G;
@@ -212,14 +226,14 @@ __device__ __forceinline__ void gj_groups(float (&w)[RA][CB], int s, float (*row
       const int jn = j0 + jj + 1;
       if (jn < s) {
         if (jj + 1 < TY)
-          gj_publish_row<TY, RA, CB, G>(w, jn, rowbuf[bs ^ 1], bad, ty, tx);
+          gj_publish_row<TY, RA, CB, G>(w, jn, rowbuf[bs ^ 1], bad, ty, tx, thr);
         else if constexpr (G + 1 < RA)
-          gj_publish_row<TY, RA, CB, G + 1>(w, jn, rowbuf[bs ^ 1], bad, ty, tx);
+          gj_publish_row<TY, RA, CB, G + 1>(w, jn, rowbuf[bs ^ 1], bad, ty, tx, thr);
       }
       __syncthreads();
       bs ^= 1;
     }
-    gj_groups<TY, RA, CB, G + 1>(w, s, rowbuf, bad, bs, ty, tx);
+    gj_groups<TY, RA, CB, G + 1>(w, s, rowbuf, bad, bs, ty, tx, thr);
   }
 }
 
@@ -230,13 +244,17 @@ __global__ void __launch_bounds__(TY * 32) k_prox_solve(SolveArgs a) {
   __shared__ float gsm[RA * TY][33];  // this chunk of G_{k(2)}^T: proximal centre, then the update
   __shared__ float red[2][TY];
   __shared__ int bad;
+  __shared__ int dmax_bits;  // largest diagonal entry of M + sigma I (a positive float's bits)
   const int t = threadIdx.x, tx = t & 31, ty = t >> 5;
   const int s = a.s, r0 = a.r0, n = a.n;
   const int i0 = blockIdx.x * a.chunk_rows;
   const int nr = min(a.chunk_rows, n - i0);
   const int ncol = s + nr;
   const float sigma = (float)a.sigma;
-  if (*a.status != 0) return;
+  __shared__ int skip;  // the status read once: other CTAs of this kernel may raise it meanwhile
+  if (t == 0) skip = *a.status != 0;
+  __syncthreads();
+  if (skip) return;
   // M and the transposed right-hand side: unconditional loads (clamped addresses) so that many
   // are in flight at once; row-major rows of both are read along the lanes
   float w[RA][CB];
@@ -258,9 +276,13 @@ __global__ void __launch_bounds__(TY * 32) k_prox_solve(SolveArgs a) {
     cp_async4(&gsm[al + r0 * be][r], a.core + al + (int64_t)r0 * ((i0 + r) + (int64_t)n * be));
   }
   cp_async_commit();
-  if (t == 0) bad = 0;
+  if (t == 0) {
+    bad = 0;
+    dmax_bits = 0;
+  }
   cp_async_wait<0>();
   __syncthreads();
+  float dloc = 0.f;
 #pragma unroll
   for (int ra = 0; ra < RA; ++ra) {
     const int i = ty + TY * ra;
@@ -271,13 +293,19 @@ __global__ void __launch_bounds__(TY * 32) k_prox_solve(SolveArgs a) {
       float v = w[ra][cb];
       if (l == i) v += sigma;
       if (in && l >= s) v = fmaf(sigma, gsm[i][l - s], v);
+      if (in && l == i) dloc = fmaxf(dloc, v);
       w[ra][cb] = in ? v : 0.f;
     }
   }
-  gj_publish_row<TY, RA, CB, 0>(w, 0, rowbuf[0], &bad, ty, tx);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) dloc = fmaxf(dloc, __shfl_xor_sync(0xffffffffu, dloc, o));
+  if (tx == 0 && dloc > 0.f) atomicMax(&dmax_bits, __float_as_int(dloc));  // positive floats order as ints
+  __syncthreads();
+  const float thr = TT_PIVOT_TOL32 * __int_as_float(dmax_bits);
+  gj_publish_row<TY, RA, CB, 0>(w, 0, rowbuf[0], &bad, ty, tx, thr);
   __syncthreads();
   int bs = 0;
-  gj_groups<TY, RA, CB, 0>(w, s, rowbuf, &bad, bs, ty, tx);
+  gj_groups<TY, RA, CB, 0>(w, s, rowbuf, &bad, bs, ty, tx, thr);
   if (bad) {  // read after the last step's barrier: the same value in every thread
     if (t == 0) atomicCAS(a.status, 0, bad);
     return;
@@ -320,8 +348,13 @@ __global__ void __launch_bounds__(TY * 32) k_prox_solve(SolveArgs a) {
       t1 += red[0][u];
       t2 += red[1][u];
     }
-    atomicAdd(a.change, (double)t1);
-    atomicAdd(a.change + 1, (double)t2);
+    if (a.part) {
+      a.part[2 * blockIdx.x] = (double)t1;
+      a.part[2 * blockIdx.x + 1] = (double)t2;
+    } else {
+      atomicAdd(a.change, (double)t1);
+      atomicAdd(a.change + 1, (double)t2);
+    }
   }
 }
 
@@ -332,11 +365,12 @@ struct SolveShape {
 };
 static const SolveShape kSolveShapes[] = {{8, 4, 2}, {8, 14, 4}, {16, 10, 6}};
 
-static cudaError_t launch_prox_solve(SolveArgs a, cudaStream_t st) {
+static cudaError_t launch_prox_solve(SolveArgs a, cudaStream_t st, int* grid_out = nullptr) {
   for (const SolveShape& sh : kSolveShapes) {
     if (a.s > sh.ty * sh.ra || a.s + 1 > 32 * sh.cb) continue;
     a.chunk_rows = std::max(1, std::min(a.n, std::min(32, 32 * sh.cb - a.s)));
     const int grid = (a.n + a.chunk_rows - 1) / a.chunk_rows;
+    if (grid_out) *grid_out = grid;
     if (sh.ra == 4)
       k_prox_solve<8, 4, 2><<<grid, 256, 0, st>>>(a);
     else if (sh.ra == 14)
@@ -361,6 +395,7 @@ constexpr int LS_NB = 32, LS_P = 33;
 __global__ void __launch_bounds__(1024) k_prox_solve_large(SolveArgs a) {
   extern __shared__ float lsm[];
   __shared__ int bad;
+  __shared__ int dmax_bits;  // largest diagonal entry of M + sigma I (a positive float's bits)
   const int s = a.s, n = a.n, r0 = a.r0;
   const int t = threadIdx.x, T = blockDim.x;
   float* P = lsm;                       // panel, rows x LS_P
@@ -369,13 +404,22 @@ __global__ void __launch_bounds__(1024) k_prox_solve_large(SolveArgs a) {
   const float* BT = a.C + (size_t)s * s;
   const float sigma = (float)a.sigma;
   if (*a.status != 0) return;
-  if (t == 0) bad = 0;
+  if (t == 0) {
+    bad = 0;
+    dmax_bits = 0;
+  }
+  __syncthreads();
+  float dloc = 0.f;
+  for (int i = t; i < s; i += T) dloc = fmaxf(dloc, M[(size_t)i * s + i] + sigma);
+  for (int o = 16; o > 0; o >>= 1) dloc = fmaxf(dloc, __shfl_xor_sync(0xffffffffu, dloc, o));
+  if ((t & 31) == 0 && dloc > 0.f) atomicMax(&dmax_bits, __float_as_int(dloc));
   for (int e = t; e < s * n; e += T) {  // Z = B^T + sigma G_c
     const int i = e / n, r = e - i * n;
     const int be = i / r0, al = i - be * r0;
     Z[e] = fmaf(sigma, a.core[al + (int64_t)r0 * (r + (int64_t)n * be)], BT[e]);
   }
   __syncthreads();
+  const float thr = TT_PIVOT_TOL32 * __int_as_float(dmax_bits);
   for (int p0 = 0; p0 < s; p0 += LS_NB) {
     const int pb = min(LS_NB, s - p0), rows = s - p0;
     for (int e = t; e < rows * LS_NB; e += T) {
@@ -387,7 +431,7 @@ __global__ void __launch_bounds__(1024) k_prox_solve_large(SolveArgs a) {
     __syncthreads();
     for (int c = 0; c < pb; ++c) {
       const float d = P[c * LS_P + c];
-      if (!(d > 0.f) || !isfinite(d)) {
+      if (!(d > thr) || !isfinite(d)) {
         if (t == 0) bad = isfinite(d) ? TT_ENOTSPD : TT_ENONFINITE;
         break;  // every thread reads the same d
       }
@@ -463,14 +507,25 @@ __global__ void __launch_bounds__(1024) k_prox_solve_large(SolveArgs a) {
     nsum = fmaf(nw, nw, nsum);
     *g = nw;
   }
-  if (a.change) {
+  if (a.change) {  // one CTA: warp sums added in warp order (the same bits on every run)
+    __shared__ float cred[2][32];
     for (int o = 16; o > 0; o >>= 1) {
       dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
       nsum += __shfl_xor_sync(0xffffffffu, nsum, o);
     }
     if ((t & 31) == 0) {
-      atomicAdd(a.change, (double)dsum);
-      atomicAdd(a.change + 1, (double)nsum);
+      cred[0][t >> 5] = dsum;
+      cred[1][t >> 5] = nsum;
+    }
+    __syncthreads();
+    if (t == 0) {
+      double t1 = 0.0, t2 = 0.0;
+      for (int w = 0; w < (T >> 5); ++w) {
+        t1 += cred[0][w];
+        t2 += cred[1][w];
+      }
+      atomicAdd(a.change, t1);
+      atomicAdd(a.change + 1, t2);
     }
   }
 }
@@ -479,6 +534,7 @@ size_t tt_large_solve_smem(int s, int n) { return sizeof(float) * ((size_t)s * L
 
 int tt_launch_prox_update(tt_ctx* c, const float* Y, const float* SH, float* core, int k,
                           double* change_slot, bool gram_zeroed) {
+  if (c->solve64) return tt_launch_prox_update64(c, Y, SH, core, k, change_slot, gram_zeroed);
   const int s = c->r[k] * c->r[k + 1];
   const int n = (int)c->n[k];
   if (!gram_zeroed) TT_CUDA(c, cudaMemsetAsync(c->d_gram, 0, sizeof(float) * (s + n) * s, c->stream));
@@ -486,11 +542,19 @@ int tt_launch_prox_update(tt_ctx* c, const float* Y, const float* SH, float* cor
   g.SH = SH;
   g.Y = Y;
   g.C = c->d_gram;
+  g.status = c->d_status;
+  g.P = c->det ? static_cast<float*>(c->d_gram_part) : nullptr;
   g.J = c->J;
   g.s = s;
   g.n = n;
-  TT_CUDA(c, launch_gram(g, c->stream));
-  TT_LAUNCH(c, "k_gram");
+  int nz = 1;
+  if ((c->flags & (TT_FLAG_TC_GRAM | TT_FLAG_TF32_GRAM)) && tt_gram_tc_fits(c->J, s, SH, Y)) {
+    TT_TRY(tt_launch_gram_tc(c, SH, Y, s, n, c->d_gram, g.P, !(c->flags & TT_FLAG_TF32_GRAM), &nz));
+  } else {
+    TT_CUDA(c, launch_gram(g, c->stream, &nz));
+    TT_LAUNCH(c, "k_gram");
+  }
+  if (c->det) TT_TRY(tt_launch_gram_reduce(c, c->d_gram_part, nz, (int64_t)(s + n) * s, c->d_gram, false));
   SolveArgs a;
   a.C = c->d_gram;
   a.core = core;
@@ -501,6 +565,7 @@ int tt_launch_prox_update(tt_ctx* c, const float* Y, const float* SH, float* cor
   a.n = n;
   a.r0 = c->r[k];
   a.r1 = c->r[k + 1];
+  a.part = nullptr;
   if (change_slot) TT_CUDA(c, cudaMemsetAsync(change_slot, 0, 2 * sizeof(double), c->stream));
   if (s > TT_MAX_S) {  // Cholesky in one CTA (sizes checked at context creation)
     const size_t smem = tt_large_solve_smem(s, n);
@@ -509,8 +574,11 @@ int tt_launch_prox_update(tt_ctx* c, const float* Y, const float* SH, float* cor
     TT_LAUNCH(c, "k_prox_solve_large");
     return TT_OK;
   }
-  TT_CUDA(c, launch_prox_solve(a, c->stream));
+  if (c->det && change_slot) a.part = c->d_part_chg;  // grid <= n_k <= the buffer's CTAs
+  int grid = 0;
+  TT_CUDA(c, launch_prox_solve(a, c->stream, &grid));
   TT_LAUNCH(c, "k_prox_solve");
+  if (a.part) TT_TRY(tt_launch_sum_partials(c, a.part, grid, change_slot));
   return TT_OK;
 }
 
@@ -1348,6 +1416,7 @@ struct ErrArgs {
   int nchunks;        // ceil(n_1 / i1chunk)
   int g0_in_smem;     // G_0 (n_0 x r_1) staged in shared memory
   double* acc;        // [0] += ||A - [[G]]||^2, [1] += ||A||^2
+  double* part;       // deterministic mode: CTA b stores its two sums at part[2 b] (no atomics)
 };
 
 template <int DT>
@@ -1538,8 +1607,13 @@ __global__ void __launch_bounds__(256) k_rel_error(ErrArgs a) {
       t1 += red[0][w];
       t2 += red[1][w];
     }
-    atomicAdd(a.acc, t1);
-    atomicAdd(a.acc + 1, t2);
+    if (a.part) {
+      a.part[2 * blockIdx.x] = t1;
+      a.part[2 * blockIdx.x + 1] = t2;
+    } else {
+      atomicAdd(a.acc, t1);
+      atomicAdd(a.acc + 1, t2);
+    }
   }
 }
 
@@ -1753,7 +1827,8 @@ __device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_
 template <int DT>
 __global__ void __launch_bounds__(256, 2) k_rel_error_stream(const void* __restrict__ A, const float* __restrict__ scales,
                                                           const float* __restrict__ g0, const float* __restrict__ R,
-                                                          int n0, int r1, int r1p, int64_t M0, double* acc) {
+                                                          int n0, int r1, int r1p, int64_t M0, double* acc,
+                                                          double* part) {
   constexpr int ES = ElemSize<DT>::value;
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ double red[2][8];
@@ -1871,8 +1946,13 @@ __global__ void __launch_bounds__(256, 2) k_rel_error_stream(const void* __restr
       t1 += red[0][w];
       t2 += red[1][w];
     }
-    atomicAdd(acc, t1);
-    atomicAdd(acc + 1, t2);
+    if (part) {
+      part[2 * blockIdx.x] = t1;
+      part[2 * blockIdx.x + 1] = t2;
+    } else {
+      atomicAdd(acc, t1);
+      atomicAdd(acc + 1, t2);
+    }
   }
 }
 
@@ -1894,17 +1974,18 @@ static int launch_rel_stream(tt_ctx* c, const void* A, const float* scales, cons
     TT_CUDA(c, cudaFuncSetAttribute(k_rel_error_stream<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     attr = true;
   }
-  int per_sm = 0, dev = 0, sms = 0;
+  int per_sm = 0;
   TT_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rel_error_stream<DT>, 256, smem));
-  TT_CUDA(c, cudaGetDevice(&dev));
-  TT_CUDA(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int sms = tt_sm_count();
   const int64_t M0 = c->N / c->n[0];
   const int64_t Q = c->n[0] / 4, FT = (256 / Q) * REL_U;
   const int64_t ntiles = (M0 + FT - 1) / FT;
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)std::max(1, per_sm) * sms));
+  double* part = c->det ? c->d_part_err : nullptr;  // at most TT_DET_PARTS CTAs: a few per SM
   k_rel_error_stream<DT><<<blocks, 256, smem, c->stream>>>(A, scales, g0, c->d_rint, (int)c->n[0], c->r[1],
-                                                          c->rint_r1p, M0, acc);
+                                                          c->rint_r1p, M0, acc, part);
   TT_LAUNCH(c, "k_rel_error_stream");
+  if (part) TT_TRY(tt_launch_sum_partials(c, part, blocks, acc));
   return TT_OK;
 }
 
@@ -1920,6 +2001,7 @@ int tt_launch_rel_error(tt_ctx* c, const void* A, const float* scales, float* co
   for (int k = 0; k <= c->d; ++k) a.r[k] = c->r[k];
   a.d = c->d;
   a.acc = acc;
+  a.part = nullptr;
   a.slabs = c->N / (c->n[0] * c->n[1]);
   // i_1 chunk (multiple of 4): W (r1 x chunk) plus G_0 (r1 x n0) within ~200 KB, at most ~16K
   // entries per item, and at least ~4 items per SM overall
@@ -1927,7 +2009,7 @@ int tt_launch_rel_error(tt_ctx* c, const void* A, const float* scales, float* co
   int64_t chunk = std::max<int64_t>(4, std::min<int64_t>(c->n[1], 16384 / std::max<int64_t>(1, c->n[0])));
   chunk = (chunk + 3) & ~3ll;
   while (chunk > 4 && (int64_t)c->r[1] * chunk + g0sz > 50 * 1024) chunk -= 4;
-  while (chunk > 4 && a.slabs * ((c->n[1] + chunk - 1) / chunk) < 152 * 4) chunk = ((chunk / 2) + 3) & ~3ll;
+  while (chunk > 4 && a.slabs * ((c->n[1] + chunk - 1) / chunk) < (int64_t)tt_sm_count() * 4) chunk = ((chunk / 2) + 3) & ~3ll;
   a.i1chunk = (int)chunk;
   a.nchunks = (int)((c->n[1] + chunk - 1) / chunk);
   a.g0_in_smem = 1;
@@ -1940,8 +2022,7 @@ int tt_launch_rel_error(tt_ctx* c, const void* A, const float* scales, float* co
     const int r2 = c->r[2];
     const int rthreads = ((per + RINT_KP - 1) / RINT_KP + 31) & ~31;
     if (rthreads <= 512 && r2 <= 16) {  // G_1 entries in registers, u_t formed in the same kernel
-      int sms = 152;
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+      const int sms = tt_sm_count();
       // one slab run per SM (one CTA fits per SM: a single wave pays the G_1 and u_t prologue once
       // per SM); a run's u_t and the two level buffers within the default 48 KB of shared memory
       int rmax = 1;
@@ -1964,7 +2045,7 @@ int tt_launch_rel_error(tt_ctx* c, const void* A, const float* scales, float* co
       const int ublocks = (int)std::max<int64_t>(1, std::min<int64_t>((a.slabs + 255) / 256, 4096));
       k_slab_u<<<ublocks, 256, 0, c->stream>>>(a, c->d_slab_u);
       TT_LAUNCH(c, "k_slab_u");
-      const int rblocks = (int)std::max<int64_t>(1, std::min<int64_t>(a.slabs, 152 * 8));
+      const int rblocks = (int)std::max<int64_t>(1, std::min<int64_t>(a.slabs, (int64_t)tt_sm_count() * 8));
       k_rint<<<rblocks, 256, 0, c->stream>>>(a, c->d_slab_u, c->d_rint, c->rint_r1p);
       TT_LAUNCH(c, "k_rint");
     }
@@ -1976,7 +2057,8 @@ int tt_launch_rel_error(tt_ctx* c, const void* A, const float* scales, float* co
     }
   }
   const int64_t items = a.slabs * a.nchunks;
-  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(items, 152 * 8));
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(items, (int64_t)tt_sm_count() * 8));
+  a.part = c->det ? c->d_part_err : nullptr;  // blocks <= 8 per SM <= TT_DET_PARTS
   switch (c->dtype) {
     case TT_F64:
       TT_CUDA(c, cudaFuncSetAttribute(k_rel_error<TT_F64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -1996,6 +2078,7 @@ int tt_launch_rel_error(tt_ctx* c, const void* A, const float* scales, float* co
       break;
   }
   TT_LAUNCH(c, "k_rel_error");
+  if (a.part) TT_TRY(tt_launch_sum_partials(c, a.part, blocks, acc));
   return TT_OK;
 }
 
@@ -2003,10 +2086,11 @@ int tt_launch_rel_error(tt_ctx* c, const void* A, const float* scales, float* co
 // Allocation-free variant of the proximal update (see tt_prox_update_noalloc in tt_sketch.h).
 //
 // Its only scratch -- the FP32 accumulators of [SH | Y]^T SH and the status word -- lives in the
-// file-scope array below, sized for s = r0*r1 <= 160 and n <= 1024. Every GPU that loads the
-// library holds these ~1.5 MB until the process exits. In host code `g_noalloc_scratch` only
-// names a host-side stand-in, so the device address is looked up once per device with
-// cudaGetSymbolAddress (on the first call made while that device is current).
+// file-scope array below, sized for s = r0*r1 <= 160 and n <= 1024: (160 + 1024) x 160 floats and
+// the status word, about 0.76 MB that every GPU loading the library holds until the process
+// exits. In host code `g_noalloc_scratch` only names a host-side stand-in, so the device address
+// is looked up once per device with cudaGetSymbolAddress (on the first call made while that
+// device is current).
 
 #include <mutex>
 
@@ -2015,7 +2099,7 @@ int tt_launch_rel_error(tt_ctx* c, const void* A, const float* scales, float* co
 #define TT_NOALLOC_GRAM ((TT_NOALLOC_MAX_S + TT_NOALLOC_MAX_N) * TT_NOALLOC_MAX_S)
 #define TT_NOALLOC_MAX_DEVICES 64
 
-static __device__ __align__(256) double g_noalloc_scratch[TT_NOALLOC_GRAM + 32];
+static __device__ __align__(256) float g_noalloc_scratch[TT_NOALLOC_GRAM + 64];  // Gram, then the status word
 
 static std::mutex g_noalloc_mutex;
 static void* g_noalloc_ptr[TT_NOALLOC_MAX_DEVICES];
@@ -2036,8 +2120,12 @@ static int noalloc_scratch(void** out) {
 extern "C" int tt_prox_update_noalloc(const float* Y_dev, const float* SH_dev, float* core_dev, int J, int n,
                                       int r0, int r1, double sigma, void* cuda_stream) {
   if (!Y_dev || !SH_dev || !core_dev) return TT_EINVAL;
-  const int s = r0 * r1;
-  if (J < 1 || n < 1 || r0 < 1 || r1 < 1 || s > TT_NOALLOC_MAX_S || n > TT_NOALLOC_MAX_N || !(sigma >= 0.0)) {
+  // each rank is bounded before the product is formed (in 64 bits), so that no pair of ranks can
+  // wrap r0 * r1 into the accepted range
+  const bool ranks_ok = r0 >= 1 && r1 >= 1 && r0 <= TT_NOALLOC_MAX_S && r1 <= TT_NOALLOC_MAX_S &&
+                        (int64_t)r0 * r1 <= TT_NOALLOC_MAX_S;
+  const int s = ranks_ok ? r0 * r1 : 0;
+  if (J < 1 || n < 1 || !ranks_ok || n > TT_NOALLOC_MAX_N || !(sigma >= 0.0)) {
     fprintf(stderr,
             "tt_prox_update_noalloc: sizes outside the static scratch (need J >= 1, 1 <= n <= %d, "
             "r0*r1 <= %d, sigma >= 0; got J=%d n=%d r0=%d r1=%d)\n",
@@ -2049,7 +2137,7 @@ extern "C" int tt_prox_update_noalloc(const float* Y_dev, const float* SH_dev, f
   int rc = noalloc_scratch(&base);
   if (rc) return rc;
   float* gram = (float*)base;
-  int* status = (int*)((double*)base + TT_NOALLOC_GRAM);
+  int* status = (int*)(gram + TT_NOALLOC_GRAM);
   // the array keeps the previous call's contents: clear the accumulators and the status word
   if (cudaMemsetAsync(gram, 0, sizeof(float) * (size_t)(s + n) * s, st) != cudaSuccess) return TT_ECUDA;
   if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return TT_ECUDA;
@@ -2057,6 +2145,8 @@ extern "C" int tt_prox_update_noalloc(const float* Y_dev, const float* SH_dev, f
   g.SH = SH_dev;
   g.Y = Y_dev;
   g.C = gram;
+  g.status = status;
+  g.P = nullptr;
   g.J = J;
   g.s = s;
   g.n = n;
@@ -2065,6 +2155,7 @@ extern "C" int tt_prox_update_noalloc(const float* Y_dev, const float* SH_dev, f
   a.C = gram;
   a.core = core_dev;
   a.change = nullptr;
+  a.part = nullptr;
   a.status = status;
   a.sigma = sigma;
   a.s = s;
@@ -2197,8 +2288,7 @@ int tt_launch_rel_error_coo(tt_ctx* c, const int32_t* idx, const float* val, int
   a.status = c->d_status;
   TT_CUDA(c, cudaMemsetAsync(c->d_err_acc, 0, sizeof(double) * 3, c->stream));
   if (nnz > 0) {
-    int sms = 152;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+    const int sms = tt_sm_count();
     const int blocks = (int)std::min<int64_t>((nnz + 255) / 256, (int64_t)sms * 8);
     if (rmax <= 8)
       k_coo_inner<8><<<blocks, 256, 0, c->stream>>>(a);

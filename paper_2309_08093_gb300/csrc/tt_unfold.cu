@@ -628,8 +628,7 @@ static int launch_cols_s(tt_ctx* c, const void* A, const float* scales, int k, f
   a.ncol = (int)c->n[k];
   a.col_fibres = c->stride[k] / c->n[0];
   a.fg = fibre_geom(fiber_bytes, VB, 1);
-  int sms = 152;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+  const int sms = tt_sm_count();
   const int ncolg = (a.ncol + G - 1) / G;
   const int slots = 2 * sms;
   // one item per CTA slot; four times as many beside the chain (shorter CTAs hand SM slots to
@@ -693,8 +692,7 @@ static int launch_gather_vbm(tt_ctx* c, const void* A, const float* scales, int 
   a.ncol = MODE0 ? 1 : (int)c->n[k];
   a.col_fibres = MODE0 ? 0 : c->stride[k] / c->n[0];
   a.fg = fibre_geom((int64_t)c->n[0] * TtElem<DT>::bytes, VB, M);
-  int sms = 152;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+  const int sms = tt_sm_count();
   // work items (column, c-segment): at most one per CTA slot (two CTAs per SM) when the columns
   // allow it, so that every CTA gets the same amount of work; segments of at most 2048 c groups
   // CTAs per SM: two (the kernel is latency-bound and needs the warps), also when the sweep runs
@@ -863,8 +861,7 @@ int tt_launch_unfold_coo(tt_ctx* c, const int32_t* idx, const float* val, int64_
     if (a.Y[s]) TT_CUDA(c, cudaMemsetAsync(a.Y[s], 0, sizeof(float) * (size_t)c->J * c->n[s], c->stream));
   }
   if (nnz == 0) return TT_OK;
-  int sms = 152;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+  const int sms = tt_sm_count();
   const int64_t blocks = std::min<int64_t>((nnz + 255) / 256, (int64_t)sms * 8);
   k_unfold_coo<<<(int)blocks, 256, 0, c->stream>>>(a);
   TT_LAUNCH(c, "k_unfold_coo");
@@ -872,6 +869,11 @@ int tt_launch_unfold_coo(tt_ctx* c, const int32_t* idx, const float* val, int64_
 }
 
 int tt_launch_unfold(tt_ctx* c, const void* A, const float* scales, int k, float* Y) {
+  if (c->det) {  // the fixed-point sketch of this mode alone
+    float* ys[TT_MAX_D] = {nullptr};
+    ys[k] = Y;
+    return tt_launch_unfold_det(c, A, scales, 1u << k, ys);
+  }
   int rc = tt_ensure_rplan(c, k);  // plan build is not part of the timed kernel
   if (rc) return rc;
   rc = tt_prof_begin(c, k);

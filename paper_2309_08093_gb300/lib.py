@@ -19,19 +19,23 @@ TT_F64, TT_F32, TT_BF16, TT_FP8E4M3 = 0, 1, 2, 3
 DTYPES = {"f64": TT_F64, "f32": TT_F32, "bf16": TT_BF16, "fp8": TT_FP8E4M3}
 TT_OK, TT_EINVAL, TT_ENOMEM, TT_ECUDA, TT_ENOTSPD, TT_ETIMEOUT, TT_ENONFINITE = 0, -1, -2, -3, -4, -5, -6
 TT_FLAG_FIXED_SKETCH = 1
+TT_FLAG_FP64_SOLVE = 2
+TT_FLAG_DETERMINISTIC = 4
+TT_FLAG_TC_GRAM = 8
+TT_FLAG_TF32_GRAM = 16
 
 EXPORTS = ["tt_sketch_init", "tt_sketch_destroy", "tt_last_error", "tt_sketch_tables",
            "tt_sketch_set_tables", "tt_sketch_unfold", "tt_sketch_unfold_coo", "tt_rel_error_coo", "tt_sketch_interface", "tt_prox_update",
            "tt_orthogonalize", "tt_prox_als_sweep", "tt_rel_error", "tt_prox_als_sweep_host",
            "tt_profile_enable", "tt_profile_read", "tt_prox_update_noalloc", "tt_batch_init",
            "tt_batch_destroy", "tt_batch_last_error", "tt_batch_sweep", "tt_batch_rel_error",
-           "tt_prox_als_sweep_sketched", "tt_prox_als_sweep_monitored",
+           "tt_prox_als_sweep_sketched", "tt_prox_als_sweep_monitored", "tt_set_workspace_limit",
            # learned warm start (include/tt_warmstart.h)
            "tt_mlp_init", "tt_mlp_destroy", "tt_mlp_last_error", "tt_mlp_set_weights", "tt_mlp_get_weights",
            "tt_mlp_forward", "tt_mlp_loss_grads", "tt_mlp_train_step", "tt_mlp_gemm_bf16",
            "tt_ws_summary_dim", "tt_ws_core_dim", "tt_ws_summary", "tt_canonicalize", "tt_ws_pack",
            "tt_ws_unpack"]
-_NOT_INT = {"tt_sketch_destroy", "tt_last_error", "tt_batch_destroy", "tt_batch_last_error", "tt_mlp_last_error",
+_NOT_INT = {"tt_sketch_destroy", "tt_set_workspace_limit", "tt_last_error", "tt_batch_destroy", "tt_batch_last_error", "tt_mlp_last_error",
             "tt_ws_summary_dim", "tt_ws_core_dim"}
 
 
@@ -93,6 +97,8 @@ def load(path: str = LIB_PATH):
     L.tt_prox_als_sweep_host.argtypes = [vp, vp, vp, ctypes.POINTER(vp), i, u64, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_double)]
     L.tt_prox_update_noalloc.argtypes = [vp, vp, vp, i, i, i, i, ctypes.c_double, vp]
+    L.tt_set_workspace_limit.argtypes = [u64]
+    L.tt_set_workspace_limit.restype = u64
     L.tt_profile_enable.argtypes = [vp, i]
     L.tt_profile_read.argtypes = [vp, ctypes.POINTER(TtProfile)]
     L.tt_batch_init.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(TtParams), vp]
@@ -362,6 +368,11 @@ def tt_mlp_gemm_bf16(A, B, C, M: int, N: int, K: int, lda: int, ldb: int, ldc: i
     stream = _current_stream() if stream is None else stream
     return L.tt_mlp_gemm_bf16(_ptr(A), int(lda), _ptr(B), int(ldb), int(M), int(N), int(K), _ptr(C), int(ldc),
                               1 if check else 0, stream)
+
+
+def tt_set_workspace_limit(nbytes: int) -> int:
+    """Process-wide cap on a context's device workspaces (0 = none); returns the previous cap."""
+    return int(load().tt_set_workspace_limit(int(nbytes)))
 
 
 def tt_prox_update_noalloc(Y, SH, core, J: int, n: int, r0: int, r1: int, sigma: float, stream=None) -> int:

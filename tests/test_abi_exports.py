@@ -16,7 +16,7 @@ def _declared():
         if fn.endswith(".h"):
             src = open(os.path.join(ROOT, "include", fn)).read()
             src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-            names |= set(re.findall(r"^\s*(?:int64_t|int|void|const char\*)\s+(tt_\w+)\s*\(", src, flags=re.M))
+            names |= set(re.findall(r"^\s*(?:u?int64_t|int|void|const char\*)\s+(tt_\w+)\s*\(", src, flags=re.M))
     return names
 
 
@@ -73,3 +73,27 @@ def test_init_rejects_bad_parameters(libpath):
     assert init((4, 5, 6), (1, 30, 20, 1), 16) == lib.TT_EINVAL     # r_k r_{k+1} > 512
     assert init((4, 500, 6), (1, 4, 100, 1), 16) == lib.TT_EINVAL   # s = 400 with n = 500: no room
     assert init((200, 5, 6), (1, 200, 2, 1), 16) == lib.TT_EINVAL   # a rank above 160
+
+
+def test_workspace_cap_gives_enomem_before_any_device_call(libpath):
+    """A cap below the planned workspaces makes tt_sketch_init return TT_ENOMEM on the host (this
+    runs without a GPU: no CUDA call is made before the check); the cap is process-wide and
+    returns its previous value."""
+    from paper_2309_08093_gb300 import lib
+
+    L = lib.load(libpath)
+    dims, ranks = (40, 30, 20), (1, 4, 4, 1)
+    n = (ctypes.c_int64 * 3)(*dims)
+    r = (ctypes.c_int * 4)(*ranks)
+    p = lib.TtParams(3, n, r, 256, 1e-3, 1, lib.TT_F32, 0)
+    ctx = ctypes.c_void_p()
+    assert lib.tt_set_workspace_limit(1 << 16) == 0
+    try:
+        assert L.tt_sketch_init(ctypes.byref(ctx), ctypes.byref(p), None) == lib.TT_ENOMEM
+        assert not ctx.value
+        # bad parameters are still reported as such, whatever the cap
+        r_bad = (ctypes.c_int * 4)(2, 4, 4, 1)
+        p_bad = lib.TtParams(3, n, r_bad, 256, 1e-3, 1, lib.TT_F32, 0)
+        assert L.tt_sketch_init(ctypes.byref(ctx), ctypes.byref(p_bad), None) == lib.TT_EINVAL
+    finally:
+        assert lib.tt_set_workspace_limit(0) == 1 << 16
