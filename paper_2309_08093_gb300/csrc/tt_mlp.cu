@@ -1,11 +1,13 @@
 // Learned warm start: the MLP's kernels and its C ABI (include/tt_warmstart.h).
 //
-//   k_gemm_tn<EPI>  : C = A B^T, A (M x K) and B (N x K) row-major BF16, one 128 x 256 tile per
-//                     CTA. Operands are staged by cp.async into shared memory in the canonical
-//                     no-swizzle K-major layout (8 x 16-byte core matrices); one thread issues
-//                     tcgen05.mma (kind::f16, BF16 x BF16 -> FP32) into a 256-column tensor-memory
-//                     accumulator; completion is signalled by tcgen05.commit on an mbarrier per
-//                     stage. Four stages: tile kt+2 loads while the MMAs of kt-1 and kt run. The
+//   k_gemm_tn<EPI>  : C = A B^T, A (M x K) and B (N x K) row-major BF16, one 128 x BN tile per
+//                     CTA (BN = 128 or 256). Operands arrive by TMA (2-D tiled cp.async.bulk.tensor
+//                     loads, 128-byte swizzle, rows past the end zero-filled) in the swizzled K-major
+//                     layout; one thread is producer and MMA issuer: tcgen05.mma (kind::f16,
+//                     BF16 x BF16 -> FP32) into a BN-column tensor-memory accumulator, a "full"
+//                     mbarrier per stage counts the TMA bytes and the MMAs of a stage commit to its
+//                     "empty" mbarrier. Four stages: a stage is refilled as soon as its MMAs
+//                     released it. The
 //                     epilogue reads the accumulator with tcgen05.ld (warp w owns lanes 32w..32w+31)
 //                     and applies one of three fused epilogues:
 //                       EPI_F32   : C (+ bias) -> FP32
@@ -33,6 +35,7 @@
 #include <string>
 
 #include "../../include/tt_warmstart.h"
+#include "tt_tc.cuh"
 
 namespace {
 
@@ -44,7 +47,6 @@ template <int BN>
 constexpr int b_stage() { return BN * GK * 2; }
 template <int BN>
 constexpr int gemm_smem() { return GSTAGES * (A_STAGE + b_stage<BN>()) + 1024 + 128; }
-constexpr unsigned long long WAIT_NS = 2000000000ull;  // an mbarrier wait gives up after 2 s
 
 enum { EPI_F32 = 0, EPI_GELU = 1, EPI_DGELU = 2 };
 
@@ -68,118 +70,12 @@ struct GemmArgs {
   int64_t slab;       // split-K: element offset between the FP32 outputs of consecutive splits
 };
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
+using namespace ttc;
 
-// tcgen05 shared-memory matrix descriptor, no swizzle: start address, leading-dimension byte
-// offset (between core matrices adjacent in K), stride byte offset (between 8-row groups), the
-// fixed 0b001 field at bits 46-48, base offset 0, swizzle mode 0.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-  d |= (uint64_t)1 << 46;
-  return d;
-}
-
-// The same for the 128-byte swizzled K-major layout that TMA writes with SWIZZLE_128B: rows of
-// 128 bytes (64 BF16 of K) whose 16-byte chunks are permuted by row mod 8, 8-row atoms 1024 bytes
-// apart (stride byte offset), leading-dimension offset unused (encoded as 16 bytes), swizzle mode 2
-// at bits 61-63. The 16-element K steps of one atom advance the start address by 32 bytes; every
-// atom starts on a 1024-byte boundary (base offset 0).
-__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
-  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)1 << 16;
-  d |= (uint64_t)(1024 >> 4) << 32;
-  d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;
-  return d;
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t addr, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(addr), "r"(bytes) : "memory");
-}
-
-// 2-D tiled TMA load of the box at (x = K column, y = row) into shared memory; completion is
-// counted on the mbarrier (complete_tx). x is a multiple of 64 BF16 (128 bytes).
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* tm, int x, int y, uint32_t mbar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(mbar)
-      : "memory");
-}
-
-// Instruction descriptor of tcgen05.mma kind::f16: D FP32 (bits 4-5 = 1), A BF16 (bits 7-9 = 1),
-// B BF16 (bits 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at 24-28.
+// Instruction descriptor of the BF16 MMAs (kind::f16): 128 x BN tiles.
 template <int BN>
 constexpr uint32_t idesc() {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(GM >> 4) << 24);
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t addr, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(addr), "r"(count) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint32_t addr, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}\n"
-      : "=r"(ok)
-      : "r"(addr), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-// Bounded wait for the completion of phase `parity`; false if it gave up.
-__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity) {
-  if (mbar_try(addr, parity)) return true;
-  const unsigned long long t0 = global_ns();
-  while (global_ns() - t0 < WAIT_NS)
-    if (mbar_try(addr, parity)) return true;
-  return false;
-}
-
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-}
-
-__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                       uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-__device__ __forceinline__ void tc_commit(uint32_t mbar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar)
-               : "memory");
-}
-
-// 32 consecutive accumulator columns of this thread's lane.
-__device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
-        "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
-        "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr)
-      : "memory");
-  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+  return tc_idesc(1u, GM, BN);
 }
 
 __device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
@@ -246,7 +142,7 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tn(const __grid_constant__ CUte
       const uint32_t sa = a0 + s * A_STAGE, sb = b0 + s * B_STAGE;
 #pragma unroll
       for (int kk = 0; kk < GK / 16; ++kk)
-        tc_mma(tmem, smem_desc_sw128(sa + kk * 32), smem_desc_sw128(sb + kk * 32), idesc<BN>(),
+        tc_mma_f16(tmem, smem_desc_sw128(sa + kk * 32), smem_desc_sw128(sb + kk * 32), idesc<BN>(),
                (kt > 0 || kk > 0) ? 1u : 0u);
       tc_commit(smem_u32(&empty[s]));
       const int t = kt - 1 + GSTAGES;  // refill the stage of tile kt-1
@@ -553,19 +449,6 @@ int mfail(tt_mlp* m, int code, const char* fmt, ...) {
     int _r = (x);               \
     if (_r != TT_OK) return _r; \
   } while (0)
-
-// cuTensorMapEncodeTiled, fetched once through the runtime (the library does not link libcuda)
-PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-  }
-  return fn;
-}
 
 // Tensor map of a row-major BF16 matrix (rows x K, row stride ld elements): boxes of 64 K columns
 // (128 bytes, the swizzle span) by box_rows rows, 128-byte swizzle, rows past the end read as 0.
