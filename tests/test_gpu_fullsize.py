@@ -14,11 +14,11 @@ tensor the benchmark streams, in the launch configuration it times.
   against the oracle's column by definition (1e-5 relative per column).
 
 Order-5 40^5 workload (J = 8192, TT ranks (1,8,8,8,8,1) with 0.8^k-decaying cores, 1e-3 noise),
-stored BF16 and FP8-E4M3 with per-mode-1-slice scales: one sweep through the same call against the
-oracle's sweep on the same quantised tensor (1e-4 per core), the reported error against the
-oracle's error of the same cores (1e-5), and the error against the unquantised FP64 tensor within
-2 delta + 1e-4 of the oracle's FP64 sweep (delta = ||A_q - A|| / ||A||: the best-approximation
-error moves by at most delta when A is replaced by A_q).
+stored BF16 and FP8-E4M3 with per-mode-1-slice scales: five sweeps through the same call from
+random cores, to the noise level, against the oracle's five sweeps on the same quantised tensor
+(reconstruction 1e-4, relative error 1e-4 of itself), and the error against the unquantised FP64
+tensor within 2 delta of the oracle's FP64 run (delta = ||A_q - A|| / ||A||: the
+best-approximation error moves by at most delta when A is replaced by A_q).
 
 Warm-start family member 256 x 256 x 3 x 128 (J = 2048, TT ranks (1,20,3,20,1), cumulative-sum
 cores, 1% noise; the CPU recipe of the family): the sketch summary the network reads (p = 8 bucket
@@ -110,40 +110,57 @@ def test_full_size_data_sketch_columns(problem, storage):
 
 
 W5 = synth.WORKLOADS["order5-40-r8"]
+W5_SWEEPS = 5  # from random cores: 1.0007, 0.654, 0.140, 7.6e-3, 1.03e-3 (FP64 oracle), the noise level
 
 
-@pytest.fixture(scope="module")
-def problem5():
+def test_full_size_order5_at_convergence_per_precision():
+    """The order-5 40^5 workload (J = 8192, ranks (1,8,8,8,8,1), cores with singular values
+    0.8^j, 1e-3 noise) stored BF16 and FP8-E4M3 with slice scales, five sweeps from random cores
+    (the error reaches the noise level). Each GPU run is compared with the oracle's five sweeps
+    on the same decoded tensor (relative error 1e-4 of itself, reconstruction 1e-4), and its
+    error against the unquantised FP64 tensor lies within 2 delta of the FP64 oracle's, delta =
+    ||A_q - A|| / ||A||. The three oracle runs (FP64, BF16, FP8: about 40 s per sweep each) run in
+    spawned worker processes beside the GPU work."""
+    import multiprocessing as mp
+
+    import oracle_runs
+
+    pool = mp.get_context("spawn").Pool(3)
+    jobs = pool.starmap_async(oracle_runs.order5_trajectory, [("f64", W5_SWEEPS), ("bf16", W5_SWEEPS),
+                                                              ("fp8", W5_SWEEPS)])
     p = synth.make_problem(W5, storage="f64")
-    ref64, _ = O.tt_ts(p.tensor, p.init_cores, p.sketch_seed, W5.J, W5.lam, 1)
-    return p, O.rel_error(p.tensor, ref64)
-
-
-@pytest.mark.parametrize("storage", ["bf16", "fp8"])
-def test_full_size_order5_sweep_matches_oracle(problem5, storage):
-    p, e_64 = problem5
     a64 = p.tensor
     assert a64.size == 40 ** 5
-    flat, scales, exact_q = synth.quantize(a64, storage)
-    delta = rel(exact_q, a64)
-    ctx = lib.Context(W5.dims, p.ranks, W5.J, W5.lam, p.sketch_seed, storage)
-    A = lib.device_tensor(flat, storage)
-    sd = torch.tensor(scales, device="cuda") if scales is not None else None
-    dc = lib.device_cores(p.init_cores)
-    errs, _ = ctx.tt_prox_als_sweep_monitored(A, dc, 1, 0, scales=sd)
-    got = lib.host_cores(dc, p.ranks, W5.dims)
-    ctx.close()
-    del A
-    ref_q, _ = O.tt_ts(exact_q, p.init_cores, p.sketch_seed, W5.J, W5.lam, 1)
-    for k in range(W5.d):
-        assert rel(got[k], ref_q[k]) <= 1e-4, (storage, k, rel(got[k], ref_q[k]))
-    got64 = [np.asarray(g, np.float32).astype(np.float64) for g in got]
-    e_q = O.rel_error(exact_q, got64)
-    assert abs(errs[0] - e_q) <= 1e-5 * e_q, (errs[0], e_q)
-    e_gpu = O.rel_error(a64, got64)
-    print(f"\n{storage}: delta={delta:.3e} rel error vs FP64 tensor after one sweep: gpu={e_gpu:.6e} "
-          f"oracle(fp64)={e_64:.6e}")
-    assert abs(e_gpu - e_64) <= 2 * delta + 1e-4
+    gpu = {}
+    for storage in ("bf16", "fp8"):
+        flat, scales, exact_q = synth.quantize(a64, storage)
+        delta = rel(exact_q, a64)
+        del exact_q
+        ctx = lib.Context(W5.dims, p.ranks, W5.J, W5.lam, p.sketch_seed, storage)
+        A = lib.device_tensor(flat, storage)
+        sd = torch.tensor(scales, device="cuda") if scales is not None else None
+        dc = lib.device_cores(p.init_cores)
+        errs, _ = ctx.tt_prox_als_sweep_monitored(A, dc, W5_SWEEPS, 0, scales=sd)
+        got = lib.host_cores(dc, p.ranks, W5.dims)
+        ctx.close()
+        del A
+        got64 = [np.asarray(g, np.float32).astype(np.float64) for g in got]
+        gpu[storage] = (got64, errs, delta, O.rel_error(a64, got64))
+    try:
+        (_, e64, _), (ref_b, eb_q, _), (ref_f, ef_q, _) = jobs.get(timeout=1800)
+    finally:
+        pool.close()
+        pool.join()
+    for storage, ref, e_ref in (("bf16", ref_b, eb_q), ("fp8", ref_f, ef_q)):
+        got64, errs, delta, e_gpu64 = gpu[storage]
+        dev = rel(O.tt_full(got64), O.tt_full(ref))
+        print(f"\n{storage}: delta={delta:.3e}; after {W5_SWEEPS} sweeps: error on the decoded tensor gpu="
+              f"{errs[-1]:.6e} oracle={e_ref:.6e}; against the FP64 tensor gpu={e_gpu64:.6e}, FP64 oracle "
+              f"{e64:.6e}; reconstruction deviation from the oracle {dev:.2e}")
+        assert abs(errs[-1] - e_ref) <= 1e-4 * e_ref, (storage, errs[-1], e_ref)
+        assert dev <= 1e-4, (storage, dev)
+        assert abs(e_gpu64 - e64) <= 2 * delta, (storage, e_gpu64, e64, delta)
+        assert e_gpu64 < 0.1  # a converged point, not the first sweep's error of about 1
 
 
 WW = synth.WORKLOADS["order4-256x256x3x128-r20"]

@@ -9,7 +9,7 @@ slice; the GPU sketches in FP32. Two kinds of checks:
         slice scale mapping the slice maximum to 448); the bounds below are 2u;
       - the best TT approximation error moves by at most delta = ||A_q - A|| / ||A|| when A is
         replaced by A_q (triangle inequality); for the ALS iterates the bound used is 2 delta.
-Observed values are printed (pytest -s) and recorded in the design notes."""
+Observed values are printed (pytest -s)."""
 import numpy as np
 import pytest
 
