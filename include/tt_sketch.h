@@ -265,13 +265,37 @@ int tt_rel_error_coo(tt_ctx* ctx, const int32_t* idx_dev, const float* val_dev, 
  * The same sweeps on HOST buffers: A_host (the dense tensor in the context's storage type,
  * layout as above), scales_host (FP8 only, else NULL) and the d FP32 cores (host array of host
  * pointers, updated in place). Each call copies the inputs to library-owned device buffers
- * (allocated on first use), runs tt_prox_als_sweep, then (if rel_error_out is not NULL) the
- * relative error of tt_rel_error, and copies the cores back; it synchronises. Host memory should
- * be page-locked for full copy bandwidth. rel_change_out as above.
+ * (allocated on first use: two for the tensor, counted against tt_set_workspace_limit), runs the
+ * sweeps of tt_prox_als_sweep, then (if rel_error_out is not NULL) the relative error of
+ * tt_rel_error, and copies the cores back; it synchronises. It is tt_prox_als_sweep_host_async
+ * followed by tt_host_sync. Host memory should be page-locked for full copy bandwidth.
+ * rel_change_out as above (at most 8192 / d sweeps per call when it is given).
  */
 int tt_prox_als_sweep_host(tt_ctx* ctx, const void* A_host, const float* scales_host,
                            float* const* cores_host, int nsweeps, uint64_t first_sweep,
                            double* rel_change_out, double* rel_error_out);
+
+/*
+ * The same call without waiting, for a stream of host-buffer problems: it enqueues the copy of
+ * A_host (and scales_host) into one of two device buffers on a library-owned copy stream, and, on
+ * the context's stream after that copy, the copy of the cores, the sweeps, the relative error and
+ * the copies back of the cores and of the result sums, then returns. The next call's tensor copy
+ * runs beside this call's sweeps, so a sequence of calls is bound by the host link rather than by
+ * copy plus sweeps. Calls run in order; consecutive calls on the same host core arrays see each
+ * other's updates. Every host buffer of a call must stay valid, and its outputs (the cores,
+ * rel_change_out, rel_error_out) unread, until tt_host_sync returns; at most four calls are in
+ * flight (a fifth call first waits for the oldest). Page-locked host arrays are read and written
+ * by a kernel, so that only the tensor copy uses a copy engine (pageable ones by copies). Returns
+ * TT_OK or an argument/launch error; the status of the sweeps (TT_ENOTSPD, TT_ENONFINITE, ...) is
+ * returned by tt_host_sync.
+ */
+int tt_prox_als_sweep_host_async(tt_ctx* ctx, const void* A_host, const float* scales_host,
+                                 float* const* cores_host, int nsweeps, uint64_t first_sweep,
+                                 double* rel_change_out, double* rel_error_out);
+
+/* Wait for every call enqueued by tt_prox_als_sweep_host_async, write their rel_change_out and
+ * rel_error_out, and return the first failure among them (TT_OK if none). */
+int tt_host_sync(tt_ctx* ctx);
 
 /*
  * Allocation-free proximal update. The paper has no counterpart: this is a service for callers

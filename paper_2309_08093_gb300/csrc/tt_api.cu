@@ -6,7 +6,7 @@
 
 #include "tt_internal.cuh"
 
-static int check_data(tt_ctx* c, const void* A, const float* scales) {
+int tt_check_data(tt_ctx* c, const void* A, const float* scales) {
   if (!A) return tt_fail(c, TT_EINVAL, "null tensor pointer");
   if (c->dtype == TT_FP8E4M3 && !scales) return tt_fail(c, TT_EINVAL, "FP8 storage needs n[0] slice scales");
   if (c->dtype != TT_FP8E4M3 && scales) return tt_fail(c, TT_EINVAL, "slice scales are only used with FP8 storage");
@@ -38,7 +38,7 @@ int tt_reset_status(tt_ctx* c) {
 extern "C" int tt_sketch_unfold(tt_ctx* c, const void* A, const float* scales, int k, uint64_t sweep,
                                 float* const* Y) {
   if (!c) return TT_EINVAL;
-  TT_TRY(check_data(c, A, scales));
+  TT_TRY(tt_check_data(c, A, scales));
   if (!Y) return tt_fail(c, TT_EINVAL, "null output array");
   if (k < -1 || k >= c->d) return tt_fail(c, TT_EINVAL, "mode %d outside [-1, %d)", k, c->d);
   for (int kk = 0; kk < c->d; ++kk)
@@ -260,7 +260,7 @@ static int run_sweeps(tt_ctx* c, const void* A, const float* scales, float* cons
 extern "C" int tt_prox_als_sweep(tt_ctx* c, const void* A, const float* scales, float* const* cores,
                                  int nsweeps, uint64_t first_sweep, double* rel_change_out) {
   if (!c) return TT_EINVAL;
-  TT_TRY(check_data(c, A, scales));
+  TT_TRY(tt_check_data(c, A, scales));
   TT_TRY(tt_check_cores(c, cores));
   if (nsweeps < 0) return tt_fail(c, TT_EINVAL, "nsweeps < 0");
   c->err.clear();
@@ -271,7 +271,7 @@ extern "C" int tt_prox_als_sweep_monitored(tt_ctx* c, const void* A, const float
                                            int nsweeps, uint64_t first_sweep, double* rel_change_out,
                                            double* rel_error_out) {
   if (!c) return TT_EINVAL;
-  TT_TRY(check_data(c, A, scales));
+  TT_TRY(tt_check_data(c, A, scales));
   TT_TRY(tt_check_cores(c, cores));
   if (nsweeps < 0) return tt_fail(c, TT_EINVAL, "nsweeps < 0");
   if (!rel_error_out) return tt_fail(c, TT_EINVAL, "null rel_error_out");
@@ -301,7 +301,7 @@ extern "C" int tt_rel_error_coo(tt_ctx* c, const int32_t* idx, const float* val,
 
 extern "C" int tt_rel_error(tt_ctx* c, const void* A, const float* scales, float* const* cores, double* out) {
   if (!c) return TT_EINVAL;
-  TT_TRY(check_data(c, A, scales));
+  TT_TRY(tt_check_data(c, A, scales));
   TT_TRY(tt_check_cores(c, cores));
   if (!out) return tt_fail(c, TT_EINVAL, "null output");
   c->err.clear();
@@ -323,40 +323,6 @@ int tt_elem_bytes(int dtype) {
     case TT_BF16: return 2;
     default: return 1;
   }
-}
-
-extern "C" int tt_prox_als_sweep_host(tt_ctx* c, const void* A_host, const float* scales_host,
-                                      float* const* cores_host, int nsweeps, uint64_t first_sweep,
-                                      double* rel_change_out, double* rel_error_out) {
-  if (!c) return TT_EINVAL;
-  TT_TRY(check_data(c, A_host, scales_host));
-  TT_TRY(tt_check_cores(c, cores_host));
-  c->err.clear();
-  const size_t abytes = (size_t)c->N * tt_elem_bytes(c->dtype);
-  if (!c->d_A_stage) {  // the staging buffers count against the workspace cap
-    uint64_t extra = abytes + sizeof(float) * c->n[0];
-    for (int k = 0; k < c->d; ++k) extra += sizeof(float) * (uint64_t)c->r[k] * c->n[k] * c->r[k + 1];
-    TT_TRY(tt_check_workspace_cap(c, extra));
-    TT_CUDA(c, cudaMalloc(&c->d_A_stage, abytes));
-  }
-  if (scales_host && !c->d_scales_stage) TT_CUDA(c, cudaMalloc((void**)&c->d_scales_stage, sizeof(float) * c->n[0]));
-  size_t csz[TT_MAX_D];
-  for (int k = 0; k < c->d; ++k) {
-    csz[k] = sizeof(float) * (size_t)c->r[k] * c->n[k] * c->r[k + 1];
-    if (!c->d_cores_stage[k]) TT_CUDA(c, cudaMalloc((void**)&c->d_cores_stage[k], csz[k]));
-  }
-  TT_CUDA(c, cudaMemcpyAsync(c->d_A_stage, A_host, abytes, cudaMemcpyHostToDevice, c->stream));
-  if (scales_host)
-    TT_CUDA(c, cudaMemcpyAsync(c->d_scales_stage, scales_host, sizeof(float) * c->n[0], cudaMemcpyHostToDevice, c->stream));
-  for (int k = 0; k < c->d; ++k)
-    TT_CUDA(c, cudaMemcpyAsync(c->d_cores_stage[k], cores_host[k], csz[k], cudaMemcpyHostToDevice, c->stream));
-  const float* sc = scales_host ? c->d_scales_stage : nullptr;
-  int rc = tt_prox_als_sweep(c, c->d_A_stage, sc, c->d_cores_stage, nsweeps, first_sweep, rel_change_out);
-  if (rc == TT_OK && rel_error_out) rc = tt_rel_error(c, c->d_A_stage, sc, c->d_cores_stage, rel_error_out);
-  for (int k = 0; k < c->d; ++k)
-    TT_CUDA(c, cudaMemcpyAsync(cores_host[k], c->d_cores_stage[k], csz[k], cudaMemcpyDeviceToHost, c->stream));
-  TT_CUDA(c, cudaStreamSynchronize(c->stream));
-  return rc;
 }
 
 // ---------------------------------------------------------------------------------------------

@@ -432,8 +432,7 @@ static void free_all(tt_ctx* c) {
                 c->d_det_misc, c->d_y64, c->d_gram_part, c->d_part_err, c->d_part_chg};
   for (void* p : ps)
     if (p) cudaFree(p);
-  if (c->d_A_stage) cudaFree(c->d_A_stage);
-  if (c->d_scales_stage) cudaFree(c->d_scales_stage);
+  tt_host_free(c);
   void* sp[] = {c->spare.h, c->spare.v};
   for (void* p : sp)
     if (p) cudaFree(p);
@@ -445,7 +444,6 @@ static void free_all(tt_ctx* c) {
     if (c->spare.ucount[k]) cudaFree(c->spare.ucount[k]);
   }
   for (int k = 0; k < TT_MAX_D; ++k) {
-    if (c->d_cores_stage[k]) cudaFree(c->d_cores_stage[k]);
     if (c->d_rplan[k]) cudaFree(c->d_rplan[k]);
     if (c->d_ulist[k]) cudaFree(c->d_ulist[k]);
     if (c->d_ustart[k]) cudaFree(c->d_ustart[k]);

@@ -173,11 +173,35 @@ struct tt_ctx {
 
   uint64_t ws_bytes = 0;        // bytes of the workspaces planned at creation (tt_workspace_each)
 
-  // host-buffer entry point staging (allocated on first use)
-  void* d_A_stage = nullptr;
-  float* d_scales_stage = nullptr;
+  // host-buffer entry points (tt_host.cu, allocated on first use): two staging buffers for the
+  // tensor (and its scales), so that the copy of the next call's tensor runs on copy_stream beside
+  // this call's sweeps; ev_copied[b] ends the copy into buffer b, ev_consumed[b] the last kernel
+  // that reads it. The results of calls not yet synchronised land in pinned host slots.
+  void* d_A_stage[2] = {nullptr, nullptr};
+  float* d_scales_stage[2] = {nullptr, nullptr};
   float* d_cores_stage[TT_MAX_D] = {nullptr};
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_copied[2] = {nullptr, nullptr};
+  cudaEvent_t ev_consumed[2] = {nullptr, nullptr};
+  bool consumed_recorded[2] = {false, false};
+  int stage_next = 0;
+  struct HostPending {
+    double* rel_change_out;
+    double* rel_error_out;
+    int nsweeps;
+    int slot;
+  };
+  std::vector<HostPending> pending;   // calls enqueued and not yet synchronised, in order
+  unsigned char* h_slots = nullptr;   // pinned: TT_HOST_SLOTS result slots (status, error, changes)
+  cudaEvent_t ev_slot[4] = {nullptr, nullptr, nullptr, nullptr};  // a slot's results have landed
+  int slot_next = 0;
+  int host_error = 0;                 // first failure of a call finished but not yet reported
 };
+#define TT_HOST_SLOTS 4
+// bytes of one pinned result slot: the status word, the two error sums, 2 d change sums per sweep
+size_t tt_host_slot_bytes(const tt_ctx* c);
+// the host-buffer calls' resources (tt_host.cu)
+void tt_host_free(tt_ctx* c);
 
 // ---------------------------------------------------------------------------------------------
 // hashing (SplitMix64 chain, see tt_sketch.h)
@@ -257,6 +281,8 @@ int tt_launch_rel_error(tt_ctx* c, const void* A, const float* scales, float* co
 int tt_read_status(tt_ctx* c);
 int tt_reset_status(tt_ctx* c);
 int tt_check_cores(tt_ctx* c, float* const* cores);
+// A non-null; slice scales given exactly for FP8 storage
+int tt_check_data(tt_ctx* c, const void* A, const float* scales);
 
 #define TT_TRY(x)            \
   do {                       \

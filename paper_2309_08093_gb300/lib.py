@@ -30,6 +30,7 @@ EXPORTS = ["tt_sketch_init", "tt_sketch_destroy", "tt_last_error", "tt_sketch_ta
            "tt_profile_enable", "tt_profile_read", "tt_prox_update_noalloc", "tt_batch_init",
            "tt_batch_destroy", "tt_batch_last_error", "tt_batch_sweep", "tt_batch_rel_error",
            "tt_prox_als_sweep_sketched", "tt_prox_als_sweep_monitored", "tt_set_workspace_limit",
+           "tt_prox_als_sweep_host_async", "tt_host_sync",
            # learned warm start (include/tt_warmstart.h)
            "tt_mlp_init", "tt_mlp_destroy", "tt_mlp_last_error", "tt_mlp_set_weights", "tt_mlp_get_weights",
            "tt_mlp_forward", "tt_mlp_loss_grads", "tt_mlp_train_step", "tt_mlp_gemm_bf16",
@@ -97,6 +98,9 @@ def load(path: str = LIB_PATH):
     L.tt_prox_als_sweep_host.argtypes = [vp, vp, vp, ctypes.POINTER(vp), i, u64, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_double)]
     L.tt_prox_update_noalloc.argtypes = [vp, vp, vp, i, i, i, i, ctypes.c_double, vp]
+    L.tt_prox_als_sweep_host_async.argtypes = [vp, vp, vp, ctypes.POINTER(vp), i, u64, ctypes.POINTER(ctypes.c_double),
+                                               ctypes.POINTER(ctypes.c_double)]
+    L.tt_host_sync.argtypes = [vp]
     L.tt_set_workspace_limit.argtypes = [u64]
     L.tt_set_workspace_limit.restype = u64
     L.tt_profile_enable.argtypes = [vp, i]
@@ -257,6 +261,23 @@ class Context:
                                                     _ptr_array(cores_host), int(nsweeps), int(first_sweep), out,
                                                     ctypes.byref(err)))
         return (list(out)[:nsweeps] if rel_change else None), err.value
+
+    def tt_prox_als_sweep_host_async(self, A_host: np.ndarray, cores_host: Sequence[np.ndarray], nsweeps: int,
+                                     first_sweep: int = 0, scales_host: Optional[np.ndarray] = None,
+                                     rel_change: bool = False, rel_error: bool = True):
+        """Enqueue a host-buffer call; returns the output arrays (filled by tt_host_sync). The host
+        arrays must stay alive and unread until then."""
+        chg = np.zeros(max(1, nsweeps)) if rel_change else None
+        err = np.zeros(1) if rel_error else None
+        keep = _ptr_array(cores_host)
+        self._check(self.lib.tt_prox_als_sweep_host_async(
+            self.ctx, _ptr(A_host), _ptr(scales_host), keep, int(nsweeps), int(first_sweep),
+            chg.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if chg is not None else None,
+            err.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if err is not None else None))
+        return chg, err
+
+    def tt_host_sync(self):
+        self._check(self.lib.tt_host_sync(self.ctx))
 
     def tt_profile_enable(self, on: bool = True):
         self._check(self.lib.tt_profile_enable(self.ctx, 1 if on else 0))
