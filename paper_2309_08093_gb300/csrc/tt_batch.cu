@@ -3,8 +3,9 @@
 // i runs on stream i mod S of a stream pool, forked from and joined to the caller's stream -- and
 // every later sweep is a single cudaGraphLaunch. The sweep index lives in a device counter that the
 // graph increments, so each replay draws the next sketch (Alg. 1 redraws S_k per outer iteration).
-// Before the first capture an autotuner times a few work-item granularities and CTA-per-SM limits
-// of the unfold kernel on each tensor's own data and keeps the fastest per mode.
+// Before the first capture an autotuner times, per mode and on each tensor's own data, the default
+// data-sketch launch and the one-column kernel at a few work-item granularities and CTA-per-SM
+// limits, and keeps the fastest.
 #include <stdio.h>
 
 #include <algorithm>
@@ -116,7 +117,9 @@ static int time_unfold(tt_ctx* c, const void* A, const float* sc, int k, float* 
 }
 
 static int autotune(tt_batch* b, const void* const* A, const float* const* S) {
-  static const int seg_mult[] = {1, 2, 4};
+  // 0 = the default launch (modes >= 1: the G-column kernel where it fits); 1, 2, 4 = the
+  // one-column kernel with that multiple of the work items
+  static const int seg_mult[] = {0, 1, 2, 4};
   static const int cps[] = {1, 2};
   for (int i = 0; i < b->count; ++i) {
     tt_ctx* c = b->ctx[i];

@@ -600,8 +600,12 @@ __global__ void __launch_bounds__(256, 2) k_unfold_cols(GArgs a) {
   }
 }
 
-// Modes >= 1 with G columns per item: 16-byte vectors (VB), S entries in flight, MV vectors per
-// lane; returns false (nothing launched) when the shape does not suit it.
+// Modes >= 1 with G columns per item: VB-byte vectors, S entries in flight, MV vectors per lane;
+// returns false (nothing launched) when the shape does not suit it. 16-byte vectors take the
+// smallest MV that covers an entry (up to 4); fibres whose length is not a multiple of 16 bytes
+// (8- or 4-byte vectors) take MV = 16 / EPV, every lane holding up to 16 elements (so the plan is
+// walked once per item and 128 bytes per lane stay in flight, rather than one 4-byte vector per
+// lane and a walk of the plan per 32 of them).
 template <int DT, int VB, int S>
 static int launch_cols_s(tt_ctx* c, const void* A, const float* scales, int k, float* Y, bool* done, size_t smax) {
   *done = false;
@@ -611,7 +615,8 @@ static int launch_cols_s(tt_ctx* c, const void* A, const float* scales, int k, f
   const int vpf = (int)(fiber_bytes / VB);
   const int mv = (G * vpf + 31) / 32;
   constexpr int EPV = TtVec<DT, VB>::EPV;
-  if (mv > 4 || mv * EPV > 16 || (c->J & 3) != 0) return TT_OK;  // at most 16 elements per lane
+  constexpr int MV_MAX = VB == 16 ? 4 : 16 / EPV;
+  if (mv > MV_MAX || mv * EPV > 16 || (c->J & 3) != 0) return TT_OK;  // at most 16 elements per lane
   GArgs a;
   a.A = (const char*)A;
   a.scales = scales;
@@ -638,18 +643,21 @@ static int launch_cols_s(tt_ctx* c, const void* A, const float* scales, int k, f
   nseg = std::max(nseg, (c->J + 2047) / 2048);
   a.nseg = nseg;
   a.segmax = (c->J + nseg - 1) / nseg + 1;
-  const size_t smem = gather_ring_bytes(true, THREADS / 32, S * 4, VB) + sizeof(float) * (size_t)G * c->J +
+  const size_t smem = gather_ring_bytes(true, THREADS / 32, S * MV_MAX, VB) + sizeof(float) * (size_t)G * c->J +
                       sizeof(int) * (2 * (size_t)a.segmax + 1);
   if (smem > smax) return TT_OK;
   *done = true;
   TT_CUDA(c, cudaMemsetAsync(Y, 0, sizeof(float) * c->J * c->n[k], c->stream));
-  void (*kern)(GArgs) = k_unfold_cols<DT, VB, S, 1, G>;
-  if constexpr (2 * EPV <= 16)
-    if (mv == 2) kern = k_unfold_cols<DT, VB, S, 2, G>;
-  if constexpr (3 * EPV <= 16)
-    if (mv == 3) kern = k_unfold_cols<DT, VB, S, 3, G>;
-  if constexpr (4 * EPV <= 16)
-    if (mv == 4) kern = k_unfold_cols<DT, VB, S, 4, G>;
+  void (*kern)(GArgs) = k_unfold_cols<DT, VB, S, MV_MAX, G>;
+  if constexpr (VB == 16) {
+    kern = k_unfold_cols<DT, VB, S, 1, G>;
+    if constexpr (2 * EPV <= 16)
+      if (mv == 2) kern = k_unfold_cols<DT, VB, S, 2, G>;
+    if constexpr (3 * EPV <= 16)
+      if (mv == 3) kern = k_unfold_cols<DT, VB, S, 3, G>;
+    if constexpr (4 * EPV <= 16)
+      if (mv == 4) kern = k_unfold_cols<DT, VB, S, 4, G>;
+  }
   TT_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int items = ncolg * a.nseg;
   kern<<<std::max(1, items), THREADS, smem, c->stream>>>(a);
@@ -732,7 +740,7 @@ static int launch_gather_vbm(tt_ctx* c, const void* A, const float* scales, int 
 
 template <int DT, int VB, bool MODE0>
 static int launch_gather_vb(tt_ctx* c, const void* A, const float* scales, int k, float* Y) {
-  if constexpr (!MODE0 && (VB == 8 || VB == 16)) {
+  if constexpr (!MODE0 && (VB == 4 || VB == 8 || VB == 16) && VB >= TtElem<DT>::bytes) {
     if (!c->tune_seg_mult[k]) {  // the autotuner times the one-column kernel's granularities
       bool done = false;
       const int rc = launch_cols<DT, VB>(c, A, scales, k, Y, &done);
@@ -741,7 +749,7 @@ static int launch_gather_vb(tt_ctx* c, const void* A, const float* scales, int k
   }
   // Several fibres per warp pay off in mode 0, whose runs are long (one flush per row); in modes
   // >= 1 a run is a few fibres and the fibre slots of a warp would flush divergently.
-  if constexpr ((VB == 16 || VB == 8) && MODE0) {
+  if constexpr ((VB == 16 || VB == 8 || VB == 4) && VB >= TtElem<DT>::bytes && MODE0) {
     constexpr int EPV = TtVec<DT, VB>::EPV;  // pick_m keeps M * EPV <= 16: only those are compiled
     const int m = pick_m((int)(c->n[0] * TtElem<DT>::bytes / VB), EPV);
     if constexpr (4 * EPV <= 16) {
@@ -758,6 +766,15 @@ static int launch_gather_vb(tt_ctx* c, const void* A, const float* scales, int k
       if (m == 2) return launch_gather_vbm<DT, VB, 2, MODE0>(c, A, scales, k, Y);
     return launch_gather_vbm<DT, VB, 1, MODE0>(c, A, scales, k, Y);
   } else {
+    if constexpr (!MODE0 && VB >= 4 && VB >= TtElem<DT>::bytes) {
+      // one fibre per warp covered by one pass of the plan: M vectors per lane (M * EPV <= 16)
+      constexpr int EPV = TtVec<DT, VB>::EPV;
+      const int vpf = (int)(c->n[0] * TtElem<DT>::bytes / VB);
+      if constexpr (4 * EPV <= 16)
+        if (vpf > 64 && vpf <= 128) return launch_gather_vbm<DT, VB, 4, MODE0>(c, A, scales, k, Y);
+      if constexpr (2 * EPV <= 16)
+        if (vpf > 32 && vpf <= 64) return launch_gather_vbm<DT, VB, 2, MODE0>(c, A, scales, k, Y);
+    }
     return launch_gather_vbm<DT, VB, 1, MODE0>(c, A, scales, k, Y);
   }
 }

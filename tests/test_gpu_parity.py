@@ -104,7 +104,10 @@ CASES_A = [((7, 5, 9), 64, "f32"), ((3, 5, 7, 2), 16, "f32"), ((50, 50, 50), 102
            ((300, 4, 5), 16384, "bf16"), ((12, 10, 8, 6, 4), 8192, "bf16"), ((41, 23, 6), 256, "f32"),
            # sketch sizes that are not powers of two (the paper's m of Sec. 5)
            ((7, 5, 9), 45, "f32"), ((20, 18, 16), 150, "bf16"), ((16, 12, 10, 8), 1000, "f32"),
-           ((33, 17, 9, 5), 200, "fp8"), ((12, 10, 8), 2000, "f64"), ((10,) * 6, 45, "f32")]
+           ((33, 17, 9, 5), 200, "fp8"), ((12, 10, 8), 2000, "f64"), ((10,) * 6, 45, "f32"),
+           # fibres whose length is not a multiple of 16 bytes (8- and 4-byte vectors, up to 16 per lane)
+           ((62, 9, 7), 512, "f32"), ((30, 7, 11), 256, "bf16"), ((123, 8, 6), 1024, "f32"),
+           ((126, 5, 4, 3), 2048, "f32"), ((67, 12, 5), 512, "fp8")]
 
 
 def _data(dims, storage, seed):
