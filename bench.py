@@ -44,7 +44,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-patterns", action="store_true", help="skip the precision/batched/warm-start patterns")
-    ap.add_argument("--only-pattern", default=None, choices=["precision", "batched", "warmstart", "gemm", "sparse"],
+    ap.add_argument("--only-pattern", default=None,
+                    choices=["precision", "batched", "warmstart", "gemm", "sparse", "order3", "order5",
+                             "deterministic", "gram"],
                     help="run one pattern and print its JSON")
     ap.add_argument("--ws-train", type=int, default=10240, help="warm-start training solves")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
@@ -144,7 +146,15 @@ def cpu_sample_main(args):
         t = time.perf_counter()
         O.tt_ts_sweep(p.tensor, p.init_cores, p.sketch_seed, 0, w.J, w.lam)
         dt = time.perf_counter() - t
-        print(json.dumps({"sweep_s": dt}))
+        hs, vs = O.draw_sketch(p.sketch_seed, 0, w.dims, w.J)  # the same columns, one thread
+        t = time.perf_counter()
+        for k in range(w.d):
+            for i in range(w.dims[k]):
+                O.sketch_unfolding_column(p.tensor, hs, vs, w.J, k, i)
+        sk = time.perf_counter() - t
+        del p
+        all_s, cores, detail = cpu_all_cores(args, dt, sk)
+        print(json.dumps({"sweep_s": dt, "sweep_all_cores_s": all_s, "cores": cores, **detail}))
         return
     # reference arm: each step sketches q columns of Y_k by definition, cycling over modes/columns
     hs, vs = O.draw_sketch(p.sketch_seed, 0, w.dims, w.J)
@@ -168,6 +178,54 @@ def cpu_sample_main(args):
     per_col = sum(timed) / (len(timed) * args.cpu_columns)
     print(json.dumps({"per_column_s": per_col, "columns_per_sweep": len(cols), "steps": len(timed),
                       "step_s": sum(timed) / len(timed), "q": args.cpu_columns}))
+
+
+_W = {}
+
+
+def _cols_worker(args):
+    """Spawned worker (one numpy thread): the oracle's data-sketch columns (k, i_k) of one draw by
+    their definition; the workload is built once per process. Returns the compute seconds."""
+    workload, storage, cols, hold = args
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    import tt_oracle as O
+    from paper_2309_08093_gb300 import synth
+
+    if _W.get("name") != (workload, storage):
+        w = synth.WORKLOADS[workload]
+        p = synth.make_problem(w, storage=storage)
+        _W.update(name=(workload, storage), p=p, w=w, hv=O.draw_sketch(p.sketch_seed, 0, w.dims, w.J))
+    p, w = _W["p"], _W["w"]
+    hs, vs = _W["hv"]
+    t = time.perf_counter()
+    for k, i in cols:
+        O.sketch_unfolding_column(p.tensor, hs, vs, w.J, k, i)
+    dt = time.perf_counter() - t
+    time.sleep(hold)  # warm-up round: keeps this worker busy so that every worker gets one task
+    return dt
+
+
+def cpu_all_cores(args, sweep_1t_s, sketch_1t_s):
+    """The sweep's data-sketch columns spread over one single-threaded process per available core
+    (os.sched_getaffinity); the rest of the sweep (interface sketches, solves, QR: the one-thread
+    sweep minus its one-thread data-sketch columns) stays serial. Returns (sweep seconds, cores,
+    detail)."""
+    import multiprocessing as mp
+
+    from paper_2309_08093_gb300 import synth
+
+    w = synth.WORKLOADS[args.workload]
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    cols = [(k, i) for k in range(w.d) for i in range(w.dims[k])]
+    tasks = [cols[j::cores * 4] for j in range(cores * 4)]
+    with mp.get_context("spawn").Pool(cores) as pool:
+        pool.map(_cols_worker, [(args.workload, args.storage, [cols[0]], 2.0)] * cores, chunksize=1)
+        t = time.perf_counter()
+        busy = pool.map(_cols_worker, [(args.workload, args.storage, tk, 0.0) for tk in tasks], chunksize=1)
+        wall = time.perf_counter() - t
+    serial_rest = max(0.0, sweep_1t_s - sketch_1t_s)
+    return wall + serial_rest, cores, {"sketch_wall_s": wall, "sketch_busy_s": sum(busy), "serial_rest_s": serial_rest,
+                                       "sketch_one_thread_s": sketch_1t_s}
 
 
 def run_cpu_child(extra):
@@ -328,6 +386,155 @@ def batched_pattern(dev, nsweeps=10, count=256):
             "note": "noise 1e-3 (the floor); sweeps timed with CUDA events around one tt_batch_sweep call "
                     "(graph replays); unfold GB/s = tensor bytes x order / sweep time, everything else in "
                     "the sweep included"}
+
+
+# ---------------------------------------------------------------------------------------------
+# Gram of the proximal update: CUDA-core FP32 (the default), tensor cores TF32 x 3 (FP32-accurate)
+# and TF32 x 1 (mixed precision), each timed over whole sweeps of the benchmark workload
+
+def gram_pattern(w, p, dev, nsweeps=20):
+    import torch
+    from paper_2309_08093_gb300 import lib
+
+    stream = torch.cuda.current_stream()
+    A = lib.device_tensor(p.storage, "f32", device=dev)
+    out = {}
+    for name, flags in (("cuda_core_fp32", 0), ("tcgen05_tf32x3", lib.TT_FLAG_TC_GRAM),
+                        ("tcgen05_tf32x1", lib.TT_FLAG_TF32_GRAM)):
+        ctx = lib.Context(w.dims, p.ranks, w.J, w.lam, p.sketch_seed, "f32", flags=flags)
+        cores = lib.device_cores(p.init_cores, device=dev)
+        ctx.tt_prox_als_sweep(A, cores, 3, 0, rel_change=False)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.tt_prox_als_sweep(A, cores, nsweeps, 3, rel_change=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / nsweeps
+        out[name] = {"ms_per_sweep": ms, "sweeps_per_s": 1e3 / ms, "rel_error": ctx.tt_rel_error(A, cores)}
+        ctx.close()
+    return {"sweeps": nsweeps, "forms": out,
+            "note": "sweeps only (no relative error inside the timed region), CUDA events, after 3 warm-up "
+                    "sweeps from the workload's initial cores"}
+
+
+# ---------------------------------------------------------------------------------------------
+# deterministic mode: the same sweeps with fixed summation orders (TT_FLAG_DETERMINISTIC), timed,
+# repeated from the same initial cores, and checked for identical bits
+
+def deterministic_pattern(w, p, dev, nsweeps=5):
+    import torch
+    from paper_2309_08093_gb300 import lib
+
+    stream = torch.cuda.current_stream()
+    A = lib.device_tensor(p.storage, "f32", device=dev)
+    runs = []
+    for _ in range(2):
+        ctx = lib.Context(w.dims, p.ranks, w.J, w.lam, p.sketch_seed, "f32", flags=lib.TT_FLAG_DETERMINISTIC)
+        warm = lib.device_cores(p.init_cores, device=dev)
+        ctx.tt_prox_als_sweep(A, warm, 1, 500, rel_change=False)
+        cores = lib.device_cores(p.init_cores, device=dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.tt_prox_als_sweep(A, cores, nsweeps, 0, rel_change=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        err = ctx.tt_rel_error(A, cores)
+        runs.append((e0.elapsed_time(e1) / nsweeps, cores, err))
+        ctx.close()
+    same = all(torch.equal(a, b) for a, b in zip(runs[0][1], runs[1][1])) and runs[0][2] == runs[1][2]
+    ms = min(runs[0][0], runs[1][0])
+    return {"sweeps_per_s": 1e3 / ms, "ms_per_sweep": ms, "sweeps": nsweeps, "rel_error": runs[0][2],
+            "bitwise_identical_runs": same,
+            "note": "TT_FLAG_DETERMINISTIC: fixed-point data sketch (one read of A for all modes, int64 "
+                    "atomics), Gram K-chunks and partial sums in fixed order; sweeps only (no relative error "
+                    "inside the timed region), CUDA events; two runs from the same initial cores compared"}
+
+
+# ---------------------------------------------------------------------------------------------
+# the other single-tensor workloads: the order-3 50^3 FP64 workload and the order-5 40^5 workload
+# stored FP32 / BF16 / FP8-E4M3 (slice scales), each timed per sweep with its error against the
+# FP64 tensor and its data-sketch bandwidth
+
+def workload_pattern(name, storages, dev, nsweeps=None):
+    import numpy as np
+    import torch
+    from paper_2309_08093_gb300 import lib, synth
+
+    w = synth.WORKLOADS[name]
+    nsweeps = nsweeps or w.sweeps
+    hbm, peak_kind = peaks()
+    stream = torch.cuda.current_stream()
+    p64 = synth.make_problem(w, storage="f64")
+    A64 = lib.device_tensor(p64.storage, "f64", device=dev)
+    ctx64 = lib.Context(w.dims, p64.ranks, w.J, w.lam, p64.sketch_seed, "f64")  # errors vs the FP64 tensor
+    nrm64 = float(np.linalg.norm(p64.tensor.ravel()))
+    forms = {}
+    for st in storages:
+        flat, scales, exact = synth.quantize(p64.tensor, st)
+        delta = float(np.linalg.norm((exact - p64.tensor).ravel()) / nrm64)
+        del exact
+        ctx = lib.Context(w.dims, p64.ranks, w.J, w.lam, p64.sketch_seed, st)
+        A = lib.device_tensor(flat, st, device=dev)
+        sd = torch.tensor(scales, device=dev) if scales is not None else None
+        warm = lib.device_cores(p64.init_cores, device=dev)
+        ctx.tt_prox_als_sweep(A, warm, 2, 1000, scales=sd, rel_change=False)  # plans, tables, kernels
+        cores = lib.device_cores(p64.init_cores, device=dev)
+        ms, errs, errs64 = [], [], []
+        ctx.tt_profile_enable(True)
+        for t in range(nsweeps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.tt_prox_als_sweep(A, cores, 1, t, scales=sd, rel_change=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            errs.append(ctx.tt_rel_error(A, cores, scales=sd))  # (the counters record data sketches only)
+            errs64.append(ctx64.tt_rel_error(A64, cores))
+        prof = ctx.tt_profile_read()
+        ctx.tt_profile_enable(False)
+        Y = [torch.zeros(w.J * n, device=dev) for n in w.dims]
+        ctx.tt_sketch_unfold(A, -1, 5000, Y, scales=sd)
+        torch.cuda.synchronize()
+        ctx.tt_profile_enable(True)
+        for t in range(10):
+            ctx.tt_sketch_unfold(A, -1, 5001 + t, Y, scales=sd)
+        torch.cuda.synchronize()
+        iso = ctx.tt_profile_read()
+        ctx.tt_profile_enable(False)
+        ctx.close()
+        del A, Y
+
+        def gbs(pr):
+            n = max(1, pr["unfold_launches"])
+            return (pr["unfold_bytes"] / n) / (pr["unfold_ms"] / n * 1e-3) / 1e9, pr["unfold_bytes"] / n
+
+        g_in, bpl = gbs(prof)
+        g_iso, _ = gbs(iso)
+        sweep_ms = sorted(ms)[len(ms) // 2]
+        forms[st] = {"sweeps_per_s": 1e3 / sweep_ms, "ms_per_sweep_median": sweep_ms,
+                     "data_sketch": {"bytes_per_launch": bpl, "gbs_in_sweep": g_in, "frac_in_sweep": g_in / hbm,
+                                     "gbs_alone": g_iso, "frac_alone": g_iso / hbm, "peak": hbm,
+                                     "peak_kind": peak_kind},
+                     "quantisation_delta": delta,
+                     "rel_error_per_sweep": [round(e, 8) for e in errs],
+                     "rel_error_vs_fp64_tensor_per_sweep": [round(e, 8) for e in errs64],
+                     "rel_error_vs_fp64_tensor_final": errs64[-1]}
+    ctx64.close()
+    base = storages[0]
+    target = forms[base]["rel_error_vs_fp64_tensor_final"] * (1 + 1e-3)
+    for st, r in forms.items():
+        hit = next((i + 1 for i, e in enumerate(r["rel_error_vs_fp64_tensor_per_sweep"]) if e <= target), None)
+        r["sweeps_to_tolerance"] = hit
+        r["sweeps_to_tolerance_per_s"] = (r["sweeps_per_s"] / hit) if hit else None
+        r["final_error_minus_baseline"] = r["rel_error_vs_fp64_tensor_final"] - forms[base]["rel_error_vs_fp64_tensor_final"]
+    return {"workload": f"{w.name}: {'x'.join(map(str, w.dims))}, TT ranks {list(p64.ranks)}, J={w.J}, "
+                        f"lambda={w.lam}, noise={w.noise}, cores {w.core_kind}",
+            "sweeps": nsweeps, "baseline_form": base, "tolerance": target, "forms": forms,
+            "note": "each sweep timed alone with CUDA events (one tt_prox_als_sweep call, synchronised); errors "
+                    "outside the timed sweeps, against the stored tensor and against the FP64 tensor; "
+                    "quantisation_delta = ||A_q - A|| / ||A||; data-sketch GB/s from CUDA events around each "
+                    "launch (algorithmic bytes: N x bytes per entry, plus n_0 scales for FP8)"}
 
 
 def bf16_peak():
@@ -581,6 +788,16 @@ def main():
             out = gemm_pattern(dev)
         elif args.only_pattern == "sparse":
             out = sparse_pattern(dev)
+        elif args.only_pattern == "order3":
+            out = workload_pattern("order3-50-r5", ["f64", "f32"], dev)
+        elif args.only_pattern == "order5":
+            out = workload_pattern("order5-40-r8", ["f32", "bf16", "fp8"], dev)
+        elif args.only_pattern == "gram":
+            w = synth.WORKLOADS[args.workload]
+            out = gram_pattern(w, synth.make_problem(w, storage="f32"), dev)
+        elif args.only_pattern == "deterministic":
+            w = synth.WORKLOADS[args.workload]
+            out = deterministic_pattern(w, synth.make_problem(w, storage="f32"), dev)
         else:
             w = synth.WORKLOADS[args.workload]
             out = precision_pattern(w, synth.make_problem(w, storage="f32"), dev, w.sweeps)
@@ -703,16 +920,29 @@ def main():
         sc_h = np.ascontiguousarray(p.scales, dtype=np.float32) if p.scales is not None else None
         ne = max(3, min(20, args.steps))
         ctx.tt_prox_als_sweep_host(A_h, cores_h, 1, 0, scales_host=sc_h)  # warm (allocates staging)
+        # one asynchronous call per step: each copies the step's tensor and cores in, sweeps, takes
+        # the relative error and copies the cores and the error out; the next step's tensor copy
+        # runs beside this step's sweep. One synchronisation at the end of the timed steps.
+        t0 = time.perf_counter()
+        outs = [ctx.tt_prox_als_sweep_host_async(A_h, cores_h, 1, t + 1, scales_host=sc_h) for t in range(ne)]
+        ctx.tt_host_sync()
+        e2e_s = (time.perf_counter() - t0) / ne
+        assert all(np.isfinite(o[1][0]) for o in outs)
+        # the same steps as synchronous calls (copy in, sweep, error, copy out, wait)
         t0 = time.perf_counter()
         for t in range(ne):
-            ctx.tt_prox_als_sweep_host(A_h, cores_h, 1, t + 1, scales_host=sc_h)
-        e2e_s = (time.perf_counter() - t0) / ne
+            ctx.tt_prox_als_sweep_host(A_h, cores_h, 1, ne + t + 1, scales_host=sc_h)
+        sync_s = (time.perf_counter() - t0) / ne
         core_bytes = sum(int(g.size) * 4 for g in cores_h)
         line["e2e"] = {"value": 1.0 / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(A_h.nbytes) + core_bytes
                        + (int(sc_h.nbytes) if sc_h is not None else 0),
-                       "d2h_bytes_per_step": core_bytes + 16,
-                       "note": "tt_prox_als_sweep_host: H2D copy of the tensor and cores, one sweep, the relative "
-                               "error, D2H of the cores, rel-change and rel error; synchronised; wall clock"}
+                       "d2h_bytes_per_step": core_bytes + 8 + 16 + 4,
+                       "synchronous_call_value": 1.0 / sync_s,
+                       "note": f"{ne} tt_prox_als_sweep_host_async calls from page-locked host memory (each: H2D "
+                               "copy of the tensor and cores, one sweep, the relative error, D2H of the cores, "
+                               "the error sums and the status), then tt_host_sync; wall clock. The tensor copy of "
+                               "a step runs beside the previous step's sweep. synchronous_call_value: the same "
+                               "steps as tt_prox_als_sweep_host calls, each waiting for its results"}
     ctx.close()
     if rank == 0 and world == 1 and not args.no_patterns and storage == "f32":
         line["patterns"] = {"precision": precision_pattern(w, p, dev, w.sweeps)}
@@ -723,12 +953,25 @@ def main():
         torch.cuda.empty_cache()
         line["patterns"]["gemm"] = gemm_pattern(dev)
         line["patterns"]["sparse"] = sparse_pattern(dev)
+        torch.cuda.empty_cache()
+        line["patterns"]["order3"] = workload_pattern("order3-50-r5", ["f64", "f32"], dev)
+        line["patterns"]["order5"] = workload_pattern("order5-40-r8", ["f32", "bf16", "fp8"], dev)
+        torch.cuda.empty_cache()
+        line["patterns"]["deterministic"] = deterministic_pattern(w, p, dev)
+        line["patterns"]["gram"] = gram_pattern(w, p, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
             res = run_cpu_child(["--workload", args.workload] + (["--storage", args.storage] if args.storage else []))
-            line["cpu_baseline"] = {"value": 1.0 / res["sweep_s"], "unit": UNIT, "cores": 1, "kind": "oracle",
-                                    "sample": "one full oracle sweep (Algorithm 1 outer iteration, FP64 numpy, "
-                                              "1 thread) on the same workload, timed once"}
+            line["cpu_baseline"] = {
+                "value": 1.0 / res["sweep_all_cores_s"], "unit": UNIT, "cores": res["cores"], "kind": "oracle",
+                "sample": (f"one oracle sweep (Algorithm 1 outer iteration, FP64 numpy) on the same workload: its "
+                           f"data-sketch columns by definition spread over {res['cores']} single-threaded "
+                           f"processes (one per core of os.sched_getaffinity; {res['sketch_wall_s']:.2f} s wall "
+                           f"for {res['sketch_busy_s']:.2f} s of column work), plus the rest of the sweep serial "
+                           f"({res['serial_rest_s']:.2f} s: the one-thread sweep minus its "
+                           f"{res['sketch_one_thread_s']:.2f} s of data-sketch columns)"),
+                "one_thread": {"value": 1.0 / res["sweep_s"], "unit": UNIT, "cores": 1,
+                               "sample": "one full oracle sweep, FP64 numpy, 1 thread, timed once"}}
         except Exception as e:  # report, do not hide
             line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
                                     "sample": f"failed: {str(e)[-200:]}"}
