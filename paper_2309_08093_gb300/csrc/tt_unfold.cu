@@ -26,43 +26,8 @@
 // Y_k is column-major (J x n_k).
 #include <algorithm>
 
-#include "tt_internal.cuh"
+#include "tt_unfold.cuh"
 
-template <>
-struct TtElem<TT_F64> {
-  using T = double;
-  static constexpr int bytes = 8;
-  __device__ static float get(const void* a, int64_t i) { return (float)__ldg((const double*)a + i); }
-};
-template <>
-struct TtElem<TT_F32> {
-  using T = float;
-  static constexpr int bytes = 4;
-  __device__ static float get(const void* a, int64_t i) { return __ldg((const float*)a + i); }
-};
-template <>
-struct TtElem<TT_BF16> {
-  using T = unsigned short;
-  static constexpr int bytes = 2;
-  __device__ static float get(const void* a, int64_t i) {
-    return __uint_as_float(((uint32_t)__ldg((const unsigned short*)a + i)) << 16);
-  }
-};
-
-// OCP FP8 E4M3 (bias 7, no infinities): decode from the bit fields.
-__device__ __forceinline__ float tt_fp8_e4m3(uint32_t c) {
-  uint32_t s = (c & 0x80u) << 24;
-  uint32_t e = (c >> 3) & 0xFu;
-  uint32_t m = c & 7u;
-  float mag = e ? __uint_as_float(((e + 120u) << 23) | (m << 20)) : (float)m * 0.001953125f;  // 2^-9
-  return __uint_as_float(__float_as_uint(mag) | s);
-}
-template <>
-struct TtElem<TT_FP8E4M3> {
-  using T = unsigned char;
-  static constexpr int bytes = 1;
-  __device__ static float get(const void* a, int64_t i) { return tt_fp8_e4m3(__ldg((const unsigned char*)a + i)); }
-};
 
 // ---------------------------------------------------------------------------------------------
 // mode 0: row-owner fiber gather
@@ -135,14 +100,6 @@ struct TtVec {
   }
 };
 
-// Vector geometry of a fibre: VB-byte loads, vpf vectors per fibre, m vectors per lane, lanes per
-// fibre slot and fibre slots per warp (several short fibres share one warp instruction). Vector v
-// of a fibre is read by lane posl of its slot as (chunk ch, sub-vector mm) with
-// v = ch * lpf * m + mm * lpf + posl, so each of a lane's m loads is coalesced across the slot.
-struct FibreGeom {
-  int64_t fiber_bytes;
-  int vpf, lpf, fpi, nchunk, m;
-};
 
 static FibreGeom fibre_geom(int64_t fiber_bytes, int VB, int M) {
   FibreGeom g;
@@ -190,33 +147,8 @@ __device__ __forceinline__ void cp_async_vec(void* smem, const void* gmem, int b
   else
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem));
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
-struct GArgs {
-  const char* A;
-  const float* scales;    // n0 FP8 scales or null
-  const int32_t* h0;      // h_0 (n0 entries)
-  const int8_t* v0;
-  const uint32_t* plan;   // fibre index at i_k = 0 | sign in bit 31, grouped by c
-  const int32_t* ulist;   // distinct c values
-  const int64_t* ustart;  // starts into plan (U + 1)
-  const int32_t* ucount;  // U
-  float* Y;               // J x ncol column-major, zeroed by the host
-  int64_t col_fibres;     // fibre-index stride of the output column (stride_k / n0); 0 for mode 0
-  int J, n0, ncol;
-  int nseg;               // c-segments per column (work items = ncol * nseg)
-  int segmax;             // capacity of the staged segment (c groups)
-  int y_vec4;             // Y 16-byte aligned and J % 4 == 0: columns flushed with 16-byte atomics
-  FibreGeom fg;
-};
 
-// Bytes of the cp.async ring at the start of the gather kernel's shared memory (none when the
-// vectors are loaded synchronously). Used by the kernel and by the host-side size computation.
-__host__ __device__ constexpr size_t gather_ring_bytes(bool async, int nwarps, int stages, int vb) {
-  return async ? (size_t)nwarps * stages * 32 * vb : 0;
-}
 
 // One work item = a contiguous segment of c groups of one output column (mode 0: of Y_0's
 // rows). The item's fibres are split evenly over the (warp, fibre-slot) pairs; each lane keeps S
@@ -632,6 +564,7 @@ static int launch_cols_s(tt_ctx* c, const void* A, const float* scales, int k, f
   a.n0 = (int)c->n[0];
   a.ncol = (int)c->n[k];
   a.col_fibres = c->stride[k] / c->n[0];
+  a.total_bytes = c->N * EB;
   a.fg = fibre_geom(fiber_bytes, VB, 1);
   const int sms = tt_sm_count();
   const int ncolg = (a.ncol + G - 1) / G;
@@ -699,6 +632,7 @@ static int launch_gather_vbm(tt_ctx* c, const void* A, const float* scales, int 
   a.n0 = (int)c->n[0];
   a.ncol = MODE0 ? 1 : (int)c->n[k];
   a.col_fibres = MODE0 ? 0 : c->stride[k] / c->n[0];
+  a.total_bytes = c->N * TtElem<DT>::bytes;
   a.fg = fibre_geom((int64_t)c->n[0] * TtElem<DT>::bytes, VB, M);
   const int sms = tt_sm_count();
   // work items (column, c-segment): at most one per CTA slot (two CTAs per SM) when the columns
@@ -783,6 +717,12 @@ template <int DT, bool MODE0>
 static int launch_gather(tt_ctx* c, const void* A, const float* scales, int k, float* Y) {
   constexpr int EB = TtElem<DT>::bytes;
   const int vb = pick_vb((int64_t)c->n[0] * EB, (uintptr_t)A, EB);
+  if (vb < 16 && ((int64_t)c->n[0] * EB) % 16 != 0) {
+    // fibres off the 16-byte grid: window staging keeps every copy 16 bytes wide
+    bool done = false;
+    const int rc = tt_launch_unfold_win(c, A, scales, k, Y, &done);
+    if (rc != TT_OK || done) return rc;
+  }
   switch (vb) {
     case 16: return launch_gather_vb<DT, 16, MODE0>(c, A, scales, k, Y);
     case 8: return launch_gather_vb<DT, (EB <= 8 ? 8 : 16), MODE0>(c, A, scales, k, Y);

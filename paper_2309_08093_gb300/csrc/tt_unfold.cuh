@@ -1,0 +1,100 @@
+// Shared by the data-sketch kernels of Alg. 1 part (a) (tt_unfold.cu: 16-, 8-, 4-, 2- and 1-byte
+// vector loads of mode-0 fibres; tt_unfold_win.cu: window staging of fibres that do not start on
+// a 16-byte boundary): element types, the kernels' argument block and the cp.async helpers.
+#pragma once
+
+#include "tt_internal.cuh"
+
+template <>
+struct TtElem<TT_F64> {
+  using T = double;
+  static constexpr int bytes = 8;
+  __device__ static float get(const void* a, int64_t i) { return (float)__ldg((const double*)a + i); }
+  __device__ static float sget(const unsigned char* p) { return (float)*reinterpret_cast<const double*>(p); }
+};
+template <>
+struct TtElem<TT_F32> {
+  using T = float;
+  static constexpr int bytes = 4;
+  __device__ static float get(const void* a, int64_t i) { return __ldg((const float*)a + i); }
+  __device__ static float sget(const unsigned char* p) { return *reinterpret_cast<const float*>(p); }
+};
+template <>
+struct TtElem<TT_BF16> {
+  using T = unsigned short;
+  static constexpr int bytes = 2;
+  __device__ static float get(const void* a, int64_t i) {
+    return __uint_as_float(((uint32_t)__ldg((const unsigned short*)a + i)) << 16);
+  }
+  __device__ static float sget(const unsigned char* p) {
+    return __uint_as_float(((uint32_t)*reinterpret_cast<const unsigned short*>(p)) << 16);
+  }
+};
+
+// OCP FP8 E4M3 (bias 7, no infinities): decode from the bit fields.
+__device__ __forceinline__ float tt_fp8_e4m3(uint32_t c) {
+  uint32_t s = (c & 0x80u) << 24;
+  uint32_t e = (c >> 3) & 0xFu;
+  uint32_t m = c & 7u;
+  float mag = e ? __uint_as_float(((e + 120u) << 23) | (m << 20)) : (float)m * 0.001953125f;  // 2^-9
+  return __uint_as_float(__float_as_uint(mag) | s);
+}
+template <>
+struct TtElem<TT_FP8E4M3> {
+  using T = unsigned char;
+  static constexpr int bytes = 1;
+  __device__ static float get(const void* a, int64_t i) { return tt_fp8_e4m3(__ldg((const unsigned char*)a + i)); }
+  __device__ static float sget(const unsigned char* p) { return tt_fp8_e4m3(*p); }
+};
+
+// Vector geometry of a fibre: VB-byte loads, vpf vectors per fibre, m vectors per lane, lanes per
+// fibre slot and fibre slots per warp (several short fibres share one warp instruction). Vector v
+// of a fibre is read by lane posl of its slot as (chunk ch, sub-vector mm) with
+// v = ch * lpf * m + mm * lpf + posl, so each of a lane's m loads is coalesced across the slot.
+struct FibreGeom {
+  int64_t fiber_bytes;
+  int vpf, lpf, fpi, nchunk, m;
+};
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// 16-byte copy global -> shared of `bytes` (1..16) valid source bytes, the rest of the 16
+// destination bytes zero-filled; both addresses 16-byte aligned
+__device__ __forceinline__ void cp_async_16z(void* smem, const void* gmem, int bytes) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(bytes));
+}
+
+struct GArgs {
+  const char* A;
+  const float* scales;    // n0 FP8 scales or null
+  const int32_t* h0;      // h_0 (n0 entries)
+  const int8_t* v0;
+  const uint32_t* plan;   // fibre index at i_k = 0 | sign in bit 31, grouped by c
+  const int32_t* ulist;   // distinct c values
+  const int64_t* ustart;  // starts into plan (U + 1)
+  const int32_t* ucount;  // U
+  float* Y;               // J x ncol column-major, zeroed by the host
+  int64_t col_fibres;     // fibre-index stride of the output column (stride_k / n0); 0 for mode 0
+  int J, n0, ncol;
+  int nseg;               // c-segments per column (work items = ncol * nseg)
+  int segmax;             // capacity of the staged segment (c groups)
+  int y_vec4;             // Y 16-byte aligned and J % 4 == 0: columns flushed with 16-byte atomics
+  int64_t total_bytes;    // bytes of A (window staging clips its last copies here)
+  int wstride;            // window staging: bytes of a fibre's region of a stage (a multiple of 16)
+  int wstage;             // window staging: bytes of one warp's stage
+  FibreGeom fg;
+};
+
+// Bytes of the cp.async ring at the start of the gather kernel's shared memory (none when the
+// vectors are loaded synchronously). Used by the kernel and by the host-side size computation.
+__host__ __device__ constexpr size_t gather_ring_bytes(bool async, int nwarps, int stages, int vb) {
+  return async ? (size_t)nwarps * stages * 32 * vb : 0;
+}
+
+// Modes k of the data sketch whose fibres do not start on a 16-byte boundary (n_0 * element bytes
+// not a multiple of 16) and A 16-byte aligned: launches the window-staging kernel on c->stream and
+// sets *done, or returns TT_OK with *done = false when the shape does not suit it.
+int tt_launch_unfold_win(tt_ctx* c, const void* A, const float* scales, int k, float* Y, bool* done);

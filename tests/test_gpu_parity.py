@@ -107,7 +107,11 @@ CASES_A = [((7, 5, 9), 64, "f32"), ((3, 5, 7, 2), 16, "f32"), ((50, 50, 50), 102
            ((33, 17, 9, 5), 200, "fp8"), ((12, 10, 8), 2000, "f64"), ((10,) * 6, 45, "f32"),
            # fibres whose length is not a multiple of 16 bytes (8- and 4-byte vectors, up to 16 per lane)
            ((62, 9, 7), 512, "f32"), ((30, 7, 11), 256, "bf16"), ((123, 8, 6), 1024, "f32"),
-           ((126, 5, 4, 3), 2048, "f32"), ((67, 12, 5), 512, "fp8")]
+           ((126, 5, 4, 3), 2048, "f32"), ((67, 12, 5), 512, "fp8"),
+           # window staging: FP64 with odd n_0, a window of 77 vectors (four per lane), windows too
+           # long for one slot (the narrow-vector path), J not a multiple of 4
+           ((25, 6, 7), 512, "f64"), ((301, 5, 3), 1024, "f32"), ((509, 3, 2), 256, "f32"),
+           ((600, 3, 2), 128, "fp8"), ((45, 9, 4), 150, "bf16")]
 
 
 def _data(dims, storage, seed):
@@ -144,6 +148,27 @@ def test_unfold_sketch_parity(dims, J, storage):
     ctx.tt_sketch_unfold(Ad, 1, 0, Y1, scales=sd)
     hs, vs = O.draw_sketch(seed, 0, dims, J)
     assert rel(Y1[1].cpu().numpy().reshape(dims[1], J).T, O.sketch_unfolding(exact, hs, vs, J, 1)) <= TOL
+    ctx.close()
+
+
+@pytest.mark.parametrize("offset", [1, 3, 4])
+def test_unfold_sketch_offset_base(offset):
+    """A tensor that starts `offset` FP32 entries into its allocation: 4 and 12 bytes off the
+    16-byte grid (the narrow-vector path) and 16 bytes (the window staging of 62-entry fibres)."""
+    dims, J, storage = (62, 9, 7), 512, "f32"
+    seed = 77 + offset
+    flat, _, exact = _data(dims, storage, seed)
+    ctx = lib.Context(dims, (1, 1, 1, 1), J, 1e-3, seed, storage)
+    buf = torch.zeros(flat.size + offset, dtype=torch.float32, device="cuda")
+    buf[offset:] = torch.from_numpy(np.ascontiguousarray(flat, dtype=np.float32)).cuda()
+    Ad = buf[offset:]
+    Y = [torch.zeros(J * n, device="cuda") for n in dims]
+    ctx.tt_sketch_unfold(Ad, -1, 0, Y)
+    hs, vs = O.draw_sketch(seed, 0, dims, J)
+    for k in range(len(dims)):
+        ref = O.sketch_unfolding(exact, hs, vs, J, k)
+        got = Y[k].cpu().numpy().reshape(dims[k], J).T
+        assert rel(got, ref) <= TOL, (k, rel(got, ref))
     ctx.close()
 
 
