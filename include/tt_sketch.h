@@ -81,6 +81,12 @@ enum {
  * the mixed-precision form). */
 #define TT_FLAG_TC_GRAM 8u
 #define TT_FLAG_TF32_GRAM 16u
+/* Batched contexts (tt_batch_init): on the first tt_batch_sweep, time every tensor's data-sketch
+ * launches alone over a few work-item counts and CTA-per-SM limits and keep the fastest. Off by
+ * default: the batch sizes the work items of each tensor by its bytes (at least 1 MB of A per
+ * item), which keeps small tensors' launches to a few CTAs so that many run side by side, and
+ * timing each launch alone optimises its own latency rather than the batch's throughput. */
+#define TT_FLAG_BATCH_AUTOTUNE 32u
 
 typedef struct {
   int d;              /* order of the tensor, 2 <= d <= 8 */
@@ -328,8 +334,9 @@ int tt_prox_update_noalloc(const float* Y_dev, const float* SH_dev, float* core_
  * array itself may be NULL when no tensor is FP8), cores_dev[i] (host array of params[i].d device
  * core pointers, updated in place). One sweep of all tensors is captured once into a CUDA graph
  * (tensors spread over the stream pool, forked from and joined to `cuda_stream`) and replayed
- * with one graph launch per sweep; the graph is recaptured when any pointer changes. The first
- * call also autotunes the unfold kernel of every tensor on its own data. Sweep t of the call uses
+ * with one graph launch per sweep; the graph is recaptured when any pointer changes. With
+ * TT_FLAG_BATCH_AUTOTUNE in a tensor's flags the first call also times that tensor's data-sketch
+ * launch shapes on its own data and keeps the fastest. Sweep t of the call uses
  * hash draw first_sweep + t (or 0 with TT_FLAG_FIXED_SKETCH). Synchronises `cuda_stream`;
  * returns TT_ENOTSPD etc. for the first tensor whose solve failed (tt_batch_last_error).
  */

@@ -3,9 +3,11 @@
 // i runs on stream i mod S of a stream pool, forked from and joined to the caller's stream -- and
 // every later sweep is a single cudaGraphLaunch. The sweep index lives in a device counter that the
 // graph increments, so each replay draws the next sketch (Alg. 1 redraws S_k per outer iteration).
-// Before the first capture an autotuner times, per mode and on each tensor's own data, the default
-// data-sketch launch and the one-column kernel at a few work-item granularities and CTA-per-SM
-// limits, and keeps the fastest.
+// The data-sketch launches of a batched tensor size their work items by its bytes
+// (TT_BATCH_ITEM_BYTES), so that a small tensor's launch takes few CTAs and those of other tensors
+// run beside it. With TT_FLAG_BATCH_AUTOTUNE an autotuner times, per mode and on the tensor's own
+// data before the first capture, the default launch and the one-column kernel at a few work-item
+// granularities and CTA-per-SM limits, and keeps the fastest alone.
 #include <stdio.h>
 
 #include <algorithm>
@@ -73,6 +75,7 @@ extern "C" int tt_batch_init(tt_batch** out, int count, const tt_params* params,
       return rc;
     }
     b->ctx[i]->d_sweep_ptr = b->d_sweep;
+    b->ctx[i]->item_bytes = TT_BATCH_ITEM_BYTES;
   }
   *out = b;
   return TT_OK;
@@ -123,7 +126,7 @@ static int autotune(tt_batch* b, const void* const* A, const float* const* S) {
   static const int cps[] = {1, 2};
   for (int i = 0; i < b->count; ++i) {
     tt_ctx* c = b->ctx[i];
-    if (c->det) continue;  // the fixed-point data sketch has no tunables
+    if (c->det || !(c->flags & TT_FLAG_BATCH_AUTOTUNE)) continue;  // no tunables / not asked for
     int rc = tt_ensure_tables(c, 0);
     if (rc) return rc;
     for (int k = 0; k < c->d; ++k) {

@@ -167,6 +167,11 @@ struct tt_ctx {
   bool capture_mode = false;
   const uint64_t* d_sweep_ptr = nullptr;
 
+  // least bytes of A per work item of a data-sketch launch (0: items sized for one tensor alone,
+  // about one per CTA slot). Contexts of a batch set it, so that a small tensor's launch takes few
+  // CTAs and the launches of the batch's other tensors run beside it.
+  int64_t item_bytes = 0;
+
   // autotuned parameters of the unfold kernel per mode (0 = default)
   int tune_seg_mult[TT_MAX_D] = {0};   // multiplier of the work-item count
   int tune_cta_per_sm[TT_MAX_D] = {0}; // CTAs per SM (1 or 2)
@@ -198,6 +203,8 @@ struct tt_ctx {
   int host_error = 0;                 // first failure of a call finished but not yet reported
 };
 #define TT_HOST_SLOTS 4
+// least bytes of A per data-sketch work item for the tensors of a batch (tt_ctx::item_bytes)
+#define TT_BATCH_ITEM_BYTES (1024 * 1024)
 // bytes of one pinned result slot: the status word, the two error sums, 2 d change sums per sweep
 size_t tt_host_slot_bytes(const tt_ctx* c);
 // the host-buffer calls' resources (tt_host.cu)

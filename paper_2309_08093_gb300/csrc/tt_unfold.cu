@@ -573,9 +573,8 @@ static int launch_cols_s(tt_ctx* c, const void* A, const float* scales, int k, f
   // the chain kernels sooner; measured best of 1, 2, 4, 8 at 100^4)
   int nseg = std::max(1, slots / ncolg);
   if (c->in_sweep) nseg *= 4;
-  nseg = std::max(nseg, (c->J + 2047) / 2048);
-  a.nseg = nseg;
-  a.segmax = (c->J + nseg - 1) / nseg + 1;
+  a.nseg = tt_unfold_nseg(c, ncolg, nseg);
+  a.segmax = (c->J + a.nseg - 1) / a.nseg + 1;
   const size_t smem = gather_ring_bytes(true, THREADS / 32, S * MV_MAX, VB) + sizeof(float) * (size_t)G * c->J +
                       sizeof(int) * (2 * (size_t)a.segmax + 1);
   if (smem > smax) return TT_OK;
@@ -644,9 +643,8 @@ static int launch_gather_vbm(tt_ctx* c, const void* A, const float* scales, int 
   int nseg = std::max(1, slots / a.ncol);
   if (c->tune_seg_mult[k]) nseg *= c->tune_seg_mult[k];
   else if (c->in_sweep) nseg *= 4;  // beside the chain: short CTAs free SM slots often
-  nseg = std::max(nseg, (c->J + 2047) / 2048);
-  a.nseg = nseg;
-  a.segmax = (c->J + nseg - 1) / nseg + 1;
+  a.nseg = tt_unfold_nseg(c, a.ncol, nseg);
+  a.segmax = (c->J + a.nseg - 1) / a.nseg + 1;
   const size_t ring = gather_ring_bytes(VB >= 4, THREADS / 32, S * M, VB);
   const size_t smem = ring + sizeof(float) * (MODE0 ? 0 : c->J) + sizeof(int) * (2 * (size_t)a.segmax + 1);
   if (smem > 220 * 1024) return tt_fail(c, TT_EINVAL, "gather kernel needs %zu bytes of shared memory", smem);

@@ -3,6 +3,8 @@
 // a 16-byte boundary): element types, the kernels' argument block and the cp.async helpers.
 #pragma once
 
+#include <algorithm>
+
 #include "tt_internal.cuh"
 
 template <>
@@ -92,6 +94,17 @@ struct GArgs {
 // vectors are loaded synchronously). Used by the kernel and by the host-side size computation.
 __host__ __device__ constexpr size_t gather_ring_bytes(bool async, int nwarps, int stages, int vb) {
   return async ? (size_t)nwarps * stages * 32 * vb : 0;
+}
+
+// c-segments per column unit (column or column group) of a data-sketch launch: `nseg` as chosen
+// for a tensor alone, at most (bytes of A / c->item_bytes) work items in all when the context sets
+// item_bytes, and at least one segment per 2048 c groups (the staged segment's capacity).
+inline int tt_unfold_nseg(const tt_ctx* c, int units, int nseg) {
+  if (c->item_bytes > 0) {
+    const int64_t cap = std::max<int64_t>(1, c->N * tt_elem_bytes(c->dtype) / c->item_bytes);
+    nseg = (int)std::min<int64_t>(nseg, std::max<int64_t>(1, cap / units));
+  }
+  return std::max(nseg, (c->J + 2047) / 2048);
 }
 
 // Modes k of the data sketch whose fibres do not start on a 16-byte boundary (n_0 * element bytes

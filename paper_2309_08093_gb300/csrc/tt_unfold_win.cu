@@ -401,13 +401,13 @@ GArgs win_args(tt_ctx* c, const void* A, const float* scales, int k, float* Y, i
   return a;
 }
 
-// segments of at most 2048 c groups, at least `slots` work items in all; four times as many
-// beside the chain of a sweep (short CTAs hand SM slots to the chain kernels sooner)
+// about `slots` work items in all, four times as many beside the chain of a sweep (short CTAs
+// hand SM slots to the chain kernels sooner), capped by tt_unfold_nseg
 int win_nseg(tt_ctx* c, int k, int units, int slots) {
   int nseg = std::max(1, slots / units);
   if (c->tune_seg_mult[k]) nseg *= c->tune_seg_mult[k];
   else if (c->in_sweep) nseg *= 4;
-  return std::max(nseg, (c->J + 2047) / 2048);
+  return tt_unfold_nseg(c, units, nseg);
 }
 
 template <int DT, int S, int EPT>

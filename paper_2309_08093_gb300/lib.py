@@ -23,6 +23,7 @@ TT_FLAG_FP64_SOLVE = 2
 TT_FLAG_DETERMINISTIC = 4
 TT_FLAG_TC_GRAM = 8
 TT_FLAG_TF32_GRAM = 16
+TT_FLAG_BATCH_AUTOTUNE = 32
 
 EXPORTS = ["tt_sketch_init", "tt_sketch_destroy", "tt_last_error", "tt_sketch_tables",
            "tt_sketch_set_tables", "tt_sketch_unfold", "tt_sketch_unfold_coo", "tt_rel_error_coo", "tt_sketch_interface", "tt_prox_update",

@@ -97,3 +97,19 @@ def test_workspace_cap_gives_enomem_before_any_device_call(libpath):
         assert L.tt_sketch_init(ctypes.byref(ctx), ctypes.byref(p_bad), None) == lib.TT_EINVAL
     finally:
         assert lib.tt_set_workspace_limit(0) == 1 << 16
+
+
+def test_binding_constants_match_the_header():
+    """Every TT_FLAG_* / storage-type / status constant of the Python binding has the value the
+    header defines."""
+    from paper_2309_08093_gb300 import lib
+
+    src = open(os.path.join(ROOT, "include", "tt_sketch.h")).read()
+    defs = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define\s+(TT_FLAG_\w+)\s+(\d+)u", src)}
+    enums = {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(TT_\w+)\s*=\s*(-?\d+)", src)}
+    assert len(defs) >= 6
+    for name, val in {**defs, **enums}.items():
+        if hasattr(lib, name):
+            assert getattr(lib, name) == val, name
+    for name in defs:
+        assert hasattr(lib, name), name

@@ -29,12 +29,18 @@ def _setup(specs):
     return As, inits, flats
 
 
-def test_batched_matches_single_tensor_path_and_oracle():
+@pytest.mark.parametrize("autotune", [False, True])
+def test_batched_matches_single_tensor_path_and_oracle(autotune):
     """Batched vs single-tensor GPU runs differ only by FP32 summation order (fibres reach a
-    group in a nondeterministic order); before convergence the iteration amplifies that, so the
-    comparison uses 1e-4. The oracle comparison keeps the FP32 tolerance 1e-5 (+1e-7 absolute)."""
+    group in a nondeterministic order, and the batch sizes its work items by bytes); before
+    convergence the iteration amplifies that, so the comparison uses 1e-4. The oracle comparison
+    keeps the FP32 tolerance 1e-5 (+1e-7 absolute). With TT_FLAG_BATCH_AUTOTUNE on every other
+    tensor, those tensors' data sketches run in the launch shapes the autotuner picked."""
     nsw = 8
     specs = synth.batched_specs(count=7, dims_range=(6, 18), rank_range=(2, 5))
+    if autotune:
+        for sp in specs[::2]:
+            sp["flags"] = lib.TT_FLAG_BATCH_AUTOTUNE
     As, inits, exact = _setup(specs)
     cores_b = [lib.device_cores(c) for c in inits]
     batch = lib.Batch(specs)
