@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--no-patterns", action="store_true", help="skip the precision/batched/warm-start patterns")
     ap.add_argument("--only-pattern", default=None,
                     choices=["precision", "batched", "warmstart", "gemm", "sparse", "order3", "order5",
-                             "deterministic", "gram"],
+                             "deterministic", "gram", "window"],
                     help="run one pattern and print its JSON")
     ap.add_argument("--ws-train", type=int, default=10240, help="warm-start training solves")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
@@ -611,6 +611,55 @@ def sparse_pattern(dev, nnz=20_000_000, reps=10):
                     "(6.5 MB per mode); input GB/s counts the int32 indices and FP32 values read"}
 
 
+def window_pattern(dev, reps=10):
+    """The data sketch of tensors whose mode-0 fibres are off the 16-byte grid (window staging),
+    each mode alone (tt_sketch_unfold, CUDA events, `reps` calls after two warm-up calls): FP32
+    with 101-entry fibres (404 bytes, on a 4-byte grid), BF16 with 101-entry fibres (202 bytes,
+    on a 2-byte grid), and the FP32 100-entry fibres of the same shape (400 bytes, on the 16-byte
+    grid) for comparison. Seeded N(0,1) entries, generated on the device; J = 1024, one draw."""
+    import numpy as np
+    import torch
+    from paper_2309_08093_gb300 import lib
+
+    hbm, hbm_src = peaks()
+    cases = [((101, 84, 93, 50), "f32"), ((101, 84, 93, 100), "bf16"), ((100, 84, 93, 50), "f32")]
+    stream = torch.cuda.current_stream()
+    out = {"peak_gbs": hbm, "peak_source": hbm_src, "cases": []}
+    for dims, dt in cases:
+        n = int(np.prod(dims))
+        g = torch.Generator(device=dev)
+        g.manual_seed(20230923)
+        a = torch.randn(n, generator=g, device=dev)
+        if dt == "bf16":
+            a = a.to(torch.bfloat16)
+        ctx = lib.Context(dims, (1, 4, 4, 4, 1), 1024, 1e-3, 7, dt)
+        Y = [torch.zeros(1024 * m, device=dev) for m in dims]
+        nbytes = a.numel() * a.element_size()
+        per_mode = []
+        for k in range(len(dims)):
+            Yk = [None] * len(dims)
+            Yk[k] = Y[k]
+            for _ in range(2):
+                ctx.tt_sketch_unfold(a, k, 0, Yk)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(reps):
+                ctx.tt_sketch_unfold(a, k, 0, Yk)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            us = e0.elapsed_time(e1) / reps * 1e3
+            gbs = nbytes / us / 1e3
+            per_mode.append({"mode": k, "us": us, "gbs": gbs, "frac": gbs / hbm})
+        ctx.close()
+        del a, Y
+        out["cases"].append({"dims": list(dims), "storage": dt, "fibre_bytes": dims[0] * (4 if dt == "f32" else 2),
+                             "tensor_mb": nbytes / 1e6, "modes": per_mode})
+    out["note"] = ("each call zeroes Y_k and launches one data-sketch kernel; GB/s = tensor bytes / call time; "
+                   "frac of the " + hbm_src + " copy peak")
+    return out
+
+
 # ---------------------------------------------------------------------------------------------
 # learned-warm-start pattern: the network (summary of the data sketch -> initial cores) trained
 # on method-generated solves of the 256 x 256 x 3 x 128 smooth-core family, then held-out tensors
@@ -795,6 +844,8 @@ def main():
         elif args.only_pattern == "gram":
             w = synth.WORKLOADS[args.workload]
             out = gram_pattern(w, synth.make_problem(w, storage="f32"), dev)
+        elif args.only_pattern == "window":
+            out = window_pattern(dev)
         elif args.only_pattern == "deterministic":
             w = synth.WORKLOADS[args.workload]
             out = deterministic_pattern(w, synth.make_problem(w, storage="f32"), dev)
@@ -959,6 +1010,8 @@ def main():
         torch.cuda.empty_cache()
         line["patterns"]["deterministic"] = deterministic_pattern(w, p, dev)
         line["patterns"]["gram"] = gram_pattern(w, p, dev)
+        torch.cuda.empty_cache()
+        line["patterns"]["window"] = window_pattern(dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
             res = run_cpu_child(["--workload", args.workload] + (["--storage", args.storage] if args.storage else []))

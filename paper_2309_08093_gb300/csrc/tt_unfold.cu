@@ -715,8 +715,9 @@ template <int DT, bool MODE0>
 static int launch_gather(tt_ctx* c, const void* A, const float* scales, int k, float* Y) {
   constexpr int EB = TtElem<DT>::bytes;
   const int vb = pick_vb((int64_t)c->n[0] * EB, (uintptr_t)A, EB);
-  if (vb < 16 && ((int64_t)c->n[0] * EB) % 16 != 0) {
-    // fibres off the 16-byte grid: window staging keeps every copy 16 bytes wide
+  if (vb <= 4 && ((int64_t)c->n[0] * EB) % 16 != 0) {
+    // fibres on a 1-, 2- or 4-byte grid: window staging keeps every copy 16 bytes wide (on an
+    // 8-byte grid the 8-byte vectors measured as fast for FP32 and faster for BF16)
     bool done = false;
     const int rc = tt_launch_unfold_win(c, A, scales, k, Y, &done);
     if (rc != TT_OK || done) return rc;

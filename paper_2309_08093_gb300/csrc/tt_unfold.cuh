@@ -107,7 +107,7 @@ inline int tt_unfold_nseg(const tt_ctx* c, int units, int nseg) {
   return std::max(nseg, (c->J + 2047) / 2048);
 }
 
-// Modes k of the data sketch whose fibres do not start on a 16-byte boundary (n_0 * element bytes
-// not a multiple of 16) and A 16-byte aligned: launches the window-staging kernel on c->stream and
-// sets *done, or returns TT_OK with *done = false when the shape does not suit it.
+// Modes k of the data sketch whose fibres lie on a 1-, 2- or 4-byte grid (n_0 * element bytes not
+// a multiple of 8; FP32, BF16 or FP8) and A 16-byte aligned: launches the window-staging kernel on
+// c->stream and sets *done, or returns TT_OK with *done = false when the shape does not suit it.
 int tt_launch_unfold_win(tt_ctx* c, const void* A, const float* scales, int k, float* Y, bool* done);

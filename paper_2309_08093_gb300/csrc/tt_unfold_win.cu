@@ -1,7 +1,8 @@
 // Part (a) of Alg. 1, the data sketch Y_k = S A_(k)^T (Eqs. (eqn_h), (eqn_v); the regrouping by
 // mode-0 fibres is that of tt_unfold.cu), for tensors whose mode-0 fibres do not start on a
 // 16-byte boundary: n_0 * element bytes is not a multiple of 16, so fibre f starts at byte
-// f * n_0 * element bytes, on a 2-, 4- or 8-byte boundary that changes from fibre to fibre.
+// f * n_0 * element bytes, on a 1-, 2- or 4-byte boundary that changes from fibre to fibre (the
+// 8-byte case keeps the 8-byte vector kernels of tt_unfold.cu).
 //
 // Window staging. A fibre is fetched as the 16-byte-aligned window around it: window vector w
 // covers bytes [16 w, 16 w + 16) from the aligned address at or below the fibre's first byte, and
@@ -515,7 +516,7 @@ int tt_launch_unfold_win(tt_ctx* c, const void* A, const float* scales, int k, f
   *done = false;
   if ((reinterpret_cast<uintptr_t>(A) & 15) != 0) return TT_OK;
   switch (c->dtype) {
-    case TT_F64: return win_dt<TT_F64>(c, A, scales, k, Y, done);
+    case TT_F64: return TT_OK;  // FP64 fibres lie on an 8-byte grid: the 8-byte vector kernels
     case TT_F32: return win_dt<TT_F32>(c, A, scales, k, Y, done);
     case TT_BF16: return win_dt<TT_BF16>(c, A, scales, k, Y, done);
     default: return win_dt<TT_FP8E4M3>(c, A, scales, k, Y, done);

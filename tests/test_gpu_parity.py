@@ -108,10 +108,10 @@ CASES_A = [((7, 5, 9), 64, "f32"), ((3, 5, 7, 2), 16, "f32"), ((50, 50, 50), 102
            # fibres whose length is not a multiple of 16 bytes (8- and 4-byte vectors, up to 16 per lane)
            ((62, 9, 7), 512, "f32"), ((30, 7, 11), 256, "bf16"), ((123, 8, 6), 1024, "f32"),
            ((126, 5, 4, 3), 2048, "f32"), ((67, 12, 5), 512, "fp8"),
-           # window staging: FP64 with odd n_0, a window of 77 vectors (four per lane), windows too
-           # long for one slot (the narrow-vector path), J not a multiple of 4
+           # FP64 with odd n_0 (8-byte grid); window staging with long fibres (one fibre per slot of
+           # 32 lanes), fibres too long for it (the narrow-vector path), J not a multiple of 4
            ((25, 6, 7), 512, "f64"), ((301, 5, 3), 1024, "f32"), ((509, 3, 2), 256, "f32"),
-           ((600, 3, 2), 128, "fp8"), ((45, 9, 4), 150, "bf16")]
+           ((515, 3, 2), 256, "f32"), ((600, 3, 2), 128, "fp8"), ((45, 9, 4), 150, "bf16")]
 
 
 def _data(dims, storage, seed):
@@ -154,8 +154,8 @@ def test_unfold_sketch_parity(dims, J, storage):
 @pytest.mark.parametrize("offset", [1, 3, 4])
 def test_unfold_sketch_offset_base(offset):
     """A tensor that starts `offset` FP32 entries into its allocation: 4 and 12 bytes off the
-    16-byte grid (the narrow-vector path) and 16 bytes (the window staging of 62-entry fibres)."""
-    dims, J, storage = (62, 9, 7), 512, "f32"
+    16-byte grid (the narrow-vector path) and 16 bytes (the window staging of 61-entry fibres)."""
+    dims, J, storage = (61, 9, 7), 512, "f32"
     seed = 77 + offset
     flat, _, exact = _data(dims, storage, seed)
     ctx = lib.Context(dims, (1, 1, 1, 1), J, 1e-3, seed, storage)
