@@ -92,9 +92,14 @@ def test_second_experiment_oscillatory_function():
     the outer two), sketch size 1000: the interior cores have 200 and 400 unknowns and go through
     the Cholesky solve. Reference: TT-SVD at the same ranks (the oracle's, within sqrt(d - 1) of
     the best approximation; a TT-ALS run at rank 20 takes the oracle about a minute). With
-    sigma = 0.5 the error after 100 sweeps must lie within 1.5x of TT-SVD's. With sigma = 0 the
-    FP32 sketched Gram of these cores is refused as not positive definite (TT_ENOTSPD) on every
-    run, recorded as not converged: the proximal term is what makes this case solvable here."""
+    sigma = 0.5 the error after 100 sweeps must lie within 1.5x of TT-SVD's. With sigma = 0 (the
+    FP64 solve) a run stops with TT_ENOTSPD at the first draw that hashes two of the 10 indices of
+    an end core into one of the m buckets: the end cores (1 x 10 x 10 and 10 x 10 x 1) are square,
+    so the sketched interface of their neighbour then loses rank, the Gram is singular, and the
+    oracle refuses the same update (test_gpu_solve64.py checks the first such refusal against the
+    oracle's). A draw has such a collision with probability about 0.086 (two end modes, 10 indices
+    into 1000 buckets each), so over 100 sweeps it is nearly certain; those runs are recorded as
+    not converged. The proximal term is what keeps this case solvable."""
     ranks = (1, 10, 20, 20, 20, 10, 1)
     A = synth.paper_function_tensor("osc")
     e_svd = O.rel_error(A, O.tt_svd(A, ranks))
