@@ -14,20 +14,22 @@
 //     Y_k[b, i_k] = sum_{i_0} v_0(i_0) Z_k[i_0, (b - h_0(i_0)) mod J],
 // i.e. column i_k is a sum of n_0 circularly rolled rows of Z_k.
 //
-// One kernel serves both. Each CTA owns a contiguous range of (column i_k, c) groups of the plan
-// and walks it in chunks of C groups. Phase 1 builds the chunk's Z rows in shared memory: the
-// chunk's fibres are split evenly over (warp, fibre-slot) pairs, each sums its runs of equal c
-// in registers (plan words prefetched one round ahead, U fibres in flight), stores inner runs and
-// adds its first/last run (possibly shared with a neighbour) with shared-memory atomics.
-// Phase 2 (k >= 1) adds coef(i_0) * Z[c, i_0] into bucket (c + h_0(i_0)) mod J of the CTA's
-// column copy; consecutive threads take consecutive c, so the shared-memory atomics hit
-// consecutive banks. The column is flushed to global with 16-byte vector atomics when the CTA
-// moves to the next column. For mode 0, phase 2 writes the finished rows straight to Y_0.
-// Y_k is column-major (J x n_k).
+// The plan of mode k (tt_context.cu) lists the fibres at i_k = 0 grouped by their tail hash c, so
+// fibres of equal c are walked one after the other and summed in registers (a "run"), and a run's
+// sum is flushed once:
+//   k_unfold_gather (mode 0; modes >= 1 when the kernel below does not apply): one output column
+//     per work item; the item's fibres are split over (warp, fibre slot) pairs, several short
+//     fibres per warp; mode 0 writes a finished run as row c of Y_0, modes >= 1 add
+//     coef(i_0) * run into bucket (c + h_0(i_0)) mod J of the CTA's column copy;
+//   k_unfold_cols (modes >= 1): G = 4 neighbouring columns per work item, one plan entry (four
+//     fibres) per warp step, every lane on the same entries, so runs end together across the warp.
+// Fibres are staged with cp.async rings (S fibres in flight per slot) in VB-byte vectors, VB the
+// widest that both the fibre length and A's base allow. Column copies live in shared memory and
+// are added to Y_k (column-major, J x n_k) with 16-byte vector atomics at the end of an item.
+// Fibres on a 1-, 2- or 4-byte grid take the window-staging kernels of tt_unfold_win.cu instead.
 #include <algorithm>
 
 #include "tt_unfold.cuh"
-
 
 // ---------------------------------------------------------------------------------------------
 // mode 0: row-owner fiber gather
@@ -100,7 +102,6 @@ struct TtVec {
   }
 };
 
-
 static FibreGeom fibre_geom(int64_t fiber_bytes, int VB, int M) {
   FibreGeom g;
   g.fiber_bytes = fiber_bytes;
@@ -147,8 +148,6 @@ __device__ __forceinline__ void cp_async_vec(void* smem, const void* gmem, int b
   else
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem));
 }
-
-
 
 // One work item = a contiguous segment of c groups of one output column (mode 0: of Y_0's
 // rows). The item's fibres are split evenly over the (warp, fibre-slot) pairs; each lane keeps S
@@ -369,7 +368,7 @@ __global__ void __launch_bounds__(256, 2) k_unfold_cols(GArgs a) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = T >> 5;
   unsigned char* ring = smraw;                                                // nw x S x MV x 32 x VB
   float* Ys = reinterpret_cast<float*>(ring + gather_ring_bytes(true, nw, S * MV, VB));  // G x J
-  int* sstart = reinterpret_cast<int*>(Ys + (size_t)G * J);                 // segmax + 1 (relative)
+  int* sstart = reinterpret_cast<int*>(Ys + (size_t)G * (J + TT_YPAD));                 // segmax + 1 (relative)
   int* scval = sstart + a.segmax + 1;                                        // segmax
   const int U_ = *a.ucount;
   const int vpf = a.fg.vpf;
@@ -411,7 +410,7 @@ __global__ void __launch_bounds__(256, 2) k_unfold_cols(GArgs a) {
       sstart[i] = (int)(__ldg(a.ustart + ua + i) - e0);
       if (i < nu) scval[i] = __ldg(a.ulist + ua + i);
     }
-    for (int i = threadIdx.x; i < G * J; i += T) Ys[i] = 0.f;
+    for (int i = threadIdx.x; i < G * (J + TT_YPAD); i += T) Ys[i] = 0.f;
     __syncthreads();
     const int ne = sstart[nu];
     const int sb = (int)((int64_t)ne * warp / nw), se = (int)((int64_t)ne * (warp + 1) / nw);
@@ -442,7 +441,7 @@ __global__ void __launch_bounds__(256, 2) k_unfold_cols(GArgs a) {
 #pragma unroll
         for (int m = 0; m < MV; ++m) {
           if (vok[m]) {
-            float* yc = Ys + (size_t)vg[m] * J;
+            float* yc = Ys + (size_t)vg[m] * (J + TT_YPAD);
 #pragma unroll
             for (int e = 0; e < EPV; ++e) atomicAdd(yc + tt_modj(cv + h0r[m][e], J), coefr[m][e] * acc[m][e]);
           }
@@ -517,7 +516,7 @@ __global__ void __launch_bounds__(256, 2) k_unfold_cols(GArgs a) {
     // flush the G column copies
     for (int g = 0; g < G && col0 + g < a.ncol; ++g) {
       float* yc = a.Y + (int64_t)J * (col0 + g);
-      const float* ys = Ys + (size_t)g * J;
+      const float* ys = Ys + (size_t)g * (J + TT_YPAD);
       if (a.y_vec4) {
         for (int b = threadIdx.x * 4; b < J; b += T * 4) {
           const float4 v4 = make_float4(ys[b], ys[b + 1], ys[b + 2], ys[b + 3]);
@@ -575,7 +574,7 @@ static int launch_cols_s(tt_ctx* c, const void* A, const float* scales, int k, f
   if (c->in_sweep) nseg *= 4;
   a.nseg = tt_unfold_nseg(c, ncolg, nseg);
   a.segmax = (c->J + a.nseg - 1) / a.nseg + 1;
-  const size_t smem = gather_ring_bytes(true, THREADS / 32, S * MV_MAX, VB) + sizeof(float) * (size_t)G * c->J +
+  const size_t smem = gather_ring_bytes(true, THREADS / 32, S * MV_MAX, VB) + sizeof(float) * (size_t)G * (c->J + TT_YPAD) +
                       sizeof(int) * (2 * (size_t)a.segmax + 1);
   if (smem > smax) return TT_OK;
   *done = true;

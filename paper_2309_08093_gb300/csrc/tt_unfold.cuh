@@ -96,6 +96,11 @@ __host__ __device__ constexpr size_t gather_ring_bytes(bool async, int nwarps, i
   return async ? (size_t)nwarps * stages * 32 * vb : 0;
 }
 
+// The G column copies of a multi-column data-sketch item lie J + TT_YPAD floats apart in shared
+// memory, so that the buckets of two columns that one flush instruction touches fall on different
+// banks (the flush adds of a run go to random buckets (c + h_0(i_0)) mod J).
+#define TT_YPAD 8
+
 // c-segments per column unit (column or column group) of a data-sketch launch: `nseg` as chosen
 // for a tensor alone, at most (bytes of A / c->item_bytes) work items in all when the context sets
 // item_bytes, and at least one segment per 2048 c groups (the staged segment's capacity).

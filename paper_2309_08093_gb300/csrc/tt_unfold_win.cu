@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(256, 2) k_unfold_cols_win(GArgs a) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = T >> 5;
   const int g = lane / LPF, posl = lane - g * LPF;
   float* Ys = reinterpret_cast<float*>(smraw + (size_t)nw * S * a.wstage);  // G x J
-  int* sstart = reinterpret_cast<int*>(Ys + (size_t)G * J);                 // segmax + 1 (relative)
+  int* sstart = reinterpret_cast<int*>(Ys + (size_t)G * (J + TT_YPAD));                 // segmax + 1 (relative)
   int* scval = sstart + a.segmax + 1;                                        // segmax
   const int U_ = *a.ucount;
   const int n0 = a.n0;
@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(256, 2) k_unfold_cols_win(GArgs a) {
       sstart[i] = (int)(__ldg(a.ustart + ua + i) - e0);
       if (i < nu) scval[i] = __ldg(a.ulist + ua + i);
     }
-    for (int i = threadIdx.x; i < G * J; i += T) Ys[i] = 0.f;
+    for (int i = threadIdx.x; i < G * (J + TT_YPAD); i += T) Ys[i] = 0.f;
     __syncthreads();
     const int ne = sstart[nu];
     const int sb = (int)((int64_t)ne * warp / nw), se = (int)((int64_t)ne * (warp + 1) / nw);
@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(256, 2) k_unfold_cols_win(GArgs a) {
       auto flush = [&]() {
         const int cv = scval[cu];
         if (colok) {
-          float* yc = Ys + (size_t)g * J;
+          float* yc = Ys + (size_t)g * (J + TT_YPAD);
 #pragma unroll
           for (int t = 0; t < EPT; ++t)
             if (posl + LPF * t < n0) atomicAdd(yc + tt_modj(cv + h0r[t], J), coefr[t] * acc[t]);
@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(256, 2) k_unfold_cols_win(GArgs a) {
     // add the G column copies to Y_k
     for (int gg = 0; gg < G && col0 + gg < a.ncol; ++gg) {
       float* yc = a.Y + (int64_t)J * (col0 + gg);
-      const float* ys = Ys + (size_t)gg * J;
+      const float* ys = Ys + (size_t)gg * (J + TT_YPAD);
       if (a.y_vec4) {
         for (int b = threadIdx.x * 4; b < J; b += T * 4) {
           const float4 v4 = make_float4(ys[b], ys[b + 1], ys[b + 2], ys[b + 3]);
@@ -434,7 +434,7 @@ int cols_win(tt_ctx* c, const void* A, const float* scales, int k, float* Y, boo
   const int ncolg = (a.ncol + G - 1) / G;
   a.nseg = win_nseg(c, k, ncolg, 2 * tt_sm_count());
   a.segmax = (c->J + a.nseg - 1) / a.nseg + 1;
-  const size_t rest = sizeof(float) * (size_t)G * c->J + sizeof(int) * (2 * (size_t)a.segmax + 1);
+  const size_t rest = sizeof(float) * (size_t)G * (c->J + TT_YPAD) + sizeof(int) * (2 * (size_t)a.segmax + 1);
   const size_t smem4 = (size_t)(WIN_THREADS / 32) * 4 * a.wstage + rest;
   const size_t smem2 = (size_t)(WIN_THREADS / 32) * 2 * a.wstage + rest;
   const size_t two_ctas = 113 * 1024;
