@@ -66,7 +66,7 @@ struct TtVec {
     for (int i = 0; i < W; ++i) r.w[i] = 0u;
     return r;
   }
-  // acc[e] += s * element e
+  // acc[e] += s * element e (s = +-1, the sign of a plan entry)
   __device__ static void fma_into(const Raw& r, float s, float* acc) {
     const uint32_t* w = r.w;
     if constexpr (DT == TT_F32 && EPV % 2 == 0) {  // pairs of entries: one fma.rn.f32x2 each
@@ -86,15 +86,10 @@ struct TtVec {
         unsigned long long b = ((unsigned long long)w[2 * e + 1] << 32) | w[2 * e];
         acc[e] = fmaf(s, (float)__longlong_as_double((long long)b), acc[e]);
       }
-    } else if constexpr (DT == TT_BF16) {  // a 32-bit word holds two entries: one fma.rn.f32x2
+    } else if constexpr (DT == TT_BF16) {  // a 32-bit word holds two entries: two mixed BF16 FMAs
+      const unsigned short sb = tt_bf16_sign(s);
 #pragma unroll
-      for (int e = 0; e < EPV; e += 2) {
-        const uint32_t ww = w[e >> 1];
-        const float2 d = tt_ffma2(make_float2(s, s), make_float2(__uint_as_float(ww << 16), __uint_as_float(ww & 0xFFFF0000u)),
-                                  make_float2(acc[e], acc[e + 1]));
-        acc[e] = d.x;
-        acc[e + 1] = d.y;
-      }
+      for (int e = 0; e < EPV; e += 2) tt_fma_bf16x2(w[e >> 1], sb, acc[e], acc[e + 1]);
     } else {
 #pragma unroll
       for (int e = 0; e < EPV; ++e) acc[e] = fmaf(s, tt_fp8_e4m3((w[e >> 2] >> (8 * (e & 3))) & 0xFFu), acc[e]);

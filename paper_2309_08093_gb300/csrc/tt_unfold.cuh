@@ -62,6 +62,23 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
+// acc += s x for a BF16 entry x (raw bits) and a sign s = +-1 (BF16 bits 0x3F80 / 0xBF80): the
+// mixed-precision FMA multiplies exactly and rounds the sum once to FP32, so the result is the
+// bits of fmaf(s, (float)x, acc) without the conversion of x to FP32
+__device__ __forceinline__ float tt_fma_bf16(unsigned short x, unsigned short s, float acc) {
+  asm("fma.rn.f32.bf16 %0, %1, %2, %0;\n" : "+f"(acc) : "h"(x), "h"(s));
+  return acc;
+}
+// the same for the two BF16 entries of a 32-bit word (low half: a0, high half: a1)
+__device__ __forceinline__ void tt_fma_bf16x2(uint32_t w, unsigned short s, float& a0, float& a1) {
+  asm("{\n .reg .b16 lo, hi;\n mov.b32 {lo, hi}, %2;\n fma.rn.f32.bf16 %0, lo, %3, %0;\n"
+      " fma.rn.f32.bf16 %1, hi, %3, %1;\n}\n"
+      : "+f"(a0), "+f"(a1)
+      : "r"(w), "h"(s));
+}
+// BF16 bits of a sign s = +-1
+__device__ __forceinline__ unsigned short tt_bf16_sign(float s) { return s < 0.f ? 0xBF80 : 0x3F80; }
+
 // 16-byte copy global -> shared of `bytes` (1..16) valid source bytes, the rest of the 16
 // destination bytes zero-filled; both addresses 16-byte aligned
 __device__ __forceinline__ void cp_async_16z(void* smem, const void* gmem, int bytes) {

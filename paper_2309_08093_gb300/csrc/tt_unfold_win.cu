@@ -47,11 +47,16 @@ __device__ __forceinline__ int win_m(int cb16, uint32_t word, int fb16) {
   return (cb16 + (int)(((word & 15u) * (uint32_t)fb16) & 15u)) & 15;
 }
 
-// acc[t] += s * entry t of the lane (entry stride lpf * element bytes from p)
+// acc[t] += s * entry t of the lane (entry stride lpf * element bytes from p; s = +-1)
 template <int DT, int LPF, int EPT>
 __device__ __forceinline__ void win_fma(const unsigned char* p, float s, float* acc) {
   constexpr int EB = TtElem<DT>::bytes;
-  if constexpr (DT == TT_F32 && EPT % 2 == 0) {
+  if constexpr (DT == TT_BF16) {
+    const unsigned short sb = tt_bf16_sign(s);
+#pragma unroll
+    for (int t = 0; t < EPT; ++t)
+      acc[t] = tt_fma_bf16(*reinterpret_cast<const unsigned short*>(p + EB * LPF * t), sb, acc[t]);
+  } else if constexpr (DT == TT_F32 && EPT % 2 == 0) {
 #pragma unroll
     for (int t = 0; t < EPT; t += 2) {
       const float2 d = tt_ffma2(make_float2(s, s),
