@@ -151,6 +151,53 @@ def test_unfold_sketch_parity(dims, J, storage):
     ctx.close()
 
 
+@pytest.mark.parametrize("n0", [256, 254])
+def test_fp8_every_finite_code(n0):
+    """Every finite OCP FP8-E4M3 code (all but S.1111.111, the format's NaN) as an entry of the
+    data, with unit scales: the data sketches against the oracle's sketch of the decoded tensor
+    (synth's decode table: subnormals m 2^-9, normals (1 + m/8) 2^(e-7), up to 448). n_0 = 256
+    takes the 16-byte vector kernels (four entries per word), n_0 = 254 window staging."""
+    dims, J = (n0, 5, 3), 512
+    finite = np.array([c for c in range(256) if (c & 0x7F) != 0x7F], np.uint8)
+    rng = np.random.default_rng(n0)
+    codes = finite[(np.arange(int(np.prod(dims))) + rng.integers(0, 254)) % finite.size]
+    exact = synth.fp8_e4m3_decode(codes).reshape(dims, order="F")
+    ctx = lib.Context(dims, (1, 1, 1, 1), J, 1e-3, 31, "fp8")
+    Ad = lib.device_tensor(codes, "fp8")
+    sd = torch.ones(n0, device="cuda")
+    Y = [torch.zeros(J * n, device="cuda") for n in dims]
+    ctx.tt_sketch_unfold(Ad, -1, 0, Y, scales=sd)
+    hs, vs = O.draw_sketch(31, 0, dims, J)
+    for k in range(3):
+        ref = O.sketch_unfolding(exact, hs, vs, J, k)
+        got = Y[k].cpu().numpy().reshape(dims[k], J).T
+        assert rel(got, ref) <= TOL, (k, rel(got, ref))
+    ctx.close()
+
+
+def test_fp8_nan_code_reaches_the_status():
+    """Code 0x7F (S.1111.111, E4M3's NaN) decodes as NaN: a sweep over data holding one returns
+    TT_ENONFINITE with finite cores (the refused update writes nothing); with the code replaced
+    the same context sweeps."""
+    dims, ranks, J = (24, 20, 18), (1, 4, 4, 1), 256
+    a = synth.random_tensor(dims, 5)
+    flat, scales, _ = synth.quantize(a, "fp8")
+    bad = flat.copy()
+    bad[1000] = 0x7F
+    ctx = lib.Context(dims, ranks, J, 1e-3, 9, "fp8")
+    sd = torch.tensor(scales, device="cuda")
+    init = synth.random_tt(dims, ranks, 6)
+    dc = lib.device_cores(init)
+    before = [t.clone() for t in dc]
+    with pytest.raises(lib.TtError) as e:
+        ctx.tt_prox_als_sweep(lib.device_tensor(bad, "fp8"), dc, 1, 0, rel_change=False, scales=sd)
+    assert e.value.code == lib.TT_ENONFINITE
+    for t in dc:
+        assert bool(torch.isfinite(t).all())
+    ctx.tt_prox_als_sweep(lib.device_tensor(flat, "fp8"), dc, 1, 0, rel_change=False, scales=sd)
+    ctx.close()
+
+
 @pytest.mark.parametrize("offset", [1, 3, 4])
 def test_unfold_sketch_offset_base(offset):
     """A tensor that starts `offset` FP32 entries into its allocation: 4 and 12 bytes off the
@@ -528,8 +575,12 @@ def test_sweeps_non_power_of_two_sketch_sizes(dims, ranks, J, nsw):
     amplifies rounding: the FP64 oracle itself moves its result after one sweep by 69x (m = 45)
     and 12x (m = 150) a 1e-7 relative perturbation of the initial cores, and after three sweeps
     by 2.3e5x and 650x. So the order-6 cases take one sweep, and the bound on the reconstructed
-    tensor is 1e-4 plus the oracle's own change under a 1e-6 perturbation (about ten FP32 ulps);
-    the relative error of the GPU's cores keeps 1e-5."""
+    tensor is 1e-4 plus the oracle's own change under two perturbations of the size of the GPU's
+    FP32 rounding: the initial cores by 1e-6 (about ten FP32 ulps), and every entry of the data by
+    eps = 2^-24 log2(N / J) relative: a data-sketch bucket sums about N / J terms as a tree (runs
+    of equal hash in registers, then the runs' sums by atomic adds), whose error is about log2 of
+    the term count in roundings of the bucket's size (8.6e-7 for N = 10^6, J = 45); the relative
+    error of the GPU's cores keeps 1e-5."""
     cores = synth.random_tt(dims, ranks, 3)
     a = synth.add_noise(synth.contract_cores(cores), 1e-2, np.random.default_rng(8))
     flat, _, exact = synth.quantize(a, "f32")
@@ -545,8 +596,10 @@ def test_sweeps_non_power_of_two_sketch_sizes(dims, ranks, J, nsw):
     xi = np.random.default_rng(1)
     pert = [g * (1.0 + 1e-6 * xi.standard_normal(g.shape)) for g in init]
     ref_p, _ = O.tt_ts(exact, pert, 31, J, 1e-3, nsw)
+    eps = 2.0 ** -24 * np.log2(max(2.0, exact.size / J))
+    ref_d, _ = O.tt_ts(exact * (1.0 + eps * xi.standard_normal(exact.shape)), init, 31, J, 1e-3, nsw)
     full_ref = O.tt_full(ref)
-    tol = 1e-4 + rel(O.tt_full(ref_p), full_ref)
+    tol = 1e-4 + rel(O.tt_full(ref_p), full_ref) + rel(O.tt_full(ref_d), full_ref)
     assert rel(O.tt_full(got), full_ref) <= tol, (rel(O.tt_full(got), full_ref), tol)
     e_ref = O.rel_error(exact, [np.asarray(g, np.float32).astype(np.float64) for g in got])
     assert abs(err - e_ref) <= 1e-5 * e_ref, (err, e_ref)
