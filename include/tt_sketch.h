@@ -50,6 +50,8 @@ extern "C" {
 typedef struct tt_ctx tt_ctx; /* opaque, library-owned */
 
 /* storage type of the data tensor A */
+/* TT_FP8E4M3: OCP FP8 E4M3 bytes (bias 7, no infinities, largest finite 448); the code S.1111.111
+ * is the format's NaN and reaches a solve as a non-finite value (TT_ENONFINITE) */
 enum { TT_F64 = 0, TT_F32 = 1, TT_BF16 = 2, TT_FP8E4M3 = 3 };
 
 /* status codes */

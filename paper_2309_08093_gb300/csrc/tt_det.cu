@@ -32,12 +32,7 @@ __device__ __forceinline__ float det_load(const void* A, int64_t i) {
   if constexpr (DT == TT_F64) return (float)__ldg((const double*)A + i);
   else if constexpr (DT == TT_F32) return __ldg((const float*)A + i);
   else if constexpr (DT == TT_BF16) return __uint_as_float(((uint32_t)__ldg((const unsigned short*)A + i)) << 16);
-  else {
-    const uint32_t c = __ldg((const unsigned char*)A + i);
-    const uint32_t s = (c & 0x80u) << 24, e = (c >> 3) & 0xFu, m = c & 7u;
-    const float mag = e ? __uint_as_float(((e + 120u) << 23) | (m << 20)) : (float)m * 0.001953125f;  // 2^-9
-    return __uint_as_float(__float_as_uint(mag) | s);
-  }
+  else return tt_e4m3_to_float(__ldg((const unsigned char*)A + i));
 }
 
 // |A(i)| with the FP8 slice scale applied (the value the sketch adds)

@@ -41,6 +41,18 @@ size_t tt_trsm64_smem(int s, int nc);   // and of its triangular solves, nc righ
 __host__ __device__ __forceinline__ int tt_modj(int x, int J) { return x >= J ? x - J : x; }
 #define TT_MAX_N 65536    // largest single mode size
 
+// OCP FP8 E4M3 byte (low 8 bits of c) -> float: the hardware conversion to FP16 (exact: every E4M3
+// value is an FP16 value; the format's NaN code S.1111.111 gives NaN), then FP16 -> FP32 (exact)
+__device__ __forceinline__ float tt_e4m3_to_float(uint32_t c) {
+  const unsigned short x = (unsigned short)(c & 0xFFu);
+  float f;
+  asm("{\n .reg .b32 h;\n .reg .b16 lo, hi;\n cvt.rn.f16x2.e4m3x2 h, %1;\n mov.b32 {lo, hi}, h;\n"
+      " cvt.f32.f16 %0, lo;\n}\n"
+      : "=f"(f)
+      : "h"(x));
+  return f;
+}
+
 struct TtPlan0;
 
 // The hash / sign tables and fibre plans of one sketch draw. A context holds two: the current draw

@@ -1424,12 +1424,7 @@ __device__ __forceinline__ float err_elem(const void* A, int64_t idx) {
   if constexpr (DT == TT_F64) return (float)__ldg((const double*)A + idx);
   if constexpr (DT == TT_F32) return __ldg((const float*)A + idx);
   if constexpr (DT == TT_BF16) return __uint_as_float(((uint32_t)__ldg((const unsigned short*)A + idx)) << 16);
-  if constexpr (DT == TT_FP8E4M3) {
-    uint32_t cc = __ldg((const unsigned char*)A + idx);
-    uint32_t sg = (cc & 0x80u) << 24, e = (cc >> 3) & 0xFu, mm = cc & 7u;
-    float mag = e ? __uint_as_float(((e + 120u) << 23) | (mm << 20)) : (float)mm * 0.001953125f;
-    return __uint_as_float(__float_as_uint(mag) | sg);
-  }
+  if constexpr (DT == TT_FP8E4M3) return tt_e4m3_to_float(__ldg((const unsigned char*)A + idx));
   return 0.f;
 }
 
@@ -1450,12 +1445,7 @@ __device__ __forceinline__ void err_load4(const void* A, int64_t idx, float* x) 
   } else {
     const uint32_t v = __ldg(reinterpret_cast<const uint32_t*>(A) + idx / 4);
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const uint32_t cc = (v >> (8 * c)) & 0xFFu;
-      const uint32_t sg = (cc & 0x80u) << 24, e = (cc >> 3) & 0xFu, mm = cc & 7u;
-      const float mag = e ? __uint_as_float(((e + 120u) << 23) | (mm << 20)) : (float)mm * 0.001953125f;
-      x[c] = __uint_as_float(__float_as_uint(mag) | sg);
-    }
+    for (int c = 0; c < 4; ++c) x[c] = tt_e4m3_to_float(v >> (8 * c));
   }
 }
 
@@ -1782,12 +1772,7 @@ __device__ __forceinline__ void smem_load4(const unsigned char* p, float* x) {
   } else {
     const uint32_t v = *reinterpret_cast<const uint32_t*>(p);
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const uint32_t cc = (v >> (8 * c)) & 0xFFu;
-      const uint32_t sg = (cc & 0x80u) << 24, e = (cc >> 3) & 0xFu, mm = cc & 7u;
-      const float mag = e ? __uint_as_float(((e + 120u) << 23) | (mm << 20)) : (float)mm * 0.001953125f;
-      x[c] = __uint_as_float(__float_as_uint(mag) | sg);
-    }
+    for (int c = 0; c < 4; ++c) x[c] = tt_e4m3_to_float(v >> (8 * c));
   }
 }
 

@@ -90,9 +90,14 @@ struct TtVec {
       const unsigned short sb = tt_bf16_sign(s);
 #pragma unroll
       for (int e = 0; e < EPV; e += 2) tt_fma_bf16x2(w[e >> 1], sb, acc[e], acc[e + 1]);
-    } else {
+    } else if constexpr (EPV % 4 == 0) {  // FP8: four entries per word, hardware conversions
+      const unsigned short sh = tt_f16_sign(s);
 #pragma unroll
-      for (int e = 0; e < EPV; ++e) acc[e] = fmaf(s, tt_fp8_e4m3((w[e >> 2] >> (8 * (e & 3))) & 0xFFu), acc[e]);
+      for (int e = 0; e < EPV; e += 4) tt_fma_e4m3x4(w[e >> 2], sh, acc[e], acc[e + 1], acc[e + 2], acc[e + 3]);
+    } else {
+      const unsigned short sh = tt_f16_sign(s);
+#pragma unroll
+      for (int e = 0; e < EPV; ++e) acc[e] = tt_fma_e4m3((unsigned short)((w[e >> 2] >> (8 * (e & 3))) & 0xFFu), sh, acc[e]);
     }
   }
 };

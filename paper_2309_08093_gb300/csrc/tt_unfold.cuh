@@ -33,14 +33,8 @@ struct TtElem<TT_BF16> {
   }
 };
 
-// OCP FP8 E4M3 (bias 7, no infinities): decode from the bit fields.
-__device__ __forceinline__ float tt_fp8_e4m3(uint32_t c) {
-  uint32_t s = (c & 0x80u) << 24;
-  uint32_t e = (c >> 3) & 0xFu;
-  uint32_t m = c & 7u;
-  float mag = e ? __uint_as_float(((e + 120u) << 23) | (m << 20)) : (float)m * 0.001953125f;  // 2^-9
-  return __uint_as_float(__float_as_uint(mag) | s);
-}
+// OCP FP8 E4M3 (bias 7, no infinities, S.1111.111 NaN)
+__device__ __forceinline__ float tt_fp8_e4m3(uint32_t c) { return tt_e4m3_to_float(c); }
 template <>
 struct TtElem<TT_FP8E4M3> {
   using T = unsigned char;
@@ -78,6 +72,30 @@ __device__ __forceinline__ void tt_fma_bf16x2(uint32_t w, unsigned short s, floa
 }
 // BF16 bits of a sign s = +-1
 __device__ __forceinline__ unsigned short tt_bf16_sign(float s) { return s < 0.f ? 0xBF80 : 0x3F80; }
+
+// acc_j += s x_j for the four E4M3 entries of a 32-bit word (byte j = entry j) and a sign s = +-1
+// (FP16 bits 0x3C00 / 0xBC00): two hardware conversions of two entries each to FP16 (exact), then
+// mixed-precision FMAs (exact product, one rounding to FP32): the bits of fmaf(s, decoded, acc)
+__device__ __forceinline__ void tt_fma_e4m3x4(uint32_t w, unsigned short s, float& a0, float& a1, float& a2,
+                                              float& a3) {
+  asm("{\n .reg .b16 p0, p1, q0, q1, q2, q3;\n .reg .b32 h01, h23;\n mov.b32 {p0, p1}, %4;\n"
+      " cvt.rn.f16x2.e4m3x2 h01, p0;\n cvt.rn.f16x2.e4m3x2 h23, p1;\n"
+      " mov.b32 {q0, q1}, h01;\n mov.b32 {q2, q3}, h23;\n"
+      " fma.rn.f32.f16 %0, q0, %5, %0;\n fma.rn.f32.f16 %1, q1, %5, %1;\n"
+      " fma.rn.f32.f16 %2, q2, %5, %2;\n fma.rn.f32.f16 %3, q3, %5, %3;\n}\n"
+      : "+f"(a0), "+f"(a1), "+f"(a2), "+f"(a3)
+      : "r"(w), "h"(s));
+}
+// the same for one E4M3 entry (low byte of x)
+__device__ __forceinline__ float tt_fma_e4m3(unsigned short x, unsigned short s, float acc) {
+  asm("{\n .reg .b32 h;\n .reg .b16 lo, hi;\n cvt.rn.f16x2.e4m3x2 h, %1;\n mov.b32 {lo, hi}, h;\n"
+      " fma.rn.f32.f16 %0, lo, %2, %0;\n}\n"
+      : "+f"(acc)
+      : "h"(x), "h"(s));
+  return acc;
+}
+// FP16 bits of a sign s = +-1
+__device__ __forceinline__ unsigned short tt_f16_sign(float s) { return s < 0.f ? 0xBC00 : 0x3C00; }
 
 // 16-byte copy global -> shared of `bytes` (1..16) valid source bytes, the rest of the 16
 // destination bytes zero-filled; both addresses 16-byte aligned

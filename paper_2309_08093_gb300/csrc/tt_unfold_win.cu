@@ -56,6 +56,10 @@ __device__ __forceinline__ void win_fma(const unsigned char* p, float s, float* 
 #pragma unroll
     for (int t = 0; t < EPT; ++t)
       acc[t] = tt_fma_bf16(*reinterpret_cast<const unsigned short*>(p + EB * LPF * t), sb, acc[t]);
+  } else if constexpr (DT == TT_FP8E4M3) {
+    const unsigned short sh = tt_f16_sign(s);
+#pragma unroll
+    for (int t = 0; t < EPT; ++t) acc[t] = tt_fma_e4m3(*(p + EB * LPF * t), sh, acc[t]);
   } else if constexpr (DT == TT_F32 && EPT % 2 == 0) {
 #pragma unroll
     for (int t = 0; t < EPT; t += 2) {
