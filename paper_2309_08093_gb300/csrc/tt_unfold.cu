@@ -368,7 +368,7 @@ __global__ void __launch_bounds__(256, 2) k_unfold_cols(GArgs a) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = T >> 5;
   unsigned char* ring = smraw;                                                // nw x S x MV x 32 x VB
   float* Ys = reinterpret_cast<float*>(ring + gather_ring_bytes(true, nw, S * MV, VB));  // G x J
-  int* sstart = reinterpret_cast<int*>(Ys + (size_t)G * (J + TT_YPAD));                 // segmax + 1 (relative)
+  int* sstart = reinterpret_cast<int*>(Ys + (size_t)G * (J + TT_YPAD));  // segmax + 1 (relative)
   int* scval = sstart + a.segmax + 1;                                        // segmax
   const int U_ = *a.ucount;
   const int vpf = a.fg.vpf;

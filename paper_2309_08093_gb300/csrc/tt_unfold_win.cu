@@ -107,8 +107,8 @@ __global__ void __launch_bounds__(256, 2) k_unfold_cols_win(GArgs a) {
   const int J = a.J, T = blockDim.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = T >> 5;
   const int g = lane / LPF, posl = lane - g * LPF;
-  float* Ys = reinterpret_cast<float*>(smraw + (size_t)nw * S * a.wstage);  // G x J
-  int* sstart = reinterpret_cast<int*>(Ys + (size_t)G * (J + TT_YPAD));                 // segmax + 1 (relative)
+  float* Ys = reinterpret_cast<float*>(smraw + (size_t)nw * S * a.wstage);  // G x (J + TT_YPAD)
+  int* sstart = reinterpret_cast<int*>(Ys + (size_t)G * (J + TT_YPAD));  // segmax + 1 (relative)
   int* scval = sstart + a.segmax + 1;                                        // segmax
   const int U_ = *a.ucount;
   const int n0 = a.n0;
