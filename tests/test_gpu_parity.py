@@ -605,6 +605,41 @@ def test_sweeps_non_power_of_two_sketch_sizes(dims, ranks, J, nsw):
     assert abs(err - e_ref) <= 1e-5 * e_ref, (err, e_ref)
 
 
+@pytest.mark.parametrize("dims,ranks,J", [
+    ((3, 4, 2, 3, 2, 3, 2, 4), (1, 2, 2, 2, 2, 2, 2, 2, 1), 64),  # order 8, the largest
+    ((50, 40), (1, 6, 1), 128),                                  # order 2, the smallest
+    ((40000, 3, 2), (1, 1, 1, 1), 256),  # the largest mode size a core allows (r n r' <= 40000), first
+    ((3, 40000, 2), (1, 1, 1, 1), 256),  # ... and inner (40,000 output columns; 12-byte fibres)
+])
+def test_extreme_shapes(dims, ranks, J):
+    """The limits of the context: every mode's data sketch against the oracle (1e-5), then two
+    sweeps against the oracle's (reconstruction 1e-4) and the relative error of the GPU's cores
+    (1e-5)."""
+    seed = 60 + len(dims) + J
+    cores = synth.random_tt(dims, ranks, seed)
+    a = synth.add_noise(synth.contract_cores(cores), 1e-2, np.random.default_rng(seed + 1))
+    flat, _, exact = synth.quantize(a, "f32")
+    ctx = lib.Context(dims, ranks, J, 1e-3, seed, "f32")
+    A = lib.device_tensor(flat, "f32")
+    Y = [torch.zeros(J * n, device="cuda") for n in dims]
+    ctx.tt_sketch_unfold(A, -1, 0, Y)
+    hs, vs = O.draw_sketch(seed, 0, dims, J)
+    for k in range(len(dims)):
+        ref = O.sketch_unfolding(exact, hs, vs, J, k)
+        got = Y[k].cpu().numpy().reshape(dims[k], J).T
+        assert rel(got, ref) <= TOL, (k, rel(got, ref))
+    init = synth.random_tt(dims, ranks, seed + 2)
+    dc = lib.device_cores(init)
+    ctx.tt_prox_als_sweep(A, dc, 2, 0, rel_change=False)
+    err = ctx.tt_rel_error(A, dc)
+    got = lib.host_cores(dc, ranks, dims)
+    ctx.close()
+    ref, _ = O.tt_ts(exact, init, seed, J, 1e-3, 2)
+    assert rel(O.tt_full(got), O.tt_full(ref)) <= 1e-4, rel(O.tt_full(got), O.tt_full(ref))
+    e_ref = O.rel_error(exact, [np.asarray(g, np.float32).astype(np.float64) for g in got])
+    assert abs(err - e_ref) <= 1e-5 * e_ref, (err, e_ref)
+
+
 def test_sweeps_with_large_cores():
     """Cores with r_k r_{k+1} = 180 > 160 unknowns (the Cholesky solve) in whole sweeps: the
     tensor after two sweeps against the oracle's (1e-4) and its relative error (1e-5)."""
