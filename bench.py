@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--no-patterns", action="store_true", help="skip the precision/batched/warm-start patterns")
     ap.add_argument("--only-pattern", default=None,
                     choices=["precision", "batched", "warmstart", "gemm", "sparse", "order3", "order5",
-                             "deterministic", "gram", "window"],
+                             "deterministic", "gram", "window", "fixed"],
                     help="run one pattern and print its JSON")
     ap.add_argument("--ws-train", type=int, default=10240, help="warm-start training solves")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
@@ -416,6 +416,39 @@ def gram_pattern(w, p, dev, nsweeps=20):
     return {"sweeps": nsweeps, "forms": out,
             "note": "sweeps only (no relative error inside the timed region), CUDA events, after 3 warm-up "
                     "sweeps from the workload's initial cores"}
+
+
+# ---------------------------------------------------------------------------------------------
+# fixed draw: the sketches drawn once (TT_FLAG_FIXED_SKETCH) instead of once per sweep (Alg. 1 as
+# written); the data sketches then depend on A alone and a call computes them in its first sweep
+
+def fixed_sketch_pattern(w, p, dev, nsweeps=20):
+    import torch
+    from paper_2309_08093_gb300 import lib
+
+    stream = torch.cuda.current_stream()
+    A = lib.device_tensor(p.storage, "f32", device=dev)
+    out = {}
+    for name, flags in (("redraw_per_sweep", 0), ("fixed_draw", lib.TT_FLAG_FIXED_SKETCH)):
+        ctx = lib.Context(w.dims, p.ranks, w.J, w.lam, p.sketch_seed, "f32", flags=flags)
+        cores = lib.device_cores(p.init_cores, device=dev)
+        warm = lib.device_cores(p.init_cores, device=dev)
+        ctx.tt_prox_als_sweep(A, warm, 3, 0, rel_change=False)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.tt_prox_als_sweep(A, cores, nsweeps, 0, rel_change=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / nsweeps
+        errs, _ = ctx.tt_prox_als_sweep_monitored(A, lib.device_cores(p.init_cores, device=dev), nsweeps, 0)
+        out[name] = {"ms_per_sweep": ms, "sweeps_per_s": 1e3 / ms, "rel_error_after": ctx.tt_rel_error(A, cores),
+                     "rel_error_per_sweep": [float(e) for e in errs]}
+        ctx.close()
+    return {"sweeps": nsweeps, "forms": out,
+            "note": f"one call of {nsweeps} sweeps from the workload's initial cores, CUDA events (no relative "
+                    "error inside the timed call); with the fixed draw the call's first sweep computes the data "
+                    "sketches and the later sweeps reuse them; errors per sweep from a second, monitored call"}
 
 
 # ---------------------------------------------------------------------------------------------
@@ -846,6 +879,9 @@ def main():
             out = gram_pattern(w, synth.make_problem(w, storage="f32"), dev)
         elif args.only_pattern == "window":
             out = window_pattern(dev)
+        elif args.only_pattern == "fixed":
+            w = synth.WORKLOADS[args.workload]
+            out = fixed_sketch_pattern(w, synth.make_problem(w, storage="f32"), dev)
         elif args.only_pattern == "deterministic":
             w = synth.WORKLOADS[args.workload]
             out = deterministic_pattern(w, synth.make_problem(w, storage="f32"), dev)
@@ -1012,6 +1048,7 @@ def main():
         line["patterns"]["gram"] = gram_pattern(w, p, dev)
         torch.cuda.empty_cache()
         line["patterns"]["window"] = window_pattern(dev)
+        line["patterns"]["fixed"] = fixed_sketch_pattern(w, p, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
             res = run_cpu_child(["--workload", args.workload] + (["--storage", args.storage] if args.storage else []))

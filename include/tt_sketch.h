@@ -66,7 +66,9 @@ enum {
 };
 
 /* flags */
-#define TT_FLAG_FIXED_SKETCH 1u /* draw h_k, v_k once (t = 0) instead of once per sweep */
+/* draw h_k, v_k once (t = 0) instead of once per sweep; the data sketches then depend on A alone,
+ * and a multi-sweep call computes them in its first sweep and reuses them in the others */
+#define TT_FLAG_FIXED_SKETCH 1u
 #define TT_FLAG_FP64_SOLVE 2u   /* solve Eq. (ite) in FP64 also when sigma > 0 (see tt_prox_update) */
 /* Fixed summation orders: repeated calls on the same inputs return the same bits (data sketches,
  * interface sketches, updated cores, relative errors and rel-changes of the dense-tensor calls).

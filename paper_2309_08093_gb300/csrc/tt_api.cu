@@ -121,7 +121,10 @@ static int sweep_body(tt_ctx* c, const void* A, const float* scales, float* cons
   // stream (plans built there too) and run concurrently with the orthogonalisation, interface
   // and solve kernels below, which use few SMs; core k's update waits only for Y_k.
   const bool fork = Ygiven == nullptr;
-  if (fork) {
+  // a fixed draw: the data sketches depend on A alone, so the call's first sweep computes them and
+  // its later sweeps reuse them (the chain's waits on the Y_k events of that sweep are met)
+  const bool fixed_draw = ((c->flags & TT_FLAG_FIXED_SKETCH) != 0 || c->user_tables) && !c->capture_mode;
+  if (fork && !c->y_reuse) {
     TT_CUDA(c, cudaEventRecord(c->ev_fork, c->stream));
     TT_CUDA(c, cudaStreamWaitEvent(c->side, c->ev_fork, 0));
     cudaStream_t main_stream = c->stream;
@@ -146,6 +149,7 @@ static int sweep_body(tt_ctx* c, const void* A, const float* scales, float* cons
     }
     c->stream = main_stream;
     c->in_sweep = false;
+    if (rc == TT_OK && fixed_draw) c->y_reuse = true;
     // the next sweep's draw and plans, behind this sweep's data sketches on the side stream (not
     // joined: it overlaps the rest of this sweep and whatever the caller does next)
     if (rc == TT_OK) rc = tt_prepare_next_draw(c, sweep + 1);
@@ -213,8 +217,19 @@ extern "C" int tt_prox_als_sweep_sketched(tt_ctx* c, float* const* Y, float* con
 
 // nsweeps outer iterations; per sweep (optional) the rel-change and the relative error of the
 // updated cores, copied back in blocks of changes_cap / d sweeps with one synchronisation each.
+static int run_sweeps_body(tt_ctx* c, const void* A, const float* scales, float* const* cores, int nsweeps,
+                           uint64_t first_sweep, double* rel_change_out, double* rel_error_out);
+
 static int run_sweeps(tt_ctx* c, const void* A, const float* scales, float* const* cores, int nsweeps,
                       uint64_t first_sweep, double* rel_change_out, double* rel_error_out) {
+  c->y_reuse = false;  // data sketches are reused within one call only (A may change between calls)
+  const int rc = run_sweeps_body(c, A, scales, cores, nsweeps, first_sweep, rel_change_out, rel_error_out);
+  c->y_reuse = false;
+  return rc;
+}
+
+static int run_sweeps_body(tt_ctx* c, const void* A, const float* scales, float* const* cores, int nsweeps,
+                           uint64_t first_sweep, double* rel_change_out, double* rel_error_out) {
   TT_TRY(tt_reset_status(c));
   const int per_block = c->changes_cap / c->d;
   std::vector<double> host, herr;

@@ -179,6 +179,11 @@ struct tt_ctx {
   bool capture_mode = false;
   const uint64_t* d_sweep_ptr = nullptr;
 
+  // The data sketches in d_Yall are those of the A of the running multi-sweep call under a draw
+  // that does not change from sweep to sweep (TT_FLAG_FIXED_SKETCH or tables set by the caller):
+  // later sweeps of the call reuse them. Cleared at the start and the end of every call.
+  bool y_reuse = false;
+
   // least bytes of A per work item of a data-sketch launch (0: items sized for one tensor alone,
   // about one per CTA slot). Contexts of a batch set it, so that a small tensor's launch takes few
   // CTAs and the launches of the batch's other tensors run beside it.

@@ -640,6 +640,43 @@ def test_extreme_shapes(dims, ranks, J):
     assert abs(err - e_ref) <= 1e-5 * e_ref, (err, e_ref)
 
 
+def test_fixed_sketch_reuses_the_data_sketches_within_a_call():
+    """With TT_FLAG_FIXED_SKETCH every sweep uses sweep 0's draw, so the data sketches depend on A
+    alone: a call's first sweep computes them (d launches) and its later sweeps reuse them. Four
+    sweeps against the oracle's four sweeps with sweep 0's draw (reconstruction 1e-4, relative
+    error 1e-5); the launch count shows the reuse; a second call on other data recomputes them
+    (a stale reuse would give the first tensor's sweeps)."""
+    dims, ranks, J, lam, seed = (24, 20, 18, 16), (1, 4, 5, 4, 1), 512, 1e-3, 57
+    probs = []
+    for s0 in (1, 2):
+        cores = synth.random_tt(dims, ranks, 10 * s0)
+        a = synth.add_noise(synth.contract_cores(cores), 1e-2, np.random.default_rng(10 * s0 + 1))
+        flat, _, exact = synth.quantize(a, "f32")
+        probs.append((lib.device_tensor(flat, "f32"), exact))
+    init = synth.random_tt(dims, ranks, 33)
+    ctx = lib.Context(dims, ranks, J, lam, seed, "f32", flags=lib.TT_FLAG_FIXED_SKETCH)
+    dc = lib.device_cores(init)
+    ctx.tt_profile_enable(True)
+    ctx.tt_prox_als_sweep(probs[0][0], dc, 4, 7, rel_change=False)
+    launches = ctx.tt_profile_read()["unfold_launches"]
+    ctx.tt_profile_enable(False)
+    assert launches == len(dims), launches
+    ref = [np.asarray(g, np.float64) for g in init]
+    for _ in range(4):
+        ref, _ = O.tt_ts_sweep(probs[0][1], ref, seed, 0, J, lam)
+    got = lib.host_cores(dc, ranks, dims)
+    assert rel(O.tt_full(got), O.tt_full(ref)) <= 1e-4, rel(O.tt_full(got), O.tt_full(ref))
+    err = ctx.tt_rel_error(probs[0][0], dc)
+    e_ref = O.rel_error(probs[0][1], [np.asarray(g, np.float32).astype(np.float64) for g in got])
+    assert abs(err - e_ref) <= 1e-5 * e_ref, (err, e_ref)
+    ctx.tt_prox_als_sweep(probs[1][0], dc, 2, 0, rel_change=False)  # the second tensor
+    for _ in range(2):
+        ref, _ = O.tt_ts_sweep(probs[1][1], ref, seed, 0, J, lam)
+    got = lib.host_cores(dc, ranks, dims)
+    ctx.close()
+    assert rel(O.tt_full(got), O.tt_full(ref)) <= 1e-4, rel(O.tt_full(got), O.tt_full(ref))
+
+
 def test_sweeps_with_large_cores():
     """Cores with r_k r_{k+1} = 180 > 160 unknowns (the Cholesky solve) in whole sweeps: the
     tensor after two sweeps against the oracle's (1e-4) and its relative error (1e-5)."""
