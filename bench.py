@@ -338,10 +338,11 @@ def batched_pattern(dev, nsweeps=10, count=256):
     from paper_2309_08093_gb300 import lib, synth
 
     specs = synth.batched_specs(count=count)
-    As, cores = [], []
+    As, cores, inits = [], [], []
     for sp in specs:
         a, init = synth.batched_tensor_gpu(sp, device=dev)
         As.append(a)
+        inits.append(init)
         cores.append(lib.device_cores(init, device=dev))
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
@@ -357,6 +358,20 @@ def batched_pattern(dev, nsweeps=10, count=256):
     ms = e0.elapsed_time(e1)
     errs = batch.tt_batch_rel_error(As, cores)
     batch.close()
+    # the same sweeps with a fixed draw per tensor (TT_FLAG_FIXED_SKETCH): a call's first sweep
+    # computes the data sketches, its later sweeps reuse them (a second graph)
+    batch_f = lib.Batch([dict(sp, flags=lib.TT_FLAG_FIXED_SKETCH) for sp in specs])
+    cores_f = [lib.device_cores(init, device=dev) for init in inits]
+    batch_f.tt_batch_sweep(As, cores_f, 1, 0)    # capture + first sweep
+    torch.cuda.synchronize()
+    e0.record(stream)
+    batch_f.tt_batch_sweep(As, cores_f, nsweeps, 1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_f = e0.elapsed_time(e1)
+    errs_f = sorted(batch_f.tt_batch_rel_error(As, cores_f))
+    batch_f.close()
+    del cores_f
     # the same sweeps one tensor at a time (a context per tensor, its own launches, no graph)
     ctxs = [lib.Context(sp["dims"], sp["ranks"], sp["J"], sp["lam"], sp["seed"], sp["dtype"]) for sp in specs]
     for c, a, cs in zip(ctxs, As, cores):
@@ -383,6 +398,10 @@ def batched_pattern(dev, nsweeps=10, count=256):
             "unfold_read_gbs_lower_bound": unfold_bytes / sweep_s / 1e9,
             "setup_s": setup_s,
             "rel_error_median": errs_sorted[len(errs) // 2], "rel_error_max": errs_sorted[-1],
+            "fixed_draw": {"ms_per_batched_sweep": ms_f / nsweeps, "tensor_sweeps_per_s": count / (ms_f / 1e3 / nsweeps),
+                           "rel_error_median": errs_f[len(errs_f) // 2], "rel_error_max": errs_f[-1],
+                           "note": f"TT_FLAG_FIXED_SKETCH on every tensor; one call of {nsweeps} sweeps: the first "
+                                   "computes the data sketches, the others reuse them"},
             "note": "noise 1e-3 (the floor); sweeps timed with CUDA events around one tt_batch_sweep call "
                     "(graph replays); unfold GB/s = tensor bytes x order / sweep time, everything else in "
                     "the sweep included"}

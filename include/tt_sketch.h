@@ -338,7 +338,8 @@ int tt_prox_update_noalloc(const float* Y_dev, const float* SH_dev, float* core_
  * array itself may be NULL when no tensor is FP8), cores_dev[i] (host array of params[i].d device
  * core pointers, updated in place). One sweep of all tensors is captured once into a CUDA graph
  * (tensors spread over the stream pool, forked from and joined to `cuda_stream`) and replayed
- * with one graph launch per sweep; the graph is recaptured when any pointer changes. With
+ * with one graph launch per sweep; the graph is recaptured when any pointer changes. Tensors with
+ * TT_FLAG_FIXED_SKETCH compute their data sketches in a call's first sweep only. With
  * TT_FLAG_BATCH_AUTOTUNE in a tensor's flags the first call also times that tensor's data-sketch
  * launch shapes on its own data and keeps the fastest. Sweep t of the call uses
  * hash draw first_sweep + t (or 0 with TT_FLAG_FIXED_SKETCH). Synchronises `cuda_stream`;

@@ -1,8 +1,11 @@
 // Batched driver: many independent tensors (each with its own shape, ranks and sketch size) swept
-// together. One sweep of Algorithm 1 for every tensor is captured once into a CUDA graph -- tensor
-// i runs on stream i mod S of a stream pool (S = 64), forked from and joined to the caller's stream -- and
-// every later sweep is a single cudaGraphLaunch. The sweep index lives in a device counter that the
-// graph increments, so each replay draws the next sketch (Alg. 1 redraws S_k per outer iteration).
+// together. One sweep of Algorithm 1 for every tensor is captured once into a CUDA graph (tensor i
+// runs on stream i mod S of a stream pool, S = 64, forked from and joined to the caller's stream),
+// and every later sweep is a single cudaGraphLaunch. The sweep index lives in a device counter that
+// the graph increments, so each replay draws the next sketch (Alg. 1 redraws S_k per outer
+// iteration). Tensors with a fixed draw (TT_FLAG_FIXED_SKETCH) also get a second graph, replayed
+// for a call's sweeps after its first, in which they reuse the data sketches that the first sweep
+// left in their contexts.
 // The data-sketch launches of a batched tensor size their work items by its bytes
 // (TT_BATCH_ITEM_BYTES), so that a small tensor's launch takes few CTAs and those of other tensors
 // run beside it. With TT_FLAG_BATCH_AUTOTUNE an autotuner times, per mode and on the tensor's own
@@ -27,12 +30,18 @@ struct tt_batch {
   uint64_t* d_sweep = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  // the sweeps after a call's first when some tensors have a fixed draw (their data sketches
+  // reused); null otherwise
+  cudaGraph_t graph_reuse = nullptr;
+  cudaGraphExec_t exec_reuse = nullptr;
   std::vector<const void*> capA;
   std::vector<const float*> capS;
   std::vector<float*> capC;  // flattened core pointers
   bool tuned = false;
   std::string err;
 };
+
+static void free_graphs(tt_batch* b);
 
 static int bfail(tt_batch* b, int code, const char* msg) {
   if (b) b->err = msg;
@@ -85,8 +94,7 @@ extern "C" void tt_batch_destroy(tt_batch* b) {
   if (!b) return;
   if (b->main) cudaStreamSynchronize(b->main);
   for (auto s : b->streams) cudaStreamSynchronize(s);
-  if (b->exec) cudaGraphExecDestroy(b->exec);
-  if (b->graph) cudaGraphDestroy(b->graph);
+  free_graphs(b);
   for (auto c : b->ctx) tt_sketch_destroy(c);
   for (auto ev : b->ev_join) cudaEventDestroy(ev);
   if (b->ev_fork) cudaEventDestroy(b->ev_fork);
@@ -154,15 +162,11 @@ static int autotune(tt_batch* b, const void* const* A, const float* const* S) {
   return TT_OK;
 }
 
-static int capture(tt_batch* b, const void* const* A, const float* const* S, float* const* const* C) {
-  if (b->exec) {
-    cudaGraphExecDestroy(b->exec);
-    b->exec = nullptr;
-  }
-  if (b->graph) {
-    cudaGraphDestroy(b->graph);
-    b->graph = nullptr;
-  }
+// Capture one sweep of every tensor into a graph. reuse: tensors with a fixed draw
+// (TT_FLAG_FIXED_SKETCH) run their sweep on the data sketches left in their context by the sweep
+// before (the first graph's), without the data-sketch launches.
+static int capture_graph(tt_batch* b, const void* const* A, const float* const* S, float* const* const* C,
+                         bool reuse, cudaGraph_t* g_out, cudaGraphExec_t* x_out) {
   cudaError_t e = cudaStreamBeginCapture(b->main, cudaStreamCaptureModeRelaxed);
   if (e != cudaSuccess) return bfail(b, TT_ECUDA, cudaGetErrorString(e));
   int rc = TT_OK;
@@ -171,7 +175,13 @@ static int capture(tt_batch* b, const void* const* A, const float* const* S, flo
   for (int i = 0; i < b->count && e == cudaSuccess && rc == TT_OK; ++i) {
     tt_ctx* c = b->ctx[i];
     c->capture_mode = true;
-    rc = tt_one_sweep(c, A[i], S ? S[i] : nullptr, C[i], 0, nullptr);
+    if (reuse && (c->flags & TT_FLAG_FIXED_SKETCH)) {
+      float* ys[TT_MAX_D];
+      for (int k = 0; k < c->d; ++k) ys[k] = c->d_Yall + c->yoff[k];
+      rc = tt_one_sweep(c, A[i], S ? S[i] : nullptr, C[i], 0, nullptr, ys);
+    } else {
+      rc = tt_one_sweep(c, A[i], S ? S[i] : nullptr, C[i], 0, nullptr);
+    }
     c->capture_mode = false;
     if (rc) b->err = c->err;
   }
@@ -194,9 +204,27 @@ static int capture(tt_batch* b, const void* const* A, const float* const* S, flo
     if (g) cudaGraphDestroy(g);
     return bfail(b, TT_ECUDA, cudaGetErrorString(e));
   }
-  b->graph = g;
-  e = cudaGraphInstantiate(&b->exec, g, 0);
+  *g_out = g;
+  e = cudaGraphInstantiate(x_out, g, 0);
   if (e != cudaSuccess) return bfail(b, TT_ECUDA, cudaGetErrorString(e));
+  return TT_OK;
+}
+
+static void free_graphs(tt_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->exec_reuse) cudaGraphExecDestroy(b->exec_reuse);
+  if (b->graph_reuse) cudaGraphDestroy(b->graph_reuse);
+  b->exec = b->exec_reuse = nullptr;
+  b->graph = b->graph_reuse = nullptr;
+}
+
+static int capture(tt_batch* b, const void* const* A, const float* const* S, float* const* const* C) {
+  free_graphs(b);
+  TT_TRY(capture_graph(b, A, S, C, false, &b->graph, &b->exec));
+  bool any_fixed = false;
+  for (auto c : b->ctx) any_fixed = any_fixed || (c->flags & TT_FLAG_FIXED_SKETCH) != 0;
+  if (any_fixed) TT_TRY(capture_graph(b, A, S, C, true, &b->graph_reuse, &b->exec_reuse));
   b->capA.assign(A, A + b->count);
   b->capS.assign(b->count, nullptr);
   if (S)
@@ -253,7 +281,10 @@ extern "C" int tt_batch_sweep(tt_batch* b, const void* const* A_dev, const float
   }
   uint64_t s0 = first_sweep;
   cudaError_t e = cudaMemcpyAsync(b->d_sweep, &s0, sizeof(s0), cudaMemcpyHostToDevice, b->main);
-  for (int t = 0; t < nsweeps && e == cudaSuccess; ++t) e = cudaGraphLaunch(b->exec, b->main);
+  // a call's first sweep computes every tensor's data sketches; with a fixed draw its later
+  // sweeps reuse them
+  for (int t = 0; t < nsweeps && e == cudaSuccess; ++t)
+    e = cudaGraphLaunch(t > 0 && b->exec_reuse ? b->exec_reuse : b->exec, b->main);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->main);
   if (e != cudaSuccess) return bfail(b, TT_ECUDA, cudaGetErrorString(e));
   for (int i = 0; i < b->count; ++i) {

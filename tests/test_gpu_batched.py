@@ -87,3 +87,35 @@ def test_batched_sweeps_continue_and_recapture():
     for a, b in zip(e1, e2):
         assert abs(a - b) <= 1e-3 * b
     batch.close()
+
+
+def test_batched_fixed_draw_reuses_data_sketches():
+    """Tensors with TT_FLAG_FIXED_SKETCH (every other one) sweep their later sweeps of a call on the
+    data sketches of its first sweep (a second graph): four sweeps in one call against the
+    single-tensor path with the same flag (1e-4 on the relative error) and, for tensor 0, the
+    oracle's four sweeps with sweep 0's draw (reconstruction 1e-4). A second call continues with
+    fresh sketches of the same data (first graph, then the reuse graph again)."""
+    specs = synth.batched_specs(count=5, dims_range=(6, 16), rank_range=(2, 4))
+    for sp in specs[::2]:
+        sp["flags"] = lib.TT_FLAG_FIXED_SKETCH
+    As, inits, exact = _setup(specs)
+    cores_b = [lib.device_cores(c) for c in inits]
+    batch = lib.Batch(specs)
+    batch.tt_batch_sweep(As, cores_b, 4, 0)
+    batch.tt_batch_sweep(As, cores_b, 2, 4)
+    errs_b = batch.tt_batch_rel_error(As, cores_b)
+    batch.close()
+    for i, sp in enumerate(specs):
+        ctx = lib.Context(sp["dims"], sp["ranks"], sp["J"], sp["lam"], sp["seed"], sp["dtype"], flags=sp.get("flags", 0))
+        cs = lib.device_cores(inits[i])
+        ctx.tt_prox_als_sweep(As[i], cs, 4, 0, rel_change=False)
+        ctx.tt_prox_als_sweep(As[i], cs, 2, 4, rel_change=False)
+        e_single = ctx.tt_rel_error(As[i], cs)
+        ctx.close()
+        assert abs(errs_b[i] - e_single) <= 1e-4 * e_single + 1e-7, (i, errs_b[i], e_single)
+    ref = [np.asarray(g, np.float64) for g in inits[0]]
+    for _ in range(6):
+        ref, _ = O.tt_ts_sweep(exact[0], ref, specs[0]["seed"], 0, specs[0]["J"], specs[0]["lam"])
+    got = lib.host_cores(cores_b[0], specs[0]["ranks"], specs[0]["dims"])
+    d = np.linalg.norm((O.tt_full(got) - O.tt_full(ref)).ravel()) / np.linalg.norm(O.tt_full(ref).ravel())
+    assert d <= 1e-4, d
