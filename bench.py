@@ -28,7 +28,7 @@ sys.path.insert(0, ROOT)
 METRIC = "ALS sweeps/s + unfold-sketch HBM GB/s at equal rel. error vs plain FP32 GPU"
 # DRAM bytes (read + write) per data-sketch launch from an ncu capture of the current kernels,
 # per (workload, storage); the roofline reports null for anything not captured.
-UNFOLD_TRAFFIC = {("order4-100-r10", "f32"): 428.5e6}
+UNFOLD_TRAFFIC = {("order4-100-r10", "f32"): 428.65e6}
 UNIT = "sweeps/s"
 DEFAULT_WORKLOAD = "order4-100-r10"
 
