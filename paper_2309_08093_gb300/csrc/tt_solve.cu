@@ -1884,6 +1884,7 @@ __global__ void __launch_bounds__(256, 2) k_rel_error_stream(const void* __restr
         for (int u = 0; u < REL_U; ++u) w[u] = *reinterpret_cast<const float4*>(tR + (size_t)(pi + P * u) * r1p + al0);
 #pragma unroll
         for (int aa = 0; aa < 4; ++aa) {
+          if (al0 + aa >= r1) break;  // rows r1 .. r1p - 1 of G_0 are padding (zero)
           const float4 g4 = *reinterpret_cast<const float4*>(G0 + (al0 + aa) * n0 + 4 * qi);
           const float2 glo = make_float2(g4.x, g4.y), ghi = make_float2(g4.z, g4.w);
 #pragma unroll
