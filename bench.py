@@ -498,8 +498,8 @@ def deterministic_pattern(w, p, dev, nsweeps=5):
     ms = min(runs[0][0], runs[1][0])
     return {"sweeps_per_s": 1e3 / ms, "ms_per_sweep": ms, "sweeps": nsweeps, "rel_error": runs[0][2],
             "bitwise_identical_runs": same,
-            "note": "TT_FLAG_DETERMINISTIC: fixed-point data sketch (one read of A for all modes, int64 "
-                    "atomics), Gram K-chunks and partial sums in fixed order; sweeps only (no relative error "
+            "note": "TT_FLAG_DETERMINISTIC: data sketch with runs summed in index order and flushed in 64-bit "
+                    "fixed point (int64 atomics), Gram K-chunks and partial sums in fixed order; sweeps only (no relative error "
                     "inside the timed region), CUDA events; two runs from the same initial cores compared"}
 
 

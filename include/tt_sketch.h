@@ -71,11 +71,14 @@ enum {
 #define TT_FLAG_FIXED_SKETCH 1u
 #define TT_FLAG_FP64_SOLVE 2u   /* solve Eq. (ite) in FP64 also when sigma > 0 (see tt_prox_update) */
 /* Fixed summation orders: repeated calls on the same inputs return the same bits (data sketches,
- * interface sketches, updated cores, relative errors and rel-changes of the dense-tensor calls).
- * The data sketch is then accumulated in 64-bit fixed point, one read of A for all modes, with
- * integer atomics, the Gram's K-chunks and all partial sums are added in a fixed order, and the
- * CountSketch of the cores adds its entries in index order. Slower: the data sketch makes one
- * 8-byte integer atomic add per entry and mode. The sparse coordinate-form calls are not covered. */
+ * interface sketches, updated cores, relative errors and rel-changes of the dense-tensor calls),
+ * on any device and whatever A's alignment. The data sketch then adds the fibres of each run of
+ * equal hash in index order (FP32), over work spans fixed by the shape, rounds each run's sum to
+ * 64-bit fixed point (one scale for the tensor, from max |A|) and adds those with integer atomics;
+ * the Gram's K-chunks and all partial sums are added in a fixed order, and the CountSketch of the
+ * cores adds its entries in index order. Slower: one more read of A for the scale, the plans of
+ * every draw built in index order, and 8-byte integer flushes. The sparse coordinate-form calls
+ * are not covered. */
 #define TT_FLAG_DETERMINISTIC 4u
 /* Gram and right-hand side of the FP32 update (sigma > 0) on the tensor cores (tcgen05, TF32
  * operands staged by TMA, FP32 accumulators in tensor memory), when J is a multiple of 4 and

@@ -45,7 +45,7 @@ extern "C" int tt_sketch_unfold(tt_ctx* c, const void* A, const float* scales, i
     if ((k == -1 || k == kk) && !Y[kk]) return tt_fail(c, TT_EINVAL, "null output for mode %d", kk);
   c->err.clear();
   TT_TRY(tt_ensure_tables(c, sweep));
-  if (c->det)  // fixed-point sketch of all requested modes in one read of A
+  if (c->det)  // fixed-point sketches of the requested modes (one scale for all)
     return tt_launch_unfold_det(c, A, scales, k == -1 ? (1u << c->d) - 1u : 1u << k, Y);
   for (int kk = 0; kk < c->d; ++kk)
     if (k == -1 || k == kk) TT_TRY(tt_launch_unfold(c, A, scales, kk, Y[kk]));
@@ -131,14 +131,10 @@ static int sweep_body(tt_ctx* c, const void* A, const float* scales, float* cons
     c->stream = c->side;
     c->in_sweep = true;
     int rc = TT_OK;
-    if (c->det) {  // every mode from one fixed-point pass over A
+    if (c->det) {  // every mode in fixed point (one scale for all), Y_k's event as it is done
       float* ys[TT_MAX_D];
       for (int k = 0; k < d; ++k) ys[k] = c->d_Yall + c->yoff[k];
-      rc = tt_launch_unfold_det(c, A, scales, (1u << d) - 1u, ys);
-      for (int k = 0; k < d && rc == TT_OK; ++k) {
-        const cudaError_t e = cudaEventRecord(c->ev_y[k], c->side);
-        if (e != cudaSuccess) rc = tt_cuda_check(c, e, "cudaEventRecord");
-      }
+      rc = tt_launch_unfold_det(c, A, scales, (1u << d) - 1u, ys, c->ev_y);
     }
     for (int k = 0; k < d && rc == TT_OK && !c->det; ++k) {
       rc = tt_launch_unfold(c, A, scales, k, c->d_Yall + c->yoff[k]);

@@ -10,14 +10,19 @@
 //   - k_det_exp: the binary exponent S such that every term |A(i)| 2^S < 2^(62 - L) with
 //     2^(L-1) >= N, so no sum of at most N terms leaves the int64 range (a NaN or Inf in A makes
 //     every sketch NaN, which the update then reports as TT_ENONFINITE);
-//   - k_unfold_fixed: one warp per mode-0 fibre, one lane per entry; each entry A(i) becomes the
-//     integer round(A(i) 2^S) (an integer conversion of the float bits, ties away from zero) and is
-//     added, with its sign prod_{s != k} v_s(i_s), to Y_k[(sum_{s != k} h_s(i_s)) mod J, i_k] for
-//     every requested mode k by 64-bit integer atomics, which are associative: the result does not
-//     depend on the order in which the adds land. One read of A serves all modes;
+//   - per mode, the vector gather of the fast path (tt_gather.cuh, DET = true) on a deterministic
+//     plan (tt_context.cu: each group's fibres in index order). Its work items and the spans into
+//     which an item's fibres are cut are fixed by the shape alone, so every run of equal hash is
+//     cut at the same places and each piece summed in FP32 in the same order on every call, on any
+//     device and with any vector width. Each piece's sum becomes the integer round(sum 2^S) (an
+//     integer conversion of the float bits, ties away from zero) and is added to the int64 sketch
+//     by 64-bit integer atomics, which are associative: the result does not depend on the order in
+//     which the adds land;
 //   - k_fixed_to_float: Y_k = float(sum 2^-S).
-// With S chosen as above each term carries an absolute error below 2^-(S+1), far below the FP32
-// rounding of the fast path for the data of this library.
+// A piece's sum has the FP32 rounding of the fast path's run sums; its conversion adds at most
+// 2^-(S+1), far below that for the data of this library. The integer total stays below 2^61 in
+// magnitude: at most N terms of at most 2^(62-L), and the FP32 rounding of a piece is far below
+// the remaining factor of two.
 //
 // The other order-dependent sums of a sweep take fixed orders in this mode: the split-K Gram
 // (k_gram_reduce sums the K-chunk partials in chunk order), the relative error and the change
@@ -25,7 +30,7 @@
 // (tt_interface.cu: one thread adds the entries in index order).
 #include <algorithm>
 
-#include "tt_internal.cuh"
+#include "tt_gather.cuh"
 
 template <int DT>
 __device__ __forceinline__ float det_load(const void* A, int64_t i) {
@@ -79,85 +84,6 @@ __global__ void k_det_exp(const unsigned* absmax, int64_t N, int* S, int* nonfin
   *S = 62 - L - e;
 }
 
-// round(x 2^S) as an int64, from the float bits: x = mant 2^e2; ties rounded away from zero
-__device__ __forceinline__ long long det_fixed(float x, int S) {
-  const uint32_t b = __float_as_uint(x);
-  const uint32_t ex = (b >> 23) & 0xFFu;
-  const long long mant = (long long)((b & 0x7FFFFFu) | (ex ? 0x800000u : 0u));
-  const int shift = (ex ? (int)ex : 1) - 150 + S;
-  long long v;
-  if (shift >= 0)
-    v = mant << shift;  // below 2^62 by the choice of S
-  else if (shift > -40)
-    v = (mant + (1ll << (-shift - 1))) >> (-shift);
-  else
-    v = 0;
-  return (b >> 31) ? -v : v;
-}
-
-struct FixedArgs {
-  const void* A;
-  const float* scales;  // n_0 FP8 scales or null
-  const int32_t* h;     // all modes' tables, mode s at noff[s]
-  const int8_t* v;
-  int64_t noff[TT_MAX_D + 1];
-  int64_t n[TT_MAX_D];
-  int64_t M0;           // mode-0 fibres, N / n_0
-  unsigned long long* Y[TT_MAX_D];  // J x n_k int64 accumulators per requested mode (null: skip)
-  const int* S;
-  const int* nonfinite;  // set by k_det_exp: nothing to accumulate
-  int d, J;
-};
-
-template <int DT>
-__global__ void __launch_bounds__(256) k_unfold_fixed(FixedArgs a) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  if (*a.nonfinite) return;
-  const int S = *a.S;
-  const int n0 = (int)a.n[0];
-  for (int64_t f = warp0; f < a.M0; f += nwarps) {
-    // the fibre's modes s >= 1: indices, hashes and signs (every lane computes the same values)
-    int ik[TT_MAX_D], hk[TT_MAX_D];
-    bool nk[TT_MAX_D];
-    int Hrest = 0;
-    bool nrest = false;
-    int64_t rem = f;
-#pragma unroll
-    for (int s = 1; s < TT_MAX_D; ++s) {
-      ik[s] = 0;
-      hk[s] = 0;
-      nk[s] = false;
-      if (s < a.d) {
-        const int i = (int)(rem % a.n[s]);
-        rem /= a.n[s];
-        ik[s] = i;
-        hk[s] = __ldg(a.h + a.noff[s] + i);
-        nk[s] = __ldg(a.v + a.noff[s] + i) < 0;
-        Hrest += hk[s];
-        nrest ^= nk[s];
-      }
-    }
-    for (int i0 = lane; i0 < n0; i0 += 32) {
-      const long long q = det_fixed(det_value<DT>(a.A, a.scales, f * n0 + i0, n0), S);
-      const int h0 = __ldg(a.h + i0);
-      const bool n0neg = __ldg(a.v + i0) < 0;
-      if (a.Y[0]) {  // mode 0: row (sum_{s>=1} h_s) mod J, column i_0, sign prod_{s>=1} v_s
-        const long long t = nrest ? -q : q;
-        atomicAdd(a.Y[0] + (Hrest % a.J) + (int64_t)a.J * i0, (unsigned long long)t);
-      }
-#pragma unroll
-      for (int k = 1; k < TT_MAX_D; ++k) {
-        if (k < a.d && a.Y[k]) {
-          const int b = (Hrest - hk[k] + h0) % a.J;
-          const long long t = (nrest != (nk[k] != n0neg)) ? -q : q;
-          atomicAdd(a.Y[k] + b + (int64_t)a.J * ik[k], (unsigned long long)t);
-        }
-      }
-    }
-  }
-}
 
 __global__ void k_fixed_to_float(const unsigned long long* Yq, int64_t count, const int* S, const int* nonfinite,
                                  float* Y) {
@@ -167,7 +93,96 @@ __global__ void k_fixed_to_float(const unsigned long long* Yq, int64_t count, co
     Y[i] = nf ? __int_as_float(0x7fc00000) : (float)ldexp((double)(long long)Yq[i], -s);
 }
 
-int tt_launch_unfold_det(tt_ctx* c, const void* A, const float* scales, unsigned mask, float* const* Y) {
+// the vectors per lane (1, 2 or 4) for a fibre of vpf vectors of epv entries: mode 0 the most
+// fibre slots per warp, modes >= 1 one slot per warp (runs there are short)
+static int det_m(bool mode0, int vpf, int epv, int vb) {
+  if (vb < 4) return 1;
+  const int m = mode0 ? pick_m(vpf, epv) : (vpf > 64 && vpf <= 128 ? 4 : vpf > 32 && vpf <= 64 ? 2 : 1);
+  return m * epv <= 16 ? m : 1;
+}
+
+// spans per work item: 8 warps times the fibre slots per warp of the widest vectors that the
+// fibre length allows (the launch's own count when A is aligned to them)
+template <int DT, bool MODE0>
+static int det_spans(const tt_ctx* c) {
+  constexpr int EB = TtElem<DT>::bytes;
+  const int64_t fb = (int64_t)c->n[0] * EB;
+  const int vb = pick_vb(fb, 0, EB);
+  const int vpf = (int)(fb / vb);
+  return 8 * fibre_geom(fb, vb, det_m(MODE0, vpf, vb / EB, vb)).fpi;
+}
+
+// The deterministic gather of mode k into the int64 sketch Yq: the fast path's vector gather
+// (tt_gather.cuh) with VB-byte vectors, M per lane and S fibres in flight per slot.
+template <int DT, int VB, int M, bool MODE0>
+static int det_gather_launch(tt_ctx* c, const void* A, const float* scales, int k, unsigned long long* Yq) {
+  constexpr int THREADS = 256, S = 12 / M;
+  GArgs a{};
+  a.A = (const char*)A;
+  a.scales = scales;
+  a.h0 = c->d_h;
+  a.v0 = c->d_v;
+  a.plan = c->d_rplan[k];
+  a.ulist = c->d_ulist[k];
+  a.ustart = c->d_ustart[k];
+  a.ucount = c->d_ucount[k];
+  a.Yq = Yq;
+  a.det_S = c->d_det_misc + 1;
+  a.J = c->J;
+  a.n0 = (int)c->n[0];
+  a.ncol = MODE0 ? 1 : (int)c->n[k];
+  a.col_fibres = MODE0 ? 0 : c->stride[k] / c->n[0];
+  a.total_bytes = c->N * TtElem<DT>::bytes;
+  a.fg = fibre_geom((int64_t)c->n[0] * TtElem<DT>::bytes, VB, M);
+  // items and spans fixed by the shape (not by the device, the vector width, the batch or
+  // whether a sweep runs beside): c-segments as the fast path picks for 152 SMs inside a sweep,
+  // and as many spans per item as the widest vectors give fibre slots per CTA
+  a.nseg = std::max(std::max(1, 1216 / a.ncol), (c->J + 2047) / 2048);
+  a.segmax = (c->J + a.nseg - 1) / a.nseg + 1;
+  a.nch = det_spans<DT, MODE0>(c);
+  const size_t smem = gather_ring_bytes(VB >= 4, THREADS / 32, S * M, VB) + sizeof(int64_t) * (MODE0 ? 0 : c->J) +
+                      sizeof(int) * (2 * (size_t)a.segmax + 1);
+  if (smem > 220 * 1024) return tt_fail(c, TT_EINVAL, "gather kernel needs %zu bytes of shared memory", smem);
+  auto kern = k_unfold_gather<DT, VB, S, M, MODE0, true>;
+  TT_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int items = a.ncol * a.nseg;
+  kern<<<std::max(1, items), THREADS, smem, c->stream>>>(a);
+  TT_LAUNCH(c, "k_unfold_gather (deterministic)");
+  return TT_OK;
+}
+
+template <int DT, int VB, bool MODE0>
+static int det_gather_vb(tt_ctx* c, const void* A, const float* scales, int k, unsigned long long* Yq) {
+  if constexpr (VB >= 4 && VB >= TtElem<DT>::bytes) {
+    constexpr int EPV = TtVec<DT, VB>::EPV;
+    const int vpf = (int)(c->n[0] * TtElem<DT>::bytes / VB);
+    const int m = det_m(MODE0, vpf, EPV, VB);
+    if constexpr (4 * EPV <= 16)
+      if (m == 4) return det_gather_launch<DT, VB, 4, MODE0>(c, A, scales, k, Yq);
+    if constexpr (2 * EPV <= 16)
+      if (m == 2) return det_gather_launch<DT, VB, 2, MODE0>(c, A, scales, k, Yq);
+  }
+  return det_gather_launch<DT, VB, 1, MODE0>(c, A, scales, k, Yq);
+}
+
+template <int DT, bool MODE0>
+static int det_gather(tt_ctx* c, const void* A, const float* scales, int k, unsigned long long* Yq) {
+  constexpr int EB = TtElem<DT>::bytes;
+  switch (pick_vb((int64_t)c->n[0] * EB, (uintptr_t)A, EB)) {
+    case 16: return det_gather_vb<DT, 16, MODE0>(c, A, scales, k, Yq);
+    case 8: return det_gather_vb<DT, (EB <= 8 ? 8 : 16), MODE0>(c, A, scales, k, Yq);
+    case 4: return det_gather_vb<DT, (EB <= 4 ? 4 : 16), MODE0>(c, A, scales, k, Yq);
+    case 2: return det_gather_vb<DT, (EB <= 2 ? 2 : 16), MODE0>(c, A, scales, k, Yq);
+    default: return det_gather_vb<DT, (EB <= 1 ? 1 : 16), MODE0>(c, A, scales, k, Yq);
+  }
+}
+
+template <int DT>
+static int det_gather_mode(tt_ctx* c, const void* A, const float* scales, int k, unsigned long long* Yq) {
+  return k == 0 ? det_gather<DT, true>(c, A, scales, k, Yq) : det_gather<DT, false>(c, A, scales, k, Yq);
+}
+
+int tt_launch_unfold_det(tt_ctx* c, const void* A, const float* scales, unsigned mask, float* const* Y, cudaEvent_t* ev) {
   const int sms = tt_sm_count();
   TT_CUDA(c, cudaMemsetAsync(c->d_det_misc, 0, 3 * sizeof(int), c->stream));
   const int ablocks = (int)std::min<int64_t>((c->N + 255) / 256, (int64_t)sms * 8);
@@ -180,41 +195,23 @@ int tt_launch_unfold_det(tt_ctx* c, const void* A, const float* scales, unsigned
   TT_LAUNCH(c, "k_det_absmax");
   k_det_exp<<<1, 1, 0, c->stream>>>((const unsigned*)c->d_det_misc, c->N, c->d_det_misc + 1, c->d_det_misc + 2);
   TT_LAUNCH(c, "k_det_exp");
-  FixedArgs a;
-  a.A = A;
-  a.scales = scales;
-  a.h = c->d_h;
-  a.v = c->d_v;
-  for (int s = 0; s <= c->d; ++s) a.noff[s] = c->noff[s];
-  for (int s = 0; s < TT_MAX_D; ++s) {
-    a.n[s] = s < c->d ? c->n[s] : 1;
-    a.Y[s] = nullptr;
-  }
-  for (int k = 0; k < c->d; ++k)
-    if (mask & (1u << k)) {
-      a.Y[k] = reinterpret_cast<unsigned long long*>(c->d_y64 + c->yoff[k]);
-      TT_CUDA(c, cudaMemsetAsync(a.Y[k], 0, sizeof(int64_t) * (size_t)c->J * c->n[k], c->stream));
+  for (int k = 0; k < c->d; ++k) {
+    if (!(mask & (1u << k))) continue;
+    TT_TRY(tt_ensure_rplan(c, k));  // deterministic plans (all modes on the first call of a draw)
+    unsigned long long* Yq = reinterpret_cast<unsigned long long*>(c->d_y64 + c->yoff[k]);
+    TT_CUDA(c, cudaMemsetAsync(Yq, 0, sizeof(int64_t) * (size_t)c->J * c->n[k], c->stream));
+    switch (c->dtype) {
+      case TT_F64: TT_TRY(det_gather_mode<TT_F64>(c, A, scales, k, Yq)); break;
+      case TT_F32: TT_TRY(det_gather_mode<TT_F32>(c, A, scales, k, Yq)); break;
+      case TT_BF16: TT_TRY(det_gather_mode<TT_BF16>(c, A, scales, k, Yq)); break;
+      default: TT_TRY(det_gather_mode<TT_FP8E4M3>(c, A, scales, k, Yq)); break;
     }
-  a.M0 = c->M0;
-  a.S = c->d_det_misc + 1;
-  a.nonfinite = c->d_det_misc + 2;
-  a.d = c->d;
-  a.J = c->J;
-  const int fblocks = (int)std::max<int64_t>(1, std::min<int64_t>((c->M0 + 7) / 8, (int64_t)sms * 8));
-  switch (c->dtype) {
-    case TT_F64: k_unfold_fixed<TT_F64><<<fblocks, 256, 0, c->stream>>>(a); break;
-    case TT_F32: k_unfold_fixed<TT_F32><<<fblocks, 256, 0, c->stream>>>(a); break;
-    case TT_BF16: k_unfold_fixed<TT_BF16><<<fblocks, 256, 0, c->stream>>>(a); break;
-    default: k_unfold_fixed<TT_FP8E4M3><<<fblocks, 256, 0, c->stream>>>(a); break;
+    const int64_t cnt = (int64_t)c->J * c->n[k];
+    k_fixed_to_float<<<(int)std::min<int64_t>((cnt + 255) / 256, (int64_t)sms * 4), 256, 0, c->stream>>>(
+        Yq, cnt, c->d_det_misc + 1, c->d_det_misc + 2, Y[k]);
+    TT_LAUNCH(c, "k_fixed_to_float");
+    if (ev) TT_CUDA(c, cudaEventRecord(ev[k], c->stream));
   }
-  TT_LAUNCH(c, "k_unfold_fixed");
-  for (int k = 0; k < c->d; ++k)
-    if (mask & (1u << k)) {
-      const int64_t cnt = (int64_t)c->J * c->n[k];
-      k_fixed_to_float<<<(int)std::min<int64_t>((cnt + 255) / 256, (int64_t)sms * 4), 256, 0, c->stream>>>(
-          a.Y[k], cnt, c->d_det_misc + 1, c->d_det_misc + 2, Y[k]);
-      TT_LAUNCH(c, "k_fixed_to_float");
-    }
   return TT_OK;
 }
 

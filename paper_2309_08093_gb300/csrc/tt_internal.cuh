@@ -151,6 +151,7 @@ struct tt_ctx {
   bool det = false;
   int* d_det_misc = nullptr;        // [0] bits of max |A|, [1] fixed-point exponent S, [2] A not finite
   int64_t* d_y64 = nullptr;         // int64 data-sketch accumulators, mode k at yoff[k]
+  int32_t* d_det_bcnt = nullptr;    // deterministic plans: per range and key, counts then first slots
   void* d_gram_part = nullptr;      // TT_DET_KSPLIT K-chunk partials of the Gram (FP32 or FP64)
   double* d_part_err = nullptr;     // per-CTA partial sums of the relative error (2 per CTA)
   double* d_part_chg = nullptr;     // per-CTA partial sums of the change norms (2 per CTA)
@@ -283,9 +284,10 @@ int tt_launch_prox_update(tt_ctx* c, const float* Y, const float* SH, float* cor
                           double* change_slot,
                           bool gram_zeroed = false);  // gram_zeroed: d_gram already zero
 // deterministic mode (tt_det.cu): the data sketches of the modes in `mask` in int64 fixed point
-// (Y[k] written for those modes), the ordered sum of per-CTA partials into acc[0..1], and the
-// ordered sum of the Gram's K-chunk partials
-int tt_launch_unfold_det(tt_ctx* c, const void* A, const float* scales, unsigned mask, float* const* Y);
+// (Y[k] written for those modes, ev[k] recorded on c->stream after Y[k] when ev is given), the
+// ordered sum of per-CTA partials into acc[0..1], and the ordered sum of the Gram's K-chunk partials
+int tt_launch_unfold_det(tt_ctx* c, const void* A, const float* scales, unsigned mask, float* const* Y,
+                         cudaEvent_t* ev = nullptr);
 int tt_launch_sum_partials(tt_ctx* c, const double* part, int nparts, double* acc);
 int tt_launch_gram_reduce(tt_ctx* c, const void* P, int nz, int64_t count, void* C, bool f64);
 // tensor-core Gram of the FP32 update (tt_gram_tc.cu): whether the shape and pointers suit TMA,

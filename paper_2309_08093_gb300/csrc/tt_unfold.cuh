@@ -97,6 +97,22 @@ __device__ __forceinline__ float tt_fma_e4m3(unsigned short x, unsigned short s,
 // FP16 bits of a sign s = +-1
 __device__ __forceinline__ unsigned short tt_f16_sign(float s) { return s < 0.f ? 0xBC00 : 0x3C00; }
 
+// round(x 2^S) as an int64, from the float bits: x = mant 2^e2; ties rounded away from zero
+__device__ __forceinline__ long long det_fixed(float x, int S) {
+  const uint32_t b = __float_as_uint(x);
+  const uint32_t ex = (b >> 23) & 0xFFu;
+  const long long mant = (long long)((b & 0x7FFFFFu) | (ex ? 0x800000u : 0u));
+  const int shift = (ex ? (int)ex : 1) - 150 + S;
+  long long v;
+  if (shift >= 0)
+    v = mant << shift;  // below 2^62 by the choice of S
+  else if (shift > -40)
+    v = (mant + (1ll << (-shift - 1))) >> (-shift);
+  else
+    v = 0;
+  return (b >> 31) ? -v : v;
+}
+
 // 16-byte copy global -> shared of `bytes` (1..16) valid source bytes, the rest of the 16
 // destination bytes zero-filled; both addresses 16-byte aligned
 __device__ __forceinline__ void cp_async_16z(void* smem, const void* gmem, int bytes) {
@@ -120,6 +136,9 @@ struct GArgs {
   int segmax;             // capacity of the staged segment (c groups)
   int y_vec4;             // Y 16-byte aligned and J % 4 == 0: columns flushed with 16-byte atomics
   int64_t total_bytes;    // bytes of A (window staging clips its last copies here)
+  unsigned long long* Yq; // deterministic mode: J x ncol int64 fixed-point accumulators (instead of Y)
+  const int* det_S;       // deterministic mode: {S, A not finite}; values scaled by 2^S
+  int nch;                // deterministic mode: spans per item (split at ne * t / nch), any slot count
   int wstride;            // window staging: bytes of a fibre's region of a stage (a multiple of 16)
   int wstage;             // window staging: bytes of one warp's stage
   FibreGeom fg;

@@ -70,6 +70,34 @@ def test_det_data_sketch_matches_oracle_and_repeats_bit_for_bit(dims, J, storage
     ctx.close()
 
 
+@pytest.mark.parametrize("storage,offsets", [("f32", (1, 2, 3)), ("bf16", (1, 2, 4))])
+def test_det_data_sketch_bits_do_not_depend_on_alignment(storage, offsets):
+    """The same tensor starting 16-byte aligned and `offset` entries into its allocation: the
+    kernels then load 4-, 8- or 2-byte vectors with fewer fibre slots per warp, but the work spans
+    are fixed by the shape, so every mode's sketch has the same bits."""
+    dims, J = (64, 9, 7), 512
+    seed = 4100 + len(storage)
+    a = synth.random_tensor(dims, seed)
+    flat, _, exact = synth.quantize(a, storage)
+    ctx = lib.Context(dims, (1,) * (len(dims) + 1), J, 1e-3, seed, storage, flags=DET)
+    base = lib.device_tensor(flat, storage)
+    Y0 = [torch.zeros(J * n, device="cuda") for n in dims]
+    ctx.tt_sketch_unfold(base, -1, 0, Y0)
+    hs, vs = O.draw_sketch(seed, 0, dims, J)
+    for k in range(len(dims)):
+        ref = O.sketch_unfolding(exact, hs, vs, J, k)
+        assert rel(Y0[k].cpu().numpy().reshape(dims[k], J).T, ref) <= TOL, k
+    for off in offsets:
+        buf = torch.zeros(base.numel() + off, dtype=base.dtype, device="cuda")
+        buf[off:] = base
+        Y = [torch.zeros(J * n, device="cuda") for n in dims]
+        ctx.tt_sketch_unfold(buf[off:], -1, 0, Y)
+        torch.cuda.synchronize()
+        for k in range(len(dims)):
+            assert torch.equal(Y[k], Y0[k]), (off, k)
+    ctx.close()
+
+
 @pytest.mark.parametrize("dims,ranks,J", [((30, 20, 10), (1, 12, 10, 1), 1024), ((6, 5, 7), (1, 2, 3, 1), 45),
                                           ((20, 30, 25, 10), (1, 4, 5, 3, 1), 16384)])
 def test_det_interface_sketch_matches_oracle(dims, ranks, J):
