@@ -349,22 +349,37 @@ __global__ void k_rplan_scatter(RPlanAll P, const int32_t* h, const int8_t* v, c
 
 // Deterministic plan (TT_FLAG_DETERMINISTIC): the fibres of each group in ascending fibre index
 // (the rest index r is walked in order and the fibre offset grows with r), so that the data-sketch
-// kernels sum every run in the same order on every call. A mode's rest fibres are split into nb
-// contiguous ranges, one warp each: k_rplan_dcount writes each range's key counts to its row of
-// `bcnt`, k_rplan_dbase turns the rows into the range's first slot per key (off[key] plus the
-// counts of the earlier ranges, in range order), and k_rplan_dscatter walks each range 32 fibres at
-// a time, ranking equal keys by lane (__match_any_sync) on top of a per-key cursor in shared
-// memory.
+// kernels sum every run in the same order on every call. A mode's rest fibres are split into
+// contiguous ranges: k_rplan_dcount writes each range's key counts to its row of `bcnt` and every
+// fibre's (key, plan entry) to `kv`; k_rplan_dbase turns the rows into the range's first slot per
+// key (off[key] plus the counts of the earlier ranges, in range order); k_rplan_dscatter walks
+// each range 32 fibres at a time (one warp), ranking equal keys by lane (__match_any_sync) on top
+// of a per-key cursor in shared memory.
 struct DPlan {
   int64_t bstart[TT_MAX_D + 1];  // first range (block) of each mode
   int64_t per[TT_MAX_D];         // rest fibres per range
+  int64_t R[TT_MAX_D];           // rest fibres of each mode
+  int64_t roff[TT_MAX_D];        // first entry of each mode in kv
 };
 
-// deterministic plans: rest fibres per range (at most 256 ranges per mode) and the ranges of all modes
-static int64_t dplan_per(int64_t R) { return std::max<int64_t>(1024, (R + 255) / 256); }
+// deterministic plans: rest fibres per range (at least 256; at most 2^21 / J ranges per mode, in
+// [32, 1024], which bounds the count table to 8 MB per mode), the ranges of all modes, and the
+// rest fibres of all modes (entries of kv)
+static int64_t dplan_per(int64_t R, int J) {
+  const int64_t nr = std::max<int64_t>(32, std::min<int64_t>(1024, (1 << 21) / J));
+  return std::max<int64_t>(256, (R + nr - 1) / nr);
+}
 static int64_t dplan_ranges(const tt_ctx* c) {
   int64_t t = 0;
-  for (int m = 0; m < c->d; ++m) t += std::max<int64_t>(1, (c->R[m] + dplan_per(c->R[m]) - 1) / dplan_per(c->R[m]));
+  for (int m = 0; m < c->d; ++m) {
+    const int64_t per = dplan_per(c->R[m], c->J);
+    t += std::max<int64_t>(1, (c->R[m] + per - 1) / per);
+  }
+  return t;
+}
+static int64_t dplan_fibres(const tt_ctx* c) {
+  int64_t t = 0;
+  for (int m = 0; m < c->d; ++m) t += c->R[m];
   return t;
 }
 
@@ -374,13 +389,14 @@ __device__ __forceinline__ int dplan_mode(const DPlan& D, int d) {
   return m;
 }
 
-__global__ void k_rplan_dcount(RPlanAll P, DPlan D, const int32_t* h, const int8_t* v, int32_t* bcnt) {
+__global__ void k_rplan_dcount(RPlanAll P, DPlan D, const int32_t* h, const int8_t* v, int32_t* bcnt, uint2* kv) {
   extern __shared__ int hist[];
   const int m = dplan_mode(D, P.d);
   const RPlanArgs& a = P.m[m];
   const int64_t r0 = ((int64_t)blockIdx.x - D.bstart[m]) * D.per[m], r1 = min(a.R, r0 + D.per[m]);
   for (int i = threadIdx.x; i < a.J; i += blockDim.x) hist[i] = 0;
   __syncthreads();
+  uint2* out = kv + D.roff[m];
   RestWalker wk;
   wk.init(a, r0 + threadIdx.x, blockDim.x);
   for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x, wk.advance(a)) {
@@ -388,51 +404,85 @@ __global__ void k_rplan_dcount(RPlanAll P, DPlan D, const int32_t* h, const int8
     int64_t ofs;
     wk.entry(a, h, v, &key, &neg, &ofs);
     atomicAdd(&hist[key], 1);  // counts: the order of the adds does not matter
+    out[r] = make_uint2((uint32_t)key, (uint32_t)ofs | ((uint32_t)neg << 31));
   }
   __syncthreads();
   int32_t* row = bcnt + (int64_t)blockIdx.x * a.J;
   for (int i = threadIdx.x; i < a.J; i += blockDim.x) row[i] = hist[i];
 }
 
-// one thread per (mode, key): the ranges' counts become their first slots, in range order
-__global__ void k_rplan_dbase(DPlan D, int d, int J, const int64_t* off_all, int32_t* bcnt) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (int64_t)d * J) return;
-  const int m = (int)(t / J), key = (int)(t - (int64_t)m * J);
+// One CTA per (mode, 32 keys), 32 x 32 threads: thread (x, y) takes key 32 t + x over the y-th
+// of 32 contiguous slices of the mode's ranges. It sums its slice's counts, the slice totals are
+// scanned in y order, and the slice is walked again, each count replaced by its range's first
+// slot: off[key] plus the counts of all earlier ranges. Loads go eight at a time.
+__global__ void __launch_bounds__(1024) k_rplan_dbase(DPlan D, int J, const int64_t* off_all, int32_t* bcnt) {
+  __shared__ int64_t part[32][33];
+  const int tiles = (J + 31) / 32;
+  const int m = blockIdx.x / tiles;
+  const int key = (blockIdx.x - m * tiles) * 32 + threadIdx.x;
+  const int64_t rb = D.bstart[m], nr = D.bstart[m + 1] - rb;
+  const int64_t per_t = (nr + 31) / 32;
+  const int64_t b0 = min(rb + nr, rb + threadIdx.y * per_t), b1 = min(rb + nr, b0 + per_t);
+  const bool ok = key < J;
+  int64_t s = 0;
+  if (ok)
+    for (int64_t b = b0; b < b1; b += 8) {
+      int32_t cnt[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) cnt[u] = b + u < b1 ? bcnt[(b + u) * J + key] : 0;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) s += cnt[u];
+    }
+  part[threadIdx.y][threadIdx.x] = s;
+  __syncthreads();
+  if (!ok) return;
   int64_t pos = off_all[(int64_t)m * (J + 1) + key];
-  for (int64_t b = D.bstart[m]; b < D.bstart[m + 1]; ++b) {
-    const int32_t cnt = bcnt[b * J + key];
-    bcnt[b * J + key] = (int32_t)pos;
-    pos += cnt;
+  for (int y = 0; y < (int)threadIdx.y; ++y) pos += part[y][threadIdx.x];
+  for (int64_t b = b0; b < b1; b += 8) {
+    int32_t cnt[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) cnt[u] = b + u < b1 ? bcnt[(b + u) * J + key] : 0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (b + u < b1) {
+        bcnt[(b + u) * J + key] = (int32_t)pos;
+        pos += cnt[u];
+      }
   }
 }
 
-// one warp per range: fibres in index order, equal keys within a step of 32 ranked by lane
-__global__ void __launch_bounds__(32) k_rplan_dscatter(RPlanAll P, DPlan D, const int32_t* h, const int8_t* v,
-                                                       const int32_t* bbase, RPlanOut o) {
+// one warp per range: fibres in index order, equal keys within a step of 32 ranked by lane; the
+// (key, entry) pairs of four steps are loaded before the four steps run
+__global__ void __launch_bounds__(32) k_rplan_dscatter(DPlan D, int d, int J, const uint2* kv, const int32_t* bbase,
+                                                       RPlanOut o) {
   extern __shared__ int cur[];
-  const int m = dplan_mode(D, P.d);
-  const RPlanArgs& a = P.m[m];
-  const int64_t r0 = ((int64_t)blockIdx.x - D.bstart[m]) * D.per[m], r1 = min(a.R, r0 + D.per[m]);
-  const int32_t* base = bbase + (int64_t)blockIdx.x * a.J;
-  for (int i = threadIdx.x; i < a.J; i += 32) cur[i] = base[i];
+  const int m = dplan_mode(D, d);
+  const int64_t r0 = ((int64_t)blockIdx.x - D.bstart[m]) * D.per[m], r1 = min(D.R[m], r0 + D.per[m]);
+  const int32_t* base = bbase + (int64_t)blockIdx.x * J;
+  for (int i = threadIdx.x; i < J; i += 32) cur[i] = base[i];
   __syncwarp();
   const int lane = threadIdx.x;
   const unsigned lt = (1u << lane) - 1u;
   uint32_t* plan = o.plan[m];
-  RestWalker wk;
-  wk.init(a, r0 + lane, 32);
-  for (int64_t rb = r0; rb < r1; rb += 32, wk.advance(a)) {
-    const int64_t r = rb + lane;
-    int key = -1 - lane, neg = 0;  // lanes past the range: a key no other lane has
-    int64_t ofs = 0;
-    if (r < r1) wk.entry(a, h, v, &key, &neg, &ofs);
-    const unsigned peers = __match_any_sync(0xffffffffu, key);
-    const int rank = __popc(peers & lt);
-    if (r < r1) plan[cur[key] + rank] = (uint32_t)ofs | ((uint32_t)neg << 31);
-    __syncwarp();
-    if (r < r1 && rank == 0) cur[key] += __popc(peers);
-    __syncwarp();
+  const uint2* src = kv + D.roff[m];
+  for (int64_t rb = r0; rb < r1; rb += 128) {
+    uint2 e[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t r = rb + 32 * u + lane;
+      e[u] = r < r1 ? src[r] : make_uint2(0u, 0u);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const bool ok = rb + 32 * u + lane < r1;
+      const int key = ok ? (int)e[u].x : -1 - lane;  // lanes past the range: a key no other lane has
+      const unsigned peers = __match_any_sync(0xffffffffu, key);
+      const int rank = __popc(peers & lt);
+      if (ok) plan[cur[key] + rank] = e[u].y;
+      __syncwarp();
+      if (ok && rank == 0) cur[key] += __popc(peers);
+      __syncwarp();
+    }
   }
 }
 
@@ -482,21 +532,24 @@ int tt_ensure_rplan(tt_ctx* c, int k) {
   if (c->det) {  // fibres of each group in index order
     DPlan D;
     D.bstart[0] = 0;
+    int64_t roff = 0;
     for (int m = 0; m < c->d; ++m) {
-      D.per[m] = dplan_per(c->R[m]);
+      D.per[m] = dplan_per(c->R[m], c->J);
       D.bstart[m + 1] = D.bstart[m] + std::max<int64_t>(1, (c->R[m] + D.per[m] - 1) / D.per[m]);
+      D.R[m] = c->R[m];
+      D.roff[m] = roff;
+      roff += c->R[m];
     }
     if (hsm > 48 * 1024) {
       TT_CUDA(c, cudaFuncSetAttribute(k_rplan_dcount, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm));
       TT_CUDA(c, cudaFuncSetAttribute(k_rplan_dscatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm));
     }
     const int nr = (int)D.bstart[c->d];
-    k_rplan_dcount<<<nr, 256, hsm, c->stream>>>(P, D, c->d_h, c->d_v, c->d_det_bcnt);
+    k_rplan_dcount<<<nr, 256, hsm, c->stream>>>(P, D, c->d_h, c->d_v, c->d_det_bcnt, c->d_det_kv);
     TT_LAUNCH(c, "k_rplan_dcount");
-    const int64_t nk = (int64_t)c->d * c->J;
-    k_rplan_dbase<<<(int)((nk + 255) / 256), 256, 0, c->stream>>>(D, c->d, c->J, c->d_rtmp, c->d_det_bcnt);
+    k_rplan_dbase<<<c->d * ((c->J + 31) / 32), dim3(32, 32), 0, c->stream>>>(D, c->J, c->d_rtmp, c->d_det_bcnt);
     TT_LAUNCH(c, "k_rplan_dbase");
-    k_rplan_dscatter<<<nr, 32, hsm, c->stream>>>(P, D, c->d_h, c->d_v, c->d_det_bcnt, o);
+    k_rplan_dscatter<<<nr, 32, hsm, c->stream>>>(D, c->d, c->J, c->d_det_kv, c->d_det_bcnt, o);
     TT_LAUNCH(c, "k_rplan_dscatter");
   } else {
     k_rplan_scatter<<<blocks, 512, hsm, c->stream>>>(P, c->d_h, c->d_v, c->d_rtmp, count, o);
@@ -539,7 +592,7 @@ static void free_all(tt_ctx* c) {
   void* ps[] = {c->d_h, c->d_v, c->d_plan0, c->d_plan0_off, c->d_plan0_cursor, c->d_ghat,
                 c->d_twiddle, c->d_twstage, c->d_suffix, c->d_prefix, c->d_prefix_tmp, c->d_SH, c->d_Y,
                 c->d_gram, c->d_core_old, c->d_changes, c->d_status, c->d_err_acc, c->d_errs, c->d_ws_acc, c->d_rint, c->d_slab_u, c->d_Yall, c->d_xgram, c->d_gram64,
-                c->d_det_misc, c->d_y64, c->d_gram_part, c->d_part_err, c->d_part_chg, c->d_det_bcnt};
+                c->d_det_misc, c->d_y64, c->d_gram_part, c->d_part_err, c->d_part_chg, c->d_det_bcnt, c->d_det_kv};
   for (void* p : ps)
     if (p) cudaFree(p);
   tt_host_free(c);
@@ -615,6 +668,7 @@ static void tt_workspace_each(tt_ctx* c, F&& A) {
     A((void**)&c->d_part_err, sizeof(double) * 2 * TT_DET_PARTS);
     A((void**)&c->d_part_chg, sizeof(double) * 2 * std::max<int64_t>(TT_DET_PARTS, c->nmax));
     A((void**)&c->d_det_bcnt, sizeof(int32_t) * (size_t)c->J * dplan_ranges(c));
+    A((void**)&c->d_det_kv, sizeof(uint2) * (size_t)dplan_fibres(c));
   }
   A((void**)&c->d_core_old, sizeof(float) * c->nmax * c->smax);
   c->changes_cap = 1024 * TT_MAX_D;

@@ -14,10 +14,10 @@
 //     plan (tt_context.cu: each group's fibres in index order). Its work items and the spans into
 //     which an item's fibres are cut are fixed by the shape alone, so every run of equal hash is
 //     cut at the same places and each piece summed in FP32 in the same order on every call, on any
-//     device and with any vector width. Each piece's sum becomes the integer round(sum 2^S) (an
-//     integer conversion of the float bits, ties away from zero) and is added to the int64 sketch
-//     by 64-bit integer atomics, which are associative: the result does not depend on the order in
-//     which the adds land;
+//     device and with any vector width. Each piece's sum becomes the integer round(sum 2^S)
+//     (products with powers of two, then the hardware conversion to int64, ties to even) and is
+//     added to the int64 sketch by 64-bit integer atomics, which are associative: the result does
+//     not depend on the order in which the adds land;
 //   - k_fixed_to_float: Y_k = float(sum 2^-S).
 // A piece's sum has the FP32 rounding of the fast path's run sums; its conversion adds at most
 // 2^-(S+1), far below that for the data of this library. The integer total stays below 2^61 in
@@ -112,6 +112,83 @@ static int det_spans(const tt_ctx* c) {
   return 8 * fibre_geom(fb, vb, det_m(MODE0, vpf, vb / EB, vb)).fpi;
 }
 
+// c-segments per output column, fixed by the shape (not by the device, the vector width, the
+// batch or whether a sweep runs beside): what the fast path picks for 152 SMs inside a sweep
+// (mode 0: 1216 segments; modes >= 1: 1216 / column groups of four), and at least one segment
+// per 2048 c groups
+static int det_nseg(const tt_ctx* c, bool mode0, int ncol) {
+  const int nseg = mode0 ? 1216 : std::max(1, 1216 / ((ncol + 3) / 4));
+  return std::max(nseg, (c->J + 2047) / 2048);
+}
+
+// Modes >= 1 on the column kernel (G = 2 columns per item, int64 copies, S entries in flight,
+// MV vectors per lane): the same c-segments and spans as det_gather_launch, so the same bits;
+// *done = false (nothing launched) when the shared memory does not allow two CTAs per SM.
+template <int DT, int VB, int S, int MV>
+static int det_cols_launch(tt_ctx* c, const void* A, const float* scales, int k, unsigned long long* Yq, bool* done) {
+  constexpr int G = 2, THREADS = 256;
+  constexpr int EB = TtElem<DT>::bytes;
+  const int64_t fiber_bytes = (int64_t)c->n[0] * EB;
+  GArgs a{};
+  a.A = (const char*)A;
+  a.scales = scales;
+  a.h0 = c->d_h;
+  a.v0 = c->d_v;
+  a.plan = c->d_rplan[k];
+  a.ulist = c->d_ulist[k];
+  a.ustart = c->d_ustart[k];
+  a.ucount = c->d_ucount[k];
+  a.Yq = Yq;
+  a.det_S = c->d_det_misc + 1;
+  a.J = c->J;
+  a.n0 = (int)c->n[0];
+  a.ncol = (int)c->n[k];
+  a.col_fibres = c->stride[k] / c->n[0];
+  a.total_bytes = c->N * EB;
+  a.fg = fibre_geom(fiber_bytes, VB, 1);
+  a.nseg = det_nseg(c, false, a.ncol);
+  a.segmax = (c->J + a.nseg - 1) / a.nseg + 1;
+  a.nch = det_spans<DT, false>(c);
+  const size_t smem = gather_ring_bytes(true, THREADS / 32, S * MV, VB) +
+                      sizeof(int64_t) * (size_t)G * (c->J + TT_YPAD) + sizeof(int) * (2 * (size_t)a.segmax + 1);
+  if (smem > 113 * 1024) return TT_OK;
+  auto kern = k_unfold_cols<DT, VB, S, MV, G, true>;
+  TT_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int items = (a.ncol + G - 1) / G * a.nseg;
+  kern<<<std::max(1, items), THREADS, smem, c->stream>>>(a);
+  TT_LAUNCH(c, "k_unfold_cols (deterministic)");
+  *done = true;
+  return TT_OK;
+}
+
+// The column kernel's shape for VB-byte vectors: MV = the vectors per lane that cover an entry
+// of G = 2 fibres (16-byte vectors: 1 to 4; narrower ones: min(8, 16 / EPV), every lane holding
+// up to 8 or 16 entries), four entries in flight for MV <= 2 and two otherwise (registers)
+template <int DT, int VB>
+static int det_cols(tt_ctx* c, const void* A, const float* scales, int k, unsigned long long* Yq, bool* done) {
+  *done = false;
+  if constexpr (VB >= 4 && VB >= TtElem<DT>::bytes) {
+    constexpr int EPV = TtVec<DT, VB>::EPV;
+    constexpr int MV_MAX = VB == 16 ? 4 : (16 / EPV < 8 ? 16 / EPV : 8);
+    const int vpf = (int)((int64_t)c->n[0] * TtElem<DT>::bytes / VB);
+    const int mv = (2 * vpf + 31) / 32;
+    if (mv > MV_MAX || mv * EPV > 16) return TT_OK;  // at most 16 elements per lane
+    if constexpr (VB == 16) {
+      if (mv == 1) return det_cols_launch<DT, VB, 4, 1>(c, A, scales, k, Yq, done);
+      if constexpr (2 * EPV <= 16)
+        if (mv == 2) return det_cols_launch<DT, VB, 4, 2>(c, A, scales, k, Yq, done);
+      if constexpr (3 * EPV <= 16)
+        if (mv == 3) return det_cols_launch<DT, VB, 2, 3>(c, A, scales, k, Yq, done);
+      if constexpr (4 * EPV <= 16)
+        if (mv == 4) return det_cols_launch<DT, VB, 2, 4>(c, A, scales, k, Yq, done);
+      return TT_OK;
+    } else {
+      return det_cols_launch<DT, VB, 2, MV_MAX>(c, A, scales, k, Yq, done);
+    }
+  }
+  return TT_OK;
+}
+
 // The deterministic gather of mode k into the int64 sketch Yq: the fast path's vector gather
 // (tt_gather.cuh) with VB-byte vectors, M per lane and S fibres in flight per slot.
 template <int DT, int VB, int M, bool MODE0>
@@ -134,10 +211,7 @@ static int det_gather_launch(tt_ctx* c, const void* A, const float* scales, int 
   a.col_fibres = MODE0 ? 0 : c->stride[k] / c->n[0];
   a.total_bytes = c->N * TtElem<DT>::bytes;
   a.fg = fibre_geom((int64_t)c->n[0] * TtElem<DT>::bytes, VB, M);
-  // items and spans fixed by the shape (not by the device, the vector width, the batch or
-  // whether a sweep runs beside): c-segments as the fast path picks for 152 SMs inside a sweep,
-  // and as many spans per item as the widest vectors give fibre slots per CTA
-  a.nseg = std::max(std::max(1, 1216 / a.ncol), (c->J + 2047) / 2048);
+  a.nseg = det_nseg(c, MODE0, a.ncol);
   a.segmax = (c->J + a.nseg - 1) / a.nseg + 1;
   a.nch = det_spans<DT, MODE0>(c);
   const size_t smem = gather_ring_bytes(VB >= 4, THREADS / 32, S * M, VB) + sizeof(int64_t) * (MODE0 ? 0 : c->J) +
@@ -153,6 +227,11 @@ static int det_gather_launch(tt_ctx* c, const void* A, const float* scales, int 
 
 template <int DT, int VB, bool MODE0>
 static int det_gather_vb(tt_ctx* c, const void* A, const float* scales, int k, unsigned long long* Yq) {
+  if constexpr (!MODE0) {
+    bool done = false;
+    TT_TRY((det_cols<DT, VB>(c, A, scales, k, Yq, &done)));
+    if (done) return TT_OK;
+  }
   if constexpr (VB >= 4 && VB >= TtElem<DT>::bytes) {
     constexpr int EPV = TtVec<DT, VB>::EPV;
     const int vpf = (int)(c->n[0] * TtElem<DT>::bytes / VB);

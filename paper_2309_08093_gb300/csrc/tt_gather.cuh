@@ -361,6 +361,219 @@ __global__ void __launch_bounds__(256, 2) k_unfold_gather(GArgs a) {
   }
 }
 
+// ---------------------------------------------------------------------------------------------
+// modes >= 1, G columns at once. The plan of mode k lists the rest fibres r by tail hash c_r and
+// is the same for every output column i_k, so one work item takes G neighbouring columns
+// (i_k = G g .. G g + G - 1) and one c-segment: a warp walks its slice of the segment and, per plan
+// entry r, gathers the G fibres A(:, r, i_k) (neighbours in memory for mode 1). Lane l holds the
+// MV vectors v = l + 32 m of the G * vpf vectors of an entry (column v / vpf, piece v % vpf), keeps
+// S entries in flight with cp.async and sums runs of equal c in registers; a run's end (the same
+// for every lane: all of them walk the same entries) adds coef(i_0) * sum into bucket
+// (c + h_0(i_0)) mod J of the CTA's copy of the column. The G column copies are flushed to Y_k
+// with 16-byte atomics at the end of the item.
+// DET: as in k_unfold_gather, int64 column copies and fixed-point flushes; an item's entries are
+// cut into a.nch spans (span t on warp t mod 8), the same spans as k_unfold_gather<DET> takes for
+// each of the columns, so the two kernels give the same bits.
+template <int DT, int VB, int S, int MV, int G, bool DET = false>
+__global__ void __launch_bounds__(256, 2) k_unfold_cols(GArgs a) {
+  constexpr int EPV = TtVec<DT, VB>::EPV;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int J = a.J;
+  const int T = blockDim.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = T >> 5;
+  unsigned char* ring = smraw;                                                // nw x S x MV x 32 x VB
+  float* Ys = reinterpret_cast<float*>(ring + gather_ring_bytes(true, nw, S * MV, VB));  // G x J
+  unsigned long long* Yqs = reinterpret_cast<unsigned long long*>(Ys);     // G x J (DET)
+  int* sstart = reinterpret_cast<int*>(Ys + (size_t)G * (J + TT_YPAD) * (DET ? 2 : 1));  // segmax + 1 (relative)
+  int* scval = sstart + a.segmax + 1;                                        // segmax
+  if constexpr (DET) {
+    if (a.det_S[1] != 0) return;  // {S, A not finite}: the sketches are written as NaN afterwards
+  }
+  const int dS = DET ? *a.det_S : 0;
+  const int U_ = *a.ucount;
+  const int vpf = a.fg.vpf;
+  unsigned char* myring = ring + ((size_t)warp * S * MV * 32 + lane) * VB;
+  // this lane's vectors of an entry and their coefficients (fixed for the whole kernel)
+  int vg[MV], vp[MV];
+  float coefr[MV][EPV];
+  int h0r[MV][EPV];
+#pragma unroll
+  for (int m = 0; m < MV; ++m) {
+    const int v = lane + 32 * m;
+    const bool in = v < G * vpf;
+    vg[m] = in ? v / vpf : 0;
+    vp[m] = in ? v - vg[m] * vpf : 0;
+#pragma unroll
+    for (int e = 0; e < EPV; ++e) {
+      const int i0 = vp[m] * EPV + e;
+      float cf = 0.f;
+      int hh = 0;
+      if (in) {
+        cf = __ldg(a.v0 + i0) < 0 ? -1.f : 1.f;
+        if (a.scales) cf *= __ldg(a.scales + i0);
+        hh = __ldg(a.h0 + i0);
+      }
+      coefr[m][e] = cf;
+      h0r[m][e] = hh;
+    }
+  }
+  const int ncolg = (a.ncol + G - 1) / G;
+  const int items = ncolg * a.nseg;
+  for (int item = blockIdx.x; item < items; item += gridDim.x) {
+    const int colg = item / a.nseg, seg = item - colg * a.nseg;
+    const int col0 = colg * G;
+    const int ua = (int)((int64_t)U_ * seg / a.nseg), ub = (int)((int64_t)U_ * (seg + 1) / a.nseg);
+    const int nu = ub - ua;
+    if (nu <= 0) continue;
+    const int64_t e0 = __ldg(a.ustart + ua);
+    for (int i = threadIdx.x; i <= nu; i += T) {
+      sstart[i] = (int)(__ldg(a.ustart + ua + i) - e0);
+      if (i < nu) scval[i] = __ldg(a.ulist + ua + i);
+    }
+    for (int i = threadIdx.x; i < G * (J + TT_YPAD); i += T) {
+      if constexpr (DET) Yqs[i] = 0ull; else Ys[i] = 0.f;
+    }
+    __syncthreads();
+    const int ne = sstart[nu];
+    const int nch = DET ? a.nch : nw;
+    const uint32_t* plan = a.plan + e0;
+    bool vok[MV];
+    const char* Alane[MV];
+#pragma unroll
+    for (int m = 0; m < MV; ++m) {
+      vok[m] = lane + 32 * m < G * vpf && col0 + vg[m] < a.ncol;
+      Alane[m] = a.A + ((int64_t)(col0 + vg[m]) * a.col_fibres) * a.fg.fiber_bytes + (int64_t)vp[m] * VB;
+    }
+    int chk = warp;
+    do {  // once in the fast path (a plain block)
+      const int sb = (int)((int64_t)ne * chk / nch), se = (int)((int64_t)ne * (chk + 1) / nch);
+      if (sb < se) {
+        int lo2 = 0, hi2 = nu;  // run containing sb: sstart[lo2] <= sb < sstart[hi2]
+        while (hi2 - lo2 > 1) {
+          const int mid = (lo2 + hi2) >> 1;
+          if (sstart[mid] <= sb) lo2 = mid; else hi2 = mid;
+        }
+        const int count = se - sb;
+        int cu = lo2;
+        int next_b = sstart[cu + 1];
+        float acc[MV][EPV];
+#pragma unroll
+        for (int m = 0; m < MV; ++m)
+#pragma unroll
+          for (int e = 0; e < EPV; ++e) acc[m][e] = 0.f;
+        auto flush = [&]() {
+          const int cv = scval[cu];
+#pragma unroll
+          for (int m = 0; m < MV; ++m) {
+            if (vok[m]) {
+              if constexpr (DET) {
+                unsigned long long* yc = Yqs + (size_t)vg[m] * (J + TT_YPAD);
+#pragma unroll
+                for (int e = 0; e < EPV; ++e)
+                  atomicAdd(yc + tt_modj(cv + h0r[m][e], J), (unsigned long long)det_fixed(coefr[m][e] * acc[m][e], dS));
+              } else {
+                float* yc = Ys + (size_t)vg[m] * (J + TT_YPAD);
+#pragma unroll
+                for (int e = 0; e < EPV; ++e) atomicAdd(yc + tt_modj(cv + h0r[m][e], J), coefr[m][e] * acc[m][e]);
+              }
+            }
+#pragma unroll
+            for (int e = 0; e < EPV; ++e) acc[m][e] = 0.f;
+          }
+        };
+        // pipeline: stage q of the ring holds entry j with j % S == q (MV pieces per lane)
+        uint32_t wcur[S], wnext[S];
+#pragma unroll
+        for (int q = 0; q < S; ++q) {
+          wcur[q] = (q < count) ? __ldg(plan + sb + q) : 0u;
+          if (q < count) {
+            const int64_t fo = (int64_t)(wcur[q] & 0x7FFFFFFFu) * a.fg.fiber_bytes;
+#pragma unroll
+            for (int m = 0; m < MV; ++m)
+              if (vok[m]) cp_async_vec(myring + (size_t)(q * MV + m) * 32 * VB, Alane[m] + fo, VB);
+          }
+          cp_async_commit();
+          wnext[q] = (S + q < count) ? __ldg(plan + sb + S + q) : 0u;
+        }
+        for (int j0 = 0; j0 < count; j0 += S) {
+#pragma unroll
+          for (int q = 0; q < S; ++q) {
+            const int j = j0 + q;
+            if (j < count) {
+              typename TtVec<DT, VB>::Raw raw[MV];
+              cp_async_wait<S - 1>();
+#pragma unroll
+              for (int m = 0; m < MV; ++m) {
+                if (vok[m]) {
+                  const unsigned char* src = myring + (size_t)(q * MV + m) * 32 * VB;
+                  if constexpr (VB == 16) {
+                    const uint4 w4 = *reinterpret_cast<const uint4*>(src);
+                    raw[m].w[0] = w4.x; raw[m].w[1] = w4.y; raw[m].w[2] = w4.z; raw[m].w[3] = w4.w;
+                  } else {
+#pragma unroll
+                    for (int t2 = 0; t2 < TtVec<DT, VB>::W; ++t2) raw[m].w[t2] = reinterpret_cast<const uint32_t*>(src)[t2];
+                  }
+                } else {
+                  raw[m] = TtVec<DT, VB>::zero();
+                }
+              }
+              const int jr = sb + j;
+              if (jr >= next_b) {
+                flush();
+                do {
+                  ++cu;
+                  next_b = sstart[cu + 1];
+                } while (jr >= next_b);
+              }
+              const float sg = (wcur[q] >> 31) ? -1.f : 1.f;
+#pragma unroll
+              for (int m = 0; m < MV; ++m) TtVec<DT, VB>::fma_into(raw[m], sg, acc[m]);
+              const int jn = j + S;
+              if (jn < count) {
+                const int64_t fo = (int64_t)(wnext[q] & 0x7FFFFFFFu) * a.fg.fiber_bytes;
+#pragma unroll
+                for (int m = 0; m < MV; ++m)
+                  if (vok[m]) cp_async_vec(myring + (size_t)(q * MV + m) * 32 * VB, Alane[m] + fo, VB);
+              }
+              cp_async_commit();
+              wcur[q] = wnext[q];
+              wnext[q] = (jn + S < count) ? __ldg(plan + sb + jn + S) : 0u;
+            }
+          }
+        }
+        cp_async_wait<0>();
+        flush();
+      }
+      chk += nw;
+    } while (DET && chk < nch);
+    __syncthreads();
+    // flush the G column copies
+    if constexpr (DET) {
+      for (int g = 0; g < G && col0 + g < a.ncol; ++g) {
+        unsigned long long* yc = a.Yq + (int64_t)J * (col0 + g);
+        const unsigned long long* ys = Yqs + (size_t)g * (J + TT_YPAD);
+        for (int b = threadIdx.x; b < J; b += T)
+          if (ys[b]) atomicAdd(yc + b, ys[b]);
+      }
+    } else {
+      for (int g = 0; g < G && col0 + g < a.ncol; ++g) {
+        float* yc = a.Y + (int64_t)J * (col0 + g);
+        const float* ys = Ys + (size_t)g * (J + TT_YPAD);
+        if (a.y_vec4) {
+          for (int b = threadIdx.x * 4; b < J; b += T * 4) {
+            const float4 v4 = make_float4(ys[b], ys[b + 1], ys[b + 2], ys[b + 3]);
+            if (v4.x != 0.f || v4.y != 0.f || v4.z != 0.f || v4.w != 0.f) atomicAdd(reinterpret_cast<float4*>(yc + b), v4);
+          }
+        } else {
+          for (int b = threadIdx.x; b < J; b += T)
+            if (ys[b] != 0.f) atomicAdd(yc + b, ys[b]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // the widest vector (16, 8, 4, 2 or 1 bytes) that both the fibre length and A's base allow
 static inline int pick_vb(int64_t fiber_bytes, uintptr_t base, int elem_bytes) {
   for (int vb = 16; vb >= elem_bytes; vb >>= 1)

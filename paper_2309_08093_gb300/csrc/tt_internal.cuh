@@ -152,6 +152,7 @@ struct tt_ctx {
   int* d_det_misc = nullptr;        // [0] bits of max |A|, [1] fixed-point exponent S, [2] A not finite
   int64_t* d_y64 = nullptr;         // int64 data-sketch accumulators, mode k at yoff[k]
   int32_t* d_det_bcnt = nullptr;    // deterministic plans: per range and key, counts then first slots
+  uint2* d_det_kv = nullptr;        // deterministic plans: (key, plan entry) of every rest fibre
   void* d_gram_part = nullptr;      // TT_DET_KSPLIT K-chunk partials of the Gram (FP32 or FP64)
   double* d_part_err = nullptr;     // per-CTA partial sums of the relative error (2 per CTA)
   double* d_part_chg = nullptr;     // per-CTA partial sums of the change norms (2 per CTA)

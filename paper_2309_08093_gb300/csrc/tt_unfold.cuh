@@ -97,20 +97,14 @@ __device__ __forceinline__ float tt_fma_e4m3(unsigned short x, unsigned short s,
 // FP16 bits of a sign s = +-1
 __device__ __forceinline__ unsigned short tt_f16_sign(float s) { return s < 0.f ? 0xBC00 : 0x3C00; }
 
-// round(x 2^S) as an int64, from the float bits: x = mant 2^e2; ties rounded away from zero
+// round(x 2^S) as an int64, ties to even: x 2^S formed by one or two products with powers of two
+// (exact, except a product below 2^-126 in magnitude, which rounds to 0 either way), then one
+// hardware conversion (cvt.rni.s64.f32). |x| 2^S < 2^62 by the choice of S.
 __device__ __forceinline__ long long det_fixed(float x, int S) {
-  const uint32_t b = __float_as_uint(x);
-  const uint32_t ex = (b >> 23) & 0xFFu;
-  const long long mant = (long long)((b & 0x7FFFFFu) | (ex ? 0x800000u : 0u));
-  const int shift = (ex ? (int)ex : 1) - 150 + S;
-  long long v;
-  if (shift >= 0)
-    v = mant << shift;  // below 2^62 by the choice of S
-  else if (shift > -40)
-    v = (mant + (1ll << (-shift - 1))) >> (-shift);
-  else
-    v = 0;
-  return (b >> 31) ? -v : v;
+  const int s1 = S < -126 ? -126 : (S > 126 ? 126 : S);
+  float t = x * __int_as_float((s1 + 127) << 23);
+  if (S != s1) t *= __int_as_float((S - s1 + 127) << 23);
+  return __float2ll_rn(t);
 }
 
 // 16-byte copy global -> shared of `bytes` (1..16) valid source bytes, the rest of the 16
