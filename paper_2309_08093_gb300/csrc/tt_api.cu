@@ -135,6 +135,7 @@ static int sweep_body(tt_ctx* c, const void* A, const float* scales, float* cons
       float* ys[TT_MAX_D];
       for (int k = 0; k < d; ++k) ys[k] = c->d_Yall + c->yoff[k];
       rc = tt_launch_unfold_det(c, A, scales, (1u << d) - 1u, ys, c->ev_y);
+      if (rc == TT_OK && !c->capture_mode) c->det_scale_reuse = true;
     }
     for (int k = 0; k < d && rc == TT_OK && !c->det; ++k) {
       rc = tt_launch_unfold(c, A, scales, k, c->d_Yall + c->yoff[k]);
@@ -218,9 +219,9 @@ static int run_sweeps_body(tt_ctx* c, const void* A, const float* scales, float*
 
 static int run_sweeps(tt_ctx* c, const void* A, const float* scales, float* const* cores, int nsweeps,
                       uint64_t first_sweep, double* rel_change_out, double* rel_error_out) {
-  c->y_reuse = false;  // data sketches are reused within one call only (A may change between calls)
+  c->y_reuse = c->det_scale_reuse = false;  // reused within one call only (A may change between calls)
   const int rc = run_sweeps_body(c, A, scales, cores, nsweeps, first_sweep, rel_change_out, rel_error_out);
-  c->y_reuse = false;
+  c->y_reuse = c->det_scale_reuse = false;
   return rc;
 }
 

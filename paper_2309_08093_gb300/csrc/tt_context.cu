@@ -562,8 +562,8 @@ int tt_ensure_rplan(tt_ctx* c, int k) {
 int tt_ensure_plan0(tt_ctx* c) { return tt_ensure_rplan(c, 0); }
 
 int tt_prepare_next_draw(tt_ctx* c, uint64_t sweep) {
-  // (the deterministic mode builds its draw, tables and plans, at the sweep's start)
-  if (c->det || c->capture_mode || c->user_tables || (c->flags & TT_FLAG_FIXED_SKETCH)) return TT_OK;
+  // (the deterministic mode's plans too: tt_ensure_rplan builds them in index order)
+  if (c->capture_mode || c->user_tables || (c->flags & TT_FLAG_FIXED_SKETCH)) return TT_OK;
   bool ready = c->spare.tables_valid && c->spare.tables_sweep == sweep;
   for (int k = 0; k < c->d; ++k) ready = ready && c->spare.rplan_valid[k];
   if (ready) return TT_OK;

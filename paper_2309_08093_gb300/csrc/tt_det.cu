@@ -261,7 +261,8 @@ static int det_gather_mode(tt_ctx* c, const void* A, const float* scales, int k,
   return k == 0 ? det_gather<DT, true>(c, A, scales, k, Yq) : det_gather<DT, false>(c, A, scales, k, Yq);
 }
 
-int tt_launch_unfold_det(tt_ctx* c, const void* A, const float* scales, unsigned mask, float* const* Y, cudaEvent_t* ev) {
+// S (and the non-finite flag) from max |A|: k_det_absmax, then k_det_exp, into d_det_misc
+static int det_scale(tt_ctx* c, const void* A, const float* scales) {
   const int sms = tt_sm_count();
   TT_CUDA(c, cudaMemsetAsync(c->d_det_misc, 0, 3 * sizeof(int), c->stream));
   const int ablocks = (int)std::min<int64_t>((c->N + 255) / 256, (int64_t)sms * 8);
@@ -274,6 +275,12 @@ int tt_launch_unfold_det(tt_ctx* c, const void* A, const float* scales, unsigned
   TT_LAUNCH(c, "k_det_absmax");
   k_det_exp<<<1, 1, 0, c->stream>>>((const unsigned*)c->d_det_misc, c->N, c->d_det_misc + 1, c->d_det_misc + 2);
   TT_LAUNCH(c, "k_det_exp");
+  return TT_OK;
+}
+
+int tt_launch_unfold_det(tt_ctx* c, const void* A, const float* scales, unsigned mask, float* const* Y, cudaEvent_t* ev) {
+  const int sms = tt_sm_count();
+  if (!c->det_scale_reuse || c->capture_mode) TT_TRY(det_scale(c, A, scales));
   for (int k = 0; k < c->d; ++k) {
     if (!(mask & (1u << k))) continue;
     TT_TRY(tt_ensure_rplan(c, k));  // deterministic plans (all modes on the first call of a draw)

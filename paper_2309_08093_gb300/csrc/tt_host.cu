@@ -182,16 +182,16 @@ extern "C" int tt_prox_als_sweep_host_async(tt_ctx* c, const void* A_host, const
   TT_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_copied[b], 0));
   const void* A = c->d_A_stage[b];
   const float* sc = scales_host ? c->d_scales_stage[b] : nullptr;
-  c->y_reuse = false;  // the sketches of this call's tensor (reused by its later sweeps)
+  c->y_reuse = c->det_scale_reuse = false;  // the sketches (and scale) of this call's tensor, reused by its later sweeps
   for (int t = 0; t < nsweeps; ++t) {
     double* slots = rel_change_out ? c->d_changes + (size_t)2 * c->d * t : nullptr;
     const int rc = tt_one_sweep(c, A, sc, c->d_cores_stage, first_sweep + t, slots);
     if (rc != TT_OK) {
-      c->y_reuse = false;
+      c->y_reuse = c->det_scale_reuse = false;
       return rc;
     }
   }
-  c->y_reuse = false;
+  c->y_reuse = c->det_scale_reuse = false;
   if (rel_error_out) TT_TRY(tt_launch_rel_error(c, A, sc, c->d_cores_stage, c->d_err_acc));
   TT_CUDA(c, cudaEventRecord(c->ev_consumed[b], c->stream));
   c->consumed_recorded[b] = true;

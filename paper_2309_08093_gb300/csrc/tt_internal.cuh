@@ -185,6 +185,10 @@ struct tt_ctx {
   // that does not change from sweep to sweep (TT_FLAG_FIXED_SKETCH or tables set by the caller):
   // later sweeps of the call reuse them. Cleared at the start and the end of every call.
   bool y_reuse = false;
+  // Deterministic mode: the fixed-point scale S in d_det_misc is that of the A of the running
+  // multi-sweep call (set by its first sweep outside graph capture; cleared with y_reuse), so the
+  // later sweeps skip the max |A| pass.
+  bool det_scale_reuse = false;
 
   // least bytes of A per work item of a data-sketch launch (0: items sized for one tensor alone,
   // about one per CTA slot). Contexts of a batch set it, so that a small tensor's launch takes few

@@ -150,6 +150,39 @@ def test_det_sweeps_repeat_bit_for_bit_and_match_the_oracle():
     assert abs(ch1[-1] - ref_ch[-1]) <= 1e-3 * ref_ch[-1] + 1e-7
 
 
+def test_det_multi_sweep_call_matches_single_sweep_calls_and_rescales_per_call():
+    """A multi-sweep call computes the fixed-point scale of A in its first sweep and reuses it: its
+    cores have the same bits as the same sweeps made one call at a time. A later call on another
+    tensor (2^40 A, whose entries at the first tensor's scale would leave the int64 range) gets
+    that tensor's scale: the same bits as a fresh context's sweep on it."""
+    dims, ranks, J, seed = (24, 20, 18, 16), (1, 4, 5, 4, 1), 512, 78
+    a = synth.add_noise(synth.contract_cores(synth.random_tt(dims, ranks, 5)), 1e-2, np.random.default_rng(8))
+    flat, _, _ = synth.quantize(a, "f32")
+    init = synth.random_tt(dims, ranks, 9)
+    Ad = lib.device_tensor(flat, "f32")
+    Abig = Ad * 2.0 ** 40
+
+    def ctx():
+        return lib.Context(dims, ranks, J, 1e-3, seed, "f32", flags=DET)
+
+    c1, c3 = ctx(), ctx()
+    one, three = lib.device_cores(init), lib.device_cores(init)
+    c1.tt_prox_als_sweep(Ad, one, 3, 0, rel_change=False)
+    for t in range(3):
+        c3.tt_prox_als_sweep(Ad, three, 1, t, rel_change=False)
+    torch.cuda.synchronize()
+    assert all(torch.equal(x, y) for x, y in zip(one, three))
+    after = [x.clone() for x in one]
+    c1.tt_prox_als_sweep(Abig, one, 1, 3, rel_change=False)
+    fresh = ctx()
+    fresh.tt_prox_als_sweep(Abig, after, 1, 3, rel_change=False)
+    torch.cuda.synchronize()
+    assert all(bool(torch.isfinite(x).all()) for x in one)
+    assert all(torch.equal(x, y) for x, y in zip(one, after))
+    for c in (c1, c3, fresh):
+        c.close()
+
+
 def test_det_sigma_zero_sinc_runs_repeat_bit_for_bit():
     """The sigma = 0 sinc case of Sec. 5 (m = 45, FP64 update): without fixed orders its 100-sweep
     errors differed between runs of one seeded test; here 30 sweeps run twice give the same bits."""
