@@ -1,14 +1,16 @@
 """The deterministic mode (TT_FLAG_DETERMINISTIC): fixed summation orders, so that repeated runs
 of the same seeded call give the same bits, and the same parity with the CPU FP64 oracle as the
-fast path. Its data sketch Y_k = S A_(k)^T (Alg. 1, Eqs. (eqn_h), (eqn_v)) is accumulated in 64-bit
+fast path. Its data sketch Y_k = S A_(k)^T (Alg. 1, Eqs. (eqn_h), (eqn_v)) sums each run of fibres
+with equal hash in index order over work spans fixed by the shape and adds the run sums in 64-bit
 fixed point; the Gram's K-chunks, the relative error and the change norms are summed in fixed
 orders, and the CountSketch of the cores adds its entries in index order.
 
 Checks: the data sketch against the oracle in every storage type (relative Frobenius and
-entrywise, as for the fast path), bit-identical on a second call; the interface sketch against
-the oracle; whole sweeps run twice on two contexts (FP32 update and sigma = 0 FP64 update, the
-latter on the paper's sinc tensor for 30 sweeps) agree bit for bit in cores, relative errors and
-rel-changes, and with the oracle."""
+entrywise, as for the fast path), bit-identical on a second call and for the tensor placed off
+the 16-byte grid; the interface sketch against the oracle; a multi-sweep call against single-sweep
+calls and a call on a rescaled tensor; whole sweeps run twice on two contexts (FP32 update and
+sigma = 0 FP64 update, the latter on the paper's sinc tensor for 30 sweeps) agree bit for bit in
+cores, relative errors and rel-changes, and with the oracle."""
 import numpy as np
 import pytest
 
