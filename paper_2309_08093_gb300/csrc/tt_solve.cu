@@ -1897,12 +1897,14 @@ __global__ void __launch_bounds__(256, 2) k_rel_error_stream(const void* __restr
         }
       }
       float2 fe2 = make_float2(0.f, 0.f), fa2 = make_float2(0.f, 0.f);
+      const bool full = f0 + FT <= M0;  // every fibre of the tile exists (all tiles but the last)
 #pragma unroll
       for (int u = 0; u < REL_U; ++u) {
-        if (f0 + pi + P * u >= M0) continue;  // past the last fibre (stale buffer entries)
+        if (!full && f0 + pi + P * u >= M0) continue;  // past the last fibre (stale buffer entries)
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          const float2 xv = make_float2(x[u][2 * h] * sc[2 * h], x[u][2 * h + 1] * sc[2 * h + 1]);
+          float2 xv = make_float2(x[u][2 * h], x[u][2 * h + 1]);
+          if constexpr (DT == TT_FP8E4M3) xv = make_float2(xv.x * sc[2 * h], xv.y * sc[2 * h + 1]);  // slice scales
           const float2 dl = make_float2(xv.x - r2[u][h].x, xv.y - r2[u][h].y);
           fe2 = tt_ffma2(dl, dl, fe2);
           fa2 = tt_ffma2(xv, xv, fa2);
