@@ -21,6 +21,17 @@ __device__ __forceinline__ float2 tt_ffma2(float2 a, float2 b, float2 c) {
   return d;
 }
 
+// Two FP32 products in one instruction (mul.rn.f32x2): d.x = a.x * b.x, d.y = a.y * b.y.
+__device__ __forceinline__ float2 tt_fmul2(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+
 #define TT_MAX_D 8
 #define TT_MAX_S 160      // largest r[k]*r[k+1] of the register solve (and largest single rank)
 #define TT_MAX_S_LARGE 512  // largest r[k]*r[k+1] of the one-CTA Cholesky solve

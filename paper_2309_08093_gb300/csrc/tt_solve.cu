@@ -17,6 +17,7 @@
 #include <stdio.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "tt_internal.cuh"
 
@@ -1776,7 +1777,7 @@ __device__ __forceinline__ void smem_load4(const unsigned char* p, float* x) {
   }
 }
 
-constexpr int REL_U = 8;   // fibres per thread per tile
+constexpr int REL_U = 4;   // fibres per thread per tile (three CTAs per SM at 100-entry FP32 fibres)
 constexpr int REL_NS = 3;  // tiles in flight per CTA
 
 __device__ __forceinline__ bool rel_mbar_try(uint32_t addr, uint32_t parity) {
@@ -1874,11 +1875,9 @@ __global__ void __launch_bounds__(256, 2) k_rel_error_stream(const void* __restr
       float x[REL_U][4];
       float2 r2[REL_U][2];
 #pragma unroll
-      for (int u = 0; u < REL_U; ++u) {
-        smem_load4<DT>(tA + ((size_t)(pi + P * u) * n0 + 4 * qi) * ES, x[u]);
-        r2[u][0] = r2[u][1] = make_float2(0.f, 0.f);
-      }
-      for (int al0 = 0; al0 < r1p; al0 += 4) {
+      for (int u = 0; u < REL_U; ++u) smem_load4<DT>(tA + ((size_t)(pi + P * u) * n0 + 4 * qi) * ES, x[u]);
+      // ranks al0 .. al0 + 3; the first block's first rank starts the sums with a product (r1 >= 1)
+      auto ranks = [&](int al0, auto first) {
         float4 w[REL_U];
 #pragma unroll
         for (int u = 0; u < REL_U; ++u) w[u] = *reinterpret_cast<const float4*>(tR + (size_t)(pi + P * u) * r1p + al0);
@@ -1891,11 +1890,18 @@ __global__ void __launch_bounds__(256, 2) k_rel_error_stream(const void* __restr
           for (int u = 0; u < REL_U; ++u) {
             const float ww = aa == 0 ? w[u].x : aa == 1 ? w[u].y : aa == 2 ? w[u].z : w[u].w;
             const float2 w2 = make_float2(ww, ww);
-            r2[u][0] = tt_ffma2(glo, w2, r2[u][0]);
-            r2[u][1] = tt_ffma2(ghi, w2, r2[u][1]);
+            if (decltype(first)::value && aa == 0) {
+              r2[u][0] = tt_fmul2(glo, w2);
+              r2[u][1] = tt_fmul2(ghi, w2);
+            } else {
+              r2[u][0] = tt_ffma2(glo, w2, r2[u][0]);
+              r2[u][1] = tt_ffma2(ghi, w2, r2[u][1]);
+            }
           }
         }
-      }
+      };
+      ranks(0, std::true_type{});
+      for (int al0 = 4; al0 < r1p; al0 += 4) ranks(al0, std::false_type{});
       float2 fe2 = make_float2(0.f, 0.f), fa2 = make_float2(0.f, 0.f);
       const bool full = f0 + FT <= M0;  // every fibre of the tile exists (all tiles but the last)
 #pragma unroll
