@@ -1024,8 +1024,13 @@ def main():
         cores_h = [torch.from_numpy(np.ascontiguousarray(np.asarray(g, np.float32).ravel(order="F"))).pin_memory().numpy()
                    for g in p.init_cores]
         sc_h = np.ascontiguousarray(p.scales, dtype=np.float32) if p.scales is not None else None
-        ne = max(3, min(20, args.steps))
+        ne = max(3, min(40, args.steps))
         ctx.tt_prox_als_sweep_host(A_h, cores_h, 1, 0, scales_host=sc_h)  # warm (allocates staging)
+        # warm the asynchronous path too (its copy stream, events and buffers); its output arrays
+        # stay referenced until the synchronisation
+        warm = [ctx.tt_prox_als_sweep_host_async(A_h, cores_h, 1, 0, scales_host=sc_h) for _ in range(3)]
+        ctx.tt_host_sync()
+        del warm
         # one asynchronous call per step: each copies the step's tensor and cores in, sweeps, takes
         # the relative error and copies the cores and the error out; the next step's tensor copy
         # runs beside this step's sweep. One synchronisation at the end of the timed steps.
