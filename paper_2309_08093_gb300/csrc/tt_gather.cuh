@@ -1,7 +1,9 @@
-// The vector gather of the data sketch (Alg. 1 part (a); the regrouping by mode-0 fibres is
-// described in tt_unfold.cu): fibres of a per-sweep plan staged with cp.async in VB-byte vectors
-// and summed in registers run by run. Shared by tt_unfold.cu (FP32 flushes) and tt_det.cu (the
-// deterministic mode's 64-bit fixed-point flushes, DET = true).
+// The gather kernels of the data sketch (Alg. 1 part (a); the regrouping by mode-0 fibres is
+// described in tt_unfold.cu): k_unfold_gather (one output column per work item) and
+// k_unfold_cols (G neighbouring columns per work item, modes >= 1). Fibres of a per-sweep plan are
+// staged with cp.async in VB-byte vectors and summed in registers run by run. Shared by
+// tt_unfold.cu (FP32 flushes) and tt_det.cu (the deterministic mode's 64-bit fixed-point flushes,
+// DET = true).
 #pragma once
 
 #include "tt_unfold.cuh"
