@@ -119,3 +119,36 @@ def test_batched_fixed_draw_reuses_data_sketches():
     got = lib.host_cores(cores_b[0], specs[0]["ranks"], specs[0]["dims"])
     d = np.linalg.norm((O.tt_full(got) - O.tt_full(ref)).ravel()) / np.linalg.norm(O.tt_full(ref).ravel())
     assert d <= 1e-4, d
+
+
+def test_batched_deterministic_repeats_and_matches_single_tensor_bits():
+    """TT_FLAG_DETERMINISTIC on every tensor of a batch: two batches over the same inputs give the
+    same bits, and so does each tensor's single-tensor deterministic sweep (its data sketch takes
+    work spans fixed by the shape, so the batch's own item sizes and the graph change nothing);
+    tensor 0 agrees with the oracle (reconstruction 1e-4, as above)."""
+    nsw = 4
+    specs = synth.batched_specs(count=4, dims_range=(6, 18), rank_range=(2, 5))
+    for sp in specs:
+        sp["flags"] = lib.TT_FLAG_DETERMINISTIC
+    As, inits, exact = _setup(specs)
+    runs = []
+    for _ in range(2):
+        cores_b = [lib.device_cores(c) for c in inits]
+        batch = lib.Batch(specs)
+        batch.tt_batch_sweep(As, cores_b, nsw, 0)
+        torch.cuda.synchronize()
+        batch.close()
+        runs.append(cores_b)
+    for i in range(len(specs)):
+        assert all(torch.equal(x, y) for x, y in zip(runs[0][i], runs[1][i])), i
+    for i, sp in enumerate(specs):
+        ctx = lib.Context(sp["dims"], sp["ranks"], sp["J"], sp["lam"], sp["seed"], sp["dtype"], flags=sp["flags"])
+        cs = lib.device_cores(inits[i])
+        ctx.tt_prox_als_sweep(As[i], cs, nsw, 0, rel_change=False)
+        torch.cuda.synchronize()
+        ctx.close()
+        assert all(torch.equal(x, y) for x, y in zip(runs[0][i], cs)), i
+    ref, _ = O.tt_ts(exact[0], inits[0], specs[0]["seed"], specs[0]["J"], specs[0]["lam"], nsw)
+    got = lib.host_cores(runs[0][0], specs[0]["ranks"], specs[0]["dims"])
+    d = np.linalg.norm((O.tt_full(got) - O.tt_full(ref)).ravel()) / np.linalg.norm(O.tt_full(ref).ravel())
+    assert d <= 1e-4, d
